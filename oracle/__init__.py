@@ -143,6 +143,8 @@ class Oracle:
         return r, len(r), len(r)
 
     def collision(self, f, rows=None, with_abs: bool = False):
+        """I_s of the rows (all by default); with_abs also returns each row's gross
+        scattering sum (the in- and out-scattering products that Eq. 2 differences)."""
         f = _f64(f)
         assert f.shape == (self.nstate,)
         r, nr, nout = self._rows(rows)

@@ -114,7 +114,9 @@ enum { OR_COLLISION = 0, OR_RATES = 1, OR_TRANSPORT = 2 };
 /*
  * One row of the channel sum, Eq. 2, for the window state with full id sid.
  *   OR_COLLISION: returns I_s = -(2pi/hbar)(1/Nq) sum g2 [G(x+w) F_abs + G(x-w) F_em]
- *                 and, if absterm, sum of |(2pi/hbar)(1/Nq) g2 [..]| over the row.
+ *                 and, if absterm, the row's gross scattering (2pi/hbar)(1/Nq) sum g2
+ *                 [G(x+w)(|f_s(1-f_p)N| + |(1-f_s)f_p(N+1)|) + G(x-w)(|f_s(1-f_p)(N+1)| +
+ *                 |(1-f_s)f_p N|)], the scale of the rounding error of any evaluation.
  *   OR_RATES:     returns 1/tau_s = (2pi/hbar)(1/Nq) sum g2 [G(x+w)(N+f_p) + G(x-w)(N+1-f_p)]
  *   OR_TRANSPORT: returns sum_c W_c F_p[alpha] for alpha = 0..2 in vec[] (f = f0)
  *                 and the row total sum_c W_c.
@@ -171,7 +173,10 @@ static double row_sum(const or_model *m, const int32_t *widx, int64_t sid, const
           const double t = g2 * (Ga * Fabs + Ge * Fem);
 #endif
           acc += t;
-          accabs += fabs(t);
+          /* gross scattering: the magnitudes of the four products that F_abs and F_em
+           * difference, i.e. the error scale of evaluating the summand in floating point */
+          accabs += g2 * (Ga * (fabs(f_s * (1.0 - f_p) * N) + fabs((1.0 - f_s) * f_p * (N + 1.0))) +
+                          Ge * (fabs(f_s * (1.0 - f_p) * (N + 1.0)) + fabs((1.0 - f_s) * f_p * N)));
         } else {
 #if ORACLE_PLANT == 5
           const double Wc = g2 * (Ga * (N + 1.0 - f_p) + Ge * (N + f_p)); /* planted: factors swapped */
