@@ -1,0 +1,424 @@
+#!/usr/bin/env python
+"""Benchmark of the e-ph collision-integral hot path on one GB300 (or N replicas).
+
+One step = one classic RK4 step of the rt-BTE (four collision-integral sweeps,
+Eq. 2) plus one three-direction transport iteration (one weighted sweep), on
+the 40^3 workload: 4 bands, 6 modes, per-band 0.3 eV window, 1.36e8 channels.
+The metric is channel evaluations per second (5 sweeps x channels per step).
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded row sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+SWEEPS_PER_STEP = 5  # 4 RK4 collision sweeps + 1 transport sweep
+LAUNCHES_PER_STEP = 13  # rk4: 1 conversion + 8 graph kernels; transport: 1 conversion + 3 kernels
+FALLBACK_HBM = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="window40")
+    ap.add_argument("--variant", default="ff")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-solve", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(name: str) -> dict:
+    if name == "window40":
+        return {"workload": "rt-BTE RK4 step + 3-direction transport iteration, 40^3 k/q grids, 4 bands, "
+                            "6 modes, per-band 0.3 eV window, sigma 8 meV, T 300 K",
+                "grid": [40, 40, 40], "bands": 4, "modes": 6, "dt_fs": 1.0}
+    if name == "tiny":
+        return {"workload": "rt-BTE RK4 step + 3-direction transport iteration, 8^3 full BZ, 2 bands, 3 modes, "
+                            "sigma 5 meV, T 300 K", "grid": [8, 8, 8], "bands": 2, "modes": 3, "dt_fs": 1.0}
+    return {"workload": name}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the GPU is busy."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        mx = max(r[1] for r in rows)
+        loaded = [r for r in rows if r[0] > 0.5 * mx] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def measured_hbm():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy burst)"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM, "fallback (6.8 TB/s)"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "device.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2511_03683_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload: str, variant: str):
+    """DRAM bytes per launch of the collision sweep from the committed ncu summary, if it
+    was captured on the current kernel source; else None."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+        e = d[f"{workload}:{variant}"]
+        if e.get("source_hash") != kernel_source_hash():
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def emit(obj):
+    print(json.dumps(obj), flush=True)
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+
+def oracle_step_sample(o, f, f0, v, rows):
+    """One bounded oracle 'step' on a row sample: four collision row-passes and one
+    transport-map row-pass (the GPU step's sweep mix)."""
+    import numpy as np
+
+    for _ in range(4):
+        o.collision(f, rows=rows)
+    o.transport_map(f0, v, np.zeros_like(v), rows=rows)
+
+
+def cpu_baseline(m, sample_every=4, reps=1):
+    import numpy as np
+
+    import oracle
+
+    o = oracle.Oracle(m)
+    f = o.window_values(m.f_hot())
+    f0 = o.window_values(m.f_fermi(m.emin() - 0.2))
+    v = o.window_values(m.vel)
+    rows = np.arange(0, o.nstate, sample_every, dtype=np.int32)
+    ch_rows = o_rows_channels(m, o, rows)
+    t = time.perf_counter()
+    for _ in range(reps):
+        oracle_step_sample(o, f, f0, v, rows)
+    dt = time.perf_counter() - t
+    value = SWEEPS_PER_STEP * ch_rows * reps / dt
+    return {"value": value, "unit": "channels/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{reps} oracle step(s) (4 collision + 1 transport-map row passes) over every "
+                      f"{sample_every}th window state ({len(rows)} rows, {ch_rows} channels per pass), "
+                      f"{dt:.1f} s"}, (o, f, f0, v, rows, ch_rows)
+
+
+def o_rows_channels(m, o, rows):
+    """Channels in the listed rows, counted from the model by the oracle's own rule."""
+    import numpy as np
+
+    nb = m.nbands
+    nk = m.nk
+    ids = o.ids
+    ik = ids // nb
+    j = np.stack([ik // (nk[1] * nk[2]), (ik // nk[2]) % nk[1], ik % nk[2]], axis=1)
+    npos = (m.omega > 0).sum(axis=1)
+    total = 0
+    for r in rows:
+        q = (j - j[r]) % np.array(nk)
+        iq = (q[:, 0] * nk[1] + q[:, 1]) * nk[2] + q[:, 2]
+        total += int(npos[iq].sum())
+    return total
+
+
+def run_reference(args):
+    ws, rank, _ = dist()
+    if rank != 0:
+        return 0
+    import synth
+
+    m = synth.make_config(args.workload)
+    every = 16 if args.workload == "window40" else 4
+    base, (o, f, f0, v, rows, ch_rows) = cpu_baseline(m, sample_every=every, reps=1)
+    for _ in range(args.warmup):
+        oracle_step_sample(o, f, f0, v, rows)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step_sample(o, f, f0, v, rows)
+    dt = time.perf_counter() - t
+    value = SWEEPS_PER_STEP * ch_rows * args.steps / dt
+    cfg = workload_config(args.workload)
+    cfg["sample"] = f"every {every}th window state ({len(rows)} rows)"
+    emit({"impl": "reference", "metric": "e-ph channels/s", "value": value, "unit": "channels/s", "n_gpus": ws,
+          "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+          "config": cfg,
+          "cpu_baseline": {"value": value, "unit": "channels/s", "cores": base["cores"], "kind": "oracle",
+                           "sample": f"{args.steps} oracle steps (4 collision + 1 transport-map row passes) over "
+                                     f"every {every}th window state ({len(rows)} rows)"},
+          "e2e": {"value": value, "unit": "channels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+    return 0
+
+
+# ---------------------------------------------------------------- GPU
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2511_03683_gb300 as pb
+
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as tdist
+
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as tdist
+
+            tdist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if ws == 1:
+            return x
+        import torch.distributed as tdist
+
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        return float(t.item())
+
+    m = synth.make_config(args.workload)
+    t0 = time.perf_counter()
+    ch = pb.Channels.from_model(m)
+    build_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    dev = pb.Device(ch, variant=args.variant, transport=True)
+    torch.cuda.synchronize()
+    create_s = time.perf_counter() - t0
+    ids = ch.state_ids()
+    ns, nch = dev.nstate, dev.nchannels
+    fh = m.f_hot().reshape(-1)[ids]
+    f0h = m.f_fermi(m.emin() - 0.2).reshape(-1)[ids]
+    vh = m.vel.reshape(-1, 3)[ids]
+    f = torch.tensor(fh, device="cuda")
+    f0 = torch.tensor(f0h, device="cuda")
+    v = torch.tensor(vh, device="cuda")
+    Fa = torch.zeros((ns, 3), dtype=torch.float64, device="cuda")
+    Fb = torch.zeros_like(Fa)
+    res = torch.zeros(3, dtype=torch.float64, device="cuda")
+    dev.transport_setup(f0)
+    dt = 1.0
+    stream = torch.cuda.current_stream()
+
+    def step(F_in, F_out):
+        dev.rk4(f, dt, 1)
+        dev.transport_iterate(v, F_in, out=F_out, resid=res)
+
+    clocks = Clocks(local)
+    for i in range(args.warmup):
+        step(Fa, Fb) if i % 2 == 0 else step(Fb, Fa)
+    barrier()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        step(Fa, Fb) if i % 2 == 0 else step(Fb, Fa)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms)
+    value = ws * SWEEPS_PER_STEP * nch * args.steps / (ms_max * 1e-3)
+
+    # rt-BTE RK4 steps per second (one call, graph replay)
+    nrk = 200
+    g = torch.tensor(fh, device="cuda")
+    dev.rk4(g, dt, 5)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    dev.rk4(g, dt, nrk)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    rk_ms = e0.elapsed_time(e1)
+
+    # transport iterations per second (device only)
+    ntr = 100
+    e0.record(stream)
+    for i in range(ntr):
+        dev.transport_iterate(v, Fa, out=Fb, resid=res) if i % 2 == 0 else dev.transport_iterate(v, Fb, out=Fa, resid=res)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tr_ms = e0.elapsed_time(e1)
+
+    # dominant kernel: the collision sweep, timed per call on the launching stream
+    ncall = 40
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ncall)]
+    out = torch.empty(ns, dtype=torch.float64, device="cuda")
+    for a, b in evs:
+        a.record(stream)
+        dev.collision(f, out=out)
+        b.record(stream)
+    torch.cuda.synchronize()
+    coll_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    rates_ms = None
+    for a, b in evs[:10]:
+        a.record(stream)
+        dev.rates(f, out=out)
+        b.record(stream)
+    torch.cuda.synchronize()
+    rates_ms = statistics.mean(a.elapsed_time(b) for a, b in evs[:10])
+    clk = clocks.stop()
+
+    bytes_launch = dev.bytes_per_channel * nch
+    achieved = bytes_launch / (coll_ms * 1e-3) / 1e9
+    peak, peak_src = measured_hbm()
+    traffic = ncu_traffic(args.workload, args.variant)
+
+    # full transport solve for x, y, z to 1e-10 (the workload's second half)
+    solve = None
+    if not args.no_solve:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Fs, iters, resid, ok = dev.transport(f0, v, tol=1e-10, maxit=1000)
+        solve = {"iterations": iters, "residual": resid, "converged": ok, "seconds": time.perf_counter() - t0}
+
+    # end to end through the host-buffer entry points: H2D of f and F, step, D2H of both
+    e2e = None
+    if not args.no_e2e:
+        f_host = torch.tensor(fh).pin_memory()
+        F_host = torch.zeros((ns, 3), dtype=torch.float64).pin_memory()
+        F_dev = torch.empty((ns, 3), dtype=torch.float64, device="cuda")
+        F_out = torch.empty_like(F_dev)
+        fnp = f_host.numpy()
+
+        def e2e_step():
+            dev.rk4_host(f_host, dt, 1, out=f_host)
+            F_dev.copy_(F_host, non_blocking=True)
+            dev.transport_iterate(v, F_dev, out=F_out)
+            F_host.copy_(F_out, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        for _ in range(min(args.warmup, 3)):
+            e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - t0)
+        assert np.isfinite(fnp).all()
+        e2e = {"value": ws * SWEEPS_PER_STEP * nch * args.steps / e2e_s, "unit": "channels/s",
+               "h2d_bytes_per_step": 8 * ns + 24 * ns, "d2h_bytes_per_step": 8 * ns + 24 * ns}
+
+    base = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        base, _ = cpu_baseline(m, sample_every=1 if args.workload != "window40" else 4)
+
+    if rank == 0:
+        cfg = workload_config(args.workload)
+        cfg.update({"nstate": ns, "channels": nch, "variant": args.variant, "l2": "inputs larger than L2 "
+                    f"({dev.bytes_per_channel * nch / 1e9:.2f} GB streamed per sweep vs 0.13 GB L2)"
+                    if args.workload == "window40" else "inputs fit in L2 (latency/parity workload)",
+                    "parallelism": f"{ws} independent replica(s)"})
+        emit({
+            "metric": "e-ph channels/s", "value": value, "unit": "channels/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32x2" if args.variant == "ff" else "f64",
+            "data": "synthetic", "config": cfg,
+            "rk4_steps_per_s": nrk / (rk_ms * 1e-3), "transport_iters_per_s": ntr / (tr_ms * 1e-3),
+            "collision_ms": coll_ms, "rates_ms": rates_ms,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic, "kernel": "collision sweep (k_stream_ff, MODE_COLL) via pb_collision",
+                         "bytes_per_channel": dev.bytes_per_channel, "bytes_per_launch": bytes_launch,
+                         "peak_source": peak_src},
+            "cpu_baseline": base, "e2e": e2e, "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+            "clocks": clk, "setup": {"build_channels_s": build_s, "device_create_s": create_s},
+            "transport_solve": solve,
+        })
+    if ws > 1:
+        import torch.distributed as tdist
+
+        tdist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

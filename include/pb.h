@@ -1,0 +1,233 @@
+/*
+ * pb.h — C ABI of the GB300 electron-phonon collision-integral library (libpb.so).
+ *
+ * What it computes (arXiv:2511.03683, "Efficient GPU Parallelization of
+ * Electronic Transport and Nonequilibrium Dynamics from Electron-Phonon
+ * Interactions in the Perturbo Code"):
+ *
+ *   Eq. 2 (collision integral of state s = (n,k)):
+ *     I_s = -(2 pi/hbar)(1/N_q) sum_{m q nu} |g_{mn nu}(k,q)|^2
+ *           [ delta(eps_s - eps_p + hbar w) F_abs + delta(eps_s - eps_p - hbar w) F_em ]
+ *   with p = (m, k+q), w = omega_{nu q}, delta a normalised Gaussian of width sigma and
+ *     F_abs = f_s (1-f_p) N - (1-f_s) f_p (N+1),
+ *     F_em  = f_s (1-f_p)(N+1) - (1-f_s) f_p N,       N = 1/(exp(hbar w / k_B T) - 1).
+ *   (The paper names F_abs and F_em without writing them out; these are the Fermi
+ *   golden-rule forms, under which each channel adds equal and opposite amounts to
+ *   I(nk) and I(mk+q), as the paper states in Sec. "Optimized GPU algorithm", step 1.)
+ *
+ * A scattering channel is the tuple (k, q, n, m, nu) (Sec. "Collision integral, e-ph
+ * coupling matrix, and scattering channels").  The library keeps every channel whose
+ * two states lie inside the energy window and whose phonon energy is positive, in a
+ * state-segmented CSR list that holds each channel under both of its states, so the
+ * per-state sums need no atomic updates (the paper's aim in its "target layer",
+ * Fig. 2) and no second "sc_col" pass (Fig. 2b-c): contribution and reduction are fused.
+ *
+ * Units: eV, fs, K; hbar = 0.6582119569 eV fs, k_B = 8.617333262e-5 eV/K.  Rates are 1/fs.
+ *
+ * Conventions shared by every call:
+ *  - Full-grid state id: id = ik * nbands + n,  ik = (j1 * N2 + j2) * N3 + j3,
+ *    k_i = 2 pi j_i / N_i.  The q grid equals the k grid (commensurate grids, N_q = N1 N2 N3).
+ *  - Window states are numbered 0..nstate-1 in ascending full-grid id.  Every device
+ *    vector (f, dfdt, inv_tau, F) is indexed by that number.
+ *  - Status: every int-returning call returns PB_OK (0) or one of the PB_E* codes below;
+ *    pb_last_error() then gives a message (thread-local; valid until the thread's next call).
+ *    No C++ exception crosses the ABI.
+ *  - Streams: `stream` is a cudaStream_t passed as void*; NULL is the legacy default stream.
+ *    Device calls are asynchronous on that stream unless stated.
+ *  - Ownership: the library owns only its opaque host handles (pb_channels, pb_dev).  All
+ *    device memory is the caller's: pb_dev_create carves its arrays out of one caller-
+ *    allocated device arena and never frees it; vectors passed to the compute calls are
+ *    caller-owned device pointers.
+ */
+#ifndef PB_H
+#define PB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  PB_OK = 0,
+  PB_EINVAL = 1,      /* bad argument (null pointer, size, dimension, non-finite input) */
+  PB_ENOMEM = 2,      /* host allocation failed, or the device arena is too small */
+  PB_ECUDA = 3,       /* a CUDA runtime call failed; message holds cudaGetErrorString */
+  PB_ENOTCLOSED = 4,  /* a channel's reverse channel is missing or has a different |g|^2 */
+  PB_ENOCONV = 5,     /* pb_iter_transport reached maxit above tol */
+  PB_ETIMEOUT = 6,    /* reserved: a bounded device-side wait gave up */
+  PB_ECALLBACK = 7,   /* the |g|^2 callback returned non-zero or a negative/non-finite value */
+  PB_EDEVICE = 8      /* no usable CUDA device, or it is not an sm_103 part */
+};
+
+/* ---------------------------------------------------------------- host model */
+
+/* One e-ph system on commensurate k/q grids (Eq. 2; Sec. "Collision integral ...").
+ * All pointers are HOST memory owned by the caller and only read during
+ * pb_build_channels (the library copies what it keeps). */
+typedef struct pb_model {
+  int32_t nk[3];        /* grid N1, N2, N3 (>= 1 each); N_q = N1*N2*N3 */
+  int32_t nbands;       /* bands per k point (1..255) */
+  int32_t nmodes;       /* phonon branches (1..255) */
+  const double *eps;    /* [N_q][nbands] band energies, eV */
+  const double *vel;    /* [N_q][nbands][3] band velocities (any length unit per fs), or NULL */
+  const double *omega;  /* [N_q][nmodes] phonon energies hbar*omega_{nu q}, eV; must be even in q */
+  const double *win;    /* [nbands][2] per-band energy window [lo, hi] (inclusive), or NULL = all states */
+  double T;             /* phonon temperature, K (> 0) */
+  double sigma;         /* Gaussian width of the delta function, eV (> 0) */
+} pb_model;
+
+/* |g|^2 (eV^2) of n channels.  s[i], p[i] are FULL-GRID ids of the two states and
+ * nu[i] the branch; write g2[i].  Must be symmetric: g2(s,p,nu) == g2(p,s,nu).
+ * Return 0 on success.  Called from one thread unless pb_build_opts.callback_threadsafe. */
+typedef int (*pb_g2_fn)(int64_t n, const int32_t *s, const int32_t *p, const int32_t *nu, double *g2,
+                        void *user);
+
+typedef struct pb_build_opts {
+  int32_t nthreads;             /* host threads (0 = all available) */
+  int32_t callback_threadsafe;  /* nonzero: g2 callback may run on several threads at once */
+  int32_t check_closure;        /* nonzero: verify every channel's reverse exists with equal g2 */
+  int32_t reserved;
+  double g2_min;                /* drop channels with g2 < g2_min (the paper's |g| cutoff); 0 keeps all */
+} pb_build_opts;
+
+typedef struct pb_channels pb_channels; /* opaque host CSR, library-owned */
+
+typedef struct pb_channels_info {
+  int64_t nstate;      /* window states (CSR rows) */
+  int64_t nchannels;   /* stored channels (each physical channel appears under both its states) */
+  int64_t nq;          /* N_q */
+  int32_t nk[3];
+  int32_t nbands;
+  int32_t nmodes;
+  int32_t reserved;
+  double T, sigma;
+  int64_t max_row;     /* longest row */
+} pb_channels_info;
+
+/* Step 1 of the paper's GPU scheme ("create the target layer", done once on the CPU):
+ * select window states, enumerate every channel (s, p, nu) with s and p in the window,
+ * q = k_p - k_s folded onto the grid and hbar*omega_{nu q} > 0, fetch |g|^2 through the
+ * callback, and store the list in CSR order: rows = window states ascending, channels
+ * within a row sorted by (partner, nu).  With check_closure, fails with PB_ENOTCLOSED
+ * unless the list is closed under s <-> p with equal |g|^2 (which makes sum_s I_s = 0).
+ * On success *out is a new handle (free with pb_channels_free). */
+int pb_build_channels(const pb_model *model, pb_g2_fn g2, void *user, const pb_build_opts *opts,
+                      pb_channels **out);
+
+int pb_channels_get_info(const pb_channels *ch, pb_channels_info *info);
+
+/* Copy the CSR to caller HOST arrays (any pointer may be NULL to skip it):
+ * row_ptr[nstate+1], col[nchannels] (partner window index), nu[nchannels],
+ * g2[nchannels], state_ids[nstate] (full-grid id of each window state). */
+int pb_channels_export(const pb_channels *ch, int64_t *row_ptr, int32_t *col, int32_t *nu, double *g2,
+                       int32_t *state_ids);
+
+void pb_channels_free(pb_channels *ch);
+
+/* ---------------------------------------------------------------- device */
+
+/* Hot-path variants.  Each evaluates the same Eq. 2 and meets the same FP64 oracle.
+ *  PB_VARIANT_FF      (default) per-channel rate coefficients, precomputed once in FP64
+ *                     and streamed as float-float (hi,lo) pairs with float-float
+ *                     accumulation: FP64-level accuracy at FP32 issue rate.
+ *  PB_VARIANT_F64     the same coefficients as doubles with native FP64 FMAs.
+ *  PB_VARIANT_LITERAL streams |g|^2 and the packed (partner, nu) index and evaluates the
+ *                     Gaussians and Bose factors per channel in FP64 registers.
+ *  PB_VARIANT_G32     |g|^2 stored FP32, per-channel arithmetic in FP32, compensated
+ *                     (Kahan) accumulation, FP64 state.
+ *  PB_VARIANT_G16     as G32 with |g|^2 stored BF16. */
+enum { PB_VARIANT_FF = 0, PB_VARIANT_F64 = 1, PB_VARIANT_LITERAL = 2, PB_VARIANT_G32 = 3, PB_VARIANT_G16 = 4 };
+
+typedef struct pb_dev_opts {
+  int32_t variant;         /* PB_VARIANT_* */
+  int32_t item_channels;   /* channels per work item (multiple of 64; 0 = 2048) */
+  int32_t ctas_per_sm;     /* resident CTAs per SM for the streaming kernels (0 = 4) */
+  int32_t transport;       /* nonzero: reserve transport buffers (weights and F) */
+} pb_dev_opts;
+
+typedef struct pb_dev pb_dev; /* opaque host handle describing device-resident data */
+
+/* Bytes of device arena pb_dev_create needs for this channel list and options. */
+int pb_dev_arena_bytes(const pb_channels *ch, const pb_dev_opts *opts, size_t *bytes);
+
+/* Upload the CSR and tables into `arena` (caller-owned device memory of at least
+ * pb_dev_arena_bytes, 256-byte aligned) and precompute per-channel coefficients on the
+ * GPU.  Synchronises `stream` before returning.  The arena must outlive the handle. */
+int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, void *arena, size_t arena_bytes, void *stream,
+                  pb_dev **out);
+
+void pb_dev_destroy(pb_dev *dev);
+
+typedef struct pb_dev_info {
+  int64_t nstate, nchannels, nchannels_padded, nitems;
+  int32_t variant, sm_count;
+  double bytes_per_channel;  /* algorithmic bytes streamed per channel by pb_collision */
+  double c;                  /* (2 pi / hbar) / N_q, 1/(eV fs) */
+} pb_dev_info;
+
+int pb_dev_get_info(const pb_dev *dev, pb_dev_info *info);
+
+/* Eq. 2: dfdt[s] = I_s[f] for every window state.  f, dfdt: device double[nstate]. */
+int pb_collision(pb_dev *dev, const double *f, double *dfdt, void *stream);
+
+/* Scattering rates 1/tau_s = -dI_s/df_s
+ *   = (2pi/hbar)(1/N_q) sum |g|^2 [G(x+w)(N+f_p) + G(x-w)(N+1-f_p)],  x = eps_s - eps_p.
+ * f, inv_tau: device double[nstate]. */
+int pb_scatter_rates(pb_dev *dev, const double *f, double *inv_tau, void *stream);
+
+/* nsteps classic RK4 steps of the field-free rt-BTE df/dt = I[f] (Eq. 1 with F = 0),
+ * step dt (fs), in place on the device vector f.  Steps are replayed from a CUDA graph
+ * captured on first use (the capture uses an internal stream). */
+int pb_rtbte_rk4_step(pb_dev *dev, double *f, double dt, int32_t nsteps, void *stream);
+
+/* Same as pb_rtbte_rk4_step with HOST buffers: copies f_host_in (double[nstate]) to the
+ * device, runs nsteps steps, copies the result to f_host_out, and synchronises `stream`.
+ * The host buffers should be pinned for asynchronous copies; pageable memory works. */
+int pb_rtbte_rk4_host(pb_dev *dev, const double *f_host_in, double *f_host_out, double dt, int32_t nsteps,
+                      void *stream);
+
+/* Iterative linearised transport for the three field directions at once
+ * (Sec. "Optimized GPU algorithm": sc_col gains a field-direction dimension):
+ *   F^{i+1}_{s a} = tau_s ( v_{s a} + sum_c W_c F^i_{p a} ),  a = x, y, z,
+ *   W_c = (2pi/hbar)(1/N_q)|g|^2 [G(x+w)(N+f0_p) + G(x-w)(N+1-f0_p)],  1/tau_s = sum_c W_c,
+ * from F^0 = tau v until max|F^{i+1}-F^i| <= tol * max|F^{i+1}|.
+ * f0: device double[nstate]; vel3, F3: device double[nstate][3].  On return (stream
+ * synchronised) *iters holds the iterations done and *resid the last relative change;
+ * PB_ENOCONV if maxit was reached first (F3 then holds the last iterate).
+ * Needs a pb_dev created with opts.transport != 0. */
+int pb_iter_transport(pb_dev *dev, const double *f0, const double *vel3, double tol, int32_t maxit, double *F3,
+                      int32_t *iters, double *resid, void *stream);
+
+/* Compute and keep the transport weights W_c and tau_s at f0 (device double[nstate])
+ * for later pb_transport_iterate calls.  pb_iter_transport and pb_transport_map call
+ * it themselves. */
+int pb_transport_setup(pb_dev *dev, const double *f0, void *stream);
+
+/* One pass of the transport map with the weights of the last pb_transport_setup:
+ * F3out = tau (v + W F3in), all device double[nstate][3], without any host
+ * synchronisation.  If resid3 (device double[3]) is not NULL it receives
+ * (max|F3out-F3in| / max|F3out|, max|F3out-F3in|, max|F3out|). */
+int pb_transport_iterate(pb_dev *dev, const double *vel3, const double *F3in, double *F3out, double *resid3,
+                         void *stream);
+
+/* One transport map application without the convergence loop: F3out = tau (v + W F3in)
+ * with W, tau at f0 (pb_transport_setup followed by pb_transport_iterate). */
+int pb_transport_map(pb_dev *dev, const double *f0, const double *vel3, const double *F3in, double *F3out,
+                     void *stream);
+
+/* Observables of a distribution: out[0] = sum_s f_s (carriers), out[1] = sum_s eps_s f_s (eV),
+ * out[2] = sum_s I_s[f] (conservation check, 1/fs).  out: device double[3]. */
+int pb_observables(pb_dev *dev, const double *f, double *out3, void *stream);
+
+const char *pb_last_error(void);
+
+/* Library version string, e.g. "pb 0.1 sm_103a". */
+const char *pb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PB_H */

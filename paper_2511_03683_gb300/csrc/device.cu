@@ -1,0 +1,739 @@
+// Device runtime of libpb.so: arena layout, upload, coefficient setup and the host
+// drivers of the public compute calls (include/pb.h).  Kernels are in kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.cuh"
+#include "pb_internal.h"
+
+using namespace pb;
+using pb::dev::Item;
+using pb::dev::Part4;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kFinBlock = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+  size_t rp, item_ptr, items, col, coefA, coefB, g2, wt, eps, kc, R, omega, tab, part, acc, y, yff, fstage, Fa, Fb,
+      Fff, tau, invtau, red, scal, obs, total;
+};
+
+struct Plan {
+  int64_t ns = 0, nchp = 0, nitems = 0;
+  std::vector<int64_t> rp;       // padded row offsets [ns+1]
+  std::vector<int32_t> item_ptr; // [ns+1]
+  std::vector<Item> items;
+  int item_ch = 0;
+};
+
+int default_item_channels(int64_t nchp, int sm_count, int ctas) {
+  // enough items for ~4 per resident warp, 256..4096 channels each, multiple of 64
+  const int64_t warps = (int64_t)sm_count * ctas * (dev::kBlock / 32);
+  int64_t ic = nchp / std::max<int64_t>(1, warps * 4);
+  ic = std::max<int64_t>(256, std::min<int64_t>(4096, ic));
+  return (int)(ic / 64 * 64);
+}
+
+void make_plan(const pb_channels *ch, int item_ch, Plan &P) {
+  const int64_t ns = ch->nstate;
+  P.ns = ns;
+  P.item_ch = item_ch;
+  P.rp.assign(ns + 1, 0);
+  P.item_ptr.assign(ns + 1, 0);
+  P.items.clear();
+  for (int64_t r = 0; r < ns; ++r) {
+    const int64_t len = ch->row_ptr[r + 1] - ch->row_ptr[r];
+    const int64_t lenp = (len + kRowPad - 1) / kRowPad * kRowPad;
+    P.rp[r + 1] = P.rp[r] + lenp;
+    P.item_ptr[r] = (int32_t)P.items.size();
+    if (lenp == 0) continue;
+    const int64_t nchunks = lenp / kRowPad;  // 8-channel chunks
+    const int64_t np = std::max<int64_t>(1, (lenp + item_ch - 1) / item_ch);
+    int64_t off = 0;
+    for (int64_t k = 0; k < np; ++k) {
+      const int64_t chunks = nchunks / np + (k < nchunks % np ? 1 : 0);
+      Item it;
+      it.start = P.rp[r] + off;
+      it.len = (int)(chunks * kRowPad);
+      it.row = (int)r;
+      if (it.len > 0) P.items.push_back(it);
+      off += chunks * kRowPad;
+    }
+  }
+  P.item_ptr[ns] = (int32_t)P.items.size();
+  P.nchp = P.rp[ns];
+  P.nitems = (int64_t)P.items.size();
+}
+
+size_t coef_bytes(int variant) {
+  switch (variant) {
+    case PB_VARIANT_FF: return sizeof(float2);
+    case PB_VARIANT_F64: return sizeof(double);
+    default: return 0;
+  }
+}
+
+Layout make_layout(const pb_channels *ch, const Plan &P, int variant, bool transport, int nfin_blocks) {
+  Layout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + std::max<size_t>(bytes, 1));
+    return at;
+  };
+  const size_t ns = (size_t)P.ns, nchp = (size_t)P.nchp;
+  L.rp = take(sizeof(int64_t) * (ns + 1));
+  L.item_ptr = take(sizeof(int32_t) * (ns + 1));
+  L.items = take(sizeof(Item) * P.nitems);
+  L.col = take(sizeof(uint32_t) * nchp);
+  L.g2 = take(sizeof(double) * nchp);
+  L.coefA = take(coef_bytes(variant) * nchp);
+  L.coefB = take(coef_bytes(variant) * nchp);
+  L.wt = take(transport ? sizeof(float2) * nchp : 0);
+  L.eps = take(sizeof(double) * ns);
+  L.kc = take(sizeof(short4) * ns);
+  L.R = take(sizeof(double) * ns);
+  L.omega = take(sizeof(double) * (size_t)ch->nq * ch->nmodes);
+  L.tab = take(sizeof(double2) * (size_t)ch->nq * ch->nmodes);
+  L.part = take(sizeof(Part4) * P.nitems);
+  L.acc = take(sizeof(double) * ns);
+  L.y = take(sizeof(double) * ns);
+  L.yff = take(sizeof(float2) * ns);
+  L.fstage = take(sizeof(double) * ns);
+  L.Fa = take(transport ? sizeof(double) * 3 * ns : 0);
+  L.Fb = take(transport ? sizeof(double) * 3 * ns : 0);
+  L.Fff = take(transport ? sizeof(float2) * 3 * ns : 0);
+  L.tau = take(sizeof(double) * ns);
+  L.invtau = take(sizeof(double) * ns);
+  L.red = take(sizeof(double2) * (size_t)nfin_blocks);
+  L.scal = take(sizeof(double) * 8);
+  L.obs = take(sizeof(double) * 8);
+  L.total = o;
+  return L;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  return set_error(PB_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define PB_CUDA(call)                                           \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);         \
+  } while (0)
+
+#define PB_LAUNCHED(what)                                       \
+  do {                                                          \
+    cudaError_t e_ = cudaGetLastError();                        \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what);          \
+  } while (0)
+
+}  // namespace
+
+struct pb_dev {
+  int variant = 0;
+  int64_t ns = 0, nch = 0, nchp = 0, nitems = 0;
+  int nk[3] = {0, 0, 0};
+  int nmodes = 0;
+  int64_t nq = 0;
+  double T = 0, sigma = 0, c = 0;
+  int sm_count = 0, ctas = 4, item_ch = 0;
+  bool transport = false;
+  char *arena = nullptr;
+  size_t arena_bytes = 0;
+  Layout L{};
+  // device views
+  int64_t *rp = nullptr;
+  int32_t *item_ptr = nullptr;
+  Item *items = nullptr;
+  uint32_t *col = nullptr;
+  double *g2 = nullptr;
+  void *coefA = nullptr, *coefB = nullptr;
+  float2 *wt = nullptr;
+  double *eps = nullptr;
+  short4 *kc = nullptr;
+  double *R = nullptr;
+  double *omega = nullptr;
+  double2 *tab = nullptr;
+  Part4 *part = nullptr;
+  double *acc = nullptr, *y = nullptr, *fstage = nullptr;
+  float2 *yff = nullptr;
+  double *Fa = nullptr, *Fb = nullptr;
+  float2 *Fff = nullptr;
+  double *tau = nullptr, *invtau = nullptr;
+  double2 *red = nullptr;
+  double *scal = nullptr, *obs = nullptr;
+  int nfin_blocks = 0;
+  size_t smem_f = 0;      // dynamic smem of the f staging (0 = gather from global)
+  size_t smem_F = 0;      // dynamic smem of the transport F staging
+  int ctas_tr = 1;        // resident transport CTAs per SM
+  // RK4 graph cache
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t rk_exec = nullptr;
+  double *rk_f = nullptr;
+  double rk_dt = 0.0;
+  // transport weights cache
+  const double *wt_f0 = nullptr;
+  bool wt_valid = false;
+  pb::dev::ChanGeom geom() const {
+    pb::dev::ChanGeom g;
+    g.col = col;
+    g.g2 = g2;
+    g.eps = eps;
+    g.kc = kc;
+    g.tab = tab;
+    g.N1 = nk[0];
+    g.N2 = nk[1];
+    g.N3 = nk[2];
+    g.nmodes = nmodes;
+    g.inv2s2 = 1.0 / (2.0 * sigma * sigma);
+    g.norm = 1.0 / (std::sqrt(2.0 * kPi) * sigma);
+    return g;
+  }
+  int stream_grid(int per_sm) const {
+    const int64_t need = (nitems * 32 + dev::kBlock - 1) / dev::kBlock;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sm_count * per_sm));
+  }
+};
+
+namespace {
+
+int check_device(int *sm_count) {
+  int devid = 0, major = 0, minor = 0;
+  cudaError_t e = cudaGetDevice(&devid);
+  if (e != cudaSuccess) return set_error(PB_EDEVICE, "no CUDA device: %s", cudaGetErrorString(e));
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, devid);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, devid);
+  if (major != 10 || minor != 3)
+    return set_error(PB_EDEVICE, "libpb.so is built for sm_103a only; device is sm_%d%d", major, minor);
+  PB_CUDA(cudaDeviceGetAttribute(sm_count, cudaDevAttrMultiProcessorCount, devid));
+  return PB_OK;
+}
+
+int resolve_opts(const pb_channels *ch, const pb_dev_opts *opts, int sm_count, pb_dev_opts &o) {
+  pb_dev_opts d{};
+  if (opts) d = *opts;
+  if (d.variant < PB_VARIANT_FF || d.variant > PB_VARIANT_LITERAL)
+    return set_error(PB_EINVAL, "pb_dev: variant %d is not available in this build", d.variant);
+  if (d.ctas_per_sm <= 0) d.ctas_per_sm = 4;
+  if (d.ctas_per_sm > 8) return set_error(PB_EINVAL, "pb_dev: ctas_per_sm must be <= 8");
+  if (d.item_channels < 0 || d.item_channels % 64 != 0)
+    return set_error(PB_EINVAL, "pb_dev: item_channels must be a non-negative multiple of 64");
+  if (d.item_channels == 0) {
+    int64_t nchp = 0;
+    for (int64_t r = 0; r < ch->nstate; ++r)
+      nchp += (ch->row_ptr[r + 1] - ch->row_ptr[r] + kRowPad - 1) / kRowPad * kRowPad;
+    d.item_channels = default_item_channels(nchp, sm_count, d.ctas_per_sm);
+  }
+  o = d;
+  return PB_OK;
+}
+
+}  // namespace
+
+extern "C" int pb_dev_arena_bytes(const pb_channels *ch, const pb_dev_opts *opts, size_t *bytes) {
+  clear_error();
+  if (!ch || !bytes) return set_error(PB_EINVAL, "pb_dev_arena_bytes: null argument");
+  int sm = 152;
+  {
+    int devid = 0;
+    if (cudaGetDevice(&devid) == cudaSuccess) cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, devid);
+    else cudaGetLastError();
+  }
+  pb_dev_opts o;
+  int rc = resolve_opts(ch, opts, sm, o);
+  if (rc) return rc;
+  Plan P;
+  make_plan(ch, o.item_channels, P);
+  const int nfin = (int)((P.ns + kFinBlock - 1) / kFinBlock);
+  *bytes = make_layout(ch, P, o.variant, o.transport != 0, nfin).total;
+  return PB_OK;
+}
+
+extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, void *arena, size_t arena_bytes,
+                             void *stream, pb_dev **out) {
+  clear_error();
+  if (!ch || !arena || !out) return set_error(PB_EINVAL, "pb_dev_create: null argument");
+  *out = nullptr;
+  if (((uintptr_t)arena) % kAlign) return set_error(PB_EINVAL, "pb_dev_create: arena must be 256-byte aligned");
+  int sm = 0;
+  int rc = check_device(&sm);
+  if (rc) return rc;
+  pb_dev_opts o;
+  rc = resolve_opts(ch, opts, sm, o);
+  if (rc) return rc;
+  if (ch->nstate > INT32_MAX / 4) return set_error(PB_EINVAL, "pb_dev_create: too many states");
+  cudaStream_t st = (cudaStream_t)stream;
+
+  pb_dev *d = new (std::nothrow) pb_dev();
+  if (!d) return set_error(PB_ENOMEM, "pb_dev_create: out of host memory");
+  Plan P;
+  try {
+    make_plan(ch, o.item_channels, P);
+  } catch (const std::bad_alloc &) {
+    delete d;
+    return set_error(PB_ENOMEM, "pb_dev_create: out of host memory");
+  }
+  if (P.nitems > INT32_MAX) {
+    delete d;
+    return set_error(PB_EINVAL, "pb_dev_create: too many work items");
+  }
+  d->variant = o.variant;
+  d->ns = ch->nstate;
+  d->nch = ch->nch;
+  d->nchp = P.nchp;
+  d->nitems = P.nitems;
+  for (int i = 0; i < 3; ++i) d->nk[i] = ch->nk[i];
+  d->nmodes = ch->nmodes;
+  d->nq = ch->nq;
+  d->T = ch->T;
+  d->sigma = ch->sigma;
+  d->c = 2.0 * kPi / (kHbar * (double)ch->nq);
+  d->sm_count = sm;
+  d->ctas = o.ctas_per_sm;
+  d->item_ch = o.item_channels;
+  d->transport = o.transport != 0;
+  d->nfin_blocks = (int)((d->ns + kFinBlock - 1) / kFinBlock);
+  d->L = make_layout(ch, P, o.variant, d->transport, d->nfin_blocks);
+  if (arena_bytes < d->L.total) {
+    const size_t need = d->L.total;
+    delete d;
+    return set_error(PB_ENOMEM, "pb_dev_create: arena of %zu bytes is smaller than the %zu needed", arena_bytes, need);
+  }
+  d->arena = (char *)arena;
+  d->arena_bytes = arena_bytes;
+  char *A = d->arena;
+  const Layout &L = d->L;
+  d->rp = (int64_t *)(A + L.rp);
+  d->item_ptr = (int32_t *)(A + L.item_ptr);
+  d->items = (Item *)(A + L.items);
+  d->col = (uint32_t *)(A + L.col);
+  d->g2 = (double *)(A + L.g2);
+  d->coefA = A + L.coefA;
+  d->coefB = A + L.coefB;
+  d->wt = (float2 *)(A + L.wt);
+  d->eps = (double *)(A + L.eps);
+  d->kc = (short4 *)(A + L.kc);
+  d->R = (double *)(A + L.R);
+  d->omega = (double *)(A + L.omega);
+  d->tab = (double2 *)(A + L.tab);
+  d->part = (Part4 *)(A + L.part);
+  d->acc = (double *)(A + L.acc);
+  d->y = (double *)(A + L.y);
+  d->yff = (float2 *)(A + L.yff);
+  d->fstage = (double *)(A + L.fstage);
+  d->Fa = (double *)(A + L.Fa);
+  d->Fb = (double *)(A + L.Fb);
+  d->Fff = (float2 *)(A + L.Fff);
+  d->tau = (double *)(A + L.tau);
+  d->invtau = (double *)(A + L.invtau);
+  d->red = (double2 *)(A + L.red);
+  d->scal = (double *)(A + L.scal);
+  d->obs = (double *)(A + L.obs);
+
+  // shared-memory staging sizes
+  int devid = 0, smem_optin = 0;
+  cudaGetDevice(&devid);
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, devid);
+  const size_t fbytes = (d->variant == PB_VARIANT_F64 ? sizeof(double) : sizeof(float2)) * (size_t)d->ns;
+  const size_t per_cta_budget = (size_t)(228 * 1024) / (size_t)d->ctas - 1024;
+  d->smem_f = (fbytes <= per_cta_budget && fbytes <= (size_t)smem_optin) ? fbytes : 0;
+  const size_t Fbytes = sizeof(float2) * 3 * (size_t)d->ns;
+  d->smem_F = Fbytes <= (size_t)smem_optin - 1024 ? Fbytes : 0;
+  d->ctas_tr = d->smem_F ? (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(228 * 1024) / (d->smem_F + 1024))) : 4;
+
+  // host staging of the padded arrays
+  int status = PB_OK;
+  try {
+    std::vector<uint32_t> colp((size_t)P.nchp);
+    std::vector<double> g2p((size_t)P.nchp, 0.0);
+    for (int64_t r = 0; r < d->ns; ++r) {
+      const int64_t a = ch->row_ptr[r], len = ch->row_ptr[r + 1] - a, b = P.rp[r], lenp = P.rp[r + 1] - b;
+      for (int64_t i = 0; i < len; ++i) {
+        colp[b + i] = (uint32_t)ch->col[a + i] | ((uint32_t)ch->nu[a + i] << kPartnerBits);
+        g2p[b + i] = ch->g2[a + i];
+      }
+      for (int64_t i = len; i < lenp; ++i) colp[b + i] = (uint32_t)r;  // padding: self, branch 0, g2 = 0
+    }
+    std::vector<short4> kc((size_t)d->ns);
+    const int N2 = ch->nk[1], N3 = ch->nk[2];
+    for (int64_t r = 0; r < d->ns; ++r) {
+      const int ik = ch->kidx[r];
+      kc[r] = make_short4((short)(ik / (N2 * N3)), (short)((ik / N3) % N2), (short)(ik % N3), 0);
+    }
+    if (ch->nk[0] > 32767 || ch->nk[1] > 32767 || ch->nk[2] > 32767) {
+      delete d;
+      return set_error(PB_EINVAL, "pb_dev_create: grid dimension above 32767");
+    }
+#define UP(dst, src, bytes)                                                          \
+  do {                                                                               \
+    cudaError_t e_ = cudaMemcpyAsync((dst), (src), (bytes), cudaMemcpyHostToDevice, st); \
+    if (e_ != cudaSuccess) {                                                         \
+      status = cuda_fail(e_, "upload");                                              \
+      break;                                                                         \
+    }                                                                                \
+  } while (0)
+    do {
+      UP(d->rp, P.rp.data(), sizeof(int64_t) * (d->ns + 1));
+      UP(d->item_ptr, P.item_ptr.data(), sizeof(int32_t) * (d->ns + 1));
+      UP(d->items, P.items.data(), sizeof(Item) * P.nitems);
+      UP(d->col, colp.data(), sizeof(uint32_t) * P.nchp);
+      UP(d->g2, g2p.data(), sizeof(double) * P.nchp);
+      UP(d->eps, ch->eps.data(), sizeof(double) * d->ns);
+      UP(d->kc, kc.data(), sizeof(short4) * d->ns);
+      UP(d->omega, ch->omega.data(), sizeof(double) * (size_t)ch->nq * ch->nmodes);
+    } while (0);
+#undef UP
+    if (status == PB_OK) {
+      const long long n = (long long)ch->nq * ch->nmodes;
+      dev::k_table<<<(int)std::min<long long>((n + 255) / 256, 4096), 256, 0, st>>>(d->omega, n, kBoltz * d->T, d->tab);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) status = cuda_fail(e, "k_table");
+    }
+    if (status == PB_OK) {
+      // per-channel coefficients (and R_s) for the coefficient variants
+      const int grid = d->stream_grid(8);
+      const dev::ChanGeom g = d->geom();
+      if (d->variant == PB_VARIANT_FF)
+        dev::k_coef<true><<<grid, dev::kBlock, 0, st>>>(d->items, (int)d->nitems, g, d->coefA, d->coefB, d->part);
+      else if (d->variant == PB_VARIANT_F64)
+        dev::k_coef<false><<<grid, dev::kBlock, 0, st>>>(d->items, (int)d->nitems, g, d->coefA, d->coefB, d->part);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) status = cuda_fail(e, "k_coef");
+      if (status == PB_OK && d->variant != PB_VARIANT_LITERAL) {
+        dev::k_rowsum<<<(int)((d->ns + 255) / 256), 256, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->R);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) status = cuda_fail(e, "k_rowsum");
+      }
+    }
+    if (status == PB_OK) {
+      cudaError_t e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) status = cuda_fail(e, "pb_dev_create: synchronize");
+    }
+  } catch (const std::bad_alloc &) {
+    status = set_error(PB_ENOMEM, "pb_dev_create: out of host memory");
+  }
+  if (status != PB_OK) {
+    delete d;
+    return status;
+  }
+  if (d->smem_f > 48 * 1024) {
+    cudaFuncSetAttribute(dev::k_stream_ff<dev::MODE_COLL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
+    cudaFuncSetAttribute(dev::k_stream_ff<dev::MODE_RATE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
+    cudaFuncSetAttribute(dev::k_stream_f64<dev::MODE_COLL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
+    cudaFuncSetAttribute(dev::k_stream_f64<dev::MODE_RATE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
+  }
+  if (d->smem_F > 48 * 1024)
+    cudaFuncSetAttribute(dev::k_stream_tr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_F);
+  cudaGetLastError();
+  *out = d;
+  return PB_OK;
+}
+
+extern "C" void pb_dev_destroy(pb_dev *d) {
+  if (!d) return;
+  if (d->rk_exec) cudaGraphExecDestroy(d->rk_exec);
+  if (d->cap) cudaStreamDestroy(d->cap);
+  delete d;
+}
+
+extern "C" int pb_dev_get_info(const pb_dev *d, pb_dev_info *info) {
+  clear_error();
+  if (!d || !info) return set_error(PB_EINVAL, "pb_dev_get_info: null argument");
+  std::memset(info, 0, sizeof *info);
+  info->nstate = d->ns;
+  info->nchannels = d->nch;
+  info->nchannels_padded = d->nchp;
+  info->nitems = d->nitems;
+  info->variant = d->variant;
+  info->sm_count = d->sm_count;
+  info->c = d->c;
+  switch (d->variant) {
+    case PB_VARIANT_FF: info->bytes_per_channel = 2 * sizeof(float2) + sizeof(uint32_t); break;
+    case PB_VARIANT_F64: info->bytes_per_channel = 2 * sizeof(double) + sizeof(uint32_t); break;
+    default: info->bytes_per_channel = sizeof(double) + sizeof(uint32_t); break;
+  }
+  return PB_OK;
+}
+
+namespace {
+
+// Stream pass over all items: part[item] = (A, B) or the literal sums.  `fd` is the
+// distribution in double, `fff` its float-float copy (used by the FF variant).
+int launch_stream(pb_dev *d, int mode, const double *fd, const float2 *fff, cudaStream_t st) {
+  const int grid = d->stream_grid(d->ctas);
+  const int n = (int)d->nitems;
+  const uint4 *col4 = (const uint4 *)d->col;
+  if (d->variant == PB_VARIANT_FF) {
+    const float4 *A4 = (const float4 *)d->coefA, *B4 = (const float4 *)d->coefB;
+    if (d->smem_f) {
+      if (mode == dev::MODE_COLL)
+        dev::k_stream_ff<dev::MODE_COLL, true><<<grid, dev::kBlock, d->smem_f, st>>>(d->items, n, A4, B4, col4, fff, (int)d->ns, d->part);
+      else
+        dev::k_stream_ff<dev::MODE_RATE, true><<<grid, dev::kBlock, d->smem_f, st>>>(d->items, n, A4, B4, col4, fff, (int)d->ns, d->part);
+    } else {
+      if (mode == dev::MODE_COLL)
+        dev::k_stream_ff<dev::MODE_COLL, false><<<grid, dev::kBlock, 0, st>>>(d->items, n, A4, B4, col4, fff, (int)d->ns, d->part);
+      else
+        dev::k_stream_ff<dev::MODE_RATE, false><<<grid, dev::kBlock, 0, st>>>(d->items, n, A4, B4, col4, fff, (int)d->ns, d->part);
+    }
+  } else if (d->variant == PB_VARIANT_F64) {
+    const double2 *A2 = (const double2 *)d->coefA, *B2 = (const double2 *)d->coefB;
+    if (d->smem_f) {
+      if (mode == dev::MODE_COLL)
+        dev::k_stream_f64<dev::MODE_COLL, true><<<grid, dev::kBlock, d->smem_f, st>>>(d->items, n, A2, B2, col4, fd, (int)d->ns, d->part);
+      else
+        dev::k_stream_f64<dev::MODE_RATE, true><<<grid, dev::kBlock, d->smem_f, st>>>(d->items, n, A2, B2, col4, fd, (int)d->ns, d->part);
+    } else {
+      if (mode == dev::MODE_COLL)
+        dev::k_stream_f64<dev::MODE_COLL, false><<<grid, dev::kBlock, 0, st>>>(d->items, n, A2, B2, col4, fd, (int)d->ns, d->part);
+      else
+        dev::k_stream_f64<dev::MODE_RATE, false><<<grid, dev::kBlock, 0, st>>>(d->items, n, A2, B2, col4, fd, (int)d->ns, d->part);
+    }
+  } else {
+    const dev::ChanGeom g = d->geom();
+    const int lgrid = d->stream_grid(8);
+    if (mode == dev::MODE_COLL)
+      dev::k_stream_literal<dev::MODE_COLL><<<lgrid, dev::kBlock, 0, st>>>(d->items, n, g, fd, d->part);
+    else
+      dev::k_stream_literal<dev::MODE_RATE><<<lgrid, dev::kBlock, 0, st>>>(d->items, n, g, fd, d->part);
+  }
+  PB_LAUNCHED("stream kernel");
+  return PB_OK;
+}
+
+int fin_grid(const pb_dev *d) { return d->nfin_blocks; }
+
+template <int STAGE>
+void launch_fin(pb_dev *d, const double *ysrc, double *out, double *f, double dt, cudaStream_t st) {
+  if (d->variant == PB_VARIANT_LITERAL)
+    dev::k_fin_coll<true, STAGE><<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->c, d->R, ysrc,
+                                                                    out, f, d->acc, d->y, d->yff, dt);
+  else
+    dev::k_fin_coll<false, STAGE><<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->c, d->R, ysrc,
+                                                                     out, f, d->acc, d->y, d->yff, dt);
+}
+
+int to_ff(pb_dev *d, const double *x, int64_t n, float2 *out, cudaStream_t st) {
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 1024));
+  dev::k_to_ff<<<grid, 256, 0, st>>>(x, (long long)n, out);
+  PB_LAUNCHED("k_to_ff");
+  return PB_OK;
+}
+
+// One RK4 step on the device vector f (the stage-0 ff copy must already be in yff).
+int rk4_launches(pb_dev *d, double *f, double dt, cudaStream_t st) {
+  int rc;
+  if ((rc = launch_stream(d, dev::MODE_COLL, f, d->yff, st))) return rc;
+  launch_fin<0>(d, f, nullptr, f, dt, st);
+  PB_LAUNCHED("rk4 stage 1");
+  if ((rc = launch_stream(d, dev::MODE_COLL, d->y, d->yff, st))) return rc;
+  launch_fin<1>(d, d->y, nullptr, f, dt, st);
+  PB_LAUNCHED("rk4 stage 2");
+  if ((rc = launch_stream(d, dev::MODE_COLL, d->y, d->yff, st))) return rc;
+  launch_fin<2>(d, d->y, nullptr, f, dt, st);
+  PB_LAUNCHED("rk4 stage 3");
+  if ((rc = launch_stream(d, dev::MODE_COLL, d->y, d->yff, st))) return rc;
+  launch_fin<3>(d, d->y, nullptr, f, dt, st);
+  PB_LAUNCHED("rk4 stage 4");
+  return PB_OK;
+}
+
+int ensure_rk_graph(pb_dev *d, double *f, double dt) {
+  if (d->rk_exec && d->rk_f == f && d->rk_dt == dt) return PB_OK;
+  if (d->rk_exec) {
+    cudaGraphExecDestroy(d->rk_exec);
+    d->rk_exec = nullptr;
+  }
+  if (!d->cap) PB_CUDA(cudaStreamCreateWithFlags(&d->cap, cudaStreamNonBlocking));
+  PB_CUDA(cudaStreamBeginCapture(d->cap, cudaStreamCaptureModeThreadLocal));
+  int rc = rk4_launches(d, f, dt, d->cap);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(d->cap, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&d->rk_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    d->rk_exec = nullptr;
+    return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  d->rk_f = f;
+  d->rk_dt = dt;
+  return PB_OK;
+}
+
+int ensure_weights(pb_dev *d, const double *f0, cudaStream_t st) {
+  if (!d->transport) return set_error(PB_EINVAL, "transport buffers were not reserved (pb_dev_opts.transport = 0)");
+  const int grid = d->stream_grid(8);
+  dev::k_weights<<<grid, dev::kBlock, 0, st>>>(d->items, (int)d->nitems, d->geom(), f0, d->c, d->wt, d->part);
+  PB_LAUNCHED("k_weights");
+  dev::k_rowsum<<<(int)((d->ns + 255) / 256), 256, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->invtau);
+  PB_LAUNCHED("k_rowsum");
+  dev::k_recip<<<(int)((d->ns + 255) / 256), 256, 0, st>>>(d->invtau, (int)d->ns, d->tau);
+  PB_LAUNCHED("k_recip");
+  return PB_OK;
+}
+
+int transport_pass(pb_dev *d, const float2 *Fin_ff, const double *vel3, const double *Fold, double *Fnew,
+                   float2 *Fnew_ff, cudaStream_t st) {
+  const int n = (int)d->nitems;
+  const uint4 *col4 = (const uint4 *)d->col;
+  const float4 *W4 = (const float4 *)d->wt;
+  const int64_t need = (d->nitems * 32 + 511) / 512;
+  if (d->smem_F) {
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)d->sm_count * d->ctas_tr));
+    dev::k_stream_tr<true><<<grid, 512, d->smem_F, st>>>(d->items, n, W4, col4, Fin_ff, (int)d->ns, d->part);
+  } else {
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)d->sm_count * d->ctas_tr));
+    dev::k_stream_tr<false><<<grid, 512, 0, st>>>(d->items, n, W4, col4, Fin_ff, (int)d->ns, d->part);
+  }
+  PB_LAUNCHED("k_stream_tr");
+  dev::k_fin_tr<<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->tau, vel3, Fold, Fnew,
+                                                    Fnew_ff, d->red);
+  PB_LAUNCHED("k_fin_tr");
+  dev::k_red_final<<<1, 256, 0, st>>>(d->red, d->nfin_blocks, d->scal);
+  PB_LAUNCHED("k_red_final");
+  return PB_OK;
+}
+
+}  // namespace
+
+extern "C" int pb_collision(pb_dev *d, const double *f, double *dfdt, void *stream) {
+  clear_error();
+  if (!d || !f || !dfdt) return set_error(PB_EINVAL, "pb_collision: null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc;
+  if (d->variant == PB_VARIANT_FF && (rc = to_ff(d, f, d->ns, d->yff, st))) return rc;
+  if ((rc = launch_stream(d, dev::MODE_COLL, f, d->yff, st))) return rc;
+  launch_fin<-1>(d, f, dfdt, nullptr, 0.0, st);
+  PB_LAUNCHED("k_fin_coll");
+  return PB_OK;
+}
+
+extern "C" int pb_scatter_rates(pb_dev *d, const double *f, double *inv_tau, void *stream) {
+  clear_error();
+  if (!d || !f || !inv_tau) return set_error(PB_EINVAL, "pb_scatter_rates: null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc;
+  if (d->variant == PB_VARIANT_FF && (rc = to_ff(d, f, d->ns, d->yff, st))) return rc;
+  if ((rc = launch_stream(d, dev::MODE_RATE, f, d->yff, st))) return rc;
+  if (d->variant == PB_VARIANT_LITERAL)
+    dev::k_fin_rate<true><<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->c, d->R, inv_tau);
+  else
+    dev::k_fin_rate<false><<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->c, d->R, inv_tau);
+  PB_LAUNCHED("k_fin_rate");
+  return PB_OK;
+}
+
+extern "C" int pb_rtbte_rk4_step(pb_dev *d, double *f, double dt, int32_t nsteps, void *stream) {
+  clear_error();
+  if (!d || !f) return set_error(PB_EINVAL, "pb_rtbte_rk4_step: null argument");
+  if (nsteps < 0 || !std::isfinite(dt)) return set_error(PB_EINVAL, "pb_rtbte_rk4_step: bad dt or nsteps");
+  if (nsteps == 0) return PB_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = ensure_rk_graph(d, f, dt);
+  if (rc) return rc;
+  if ((rc = to_ff(d, f, d->ns, d->yff, st))) return rc;
+  for (int32_t i = 0; i < nsteps; ++i) PB_CUDA(cudaGraphLaunch(d->rk_exec, st));
+  return PB_OK;
+}
+
+extern "C" int pb_rtbte_rk4_host(pb_dev *d, const double *f_host_in, double *f_host_out, double dt, int32_t nsteps,
+                                 void *stream) {
+  clear_error();
+  if (!d || !f_host_in || !f_host_out) return set_error(PB_EINVAL, "pb_rtbte_rk4_host: null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double) * (size_t)d->ns;
+  PB_CUDA(cudaMemcpyAsync(d->fstage, f_host_in, bytes, cudaMemcpyHostToDevice, st));
+  int rc = pb_rtbte_rk4_step(d, d->fstage, dt, nsteps, stream);
+  if (rc) return rc;
+  PB_CUDA(cudaMemcpyAsync(f_host_out, d->fstage, bytes, cudaMemcpyDeviceToHost, st));
+  PB_CUDA(cudaStreamSynchronize(st));
+  return PB_OK;
+}
+
+extern "C" int pb_transport_setup(pb_dev *d, const double *f0, void *stream) {
+  clear_error();
+  if (!d || !f0) return set_error(PB_EINVAL, "pb_transport_setup: null argument");
+  return ensure_weights(d, f0, (cudaStream_t)stream);
+}
+
+extern "C" int pb_transport_iterate(pb_dev *d, const double *vel3, const double *F3in, double *F3out,
+                                    double *resid3, void *stream) {
+  clear_error();
+  if (!d || !vel3 || !F3in || !F3out) return set_error(PB_EINVAL, "pb_transport_iterate: null argument");
+  if (!d->transport) return set_error(PB_EINVAL, "transport buffers were not reserved (pb_dev_opts.transport = 0)");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc;
+  if ((rc = to_ff(d, F3in, 3 * d->ns, d->Fff, st))) return rc;
+  if ((rc = transport_pass(d, d->Fff, vel3, F3in, F3out, d->Fff, st))) return rc;
+  if (resid3) PB_CUDA(cudaMemcpyAsync(resid3, d->scal, 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return PB_OK;
+}
+
+extern "C" int pb_transport_map(pb_dev *d, const double *f0, const double *vel3, const double *F3in, double *F3out,
+                                void *stream) {
+  clear_error();
+  if (!d || !f0 || !vel3 || !F3in || !F3out) return set_error(PB_EINVAL, "pb_transport_map: null argument");
+  int rc = pb_transport_setup(d, f0, stream);
+  if (rc) return rc;
+  return pb_transport_iterate(d, vel3, F3in, F3out, nullptr, stream);
+}
+
+extern "C" int pb_iter_transport(pb_dev *d, const double *f0, const double *vel3, double tol, int32_t maxit,
+                                 double *F3, int32_t *iters, double *resid, void *stream) {
+  clear_error();
+  if (!d || !f0 || !vel3 || !F3) return set_error(PB_EINVAL, "pb_iter_transport: null argument");
+  if (maxit < 0 || !(tol >= 0.0)) return set_error(PB_EINVAL, "pb_iter_transport: bad tol or maxit");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc;
+  if ((rc = ensure_weights(d, f0, st))) return rc;
+  const int g3 = (int)((3 * d->ns + 255) / 256);
+  dev::k_tr_init<<<g3, 256, 0, st>>>(d->tau, vel3, (int)d->ns, d->Fa, d->Fff);
+  PB_LAUNCHED("k_tr_init");
+  double *Fcur = d->Fa, *Fnext = d->Fb;
+  double res = INFINITY;
+  int32_t it = 0;
+  double h[3] = {0, 0, 0};
+  while (it < maxit) {
+    if ((rc = transport_pass(d, d->Fff, vel3, Fcur, Fnext, d->Fff, st))) return rc;
+    PB_CUDA(cudaMemcpyAsync(h, d->scal, sizeof h, cudaMemcpyDeviceToHost, st));
+    PB_CUDA(cudaStreamSynchronize(st));
+    std::swap(Fcur, Fnext);
+    ++it;
+    res = h[0];
+    if (!std::isfinite(res)) break;
+    if (res <= tol) break;
+  }
+  PB_CUDA(cudaMemcpyAsync(F3, Fcur, sizeof(double) * 3 * d->ns, cudaMemcpyDeviceToDevice, st));
+  PB_CUDA(cudaStreamSynchronize(st));
+  if (iters) *iters = it;
+  if (resid) *resid = res;
+  if (!(res <= tol))
+    return set_error(PB_ENOCONV, "pb_iter_transport: relative change %.3e after %d iterations (tol %.3e)", res, it, tol);
+  return PB_OK;
+}
+
+extern "C" int pb_observables(pb_dev *d, const double *f, double *out3, void *stream) {
+  clear_error();
+  if (!d || !f || !out3) return set_error(PB_EINVAL, "pb_observables: null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = pb_collision(d, f, d->acc, stream);
+  if (rc) return rc;
+  dev::k_observables<<<1, 1024, 0, st>>>(f, d->eps, d->acc, (int)d->ns, out3);
+  PB_LAUNCHED("k_observables");
+  return PB_OK;
+}

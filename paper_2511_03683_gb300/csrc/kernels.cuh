@@ -1,0 +1,548 @@
+// Device kernels of libpb.so (sm_103a).
+//
+// The hot path is the channel sum of Eq. 2 (arXiv:2511.03683), evaluated as a
+// streaming segmented reduction over the state-segmented CSR list: every work item
+// is a contiguous piece of one state's row, one warp streams it with 128-bit loads,
+// gathers the partner occupations from shared memory, reduces with warp shuffles
+// and writes one partial per item; a finaliser adds each row's partials in a fixed
+// order.  No global atomics anywhere (the paper's motivation for its target layer,
+// Sec. "Optimized GPU algorithm"), and results are deterministic run to run.
+//
+// Algebra used by the coefficient variants.  With G_a = G(x+w), G_e = G(x-w):
+//   term_c = f_s (1-f_p) P_out - (1-f_s) f_p P_in,
+//   P_out  = g2 [G_a N + G_e (N+1)]   (rate s -> p),
+//   P_in   = g2 [G_a (N+1) + G_e N]   (rate p -> s),   D = P_out - P_in = g2 (G_e - G_a),
+// so  I_s = c [ A_s - f_s (R_s - B_s) ],  A_s = sum f_p P_in,  B_s = sum f_p D,
+//     R_s = sum P_out,  and  1/tau_s = c (R_s - B_s),  c = 2 pi / (hbar N_q).
+// This is Eq. 2 with F_abs, F_em expanded (exact up to rounding order).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pb {
+namespace dev {
+
+struct Item {
+  long long start;  // first channel (padded CSR offset; multiple of 8)
+  int len;          // channels (multiple of 8)
+  int row;          // window state
+};
+
+constexpr int kBlock = 256;  // threads per CTA of the streaming kernels
+
+// Per-item partial sums (up to three accumulators plus one spare), 32-byte aligned.
+struct alignas(32) Part4 {
+  double x, y, z, w;
+};
+
+__device__ __forceinline__ Part4 make_part4(double x, double y, double z, double w) {
+  Part4 p;
+  p.x = x;
+  p.y = y;
+  p.z = z;
+  p.w = w;
+  return p;
+}
+
+// ------------------------------------------------------------ float-float helpers
+// A float-float value is hi + lo with |lo| <= ulp(hi)/2: a 48-bit significand with the
+// FP32 exponent range.  Error-free transformations (Dekker 1971, Knuth TwoSum) use
+// explicitly rounded intrinsics so the compiler never contracts them.
+
+__device__ __forceinline__ float2 ff_split(double v) {
+  const float h = __double2float_rn(v);
+  return make_float2(h, __double2float_rn(v - (double)h));
+}
+
+__device__ __forceinline__ double ff_to_double(float h, float l) { return (double)h + (double)l; }
+
+// (h, l) += x * (ah, al)
+__device__ __forceinline__ void ff_mac(float &h, float &l, float2 x, float ah, float al) {
+  const float p = __fmul_rn(x.x, ah);
+  float e = __fmaf_rn(x.x, ah, -p);
+  e = __fmaf_rn(x.x, al, e);
+  e = __fmaf_rn(x.y, ah, e);
+  const float s = __fadd_rn(h, p);
+  const float bb = __fsub_rn(s, h);
+  float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  err = __fadd_rn(err, __fadd_rn(l, e));
+  h = __fadd_rn(s, err);
+  l = __fsub_rn(err, __fsub_rn(h, s));
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double gauss(double x, double inv2s2, double norm) { return norm * exp(-x * x * inv2s2); }
+
+__device__ __forceinline__ int q_of(short4 ks, short4 kp, int N1, int N2, int N3) {
+  int d1 = kp.x - ks.x, d2 = kp.y - ks.y, d3 = kp.z - ks.z;
+  d1 += d1 < 0 ? N1 : 0;
+  d2 += d2 < 0 ? N2 : 0;
+  d3 += d3 < 0 ? N3 : 0;
+  return (d1 * N2 + d2) * N3 + d3;
+}
+
+// ------------------------------------------------------------ setup kernels
+
+// (hbar w, N) per (q, nu); N = 1/(exp(w/kT)-1) for w > 0, else 0 (such channels are not stored)
+__global__ void k_table(const double *__restrict__ omega, long long n, double kT, double2 *__restrict__ tab) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double w = omega[i];
+    tab[i] = make_double2(w, w > 0.0 ? 1.0 / expm1(w / kT) : 0.0);
+  }
+}
+
+__global__ void k_to_ff(const double *__restrict__ x, long long n, float2 *__restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = ff_split(x[i]);
+}
+
+struct ChanGeom {
+  const uint32_t *col;   // packed partner | nu << 24
+  const double *g2;      // |g|^2 per channel (0 on padding)
+  const double *eps;     // [ns]
+  const short4 *kc;      // [ns] grid coordinates
+  const double2 *tab;    // [nq][nmodes] (w, N)
+  int N1, N2, N3, nmodes;
+  double inv2s2, norm;   // 1/(2 sigma^2), 1/(sqrt(2 pi) sigma)
+};
+
+__device__ __forceinline__ void channel_deltas(const ChanGeom &g, int r, uint32_t cw, double &g2, double &Ga,
+                                               double &Ge, double &N, int &p, long long c) {
+  p = (int)(cw & 0xFFFFFFu);
+  const int nu = (int)(cw >> 24);
+  const int iq = q_of(g.kc[r], g.kc[p], g.N1, g.N2, g.N3);
+  const double2 wN = g.tab[(long long)iq * g.nmodes + nu];
+  const double x = g.eps[r] - g.eps[p];
+  g2 = g.g2[c];
+  Ga = gauss(x + wN.x, g.inv2s2, g.norm);
+  Ge = gauss(x - wN.x, g.inv2s2, g.norm);
+  N = wN.y;
+}
+
+// Per-channel rate coefficients (P_in, D) in FP64, stored as float-float (FF=true) or
+// double; part[item].x = sum over the item of P_out (for R_s).
+template <bool FF>
+__global__ void __launch_bounds__(kBlock) k_coef(const Item *__restrict__ items, int nitems, ChanGeom g,
+                                                 void *__restrict__ coefA, void *__restrict__ coefB,
+                                                 Part4 *__restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    double acc = 0.0;
+    for (int j = lane; j < I.len; j += 32) {
+      const long long c = I.start + j;
+      double g2, Ga, Ge, N;
+      int p;
+      channel_deltas(g, I.row, g.col[c], g2, Ga, Ge, N, p, c);
+      const double pin = g2 * (Ga * (N + 1.0) + Ge * N);
+      const double dd = g2 * (Ge - Ga);
+      acc += g2 * (Ga * N + Ge * (N + 1.0));
+      if (FF) {
+        ((float2 *)coefA)[c] = ff_split(pin);
+        ((float2 *)coefB)[c] = ff_split(dd);
+      } else {
+        ((double *)coefA)[c] = pin;
+        ((double *)coefB)[c] = dd;
+      }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) part[it] = make_part4(acc, 0.0, 0.0, 0.0);
+  }
+}
+
+// Transport weights W_c = c g2 [G_a (N + f0_p) + G_e (N + 1 - f0_p)] stored float-float;
+// part[item].x = sum of W over the item (for 1/tau_s at f0).
+__global__ void __launch_bounds__(kBlock) k_weights(const Item *__restrict__ items, int nitems, ChanGeom g,
+                                                    const double *__restrict__ f0, double cpref,
+                                                    float2 *__restrict__ wt, Part4 *__restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    double acc = 0.0;
+    for (int j = lane; j < I.len; j += 32) {
+      const long long c = I.start + j;
+      double g2, Ga, Ge, N;
+      int p;
+      channel_deltas(g, I.row, g.col[c], g2, Ga, Ge, N, p, c);
+      const double fp = f0[p];
+      const double W = cpref * g2 * (Ga * (N + fp) + Ge * (N + 1.0 - fp));
+      wt[c] = ff_split(W);
+      acc += W;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) part[it] = make_part4(acc, 0.0, 0.0, 0.0);
+  }
+}
+
+// out[r] = sum of part[i].x over the items of row r, in item order
+__global__ void k_rowsum(const int *__restrict__ item_ptr, const Part4 *__restrict__ part, int ns,
+                         double *__restrict__ out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= ns) return;
+  double s = 0.0;
+  for (int i = item_ptr[r]; i < item_ptr[r + 1]; ++i) s += part[i].x;
+  out[r] = s;
+}
+
+__global__ void k_recip(const double *__restrict__ x, int n, double *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = x[i] > 0.0 ? 1.0 / x[i] : 0.0;
+}
+
+// ------------------------------------------------------------ streaming kernels
+enum { MODE_COLL = 0, MODE_RATE = 1 };
+
+// Float-float coefficient stream.  Channel c: coefA[c] = P_in (hi,lo), coefB[c] = D (hi,lo),
+// col4 = packed partner index.  One warp per item, each lane two 4-channel groups per trip.
+// part[item] = (A, B) where A = sum f_p P_in, B = sum f_p D (MODE_RATE: only B).
+template <int MODE, bool SMEM>
+__global__ void __launch_bounds__(kBlock) k_stream_ff(const Item *__restrict__ items, int nitems,
+                                                      const float4 *__restrict__ A4, const float4 *__restrict__ B4,
+                                                      const uint4 *__restrict__ col4,
+                                                      const float2 *__restrict__ fg, int ns,
+                                                      Part4 *__restrict__ part) {
+  extern __shared__ float2 fsm[];
+  if (SMEM) {
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) fsm[i] = fg[i];
+    __syncthreads();
+  }
+  const float2 *__restrict__ fv = SMEM ? fsm : fg;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    const long long g0 = I.start >> 2;
+    const int ng = I.len >> 2;
+    float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;
+    int g = lane;
+    for (; g + 32 < ng; g += 64) {
+      const long long q0 = g0 + g, q1 = q0 + 32;
+      const uint4 c0 = __ldcs(col4 + q0), c1 = __ldcs(col4 + q1);
+      float4 a00, a01, a10, a11;
+      if (MODE == MODE_COLL) {
+        a00 = __ldcs(A4 + 2 * q0); a01 = __ldcs(A4 + 2 * q0 + 1);
+        a10 = __ldcs(A4 + 2 * q1); a11 = __ldcs(A4 + 2 * q1 + 1);
+      }
+      const float4 b00 = __ldcs(B4 + 2 * q0), b01 = __ldcs(B4 + 2 * q0 + 1);
+      const float4 b10 = __ldcs(B4 + 2 * q1), b11 = __ldcs(B4 + 2 * q1 + 1);
+      const float2 f0 = fv[c0.x & 0xFFFFFFu], f1 = fv[c0.y & 0xFFFFFFu], f2 = fv[c0.z & 0xFFFFFFu], f3 = fv[c0.w & 0xFFFFFFu];
+      const float2 f4 = fv[c1.x & 0xFFFFFFu], f5 = fv[c1.y & 0xFFFFFFu], f6 = fv[c1.z & 0xFFFFFFu], f7 = fv[c1.w & 0xFFFFFFu];
+      if (MODE == MODE_COLL) {
+        ff_mac(ah, al, f0, a00.x, a00.y); ff_mac(ah, al, f1, a00.z, a00.w);
+        ff_mac(ah, al, f2, a01.x, a01.y); ff_mac(ah, al, f3, a01.z, a01.w);
+        ff_mac(ah, al, f4, a10.x, a10.y); ff_mac(ah, al, f5, a10.z, a10.w);
+        ff_mac(ah, al, f6, a11.x, a11.y); ff_mac(ah, al, f7, a11.z, a11.w);
+      }
+      ff_mac(bh, bl, f0, b00.x, b00.y); ff_mac(bh, bl, f1, b00.z, b00.w);
+      ff_mac(bh, bl, f2, b01.x, b01.y); ff_mac(bh, bl, f3, b01.z, b01.w);
+      ff_mac(bh, bl, f4, b10.x, b10.y); ff_mac(bh, bl, f5, b10.z, b10.w);
+      ff_mac(bh, bl, f6, b11.x, b11.y); ff_mac(bh, bl, f7, b11.z, b11.w);
+    }
+    if (g < ng) {
+      const long long q0 = g0 + g;
+      const uint4 c0 = __ldcs(col4 + q0);
+      const float2 f0 = fv[c0.x & 0xFFFFFFu], f1 = fv[c0.y & 0xFFFFFFu], f2 = fv[c0.z & 0xFFFFFFu], f3 = fv[c0.w & 0xFFFFFFu];
+      if (MODE == MODE_COLL) {
+        const float4 a00 = __ldcs(A4 + 2 * q0), a01 = __ldcs(A4 + 2 * q0 + 1);
+        ff_mac(ah, al, f0, a00.x, a00.y); ff_mac(ah, al, f1, a00.z, a00.w);
+        ff_mac(ah, al, f2, a01.x, a01.y); ff_mac(ah, al, f3, a01.z, a01.w);
+      }
+      const float4 b00 = __ldcs(B4 + 2 * q0), b01 = __ldcs(B4 + 2 * q0 + 1);
+      ff_mac(bh, bl, f0, b00.x, b00.y); ff_mac(bh, bl, f1, b00.z, b00.w);
+      ff_mac(bh, bl, f2, b01.x, b01.y); ff_mac(bh, bl, f3, b01.z, b01.w);
+    }
+    const double A = warp_sum(MODE == MODE_COLL ? ff_to_double(ah, al) : 0.0);
+    const double B = warp_sum(ff_to_double(bh, bl));
+    if (lane == 0) part[it] = make_part4(A, B, 0.0, 0.0);
+  }
+}
+
+// Same coefficient stream held as doubles, with native FP64 FMAs (f gathered as double).
+template <int MODE, bool SMEM>
+__global__ void __launch_bounds__(kBlock) k_stream_f64(const Item *__restrict__ items, int nitems,
+                                                       const double2 *__restrict__ A2, const double2 *__restrict__ B2,
+                                                       const uint4 *__restrict__ col4, const double *__restrict__ fg,
+                                                       int ns, Part4 *__restrict__ part) {
+  extern __shared__ double fsd[];
+  if (SMEM) {
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) fsd[i] = fg[i];
+    __syncthreads();
+  }
+  const double *__restrict__ fv = SMEM ? fsd : fg;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    const long long g0 = I.start >> 2;
+    const int ng = I.len >> 2;
+    double A = 0.0, B = 0.0;
+    for (int g = lane; g < ng; g += 32) {
+      const long long q = g0 + g;
+      const uint4 c = __ldcs(col4 + q);
+      const double f0 = fv[c.x & 0xFFFFFFu], f1 = fv[c.y & 0xFFFFFFu], f2 = fv[c.z & 0xFFFFFFu], f3 = fv[c.w & 0xFFFFFFu];
+      if (MODE == MODE_COLL) {
+        const double2 a0 = __ldcs(A2 + 2 * q), a1 = __ldcs(A2 + 2 * q + 1);
+        A = fma(f0, a0.x, A); A = fma(f1, a0.y, A); A = fma(f2, a1.x, A); A = fma(f3, a1.y, A);
+      }
+      const double2 b0 = __ldcs(B2 + 2 * q), b1 = __ldcs(B2 + 2 * q + 1);
+      B = fma(f0, b0.x, B); B = fma(f1, b0.y, B); B = fma(f2, b1.x, B); B = fma(f3, b1.y, B);
+    }
+    A = warp_sum(A);
+    B = warp_sum(B);
+    if (lane == 0) part[it] = make_part4(A, B, 0.0, 0.0);
+  }
+}
+
+// The literal form: stream |g|^2 and the packed (partner, nu) word, and evaluate the two
+// Gaussians, the Bose factor lookup and F_abs / F_em of Eq. 2 in FP64 registers.
+// part[item].x = sum of g2 [G_a F_abs + G_e F_em] (MODE_COLL) or of the rate summand.
+template <int MODE>
+__global__ void __launch_bounds__(kBlock) k_stream_literal(const Item *__restrict__ items, int nitems, ChanGeom g,
+                                                           const double *__restrict__ f, Part4 *__restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    const double fs = f[I.row];
+    double acc = 0.0;
+    for (int j = lane; j < I.len; j += 32) {
+      const long long c = I.start + j;
+      double g2, Ga, Ge, N;
+      int p;
+      channel_deltas(g, I.row, __ldcs(g.col + c), g2, Ga, Ge, N, p, c);
+      const double fp = f[p];
+      if (MODE == MODE_COLL) {
+        const double Fabs = fs * (1.0 - fp) * N - (1.0 - fs) * fp * (N + 1.0);
+        const double Fem = fs * (1.0 - fp) * (N + 1.0) - (1.0 - fs) * fp * N;
+        acc += g2 * (Ga * Fabs + Ge * Fem);
+      } else {
+        acc += g2 * (Ga * (N + fp) + Ge * (N + 1.0 - fp));
+      }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) part[it] = make_part4(acc, 0.0, 0.0, 0.0);
+  }
+}
+
+// Transport: stream W (float-float, c folded in) and the packed index; gather F[p][0..2]
+// (float-float, [ns][3]) and accumulate the three field directions in one pass.
+template <bool SMEM>
+__global__ void __launch_bounds__(512) k_stream_tr(const Item *__restrict__ items, int nitems,
+                                                   const float4 *__restrict__ W4, const uint4 *__restrict__ col4,
+                                                   const float2 *__restrict__ Fg, int ns,
+                                                   Part4 *__restrict__ part) {
+  extern __shared__ float2 Fsm[];
+  if (SMEM) {
+    for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) Fsm[i] = Fg[i];
+    __syncthreads();
+  }
+  const float2 *__restrict__ Fv = SMEM ? Fsm : Fg;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    const long long g0 = I.start >> 2;
+    const int ng = I.len >> 2;
+    float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f, zh = 0.f, zl = 0.f;
+    for (int g = lane; g < ng; g += 32) {
+      const long long q = g0 + g;
+      const uint4 c = __ldcs(col4 + q);
+      const float4 w0 = __ldcs(W4 + 2 * q), w1 = __ldcs(W4 + 2 * q + 1);
+      const unsigned p[4] = {c.x & 0xFFFFFFu, c.y & 0xFFFFFFu, c.z & 0xFFFFFFu, c.w & 0xFFFFFFu};
+      const float wh[4] = {w0.x, w0.z, w1.x, w1.z};
+      const float wl[4] = {w0.y, w0.w, w1.y, w1.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 *F = Fv + 3 * p[k];
+        ff_mac(xh, xl, F[0], wh[k], wl[k]);
+        ff_mac(yh, yl, F[1], wh[k], wl[k]);
+        ff_mac(zh, zl, F[2], wh[k], wl[k]);
+      }
+    }
+    const double X = warp_sum(ff_to_double(xh, xl));
+    const double Y = warp_sum(ff_to_double(yh, yl));
+    const double Z = warp_sum(ff_to_double(zh, zl));
+    if (lane == 0) part[it] = make_part4(X, Y, Z, 0.0);
+  }
+}
+
+// ------------------------------------------------------------ finalisers
+
+// Row totals of the (A, B) partials (coefficient variants) or of the literal sums.
+__device__ __forceinline__ void row_partials(const int *__restrict__ item_ptr, const Part4 *__restrict__ part, int r,
+                                             double &A, double &B) {
+  A = 0.0;
+  B = 0.0;
+  for (int i = item_ptr[r]; i < item_ptr[r + 1]; ++i) {
+    const Part4 v = part[i];
+    A += v.x;
+    B += v.y;
+  }
+}
+
+// Collision epilogue fused with the RK4 stage arithmetic.
+//   STAGE < 0 : out[r] = I_r (plain pb_collision)
+//   STAGE 0..3: classic RK4 stage k_{STAGE+1} = I[y]; see the host driver for buffers.
+template <bool LIT, int STAGE>
+__global__ void k_fin_coll(const int *__restrict__ item_ptr, const Part4 *__restrict__ part, int ns, double c,
+                           const double *__restrict__ R, const double *__restrict__ ysrc, double *__restrict__ out,
+                           double *__restrict__ f, double *__restrict__ acc, double *__restrict__ y,
+                           float2 *__restrict__ yff, double dt) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= ns) return;
+  double A, B;
+  row_partials(item_ptr, part, r, A, B);
+  const double I = LIT ? -c * A : c * (A - ysrc[r] * (R[r] - B));
+  if (STAGE < 0) {
+    out[r] = I;
+    return;
+  }
+  const double fr = f[r];
+  double yn;
+  if (STAGE == 0) {
+    acc[r] = I;
+    yn = fr + 0.5 * dt * I;
+  } else if (STAGE == 1) {
+    acc[r] += 2.0 * I;
+    yn = fr + 0.5 * dt * I;
+  } else if (STAGE == 2) {
+    acc[r] += 2.0 * I;
+    yn = fr + dt * I;
+  } else {
+    yn = fr + dt / 6.0 * (acc[r] + I);
+    f[r] = yn;
+  }
+  y[r] = yn;
+  yff[r] = ff_split(yn);
+}
+
+template <bool LIT>
+__global__ void k_fin_rate(const int *__restrict__ item_ptr, const Part4 *__restrict__ part, int ns, double c,
+                           const double *__restrict__ R, double *__restrict__ out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= ns) return;
+  double A, B;
+  row_partials(item_ptr, part, r, A, B);
+  out[r] = LIT ? c * A : c * (R[r] - B);
+}
+
+// F_new = tau (v + sum W F); ff copy for the next pass; per-block max |dF| and max |F|.
+__global__ void __launch_bounds__(256) k_fin_tr(const int *__restrict__ item_ptr, const Part4 *__restrict__ part,
+                                                int ns, const double *__restrict__ tau,
+                                                const double *__restrict__ vel3, const double *__restrict__ Fold,
+                                                double *__restrict__ Fnew, float2 *__restrict__ Fff,
+                                                double2 *__restrict__ red) {
+  __shared__ double sd[256], sf[256];
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  double dm = 0.0, fm = 0.0;
+  if (r < ns) {
+    double X = 0.0, Y = 0.0, Z = 0.0;
+    for (int i = item_ptr[r]; i < item_ptr[r + 1]; ++i) {
+      const Part4 v = part[i];
+      X += v.x;
+      Y += v.y;
+      Z += v.z;
+    }
+    const double S[3] = {X, Y, Z};
+    const double t = tau[r];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double Fn = t * (vel3[3 * r + a] + S[a]);
+      if (Fold) dm = fmax(dm, fabs(Fn - Fold[3 * r + a]));
+      fm = fmax(fm, fabs(Fn));
+      Fnew[3 * r + a] = Fn;
+      Fff[3 * r + a] = ff_split(Fn);
+    }
+  }
+  sd[threadIdx.x] = dm;
+  sf[threadIdx.x] = fm;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sd[threadIdx.x] = fmax(sd[threadIdx.x], sd[threadIdx.x + o]);
+      sf[threadIdx.x] = fmax(sf[threadIdx.x], sf[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) red[blockIdx.x] = make_double2(sd[0], sf[0]);
+}
+
+__global__ void k_red_final(const double2 *__restrict__ red, int n, double *__restrict__ out) {
+  __shared__ double sd[256], sf[256];
+  double d = 0.0, m = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    d = fmax(d, red[i].x);
+    m = fmax(m, red[i].y);
+  }
+  sd[threadIdx.x] = d;
+  sf[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sd[threadIdx.x] = fmax(sd[threadIdx.x], sd[threadIdx.x + o]);
+      sf[threadIdx.x] = fmax(sf[threadIdx.x], sf[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = sf[0] > 0.0 ? sd[0] / sf[0] : 0.0;
+    out[1] = sd[0];
+    out[2] = sf[0];
+  }
+}
+
+// F^0 = tau v and its float-float copy
+__global__ void k_tr_init(const double *__restrict__ tau, const double *__restrict__ vel3, int ns,
+                          double *__restrict__ F, float2 *__restrict__ Fff) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * ns) return;
+  const double v = tau[i / 3] * vel3[i];
+  F[i] = v;
+  Fff[i] = ff_split(v);
+}
+
+// Deterministic single-block sums: out[0] = sum f, out[1] = sum eps f, out[2] = sum I.
+__global__ void k_observables(const double *__restrict__ f, const double *__restrict__ eps,
+                              const double *__restrict__ I, int ns, double *__restrict__ out) {
+  __shared__ double s0[1024], s1[1024], s2[1024];
+  double a = 0.0, b = 0.0, d = 0.0;
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+    a += f[i];
+    b += eps[i] * f[i];
+    d += I[i];
+  }
+  s0[threadIdx.x] = a;
+  s1[threadIdx.x] = b;
+  s2[threadIdx.x] = d;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s0[threadIdx.x] += s0[threadIdx.x + o];
+      s1[threadIdx.x] += s1[threadIdx.x + o];
+      s2[threadIdx.x] += s2[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = s0[0];
+    out[1] = s1[0];
+    out[2] = s2[0];
+  }
+}
+
+}  // namespace dev
+}  // namespace pb

@@ -1,0 +1,117 @@
+"""Host-side tests of the C ABI (no GPU): the library loads, exports every symbol the
+header declares, and the channel builder (host C++) produces the CSR the paper's
+problem statement defines, checked against the oracle's own enumeration."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pb():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2511_03683_gb300 as pb
+
+    return pb
+
+
+def test_every_declared_symbol_is_exported(pb):
+    hdr = open(os.path.join(ROOT, "include", "pb.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    names = set(re.findall(r"\b(pb_[a-z0-9_]+)\s*\(", hdr))
+    names -= {"pb_g2_fn"}
+    assert len(names) >= 15
+    L = ctypes.CDLL(pb.LIB_PATH)
+    missing = [n for n in sorted(names) if not hasattr(L, n)]
+    assert not missing, missing
+    assert pb.lib().pb_version().decode().startswith("pb ")
+
+
+def test_no_global_atomics_in_device_code():
+    src = open(os.path.join(ROOT, "paper_2511_03683_gb300", "csrc", "kernels.cuh")).read()
+    src += open(os.path.join(ROOT, "paper_2511_03683_gb300", "csrc", "device.cu")).read()
+    code = re.sub(r"//[^\n]*", "", re.sub(r"/\*.*?\*/", "", src, flags=re.S))
+    assert not re.search(r"\batomic[A-Za-z_]*\s*\(|\bred\.|\batom\.", code)
+
+
+@pytest.mark.parametrize("model", [synth.make_tiny(4), synth.make_window4(12), synth.make_window4(16)],
+                         ids=["tiny4", "win12", "win16"])
+def test_builder_csr_matches_oracle_enumeration(pb, model):
+    ch = pb.Channels.from_model(model)
+    o = oracle.Oracle(model)
+    assert ch.nstate == o.nstate
+    assert ch.nchannels == o.count_channels()
+    e = ch.export()
+    assert np.array_equal(e["state_ids"], o.ids)
+    rp = e["row_ptr"]
+    assert rp[0] == 0 and rp[-1] == ch.nchannels and np.all(np.diff(rp) >= 0)
+    nk = model.nk
+    nb = model.nbands
+    ik = o.ids // nb
+    j = np.stack([ik // (nk[1] * nk[2]), (ik // nk[2]) % nk[1], ik % nk[2]], axis=1)
+    for r in [0, 1, ch.nstate // 2, ch.nstate - 1]:
+        cols = e["col"][rp[r]:rp[r + 1]]
+        nus = e["nu"][rp[r]:rp[r + 1]]
+        # sorted by (partner, nu), every partner in range
+        key = cols.astype(np.int64) * 256 + nus
+        assert np.all(np.diff(key) > 0)
+        q = (j[cols] - j[r]) % np.array(nk)
+        iq = (q[:, 0] * nk[1] + q[:, 1]) * nk[2] + q[:, 2]
+        assert np.all(model.omega[iq, nus] > 0)
+        # |g|^2 comes from the callback with full-grid ids
+        g = [model.g2(int(o.ids[r]), int(o.ids[p]), int(v)) for p, v in zip(cols[:20], nus[:20])]
+        assert np.array_equal(np.array(g), e["g2"][rp[r]:rp[r] + 20])
+
+
+def test_python_callback_and_closure_check(pb):
+    m = synth.make_tiny(3)
+    sym = pb.Channels.build(m.nk, m.nbands, m.nmodes, m.eps, m.omega, m.T, m.sigma,
+                            lambda s, p, nu: 1e-3 * (1.0 + 0.1 * ((s + p) % 7) + 0.01 * nu))
+    assert sym.nchannels == (27 * 2) ** 2 * 3
+    with pytest.raises(pb.PBError) as ei:
+        pb.Channels.build(m.nk, m.nbands, m.nmodes, m.eps, m.omega, m.T, m.sigma,
+                          lambda s, p, nu: 1e-3 * (1.0 + 0.1 * (s % 5)))
+    assert ei.value.code == pb.PB_ENOTCLOSED
+    with pytest.raises(pb.PBError) as ei:
+        pb.Channels.build(m.nk, m.nbands, m.nmodes, m.eps, m.omega, m.T, m.sigma, lambda s, p, nu: -np.ones(len(s)))
+    assert ei.value.code == pb.PB_ECALLBACK
+
+
+def test_builder_rejects_bad_input(pb):
+    m = synth.make_tiny(3)
+    with pytest.raises(pb.PBError) as ei:
+        pb.Channels.build(m.nk, m.nbands, m.nmodes, m.eps, m.omega, -1.0, m.sigma, m.g2_batch_ptr(), m.g2_user_ptr())
+    assert ei.value.code == pb.PB_EINVAL
+    win = np.array([[10.0, 11.0], [10.0, 11.0]])
+    with pytest.raises(pb.PBError) as ei:
+        pb.Channels.build(m.nk, m.nbands, m.nmodes, m.eps, m.omega, m.T, m.sigma, m.g2_batch_ptr(), m.g2_user_ptr(),
+                          win=win)
+    assert ei.value.code == pb.PB_EINVAL
+    bad = m.eps.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(pb.PBError):
+        pb.Channels.build(m.nk, m.nbands, m.nmodes, bad, m.omega, m.T, m.sigma, m.g2_batch_ptr(), m.g2_user_ptr())
+
+
+def test_g2_cutoff_drops_channels_symmetrically(pb):
+    m = synth.make_tiny(4)
+    full = pb.Channels.from_model(m)
+    cut = pb.Channels.from_model(m, g2_min=1e-3)
+    g = full.export()["g2"]
+    assert cut.nchannels == int((g >= 1e-3).sum()) < full.nchannels
+
+
+def test_acoustic_only_gamma_has_no_channels(pb):
+    """A 1x1x1 grid with only acoustic modes: hbar*w(Gamma) = 0 removes every channel."""
+    eps = np.array([[0.0, 0.1]])
+    ch = pb.Channels.build((1, 1, 1), 2, 1, eps, np.zeros((1, 1)), 300.0, 0.01, lambda s, p, nu: np.ones(len(s)))
+    assert ch.nstate == 2 and ch.nchannels == 0

@@ -1,0 +1,217 @@
+"""GPU parity: the sm_103a library (through its C ABI) against the FP64 CPU oracle.
+
+Error measures for the FP64-accurate variants (per-element relative error is
+undefined where the collision integral vanishes):
+  * e_abs = max_s |I_gpu - I_ref| / max_s S_s <= 1e-13 always, where S_s is the row's
+    gross scattering (the magnitudes of the in- and out-scattering products that F_abs
+    and F_em difference): the error scale of any floating-point evaluation of Eq. 2,
+    whatever the cancellation;
+  * e = max_s |I_gpu - I_ref| / max_s |I_ref| <= 1e-12 whenever the integral is not
+    dominated by cancellation (max|I_ref| >= 1e-2 max_s S_s).
+Rates, RK4 states and transport iterates have no such cancellation: e <= 1e-12.
+Conservation: |sum_s I_s| <= 1e-13 * sum_s S_s.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def pb():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2511_03683_gb300 as pb
+    import torch
+
+    assert torch.cuda.is_available()
+    return pb
+
+
+def nrel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(b).max(), 1e-300))
+
+
+def check_I(I, ref, absum, tol=TOL):
+    """Collision-integral parity with the conditioning-aware measures above."""
+    d = np.abs(np.asarray(I) - ref).max()
+    scale = np.abs(absum).max()
+    assert d <= 1e-13 * scale, f"e_abs = {d / scale:.3e}"
+    if np.abs(ref).max() >= 1e-2 * scale:
+        assert d <= tol * np.abs(ref).max(), f"e = {d / np.abs(ref).max():.3e}"
+
+
+def T(x):
+    import torch
+
+    return torch.tensor(np.ascontiguousarray(x, dtype=np.float64), device="cuda")
+
+
+SMALL = {
+    "tiny4": lambda: synth.make_tiny(4),
+    "tiny5": lambda: synth.make_tiny(5),
+    "win12": lambda: synth.make_window4(12),
+    "win16": lambda: synth.make_window4(16),
+    "tiny8": lambda: synth.make_config("tiny"),
+}
+VARIANTS = ["ff", "f64", "literal"]
+
+_cache = {}
+
+
+def setup_case(pb, name, variant, **kw):
+    key = (name, variant, tuple(sorted(kw.items())))
+    if key not in _cache:
+        m = SMALL[name]()
+        ch = pb.Channels.from_model(m)
+        dev = pb.Device(ch, variant=variant, transport=True, **kw)
+        _cache[key] = (m, oracle.Oracle(m), dev)
+    return _cache[key]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("name", list(SMALL))
+def test_collision_and_rates(pb, name, variant):
+    m, o, dev = setup_case(pb, name, variant)
+    assert dev.nstate == o.nstate and dev.nchannels == o.count_channels()
+    for f in (np.random.default_rng(7).uniform(0, 1, o.nstate), o.window_values(m.f_hot())):
+        ref, ab = o.collision(f, with_abs=True)
+        check_I(dev.collision(T(f)).cpu().numpy(), ref, ab)
+        assert nrel(dev.rates(T(f)).cpu().numpy(), o.rates(f)) <= TOL
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_conservation(pb, variant):
+    m, o, dev = setup_case(pb, "tiny8", variant)
+    f = o.window_values(m.f_hot())
+    _, ab = o.collision(f, with_abs=True)
+    obs = dev.observables(T(f)).cpu().numpy()
+    assert abs(obs[2]) <= 1e-13 * ab.sum()
+    assert abs(obs[0] - f.sum()) <= 1e-14 * f.sum()
+    assert abs(obs[1] - (o.model.eps.reshape(-1)[o.ids] * f).sum()) <= 1e-13 * abs((o.model.eps.reshape(-1)[o.ids] * f).sum())
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_rk4_tiny_workload(pb, variant):
+    """The 8^3 workload's dynamics: 10 RK4 steps of 1 fs from the hot population."""
+    m, o, dev = setup_case(pb, "tiny8", variant)
+    f0 = o.window_values(m.f_hot())
+    ft = T(f0)
+    dev.rk4(ft, 1.0, 10)
+    ref = o.rk4(f0, 1.0, 10)
+    assert nrel(ft.cpu().numpy(), ref) <= TOL
+    # the host-buffer entry point gives the same trajectory
+    out = dev.rk4_host(f0, 1.0, 10)
+    assert np.array_equal(out, ft.cpu().numpy())
+
+
+@pytest.mark.parametrize("item_channels", [64, 256, 4096])
+def test_item_split_is_invisible(pb, item_channels):
+    """Rows split into many small items (ragged tails, several tiles per row) or few large
+    ones give the same integral."""
+    m, o, dev = setup_case(pb, "win16", "ff", item_channels=item_channels)
+    f = np.random.default_rng(3).uniform(0, 1, o.nstate)
+    ref, ab = o.collision(f, with_abs=True)
+    check_I(dev.collision(T(f)).cpu().numpy(), ref, ab)
+
+
+def test_transport_map_and_solve(pb):
+    m = synth.make_tiny(4).with_(sigma=0.01)
+    o = oracle.Oracle(m)
+    dev = pb.Device(pb.Channels.from_model(m), transport=True)
+    f0 = o.window_values(m.f_fermi(0.0))
+    v = o.window_values(m.vel)
+    Fin = np.random.default_rng(5).normal(size=(o.nstate, 3))
+    ref, _ = o.transport_map(f0, v, Fin)
+    assert nrel(dev.transport_map(T(f0), T(v), T(Fin)).cpu().numpy(), ref) <= TOL
+    F, iters, res, ok = dev.transport(T(f0), T(v), tol=1e-12, maxit=3000)
+    Fr, iters_r, res_r, ok_r = o.transport(f0, v, tol=1e-12, maxit=3000)
+    assert ok and ok_r and abs(iters - iters_r) <= 1
+    F = F.cpu().numpy()
+    wgt = (f0 * (1 - f0))[:, None]
+    s_gpu, s_ref = (wgt * v * F).sum(0), (wgt * v * Fr).sum(0)
+    assert np.abs(s_gpu - s_ref).max() <= 1e-10 * np.abs(s_ref).max()
+    assert nrel(F, Fr) <= 1e-9
+
+
+def test_no_channels(pb):
+    """Acoustic-only modes on a 1x1x1 grid: no channel survives, every output is zero."""
+    eps = np.array([[0.0, 0.1]])
+    ch = pb.Channels.build((1, 1, 1), 2, 1, eps, np.zeros((1, 1)), 300.0, 0.01, lambda s, p, nu: np.ones(len(s)))
+    dev = pb.Device(ch, transport=True)
+    f = T([0.3, 0.6])
+    assert np.all(dev.collision(f).cpu().numpy() == 0.0)
+    assert np.all(dev.rates(f).cpu().numpy() == 0.0)
+    dev.rk4(f, 1.0, 3)
+    assert np.array_equal(f.cpu().numpy(), [0.3, 0.6])
+
+
+def test_single_state(pb):
+    """One state, one Einstein mode: only the self channel, which contributes nothing to I."""
+    ch = pb.Channels.build((1, 1, 1), 1, 1, np.array([[0.0]]), np.array([[0.03]]), 300.0, 0.01,
+                           lambda s, p, nu: np.full(len(s), 2e-3))
+    dev = pb.Device(ch)
+    assert dev.nchannels == 1
+    # 1/tau of the self channel: c g2 G(w) (2N+1)
+    N = 1 / np.expm1(0.03 / (8.617333262e-5 * 300))
+    G = np.exp(-0.03 ** 2 / (2 * 0.01 ** 2)) / (np.sqrt(2 * np.pi) * 0.01)
+    ref = 2 * np.pi / 0.6582119569 * 2e-3 * G * (2 * N + 1)
+    assert abs(dev.rates(T([0.4])).cpu().numpy()[0] - ref) <= 1e-13 * ref
+    # the self channel's in- and out-scattering cancel
+    assert abs(dev.collision(T([0.4])).cpu().numpy()[0]) <= 1e-13 * 0.4 * ref
+
+
+# ------------------------------------------------------------------ full size (40^3)
+
+@pytest.fixture(scope="module")
+def big(pb):
+    m = synth.make_config("window40")
+    ch = pb.Channels.from_model(m)
+    dev = pb.Device(ch, variant="ff", transport=True)
+    return m, oracle.Oracle(m), dev
+
+
+def test_full_size_counts(big):
+    m, o, dev = big
+    assert dev.nstate == o.nstate == 4756
+    assert dev.nchannels == o.count_channels()
+
+
+def test_full_size_collision_sampled_and_conserved(big):
+    m, o, dev = big
+    f = o.window_values(m.f_hot())
+    I = dev.collision(T(f)).cpu().numpy()
+    rows = np.unique(np.concatenate([np.arange(0, o.nstate, 97), [o.nstate - 1]]))
+    ref, ab = o.collision(f, rows=rows, with_abs=True)
+    check_I(I[rows], ref, ab)
+    Ifull, abfull = o.collision(f, with_abs=True)
+    check_I(I, Ifull, abfull)
+    assert np.abs(Ifull).max() >= 1e-2 * abfull.max()  # the hot population is well conditioned
+    assert abs(I.sum()) <= 1e-13 * abfull.sum()
+    r = dev.rates(T(f)).cpu().numpy()
+    assert nrel(r[rows], o.rates(f, rows=rows)) <= TOL
+
+
+def test_full_size_rk4_two_steps(big):
+    m, o, dev = big
+    f0 = o.window_values(m.f_hot())
+    ft = T(f0)
+    dev.rk4(ft, 1.0, 2)
+    assert nrel(ft.cpu().numpy(), o.rk4(f0, 1.0, 2)) <= TOL
+
+
+def test_full_size_transport_map_sampled(big):
+    m, o, dev = big
+    f0 = o.window_values(m.f_fermi(o.model.emin() - 0.2))
+    v = o.window_values(m.vel)
+    Fin = np.random.default_rng(11).normal(size=(o.nstate, 3))
+    out = dev.transport_map(T(f0), T(v), T(Fin)).cpu().numpy()
+    rows = np.arange(5, o.nstate, 211)
+    ref, _ = o.transport_map(f0, v, Fin, rows=rows)
+    assert np.abs(out[rows] - ref).max() <= TOL * np.abs(ref).max()
