@@ -261,11 +261,13 @@ def make_two_level(n: int = 3, e0: float = 0.0, w0: float = 0.05, g2: float = 2e
 
 def make_config(name: str) -> Model:
     """Named workloads: 'tiny' (8^3, ~3.1M channels), 'window40' (40^3, ~1.36e8 channels),
-    'window24' (24^3, ~6.3e6 channels)."""
+    'window24' (24^3, ~6.3e6 channels), and 'window<N>' for the same rule on an N^3 grid."""
     if name == "tiny":
         return make_tiny(8, seed=20251103)
     if name == "window40":
         return make_window4(40, seed=20251104)
     if name == "window24":
         return make_window4(24, seed=20251106)
+    if name.startswith("window") and name[6:].isdigit():
+        return make_window4(int(name[6:]), seed=20251100 + int(name[6:]))
     raise KeyError(name)
