@@ -221,6 +221,26 @@ int pb_transport_map(pb_dev *dev, const double *f0, const double *vel3, const do
  * out[2] = sum_s I_s[f] (conservation check, 1/fs).  out: device double[3]. */
 int pb_observables(pb_dev *dev, const double *f, double *out3, void *stream);
 
+/* No-allocation form of pb_collision.  It is for callers that cannot allocate device
+ * memory at all: code embedded in a host application whose device memory belongs to
+ * another allocator (a framework's caching pool, or a fixed budget carved out at
+ * start-up), so that neither the caller nor a library it calls may use cudaMalloc.
+ * The caller passes the same inputs and outputs as to pb_collision (a pb_dev, f and
+ * dfdt, device double[nstate]).  The per-call scratch (the float-float copy of f and
+ * one partial sum per work item) lives in a file-scope device array of
+ * PB_STATIC_SCRATCH_BYTES inside libpb.so, which every GPU that loads the library
+ * keeps until the process exits.  A problem needs 8*nstate (rounded up to 256) +
+ * 32*nitems bytes of it; larger ones fail with PB_EINVAL and say so (pb_collision
+ * has no such limit).  The call itself allocates nothing.
+ * The first call on each device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the one array and it keeps the last call's contents:
+ * calls that overlap on the GPU (other streams or threads) race, so the caller must
+ * serialise them.  Each call writes every scratch byte it reads before reading it,
+ * so nothing needs clearing.  The paper has no counterpart of this entry point. */
+#define PB_STATIC_SCRATCH_BYTES (4u << 20)
+int pb_collision_static(pb_dev *dev, const double *f, double *dfdt, void *stream);
+
 const char *pb_last_error(void);
 
 /* Library version string, e.g. "pb 0.1 sm_103a". */

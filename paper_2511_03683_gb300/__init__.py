@@ -106,6 +106,7 @@ def lib() -> ctypes.CDLL:
         "pb_dev_create": [vp, ctypes.POINTER(_DevOpts), vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
         "pb_dev_get_info": [vp, ctypes.POINTER(_DevInfo)],
         "pb_collision": [vp, vp, vp, vp],
+        "pb_collision_static": [vp, vp, vp, vp],
         "pb_scatter_rates": [vp, vp, vp, vp],
         "pb_rtbte_rk4_step": [vp, vp, dbl, i32, vp],
         "pb_rtbte_rk4_host": [vp, vp, vp, dbl, i32, vp],
@@ -290,6 +291,13 @@ class Device:
         fp = _dev_vec(f, self.nstate, "f")
         out = self._new(self.nstate) if out is None else out
         _check(lib().pb_collision(self._h, fp, _dev_vec(out, self.nstate, "out"), _stream_ptr(stream)))
+        return out
+
+    def collision_static(self, f, out, stream=None):
+        """pb_collision_static: the same integral with scratch in the library's fixed
+        device array (no allocation anywhere, so ``out`` must be given)."""
+        _check(lib().pb_collision_static(self._h, _dev_vec(f, self.nstate, "f"), _dev_vec(out, self.nstate, "out"),
+                                         _stream_ptr(stream)))
         return out
 
     def rates(self, f, out=None, stream=None):

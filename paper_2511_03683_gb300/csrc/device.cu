@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -735,5 +736,91 @@ extern "C" int pb_observables(pb_dev *d, const double *f, double *out3, void *st
   if (rc) return rc;
   dev::k_observables<<<1, 1024, 0, st>>>(f, d->eps, d->acc, (int)d->ns, out3);
   PB_LAUNCHED("k_observables");
+  return PB_OK;
+}
+
+// ---------------------------------------------------------------- no-allocation collision
+//
+// pb_collision_static: the collision sweep for callers that may not allocate device
+// memory.  Its per-call scratch (the float-float copy of f and one partial per work
+// item) lives in this file-scope device array instead of the arena's scratch regions.
+// Every GPU that loads the library holds the array until the process exits.  In host
+// code the symbol only names the array; its device address comes from
+// cudaGetSymbolAddress, looked up once per device with that device current.
+static __device__ __align__(256) unsigned char pb_static_scratch[PB_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxStaticDevices = 64;
+std::mutex g_static_mu;
+void *g_static_addr[kMaxStaticDevices] = {};
+
+int static_scratch_address(void **out) {
+  int devid = 0;
+  PB_CUDA(cudaGetDevice(&devid));
+  if (devid < 0 || devid >= kMaxStaticDevices)
+    return set_error(PB_EDEVICE, "pb_collision_static: device %d is beyond the %d devices it tracks", devid,
+                     kMaxStaticDevices);
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[devid]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, pb_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "pb_collision_static: cudaGetSymbolAddress");
+    g_static_addr[devid] = p;
+  }
+  *out = g_static_addr[devid];
+  return PB_OK;
+}
+
+}  // namespace
+
+extern "C" int pb_collision_static(pb_dev *d, const double *f, double *dfdt, void *stream) {
+  clear_error();
+  if (!d || !f || !dfdt) return set_error(PB_EINVAL, "pb_collision_static: null argument");
+  const size_t ff_bytes = align_up(sizeof(float2) * (size_t)d->ns);
+  const size_t part_bytes = sizeof(Part4) * (size_t)d->nitems;
+  if (ff_bytes + part_bytes > (size_t)PB_STATIC_SCRATCH_BYTES)
+    return set_error(PB_EINVAL,
+                     "pb_collision_static: this problem needs %zu bytes of scratch (%lld states, %lld work items) "
+                     "but the static array holds %zu bytes; use pb_collision or larger work items",
+                     ff_bytes + part_bytes, (long long)d->ns, (long long)d->nitems, (size_t)PB_STATIC_SCRATCH_BYTES);
+  void *base = nullptr;
+  int rc = static_scratch_address(&base);
+  if (rc) return rc;
+  float2 *fff = (float2 *)base;
+  Part4 *part = (Part4 *)((char *)base + ff_bytes);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = (int)d->nitems;
+  const uint4 *col4 = (const uint4 *)d->col;
+  if (d->variant == PB_VARIANT_FF) {
+    if ((rc = to_ff(d, f, d->ns, fff, st))) return rc;
+    const int grid = d->stream_grid(d->ctas);
+    const float4 *A4 = (const float4 *)d->coefA, *B4 = (const float4 *)d->coefB;
+    if (d->smem_f)
+      dev::k_stream_ff<dev::MODE_COLL, true><<<grid, dev::kBlock, d->smem_f, st>>>(d->items, n, A4, B4, col4, fff,
+                                                                                  (int)d->ns, part);
+    else
+      dev::k_stream_ff<dev::MODE_COLL, false><<<grid, dev::kBlock, 0, st>>>(d->items, n, A4, B4, col4, fff,
+                                                                           (int)d->ns, part);
+  } else if (d->variant == PB_VARIANT_F64) {
+    const int grid = d->stream_grid(d->ctas);
+    const double2 *A2 = (const double2 *)d->coefA, *B2 = (const double2 *)d->coefB;
+    if (d->smem_f)
+      dev::k_stream_f64<dev::MODE_COLL, true><<<grid, dev::kBlock, d->smem_f, st>>>(d->items, n, A2, B2, col4, f,
+                                                                                   (int)d->ns, part);
+    else
+      dev::k_stream_f64<dev::MODE_COLL, false><<<grid, dev::kBlock, 0, st>>>(d->items, n, A2, B2, col4, f,
+                                                                            (int)d->ns, part);
+  } else {
+    dev::k_stream_literal<dev::MODE_COLL><<<d->stream_grid(8), dev::kBlock, 0, st>>>(d->items, n, d->geom(), f, part);
+  }
+  PB_LAUNCHED("pb_collision_static: stream kernel");
+  if (d->variant == PB_VARIANT_LITERAL)
+    dev::k_fin_coll<true, -1><<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, part, (int)d->ns, d->c, d->R, f, dfdt,
+                                                                 nullptr, nullptr, nullptr, nullptr, 0.0);
+  else
+    dev::k_fin_coll<false, -1><<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, part, (int)d->ns, d->c, d->R, f, dfdt,
+                                                                  nullptr, nullptr, nullptr, nullptr, 0.0);
+  PB_LAUNCHED("pb_collision_static: k_fin_coll");
   return PB_OK;
 }
