@@ -41,6 +41,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--mixed-steps", type=int, default=1000)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-instances", type=int, default=64)
+    ap.add_argument("--batched-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -113,10 +118,40 @@ def measured_hbm():
         return FALLBACK_HBM, "fallback (6.8 TB/s)"
 
 
-def kernel_source_hash() -> str:
+def function_source(text: str, name: str) -> str:
+    """Source of the device function or kernel `name` in kernels.cuh: from its template/
+    qualifier line to the brace that closes its body (every overload, concatenated)."""
+    out = []
+    lines = text.split("\n")
+    for i, line in enumerate(lines):
+        if (f" {name}(" not in line and f" {name}<" not in line) or line.strip().startswith("//") \
+                or line.rstrip().endswith(";"):
+            continue
+        if "__device__" not in line and "__global__" not in line and "__launch_bounds__" not in line:
+            continue
+        start = i
+        while start > 0 and lines[start - 1].startswith("template"):
+            start -= 1
+        depth, j, seen = 0, i, False
+        while j < len(lines):
+            depth += lines[j].count("{") - lines[j].count("}")
+            seen = seen or "{" in lines[j]
+            if seen and depth == 0:
+                break
+            j += 1
+        out.append("\n".join(lines[start:j + 1]))
+    return "\n".join(out)
+
+
+HOT_FUNCTIONS = ("ff_split", "ff_to_double", "ff_mac", "warp_sum", "partners4", "k_stream_ff")
+
+
+def kernel_source_hash(names=HOT_FUNCTIONS) -> str:
+    """Hash of the collision sweep's own source (the kernel and the helpers it inlines)."""
+    text = open(os.path.join(ROOT, "paper_2511_03683_gb300", "csrc", "kernels.cuh")).read()
     h = hashlib.sha256()
-    for f in ("kernels.cuh", "device.cu"):
-        h.update(open(os.path.join(ROOT, "paper_2511_03683_gb300", "csrc", f), "rb").read())
+    for n in names:
+        h.update(function_source(text, n).encode())
     return h.hexdigest()[:16]
 
 
@@ -227,6 +262,138 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU
+
+
+def time_calls(fn, n, stream):
+    import torch
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    fn()
+    for a, b in evs:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in evs)
+
+
+def batched_report(pb, ninst, nsteps, stream):
+    """The batched workload: ninst instances (grids 16^3..36^3, 2-4 bands, 3-6 modes,
+    T 100-500 K, excitation 0.1-0.5 eV) in one launch per RK4 stage with FP32 |g|^2, against
+    the same instances advanced one after the other on the FP64-accurate path and on the
+    unbatched FP32 path."""
+    import numpy as np
+    import torch
+
+    import synth
+
+    inst = [synth.make_batch_instance(i) for i in range(ninst)]
+    t0 = time.perf_counter()
+    chs = [pb.Channels.from_model(m) for m, _ in inst]
+    build_s = time.perf_counter() - t0
+    fs = [m.f_hot(e_exc=e).reshape(-1)[c.state_ids()] for (m, e), c in zip(inst, chs)]
+    b = pb.Batch(chs)
+    f = torch.tensor(np.concatenate(fs), device="cuda")
+    item, ctas, tune_ms = b.autotune(f)
+    nch = b.nchannels
+    g = f.clone()
+    b.rk4(g, 1.0, 3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.rk4(g, 1.0, nsteps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1)
+    Ib = b.collision(f).cpu().numpy()
+
+    def sequential(variant):
+        devs = [pb.Device(c, variant=variant) for c in chs]
+        fl = [torch.tensor(x, device="cuda") for x in fs]
+        for d, x in zip(devs, fl):
+            d.rk4(x, 1.0, 2)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for d, x in zip(devs, fl):
+            d.rk4(x, 1.0, nsteps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        err = 0.0
+        if variant == "ff":
+            for i, (d, x) in enumerate(zip(devs, fs)):
+                ref = d.collision(torch.tensor(x, device="cuda")).cpu().numpy()
+                a, e = b.offsets[i], b.offsets[i + 1]
+                err = max(err, float(np.abs(Ib[a:e] - ref).max() / max(np.abs(ref).max(), 1e-300)))
+        for d in devs:
+            d.close()
+        return ms, err
+
+    ms_ff, err = sequential("ff")
+    ms_g, _ = sequential("g32")
+    b.close()
+    return {"instances": ninst, "states": b.nstate, "channels": nch, "build_channels_s": build_s,
+            "autotuned": {"item_channels": item, "ctas_per_sm": ctas, "sweep_ms": tune_ms},
+            "rk4_steps": nsteps, "batched_ms": ms_b,
+            "batched_channels_per_s": 4 * nch * nsteps / (ms_b * 1e-3),
+            "batched_rk4_steps_per_s": nsteps / (ms_b * 1e-3),
+            "sequential_ff_ms": ms_ff, "sequential_g32_ms": ms_g,
+            "speedup_vs_sequential_fp64_path": ms_ff / ms_b, "speedup_vs_sequential_fp32": ms_g / ms_b,
+            "dfdt_err_vs_fp64_max_over_instances": err}
+
+
+def compare_variants(pb, ch, dev_ff, fh, ff_ms, mixed_steps, stream):
+    """Collision sweep of every variant on the same channel list: time, channels/s,
+    speed-up over the FP64-accurate default and over native FP64, and df/dt error against
+    the default (which the tests hold to the FP64 oracle at 1e-12)."""
+    import numpy as np
+    import torch
+
+    f = torch.tensor(fh, device="cuda")
+    ref = dev_ff.collision(f).cpu().numpy()
+    out = {}
+    ms = {"ff": ff_ms}
+    devs = {}
+    for v in ("f64", "literal", "g32", "g16"):
+        d = pb.Device(ch, variant=v)
+        o = torch.empty(d.nstate, dtype=torch.float64, device="cuda")
+        ms[v] = time_calls(lambda: d.collision(f, out=o), 5 if v == "literal" else 20, stream)
+        err = float(np.abs(o.cpu().numpy() - ref).max() / np.abs(ref).max())
+        out[v] = {"collision_ms": ms[v], "channels_per_s": dev_ff.nchannels / (ms[v] * 1e-3),
+                  "hbm_gb_s": d.bytes_per_channel * d.nchannels / (ms[v] * 1e-3) / 1e9,
+                  "bytes_per_channel": d.bytes_per_channel, "speedup_vs_ff": ff_ms / ms[v],
+                  "dfdt_err_vs_fp64": err}
+        if v in ("g32", "g16"):
+            devs[v] = d
+        else:
+            d.close()
+    for v in out:
+        out[v]["speedup_vs_f64"] = ms["f64"] / ms[v]
+    out["ff"] = {"collision_ms": ff_ms, "channels_per_s": dev_ff.nchannels / (ff_ms * 1e-3),
+                 "speedup_vs_f64": ms["f64"] / ff_ms, "bytes_per_channel": dev_ff.bytes_per_channel}
+    # mixed precision along an FP64-accurate RK4 trajectory: per-step df/dt error
+    if mixed_steps > 0:
+        traj = torch.tensor(fh, device="cuda")
+        a = torch.empty_like(traj)
+        errs = {v: [] for v in devs}
+        bufs = {v: torch.empty_like(traj) for v in devs}
+        for _ in range(mixed_steps):
+            dev_ff.collision(traj, out=a)
+            for v, d in devs.items():
+                d.collision(traj, out=bufs[v])
+            an = a.abs().max()
+            for v in devs:
+                errs[v].append(((bufs[v] - a).abs().max() / an))
+            dev_ff.rk4(traj, 1.0, 1)
+        for v in devs:
+            e = torch.stack(errs[v]).cpu().numpy()
+            out[v]["dfdt_err_over_steps"] = {"steps": mixed_steps, "max": float(e.max()), "median": float(np.median(e)),
+                                             "final": float(e[-1])}
+            rk_ms = time_calls(lambda: devs[v].rk4(traj.clone(), 1.0, 20), 3, stream)
+            out[v]["rk4_steps_per_s"] = 20 / (rk_ms * 1e-3)
+    for d in devs.values():
+        d.close()
+    return out
 
 
 def run_ours(args):
@@ -381,6 +548,15 @@ def run_ours(args):
         e2e = {"value": ws * SWEEPS_PER_STEP * nch * args.steps / e2e_s, "unit": "channels/s",
                "h2d_bytes_per_step": 8 * ns + 24 * ns, "d2h_bytes_per_step": 8 * ns + 24 * ns}
 
+    variants = None
+    if not args.no_variants and ws == 1:
+        variants = compare_variants(pb, ch, dev, fh, coll_ms, args.mixed_steps, stream)
+
+    batched = None
+    if not args.no_batched and ws == 1:
+        dev.close()
+        batched = batched_report(pb, args.batched_instances, args.batched_steps, stream)
+
     base = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         base, _ = cpu_baseline(m, sample_every=1 if args.workload != "window40" else 4)
@@ -404,7 +580,7 @@ def run_ours(args):
                          "peak_source": peak_src},
             "cpu_baseline": base, "e2e": e2e, "gpu_launches": LAUNCHES_PER_STEP * args.steps,
             "clocks": clk, "setup": {"build_channels_s": build_s, "device_create_s": create_s},
-            "transport_solve": solve,
+            "transport_solve": solve, "variants": variants, "batched": batched,
         })
     if ws > 1:
         import torch.distributed as tdist

@@ -141,10 +141,12 @@ void pb_channels_free(pb_channels *ch);
 enum { PB_VARIANT_FF = 0, PB_VARIANT_F64 = 1, PB_VARIANT_LITERAL = 2, PB_VARIANT_G32 = 3, PB_VARIANT_G16 = 4 };
 
 typedef struct pb_dev_opts {
-  int32_t variant;         /* PB_VARIANT_* */
-  int32_t item_channels;   /* channels per work item (multiple of 64; 0 = 2048) */
-  int32_t ctas_per_sm;     /* resident CTAs per SM for the streaming kernels (0 = 4) */
-  int32_t transport;       /* nonzero: reserve transport buffers (weights and F) */
+  int32_t variant;           /* PB_VARIANT_* */
+  int32_t item_channels;     /* channels per work item (multiple of 64; 0 = automatic, 256..4096) */
+  int32_t ctas_per_sm;       /* resident CTAs per SM for the coefficient sweeps (0 = 3) */
+  int32_t transport;         /* nonzero: reserve transport buffers (weights and F) */
+  int32_t transport_gather;  /* transport F gather: 0 automatic (= 2), 1 shared memory, 2 through L1 */
+  int32_t transport_ctas;    /* resident 512-thread transport CTAs per SM (0 = 3 with L1 gathers) */
 } pb_dev_opts;
 
 typedef struct pb_dev pb_dev; /* opaque host handle describing device-resident data */
@@ -216,6 +218,70 @@ int pb_transport_iterate(pb_dev *dev, const double *vel3, const double *F3in, do
  * with W, tau at f0 (pb_transport_setup followed by pb_transport_iterate). */
 int pb_transport_map(pb_dev *dev, const double *f0, const double *vel3, const double *F3in, double *F3out,
                      void *stream);
+
+/* ---------------------------------------------------------------- adjoint (reverse mode) */
+
+/* Vector-Jacobian product of the collision integral (Eq. 2) at f:
+ *   grad_f[x] = sum_s lam[s] dI_s/df_x                       (device double[nstate], overwritten)
+ *   grad_g2[c] += lam[s_c] dI_{s_c}/dg2_c for every stored channel c in the CSR order of
+ *                 pb_channels_export (device double[nchannels], accumulated; may be NULL).
+ * Each stored channel's |g|^2 is its own variable here; the derivative with respect to the
+ * shared |g|^2 of a channel and its reverse is the sum of the two entries.  The transposed
+ * sum is evaluated as a gather over each state's own row (the list is closed under
+ * s <-> p), so no atomic updates are needed.  Needs the PB_VARIANT_FF device. */
+int pb_collision_vjp(pb_dev *dev, const double *f, const double *lam, double *grad_f, double *grad_g2,
+                     void *stream);
+
+/* Discrete adjoint of one classic RK4 step from f (device double[nstate]): on entry lam holds
+ * dL/df_{n+1}, on return dL/df_n; grad_g2 (or NULL) accumulates dL/dg2 as above.  The four
+ * stage inputs are recomputed from f. */
+int pb_rtbte_rk4_vjp(pb_dev *dev, const double *f, double *lam, double dt, double *grad_g2, void *stream);
+
+/* Replace the device |g|^2 (device double[nchannels], CSR order of pb_channels_export) and
+ * recompute the per-channel coefficients.  Transport weights are not refreshed: call
+ * pb_transport_setup again before iterating. */
+int pb_dev_set_g2(pb_dev *dev, const double *g2, void *stream);
+
+/* ---------------------------------------------------------------- batched rt-BTE */
+
+/* Many independent systems (different grids, bands, modes, temperatures) advanced together:
+ * one persistent launch per RK4 stage sweeps every instance's channels in the literal
+ * per-channel form of Eq. 2 with |g|^2 stored in FP32 (rounded on the host), FP32
+ * per-channel arithmetic with Kahan lane sums and FP64 states; a CUDA graph replays the
+ * eight launches of a step.  Device vectors are the instances' state vectors concatenated
+ * in instance order (offsets from pb_batch_get_info). */
+typedef struct pb_batch pb_batch;
+
+typedef struct pb_batch_opts {
+  int32_t item_channels;  /* channels per work item (0 = 2048; else a multiple of 64, >= 1024) */
+  int32_t ctas_per_sm;    /* resident 512-thread CTAs per SM (0 = 2) */
+  int32_t reserved[2];
+} pb_batch_opts;
+
+int pb_batch_arena_bytes(const pb_channels *const *chs, int32_t n, const pb_batch_opts *opts, size_t *bytes);
+
+/* Upload n channel lists into `arena` (caller-owned device memory, 256-byte aligned, of at
+ * least pb_batch_arena_bytes).  Synchronises `stream`.  The channel lists may be freed after. */
+int pb_batch_create(const pb_channels *const *chs, int32_t n, const pb_batch_opts *opts, void *arena,
+                    size_t arena_bytes, void *stream, pb_batch **out);
+
+void pb_batch_destroy(pb_batch *batch);
+
+/* Total states and channels, state_offsets[n+1] (may be NULL), current launch shape. */
+int pb_batch_get_info(const pb_batch *batch, int64_t *nstate, int64_t *nchannels, int64_t *state_offsets,
+                      int32_t *item_channels, int32_t *ctas_per_sm);
+
+/* dfdt = I[f] for every state of every instance (device double[nstate total]). */
+int pb_batch_collision(pb_batch *batch, const double *f, double *dfdt, void *stream);
+
+/* nsteps classic RK4 steps of every instance, in place on f (device double[nstate total]). */
+int pb_batch_rk4_step(pb_batch *batch, double *f, double dt, int32_t nsteps, void *stream);
+
+/* Time candidate launch shapes (work-item sizes 1024/2048/4096 channels x 2/3/4 CTAs per SM)
+ * on collision sweeps at f and keep the fastest; reports it (any pointer may be NULL).
+ * Synchronises `stream`. */
+int pb_batch_autotune(pb_batch *batch, const double *f, void *stream, int32_t *best_item_channels,
+                      int32_t *best_ctas_per_sm, double *best_ms);
 
 /* Observables of a distribution: out[0] = sum_s f_s (carriers), out[1] = sum_s eps_s f_s (eV),
  * out[2] = sum_s I_s[f] (conservation check, 1/fs).  out: device double[3]. */

@@ -86,6 +86,12 @@ def lib(plant: int = 0) -> ctypes.CDLL:
         L.oracle_count_channels.restype = ctypes.c_int64
         L.oracle_count_channels.argtypes = [P]
         L.oracle_max_threads.restype = ctypes.c_int
+        L.oracle_collision_vjp.restype = ctypes.c_int
+        L.oracle_collision_vjp.argtypes = [P, vp, vp, vp]
+        L.oracle_g2_grad.restype = ctypes.c_int
+        L.oracle_g2_grad.argtypes = [P, vp, vp, ctypes.c_int64, vp, vp, vp, vp]
+        L.oracle_rk4_vjp.restype = ctypes.c_int
+        L.oracle_rk4_vjp.argtypes = [P, vp, ctypes.c_double, ctypes.c_int32, vp]
         _libs[plant] = L
     return _libs[plant]
 
@@ -194,6 +200,40 @@ class Oracle:
         if rc < 0:
             raise MemoryError("oracle_transport failed")
         return F, int(it.value), float(res.value), rc == 0
+
+
+    # ---------------------------------------------------------------- adjoint
+
+    def collision_vjp(self, f, lam):
+        """(J^T lam)_x = sum_s lam_s dI_s/df_x."""
+        f, lam = _f64(f), _f64(lam)
+        out = np.empty(self.nstate)
+        if self._L.oracle_collision_vjp(ctypes.byref(self._m), f.ctypes.data, lam.ctypes.data, out.ctypes.data):
+            raise MemoryError("oracle_collision_vjp failed")
+        return out
+
+    def g2_grad(self, f, lam, s, p, nu):
+        """dL/dg2 of the ordered channels (s[i] -> p[i], nu[i]) for L = sum_s lam_s I_s."""
+        f, lam = _f64(f), _f64(lam)
+        s = np.ascontiguousarray(s, np.int32)
+        p = np.ascontiguousarray(p, np.int32)
+        nu = np.ascontiguousarray(nu, np.int32)
+        out = np.empty(len(s))
+        rc = self._L.oracle_g2_grad(ctypes.byref(self._m), f.ctypes.data, lam.ctypes.data, len(s), s.ctypes.data,
+                                    p.ctypes.data, nu.ctypes.data, out.ctypes.data)
+        if rc == -1:
+            raise MemoryError("oracle_g2_grad failed")
+        if rc == -2:
+            raise ValueError("a listed channel does not exist (phonon energy <= 0)")
+        return out
+
+    def rk4_vjp(self, f0, dt, nsteps, lam):
+        """dL/df0 for L depending on f(T) after nsteps RK4 steps, given lam = dL/df(T)."""
+        f0 = _f64(f0)
+        lam = _f64(lam).copy()
+        if self._L.oracle_rk4_vjp(ctypes.byref(self._m), f0.ctypes.data, float(dt), int(nsteps), lam.ctypes.data):
+            raise MemoryError("oracle_rk4_vjp failed")
+        return lam
 
 
 def max_threads() -> int:

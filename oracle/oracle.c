@@ -375,3 +375,140 @@ int oracle_max_threads(void) {
   return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------ adjoint (reverse mode)
+ *
+ * Vector-Jacobian products of the collision integral, by the definition: I_s = -c sum_c t_c
+ * with t_c = g2 [G(x+w) F_abs + G(x-w) F_em], so for each channel (s -> p)
+ *   dI_s/df_s += -c g2 [G(x+w)((1-f_p)N + f_p(N+1)) + G(x-w)((1-f_p)(N+1) + f_p N)]
+ *   dI_s/df_p += -c g2 [G(x+w)(-f_s N - (1-f_s)(N+1)) + G(x-w)(-f_s(N+1) - (1-f_s)N)]
+ * (derivatives of the F_abs, F_em readings stated at the top of this file).
+ */
+
+/* out[x] = sum_s lam[s] dI_s/df_x for every window state x (serial scatter: plain). */
+int oracle_collision_vjp(const or_model *m, const double *f, const double *lam, double *out) {
+  int32_t *widx = window_index(m);
+  if (!widx) return -1;
+  const int64_t ns = oracle_window(m, NULL);
+  int32_t *ids = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ns > 0 ? ns : 1));
+  if (!ids) { free(widx); return -1; }
+  oracle_window(m, ids);
+  const int32_t nb = m->nbands, nm = m->nmodes;
+  const int32_t N1 = m->nk[0], N2 = m->nk[1], N3 = m->nk[2];
+  const int64_t Nq = nk_total(m);
+  const double c = 2.0 * OR_PI / (OR_HBAR * (double)Nq);
+  for (int64_t i = 0; i < ns; ++i) out[i] = 0.0;
+  for (int64_t r = 0; r < ns; ++r) {
+    const int64_t sid = ids[r];
+    const int64_t ik = sid / nb;
+    const int32_t j1 = (int32_t)(ik / ((int64_t)N2 * N3)), j2 = (int32_t)((ik / N3) % N2), j3 = (int32_t)(ik % N3);
+    const double eps_s = m->eps[sid], f_s = f[r];
+    for (int64_t iq = 0; iq < Nq; ++iq) {
+      const int32_t q1 = (int32_t)(iq / ((int64_t)N2 * N3)), q2 = (int32_t)((iq / N3) % N2), q3 = (int32_t)(iq % N3);
+      const int64_t ikq = ((int64_t)((j1 + q1) % N1) * N2 + (j2 + q2) % N2) * N3 + (j3 + q3) % N3;
+      for (int32_t mb = 0; mb < nb; ++mb) {
+        const int64_t pid = ikq * nb + mb;
+        const int32_t rp = widx[pid];
+        if (rp < 0) continue;
+        const double f_p = f[rp];
+        const double x = eps_s - m->eps[pid];
+        for (int32_t nu = 0; nu < nm; ++nu) {
+          const double w = m->omega[iq * nm + nu];
+          if (!(w > 0.0)) continue;
+          const double N = bose(w, m->T);
+          const double g2 = m->g2((int32_t)sid, (int32_t)pid, nu, m->g2_user);
+          const double Ga = gauss(x + w, m->sigma), Ge = gauss(x - w, m->sigma);
+          const double dts = g2 * (Ga * ((1.0 - f_p) * N + f_p * (N + 1.0)) + Ge * ((1.0 - f_p) * (N + 1.0) + f_p * N));
+          const double dtp = g2 * (Ga * (-f_s * N - (1.0 - f_s) * (N + 1.0)) + Ge * (-f_s * (N + 1.0) - (1.0 - f_s) * N));
+          out[r] += lam[r] * (-c) * dts;
+          out[rp] += lam[r] * (-c) * dtp;
+        }
+      }
+    }
+  }
+  free(ids);
+  free(widx);
+  return 0;
+}
+
+/* Derivative of L = sum_s lam[s] I_s with respect to the |g|^2 of each listed ORDERED channel
+ * (window states s[i] -> p[i], branch nu[i]); only row s depends on it:
+ *   dL/dg2 = -c lam_s [G(x+w) F_abs + G(x-w) F_em].  Returns -2 if a channel does not exist. */
+int oracle_g2_grad(const or_model *m, const double *f, const double *lam, int64_t n, const int32_t *s,
+                   const int32_t *p, const int32_t *nu, double *out) {
+  const int64_t ns = oracle_window(m, NULL);
+  int32_t *ids = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ns > 0 ? ns : 1));
+  if (!ids) return -1;
+  oracle_window(m, ids);
+  const int32_t nb = m->nbands, nm = m->nmodes;
+  const int32_t N2 = m->nk[1], N3 = m->nk[2];
+  const int64_t Nq = nk_total(m);
+  const double c = 2.0 * OR_PI / (OR_HBAR * (double)Nq);
+  int rc = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t sid = ids[s[i]], pid = ids[p[i]];
+    const int64_t iks = sid / nb, ikp = pid / nb;
+    const int64_t s1 = iks / ((int64_t)N2 * N3), s2 = (iks / N3) % N2, s3 = iks % N3;
+    const int64_t p1 = ikp / ((int64_t)N2 * N3), p2 = (ikp / N3) % N2, p3 = ikp % N3;
+    const int64_t iq = (((p1 - s1 + m->nk[0]) % m->nk[0]) * N2 + (p2 - s2 + N2) % N2) * N3 + (p3 - s3 + N3) % N3;
+    const double w = m->omega[iq * nm + nu[i]];
+    if (!(w > 0.0)) { rc = -2; out[i] = 0.0; continue; }
+    const double N = bose(w, m->T);
+    const double g2 = m->g2((int32_t)sid, (int32_t)pid, nu[i], m->g2_user);
+    (void)g2;
+    const double x = m->eps[sid] - m->eps[pid];
+    const double Ga = gauss(x + w, m->sigma), Ge = gauss(x - w, m->sigma);
+    const double f_s = f[s[i]], f_p = f[p[i]];
+    const double Fabs = f_s * (1.0 - f_p) * N - (1.0 - f_s) * f_p * (N + 1.0);
+    const double Fem = f_s * (1.0 - f_p) * (N + 1.0) - (1.0 - f_s) * f_p * N;
+    out[i] = -c * lam[s[i]] * (Ga * Fabs + Ge * Fem);
+  }
+  free(ids);
+  return rc;
+}
+
+/* Discrete adjoint of nsteps classic RK4 steps from f0: given lam = dL/df(T) on entry,
+ * returns dL/df0 in lam.  Stores every stage input of the forward pass (plain, not
+ * checkpointed).  Stage weights follow the forward scheme of oracle_rk4. */
+int oracle_rk4_vjp(const or_model *m, const double *f0, double dt, int32_t nsteps, double *lam) {
+  const int64_t ns = oracle_window(m, NULL);
+  const size_t vb = sizeof(double) * (size_t)(ns > 0 ? ns : 1);
+  double *U = (double *)malloc(vb * 4 * (size_t)(nsteps > 0 ? nsteps : 1));
+  double *k = (double *)malloc(vb), *y = (double *)malloc(vb), *g = (double *)malloc(vb);
+  double *mu = (double *)malloc(vb), *acc = (double *)malloc(vb), *mprev = (double *)malloc(vb);
+  int rc = (!U || !k || !y || !g || !mu || !acc || !mprev) ? -1 : 0;
+  if (rc == 0) {
+    memcpy(y, f0, vb);
+    for (int32_t st = 0; st < nsteps && rc == 0; ++st) {
+      double *u1 = U + (size_t)(4 * st + 0) * ns, *u2 = U + (size_t)(4 * st + 1) * ns;
+      double *u3 = U + (size_t)(4 * st + 2) * ns, *u4 = U + (size_t)(4 * st + 3) * ns;
+      memcpy(u1, y, vb);
+      rc |= oracle_collision(m, u1, NULL, 0, k, NULL);
+      for (int64_t i = 0; i < ns; ++i) { u2[i] = u1[i] + 0.5 * dt * k[i]; acc[i] = k[i]; }
+      rc |= oracle_collision(m, u2, NULL, 0, k, NULL);
+      for (int64_t i = 0; i < ns; ++i) { u3[i] = u1[i] + 0.5 * dt * k[i]; acc[i] += 2.0 * k[i]; }
+      rc |= oracle_collision(m, u3, NULL, 0, k, NULL);
+      for (int64_t i = 0; i < ns; ++i) { u4[i] = u1[i] + dt * k[i]; acc[i] += 2.0 * k[i]; }
+      rc |= oracle_collision(m, u4, NULL, 0, k, NULL);
+      for (int64_t i = 0; i < ns; ++i) y[i] = u1[i] + dt / 6.0 * (acc[i] + k[i]);
+    }
+    /* y_{n+1} = y_n + dt/6 (k1 + 2k2 + 2k3 + k4), k_i = I(u_i), u2 = y + dt/2 k1,
+     * u3 = y + dt/2 k2, u4 = y + dt k3.  Reverse: with lam = dL/dy_{n+1},
+     * dL/dk4 = dt/6 lam, dL/dk3 = dt/3 lam + dt J4^T dL/dk4, dL/dk2 = dt/3 lam + dt/2 J3^T dL/dk3,
+     * dL/dk1 = dt/6 lam + dt/2 J2^T dL/dk2, dL/dy_n = lam + sum_i J_i^T dL/dk_i. */
+    for (int32_t st = nsteps - 1; st >= 0 && rc == 0; --st) {
+      const double wl[4] = {dt / 6.0, dt / 3.0, dt / 3.0, dt / 6.0};
+      const double wm[4] = {0.5 * dt, 0.5 * dt, dt, 0.0}; /* u_{i+1} = y + wm[i] k_i */
+      for (int64_t i = 0; i < ns; ++i) { acc[i] = lam[i]; mprev[i] = 0.0; }
+      for (int j = 3; j >= 0 && rc == 0; --j) {
+        const double *u = U + (size_t)(4 * st + j) * ns;
+        for (int64_t i = 0; i < ns; ++i) g[i] = wl[j] * lam[i] + wm[j] * mprev[i];
+        rc |= oracle_collision_vjp(m, u, g, mu);
+        for (int64_t i = 0; i < ns; ++i) { acc[i] += mu[i]; mprev[i] = mu[i]; }
+      }
+      memcpy(lam, acc, vb);
+    }
+  }
+  free(U); free(k); free(y); free(g); free(mu); free(acc); free(mprev);
+  return rc;
+}

@@ -16,7 +16,7 @@ import os
 
 import numpy as np
 
-__all__ = ["Channels", "Device", "PBError", "lib", "VARIANTS", "G2_BATCH_FN"]
+__all__ = ["Channels", "Device", "Batch", "PBError", "lib", "VARIANTS", "G2_BATCH_FN"]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "lib", "libpb.so")
@@ -53,7 +53,8 @@ class _ChInfo(ctypes.Structure):
 
 class _DevOpts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("item_channels", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("transport", ctypes.c_int32)]
+                ("transport", ctypes.c_int32), ("transport_gather", ctypes.c_int32),
+                ("transport_ctas", ctypes.c_int32)]
 
 
 class _DevInfo(ctypes.Structure):
@@ -115,6 +116,16 @@ def lib() -> ctypes.CDLL:
         "pb_transport_setup": [vp, vp, vp],
         "pb_transport_iterate": [vp, vp, vp, vp, vp, vp],
         "pb_observables": [vp, vp, vp, vp],
+        "pb_collision_vjp": [vp, vp, vp, vp, vp, vp],
+        "pb_batch_arena_bytes": [vp, i32, vp, ctypes.POINTER(ctypes.c_size_t)],
+        "pb_batch_create": [vp, i32, vp, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
+        "pb_batch_get_info": [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), vp, ctypes.POINTER(i32),
+                              ctypes.POINTER(i32)],
+        "pb_batch_collision": [vp, vp, vp, vp],
+        "pb_batch_rk4_step": [vp, vp, dbl, i32, vp],
+        "pb_batch_autotune": [vp, vp, vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(dbl)],
+        "pb_rtbte_rk4_vjp": [vp, vp, vp, dbl, vp, vp],
+        "pb_dev_set_g2": [vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -124,6 +135,8 @@ def lib() -> ctypes.CDLL:
     L.pb_channels_free.restype = None
     L.pb_dev_destroy.argtypes = [vp]
     L.pb_dev_destroy.restype = None
+    L.pb_batch_destroy.argtypes = [vp]
+    L.pb_batch_destroy.restype = None
     L.pb_last_error.restype = ctypes.c_char_p
     L.pb_version.restype = ctypes.c_char_p
     _lib = L
@@ -256,14 +269,15 @@ class Device:
     """Device-resident channel list and tables (pb_dev_create) in one torch arena."""
 
     def __init__(self, channels: Channels, variant: str = "ff", item_channels: int = 0, ctas_per_sm: int = 0,
-                 transport: bool = False, stream=None):
+                 transport: bool = False, transport_gather: int = 0, transport_ctas: int = 0, stream=None):
         import torch
 
         if not torch.cuda.is_available():
             raise PBError(PB_EDEVICE, "no CUDA device is visible")
         self.channels = channels
         self.variant = variant
-        o = _DevOpts(VARIANTS[variant], int(item_channels), int(ctas_per_sm), 1 if transport else 0)
+        o = _DevOpts(VARIANTS[variant], int(item_channels), int(ctas_per_sm), 1 if transport else 0,
+                     int(transport_gather), int(transport_ctas))
         nbytes = ctypes.c_size_t(0)
         _check(lib().pb_dev_arena_bytes(channels._h, ctypes.byref(o), ctypes.byref(nbytes)))
         self.arena = torch.empty(int(nbytes.value), dtype=torch.uint8, device="cuda")
@@ -359,6 +373,27 @@ class Device:
                                           rp, _stream_ptr(stream)))
         return out
 
+    # ------------------------------------------------------------ adjoint
+
+    def collision_vjp(self, f, lam, out=None, grad_g2=None, stream=None):
+        """grad_f = J(f)^T lam; grad_g2 (CUDA double[nchannels], CSR order) accumulates dL/dg2."""
+        out = self._new(self.nstate) if out is None else out
+        gp = None if grad_g2 is None else _dev_vec(grad_g2, self.nchannels, "grad_g2")
+        _check(lib().pb_collision_vjp(self._h, _dev_vec(f, self.nstate, "f"), _dev_vec(lam, self.nstate, "lam"),
+                                      _dev_vec(out, self.nstate, "out"), gp, _stream_ptr(stream)))
+        return out
+
+    def rk4_vjp(self, f, lam, dt, grad_g2=None, stream=None):
+        """In place: lam = dL/df_n from dL/df_{n+1} for the RK4 step from f."""
+        gp = None if grad_g2 is None else _dev_vec(grad_g2, self.nchannels, "grad_g2")
+        _check(lib().pb_rtbte_rk4_vjp(self._h, _dev_vec(f, self.nstate, "f"), _dev_vec(lam, self.nstate, "lam"),
+                                      float(dt), gp, _stream_ptr(stream)))
+        return lam
+
+    def set_g2(self, g2, stream=None):
+        """Replace |g|^2 (CUDA double[nchannels], CSR order) and recompute the coefficients."""
+        _check(lib().pb_dev_set_g2(self._h, _dev_vec(g2, self.nchannels, "g2"), _stream_ptr(stream)))
+
     def observables(self, f, out=None, stream=None):
         """(sum f, sum eps f, sum I[f]) as a CUDA tensor of 3 doubles."""
         out = self._new(3) if out is None else out
@@ -376,6 +411,75 @@ class Device:
             self.close()
         except Exception:  # noqa: BLE001
             pass
+
+
+class _BatchOpts(ctypes.Structure):
+    _fields_ = [("item_channels", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+
+
+class Batch:
+    """Many channel lists advanced together (pb_batch_*): FP32 |g|^2, one launch per stage."""
+
+    def __init__(self, channels, item_channels: int = 0, ctas_per_sm: int = 0, stream=None):
+        import torch
+
+        self.channels = list(channels)
+        arr = (ctypes.c_void_p * len(self.channels))(*[c._h.value for c in self.channels])
+        self._arr = arr
+        o = _BatchOpts(int(item_channels), int(ctas_per_sm))
+        nbytes = ctypes.c_size_t(0)
+        _check(lib().pb_batch_arena_bytes(arr, len(self.channels), ctypes.byref(o), ctypes.byref(nbytes)))
+        self.arena = torch.empty(int(nbytes.value), dtype=torch.uint8, device="cuda")
+        h = ctypes.c_void_p()
+        _check(lib().pb_batch_create(arr, len(self.channels), ctypes.byref(o), ctypes.c_void_p(self.arena.data_ptr()),
+                                     ctypes.c_size_t(int(nbytes.value)), _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+        self.refresh_info()
+
+    def refresh_info(self):
+        ns, nc = ctypes.c_int64(0), ctypes.c_int64(0)
+        ic, ct = ctypes.c_int32(0), ctypes.c_int32(0)
+        offs = np.empty(len(self.channels) + 1, np.int64)
+        _check(lib().pb_batch_get_info(self._h, ctypes.byref(ns), ctypes.byref(nc), offs.ctypes.data, ctypes.byref(ic),
+                                       ctypes.byref(ct)))
+        self.nstate, self.nchannels = int(ns.value), int(nc.value)
+        self.offsets = offs
+        self.item_channels, self.ctas_per_sm = int(ic.value), int(ct.value)
+
+    def collision(self, f, out=None, stream=None):
+        out = torch_empty(self.nstate) if out is None else out
+        _check(lib().pb_batch_collision(self._h, _dev_vec(f, self.nstate, "f"), _dev_vec(out, self.nstate, "out"),
+                                        _stream_ptr(stream)))
+        return out
+
+    def rk4(self, f, dt: float, nsteps: int = 1, stream=None):
+        _check(lib().pb_batch_rk4_step(self._h, _dev_vec(f, self.nstate, "f"), float(dt), int(nsteps),
+                                       _stream_ptr(stream)))
+        return f
+
+    def autotune(self, f, stream=None):
+        bi, bc, bm = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0.0)
+        _check(lib().pb_batch_autotune(self._h, _dev_vec(f, self.nstate, "f"), _stream_ptr(stream), ctypes.byref(bi),
+                                       ctypes.byref(bc), ctypes.byref(bm)))
+        self.refresh_info()
+        return int(bi.value), int(bc.value), float(bm.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pb_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+def torch_empty(n):
+    import torch
+
+    return torch.empty(n, dtype=torch.float64, device="cuda")
 
 
 # fail loudly at import time when the native library is missing

@@ -1,0 +1,59 @@
+"""Reverse-mode derivatives of rt-BTE trajectories through the C ABI.
+
+``trajectory(dev, f0, g2, dt, nsteps, every)`` returns f after nsteps classic RK4 steps of
+df/dt = I[f] (Eq. 2, Eq. 1 with no field) as a differentiable function of the initial
+occupations f0 and of the couplings |g|^2 (one entry per stored channel, in the CSR order
+of ``Channels.export``).  The forward pass keeps f every ``every`` steps; the backward pass
+recomputes each segment from its checkpoint and applies ``pb_rtbte_rk4_vjp`` step by step
+in reverse.  Every arithmetic step runs in libpb.so; this module only orders the calls.
+"""
+from __future__ import annotations
+
+import torch
+
+
+class _Trajectory(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, f0, g2, dev, dt, nsteps, every):
+        f = f0.detach().clone().contiguous()
+        ckpts = []
+        n = 0
+        while n < nsteps:
+            m = min(every, nsteps - n)
+            ckpts.append((n, m, f.clone()))
+            dev.rk4(f, dt, m)
+            n += m
+        ctx.dev, ctx.dt = dev, float(dt)
+        ctx.ckpts = ckpts
+        ctx.want_g2 = g2 is not None and g2.requires_grad
+        return f
+
+    @staticmethod
+    def backward(ctx, gout):
+        dev, dt = ctx.dev, ctx.dt
+        lam = gout.detach().clone().contiguous()
+        gg2 = torch.zeros(dev.nchannels, dtype=torch.float64, device=lam.device) if ctx.want_g2 else None
+        y = torch.empty_like(lam)
+        for n0, m, fck in reversed(ctx.ckpts):
+            states = [fck]
+            y.copy_(fck)
+            for _ in range(m - 1):
+                dev.rk4(y, dt, 1)
+                states.append(y.clone())
+            for k in reversed(range(m)):
+                dev.rk4_vjp(states[k], lam, dt, grad_g2=gg2)
+        return lam, gg2, None, None, None, None
+
+
+def trajectory(dev, f0, g2=None, dt=1.0, nsteps=1, every=20):
+    """Differentiable RK4 trajectory on ``dev`` (a Device of the FF variant).  ``g2`` is a
+    CUDA float64 tensor of the stored couplings (its values must be those on the device,
+    e.g. from ``g2_tensor``); pass it with requires_grad to get dL/dg2."""
+    if g2 is None:
+        g2 = torch.zeros(0, dtype=torch.float64, device=f0.device)
+    return _Trajectory.apply(f0, g2, dev, dt, int(nsteps), int(every))
+
+
+def g2_tensor(channels, device="cuda"):
+    """The stored couplings in CSR order as a CUDA float64 tensor."""
+    return torch.tensor(channels.export()["g2"], dtype=torch.float64, device=device)

@@ -1,0 +1,575 @@
+// Batched rt-BTE: many independent e-ph systems (different grids, bands, modes,
+// temperatures) advanced together.  Included at the end of device.cu (one translation unit).
+//
+// All instances' channel lists are concatenated (rows padded to 8 channels) with |g|^2 in
+// FP32, one padded FP32 phonon table per instance, one 16-byte record per state, and a single
+// work-item list whose items carry an instance id.  One persistent launch per RK4 stage
+// sweeps every instance: each CTA takes a contiguous range of items (mostly one instance, so
+// the partner records it gathers stay in L1), evaluates the literal per-channel form of
+// Eq. 2 in FP32 with Kahan lane sums, and one finaliser applies each state's prefactor and
+// the FP64 RK4 stage arithmetic.  A CUDA graph of the 8 launches replays each step.  The item
+// size and CTAs per SM come from a small autotuner that times candidate launch shapes.
+
+namespace pb {
+namespace dev {
+
+struct BInst {
+  const float4 *tab;  // this instance's padded phonon table
+  int cpad;           // L(N1,N2,N3) * nmodes of the instance
+  float k2;           // -log2(e) / (2 sigma^2)
+  int soff;           // first global state of the instance
+  int pad;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(512) k_stream_gbatch(const Item *__restrict__ items,
+                                                       const int *__restrict__ item_inst, int nitems,
+                                                       const BInst *__restrict__ inst,
+                                                       const uint32_t *__restrict__ col,
+                                                       const float *__restrict__ g2v,
+                                                       const uint4 *__restrict__ gstate, Part4 *__restrict__ part) {
+  const int per = (nitems + gridDim.x - 1) / gridDim.x;
+  const int begin = blockIdx.x * per;
+  const int end = min(nitems, begin + per);
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint4 *__restrict__ col4 = (const uint4 *)col;
+  for (int it = begin + wib; it < end; it += nw) {
+    const Item I = items[it];
+    const BInst B = inst[item_inst[it]];
+    GGeom g;
+    g.col = col;
+    g.tabp = B.tab;
+    g.cpad = B.cpad;
+    g.k2 = B.k2;
+    const uint4 ss = __ldg(gstate + I.row);
+    const int base = B.cpad - (int)ss.w;
+    const uint4 *__restrict__ gsi = gstate + B.soff;
+    const long long g0 = I.start >> 2;
+    const int ng = I.len >> 2;
+    float sum = 0.f, comp = 0.f;
+    uint4 c = make_uint4(0u, 0u, 0u, 0u);
+    float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lane < ng) {
+      c = __ldcs(col4 + g0 + lane);
+      gv = load_g2x4(g2v, g0 + lane);
+    }
+    for (int q = lane; q < ng; q += 32) {
+      uint4 cn = make_uint4(0u, 0u, 0u, 0u);
+      float4 gn = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (q + 32 < ng) {
+        cn = __ldcs(col4 + g0 + q + 32);
+        gn = load_g2x4(g2v, g0 + q + 32);
+      }
+      const float t0 = g_term<MODE>(g, ss, __ldg(gsi + (c.x & 0xFFFFFFu)), c.x, base, gv.x);
+      const float t1 = g_term<MODE>(g, ss, __ldg(gsi + (c.y & 0xFFFFFFu)), c.y, base, gv.y);
+      const float t2 = g_term<MODE>(g, ss, __ldg(gsi + (c.z & 0xFFFFFFu)), c.z, base, gv.z);
+      const float t3 = g_term<MODE>(g, ss, __ldg(gsi + (c.w & 0xFFFFFFu)), c.w, base, gv.w);
+      kahan_add(sum, comp, t0);
+      kahan_add(sum, comp, t1);
+      kahan_add(sum, comp, t2);
+      kahan_add(sum, comp, t3);
+      c = cn;
+      gv = gn;
+    }
+    const double v = warp_sum((double)sum - (double)comp);
+    if (lane == 0) part[it] = make_part4(v, 0.0, 0.0, 0.0);
+  }
+}
+
+// I_r = -cs[r] * (row sum); cs = (2 pi / hbar N_q) / (sqrt(2 pi) sigma) of the row's instance.
+// STAGE < 0 writes I; STAGE 0..3 does the RK4 stage arithmetic as k_fin_coll does.
+template <int STAGE>
+__global__ void k_fin_gbatch(const int *__restrict__ item_ptr, const Part4 *__restrict__ part, int ns,
+                             const double *__restrict__ cs, const double *__restrict__ ysrc, double *__restrict__ out,
+                             double *__restrict__ f, double *__restrict__ acc, double *__restrict__ y,
+                             uint4 *__restrict__ gstate, double dt) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= ns) return;
+  double S = 0.0;
+  for (int i = item_ptr[r]; i < item_ptr[r + 1]; ++i) S += part[i].x;
+  const double I = -cs[r] * S;
+  (void)ysrc;
+  if (STAGE < 0) {
+    out[r] = I;
+    return;
+  }
+  const double fr = f[r];
+  double yn;
+  if (STAGE == 0) {
+    acc[r] = I;
+    yn = fr + 0.5 * dt * I;
+  } else if (STAGE == 1) {
+    acc[r] += 2.0 * I;
+    yn = fr + 0.5 * dt * I;
+  } else if (STAGE == 2) {
+    acc[r] += 2.0 * I;
+    yn = fr + dt * I;
+  } else {
+    yn = fr + dt / 6.0 * (acc[r] + I);
+    f[r] = yn;
+  }
+  y[r] = yn;
+  ((float *)gstate)[4 * r + 2] = __double2float_rn(yn);
+}
+
+}  // namespace dev
+}  // namespace pb
+
+struct pb_batch {
+  int n = 0;
+  int64_t ns = 0, nchp = 0, nitems = 0, nitems_cap = 0;
+  int sm_count = 0, item_ch = 2048, ctas = 2;
+  std::vector<int64_t> soff;       // [n+1] state offsets
+  std::vector<int64_t> lenp;       // padded length of every global row
+  std::vector<int32_t> row_inst;   // instance of every global row
+  std::vector<int64_t> nch;        // [n] stored channels per instance
+  char *arena = nullptr;
+  size_t bytes = 0;
+  Item *items = nullptr;
+  int32_t *item_inst = nullptr, *item_ptr = nullptr;
+  uint32_t *col = nullptr;
+  float *g2 = nullptr;
+  uint4 *gstate = nullptr;
+  float4 *tabs = nullptr;
+  pb::dev::BInst *inst = nullptr;
+  double *cs = nullptr;
+  Part4 *part = nullptr;
+  double *acc = nullptr, *y = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double *rk_f = nullptr;
+  double rk_dt = 0.0;
+};
+
+namespace {
+
+struct BatchPlan {
+  std::vector<Item> items;
+  std::vector<int32_t> item_inst, item_ptr;
+};
+
+void batch_plan(const pb_batch *b, int item_ch, BatchPlan &P) {
+  P.items.clear();
+  P.item_inst.clear();
+  P.item_ptr.assign(b->ns + 1, 0);
+  int64_t off = 0;
+  for (int64_t r = 0; r < b->ns; ++r) {
+    P.item_ptr[r] = (int32_t)P.items.size();
+    const int64_t lenp = b->lenp[r];
+    if (lenp > 0) {
+      const int64_t chunks = lenp / kRowPad;
+      const int64_t np = std::max<int64_t>(1, (lenp + item_ch - 1) / item_ch);
+      int64_t o = 0;
+      for (int64_t k = 0; k < np; ++k) {
+        const int64_t c = chunks / np + (k < chunks % np ? 1 : 0);
+        if (c > 0) {
+          Item it;
+          it.start = off + o;
+          it.len = (int)(c * kRowPad);
+          it.row = (int)r;
+          P.items.push_back(it);
+          P.item_inst.push_back(b->row_inst[r]);
+        }
+        o += c * kRowPad;
+      }
+    }
+    off += lenp;
+  }
+  P.item_ptr[b->ns] = (int32_t)P.items.size();
+}
+
+int64_t batch_items_count(const std::vector<int64_t> &lenp, int item_ch) {
+  int64_t n = 0;
+  for (int64_t l : lenp)
+    if (l > 0) n += std::max<int64_t>(1, (l + item_ch - 1) / item_ch);
+  return n;
+}
+
+constexpr int kBatchMinItem = 1024;  // smallest item size the arena is planned for
+
+struct BatchLayout {
+  size_t items, item_inst, item_ptr, col, g2, gstate, tabs, inst, cs, part, acc, y, omega_tmp, tab_tmp, eps_tmp,
+      kc_tmp, total;
+};
+
+BatchLayout batch_layout(const pb_channels *const *chs, int n, int64_t ns, int64_t nchp, int64_t nitems_cap) {
+  BatchLayout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + std::max<size_t>(bytes, 1));
+    return at;
+  };
+  size_t tab = 0, maxq = 0, maxs = 0;
+  for (int i = 0; i < n; ++i) {
+    size_t r = 1;
+    for (int a = 0; a < 3; ++a) r *= (size_t)(chs[i]->nk[a] > 1 ? 2 * chs[i]->nk[a] : 1);
+    tab += align_up(sizeof(float4) * r * chs[i]->nmodes);
+    maxq = std::max(maxq, (size_t)chs[i]->nq * chs[i]->nmodes);
+    maxs = std::max(maxs, (size_t)chs[i]->nstate);
+  }
+  L.items = take(sizeof(Item) * nitems_cap);
+  L.item_inst = take(sizeof(int32_t) * nitems_cap);
+  L.item_ptr = take(sizeof(int32_t) * (ns + 1));
+  L.col = take(sizeof(uint32_t) * nchp);
+  L.g2 = take(sizeof(float) * nchp);
+  L.gstate = take(sizeof(uint4) * ns);
+  L.tabs = take(tab);
+  L.inst = take(sizeof(pb::dev::BInst) * n);
+  L.cs = take(sizeof(double) * ns);
+  L.part = take(sizeof(Part4) * nitems_cap);
+  L.acc = take(sizeof(double) * ns);
+  L.y = take(sizeof(double) * ns);
+  L.omega_tmp = take(sizeof(double) * maxq);
+  L.tab_tmp = take(sizeof(double2) * maxq);
+  L.eps_tmp = take(sizeof(double) * maxs);
+  L.kc_tmp = take(sizeof(short4) * maxs);
+  L.total = o;
+  return L;
+}
+
+int batch_check(const pb_channels *const *chs, int32_t n, int64_t *ns, int64_t *nchp) {
+  if (!chs || n <= 0) return set_error(PB_EINVAL, "pb_batch: need at least one channel list");
+  int64_t s = 0, c = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!chs[i]) return set_error(PB_EINVAL, "pb_batch: channel list %d is null", i);
+    s += chs[i]->nstate;
+    for (int64_t r = 0; r < chs[i]->nstate; ++r)
+      c += (chs[i]->row_ptr[r + 1] - chs[i]->row_ptr[r] + kRowPad - 1) / kRowPad * kRowPad;
+  }
+  if (s >= INT32_MAX / 4) return set_error(PB_EINVAL, "pb_batch: too many states");
+  *ns = s;
+  *nchp = c;
+  return PB_OK;
+}
+
+std::vector<int64_t> batch_lenp(const pb_channels *const *chs, int32_t n) {
+  std::vector<int64_t> lenp;
+  for (int i = 0; i < n; ++i)
+    for (int64_t r = 0; r < chs[i]->nstate; ++r)
+      lenp.push_back((chs[i]->row_ptr[r + 1] - chs[i]->row_ptr[r] + kRowPad - 1) / kRowPad * kRowPad);
+  return lenp;
+}
+
+int batch_upload_plan(pb_batch *b, int item_ch, cudaStream_t st) {
+  BatchPlan P;
+  batch_plan(b, item_ch, P);
+  if ((int64_t)P.items.size() > b->nitems_cap)
+    return set_error(PB_EINVAL, "pb_batch: item size %d needs more items than the arena holds", item_ch);
+  PB_CUDA(cudaMemcpyAsync(b->items, P.items.data(), sizeof(Item) * P.items.size(), cudaMemcpyHostToDevice, st));
+  PB_CUDA(cudaMemcpyAsync(b->item_inst, P.item_inst.data(), sizeof(int32_t) * P.item_inst.size(), cudaMemcpyHostToDevice, st));
+  PB_CUDA(cudaMemcpyAsync(b->item_ptr, P.item_ptr.data(), sizeof(int32_t) * P.item_ptr.size(), cudaMemcpyHostToDevice, st));
+  PB_CUDA(cudaStreamSynchronize(st));  // the plan vectors are released on return
+  b->nitems = (int64_t)P.items.size();
+  b->item_ch = item_ch;
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  return PB_OK;
+}
+
+int batch_sweep(pb_batch *b, cudaStream_t st) {
+  const int64_t need = (b->nitems * 32 + 511) / 512;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)b->sm_count * b->ctas));
+  pb::dev::k_stream_gbatch<dev::MODE_COLL><<<grid, 512, 0, st>>>(b->items, b->item_inst, (int)b->nitems, b->inst,
+                                                                 b->col, b->g2, b->gstate, b->part);
+  PB_LAUNCHED("k_stream_gbatch");
+  return PB_OK;
+}
+
+template <int STAGE>
+int batch_fin(pb_batch *b, double *out, double *f, double dt, cudaStream_t st) {
+  pb::dev::k_fin_gbatch<STAGE><<<(int)((b->ns + 255) / 256), 256, 0, st>>>(b->item_ptr, b->part, (int)b->ns, b->cs,
+                                                                            nullptr, out, f, b->acc, b->y, b->gstate, dt);
+  PB_LAUNCHED("k_fin_gbatch");
+  return PB_OK;
+}
+
+int batch_stage_input(pb_batch *b, const double *f, cudaStream_t st) {
+  dev::k_gstate_f<<<(int)((b->ns + 255) / 256), 256, 0, st>>>(f, (int)b->ns, b->gstate);
+  PB_LAUNCHED("k_gstate_f");
+  return PB_OK;
+}
+
+int batch_rk4_launches(pb_batch *b, double *f, double dt, cudaStream_t st) {
+  int rc;
+  if ((rc = batch_sweep(b, st)) || (rc = batch_fin<0>(b, nullptr, f, dt, st))) return rc;
+  if ((rc = batch_sweep(b, st)) || (rc = batch_fin<1>(b, nullptr, f, dt, st))) return rc;
+  if ((rc = batch_sweep(b, st)) || (rc = batch_fin<2>(b, nullptr, f, dt, st))) return rc;
+  if ((rc = batch_sweep(b, st)) || (rc = batch_fin<3>(b, nullptr, f, dt, st))) return rc;
+  return PB_OK;
+}
+
+}  // namespace
+
+extern "C" int pb_batch_arena_bytes(const pb_channels *const *chs, int32_t n, const pb_batch_opts *opts,
+                                    size_t *bytes) {
+  clear_error();
+  (void)opts;
+  if (!bytes) return set_error(PB_EINVAL, "pb_batch_arena_bytes: null argument");
+  int64_t ns = 0, nchp = 0;
+  int rc = batch_check(chs, n, &ns, &nchp);
+  if (rc) return rc;
+  const int64_t cap = batch_items_count(batch_lenp(chs, n), kBatchMinItem);
+  *bytes = batch_layout(chs, n, ns, nchp, cap).total;
+  return PB_OK;
+}
+
+extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const pb_batch_opts *opts, void *arena,
+                               size_t bytes, void *stream, pb_batch **out) {
+  clear_error();
+  if (!arena || !out) return set_error(PB_EINVAL, "pb_batch_create: null argument");
+  *out = nullptr;
+  if (((uintptr_t)arena) % kAlign) return set_error(PB_EINVAL, "pb_batch_create: arena must be 256-byte aligned");
+  int sm = 0;
+  int rc = check_device(&sm);
+  if (rc) return rc;
+  int64_t ns = 0, nchp = 0;
+  if ((rc = batch_check(chs, n, &ns, &nchp))) return rc;
+  pb_batch_opts o{};
+  if (opts) o = *opts;
+  if (o.item_channels < 0 || (o.item_channels && (o.item_channels % 64 || o.item_channels < kBatchMinItem)))
+    return set_error(PB_EINVAL, "pb_batch_create: item_channels must be 0 or a multiple of 64 >= %d", kBatchMinItem);
+  if (o.ctas_per_sm < 0 || o.ctas_per_sm > 4) return set_error(PB_EINVAL, "pb_batch_create: ctas_per_sm must be 0..4");
+  cudaStream_t st = (cudaStream_t)stream;
+  pb_batch *b = new (std::nothrow) pb_batch();
+  if (!b) return set_error(PB_ENOMEM, "pb_batch_create: out of host memory");
+  int status = PB_OK;
+  try {
+    b->n = n;
+    b->ns = ns;
+    b->nchp = nchp;
+    b->sm_count = sm;
+    b->lenp = batch_lenp(chs, n);
+    b->nitems_cap = batch_items_count(b->lenp, kBatchMinItem);
+    b->soff.assign(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+      b->soff[i + 1] = b->soff[i] + chs[i]->nstate;
+      b->nch.push_back(chs[i]->nch);
+      for (int64_t r = 0; r < chs[i]->nstate; ++r) b->row_inst.push_back(i);
+    }
+    const BatchLayout L = batch_layout(chs, n, ns, nchp, b->nitems_cap);
+    if (bytes < L.total) {
+      delete b;
+      return set_error(PB_ENOMEM, "pb_batch_create: arena of %zu bytes is smaller than the %zu needed", bytes, L.total);
+    }
+    char *A = (char *)arena;
+    b->arena = A;
+    b->bytes = bytes;
+    b->items = (Item *)(A + L.items);
+    b->item_inst = (int32_t *)(A + L.item_inst);
+    b->item_ptr = (int32_t *)(A + L.item_ptr);
+    b->col = (uint32_t *)(A + L.col);
+    b->g2 = (float *)(A + L.g2);
+    b->gstate = (uint4 *)(A + L.gstate);
+    b->tabs = (float4 *)(A + L.tabs);
+    b->inst = (pb::dev::BInst *)(A + L.inst);
+    b->cs = (double *)(A + L.cs);
+    b->part = (Part4 *)(A + L.part);
+    b->acc = (double *)(A + L.acc);
+    b->y = (double *)(A + L.y);
+    double *om = (double *)(A + L.omega_tmp);
+    double2 *tt = (double2 *)(A + L.tab_tmp);
+    double *ep = (double *)(A + L.eps_tmp);
+    short4 *kc = (short4 *)(A + L.kc_tmp);
+
+    // per-instance tables, records and prefactors; channel words and FP32 |g|^2
+    std::vector<pb::dev::BInst> hin(n);
+    std::vector<double> hcs((size_t)ns);
+    std::vector<uint32_t> hcol((size_t)nchp);
+    std::vector<float> hg2((size_t)nchp, 0.f);
+    size_t tab_off = 0;  // in float4
+    int64_t coff = 0;
+    for (int i = 0; i < n && status == PB_OK; ++i) {
+      const pb_channels *ch = chs[i];
+      int rad[3];
+      size_t r = 1;
+      for (int a = 0; a < 3; ++a) {
+        rad[a] = ch->nk[a] > 1 ? 2 * ch->nk[a] : 1;
+        r *= (size_t)rad[a];
+      }
+      const int64_t nt = (int64_t)r * ch->nmodes;
+      if ((double)nt >= 2147483647.0) status = set_error(PB_EINVAL, "pb_batch_create: instance %d table too large", i);
+      if (ch->nk[0] > 32767 || ch->nk[1] > 32767 || ch->nk[2] > 32767)
+        status = set_error(PB_EINVAL, "pb_batch_create: instance %d grid dimension above 32767", i);
+      if (status) break;
+      const double c = 2.0 * kPi / (kHbar * (double)ch->nq);
+      const double norm = 1.0 / (std::sqrt(2.0 * kPi) * ch->sigma);
+      const int n1 = rad[0] > 1 ? ch->nk[0] : 0, n2 = rad[1] > 1 ? ch->nk[1] : 0, n3 = rad[2] > 1 ? ch->nk[2] : 0;
+      hin[i].tab = b->tabs + tab_off;
+      hin[i].cpad = ((n1 * rad[1] + n2) * rad[2] + n3) * ch->nmodes;
+      hin[i].k2 = (float)(-1.4426950408889634 / (2.0 * ch->sigma * ch->sigma));
+      hin[i].soff = (int)b->soff[i];
+      hin[i].pad = 0;
+      for (int64_t s = 0; s < ch->nstate; ++s) hcs[b->soff[i] + s] = c * norm;
+      for (int64_t s = 0; s < ch->nstate; ++s) {
+        const int64_t a = ch->row_ptr[s], len = ch->row_ptr[s + 1] - a, lp = b->lenp[b->soff[i] + s];
+        for (int64_t k = 0; k < len; ++k) {
+          hcol[coff + k] = (uint32_t)ch->col[a + k] | ((uint32_t)ch->nu[a + k] << kPartnerBits);
+          hg2[coff + k] = (float)ch->g2[a + k];
+        }
+        for (int64_t k = len; k < lp; ++k) hcol[coff + k] = (uint32_t)s;
+        coff += lp;
+      }
+      // device: (w, N) table, padded FP32 table, state records
+      std::vector<short4> hkc((size_t)ch->nstate);
+      const int N2 = ch->nk[1], N3 = ch->nk[2];
+      for (int64_t s = 0; s < ch->nstate; ++s) {
+        const int ik = ch->kidx[s];
+        hkc[s] = make_short4((short)(ik / (N2 * N3)), (short)((ik / N3) % N2), (short)(ik % N3), 0);
+      }
+      const size_t nq = (size_t)ch->nq * ch->nmodes;
+      cudaError_t e = cudaMemcpyAsync(om, ch->omega.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(ep, ch->eps.data(), sizeof(double) * ch->nstate, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(kc, hkc.data(), sizeof(short4) * ch->nstate, cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) {
+        status = cuda_fail(e, "pb_batch_create: upload");
+        break;
+      }
+      dev::k_table<<<(int)std::min<size_t>((nq + 255) / 256, 4096), 256, 0, st>>>(om, (long long)nq, kBoltz * ch->T, tt);
+      dev::k_tab_padded<<<(int)std::min<int64_t>((nt + 255) / 256, 8192), 256, 0, st>>>(
+          tt, ch->nk[0], ch->nk[1], ch->nk[2], rad[0], rad[1], rad[2], ch->nmodes, b->tabs + tab_off);
+      dev::k_gstate_init<<<(int)((ch->nstate + 255) / 256), 256, 0, st>>>(ep, kc, (int)ch->nstate, rad[1], rad[2],
+                                                                         ch->nmodes, b->gstate + b->soff[i]);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // temporaries are reused by the next instance
+      if (e != cudaSuccess) {
+        status = cuda_fail(e, "pb_batch_create: instance setup");
+        break;
+      }
+      tab_off += align_up(sizeof(float4) * (size_t)nt) / sizeof(float4);
+    }
+    if (status == PB_OK) {
+      cudaError_t e = cudaMemcpyAsync(b->inst, hin.data(), sizeof(pb::dev::BInst) * n, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(b->cs, hcs.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(b->col, hcol.data(), sizeof(uint32_t) * nchp, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(b->g2, hg2.data(), sizeof(float) * nchp, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) status = cuda_fail(e, "pb_batch_create: upload");
+    }
+    if (status == PB_OK) {
+      b->ctas = o.ctas_per_sm ? o.ctas_per_sm : 2;
+      status = batch_upload_plan(b, o.item_channels ? o.item_channels : 2048, st);
+    }
+  } catch (const std::bad_alloc &) {
+    status = set_error(PB_ENOMEM, "pb_batch_create: out of host memory");
+  }
+  if (status != PB_OK) {
+    delete b;
+    return status;
+  }
+  *out = b;
+  return PB_OK;
+}
+
+extern "C" void pb_batch_destroy(pb_batch *b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+extern "C" int pb_batch_get_info(const pb_batch *b, int64_t *nstate, int64_t *nchannels, int64_t *state_offsets,
+                                 int32_t *item_channels, int32_t *ctas_per_sm) {
+  clear_error();
+  if (!b) return set_error(PB_EINVAL, "pb_batch_get_info: null handle");
+  if (nstate) *nstate = b->ns;
+  if (nchannels) {
+    int64_t s = 0;
+    for (int64_t c : b->nch) s += c;
+    *nchannels = s;
+  }
+  if (state_offsets) std::memcpy(state_offsets, b->soff.data(), sizeof(int64_t) * (b->n + 1));
+  if (item_channels) *item_channels = b->item_ch;
+  if (ctas_per_sm) *ctas_per_sm = b->ctas;
+  return PB_OK;
+}
+
+extern "C" int pb_batch_collision(pb_batch *b, const double *f, double *dfdt, void *stream) {
+  clear_error();
+  if (!b || !f || !dfdt) return set_error(PB_EINVAL, "pb_batch_collision: null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc;
+  if ((rc = batch_stage_input(b, f, st)) || (rc = batch_sweep(b, st))) return rc;
+  return batch_fin<-1>(b, dfdt, nullptr, 0.0, st);
+}
+
+extern "C" int pb_batch_rk4_step(pb_batch *b, double *f, double dt, int32_t nsteps, void *stream) {
+  clear_error();
+  if (!b || !f) return set_error(PB_EINVAL, "pb_batch_rk4_step: null argument");
+  if (nsteps < 0 || !std::isfinite(dt)) return set_error(PB_EINVAL, "pb_batch_rk4_step: bad dt or nsteps");
+  if (nsteps == 0) return PB_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!(b->exec && b->rk_f == f && b->rk_dt == dt)) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    if (!b->cap) PB_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+    PB_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = batch_rk4_launches(b, f, dt, b->cap);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      b->exec = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    b->rk_f = f;
+    b->rk_dt = dt;
+  }
+  int rc = batch_stage_input(b, f, st);
+  if (rc) return rc;
+  for (int32_t i = 0; i < nsteps; ++i) PB_CUDA(cudaGraphLaunch(b->exec, st));
+  return PB_OK;
+}
+
+extern "C" int pb_batch_autotune(pb_batch *b, const double *f, void *stream, int32_t *best_item, int32_t *best_ctas,
+                                 double *best_ms) {
+  clear_error();
+  if (!b || !f) return set_error(PB_EINVAL, "pb_batch_autotune: null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int items[3] = {1024, 2048, 4096};
+  const int ctas[3] = {2, 3, 4};
+  int bi = b->item_ch, bc = b->ctas;
+  float best = 1e30f;
+  cudaEvent_t e0, e1;
+  PB_CUDA(cudaEventCreate(&e0));
+  PB_CUDA(cudaEventCreate(&e1));
+  int rc = batch_stage_input(b, f, st);
+  for (int a = 0; a < 3 && rc == PB_OK; ++a) {
+    if ((rc = batch_upload_plan(b, items[a], st))) break;
+    for (int c = 0; c < 3 && rc == PB_OK; ++c) {
+      b->ctas = ctas[c];
+      if ((rc = batch_sweep(b, st))) break;  // warm-up
+      cudaEventRecord(e0, st);
+      for (int k = 0; k < 3 && rc == PB_OK; ++k) rc = batch_sweep(b, st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        bi = items[a];
+        bc = ctas[c];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  b->ctas = bc;
+  if ((rc = batch_upload_plan(b, bi, st))) return rc;
+  if (best_item) *best_item = bi;
+  if (best_ctas) *best_ctas = bc;
+  if (best_ms) *best_ms = best / 3.0;
+  return PB_OK;
+}

@@ -25,7 +25,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
   size_t rp, item_ptr, items, col, coefA, coefB, g2, wt, eps, kc, R, omega, tab, part, acc, y, yff, fstage, Fa, Fb,
-      Fff, tau, invtau, red, scal, obs, total;
+      Fff, tau, invtau, red, scal, obs, g2lo, gstate, tab32, col16, rp_real, vjpG, vecs, total;
 };
 
 struct Plan {
@@ -118,6 +118,15 @@ Layout make_layout(const pb_channels *ch, const Plan &P, int variant, bool trans
   L.red = take(sizeof(double2) * (size_t)nfin_blocks);
   L.scal = take(sizeof(double) * 8);
   L.obs = take(sizeof(double) * 8);
+  const bool mixed = variant == PB_VARIANT_G32 || variant == PB_VARIANT_G16;
+  L.g2lo = take(mixed ? (variant == PB_VARIANT_G32 ? 4 : 2) * nchp : 0);
+  L.gstate = take(mixed ? 16 * ns : 0);
+  auto rad = [](int n) { return (size_t)(n > 1 ? 2 * n : 1); };
+  L.tab32 = take(mixed ? sizeof(float4) * rad(ch->nk[0]) * rad(ch->nk[1]) * rad(ch->nk[2]) * ch->nmodes : 0);
+  L.col16 = take(ns <= 65536 ? sizeof(uint16_t) * nchp : 0);
+  L.rp_real = take(sizeof(int64_t) * (ns + 1));
+  L.vjpG = take(sizeof(float2) * 3 * ns);
+  L.vecs = take(sizeof(double) * 8 * ns);
   L.total = o;
   return L;
 }
@@ -173,10 +182,19 @@ struct pb_dev {
   double *tau = nullptr, *invtau = nullptr;
   double2 *red = nullptr;
   double *scal = nullptr, *obs = nullptr;
+  void *g2lo = nullptr;     // |g|^2 in FP32 or BF16 (mixed-precision variants)
+  uint4 *gstate = nullptr;  // per-state records of the mixed-precision sweep
+  float4 *tab32 = nullptr;  // padded-grid (hbar w hi, hbar w lo, N, 0) in FP32
+  uint16_t *col16 = nullptr;  // 16-bit partner indices (nstate <= 65536), else null
+  int64_t *rp_real = nullptr;  // unpadded CSR row offsets [ns+1]
+  float2 *vjpG = nullptr;      // adjoint gather table [ns][3]
+  double *vecs = nullptr;      // 8 scratch vectors of nstate doubles (adjoint stages)
+  int rad[3] = {1, 1, 1};   // padded-grid radices of the FP32 phonon table
   int nfin_blocks = 0;
   size_t smem_f = 0;      // dynamic smem of the f staging (0 = gather from global)
   size_t smem_F = 0;      // dynamic smem of the transport F staging
   int ctas_tr = 1;        // resident transport CTAs per SM
+  size_t smem_G = 0;      // dynamic smem of the adjoint gather table
   // RK4 graph cache
   cudaStream_t cap = nullptr;
   cudaGraphExec_t rk_exec = nullptr;
@@ -200,6 +218,17 @@ struct pb_dev {
     g.norm = 1.0 / (std::sqrt(2.0 * kPi) * sigma);
     return g;
   }
+  bool mixed() const { return variant == PB_VARIANT_G32 || variant == PB_VARIANT_G16; }
+  pb::dev::GGeom ggeom() const {
+    pb::dev::GGeom g;
+    g.col = col;
+    g.tabp = tab32;
+    const int n1 = rad[0] > 1 ? nk[0] : 0, n2 = rad[1] > 1 ? nk[1] : 0, n3 = rad[2] > 1 ? nk[2] : 0;
+    g.cpad = ((n1 * rad[1] + n2) * rad[2] + n3) * nmodes;
+    g.k2 = (float)(-1.4426950408889634 / (2.0 * sigma * sigma));
+    return g;
+  }
+  double gnorm() const { return 1.0 / (std::sqrt(2.0 * kPi) * sigma); }
   int stream_grid(int per_sm) const {
     const int64_t need = (nitems * 32 + dev::kBlock - 1) / dev::kBlock;
     return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sm_count * per_sm));
@@ -223,10 +252,12 @@ int check_device(int *sm_count) {
 int resolve_opts(const pb_channels *ch, const pb_dev_opts *opts, int sm_count, pb_dev_opts &o) {
   pb_dev_opts d{};
   if (opts) d = *opts;
-  if (d.variant < PB_VARIANT_FF || d.variant > PB_VARIANT_LITERAL)
+  if (d.variant < PB_VARIANT_FF || d.variant > PB_VARIANT_G16)
     return set_error(PB_EINVAL, "pb_dev: variant %d is not available in this build", d.variant);
-  if (d.ctas_per_sm <= 0) d.ctas_per_sm = 4;
+  if (d.ctas_per_sm <= 0) d.ctas_per_sm = 3;  // measured best on GB300 for the coefficient sweeps
   if (d.ctas_per_sm > 8) return set_error(PB_EINVAL, "pb_dev: ctas_per_sm must be <= 8");
+  if (d.transport_gather < 0 || d.transport_gather > 2 || d.transport_ctas < 0 || d.transport_ctas > 4)
+    return set_error(PB_EINVAL, "pb_dev: transport_gather must be 0..2 and transport_ctas 0..4");
   if (d.item_channels < 0 || d.item_channels % 64 != 0)
     return set_error(PB_EINVAL, "pb_dev: item_channels must be a non-negative multiple of 64");
   if (d.item_channels == 0) {
@@ -237,6 +268,18 @@ int resolve_opts(const pb_channels *ch, const pb_dev_opts *opts, int sm_count, p
   }
   o = d;
   return PB_OK;
+}
+
+}  // namespace
+
+namespace {
+
+template <typename IDX>
+void set_stream_smem(int bytes) {
+  cudaFuncSetAttribute(dev::k_stream_ff<dev::MODE_COLL, true, IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(dev::k_stream_ff<dev::MODE_RATE, true, IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(dev::k_stream_f64<dev::MODE_COLL, true, IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(dev::k_stream_f64<dev::MODE_RATE, true, IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 }  // namespace
@@ -340,17 +383,48 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->red = (double2 *)(A + L.red);
   d->scal = (double *)(A + L.scal);
   d->obs = (double *)(A + L.obs);
+  d->g2lo = A + L.g2lo;
+  d->gstate = (uint4 *)(A + L.gstate);
+  d->tab32 = (float4 *)(A + L.tab32);
+  d->col16 = d->ns <= 65536 ? (uint16_t *)(A + L.col16) : nullptr;
+  d->rp_real = (int64_t *)(A + L.rp_real);
+  d->vjpG = (float2 *)(A + L.vjpG);
+  d->vecs = (double *)(A + L.vecs);
 
   // shared-memory staging sizes
   int devid = 0, smem_optin = 0;
   cudaGetDevice(&devid);
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, devid);
-  const size_t fbytes = (d->variant == PB_VARIANT_F64 ? sizeof(double) : sizeof(float2)) * (size_t)d->ns;
+  size_t fbytes = (d->variant == PB_VARIANT_F64 ? sizeof(double) : sizeof(float2)) * (size_t)d->ns;
+  if (d->mixed()) {
+    fbytes = sizeof(uint4) * (size_t)d->ns;
+    if (fbytes + 1024 > (size_t)smem_optin) {
+      delete d;
+      return set_error(PB_EINVAL, "pb_dev_create: the FP32/BF16 variants stage 16 bytes per state in shared memory; "
+                                  "%lld states exceed it", (long long)ch->nstate);
+    }
+    for (int i = 0; i < 3; ++i) d->rad[i] = ch->nk[i] > 1 ? 2 * ch->nk[i] : 1;
+    if ((double)d->rad[0] * d->rad[1] * d->rad[2] * ch->nmodes >= 2147483647.0) {
+      delete d;
+      return set_error(PB_EINVAL, "pb_dev_create: padded phonon table too large for 32-bit indices");
+    }
+    d->ctas = (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(228 * 1024) / (fbytes + 1024)));  // of 512 threads
+  }
   const size_t per_cta_budget = (size_t)(228 * 1024) / (size_t)d->ctas - 1024;
   d->smem_f = (fbytes <= per_cta_budget && fbytes <= (size_t)smem_optin) ? fbytes : 0;
+  if (d->mixed()) d->smem_f = fbytes;
   const size_t Fbytes = sizeof(float2) * 3 * (size_t)d->ns;
-  d->smem_F = Fbytes <= (size_t)smem_optin - 1024 ? Fbytes : 0;
-  d->ctas_tr = d->smem_F ? (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(228 * 1024) / (d->smem_F + 1024))) : 4;
+  const bool F_fits = Fbytes <= (size_t)smem_optin - 1024;
+  // automatic: gather F through L1 (measured faster on GB300 than shared-memory staging,
+  // which limits residency to one 512-thread CTA per SM at 40^3)
+  d->smem_F = (o.transport_gather == 1 && F_fits) ? Fbytes : 0;
+  if (o.transport_gather == 1 && !F_fits) {
+    delete d;
+    return set_error(PB_EINVAL, "pb_dev_create: F of %lld states does not fit in shared memory", (long long)ch->nstate);
+  }
+  d->ctas_tr = d->smem_F ? (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(228 * 1024) / (d->smem_F + 1024))) : 3;
+  if (o.transport_ctas > 0) d->ctas_tr = std::min(d->ctas_tr, o.transport_ctas);
+  if (!d->smem_F && o.transport_ctas > 0) d->ctas_tr = o.transport_ctas;
 
   // host staging of the padded arrays
   int status = PB_OK;
@@ -385,9 +459,15 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   } while (0)
     do {
       UP(d->rp, P.rp.data(), sizeof(int64_t) * (d->ns + 1));
+      UP(d->rp_real, ch->row_ptr.data(), sizeof(int64_t) * (d->ns + 1));
       UP(d->item_ptr, P.item_ptr.data(), sizeof(int32_t) * (d->ns + 1));
       UP(d->items, P.items.data(), sizeof(Item) * P.nitems);
       UP(d->col, colp.data(), sizeof(uint32_t) * P.nchp);
+      if (d->col16) {
+        std::vector<uint16_t> c16((size_t)P.nchp);
+        for (int64_t i = 0; i < P.nchp; ++i) c16[i] = (uint16_t)(colp[i] & kPartnerMask);
+        UP(d->col16, c16.data(), sizeof(uint16_t) * P.nchp);  // pageable source: staged before return
+      }
       UP(d->g2, g2p.data(), sizeof(double) * P.nchp);
       UP(d->eps, ch->eps.data(), sizeof(double) * d->ns);
       UP(d->kc, kc.data(), sizeof(short4) * d->ns);
@@ -416,6 +496,21 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
         if (e != cudaSuccess) status = cuda_fail(e, "k_rowsum");
       }
     }
+    if (status == PB_OK && d->mixed()) {
+      const long long n = (long long)P.nchp;
+      const int cg = (int)std::min<long long>((n + 255) / 256, 8192);
+      if (d->variant == PB_VARIANT_G32)
+        dev::k_cvt_g2<float><<<cg, 256, 0, st>>>(d->g2, n, (float *)d->g2lo);
+      else
+        dev::k_cvt_g2<__nv_bfloat16><<<cg, 256, 0, st>>>(d->g2, n, (__nv_bfloat16 *)d->g2lo);
+      dev::k_gstate_init<<<(int)((d->ns + 255) / 256), 256, 0, st>>>(d->eps, d->kc, (int)d->ns, d->rad[1], d->rad[2],
+                                                                      ch->nmodes, d->gstate);
+      const long long nt = (long long)d->rad[0] * d->rad[1] * d->rad[2] * ch->nmodes;
+      dev::k_tab_padded<<<(int)std::min<long long>((nt + 255) / 256, 8192), 256, 0, st>>>(
+          d->tab, ch->nk[0], ch->nk[1], ch->nk[2], d->rad[0], d->rad[1], d->rad[2], ch->nmodes, d->tab32);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) status = cuda_fail(e, "mixed-precision setup");
+    }
     if (status == PB_OK) {
       cudaError_t e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) status = cuda_fail(e, "pb_dev_create: synchronize");
@@ -428,13 +523,27 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
     return status;
   }
   if (d->smem_f > 48 * 1024) {
-    cudaFuncSetAttribute(dev::k_stream_ff<dev::MODE_COLL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
-    cudaFuncSetAttribute(dev::k_stream_ff<dev::MODE_RATE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
-    cudaFuncSetAttribute(dev::k_stream_f64<dev::MODE_COLL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
-    cudaFuncSetAttribute(dev::k_stream_f64<dev::MODE_RATE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
+    set_stream_smem<uint32_t>((int)d->smem_f);
+    set_stream_smem<uint16_t>((int)d->smem_f);
   }
-  if (d->smem_F > 48 * 1024)
-    cudaFuncSetAttribute(dev::k_stream_tr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_F);
+  if (d->smem_F > 48 * 1024) {
+    cudaFuncSetAttribute(dev::k_stream_tr<true, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_F);
+    cudaFuncSetAttribute(dev::k_stream_tr<true, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_F);
+  }
+  {
+    const size_t gb = sizeof(float2) * 3 * (size_t)d->ns;
+    if (gb > 48 * 1024 && gb + 1024 <= (size_t)smem_optin) {
+      cudaFuncSetAttribute(dev::k_stream_vjp<true, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gb);
+      cudaFuncSetAttribute(dev::k_stream_vjp<true, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gb);
+    }
+    d->smem_G = gb + 1024 <= (size_t)smem_optin ? gb : 0;
+  }
+  if (d->mixed() && d->smem_f > 48 * 1024) {
+    cudaFuncSetAttribute(dev::k_stream_g<dev::MODE_COLL, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
+    cudaFuncSetAttribute(dev::k_stream_g<dev::MODE_RATE, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
+    cudaFuncSetAttribute(dev::k_stream_g<dev::MODE_COLL, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
+    cudaFuncSetAttribute(dev::k_stream_g<dev::MODE_RATE, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
+  }
   cudaGetLastError();
   *out = d;
   return PB_OK;
@@ -459,8 +568,10 @@ extern "C" int pb_dev_get_info(const pb_dev *d, pb_dev_info *info) {
   info->sm_count = d->sm_count;
   info->c = d->c;
   switch (d->variant) {
-    case PB_VARIANT_FF: info->bytes_per_channel = 2 * sizeof(float2) + sizeof(uint32_t); break;
-    case PB_VARIANT_F64: info->bytes_per_channel = 2 * sizeof(double) + sizeof(uint32_t); break;
+    case PB_VARIANT_FF: info->bytes_per_channel = 2 * sizeof(float2) + (d->col16 ? 2 : 4); break;
+    case PB_VARIANT_F64: info->bytes_per_channel = 2 * sizeof(double) + (d->col16 ? 2 : 4); break;
+    case PB_VARIANT_G32: info->bytes_per_channel = sizeof(float) + sizeof(uint32_t); break;
+    case PB_VARIANT_G16: info->bytes_per_channel = 2 + sizeof(uint32_t); break;
     default: info->bytes_per_channel = sizeof(double) + sizeof(uint32_t); break;
   }
   return PB_OK;
@@ -469,54 +580,72 @@ extern "C" int pb_dev_get_info(const pb_dev *d, pb_dev_info *info) {
 namespace {
 
 // Stream pass over all items: part[item] = (A, B) or the literal sums.  `fd` is the
-// distribution in double, `fff` its float-float copy (used by the FF variant).
-int launch_stream(pb_dev *d, int mode, const double *fd, const float2 *fff, cudaStream_t st) {
+// distribution in double, `fff` its float-float copy (used by the FF variant); `colp` the
+// partner indices (packed 32-bit words or the 16-bit copy).
+template <typename IDX>
+int launch_stream_t(pb_dev *d, int mode, const double *fd, const float2 *fff, const IDX *colp, Part4 *part,
+                    cudaStream_t st) {
   const int grid = d->stream_grid(d->ctas);
   const int n = (int)d->nitems;
-  const uint4 *col4 = (const uint4 *)d->col;
+  const int ns = (int)d->ns;
+  const bool coll = mode == dev::MODE_COLL;
   if (d->variant == PB_VARIANT_FF) {
     const float4 *A4 = (const float4 *)d->coefA, *B4 = (const float4 *)d->coefB;
     if (d->smem_f) {
-      if (mode == dev::MODE_COLL)
-        dev::k_stream_ff<dev::MODE_COLL, true><<<grid, dev::kBlock, d->smem_f, st>>>(d->items, n, A4, B4, col4, fff, (int)d->ns, d->part);
-      else
-        dev::k_stream_ff<dev::MODE_RATE, true><<<grid, dev::kBlock, d->smem_f, st>>>(d->items, n, A4, B4, col4, fff, (int)d->ns, d->part);
+      if (coll) dev::k_stream_ff<dev::MODE_COLL, true, IDX><<<grid, dev::kBlock, d->smem_f, st>>>(d->items, n, A4, B4, colp, fff, ns, part);
+      else      dev::k_stream_ff<dev::MODE_RATE, true, IDX><<<grid, dev::kBlock, d->smem_f, st>>>(d->items, n, A4, B4, colp, fff, ns, part);
     } else {
-      if (mode == dev::MODE_COLL)
-        dev::k_stream_ff<dev::MODE_COLL, false><<<grid, dev::kBlock, 0, st>>>(d->items, n, A4, B4, col4, fff, (int)d->ns, d->part);
-      else
-        dev::k_stream_ff<dev::MODE_RATE, false><<<grid, dev::kBlock, 0, st>>>(d->items, n, A4, B4, col4, fff, (int)d->ns, d->part);
+      if (coll) dev::k_stream_ff<dev::MODE_COLL, false, IDX><<<grid, dev::kBlock, 0, st>>>(d->items, n, A4, B4, colp, fff, ns, part);
+      else      dev::k_stream_ff<dev::MODE_RATE, false, IDX><<<grid, dev::kBlock, 0, st>>>(d->items, n, A4, B4, colp, fff, ns, part);
     }
   } else if (d->variant == PB_VARIANT_F64) {
     const double2 *A2 = (const double2 *)d->coefA, *B2 = (const double2 *)d->coefB;
     if (d->smem_f) {
-      if (mode == dev::MODE_COLL)
-        dev::k_stream_f64<dev::MODE_COLL, true><<<grid, dev::kBlock, d->smem_f, st>>>(d->items, n, A2, B2, col4, fd, (int)d->ns, d->part);
-      else
-        dev::k_stream_f64<dev::MODE_RATE, true><<<grid, dev::kBlock, d->smem_f, st>>>(d->items, n, A2, B2, col4, fd, (int)d->ns, d->part);
+      if (coll) dev::k_stream_f64<dev::MODE_COLL, true, IDX><<<grid, dev::kBlock, d->smem_f, st>>>(d->items, n, A2, B2, colp, fd, ns, part);
+      else      dev::k_stream_f64<dev::MODE_RATE, true, IDX><<<grid, dev::kBlock, d->smem_f, st>>>(d->items, n, A2, B2, colp, fd, ns, part);
     } else {
-      if (mode == dev::MODE_COLL)
-        dev::k_stream_f64<dev::MODE_COLL, false><<<grid, dev::kBlock, 0, st>>>(d->items, n, A2, B2, col4, fd, (int)d->ns, d->part);
-      else
-        dev::k_stream_f64<dev::MODE_RATE, false><<<grid, dev::kBlock, 0, st>>>(d->items, n, A2, B2, col4, fd, (int)d->ns, d->part);
+      if (coll) dev::k_stream_f64<dev::MODE_COLL, false, IDX><<<grid, dev::kBlock, 0, st>>>(d->items, n, A2, B2, colp, fd, ns, part);
+      else      dev::k_stream_f64<dev::MODE_RATE, false, IDX><<<grid, dev::kBlock, 0, st>>>(d->items, n, A2, B2, colp, fd, ns, part);
+    }
+  } else if (d->mixed()) {
+    const dev::GGeom g = d->ggeom();
+    const int gg = (int)std::max<int64_t>(1, std::min<int64_t>((d->nitems * 32 + 511) / 512, (int64_t)d->sm_count * d->ctas));
+    if (d->variant == PB_VARIANT_G32) {
+      if (coll) dev::k_stream_g<dev::MODE_COLL, float><<<gg, 512, d->smem_f, st>>>(d->items, n, g, (const float *)d->g2lo, d->gstate, ns, part);
+      else      dev::k_stream_g<dev::MODE_RATE, float><<<gg, 512, d->smem_f, st>>>(d->items, n, g, (const float *)d->g2lo, d->gstate, ns, part);
+    } else {
+      if (coll) dev::k_stream_g<dev::MODE_COLL, __nv_bfloat16><<<gg, 512, d->smem_f, st>>>(d->items, n, g, (const __nv_bfloat16 *)d->g2lo, d->gstate, ns, part);
+      else      dev::k_stream_g<dev::MODE_RATE, __nv_bfloat16><<<gg, 512, d->smem_f, st>>>(d->items, n, g, (const __nv_bfloat16 *)d->g2lo, d->gstate, ns, part);
     }
   } else {
     const dev::ChanGeom g = d->geom();
     const int lgrid = d->stream_grid(8);
-    if (mode == dev::MODE_COLL)
-      dev::k_stream_literal<dev::MODE_COLL><<<lgrid, dev::kBlock, 0, st>>>(d->items, n, g, fd, d->part);
-    else
-      dev::k_stream_literal<dev::MODE_RATE><<<lgrid, dev::kBlock, 0, st>>>(d->items, n, g, fd, d->part);
+    if (coll) dev::k_stream_literal<dev::MODE_COLL><<<lgrid, dev::kBlock, 0, st>>>(d->items, n, g, fd, part);
+    else      dev::k_stream_literal<dev::MODE_RATE><<<lgrid, dev::kBlock, 0, st>>>(d->items, n, g, fd, part);
   }
   PB_LAUNCHED("stream kernel");
   return PB_OK;
+}
+
+int launch_stream_to(pb_dev *d, int mode, const double *fd, const float2 *fff, Part4 *part, cudaStream_t st) {
+  if (d->col16) return launch_stream_t<uint16_t>(d, mode, fd, fff, d->col16, part, st);
+  return launch_stream_t<uint32_t>(d, mode, fd, fff, d->col, part, st);
+}
+
+int launch_stream(pb_dev *d, int mode, const double *fd, const float2 *fff, cudaStream_t st) {
+  return launch_stream_to(d, mode, fd, fff, d->part, st);
 }
 
 int fin_grid(const pb_dev *d) { return d->nfin_blocks; }
 
 template <int STAGE>
 void launch_fin(pb_dev *d, const double *ysrc, double *out, double *f, double dt, cudaStream_t st) {
-  if (d->variant == PB_VARIANT_LITERAL)
+  if (d->mixed())
+    dev::k_fin_coll<true, STAGE, true><<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, (int)d->ns,
+                                                                          d->c * d->gnorm(), d->R,
+                                                                          ysrc, out, f, d->acc, d->y,
+                                                                          (float2 *)d->gstate, dt);
+  else if (d->variant == PB_VARIANT_LITERAL)
     dev::k_fin_coll<true, STAGE><<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->c, d->R, ysrc,
                                                                     out, f, d->acc, d->y, d->yff, dt);
   else
@@ -528,6 +657,16 @@ int to_ff(pb_dev *d, const double *x, int64_t n, float2 *out, cudaStream_t st) {
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 1024));
   dev::k_to_ff<<<grid, 256, 0, st>>>(x, (long long)n, out);
   PB_LAUNCHED("k_to_ff");
+  return PB_OK;
+}
+
+// Stage-input conversion the streaming kernel of this variant reads.
+int stage_input(pb_dev *d, const double *f, cudaStream_t st) {
+  if (d->variant == PB_VARIANT_FF) return to_ff(d, f, d->ns, d->yff, st);
+  if (d->mixed()) {
+    dev::k_gstate_f<<<(int)((d->ns + 255) / 256), 256, 0, st>>>(f, (int)d->ns, d->gstate);
+    PB_LAUNCHED("k_gstate_f");
+  }
   return PB_OK;
 }
 
@@ -591,15 +730,15 @@ int ensure_weights(pb_dev *d, const double *f0, cudaStream_t st) {
 int transport_pass(pb_dev *d, const float2 *Fin_ff, const double *vel3, const double *Fold, double *Fnew,
                    float2 *Fnew_ff, cudaStream_t st) {
   const int n = (int)d->nitems;
-  const uint4 *col4 = (const uint4 *)d->col;
   const float4 *W4 = (const float4 *)d->wt;
   const int64_t need = (d->nitems * 32 + 511) / 512;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)d->sm_count * d->ctas_tr));
   if (d->smem_F) {
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)d->sm_count * d->ctas_tr));
-    dev::k_stream_tr<true><<<grid, 512, d->smem_F, st>>>(d->items, n, W4, col4, Fin_ff, (int)d->ns, d->part);
+    if (d->col16) dev::k_stream_tr<true, uint16_t><<<grid, 512, d->smem_F, st>>>(d->items, n, W4, d->col16, Fin_ff, (int)d->ns, d->part);
+    else          dev::k_stream_tr<true, uint32_t><<<grid, 512, d->smem_F, st>>>(d->items, n, W4, d->col, Fin_ff, (int)d->ns, d->part);
   } else {
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)d->sm_count * d->ctas_tr));
-    dev::k_stream_tr<false><<<grid, 512, 0, st>>>(d->items, n, W4, col4, Fin_ff, (int)d->ns, d->part);
+    if (d->col16) dev::k_stream_tr<false, uint16_t><<<grid, 512, 0, st>>>(d->items, n, W4, d->col16, Fin_ff, (int)d->ns, d->part);
+    else          dev::k_stream_tr<false, uint32_t><<<grid, 512, 0, st>>>(d->items, n, W4, d->col, Fin_ff, (int)d->ns, d->part);
   }
   PB_LAUNCHED("k_stream_tr");
   dev::k_fin_tr<<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->tau, vel3, Fold, Fnew,
@@ -617,7 +756,7 @@ extern "C" int pb_collision(pb_dev *d, const double *f, double *dfdt, void *stre
   if (!d || !f || !dfdt) return set_error(PB_EINVAL, "pb_collision: null argument");
   cudaStream_t st = (cudaStream_t)stream;
   int rc;
-  if (d->variant == PB_VARIANT_FF && (rc = to_ff(d, f, d->ns, d->yff, st))) return rc;
+  if ((rc = stage_input(d, f, st))) return rc;
   if ((rc = launch_stream(d, dev::MODE_COLL, f, d->yff, st))) return rc;
   launch_fin<-1>(d, f, dfdt, nullptr, 0.0, st);
   PB_LAUNCHED("k_fin_coll");
@@ -629,10 +768,11 @@ extern "C" int pb_scatter_rates(pb_dev *d, const double *f, double *inv_tau, voi
   if (!d || !f || !inv_tau) return set_error(PB_EINVAL, "pb_scatter_rates: null argument");
   cudaStream_t st = (cudaStream_t)stream;
   int rc;
-  if (d->variant == PB_VARIANT_FF && (rc = to_ff(d, f, d->ns, d->yff, st))) return rc;
+  if ((rc = stage_input(d, f, st))) return rc;
   if ((rc = launch_stream(d, dev::MODE_RATE, f, d->yff, st))) return rc;
-  if (d->variant == PB_VARIANT_LITERAL)
-    dev::k_fin_rate<true><<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->c, d->R, inv_tau);
+  if (d->variant == PB_VARIANT_LITERAL || d->mixed())
+    dev::k_fin_rate<true><<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, (int)d->ns,
+                                                             d->mixed() ? d->c * d->gnorm() : d->c, d->R, inv_tau);
   else
     dev::k_fin_rate<false><<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->c, d->R, inv_tau);
   PB_LAUNCHED("k_fin_rate");
@@ -647,7 +787,7 @@ extern "C" int pb_rtbte_rk4_step(pb_dev *d, double *f, double dt, int32_t nsteps
   cudaStream_t st = (cudaStream_t)stream;
   int rc = ensure_rk_graph(d, f, dt);
   if (rc) return rc;
-  if ((rc = to_ff(d, f, d->ns, d->yff, st))) return rc;
+  if ((rc = stage_input(d, f, st))) return rc;
   for (int32_t i = 0; i < nsteps; ++i) PB_CUDA(cudaGraphLaunch(d->rk_exec, st));
   return PB_OK;
 }
@@ -739,6 +879,123 @@ extern "C" int pb_observables(pb_dev *d, const double *f, double *out3, void *st
   return PB_OK;
 }
 
+// ---------------------------------------------------------------- adjoint
+
+namespace {
+
+int coef_setup(pb_dev *d, cudaStream_t st) {
+  const int grid = d->stream_grid(8);
+  const dev::ChanGeom g = d->geom();
+  if (d->variant == PB_VARIANT_FF)
+    dev::k_coef<true><<<grid, dev::kBlock, 0, st>>>(d->items, (int)d->nitems, g, d->coefA, d->coefB, d->part);
+  else if (d->variant == PB_VARIANT_F64)
+    dev::k_coef<false><<<grid, dev::kBlock, 0, st>>>(d->items, (int)d->nitems, g, d->coefA, d->coefB, d->part);
+  PB_LAUNCHED("k_coef");
+  if (d->variant == PB_VARIANT_FF || d->variant == PB_VARIANT_F64) {
+    dev::k_rowsum<<<(int)((d->ns + 255) / 256), 256, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->R);
+    PB_LAUNCHED("k_rowsum");
+  }
+  if (d->mixed()) {
+    const long long n = (long long)d->nchp;
+    const int cg = (int)std::min<long long>((n + 255) / 256, 8192);
+    if (d->variant == PB_VARIANT_G32)
+      dev::k_cvt_g2<float><<<cg, 256, 0, st>>>(d->g2, n, (float *)d->g2lo);
+    else
+      dev::k_cvt_g2<__nv_bfloat16><<<cg, 256, 0, st>>>(d->g2, n, (__nv_bfloat16 *)d->g2lo);
+    PB_LAUNCHED("k_cvt_g2");
+  }
+  return PB_OK;
+}
+
+// grad_f = J(f)^T lam (FF coefficients); grad_g2 (unpadded CSR order) += dL/dg2 if not null
+int vjp_launch(pb_dev *d, const double *f, const double *lam, double *grad_f, double *grad_g2, cudaStream_t st) {
+  const int ns = (int)d->ns, n = (int)d->nitems;
+  dev::k_vjp_prep<<<(ns + 255) / 256, 256, 0, st>>>(f, lam, ns, d->vjpG);
+  PB_LAUNCHED("k_vjp_prep");
+  const int grid = d->stream_grid(d->smem_G ? std::max(1, std::min(d->ctas, (int)((228 * 1024) / (d->smem_G + 1024)))) : d->ctas);
+  const float4 *A4 = (const float4 *)d->coefA, *B4 = (const float4 *)d->coefB;
+  if (d->smem_G) {
+    if (d->col16) dev::k_stream_vjp<true, uint16_t><<<grid, dev::kBlock, d->smem_G, st>>>(d->items, n, A4, B4, d->col16, d->vjpG, ns, d->part);
+    else          dev::k_stream_vjp<true, uint32_t><<<grid, dev::kBlock, d->smem_G, st>>>(d->items, n, A4, B4, d->col, d->vjpG, ns, d->part);
+  } else {
+    if (d->col16) dev::k_stream_vjp<false, uint16_t><<<grid, dev::kBlock, 0, st>>>(d->items, n, A4, B4, d->col16, d->vjpG, ns, d->part);
+    else          dev::k_stream_vjp<false, uint32_t><<<grid, dev::kBlock, 0, st>>>(d->items, n, A4, B4, d->col, d->vjpG, ns, d->part);
+  }
+  PB_LAUNCHED("k_stream_vjp");
+  dev::k_fin_vjp<<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, ns, d->c, d->R, lam, grad_f);
+  PB_LAUNCHED("k_fin_vjp");
+  if (grad_g2) {
+    const int gg = d->stream_grid(8);
+    const float2 *A = (const float2 *)d->coefA, *B = (const float2 *)d->coefB;
+    if (d->col16)
+      dev::k_g2grad<uint16_t><<<gg, dev::kBlock, 0, st>>>(d->items, n, (const long long *)d->rp, (const long long *)d->rp_real,
+                                                          A, B, d->col16, d->g2, f, lam, d->c, grad_g2);
+    else
+      dev::k_g2grad<uint32_t><<<gg, dev::kBlock, 0, st>>>(d->items, n, (const long long *)d->rp, (const long long *)d->rp_real,
+                                                          A, B, d->col, d->g2, f, lam, d->c, grad_g2);
+    PB_LAUNCHED("k_g2grad");
+  }
+  return PB_OK;
+}
+
+int lincomb(pb_dev *d, double a, const double *x, double b, const double *y, double *out, cudaStream_t st) {
+  dev::k_lincomb<<<(int)((d->ns + 255) / 256), 256, 0, st>>>((int)d->ns, a, x, b, y, out);
+  PB_LAUNCHED("k_lincomb");
+  return PB_OK;
+}
+
+}  // namespace
+
+extern "C" int pb_collision_vjp(pb_dev *d, const double *f, const double *lam, double *grad_f, double *grad_g2,
+                                void *stream) {
+  clear_error();
+  if (!d || !f || !lam || !grad_f) return set_error(PB_EINVAL, "pb_collision_vjp: null argument");
+  if (d->variant != PB_VARIANT_FF) return set_error(PB_EINVAL, "pb_collision_vjp: needs the FF variant");
+  return vjp_launch(d, f, lam, grad_f, grad_g2, (cudaStream_t)stream);
+}
+
+extern "C" int pb_rtbte_rk4_vjp(pb_dev *d, const double *f, double *lam, double dt, double *grad_g2, void *stream) {
+  clear_error();
+  if (!d || !f || !lam) return set_error(PB_EINVAL, "pb_rtbte_rk4_vjp: null argument");
+  if (d->variant != PB_VARIANT_FF) return set_error(PB_EINVAL, "pb_rtbte_rk4_vjp: needs the FF variant");
+  if (!std::isfinite(dt)) return set_error(PB_EINVAL, "pb_rtbte_rk4_vjp: bad dt");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t ns = d->ns;
+  double *u2 = d->vecs, *u3 = u2 + ns, *u4 = u3 + ns, *k = u4 + ns, *g = k + ns, *mu = g + ns, *acc = mu + ns,
+         *mprev = acc + ns;
+  int rc;
+  // forward stages (u1 = f)
+  if ((rc = pb_collision(d, f, k, stream))) return rc;
+  if ((rc = lincomb(d, 1.0, f, 0.5 * dt, k, u2, st))) return rc;
+  if ((rc = pb_collision(d, u2, k, stream))) return rc;
+  if ((rc = lincomb(d, 1.0, f, 0.5 * dt, k, u3, st))) return rc;
+  if ((rc = pb_collision(d, u3, k, stream))) return rc;
+  if ((rc = lincomb(d, 1.0, f, dt, k, u4, st))) return rc;
+  // reverse: dL/dk4 = dt/6 lam; dL/dk3 = dt/3 lam + dt mu4; dL/dk2 = dt/3 lam + dt/2 mu3;
+  // dL/dk1 = dt/6 lam + dt/2 mu2; dL/df = lam + mu1 + mu2 + mu3 + mu4, mu_i = J(u_i)^T dL/dk_i
+  const double *U[4] = {f, u2, u3, u4};
+  const double wl[4] = {dt / 6.0, dt / 3.0, dt / 3.0, dt / 6.0};
+  const double wm[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
+  if ((rc = lincomb(d, 1.0, lam, 0.0, nullptr, acc, st))) return rc;
+  for (int j = 3; j >= 0; --j) {
+    if ((rc = lincomb(d, wl[j], lam, wm[j], j == 3 ? nullptr : mprev, g, st))) return rc;
+    if ((rc = vjp_launch(d, U[j], g, mu, grad_g2, st))) return rc;
+    if ((rc = lincomb(d, 1.0, acc, 1.0, mu, acc, st))) return rc;
+    if ((rc = lincomb(d, 1.0, mu, 0.0, nullptr, mprev, st))) return rc;
+  }
+  return lincomb(d, 1.0, acc, 0.0, nullptr, lam, st);
+}
+
+extern "C" int pb_dev_set_g2(pb_dev *d, const double *g2, void *stream) {
+  clear_error();
+  if (!d || !g2) return set_error(PB_EINVAL, "pb_dev_set_g2: null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  dev::k_set_g2<<<d->stream_grid(8), dev::kBlock, 0, st>>>(d->items, (int)d->nitems, (const long long *)d->rp,
+                                                           (const long long *)d->rp_real, g2, d->g2);
+  PB_LAUNCHED("k_set_g2");
+  return coef_setup(d, st);
+}
+
 // ---------------------------------------------------------------- no-allocation collision
 //
 // pb_collision_static: the collision sweep for callers that may not allocate device
@@ -777,6 +1034,8 @@ int static_scratch_address(void **out) {
 extern "C" int pb_collision_static(pb_dev *d, const double *f, double *dfdt, void *stream) {
   clear_error();
   if (!d || !f || !dfdt) return set_error(PB_EINVAL, "pb_collision_static: null argument");
+  if (d->mixed())
+    return set_error(PB_EINVAL, "pb_collision_static: available for the FF, F64 and literal variants only");
   const size_t ff_bytes = align_up(sizeof(float2) * (size_t)d->ns);
   const size_t part_bytes = sizeof(Part4) * (size_t)d->nitems;
   if (ff_bytes + part_bytes > (size_t)PB_STATIC_SCRATCH_BYTES)
@@ -790,30 +1049,8 @@ extern "C" int pb_collision_static(pb_dev *d, const double *f, double *dfdt, voi
   float2 *fff = (float2 *)base;
   Part4 *part = (Part4 *)((char *)base + ff_bytes);
   cudaStream_t st = (cudaStream_t)stream;
-  const int n = (int)d->nitems;
-  const uint4 *col4 = (const uint4 *)d->col;
-  if (d->variant == PB_VARIANT_FF) {
-    if ((rc = to_ff(d, f, d->ns, fff, st))) return rc;
-    const int grid = d->stream_grid(d->ctas);
-    const float4 *A4 = (const float4 *)d->coefA, *B4 = (const float4 *)d->coefB;
-    if (d->smem_f)
-      dev::k_stream_ff<dev::MODE_COLL, true><<<grid, dev::kBlock, d->smem_f, st>>>(d->items, n, A4, B4, col4, fff,
-                                                                                  (int)d->ns, part);
-    else
-      dev::k_stream_ff<dev::MODE_COLL, false><<<grid, dev::kBlock, 0, st>>>(d->items, n, A4, B4, col4, fff,
-                                                                           (int)d->ns, part);
-  } else if (d->variant == PB_VARIANT_F64) {
-    const int grid = d->stream_grid(d->ctas);
-    const double2 *A2 = (const double2 *)d->coefA, *B2 = (const double2 *)d->coefB;
-    if (d->smem_f)
-      dev::k_stream_f64<dev::MODE_COLL, true><<<grid, dev::kBlock, d->smem_f, st>>>(d->items, n, A2, B2, col4, f,
-                                                                                   (int)d->ns, part);
-    else
-      dev::k_stream_f64<dev::MODE_COLL, false><<<grid, dev::kBlock, 0, st>>>(d->items, n, A2, B2, col4, f,
-                                                                            (int)d->ns, part);
-  } else {
-    dev::k_stream_literal<dev::MODE_COLL><<<d->stream_grid(8), dev::kBlock, 0, st>>>(d->items, n, d->geom(), f, part);
-  }
+  if (d->variant == PB_VARIANT_FF && (rc = to_ff(d, f, d->ns, fff, st))) return rc;
+  if ((rc = launch_stream_to(d, dev::MODE_COLL, f, fff, part, st))) return rc;
   PB_LAUNCHED("pb_collision_static: stream kernel");
   if (d->variant == PB_VARIANT_LITERAL)
     dev::k_fin_coll<true, -1><<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, part, (int)d->ns, d->c, d->R, f, dfdt,
@@ -824,3 +1061,6 @@ extern "C" int pb_collision_static(pb_dev *d, const double *f, double *dfdt, voi
   PB_LAUNCHED("pb_collision_static: k_fin_coll");
   return PB_OK;
 }
+
+// ---------------------------------------------------------------- batched rt-BTE
+#include "batch.cuh"

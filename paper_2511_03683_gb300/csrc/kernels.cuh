@@ -18,6 +18,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace pb {
@@ -199,16 +200,31 @@ __global__ void k_recip(const double *__restrict__ x, int n, double *__restrict_
   if (i < n) out[i] = x[i] > 0.0 ? 1.0 / x[i] : 0.0;
 }
 
+// Partner indices of the 4-channel group q, from the packed 32-bit words (partner in the
+// low 24 bits) or from the compact 16-bit copy kept when nstate <= 65536.
+template <typename IDX>
+__device__ __forceinline__ uint4 partners4(const IDX *__restrict__ col, long long q);
+template <>
+__device__ __forceinline__ uint4 partners4<uint32_t>(const uint32_t *__restrict__ col, long long q) {
+  const uint4 c = __ldcs((const uint4 *)col + q);
+  return make_uint4(c.x & 0xFFFFFFu, c.y & 0xFFFFFFu, c.z & 0xFFFFFFu, c.w & 0xFFFFFFu);
+}
+template <>
+__device__ __forceinline__ uint4 partners4<uint16_t>(const uint16_t *__restrict__ col, long long q) {
+  const uint2 c = __ldcs((const uint2 *)col + q);
+  return make_uint4(c.x & 0xFFFFu, c.x >> 16, c.y & 0xFFFFu, c.y >> 16);
+}
+
 // ------------------------------------------------------------ streaming kernels
 enum { MODE_COLL = 0, MODE_RATE = 1 };
 
 // Float-float coefficient stream.  Channel c: coefA[c] = P_in (hi,lo), coefB[c] = D (hi,lo),
 // col4 = packed partner index.  One warp per item, each lane two 4-channel groups per trip.
 // part[item] = (A, B) where A = sum f_p P_in, B = sum f_p D (MODE_RATE: only B).
-template <int MODE, bool SMEM>
+template <int MODE, bool SMEM, typename IDX>
 __global__ void __launch_bounds__(kBlock) k_stream_ff(const Item *__restrict__ items, int nitems,
                                                       const float4 *__restrict__ A4, const float4 *__restrict__ B4,
-                                                      const uint4 *__restrict__ col4,
+                                                      const IDX *__restrict__ colp,
                                                       const float2 *__restrict__ fg, int ns,
                                                       Part4 *__restrict__ part) {
   extern __shared__ float2 fsm[];
@@ -228,7 +244,7 @@ __global__ void __launch_bounds__(kBlock) k_stream_ff(const Item *__restrict__ i
     int g = lane;
     for (; g + 32 < ng; g += 64) {
       const long long q0 = g0 + g, q1 = q0 + 32;
-      const uint4 c0 = __ldcs(col4 + q0), c1 = __ldcs(col4 + q1);
+      const uint4 c0 = partners4(colp, q0), c1 = partners4(colp, q1);
       float4 a00, a01, a10, a11;
       if (MODE == MODE_COLL) {
         a00 = __ldcs(A4 + 2 * q0); a01 = __ldcs(A4 + 2 * q0 + 1);
@@ -236,8 +252,8 @@ __global__ void __launch_bounds__(kBlock) k_stream_ff(const Item *__restrict__ i
       }
       const float4 b00 = __ldcs(B4 + 2 * q0), b01 = __ldcs(B4 + 2 * q0 + 1);
       const float4 b10 = __ldcs(B4 + 2 * q1), b11 = __ldcs(B4 + 2 * q1 + 1);
-      const float2 f0 = fv[c0.x & 0xFFFFFFu], f1 = fv[c0.y & 0xFFFFFFu], f2 = fv[c0.z & 0xFFFFFFu], f3 = fv[c0.w & 0xFFFFFFu];
-      const float2 f4 = fv[c1.x & 0xFFFFFFu], f5 = fv[c1.y & 0xFFFFFFu], f6 = fv[c1.z & 0xFFFFFFu], f7 = fv[c1.w & 0xFFFFFFu];
+      const float2 f0 = fv[c0.x], f1 = fv[c0.y], f2 = fv[c0.z], f3 = fv[c0.w];
+      const float2 f4 = fv[c1.x], f5 = fv[c1.y], f6 = fv[c1.z], f7 = fv[c1.w];
       if (MODE == MODE_COLL) {
         ff_mac(ah, al, f0, a00.x, a00.y); ff_mac(ah, al, f1, a00.z, a00.w);
         ff_mac(ah, al, f2, a01.x, a01.y); ff_mac(ah, al, f3, a01.z, a01.w);
@@ -251,8 +267,8 @@ __global__ void __launch_bounds__(kBlock) k_stream_ff(const Item *__restrict__ i
     }
     if (g < ng) {
       const long long q0 = g0 + g;
-      const uint4 c0 = __ldcs(col4 + q0);
-      const float2 f0 = fv[c0.x & 0xFFFFFFu], f1 = fv[c0.y & 0xFFFFFFu], f2 = fv[c0.z & 0xFFFFFFu], f3 = fv[c0.w & 0xFFFFFFu];
+      const uint4 c0 = partners4(colp, q0);
+      const float2 f0 = fv[c0.x], f1 = fv[c0.y], f2 = fv[c0.z], f3 = fv[c0.w];
       if (MODE == MODE_COLL) {
         const float4 a00 = __ldcs(A4 + 2 * q0), a01 = __ldcs(A4 + 2 * q0 + 1);
         ff_mac(ah, al, f0, a00.x, a00.y); ff_mac(ah, al, f1, a00.z, a00.w);
@@ -269,10 +285,10 @@ __global__ void __launch_bounds__(kBlock) k_stream_ff(const Item *__restrict__ i
 }
 
 // Same coefficient stream held as doubles, with native FP64 FMAs (f gathered as double).
-template <int MODE, bool SMEM>
+template <int MODE, bool SMEM, typename IDX>
 __global__ void __launch_bounds__(kBlock) k_stream_f64(const Item *__restrict__ items, int nitems,
                                                        const double2 *__restrict__ A2, const double2 *__restrict__ B2,
-                                                       const uint4 *__restrict__ col4, const double *__restrict__ fg,
+                                                       const IDX *__restrict__ colp, const double *__restrict__ fg,
                                                        int ns, Part4 *__restrict__ part) {
   extern __shared__ double fsd[];
   if (SMEM) {
@@ -290,8 +306,8 @@ __global__ void __launch_bounds__(kBlock) k_stream_f64(const Item *__restrict__ 
     double A = 0.0, B = 0.0;
     for (int g = lane; g < ng; g += 32) {
       const long long q = g0 + g;
-      const uint4 c = __ldcs(col4 + q);
-      const double f0 = fv[c.x & 0xFFFFFFu], f1 = fv[c.y & 0xFFFFFFu], f2 = fv[c.z & 0xFFFFFFu], f3 = fv[c.w & 0xFFFFFFu];
+      const uint4 c = partners4(colp, q);
+      const double f0 = fv[c.x], f1 = fv[c.y], f2 = fv[c.z], f3 = fv[c.w];
       if (MODE == MODE_COLL) {
         const double2 a0 = __ldcs(A2 + 2 * q), a1 = __ldcs(A2 + 2 * q + 1);
         A = fma(f0, a0.x, A); A = fma(f1, a0.y, A); A = fma(f2, a1.x, A); A = fma(f3, a1.y, A);
@@ -337,11 +353,33 @@ __global__ void __launch_bounds__(kBlock) k_stream_literal(const Item *__restric
   }
 }
 
-// Transport: stream W (float-float, c folded in) and the packed index; gather F[p][0..2]
-// (float-float, [ns][3]) and accumulate the three field directions in one pass.
+// Transport: stream W (float-float, c folded in) and the partner index; gather F[p][0..2]
+// (float-float, [ns][3]) from shared memory (SMEM) or through L1 (__ldg), and accumulate the
+// three field directions in one pass, two 4-channel groups per lane per trip.
 template <bool SMEM>
+__device__ __forceinline__ float2 ldF(const float2 *__restrict__ F, unsigned i) {
+  if (SMEM) return F[i];
+  return __ldg(F + i);
+}
+
+template <bool SMEM>
+__device__ __forceinline__ void tr_group(const float2 *__restrict__ Fv, uint4 c, float4 w0, float4 w1, float &xh,
+                                         float &xl, float &yh, float &yl, float &zh, float &zl) {
+  const unsigned p[4] = {c.x, c.y, c.z, c.w};
+  const float wh[4] = {w0.x, w0.z, w1.x, w1.z};
+  const float wl[4] = {w0.y, w0.w, w1.y, w1.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const unsigned b = 3u * p[k];
+    ff_mac(xh, xl, ldF<SMEM>(Fv, b), wh[k], wl[k]);
+    ff_mac(yh, yl, ldF<SMEM>(Fv, b + 1), wh[k], wl[k]);
+    ff_mac(zh, zl, ldF<SMEM>(Fv, b + 2), wh[k], wl[k]);
+  }
+}
+
+template <bool SMEM, typename IDX>
 __global__ void __launch_bounds__(512) k_stream_tr(const Item *__restrict__ items, int nitems,
-                                                   const float4 *__restrict__ W4, const uint4 *__restrict__ col4,
+                                                   const float4 *__restrict__ W4, const IDX *__restrict__ colp,
                                                    const float2 *__restrict__ Fg, int ns,
                                                    Part4 *__restrict__ part) {
   extern __shared__ float2 Fsm[];
@@ -358,26 +396,330 @@ __global__ void __launch_bounds__(512) k_stream_tr(const Item *__restrict__ item
     const long long g0 = I.start >> 2;
     const int ng = I.len >> 2;
     float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f, zh = 0.f, zl = 0.f;
-    for (int g = lane; g < ng; g += 32) {
-      const long long q = g0 + g;
-      const uint4 c = __ldcs(col4 + q);
-      const float4 w0 = __ldcs(W4 + 2 * q), w1 = __ldcs(W4 + 2 * q + 1);
-      const unsigned p[4] = {c.x & 0xFFFFFFu, c.y & 0xFFFFFFu, c.z & 0xFFFFFFu, c.w & 0xFFFFFFu};
-      const float wh[4] = {w0.x, w0.z, w1.x, w1.z};
-      const float wl[4] = {w0.y, w0.w, w1.y, w1.w};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float2 *F = Fv + 3 * p[k];
-        ff_mac(xh, xl, F[0], wh[k], wl[k]);
-        ff_mac(yh, yl, F[1], wh[k], wl[k]);
-        ff_mac(zh, zl, F[2], wh[k], wl[k]);
-      }
+    int g = lane;
+    for (; g + 32 < ng; g += 64) {
+      const long long q0 = g0 + g, q1 = q0 + 32;
+      const uint4 c0 = partners4(colp, q0), c1 = partners4(colp, q1);
+      const float4 a0 = __ldcs(W4 + 2 * q0), a1 = __ldcs(W4 + 2 * q0 + 1);
+      const float4 b0 = __ldcs(W4 + 2 * q1), b1 = __ldcs(W4 + 2 * q1 + 1);
+      tr_group<SMEM>(Fv, c0, a0, a1, xh, xl, yh, yl, zh, zl);
+      tr_group<SMEM>(Fv, c1, b0, b1, xh, xl, yh, yl, zh, zl);
+    }
+    if (g < ng) {
+      const long long q0 = g0 + g;
+      const uint4 c0 = partners4(colp, q0);
+      tr_group<SMEM>(Fv, c0, __ldcs(W4 + 2 * q0), __ldcs(W4 + 2 * q0 + 1), xh, xl, yh, yl, zh, zl);
     }
     const double X = warp_sum(ff_to_double(xh, xl));
     const double Y = warp_sum(ff_to_double(yh, yl));
     const double Z = warp_sum(ff_to_double(zh, zl));
     if (lane == 0) part[it] = make_part4(X, Y, Z, 0.0);
   }
+}
+
+// ------------------------------------------------------------ mixed precision (FP32 / BF16 |g|^2)
+//
+// The literal per-channel form of Eq. 2 in FP32: stream |g|^2 (FP32 or BF16) and the packed
+// (partner, branch) word; gather the partner's record (energy as a float-float pair,
+// occupation in FP32, padded grid index) from shared memory and (hbar w hi, hbar w lo, N)
+// from an FP32 table in L2; evaluate the two Gaussians with ex2 and F_abs / F_em in
+// registers; accumulate each lane with Kahan compensation.  Partials, finalisers, RK4 and
+// transport stay FP64.
+//
+// Phonon table index without a modulo: the table is laid out on a padded grid of radix
+// R_i = 2 N_i (R_i = 1 when N_i = 1), indexed by D_i = j_p,i - j_s,i + N_i in [1, 2 N_i).
+// With L(k) = (j1 R2 + j2) R3 + j3 the index is L(k_p) - L(k_s) + L(N1, N2, N3), so each
+// state carries L(k) * nmodes and a channel needs two integer adds.  The Gaussian
+// normalisation 1/(sqrt(2 pi) sigma) is applied once by the finaliser.
+
+struct GGeom {
+  const uint32_t *col;
+  const float4 *tabp;  // padded [R1 R2 R3][nmodes] (w hi, w lo, N, 0)
+  int cpad;            // L(N1, N2, N3) * nmodes
+  float k2;            // -log2(e) / (2 sigma^2)
+};
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ void kahan_add(float &sum, float &comp, float t) {
+  const float y = __fsub_rn(t, comp);
+  const float s2 = __fadd_rn(sum, y);
+  comp = __fsub_rn(__fsub_rn(s2, sum), y);
+  sum = s2;
+}
+
+// One channel: g2 * [G_a F_abs + G_e F_em] (MODE_COLL) or g2 * [G_a (N+f_p) + G_e (N+1-f_p)]
+// without the Gaussian normalisation.  ss/sp: row and partner records; base = cpad - L_s nm.
+template <int MODE>
+__device__ __forceinline__ float g_term(const GGeom &g, uint4 ss, uint4 sp, uint32_t cw, int base, float g2) {
+  const float4 t = __ldg(g.tabp + (base + (int)sp.w + (int)(cw >> 24)));
+  const float dh = __fsub_rn(__uint_as_float(ss.x), __uint_as_float(sp.x));
+  const float dl = __fsub_rn(__uint_as_float(ss.y), __uint_as_float(sp.y));
+  const float a = (dh + t.x) + (dl + t.y);  // x + w
+  const float e = (dh - t.x) + (dl - t.y);  // x - w
+  const float Ga = ex2_approx(a * a * g.k2);
+  const float Ge = ex2_approx(e * e * g.k2);
+  const float fs = __uint_as_float(ss.z), fp = __uint_as_float(sp.z), N = t.z;
+  if (MODE == MODE_COLL) {
+    // F_abs = (f_s - f_p) N - B,  F_em = (f_s - f_p) N + A,  A = f_s (1-f_p), B = (1-f_s) f_p
+    const float P = fs * fp;
+    const float A = fs - P, B = fp - P;
+    const float DN = (fs - fp) * N;
+    float u = (Ga + Ge) * DN;
+    u = fmaf(Ge, A, u);
+    u = fmaf(-Ga, B, u);
+    return g2 * u;
+  }
+  return g2 * fmaf(Ga - Ge, fp, (Ga + Ge) * N + Ge);
+}
+
+// four consecutive |g|^2 values as FP32 (a 16-byte FP32 load or an 8-byte BF16 load)
+template <typename G2T>
+__device__ __forceinline__ float4 load_g2x4(const G2T *__restrict__ g2v, long long q) {
+  if (sizeof(G2T) == 4) return __ldcs((const float4 *)g2v + q);
+  const uint2 v = __ldcs((const uint2 *)g2v + q);
+  return make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xFFFF0000u), __uint_as_float(v.y << 16),
+                     __uint_as_float(v.y & 0xFFFF0000u));
+}
+
+// part[item].x = sum over the item of the channel terms above.
+template <int MODE, typename G2T>
+__global__ void __launch_bounds__(512) k_stream_g(const Item *__restrict__ items, int nitems, GGeom g,
+                                                  const G2T *__restrict__ g2v, const uint4 *__restrict__ gstate,
+                                                  int ns, Part4 *__restrict__ part) {
+  extern __shared__ uint4 gs[];
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) gs[i] = gstate[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint4 *__restrict__ col4 = (const uint4 *)g.col;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    const uint4 ss = gs[I.row];
+    const int base = g.cpad - (int)ss.w;
+    const long long g0 = I.start >> 2;
+    const int ng = I.len >> 2;
+    float sum = 0.f, comp = 0.f;
+    // software pipeline: the next group's stream words are in flight while this group's
+    // partner records and phonon-table entries are gathered and evaluated
+    uint4 c = make_uint4(0u, 0u, 0u, 0u);
+    float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lane < ng) {
+      c = __ldcs(col4 + g0 + lane);
+      gv = load_g2x4(g2v, g0 + lane);
+    }
+    for (int q = lane; q < ng; q += 32) {
+      uint4 cn = make_uint4(0u, 0u, 0u, 0u);
+      float4 gn = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (q + 32 < ng) {
+        cn = __ldcs(col4 + g0 + q + 32);
+        gn = load_g2x4(g2v, g0 + q + 32);
+      }
+      const float t0 = g_term<MODE>(g, ss, gs[c.x & 0xFFFFFFu], c.x, base, gv.x);
+      const float t1 = g_term<MODE>(g, ss, gs[c.y & 0xFFFFFFu], c.y, base, gv.y);
+      const float t2 = g_term<MODE>(g, ss, gs[c.z & 0xFFFFFFu], c.z, base, gv.z);
+      const float t3 = g_term<MODE>(g, ss, gs[c.w & 0xFFFFFFu], c.w, base, gv.w);
+      kahan_add(sum, comp, t0);
+      kahan_add(sum, comp, t1);
+      kahan_add(sum, comp, t2);
+      kahan_add(sum, comp, t3);
+      c = cn;
+      gv = gn;
+    }
+    const double v = warp_sum((double)sum - (double)comp);
+    if (lane == 0) part[it] = make_part4(v, 0.0, 0.0, 0.0);
+  }
+}
+
+// |g|^2 in the storage type of the mixed-precision variants (round to nearest)
+template <typename G2T>
+__global__ void k_cvt_g2(const double *__restrict__ g2, long long n, G2T *__restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (sizeof(G2T) == 4)
+      ((float *)out)[i] = __double2float_rn(g2[i]);
+    else
+      ((__nv_bfloat16 *)out)[i] = __double2bfloat16(g2[i]);
+  }
+}
+
+// Per-state records of the mixed-precision sweep: eps as a float-float pair, padded grid
+// index times nmodes.
+__global__ void k_gstate_init(const double *__restrict__ eps, const short4 *__restrict__ kc, int n, int R2, int R3,
+                              int nmodes, uint4 *__restrict__ gstate) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float2 e = ff_split(eps[i]);
+  const short4 k = kc[i];
+  const int L = ((int)k.x * R2 + (int)k.y) * R3 + (int)k.z;
+  gstate[i] = make_uint4(__float_as_uint(e.x), __float_as_uint(e.y), 0u, (unsigned)(L * nmodes));
+}
+
+// Padded phonon table: entry (D1, D2, D3, nu) holds q = (D_i - N_i) mod N_i.
+__global__ void k_tab_padded(const double2 *__restrict__ tab, int N1, int N2, int N3, int R1, int R2, int R3,
+                             int nmodes, float4 *__restrict__ out) {
+  const long long n = (long long)R1 * R2 * R3 * nmodes;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int nu = (int)(i % nmodes);
+    long long r = i / nmodes;
+    const int D3 = (int)(r % R3);
+    r /= R3;
+    const int D2 = (int)(r % R2);
+    const int D1 = (int)(r / R2);
+    const int q1 = ((D1 - (R1 > 1 ? N1 : 0)) % N1 + N1) % N1;
+    const int q2 = ((D2 - (R2 > 1 ? N2 : 0)) % N2 + N2) % N2;
+    const int q3 = ((D3 - (R3 > 1 ? N3 : 0)) % N3 + N3) % N3;
+    const double2 wN = tab[((long long)(q1 * N2 + q2) * N3 + q3) * nmodes + nu];
+    const float wh = __double2float_rn(wN.x);
+    out[i] = make_float4(wh, __double2float_rn(wN.x - (double)wh), __double2float_rn(wN.y), 0.f);
+  }
+}
+
+// gstate.z = (float) f  (the stage input of the mixed-precision sweep)
+__global__ void k_gstate_f(const double *__restrict__ f, int n, uint4 *__restrict__ gstate) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) ((float *)gstate)[4 * i + 2] = __double2float_rn(f[i]);
+}
+
+// ------------------------------------------------------------ adjoint (reverse mode)
+//
+// VJP of the collision integral.  With I_s = c sum_{row s} [f_p P_in + f_s f_p D - f_s P_out]
+// and the reverse channel of every channel in the list (P_in <-> P_out, D -> -D), the
+// transposed sum over the channels whose partner is x becomes a sum over row x itself:
+//   (J^T lam)_x = c [ sum_{row x} lam_p (P_in + (1 - f_p) D) + lam_x (B_x - R_x) ],
+//   B_x = sum_{row x} f_p D.
+// So the adjoint is another segmented gather over the same stream: no scatter, no atomics.
+
+// G[3i] = lam_i, G[3i+1] = lam_i f_i, G[3i+2] = f_i as float-float pairs
+__global__ void k_vjp_prep(const double *__restrict__ f, const double *__restrict__ lam, int n,
+                           float2 *__restrict__ G) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  G[3 * i] = ff_split(lam[i]);
+  G[3 * i + 1] = ff_split(lam[i] * f[i]);
+  G[3 * i + 2] = ff_split(f[i]);
+}
+
+// part[item] = (sum lam_p P_in, sum lam_p D, sum lam_p f_p D, sum f_p D)
+template <bool SMEM, typename IDX>
+__global__ void __launch_bounds__(kBlock) k_stream_vjp(const Item *__restrict__ items, int nitems,
+                                                       const float4 *__restrict__ A4, const float4 *__restrict__ B4,
+                                                       const IDX *__restrict__ colp, const float2 *__restrict__ Gg,
+                                                       int ns, Part4 *__restrict__ part) {
+  extern __shared__ float2 Gsm[];
+  if (SMEM) {
+    for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) Gsm[i] = Gg[i];
+    __syncthreads();
+  }
+  const float2 *__restrict__ Gv = SMEM ? Gsm : Gg;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    const long long g0 = I.start >> 2;
+    const int ng = I.len >> 2;
+    float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f, h3 = 0.f, l3 = 0.f, h4 = 0.f, l4 = 0.f;
+    for (int g = lane; g < ng; g += 32) {
+      const long long q = g0 + g;
+      const uint4 c = partners4(colp, q);
+      const float4 a0 = __ldcs(A4 + 2 * q), a1 = __ldcs(A4 + 2 * q + 1);
+      const float4 b0 = __ldcs(B4 + 2 * q), b1 = __ldcs(B4 + 2 * q + 1);
+      const unsigned p[4] = {c.x, c.y, c.z, c.w};
+      const float ah[4] = {a0.x, a0.z, a1.x, a1.z}, al[4] = {a0.y, a0.w, a1.y, a1.w};
+      const float bh[4] = {b0.x, b0.z, b1.x, b1.z}, bl[4] = {b0.y, b0.w, b1.y, b1.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 lp = Gv[3 * p[k]], mp = Gv[3 * p[k] + 1], fp = Gv[3 * p[k] + 2];
+        ff_mac(h1, l1, lp, ah[k], al[k]);
+        ff_mac(h2, l2, lp, bh[k], bl[k]);
+        ff_mac(h3, l3, mp, bh[k], bl[k]);
+        ff_mac(h4, l4, fp, bh[k], bl[k]);
+      }
+    }
+    const double S1 = warp_sum(ff_to_double(h1, l1)), S2 = warp_sum(ff_to_double(h2, l2));
+    const double S3 = warp_sum(ff_to_double(h3, l3)), S4 = warp_sum(ff_to_double(h4, l4));
+    if (lane == 0) part[it] = make_part4(S1, S2, S3, S4);
+  }
+}
+
+__global__ void k_fin_vjp(const int *__restrict__ item_ptr, const Part4 *__restrict__ part, int ns, double c,
+                          const double *__restrict__ R, const double *__restrict__ lam, double *__restrict__ out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= ns) return;
+  double S1 = 0.0, S2 = 0.0, S3 = 0.0, S4 = 0.0;
+  for (int i = item_ptr[r]; i < item_ptr[r + 1]; ++i) {
+    const Part4 v = part[i];
+    S1 += v.x;
+    S2 += v.y;
+    S3 += v.z;
+    S4 += v.w;
+  }
+  out[r] = c * ((S1 + S2 - S3) + lam[r] * (S4 - R[r]));
+}
+
+// grad_g2[c] += -c lam_s [G_a F_abs + G_e F_em] for every stored channel c (CSR order without
+// padding); the bracket is (f_s (1-f_p) P_out - (1-f_s) f_p P_in) / g2, P_out = P_in + D.
+template <typename IDX>
+__global__ void __launch_bounds__(kBlock) k_g2grad(const Item *__restrict__ items, int nitems,
+                                                   const long long *__restrict__ rp_pad,
+                                                   const long long *__restrict__ rp_real,
+                                                   const float2 *__restrict__ A, const float2 *__restrict__ B,
+                                                   const IDX *__restrict__ colp, const double *__restrict__ g2,
+                                                   const double *__restrict__ f, const double *__restrict__ lam,
+                                                   double c, double *__restrict__ grad) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    const int r = I.row;
+    const long long off = I.start - rp_pad[r];
+    const long long real_len = rp_real[r + 1] - rp_real[r];
+    const double fs = f[r], ls = lam[r];
+    for (int j = lane; j < I.len; j += 32) {
+      const long long k = off + j;
+      if (k >= real_len) continue;
+      const long long cpos = I.start + j;
+      const double gv = g2[cpos];
+      if (!(gv > 0.0)) continue;
+      const unsigned p = (unsigned)colp[cpos] & 0xFFFFFFu;
+      const double fp = f[p];
+      const double pin = ff_to_double(A[cpos].x, A[cpos].y);
+      const double dd = ff_to_double(B[cpos].x, B[cpos].y);
+      const double t = fs * (1.0 - fp) * (pin + dd) - (1.0 - fs) * fp * pin;
+      grad[rp_real[r] + k] += -c * ls * t / gv;
+    }
+  }
+}
+
+// padded g2 from the unpadded CSR order (padding stays zero)
+__global__ void k_set_g2(const Item *__restrict__ items, int nitems, const long long *__restrict__ rp_pad,
+                         const long long *__restrict__ rp_real, const double *__restrict__ in,
+                         double *__restrict__ g2) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    const long long off = I.start - rp_pad[I.row];
+    const long long real_len = rp_real[I.row + 1] - rp_real[I.row];
+    for (int j = lane; j < I.len; j += 32) {
+      const long long k = off + j;
+      g2[I.start + j] = k < real_len ? in[rp_real[I.row] + k] : 0.0;
+    }
+  }
+}
+
+// out = a x + b y (y may be null)
+__global__ void k_lincomb(int n, double a, const double *__restrict__ x, double b, const double *__restrict__ y,
+                          double *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a * x[i] + (y ? b * y[i] : 0.0);
 }
 
 // ------------------------------------------------------------ finalisers
@@ -397,7 +739,7 @@ __device__ __forceinline__ void row_partials(const int *__restrict__ item_ptr, c
 // Collision epilogue fused with the RK4 stage arithmetic.
 //   STAGE < 0 : out[r] = I_r (plain pb_collision)
 //   STAGE 0..3: classic RK4 stage k_{STAGE+1} = I[y]; see the host driver for buffers.
-template <bool LIT, int STAGE>
+template <bool LIT, int STAGE, bool GSTATE = false>
 __global__ void k_fin_coll(const int *__restrict__ item_ptr, const Part4 *__restrict__ part, int ns, double c,
                            const double *__restrict__ R, const double *__restrict__ ysrc, double *__restrict__ out,
                            double *__restrict__ f, double *__restrict__ acc, double *__restrict__ y,
@@ -427,7 +769,10 @@ __global__ void k_fin_coll(const int *__restrict__ item_ptr, const Part4 *__rest
     f[r] = yn;
   }
   y[r] = yn;
-  yff[r] = ff_split(yn);
+  if (GSTATE)
+    ((float *)yff)[4 * r + 2] = __double2float_rn(yn);  // yff points at the uint4 gstate array
+  else
+    yff[r] = ff_split(yn);
 }
 
 template <bool LIT>

@@ -259,6 +259,32 @@ def make_two_level(n: int = 3, e0: float = 0.0, w0: float = 0.05, g2: float = 2e
                  g2_sigma_ln=0.0, seed=seed)
 
 
+_BAND_OFFSETS = [0.0, 0.2, 1.1, 1.3]
+
+
+def make_batch_instance(i: int, seed: int = 20251107) -> tuple:
+    """Instance i of the batched workload: grid N^3 with N uniform in 16..36, 2-4 bands
+    (offsets from 0/0.2/1.1/1.3 eV), 3-6 modes (acoustic 15/20/25 meV x s(q), then optical
+    flat 35/47.5/60 meV), T uniform in 100..500 K, per-band 0.3 eV window, sigma 8 meV.
+    Returns (model, excitation energy in eV, uniform in 0.1..0.5)."""
+    rng = np.random.default_rng([seed, i])
+    n = int(rng.integers(16, 37))
+    nb = int(rng.integers(2, 5))
+    nm = int(rng.integers(3, 7))
+    T = float(rng.uniform(100.0, 500.0))
+    e_exc = float(rng.uniform(0.1, 0.5))
+    nk = (n, n, n)
+    offsets = _BAND_OFFSETS[:nb]
+    eps, vel = tight_binding(nk, offsets)
+    s = acoustic_shape(nk)
+    branches = [15e-3 * s, 20e-3 * s, 25e-3 * s, np.full_like(s, 35e-3), np.full_like(s, 47.5e-3),
+                np.full_like(s, 60e-3)]
+    omega = np.stack(branches[:nm], axis=1)
+    win = np.array([[e - 1.0, e + 0.3] for e in offsets])
+    m = Model(f"batch{i}_{n}", nk, nb, nm, eps, vel, omega, win, T, 0.008, seed=seed * 1000 + i)
+    return m, e_exc
+
+
 def make_config(name: str) -> Model:
     """Named workloads: 'tiny' (8^3, ~3.1M channels), 'window40' (40^3, ~1.36e8 channels),
     'window24' (24^3, ~6.3e6 channels), and 'window<N>' for the same rule on an N^3 grid."""

@@ -1,0 +1,132 @@
+"""GPU adjoint (NEXT-3): collision VJP, per-channel |g|^2 gradients and RK4 trajectory
+gradients, against the FP64 oracle's reverse mode and against central finite differences
+of the GPU forward map (h = 1e-6, random directions)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pb():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2511_03683_gb300 as pb
+    import torch
+
+    assert torch.cuda.is_available()
+    return pb
+
+
+def T(x):
+    import torch
+
+    return torch.tensor(np.ascontiguousarray(x, dtype=np.float64), device="cuda")
+
+
+def nrel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.mark.parametrize("model", [synth.make_tiny(4), synth.make_window4(12), synth.make_config("tiny")],
+                         ids=["tiny4", "win12", "tiny8"])
+def test_collision_vjp_matches_oracle(pb, model):
+    import torch
+
+    ch = pb.Channels.from_model(model)
+    dev = pb.Device(ch)
+    o = oracle.Oracle(model)
+    rng = np.random.default_rng(3)
+    f = rng.uniform(0, 1, o.nstate)
+    lam = rng.normal(size=o.nstate)
+    gg2 = torch.zeros(dev.nchannels, dtype=torch.float64, device="cuda")
+    g = dev.collision_vjp(T(f), T(lam), grad_g2=gg2).cpu().numpy()
+    assert nrel(g, o.collision_vjp(f, lam)) <= 1e-11
+    e = ch.export()
+    rows = np.repeat(np.arange(ch.nstate), np.diff(e["row_ptr"]))
+    pick = rng.choice(ch.nchannels, size=min(300, ch.nchannels), replace=False)
+    ref = o.g2_grad(f, lam, rows[pick], e["col"][pick], e["nu"][pick])
+    got = gg2.cpu().numpy()[pick]
+    assert nrel(got, ref) <= 1e-11
+
+
+def test_rk4_step_adjoint_matches_oracle(pb):
+    m = synth.make_config("tiny")
+    dev = pb.Device(pb.Channels.from_model(m))
+    o = oracle.Oracle(m)
+    f0 = o.window_values(m.f_hot())
+    eps = o.window_values(m.eps)
+    lam = T(eps)
+    dev.rk4_vjp(T(f0), lam, 1.0)
+    assert nrel(lam.cpu().numpy(), o.rk4_vjp(f0, 1.0, 1, eps)) <= 1e-11
+
+
+def _carrier_energy_grad(pb, model, nsteps, every):
+    import torch
+    from paper_2511_03683_gb300 import autograd as pa
+
+    ch = pb.Channels.from_model(model)
+    dev = pb.Device(ch)
+    ids = ch.state_ids()
+    f0 = torch.tensor(model.f_hot().reshape(-1)[ids], device="cuda", requires_grad=True)
+    eps = torch.tensor(model.eps.reshape(-1)[ids], device="cuda")
+    g2 = pa.g2_tensor(ch).requires_grad_(True)
+    L = (eps * pa.trajectory(dev, f0, g2, 1.0, nsteps, every)).sum()
+    L.backward()
+    return ch, dev, f0, eps, g2, L
+
+
+def test_trajectory_gradient_matches_oracle_adjoint(pb):
+    """Short trajectory on the 8^3 workload: autograd gradient w.r.t. f0 == oracle adjoint."""
+    m = synth.make_config("tiny")
+    ch, dev, f0, eps, g2, L = _carrier_energy_grad(pb, m, nsteps=6, every=4)
+    o = oracle.Oracle(m)
+    ref = o.rk4_vjp(o.window_values(m.f_hot()), 1.0, 6, o.window_values(m.eps))
+    assert nrel(f0.grad.cpu().numpy(), ref) <= 1e-10
+
+
+def test_trajectory_gradient_finite_differences_24cubed(pb):
+    """The adjoint workload: 24^3 grids, 4 bands, 6 modes, loss = carrier energy after
+    200 RK4 steps of 1 fs, checkpoints every 20 steps; 50 random directions in f0 and 5 in
+    |g|^2, central differences with h = 1e-6."""
+    import torch
+
+    m = synth.make_config("window24")
+    ch, dev, f0, eps, g2, L = _carrier_energy_grad(pb, m, nsteps=200, every=20)
+    gf = f0.grad.detach()
+    gg = g2.grad.detach()
+    rng = np.random.default_rng(24)
+    h = 1e-6
+
+    fbuf = torch.empty_like(f0.detach())
+
+    def loss(f_init):
+        fbuf.copy_(f_init)  # one buffer: the RK4 graph is captured once
+        dev.rk4(fbuf, 1.0, 200)
+        return float((eps * fbuf).sum())
+
+    base = f0.detach()
+    worst = 0.0
+    for _ in range(50):
+        d = torch.tensor(rng.normal(size=dev.nstate), device="cuda") * base.abs().max()
+        fd = (loss(base + h * d) - loss(base - h * d)) / (2 * h)
+        an = float((gf * d).sum())
+        worst = max(worst, abs(an - fd) / max(abs(fd), 1e-30))
+    assert worst <= 1e-6, worst
+    g2v = g2.detach().clone()
+    worst = 0.0
+    for _ in range(5):
+        d = torch.tensor(rng.normal(size=dev.nchannels), device="cuda") * g2v
+        vals = []
+        for sgn in (1.0, -1.0):
+            dev.set_g2(g2v + sgn * h * d)
+            vals.append(loss(base))
+        dev.set_g2(g2v)
+        fd = (vals[0] - vals[1]) / (2 * h)
+        an = float((gg * d).sum())
+        worst = max(worst, abs(an - fd) / max(abs(fd), 1e-30))
+    assert worst <= 1e-6, worst

@@ -1,0 +1,85 @@
+"""Batched rt-BTE (NEXT-2): many instances of the batched workload in one launch per stage,
+against the unbatched FP32 device and the FP64 oracle of each instance."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pb():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2511_03683_gb300 as pb
+    import torch
+
+    assert torch.cuda.is_available()
+    return pb
+
+
+def small_instances(k=10):
+    """The k smallest-grid instances among the first 40 of the batched workload (fast oracle)."""
+    inst = [synth.make_batch_instance(i) for i in range(40)]
+    inst.sort(key=lambda t: np.prod(t[0].nk) * t[0].nbands)
+    return inst[:k]
+
+
+@pytest.fixture(scope="module")
+def batch(pb):
+    import torch
+
+    inst = small_instances()
+    chs = [pb.Channels.from_model(m) for m, _ in inst]
+    b = pb.Batch(chs)
+    f = np.concatenate([m.f_hot(e_exc=e).reshape(-1)[c.state_ids()] for (m, e), c in zip(inst, chs)])
+    return inst, chs, b, f
+
+
+def test_batch_collision_matches_unbatched_and_oracle(pb, batch):
+    import torch
+
+    inst, chs, b, f = batch
+    assert b.nstate == sum(c.nstate for c in chs) and b.nchannels == sum(c.nchannels for c in chs)
+    rng = np.random.default_rng(9)
+    fr = rng.uniform(0, 1, b.nstate)
+    I = b.collision(torch.tensor(fr, device="cuda")).cpu().numpy()
+    for i, ((m, _), ch) in enumerate(zip(inst, chs)):
+        a, e = b.offsets[i], b.offsets[i + 1]
+        dev = pb.Device(ch, variant="g32")
+        ref32 = dev.collision(torch.tensor(fr[a:e], device="cuda")).cpu().numpy()
+        assert np.abs(I[a:e] - ref32).max() <= 1e-6 * np.abs(ref32).max()
+        o = oracle.Oracle(m)
+        ref, ab = o.collision(fr[a:e], with_abs=True)
+        d = np.abs(I[a:e] - ref).max()
+        assert d <= 1e-6 * ab.max()
+        if np.abs(ref).max() >= 1e-2 * ab.max():
+            assert d <= 1e-6 * np.abs(ref).max()
+
+
+def test_batch_rk4_matches_oracle(pb, batch):
+    import torch
+
+    inst, chs, b, f = batch
+    ft = torch.tensor(f, device="cuda")
+    b.rk4(ft, 1.0, 5)
+    got = ft.cpu().numpy()
+    for i, ((m, _), ch) in enumerate(zip(inst[:4], chs[:4])):
+        a, e = b.offsets[i], b.offsets[i + 1]
+        ref = oracle.Oracle(m).rk4(f[a:e], 1.0, 5)
+        assert np.abs(got[a:e] - ref).max() <= 1e-6 * np.abs(ref).max()
+
+
+def test_batch_autotune_keeps_results(pb, batch):
+    import torch
+
+    inst, chs, b, f = batch
+    ft = torch.tensor(f, device="cuda")
+    before = b.collision(ft).cpu().numpy()
+    item, ctas, ms = b.autotune(ft)
+    assert item in (1024, 2048, 4096) and ctas in (2, 3, 4) and ms > 0
+    after = b.collision(ft).cpu().numpy()
+    assert np.abs(after - before).max() <= 1e-6 * np.abs(before).max()
