@@ -90,6 +90,8 @@ typedef struct pb_build_opts {
   int32_t check_closure;        /* nonzero: verify every channel's reverse exists with equal g2 */
   int32_t reserved;
   double g2_min;                /* drop channels with g2 < g2_min (the paper's |g| cutoff); 0 keeps all */
+  double delta_nsigma;          /* drop channels with min(|x+w|, |x-w|) > delta_nsigma * sigma, x = eps_s -
+                                   eps_p (the paper's approximate energy conservation); 0 keeps all */
 } pb_build_opts;
 
 typedef struct pb_channels pb_channels; /* opaque host CSR, library-owned */

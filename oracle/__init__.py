@@ -46,6 +46,8 @@ class OrModel(ctypes.Structure):
         ("sigma", ctypes.c_double),
         ("g2", ctypes.c_void_p),
         ("g2_user", ctypes.c_void_p),
+        ("g2_min", ctypes.c_double),
+        ("delta_nsigma", ctypes.c_double),
     ]
 
 
@@ -104,7 +106,7 @@ class Oracle:
     """Bind one synth.Model to the C oracle.  Arrays passed in and out are over the
     window states in ascending full-grid id order (see ``window_ids``)."""
 
-    def __init__(self, model, nthreads: int = 0, plant: int = 0):
+    def __init__(self, model, nthreads: int = 0, plant: int = 0, g2_min: float = 0.0, delta_nsigma: float = 0.0):
         self.model = model
         self._L = lib(plant)
         self._eps = _f64(model.eps)
@@ -123,6 +125,8 @@ class Oracle:
         m.sigma = float(model.sigma)
         m.g2 = model.g2_fn_ptr()
         m.g2_user = model.g2_user_ptr()
+        m.g2_min = float(g2_min)
+        m.delta_nsigma = float(delta_nsigma)
         self._m = m
         n = self._L.oracle_window(ctypes.byref(m), None)
         ids = np.empty(max(n, 1), dtype=np.int32)

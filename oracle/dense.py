@@ -15,7 +15,7 @@ KB_EVK = 8.617333262e-5
 
 
 class Dense:
-    def __init__(self, model):
+    def __init__(self, model, g2_min: float = 0.0, delta_nsigma: float = 0.0):
         self.model = model
         nb, nm = model.nbands, model.nmodes
         N1, N2, N3 = model.nk
@@ -42,7 +42,15 @@ class Dense:
         self.Ga = norm * np.exp(-((x[..., None] + self.w) ** 2) / (2 * sig * sig))
         self.Ge = norm * np.exp(-((x[..., None] - self.w) ** 2) / (2 * sig * sig))
         self.c = 2.0 * np.pi / (HBAR_EVFS * N1 * N2 * N3)
-        self.nchannels = int(self.valid.sum())
+        keep = self.valid.copy()
+        if g2_min > 0.0:
+            keep &= self.g2 >= g2_min
+        if delta_nsigma > 0.0:
+            lim = delta_nsigma * sig
+            keep &= ~((np.abs(x[..., None] + self.w) > lim) & (np.abs(x[..., None] - self.w) > lim))
+        self.g2 = np.where(keep, self.g2, 0.0)
+        self.valid = keep
+        self.nchannels = int(keep.sum())
 
     @property
     def nstate(self) -> int:

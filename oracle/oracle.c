@@ -73,7 +73,21 @@ typedef struct {
   double sigma;         /* eV */
   or_g2_fn g2;          /* |g|^2 in eV^2 of the channel (s_full -> p_full, nu) */
   const void *g2_user;
+  double g2_min;        /* drop channels with |g|^2 < g2_min (0: keep all) */
+  double delta_nsigma;  /* drop channels with min(|x+w|, |x-w|) > delta_nsigma * sigma (0: keep all) */
 } or_model;
+
+/* The paper prunes channels by a |g| cutoff and by approximate energy conservation (Sec.
+ * "Collision integral, e-ph coupling matrix, and scattering channels"); both are optional
+ * here and off by default.  A channel is kept when both tests pass. */
+static int keep_channel(const or_model *m, double g2, double x, double w) {
+  if (m->g2_min > 0.0 && g2 < m->g2_min) return 0;
+  if (m->delta_nsigma > 0.0) {
+    const double lim = m->delta_nsigma * m->sigma;
+    if (fabs(x + w) > lim && fabs(x - w) > lim) return 0;
+  }
+  return 1;
+}
 
 static int64_t nk_total(const or_model *m) { return (int64_t)m->nk[0] * m->nk[1] * m->nk[2]; }
 
@@ -153,6 +167,7 @@ static double row_sum(const or_model *m, const int32_t *widx, int64_t sid, const
         if (!(w > 0.0)) continue;
         const double N = bose(w, m->T);
         const double g2 = m->g2((int32_t)sid, (int32_t)pid, nu, m->g2_user);
+        if (!keep_channel(m, g2, x, w)) continue;
 #if ORACLE_PLANT == 3
         const double Ga = gauss(x - w, m->sigma); /* planted: deltas swapped */
         const double Ge = gauss(x + w, m->sigma);
@@ -357,6 +372,20 @@ int64_t oracle_count_channels(const or_model *m) {
     for (int64_t iq = 0; iq < Nq; ++iq) {
       int32_t q1 = (int32_t)(iq / ((int64_t)N2 * N3)), q2 = (int32_t)((iq / N3) % N2), q3 = (int32_t)(iq % N3);
       int64_t ikq = ((int64_t)((j1 + q1) % N1) * N2 + (j2 + q2) % N2) * N3 + (j3 + q3) % N3;
+      if (m->g2_min > 0.0 || m->delta_nsigma > 0.0) {
+        for (int32_t mb = 0; mb < nb; ++mb) {
+          const int64_t pid = ikq * nb + mb;
+          if (widx[pid] < 0) continue;
+          const double x = m->eps[ids[r]] - m->eps[pid];
+          for (int32_t nu = 0; nu < nm; ++nu) {
+            const double w = m->omega[iq * nm + nu];
+            if (!(w > 0.0)) continue;
+            const double g2 = m->g2 ? m->g2(ids[r], (int32_t)pid, nu, m->g2_user) : 0.0;
+            total += keep_channel(m, g2, x, w);
+          }
+        }
+        continue;
+      }
       int nmw = 0;
       for (int32_t nu = 0; nu < nm; ++nu) nmw += m->omega[iq * nm + nu] > 0.0;
       for (int32_t mb = 0; mb < nb; ++mb)
@@ -417,6 +446,7 @@ int oracle_collision_vjp(const or_model *m, const double *f, const double *lam, 
           if (!(w > 0.0)) continue;
           const double N = bose(w, m->T);
           const double g2 = m->g2((int32_t)sid, (int32_t)pid, nu, m->g2_user);
+          if (!keep_channel(m, g2, x, w)) continue;
           const double Ga = gauss(x + w, m->sigma), Ge = gauss(x - w, m->sigma);
           const double dts = g2 * (Ga * ((1.0 - f_p) * N + f_p * (N + 1.0)) + Ge * ((1.0 - f_p) * (N + 1.0) + f_p * N));
           const double dtp = g2 * (Ga * (-f_s * N - (1.0 - f_s) * (N + 1.0)) + Ge * (-f_s * (N + 1.0) - (1.0 - f_s) * N));

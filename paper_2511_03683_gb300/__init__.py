@@ -41,7 +41,8 @@ class _Model(ctypes.Structure):
 
 class _BuildOpts(ctypes.Structure):
     _fields_ = [("nthreads", ctypes.c_int32), ("callback_threadsafe", ctypes.c_int32),
-                ("check_closure", ctypes.c_int32), ("reserved", ctypes.c_int32), ("g2_min", ctypes.c_double)]
+                ("check_closure", ctypes.c_int32), ("reserved", ctypes.c_int32), ("g2_min", ctypes.c_double),
+                ("delta_nsigma", ctypes.c_double)]
 
 
 class _ChInfo(ctypes.Structure):
@@ -172,7 +173,7 @@ class Channels:
 
     @classmethod
     def build(cls, nk, nbands, nmodes, eps, omega, T, sigma, g2, g2_user=None, vel=None, win=None,
-              nthreads=0, threadsafe=True, check_closure=True, g2_min=0.0) -> "Channels":
+              nthreads=0, threadsafe=True, check_closure=True, g2_min=0.0, delta_nsigma=0.0) -> "Channels":
         """``g2`` is either the address of a C function with the pb_g2_fn signature (then
         ``g2_user`` is its user pointer) or a Python callable g2(s, p, nu) -> array on
         numpy int32 id arrays (full-grid ids), called one row at a time."""
@@ -187,7 +188,8 @@ class Channels:
         m.vel = None if vel_a is None else vel_a.ctypes.data
         m.win = None if win_a is None else win_a.ctypes.data
         m.T, m.sigma = float(T), float(sigma)
-        o = _BuildOpts(int(nthreads), 1 if threadsafe else 0, 1 if check_closure else 0, 0, float(g2_min))
+        o = _BuildOpts(int(nthreads), 1 if threadsafe else 0, 1 if check_closure else 0, 0, float(g2_min),
+                       float(delta_nsigma))
         keep = []
         if callable(g2):
             pyfn = g2

@@ -80,6 +80,7 @@ extern "C" int pb_build_channels(const pb_model *m, pb_g2_fn g2fn, void *user, c
   if (!(m->T > 0.0) || !(m->sigma > 0.0) || !std::isfinite(m->T) || !std::isfinite(m->sigma))
     return set_error(PB_EINVAL, "pb_build_channels: T and sigma must be positive and finite");
   const double g2_min = opts ? opts->g2_min : 0.0;
+  const double dlim = (opts && opts->delta_nsigma > 0.0) ? opts->delta_nsigma * m->sigma : 0.0;
   const bool check = opts ? opts->check_closure != 0 : true;
   const bool cb_parallel = opts ? opts->callback_threadsafe != 0 : false;
   const int nt = nthreads_of(opts);
@@ -144,13 +145,28 @@ extern "C" int pb_build_channels(const pb_model *m, pb_g2_fn g2fn, void *user, c
       npos[q] = (uint8_t)c;
     }
 
+    // approximate energy conservation (the paper's delta cutoff, optional): keep a channel
+    // unless both Gaussian arguments x + w and x - w lie beyond dlim
+    auto keep_delta = [&](int64_t r, int64_t p, int64_t q, int v) {
+      if (dlim <= 0.0) return true;
+      const double x = ch->eps[r] - ch->eps[p], w = ch->omega[q * nm + v];
+      return !(std::fabs(x + w) > dlim && std::fabs(x - w) > dlim);
+    };
     // row lengths, then the CSR offsets
     std::vector<int64_t> len((size_t)ns);
 #pragma omp parallel for num_threads(nt) schedule(dynamic, 16)
     for (int64_t r = 0; r < ns; ++r) {
       int64_t c = 0;
       const int64_t iks = ch->kidx[r];
-      for (int64_t p = 0; p < ns; ++p) c += npos[q_index(m->nk, iks, ch->kidx[p])];
+      for (int64_t p = 0; p < ns; ++p) {
+        const int64_t q = q_index(m->nk, iks, ch->kidx[p]);
+        if (dlim <= 0.0) {
+          c += npos[q];
+          continue;
+        }
+        for (int v = 0; v < nm; ++v)
+          if (ch->omega[q * nm + v] > 0.0 && keep_delta(r, p, q, v)) ++c;
+      }
       len[r] = c;
     }
     ch->row_ptr.assign(ns + 1, 0);
@@ -167,7 +183,7 @@ extern "C" int pb_build_channels(const pb_model *m, pb_g2_fn g2fn, void *user, c
       for (int64_t p = 0; p < ns; ++p) {
         const int64_t q = q_index(m->nk, iks, ch->kidx[p]);
         for (int v = 0; v < nm; ++v)
-          if (ch->omega[q * nm + v] > 0.0) {
+          if (ch->omega[q * nm + v] > 0.0 && keep_delta(r, p, q, v)) {
             ch->col[c] = (int32_t)p;
             ch->nu[c] = (uint8_t)v;
             ++c;

@@ -115,3 +115,10 @@ def test_acoustic_only_gamma_has_no_channels(pb):
     eps = np.array([[0.0, 0.1]])
     ch = pb.Channels.build((1, 1, 1), 2, 1, eps, np.zeros((1, 1)), 300.0, 0.01, lambda s, p, nu: np.ones(len(s)))
     assert ch.nstate == 2 and ch.nchannels == 0
+
+
+@pytest.mark.parametrize("g2_min,nsig", [(1e-3, 0.0), (0.0, 3.0), (5e-4, 4.0)])
+def test_builder_cutoffs_match_oracle_count(pb, g2_min, nsig):
+    m = synth.make_window4(16)
+    ch = pb.Channels.from_model(m, g2_min=g2_min, delta_nsigma=nsig)
+    assert ch.nchannels == oracle.Oracle(m, g2_min=g2_min, delta_nsigma=nsig).count_channels()

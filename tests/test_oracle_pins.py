@@ -202,3 +202,17 @@ def test_transport_cubic_symmetry():
     diag = np.diag(S)
     assert np.abs(diag - diag.mean()).max() <= 1e-10 * abs(diag.mean())
     assert np.abs(S - np.diag(diag)).max() <= 1e-10 * abs(diag.mean())
+
+
+@pytest.mark.parametrize("g2_min,nsig", [(1e-3, 0.0), (0.0, 3.0), (5e-4, 4.0)])
+def test_cutoffs_loop_matches_dense(g2_min, nsig):
+    """The paper's optional |g| and delta cutoffs: C loop == brute force with the same mask,
+    and the pruned sum stays antisymmetric (conservation)."""
+    m = synth.make_window4(12)
+    o, d = oracle.Oracle(m, g2_min=g2_min, delta_nsigma=nsig), Dense(m, g2_min=g2_min, delta_nsigma=nsig)
+    assert o.count_channels() == d.nchannels < Dense(m).nchannels
+    f = np.random.default_rng(2).uniform(0, 1, o.nstate)
+    assert nrel(o.collision(f), d.collision(f)) < 1e-13
+    assert nrel(o.rates(f), d.rates(f)) < 1e-13
+    I, ab = o.collision(f, with_abs=True)
+    assert abs(I.sum()) <= 1e-13 * ab.sum()
