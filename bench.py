@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--mixed-steps", type=int, default=1000)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-ablation", action="store_true")
     ap.add_argument("--batched-instances", type=int, default=64)
     ap.add_argument("--batched-steps", type=int, default=20)
     return ap.parse_args()
@@ -166,6 +167,23 @@ def ncu_traffic(workload: str, variant: str):
         return float(e["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
         return None
+
+
+def max_over_ranks(x: float, ws: int, device=None) -> float:
+    """The largest value of x over all ranks (the timed region's max-over-ranks)."""
+    if ws == 1:
+        return float(x)
+    import torch
+    import torch.distributed as tdist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank: float, ws: int, seconds_max: float) -> float:
+    """Throughput of the whole job: units processed by all replicas / slowest rank's time."""
+    return ws * units_per_rank / seconds_max
 
 
 def dist():
@@ -342,6 +360,33 @@ def batched_report(pb, ninst, nsteps, stream):
             "dfdt_err_vs_fp64_max_over_instances": err}
 
 
+def ablation_report(pb, m, ch_full, stream):
+    """The paper's own layout (each channel once, sc_col written then gathered with signs)
+    against the full-list fused sweep, on the whole list and with the paper's cutoffs on
+    (delta at 6 sigma, |g|^2 >= 1e-5 eV^2)."""
+    import torch
+
+    out = {}
+    for label, kw in (("no_cutoffs", None), ("cutoffs_delta6sigma_g2min1e-5", {"g2_min": 1e-5, "delta_nsigma": 6.0})):
+        ch = ch_full if kw is None else pb.Channels.from_model(m, **kw)
+        ids = ch.state_ids()
+        f = torch.tensor(m.f_hot().reshape(-1)[ids], device="cuda")
+        res = {"channels": ch.nchannels}
+        for v in ("ff", "paper"):
+            d = pb.Device(ch, variant=v)
+            o = torch.empty(d.nstate, dtype=torch.float64, device="cuda")
+            ms = time_calls(lambda: d.collision(f, out=o), 20, stream)
+            res[v] = {"collision_ms": ms, "channels_per_s": ch.nchannels / (ms * 1e-3),
+                      "bytes_per_channel": d.bytes_per_channel,
+                      "algorithmic_gb_s": d.bytes_per_channel * ch.nchannels / (ms * 1e-3) / 1e9}
+            d.close()
+        res["paper_time_over_ff"] = res["paper"]["collision_ms"] / res["ff"]["collision_ms"]
+        out[label] = res
+        if kw is not None:
+            ch.close()
+    return out
+
+
 def compare_variants(pb, ch, dev_ff, fh, ff_ms, mixed_steps, stream):
     """Collision sweep of every variant on the same channel list: time, channels/s,
     speed-up over the FP64-accurate default and over native FP64, and df/dt error against
@@ -417,14 +462,8 @@ def run_ours(args):
             tdist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x: float) -> float:
-        if ws == 1:
-            return x
-        import torch.distributed as tdist
-
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        return float(t.item())
+    def rank_max(x: float) -> float:
+        return max_over_ranks(x, ws, device="cuda")
 
     m = synth.make_config(args.workload)
     t0 = time.perf_counter()
@@ -465,8 +504,8 @@ def run_ours(args):
     e1.record(stream)
     barrier()
     ms = e0.elapsed_time(e1)
-    ms_max = max_over_ranks(ms)
-    value = ws * SWEEPS_PER_STEP * nch * args.steps / (ms_max * 1e-3)
+    ms_max = rank_max(ms)
+    value = whole_job_value(SWEEPS_PER_STEP * nch * args.steps, ws, ms_max * 1e-3)
 
     # rt-BTE RK4 steps per second (one call, graph replay)
     nrk = 200
@@ -543,7 +582,7 @@ def run_ours(args):
         for _ in range(args.steps):
             e2e_step()
         torch.cuda.synchronize()
-        e2e_s = max_over_ranks(time.perf_counter() - t0)
+        e2e_s = rank_max(time.perf_counter() - t0)
         assert np.isfinite(fnp).all()
         e2e = {"value": ws * SWEEPS_PER_STEP * nch * args.steps / e2e_s, "unit": "channels/s",
                "h2d_bytes_per_step": 8 * ns + 24 * ns, "d2h_bytes_per_step": 8 * ns + 24 * ns}
@@ -551,6 +590,10 @@ def run_ours(args):
     variants = None
     if not args.no_variants and ws == 1:
         variants = compare_variants(pb, ch, dev, fh, coll_ms, args.mixed_steps, stream)
+
+    ablation = None
+    if not args.no_ablation and ws == 1:
+        ablation = ablation_report(pb, m, ch, stream)
 
     batched = None
     if not args.no_batched and ws == 1:
@@ -580,7 +623,7 @@ def run_ours(args):
                          "peak_source": peak_src},
             "cpu_baseline": base, "e2e": e2e, "gpu_launches": LAUNCHES_PER_STEP * args.steps,
             "clocks": clk, "setup": {"build_channels_s": build_s, "device_create_s": create_s},
-            "transport_solve": solve, "variants": variants, "batched": batched,
+            "transport_solve": solve, "variants": variants, "batched": batched, "paper_layout": ablation,
         })
     if ws > 1:
         import torch.distributed as tdist

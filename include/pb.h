@@ -139,16 +139,25 @@ void pb_channels_free(pb_channels *ch);
  *                     Gaussians and Bose factors per channel in FP64 registers.
  *  PB_VARIANT_G32     |g|^2 stored FP32, per-channel arithmetic in FP32, compensated
  *                     (Kahan) accumulation, FP64 state.
- *  PB_VARIANT_G16     as G32 with |g|^2 stored BF16. */
-enum { PB_VARIANT_FF = 0, PB_VARIANT_F64 = 1, PB_VARIANT_LITERAL = 2, PB_VARIANT_G32 = 3, PB_VARIANT_G16 = 4 };
+ *  PB_VARIANT_G16     as G32 with |g|^2 stored BF16.
+ *  PB_VARIANT_PAPER   the paper's own layout (Sec. "Optimized GPU algorithm", Fig. 2), for
+ *                     comparison: every channel stored once, per-channel contributions written
+ *                     to sc_col (step 2), then gathered with signs by each state's target list
+ *                     (step 3).  Collision integral and RK4 only (no scattering rates). */
+enum { PB_VARIANT_FF = 0, PB_VARIANT_F64 = 1, PB_VARIANT_LITERAL = 2, PB_VARIANT_G32 = 3, PB_VARIANT_G16 = 4,
+       PB_VARIANT_PAPER = 5 };
 
 typedef struct pb_dev_opts {
   int32_t variant;           /* PB_VARIANT_* */
   int32_t item_channels;     /* channels per work item (multiple of 64; 0 = automatic, 256..4096) */
   int32_t ctas_per_sm;       /* resident CTAs per SM for the coefficient sweeps (0 = 3) */
   int32_t transport;         /* nonzero: reserve transport buffers (weights and F) */
-  int32_t transport_gather;  /* transport F gather: 0 automatic (= 2), 1 shared memory, 2 through L1 */
-  int32_t transport_ctas;    /* resident 512-thread transport CTAs per SM (0 = 3 with L1 gathers) */
+  int32_t transport_gather;  /* transport F gather: 0 automatic (= 3), 1 shared memory, 2 through L1 with
+                                4-channel groups per lane, 3 through L1 with one channel per lane */
+  int32_t transport_ctas;    /* resident 256-thread transport CTAs per SM, 1..8 (0 = 8 with L1 gathers) */
+  int32_t channel_per_lane;  /* FP32/BF16 sweep lane mapping: 0 automatic (= 1), 1 one channel per lane,
+                                2 four-channel groups per lane */
+  int32_t reserved;
 } pb_dev_opts;
 
 typedef struct pb_dev pb_dev; /* opaque host handle describing device-resident data */
@@ -230,7 +239,8 @@ int pb_transport_map(pb_dev *dev, const double *f0, const double *vel3, const do
  * Each stored channel's |g|^2 is its own variable here; the derivative with respect to the
  * shared |g|^2 of a channel and its reverse is the sum of the two entries.  The transposed
  * sum is evaluated as a gather over each state's own row (the list is closed under
- * s <-> p), so no atomic updates are needed.  Needs the PB_VARIANT_FF device. */
+ * s <-> p), so no atomic updates are needed.  Needs a PB_VARIANT_FF device (FP64-accurate) or a
+ * PB_VARIANT_G32 / G16 device (FP32 per-channel terms, FP64 accumulation). */
 int pb_collision_vjp(pb_dev *dev, const double *f, const double *lam, double *grad_f, double *grad_g2,
                      void *stream);
 

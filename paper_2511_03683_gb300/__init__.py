@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_PKG, "lib", "libpb.so")
 PB_OK, PB_EINVAL, PB_ENOMEM, PB_ECUDA, PB_ENOTCLOSED, PB_ENOCONV, PB_ETIMEOUT, PB_ECALLBACK, PB_EDEVICE = range(9)
 _CODES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCLOSED", 5: "ENOCONV", 6: "ETIMEOUT", 7: "ECALLBACK",
           8: "EDEVICE"}
-VARIANTS = {"ff": 0, "f64": 1, "literal": 2, "g32": 3, "g16": 4}
+VARIANTS = {"ff": 0, "f64": 1, "literal": 2, "g32": 3, "g16": 4, "paper": 5}
 
 
 class PBError(RuntimeError):
@@ -55,7 +55,7 @@ class _ChInfo(ctypes.Structure):
 class _DevOpts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("item_channels", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("transport", ctypes.c_int32), ("transport_gather", ctypes.c_int32),
-                ("transport_ctas", ctypes.c_int32)]
+                ("transport_ctas", ctypes.c_int32), ("channel_per_lane", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class _DevInfo(ctypes.Structure):
@@ -271,7 +271,8 @@ class Device:
     """Device-resident channel list and tables (pb_dev_create) in one torch arena."""
 
     def __init__(self, channels: Channels, variant: str = "ff", item_channels: int = 0, ctas_per_sm: int = 0,
-                 transport: bool = False, transport_gather: int = 0, transport_ctas: int = 0, stream=None):
+                 transport: bool = False, transport_gather: int = 0, transport_ctas: int = 0,
+                 channel_per_lane: int = 0, stream=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -279,7 +280,7 @@ class Device:
         self.channels = channels
         self.variant = variant
         o = _DevOpts(VARIANTS[variant], int(item_channels), int(ctas_per_sm), 1 if transport else 0,
-                     int(transport_gather), int(transport_ctas))
+                     int(transport_gather), int(transport_ctas), int(channel_per_lane), 0)
         nbytes = ctypes.c_size_t(0)
         _check(lib().pb_dev_arena_bytes(channels._h, ctypes.byref(o), ctypes.byref(nbytes)))
         self.arena = torch.empty(int(nbytes.value), dtype=torch.uint8, device="cuda")

@@ -25,7 +25,8 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
   size_t rp, item_ptr, items, col, coefA, coefB, g2, wt, eps, kc, R, omega, tab, part, acc, y, yff, fstage, Fa, Fb,
-      Fff, tau, invtau, red, scal, obs, g2lo, gstate, tab32, col16, rp_real, vjpG, vecs, total;
+      Fff, tau, invtau, red, scal, obs, g2lo, gstate, tab32, col16, rp_real, vjpG, vecs, hcol, hg2, hA, hB, sc,
+      entries, hitems, titems, t_item_ptr, total;
 };
 
 struct Plan {
@@ -75,6 +76,26 @@ void make_plan(const pb_channels *ch, int item_ch, Plan &P) {
   P.nitems = (int64_t)P.items.size();
 }
 
+// Paper layout (PB_VARIANT_PAPER): half list = the channels of row s with partner >= s;
+// target list of state x = its half channels (+) and the half channels (s -> x), s < x (-),
+// which by closure are as many as the full row of x.
+struct PaperSizes {
+  int64_t nh = 0, nhp = 0, nent = 0, nentp = 0;
+};
+
+PaperSizes paper_sizes(const pb_channels *ch) {
+  PaperSizes z;
+  for (int64_t r = 0; r < ch->nstate; ++r) {
+    const int32_t *b = ch->col.data() + ch->row_ptr[r], *e = ch->col.data() + ch->row_ptr[r + 1];
+    const int64_t h = e - std::lower_bound(b, e, (int32_t)r);
+    z.nh += h;
+    z.nhp += (h + kRowPad - 1) / kRowPad * kRowPad;
+    z.nent += e - b;
+    z.nentp += (e - b + kRowPad - 1) / kRowPad * kRowPad;
+  }
+  return z;
+}
+
 size_t coef_bytes(int variant) {
   switch (variant) {
     case PB_VARIANT_FF: return sizeof(float2);
@@ -105,7 +126,6 @@ Layout make_layout(const pb_channels *ch, const Plan &P, int variant, bool trans
   L.R = take(sizeof(double) * ns);
   L.omega = take(sizeof(double) * (size_t)ch->nq * ch->nmodes);
   L.tab = take(sizeof(double2) * (size_t)ch->nq * ch->nmodes);
-  L.part = take(sizeof(Part4) * P.nitems);
   L.acc = take(sizeof(double) * ns);
   L.y = take(sizeof(double) * ns);
   L.yff = take(sizeof(float2) * ns);
@@ -124,6 +144,19 @@ Layout make_layout(const pb_channels *ch, const Plan &P, int variant, bool trans
   auto rad = [](int n) { return (size_t)(n > 1 ? 2 * n : 1); };
   L.tab32 = take(mixed ? sizeof(float4) * rad(ch->nk[0]) * rad(ch->nk[1]) * rad(ch->nk[2]) * ch->nmodes : 0);
   L.col16 = take(ns <= 65536 ? sizeof(uint16_t) * nchp : 0);
+  PaperSizes z;
+  if (variant == PB_VARIANT_PAPER) z = paper_sizes(ch);
+  const int64_t nhi = (variant == PB_VARIANT_PAPER) ? z.nhp / kRowPad + (int64_t)ns : 0;  // upper bound of items
+  L.hcol = take(sizeof(uint32_t) * z.nhp);
+  L.hg2 = take(sizeof(double) * z.nhp);
+  L.hA = take(sizeof(float2) * z.nhp);
+  L.hB = take(sizeof(float2) * z.nhp);
+  L.sc = take(sizeof(float2) * (z.nhp + 8));
+  L.entries = take(sizeof(int32_t) * z.nentp);
+  L.hitems = take(sizeof(Item) * nhi);
+  L.titems = take(sizeof(Item) * ((variant == PB_VARIANT_PAPER) ? z.nentp / kRowPad + (int64_t)ns : 0));
+  L.t_item_ptr = take(sizeof(int32_t) * (ns + 1));
+  L.part = take(sizeof(Part4) * std::max<int64_t>(P.nitems, (variant == PB_VARIANT_PAPER) ? z.nentp / kRowPad + (int64_t)ns : 0));
   L.rp_real = take(sizeof(int64_t) * (ns + 1));
   L.vjpG = take(sizeof(float2) * 3 * ns);
   L.vecs = take(sizeof(double) * 8 * ns);
@@ -189,12 +222,21 @@ struct pb_dev {
   int64_t *rp_real = nullptr;  // unpadded CSR row offsets [ns+1]
   float2 *vjpG = nullptr;      // adjoint gather table [ns][3]
   double *vecs = nullptr;      // 8 scratch vectors of nstate doubles (adjoint stages)
+  // paper layout (PB_VARIANT_PAPER)
+  uint32_t *hcol = nullptr;
+  double *hg2 = nullptr;
+  float2 *hA = nullptr, *hB = nullptr, *sc = nullptr;
+  int32_t *entries = nullptr, *t_item_ptr = nullptr;
+  Item *hitems = nullptr, *titems = nullptr;
+  int64_t nhitems = 0, ntitems = 0, nh = 0, nhp = 0, nent = 0;
   int rad[3] = {1, 1, 1};   // padded-grid radices of the FP32 phonon table
   int nfin_blocks = 0;
   size_t smem_f = 0;      // dynamic smem of the f staging (0 = gather from global)
   size_t smem_F = 0;      // dynamic smem of the transport F staging
   int ctas_tr = 1;        // resident transport CTAs per SM
   size_t smem_G = 0;      // dynamic smem of the adjoint gather table
+  bool tr_lane = true;    // L1-gather transport with consecutive lanes on consecutive channels
+  bool g_lane = true;     // mixed-precision sweep with consecutive lanes on consecutive channels
   // RK4 graph cache
   cudaStream_t cap = nullptr;
   cudaGraphExec_t rk_exec = nullptr;
@@ -252,12 +294,14 @@ int check_device(int *sm_count) {
 int resolve_opts(const pb_channels *ch, const pb_dev_opts *opts, int sm_count, pb_dev_opts &o) {
   pb_dev_opts d{};
   if (opts) d = *opts;
-  if (d.variant < PB_VARIANT_FF || d.variant > PB_VARIANT_G16)
+  if (d.variant < PB_VARIANT_FF || d.variant > PB_VARIANT_PAPER)
     return set_error(PB_EINVAL, "pb_dev: variant %d is not available in this build", d.variant);
   if (d.ctas_per_sm <= 0) d.ctas_per_sm = 3;  // measured best on GB300 for the coefficient sweeps
   if (d.ctas_per_sm > 8) return set_error(PB_EINVAL, "pb_dev: ctas_per_sm must be <= 8");
-  if (d.transport_gather < 0 || d.transport_gather > 2 || d.transport_ctas < 0 || d.transport_ctas > 4)
-    return set_error(PB_EINVAL, "pb_dev: transport_gather must be 0..2 and transport_ctas 0..4");
+  if (d.channel_per_lane < 0 || d.channel_per_lane > 2)
+    return set_error(PB_EINVAL, "pb_dev: channel_per_lane must be 0..2");
+  if (d.transport_gather < 0 || d.transport_gather > 3 || d.transport_ctas < 0 || d.transport_ctas > 8)
+    return set_error(PB_EINVAL, "pb_dev: transport_gather must be 0..3 and transport_ctas 0..8");
   if (d.item_channels < 0 || d.item_channels % 64 != 0)
     return set_error(PB_EINVAL, "pb_dev: item_channels must be a non-negative multiple of 64");
   if (d.item_channels == 0) {
@@ -273,6 +317,93 @@ int resolve_opts(const pb_channels *ch, const pb_dev_opts *opts, int sm_count, p
 }  // namespace
 
 namespace {
+
+void plan_items(const std::vector<int64_t> &rp, int item_ch, std::vector<Item> &items, std::vector<int32_t> &ptr) {
+  const int64_t ns = (int64_t)rp.size() - 1;
+  items.clear();
+  ptr.assign(ns + 1, 0);
+  for (int64_t r = 0; r < ns; ++r) {
+    ptr[r] = (int32_t)items.size();
+    const int64_t lenp = rp[r + 1] - rp[r];
+    if (lenp == 0) continue;
+    const int64_t chunks = lenp / kRowPad, np = std::max<int64_t>(1, (lenp + item_ch - 1) / item_ch);
+    int64_t off = 0;
+    for (int64_t k = 0; k < np; ++k) {
+      const int64_t c = chunks / np + (k < chunks % np ? 1 : 0);
+      if (c > 0) {
+        Item it;
+        it.start = rp[r] + off;
+        it.len = (int)(c * kRowPad);
+        it.row = (int)r;
+        items.push_back(it);
+      }
+      off += c * kRowPad;
+    }
+  }
+  ptr[ns] = (int32_t)items.size();
+}
+
+// Half list, per-channel coefficients of the half list, and the signed target layer.
+int paper_setup(pb_dev *d, const pb_channels *ch, int item_ch, cudaStream_t st) {
+  const int64_t ns = ch->nstate;
+  std::vector<int64_t> hstart(ns), hlen(ns), hrp(ns + 1, 0), trp(ns + 1, 0);
+  for (int64_t r = 0; r < ns; ++r) {
+    const int32_t *b = ch->col.data() + ch->row_ptr[r], *e = ch->col.data() + ch->row_ptr[r + 1];
+    const int32_t *lo = std::lower_bound(b, e, (int32_t)r);
+    hstart[r] = lo - ch->col.data();
+    hlen[r] = e - lo;
+    hrp[r + 1] = hrp[r] + (hlen[r] + kRowPad - 1) / kRowPad * kRowPad;
+    const int64_t full = e - b;
+    trp[r + 1] = trp[r] + (full + kRowPad - 1) / kRowPad * kRowPad;
+  }
+  const int64_t nhp = hrp[ns], nentp = trp[ns];
+  std::vector<uint32_t> hcol((size_t)nhp);
+  std::vector<double> hg2((size_t)nhp, 0.0);
+  std::vector<int32_t> ent((size_t)nentp, (int32_t)nhp);  // padding entries read the zero slot
+  std::vector<int64_t> fill(ns, 0);
+  int64_t nh = 0, nent = 0;
+  for (int64_t r = 0; r < ns; ++r) {
+    for (int64_t k = 0; k < hlen[r]; ++k) {
+      const int64_t c = hstart[r] + k, h = hrp[r] + k;
+      const int32_t p = ch->col[c];
+      hcol[h] = (uint32_t)p | ((uint32_t)ch->nu[c] << kPartnerBits);
+      hg2[h] = ch->g2[c];
+      ent[trp[r] + fill[r]++] = (int32_t)h;
+      ++nent;
+      if (p != (int32_t)r) {
+        ent[trp[p] + fill[p]++] = (int32_t)(h | (int64_t)0x80000000LL);
+        ++nent;
+      }
+      ++nh;
+    }
+    for (int64_t k = hlen[r]; k < hrp[r + 1] - hrp[r]; ++k) hcol[hrp[r] + k] = (uint32_t)r;
+  }
+  std::vector<Item> hitems, titems;
+  std::vector<int32_t> hptr, tptr;
+  plan_items(hrp, item_ch, hitems, hptr);
+  plan_items(trp, item_ch, titems, tptr);
+  PB_CUDA(cudaMemcpyAsync(d->hcol, hcol.data(), sizeof(uint32_t) * nhp, cudaMemcpyHostToDevice, st));
+  PB_CUDA(cudaMemcpyAsync(d->hg2, hg2.data(), sizeof(double) * nhp, cudaMemcpyHostToDevice, st));
+  PB_CUDA(cudaMemcpyAsync(d->entries, ent.data(), sizeof(int32_t) * nentp, cudaMemcpyHostToDevice, st));
+  PB_CUDA(cudaMemcpyAsync(d->hitems, hitems.data(), sizeof(Item) * hitems.size(), cudaMemcpyHostToDevice, st));
+  PB_CUDA(cudaMemcpyAsync(d->titems, titems.data(), sizeof(Item) * titems.size(), cudaMemcpyHostToDevice, st));
+  PB_CUDA(cudaMemcpyAsync(d->t_item_ptr, tptr.data(), sizeof(int32_t) * (ns + 1), cudaMemcpyHostToDevice, st));
+  PB_CUDA(cudaMemsetAsync(d->sc, 0, sizeof(float2) * (nhp + 8), st));
+  d->nhitems = (int64_t)hitems.size();
+  d->ntitems = (int64_t)titems.size();
+  d->nh = nh;
+  d->nhp = nhp;
+  d->nent = nent;
+  pb::dev::ChanGeom g = d->geom();
+  g.col = d->hcol;
+  g.g2 = d->hg2;
+  const int64_t need = (d->nhitems * 32 + dev::kBlock - 1) / dev::kBlock;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)d->sm_count * 8));
+  dev::k_coef<true><<<grid, dev::kBlock, 0, st>>>(d->hitems, (int)d->nhitems, g, d->hA, d->hB, d->part);
+  PB_LAUNCHED("k_coef (half list)");
+  PB_CUDA(cudaStreamSynchronize(st));  // host staging vectors are released on return
+  return PB_OK;
+}
 
 template <typename IDX>
 void set_stream_smem(int bytes) {
@@ -390,6 +521,15 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->rp_real = (int64_t *)(A + L.rp_real);
   d->vjpG = (float2 *)(A + L.vjpG);
   d->vecs = (double *)(A + L.vecs);
+  d->hcol = (uint32_t *)(A + L.hcol);
+  d->hg2 = (double *)(A + L.hg2);
+  d->hA = (float2 *)(A + L.hA);
+  d->hB = (float2 *)(A + L.hB);
+  d->sc = (float2 *)(A + L.sc);
+  d->entries = (int32_t *)(A + L.entries);
+  d->hitems = (Item *)(A + L.hitems);
+  d->titems = (Item *)(A + L.titems);
+  d->t_item_ptr = (int32_t *)(A + L.t_item_ptr);
 
   // shared-memory staging sizes
   int devid = 0, smem_optin = 0;
@@ -418,11 +558,13 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   // automatic: gather F through L1 (measured faster on GB300 than shared-memory staging,
   // which limits residency to one 512-thread CTA per SM at 40^3)
   d->smem_F = (o.transport_gather == 1 && F_fits) ? Fbytes : 0;
+  d->tr_lane = o.transport_gather != 2;  // 2 = L1 gathers with 4-channel groups per lane
+  d->g_lane = o.channel_per_lane != 2;   // 2 = 4-channel groups per lane in the mixed-precision sweep
   if (o.transport_gather == 1 && !F_fits) {
     delete d;
     return set_error(PB_EINVAL, "pb_dev_create: F of %lld states does not fit in shared memory", (long long)ch->nstate);
   }
-  d->ctas_tr = d->smem_F ? (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(228 * 1024) / (d->smem_F + 1024))) : 3;
+  d->ctas_tr = d->smem_F ? (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(228 * 1024) / (d->smem_F + 1024))) : 8;
   if (o.transport_ctas > 0) d->ctas_tr = std::min(d->ctas_tr, o.transport_ctas);
   if (!d->smem_F && o.transport_ctas > 0) d->ctas_tr = o.transport_ctas;
 
@@ -496,6 +638,7 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
         if (e != cudaSuccess) status = cuda_fail(e, "k_rowsum");
       }
     }
+    if (status == PB_OK && d->variant == PB_VARIANT_PAPER) status = paper_setup(d, ch, o.item_channels, st);
     if (status == PB_OK && d->mixed()) {
       const long long n = (long long)P.nchp;
       const int cg = (int)std::min<long long>((n + 255) / 256, 8192);
@@ -525,6 +668,7 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   if (d->smem_f > 48 * 1024) {
     set_stream_smem<uint32_t>((int)d->smem_f);
     set_stream_smem<uint16_t>((int)d->smem_f);
+    cudaFuncSetAttribute(dev::k_paper_sc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
   }
   if (d->smem_F > 48 * 1024) {
     cudaFuncSetAttribute(dev::k_stream_tr<true, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_F);
@@ -538,7 +682,18 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
     }
     d->smem_G = gb + 1024 <= (size_t)smem_optin ? gb : 0;
   }
+  if (d->mixed()) {
+    const int vb = (int)((sizeof(uint4) + sizeof(float)) * (size_t)d->ns);
+    if (vb > 48 * 1024) {
+      cudaFuncSetAttribute(dev::k_stream_g_vjp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, vb);
+      cudaFuncSetAttribute(dev::k_stream_g_vjp<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, vb);
+    }
+  }
   if (d->mixed() && d->smem_f > 48 * 1024) {
+    cudaFuncSetAttribute(dev::k_stream_g_lane<dev::MODE_COLL, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
+    cudaFuncSetAttribute(dev::k_stream_g_lane<dev::MODE_RATE, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
+    cudaFuncSetAttribute(dev::k_stream_g_lane<dev::MODE_COLL, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
+    cudaFuncSetAttribute(dev::k_stream_g_lane<dev::MODE_RATE, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
     cudaFuncSetAttribute(dev::k_stream_g<dev::MODE_COLL, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
     cudaFuncSetAttribute(dev::k_stream_g<dev::MODE_RATE, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
     cudaFuncSetAttribute(dev::k_stream_g<dev::MODE_COLL, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
@@ -572,6 +727,9 @@ extern "C" int pb_dev_get_info(const pb_dev *d, pb_dev_info *info) {
     case PB_VARIANT_F64: info->bytes_per_channel = 2 * sizeof(double) + (d->col16 ? 2 : 4); break;
     case PB_VARIANT_G32: info->bytes_per_channel = sizeof(float) + sizeof(uint32_t); break;
     case PB_VARIANT_G16: info->bytes_per_channel = 2 + sizeof(uint32_t); break;
+    case PB_VARIANT_PAPER:  // step 2: P_in, D, index, sc_col write; step 3: entry + sc_col gather
+      info->bytes_per_channel = d->nch ? (28.0 * (double)d->nh + 12.0 * (double)d->nent) / (double)d->nch : 0.0;
+      break;
     default: info->bytes_per_channel = sizeof(double) + sizeof(uint32_t); break;
   }
   return PB_OK;
@@ -607,15 +765,38 @@ int launch_stream_t(pb_dev *d, int mode, const double *fd, const float2 *fff, co
       if (coll) dev::k_stream_f64<dev::MODE_COLL, false, IDX><<<grid, dev::kBlock, 0, st>>>(d->items, n, A2, B2, colp, fd, ns, part);
       else      dev::k_stream_f64<dev::MODE_RATE, false, IDX><<<grid, dev::kBlock, 0, st>>>(d->items, n, A2, B2, colp, fd, ns, part);
     }
+  } else if (d->variant == PB_VARIANT_PAPER) {
+    if (!coll) return set_error(PB_EINVAL, "scattering rates are not available in the paper layout");
+    const int64_t nh32 = (d->nhitems * 32 + dev::kBlock - 1) / dev::kBlock;
+    const int gh = (int)std::max<int64_t>(1, std::min<int64_t>(nh32, (int64_t)d->sm_count * d->ctas));
+    const float4 *A4 = (const float4 *)d->hA, *B4 = (const float4 *)d->hB;
+    if (d->smem_f)
+      dev::k_paper_sc<true><<<gh, dev::kBlock, d->smem_f, st>>>(d->hitems, (int)d->nhitems, A4, B4, d->hcol, fff, ns, (float4 *)d->sc);
+    else
+      dev::k_paper_sc<false><<<gh, dev::kBlock, 0, st>>>(d->hitems, (int)d->nhitems, A4, B4, d->hcol, fff, ns, (float4 *)d->sc);
+    PB_LAUNCHED("k_paper_sc");
+    const int64_t nt32 = (d->ntitems * 32 + dev::kBlock - 1) / dev::kBlock;
+    const int gt = (int)std::max<int64_t>(1, std::min<int64_t>(nt32, (int64_t)d->sm_count * 4));
+    dev::k_paper_gather<<<gt, dev::kBlock, 0, st>>>(d->titems, (int)d->ntitems, d->entries, d->sc, part);
   } else if (d->mixed()) {
     const dev::GGeom g = d->ggeom();
     const int gg = (int)std::max<int64_t>(1, std::min<int64_t>((d->nitems * 32 + 511) / 512, (int64_t)d->sm_count * d->ctas));
-    if (d->variant == PB_VARIANT_G32) {
-      if (coll) dev::k_stream_g<dev::MODE_COLL, float><<<gg, 512, d->smem_f, st>>>(d->items, n, g, (const float *)d->g2lo, d->gstate, ns, part);
-      else      dev::k_stream_g<dev::MODE_RATE, float><<<gg, 512, d->smem_f, st>>>(d->items, n, g, (const float *)d->g2lo, d->gstate, ns, part);
+    const float *g32 = (const float *)d->g2lo;
+    const __nv_bfloat16 *g16 = (const __nv_bfloat16 *)d->g2lo;
+    if (d->g_lane) {
+      if (d->variant == PB_VARIANT_G32) {
+        if (coll) dev::k_stream_g_lane<dev::MODE_COLL, float><<<gg, 512, d->smem_f, st>>>(d->items, n, g, g32, d->gstate, ns, part);
+        else      dev::k_stream_g_lane<dev::MODE_RATE, float><<<gg, 512, d->smem_f, st>>>(d->items, n, g, g32, d->gstate, ns, part);
+      } else {
+        if (coll) dev::k_stream_g_lane<dev::MODE_COLL, __nv_bfloat16><<<gg, 512, d->smem_f, st>>>(d->items, n, g, g16, d->gstate, ns, part);
+        else      dev::k_stream_g_lane<dev::MODE_RATE, __nv_bfloat16><<<gg, 512, d->smem_f, st>>>(d->items, n, g, g16, d->gstate, ns, part);
+      }
+    } else if (d->variant == PB_VARIANT_G32) {
+      if (coll) dev::k_stream_g<dev::MODE_COLL, float><<<gg, 512, d->smem_f, st>>>(d->items, n, g, g32, d->gstate, ns, part);
+      else      dev::k_stream_g<dev::MODE_RATE, float><<<gg, 512, d->smem_f, st>>>(d->items, n, g, g32, d->gstate, ns, part);
     } else {
-      if (coll) dev::k_stream_g<dev::MODE_COLL, __nv_bfloat16><<<gg, 512, d->smem_f, st>>>(d->items, n, g, (const __nv_bfloat16 *)d->g2lo, d->gstate, ns, part);
-      else      dev::k_stream_g<dev::MODE_RATE, __nv_bfloat16><<<gg, 512, d->smem_f, st>>>(d->items, n, g, (const __nv_bfloat16 *)d->g2lo, d->gstate, ns, part);
+      if (coll) dev::k_stream_g<dev::MODE_COLL, __nv_bfloat16><<<gg, 512, d->smem_f, st>>>(d->items, n, g, g16, d->gstate, ns, part);
+      else      dev::k_stream_g<dev::MODE_RATE, __nv_bfloat16><<<gg, 512, d->smem_f, st>>>(d->items, n, g, g16, d->gstate, ns, part);
     }
   } else {
     const dev::ChanGeom g = d->geom();
@@ -645,8 +826,9 @@ void launch_fin(pb_dev *d, const double *ysrc, double *out, double *f, double dt
                                                                           d->c * d->gnorm(), d->R,
                                                                           ysrc, out, f, d->acc, d->y,
                                                                           (float2 *)d->gstate, dt);
-  else if (d->variant == PB_VARIANT_LITERAL)
-    dev::k_fin_coll<true, STAGE><<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->c, d->R, ysrc,
+  else if (d->variant == PB_VARIANT_LITERAL || d->variant == PB_VARIANT_PAPER)
+    dev::k_fin_coll<true, STAGE><<<fin_grid(d), kFinBlock, 0, st>>>(
+        d->variant == PB_VARIANT_PAPER ? d->t_item_ptr : d->item_ptr, d->part, (int)d->ns, d->c, d->R, ysrc,
                                                                     out, f, d->acc, d->y, d->yff, dt);
   else
     dev::k_fin_coll<false, STAGE><<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->c, d->R, ysrc,
@@ -662,7 +844,7 @@ int to_ff(pb_dev *d, const double *x, int64_t n, float2 *out, cudaStream_t st) {
 
 // Stage-input conversion the streaming kernel of this variant reads.
 int stage_input(pb_dev *d, const double *f, cudaStream_t st) {
-  if (d->variant == PB_VARIANT_FF) return to_ff(d, f, d->ns, d->yff, st);
+  if (d->variant == PB_VARIANT_FF || d->variant == PB_VARIANT_PAPER) return to_ff(d, f, d->ns, d->yff, st);
   if (d->mixed()) {
     dev::k_gstate_f<<<(int)((d->ns + 255) / 256), 256, 0, st>>>(f, (int)d->ns, d->gstate);
     PB_LAUNCHED("k_gstate_f");
@@ -731,14 +913,17 @@ int transport_pass(pb_dev *d, const float2 *Fin_ff, const double *vel3, const do
                    float2 *Fnew_ff, cudaStream_t st) {
   const int n = (int)d->nitems;
   const float4 *W4 = (const float4 *)d->wt;
-  const int64_t need = (d->nitems * 32 + 511) / 512;
+  const int64_t need = (d->nitems * 32 + dev::kBlock - 1) / dev::kBlock;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)d->sm_count * d->ctas_tr));
   if (d->smem_F) {
-    if (d->col16) dev::k_stream_tr<true, uint16_t><<<grid, 512, d->smem_F, st>>>(d->items, n, W4, d->col16, Fin_ff, (int)d->ns, d->part);
-    else          dev::k_stream_tr<true, uint32_t><<<grid, 512, d->smem_F, st>>>(d->items, n, W4, d->col, Fin_ff, (int)d->ns, d->part);
+    if (d->col16) dev::k_stream_tr<true, uint16_t><<<grid, dev::kBlock, d->smem_F, st>>>(d->items, n, W4, d->col16, Fin_ff, (int)d->ns, d->part);
+    else          dev::k_stream_tr<true, uint32_t><<<grid, dev::kBlock, d->smem_F, st>>>(d->items, n, W4, d->col, Fin_ff, (int)d->ns, d->part);
+  } else if (d->tr_lane) {
+    if (d->col16) dev::k_stream_tr_lane<uint16_t><<<grid, dev::kBlock, 0, st>>>(d->items, n, d->wt, d->col16, Fin_ff, d->part);
+    else          dev::k_stream_tr_lane<uint32_t><<<grid, dev::kBlock, 0, st>>>(d->items, n, d->wt, d->col, Fin_ff, d->part);
   } else {
-    if (d->col16) dev::k_stream_tr<false, uint16_t><<<grid, 512, 0, st>>>(d->items, n, W4, d->col16, Fin_ff, (int)d->ns, d->part);
-    else          dev::k_stream_tr<false, uint32_t><<<grid, 512, 0, st>>>(d->items, n, W4, d->col, Fin_ff, (int)d->ns, d->part);
+    if (d->col16) dev::k_stream_tr<false, uint16_t><<<grid, dev::kBlock, 0, st>>>(d->items, n, W4, d->col16, Fin_ff, (int)d->ns, d->part);
+    else          dev::k_stream_tr<false, uint32_t><<<grid, dev::kBlock, 0, st>>>(d->items, n, W4, d->col, Fin_ff, (int)d->ns, d->part);
   }
   PB_LAUNCHED("k_stream_tr");
   dev::k_fin_tr<<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->tau, vel3, Fold, Fnew,
@@ -907,8 +1092,39 @@ int coef_setup(pb_dev *d, cudaStream_t st) {
   return PB_OK;
 }
 
+// Mixed-precision adjoint: FP32 per-channel terms, FP64 partials and output.
+int vjp_launch_mixed(pb_dev *d, const double *f, const double *lam, double *grad_f, double *grad_g2,
+                     cudaStream_t st) {
+  const int ns = (int)d->ns, n = (int)d->nitems;
+  int rc = stage_input(d, f, st);
+  if (rc) return rc;
+  float *lam32 = (float *)d->vjpG;  // ns floats fit in the [ns][3] float2 table
+  dev::k_to_f32<<<(ns + 255) / 256, 256, 0, st>>>(lam, ns, lam32);
+  PB_LAUNCHED("k_to_f32");
+  const dev::GGeom g = d->ggeom();
+  const size_t smem = (sizeof(uint4) + sizeof(float)) * (size_t)ns;
+  const int ctas = (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(228 * 1024) / (smem + 1024)));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((d->nitems * 32 + 511) / 512, (int64_t)d->sm_count * ctas));
+  if (d->variant == PB_VARIANT_G32)
+    dev::k_stream_g_vjp<float><<<grid, 512, smem, st>>>(d->items, n, g, (const float *)d->g2lo, d->gstate, lam32, ns, d->part);
+  else
+    dev::k_stream_g_vjp<__nv_bfloat16><<<grid, 512, smem, st>>>(d->items, n, g, (const __nv_bfloat16 *)d->g2lo, d->gstate,
+                                                                lam32, ns, d->part);
+  PB_LAUNCHED("k_stream_g_vjp");
+  dev::k_fin_rate<true><<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, ns, -d->c * d->gnorm(), d->R, grad_f);
+  PB_LAUNCHED("k_fin_rate (vjp)");
+  if (grad_g2) {
+    dev::k_g2grad_g<<<d->stream_grid(8), dev::kBlock, 0, st>>>(d->items, n, g, d->gstate, (const long long *)d->rp,
+                                                               (const long long *)d->rp_real, lam,
+                                                               -d->c * d->gnorm(), grad_g2);
+    PB_LAUNCHED("k_g2grad_g");
+  }
+  return PB_OK;
+}
+
 // grad_f = J(f)^T lam (FF coefficients); grad_g2 (unpadded CSR order) += dL/dg2 if not null
 int vjp_launch(pb_dev *d, const double *f, const double *lam, double *grad_f, double *grad_g2, cudaStream_t st) {
+  if (d->mixed()) return vjp_launch_mixed(d, f, lam, grad_f, grad_g2, st);
   const int ns = (int)d->ns, n = (int)d->nitems;
   dev::k_vjp_prep<<<(ns + 255) / 256, 256, 0, st>>>(f, lam, ns, d->vjpG);
   PB_LAUNCHED("k_vjp_prep");
@@ -950,14 +1166,16 @@ extern "C" int pb_collision_vjp(pb_dev *d, const double *f, const double *lam, d
                                 void *stream) {
   clear_error();
   if (!d || !f || !lam || !grad_f) return set_error(PB_EINVAL, "pb_collision_vjp: null argument");
-  if (d->variant != PB_VARIANT_FF) return set_error(PB_EINVAL, "pb_collision_vjp: needs the FF variant");
+  if (d->variant != PB_VARIANT_FF && !d->mixed())
+    return set_error(PB_EINVAL, "pb_collision_vjp: needs the FF, G32 or G16 variant");
   return vjp_launch(d, f, lam, grad_f, grad_g2, (cudaStream_t)stream);
 }
 
 extern "C" int pb_rtbte_rk4_vjp(pb_dev *d, const double *f, double *lam, double dt, double *grad_g2, void *stream) {
   clear_error();
   if (!d || !f || !lam) return set_error(PB_EINVAL, "pb_rtbte_rk4_vjp: null argument");
-  if (d->variant != PB_VARIANT_FF) return set_error(PB_EINVAL, "pb_rtbte_rk4_vjp: needs the FF variant");
+  if (d->variant != PB_VARIANT_FF && !d->mixed())
+    return set_error(PB_EINVAL, "pb_rtbte_rk4_vjp: needs the FF, G32 or G16 variant");
   if (!std::isfinite(dt)) return set_error(PB_EINVAL, "pb_rtbte_rk4_vjp: bad dt");
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t ns = d->ns;
@@ -1034,7 +1252,7 @@ int static_scratch_address(void **out) {
 extern "C" int pb_collision_static(pb_dev *d, const double *f, double *dfdt, void *stream) {
   clear_error();
   if (!d || !f || !dfdt) return set_error(PB_EINVAL, "pb_collision_static: null argument");
-  if (d->mixed())
+  if (d->mixed() || d->variant == PB_VARIANT_PAPER)
     return set_error(PB_EINVAL, "pb_collision_static: available for the FF, F64 and literal variants only");
   const size_t ff_bytes = align_up(sizeof(float2) * (size_t)d->ns);
   const size_t part_bytes = sizeof(Part4) * (size_t)d->nitems;

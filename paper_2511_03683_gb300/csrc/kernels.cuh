@@ -378,10 +378,10 @@ __device__ __forceinline__ void tr_group(const float2 *__restrict__ Fv, uint4 c,
 }
 
 template <bool SMEM, typename IDX>
-__global__ void __launch_bounds__(512) k_stream_tr(const Item *__restrict__ items, int nitems,
-                                                   const float4 *__restrict__ W4, const IDX *__restrict__ colp,
-                                                   const float2 *__restrict__ Fg, int ns,
-                                                   Part4 *__restrict__ part) {
+__global__ void __launch_bounds__(kBlock) k_stream_tr(const Item *__restrict__ items, int nitems,
+                                                      const float4 *__restrict__ W4, const IDX *__restrict__ colp,
+                                                      const float2 *__restrict__ Fg, int ns,
+                                                      Part4 *__restrict__ part) {
   extern __shared__ float2 Fsm[];
   if (SMEM) {
     for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) Fsm[i] = Fg[i];
@@ -396,19 +396,73 @@ __global__ void __launch_bounds__(512) k_stream_tr(const Item *__restrict__ item
     const long long g0 = I.start >> 2;
     const int ng = I.len >> 2;
     float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f, zh = 0.f, zl = 0.f;
-    int g = lane;
-    for (; g + 32 < ng; g += 64) {
-      const long long q0 = g0 + g, q1 = q0 + 32;
-      const uint4 c0 = partners4(colp, q0), c1 = partners4(colp, q1);
-      const float4 a0 = __ldcs(W4 + 2 * q0), a1 = __ldcs(W4 + 2 * q0 + 1);
-      const float4 b0 = __ldcs(W4 + 2 * q1), b1 = __ldcs(W4 + 2 * q1 + 1);
-      tr_group<SMEM>(Fv, c0, a0, a1, xh, xl, yh, yl, zh, zl);
-      tr_group<SMEM>(Fv, c1, b0, b1, xh, xl, yh, yl, zh, zl);
+    // software pipeline: the next group's weights and indices load while this group computes
+    uint4 c = make_uint4(0u, 0u, 0u, 0u);
+    float4 w0 = make_float4(0.f, 0.f, 0.f, 0.f), w1 = w0;
+    if (lane < ng) {
+      c = partners4(colp, g0 + lane);
+      w0 = __ldcs(W4 + 2 * (g0 + lane));
+      w1 = __ldcs(W4 + 2 * (g0 + lane) + 1);
     }
-    if (g < ng) {
-      const long long q0 = g0 + g;
-      const uint4 c0 = partners4(colp, q0);
-      tr_group<SMEM>(Fv, c0, __ldcs(W4 + 2 * q0), __ldcs(W4 + 2 * q0 + 1), xh, xl, yh, yl, zh, zl);
+    for (int g = lane; g < ng; g += 32) {
+      uint4 cn = make_uint4(0u, 0u, 0u, 0u);
+      float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0;
+      if (g + 32 < ng) {
+        const long long qn = g0 + g + 32;
+        cn = partners4(colp, qn);
+        n0 = __ldcs(W4 + 2 * qn);
+        n1 = __ldcs(W4 + 2 * qn + 1);
+      }
+      tr_group<SMEM>(Fv, c, w0, w1, xh, xl, yh, yl, zh, zl);
+      c = cn;
+      w0 = n0;
+      w1 = n1;
+    }
+    const double X = warp_sum(ff_to_double(xh, xl));
+    const double Y = warp_sum(ff_to_double(yh, yl));
+    const double Z = warp_sum(ff_to_double(zh, zl));
+    if (lane == 0) part[it] = make_part4(X, Y, Z, 0.0);
+  }
+}
+
+// Transport sweep with consecutive lanes on consecutive channels: a warp's 32 channels share
+// about 32/nmodes partners, so each F gather touches few L1 sectors; weights (8 B) and 16-bit
+// indices stay fully coalesced across the warp.  Four channels per lane per trip.
+template <typename IDX>
+__global__ void __launch_bounds__(kBlock) k_stream_tr_lane(const Item *__restrict__ items, int nitems,
+                                                           const float2 *__restrict__ W, const IDX *__restrict__ colp,
+                                                           const float2 *__restrict__ F, Part4 *__restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    const long long c0 = I.start;
+    float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f, zh = 0.f, zl = 0.f;
+    int j = lane;
+    for (; j + 96 < I.len; j += 128) {
+      float2 w[4];
+      unsigned p[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        w[k] = __ldcs(W + c0 + j + 32 * k);
+        p[k] = (unsigned)__ldcs(colp + c0 + j + 32 * k) & 0xFFFFFFu;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 *Fp = F + 3 * p[k];
+        ff_mac(xh, xl, __ldg(Fp), w[k].x, w[k].y);
+        ff_mac(yh, yl, __ldg(Fp + 1), w[k].x, w[k].y);
+        ff_mac(zh, zl, __ldg(Fp + 2), w[k].x, w[k].y);
+      }
+    }
+    for (; j < I.len; j += 32) {
+      const float2 wk = __ldcs(W + c0 + j);
+      const unsigned pk = (unsigned)__ldcs(colp + c0 + j) & 0xFFFFFFu;
+      const float2 *Fp = F + 3 * pk;
+      ff_mac(xh, xl, __ldg(Fp), wk.x, wk.y);
+      ff_mac(yh, yl, __ldg(Fp + 1), wk.x, wk.y);
+      ff_mac(zh, zl, __ldg(Fp + 2), wk.x, wk.y);
     }
     const double X = warp_sum(ff_to_double(xh, xl));
     const double Y = warp_sum(ff_to_double(yh, yl));
@@ -534,6 +588,128 @@ __global__ void __launch_bounds__(512) k_stream_g(const Item *__restrict__ items
     const double v = warp_sum((double)sum - (double)comp);
     if (lane == 0) part[it] = make_part4(v, 0.0, 0.0, 0.0);
   }
+}
+
+// The same sweep with consecutive lanes on consecutive channels: a warp's 32 channels share
+// about 32/nmodes partners, so the partner-record and phonon-table gathers touch few banks and
+// sectors; |g|^2 and the index words stay coalesced.  Four channels per lane per trip.
+template <typename G2T>
+__device__ __forceinline__ float g2_at(const G2T *__restrict__ g2v, long long i);
+template <>
+__device__ __forceinline__ float g2_at<float>(const float *__restrict__ g2v, long long i) { return __ldcs(g2v + i); }
+template <>
+__device__ __forceinline__ float g2_at<__nv_bfloat16>(const __nv_bfloat16 *__restrict__ g2v, long long i) {
+  return __uint_as_float((unsigned)__ldcs((const unsigned short *)g2v + i) << 16);
+}
+
+template <int MODE, typename G2T>
+__global__ void __launch_bounds__(512) k_stream_g_lane(const Item *__restrict__ items, int nitems, GGeom g,
+                                                       const G2T *__restrict__ g2v, const uint4 *__restrict__ gstate,
+                                                       int ns, Part4 *__restrict__ part) {
+  extern __shared__ uint4 gsl[];
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) gsl[i] = gstate[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    const uint4 ss = gsl[I.row];
+    const int base = g.cpad - (int)ss.w;
+    const long long c0 = I.start;
+    float sum = 0.f, comp = 0.f;
+    int j = lane;
+    for (; j + 96 < I.len; j += 128) {
+      unsigned cw[4];
+      float gv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        cw[k] = __ldcs(g.col + c0 + j + 32 * k);
+        gv[k] = g2_at(g2v, c0 + j + 32 * k);
+      }
+      float t[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) t[k] = g_term<MODE>(g, ss, gsl[cw[k] & 0xFFFFFFu], cw[k], base, gv[k]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) kahan_add(sum, comp, t[k]);
+    }
+    for (; j < I.len; j += 32) {
+      const unsigned cw = __ldcs(g.col + c0 + j);
+      kahan_add(sum, comp, g_term<MODE>(g, ss, gsl[cw & 0xFFFFFFu], cw, base, g2_at(g2v, c0 + j)));
+    }
+    const double v = warp_sum((double)sum - (double)comp);
+    if (lane == 0) part[it] = make_part4(v, 0.0, 0.0, 0.0);
+  }
+}
+
+// FP32 adjoint of the mixed-precision sweep.  With w_c(f_p) = g2 [G_a (N+f_p) + G_e (N+1-f_p)]
+// (the rate summand) the VJP of Eq. 2 is  (J^T lam)_x = -c sum_{row x} (lam_x - lam_p) w_c(f_p):
+// the coefficient form's c [sum lam_p (P_in + (1-f_p) D) - lam_x sum W] written per channel.
+// lam32 holds lam in FP32 (staged in shared memory after the state records).
+template <typename G2T>
+__global__ void __launch_bounds__(512) k_stream_g_vjp(const Item *__restrict__ items, int nitems, GGeom g,
+                                                      const G2T *__restrict__ g2v, const uint4 *__restrict__ gstate,
+                                                      const float *__restrict__ lam32, int ns,
+                                                      Part4 *__restrict__ part) {
+  extern __shared__ uint4 gsv[];
+  float *lsm = (float *)(gsv + ns);
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+    gsv[i] = gstate[i];
+    lsm[i] = lam32[i];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    const uint4 ss = gsv[I.row];
+    const float ls = lsm[I.row];
+    const int base = g.cpad - (int)ss.w;
+    float sum = 0.f, comp = 0.f;
+    for (int j = lane; j < I.len; j += 32) {
+      const unsigned cw = __ldcs(g.col + I.start + j);
+      const unsigned p = cw & 0xFFFFFFu;
+      const float w = g_term<MODE_RATE>(g, ss, gsv[p], cw, base, g2_at(g2v, I.start + j));
+      kahan_add(sum, comp, (ls - lsm[p]) * w);
+    }
+    const double v = warp_sum((double)sum - (double)comp);
+    if (lane == 0) part[it] = make_part4(v, 0.0, 0.0, 0.0);
+  }
+}
+
+// grad_g2[c] += scale * lam_s * [G_a F_abs + G_e F_em] (FP32 terms, FP64 accumulation), stored
+// channels in CSR order without padding; scale = -(2 pi / hbar N_q) / (sqrt(2 pi) sigma).
+__global__ void __launch_bounds__(kBlock) k_g2grad_g(const Item *__restrict__ items, int nitems, GGeom g,
+                                                     const uint4 *__restrict__ gstate,
+                                                     const long long *__restrict__ rp_pad,
+                                                     const long long *__restrict__ rp_real,
+                                                     const double *__restrict__ lam, double scale,
+                                                     double *__restrict__ grad) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    const int r = I.row;
+    const uint4 ss = __ldg(gstate + r);
+    const int base = g.cpad - (int)ss.w;
+    const long long off = I.start - rp_pad[r];
+    const long long real_len = rp_real[r + 1] - rp_real[r];
+    const double sl = scale * lam[r];
+    for (int j = lane; j < I.len; j += 32) {
+      const long long k = off + j;
+      if (k >= real_len) continue;
+      const unsigned cw = g.col[I.start + j];
+      const float t = g_term<MODE_COLL>(g, ss, __ldg(gstate + (cw & 0xFFFFFFu)), cw, base, 1.0f);
+      grad[rp_real[r] + k] += sl * (double)t;
+    }
+  }
+}
+
+__global__ void k_to_f32(const double *__restrict__ x, int n, float *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = __double2float_rn(x[i]);
 }
 
 // |g|^2 in the storage type of the mixed-precision variants (round to nearest)
@@ -720,6 +896,105 @@ __global__ void k_lincomb(int n, double a, const double *__restrict__ x, double 
                           double *__restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = a * x[i] + (y ? b * y[i] : 0.0);
+}
+
+// ------------------------------------------------------------ paper layout (ablation)
+//
+// The paper's GPU scheme (Sec. "Optimized GPU algorithm", Fig. 2): every physical channel
+// is stored once (here: under the state with the lower index), step 2 writes its
+// contribution to a per-channel array sc_col, and step 3 lets every state gather +/- sc_col
+// over its target list (the signed stargets_sources), with no atomics.  It trades half the
+// coefficient storage for an extra write and read of sc_col and a scattered gather.
+
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float bb = __fsub_rn(s, a.x);
+  float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+  err = __fadd_rn(err, __fadd_rn(a.y, b.y));
+  const float h = __fadd_rn(s, err);
+  return make_float2(h, __fsub_rn(err, __fsub_rn(h, s)));
+}
+
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  const float h = __fadd_rn(p, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, p)));
+}
+
+// sc_col[c] = f_p (P_in + f_s D) - f_s P_out for each stored channel (orientation s -> p);
+// its contribution to I_p is -sc_col[c].
+template <bool SMEM>
+__global__ void __launch_bounds__(kBlock) k_paper_sc(const Item *__restrict__ items, int nitems,
+                                                     const float4 *__restrict__ A4, const float4 *__restrict__ B4,
+                                                     const uint32_t *__restrict__ hcol,
+                                                     const float2 *__restrict__ fg, int ns, float4 *__restrict__ sc4) {
+  extern __shared__ float2 fsp[];
+  if (SMEM) {
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) fsp[i] = fg[i];
+    __syncthreads();
+  }
+  const float2 *__restrict__ fv = SMEM ? fsp : fg;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    const float2 fs = fv[I.row];
+    const long long g0 = I.start >> 2;
+    const int ng = I.len >> 2;
+    for (int g = lane; g < ng; g += 32) {
+      const long long q = g0 + g;
+      const uint4 c = partners4(hcol, q);
+      const float4 a0 = __ldcs(A4 + 2 * q), a1 = __ldcs(A4 + 2 * q + 1);
+      const float4 b0 = __ldcs(B4 + 2 * q), b1 = __ldcs(B4 + 2 * q + 1);
+      const unsigned p[4] = {c.x, c.y, c.z, c.w};
+      const float2 pin[4] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w), make_float2(a1.x, a1.y),
+                             make_float2(a1.z, a1.w)};
+      const float2 dd[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w), make_float2(b1.x, b1.y),
+                            make_float2(b1.z, b1.w)};
+      float2 out[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 fp = fv[p[k]];
+        const float2 in = ff_mul(fp, ff_add(pin[k], ff_mul(fs, dd[k])));
+        const float2 outs = ff_mul(fs, ff_add(pin[k], dd[k]));
+        out[k] = ff_add(in, make_float2(-outs.x, -outs.y));
+      }
+      __stcs(sc4 + 2 * q, make_float4(out[0].x, out[0].y, out[1].x, out[1].y));
+      __stcs(sc4 + 2 * q + 1, make_float4(out[2].x, out[2].y, out[3].x, out[3].y));
+    }
+  }
+}
+
+// part[item].x = -(sum of signed sc_col over the item's target entries); entry bit 31 = minus.
+__global__ void __launch_bounds__(kBlock) k_paper_gather(const Item *__restrict__ items, int nitems,
+                                                         const int *__restrict__ entries,
+                                                         const float2 *__restrict__ sc, Part4 *__restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int4 *__restrict__ e4 = (const int4 *)entries;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    const long long g0 = I.start >> 2;
+    const int ng = I.len >> 2;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int g = lane; g < ng; g += 32) {
+      const int4 e = __ldcs(e4 + g0 + g);
+      const int ev[4] = {e.x, e.y, e.z, e.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float2 v = __ldg(sc + (ev[k] & 0x7FFFFFFF));
+        if (ev[k] < 0) v = make_float2(-v.x, -v.y);
+        acc = ff_add(acc, v);
+      }
+    }
+    const double S = warp_sum(ff_to_double(acc.x, acc.y));
+    if (lane == 0) part[it] = make_part4(-S, 0.0, 0.0, 0.0);
+  }
 }
 
 // ------------------------------------------------------------ finalisers

@@ -130,3 +130,53 @@ def test_trajectory_gradient_finite_differences_24cubed(pb):
         an = float((gg * d).sum())
         worst = max(worst, abs(an - fd) / max(abs(fd), 1e-30))
     assert worst <= 1e-6, worst
+
+
+# ------------------------------------------------------------------ FP32 adjoint (G32 variant)
+
+def test_fp32_collision_vjp_against_fp64_oracle(pb):
+    import torch
+
+    m = synth.make_window4(16)
+    ch = pb.Channels.from_model(m)
+    dev = pb.Device(ch, variant="g32")
+    o = oracle.Oracle(m)
+    rng = np.random.default_rng(31)
+    f = rng.uniform(0, 1, o.nstate)
+    lam = rng.normal(size=o.nstate)
+    gg2 = torch.zeros(dev.nchannels, dtype=torch.float64, device="cuda")
+    g = dev.collision_vjp(T(f), T(lam), grad_g2=gg2).cpu().numpy()
+    err = nrel(g, o.collision_vjp(f, lam))
+    print(f"fp32 vjp normwise error {err:.2e}")
+    assert err <= 1e-5
+    e = ch.export()
+    rows = np.repeat(np.arange(ch.nstate), np.diff(e["row_ptr"]))
+    pick = rng.choice(ch.nchannels, size=500, replace=False)
+    ref = o.g2_grad(f, lam, rows[pick], e["col"][pick], e["nu"][pick])
+    err2 = nrel(gg2.cpu().numpy()[pick], ref)
+    print(f"fp32 g2-gradient normwise error {err2:.2e}")
+    assert err2 <= 1e-5
+
+
+def test_fp32_trajectory_gradient_against_fp64(pb):
+    """The adjoint workload in FP32 (G32): gradient of the carrier energy after 200 RK4 steps
+    against the FP64-accurate (FF) gradient."""
+    import torch
+    from paper_2511_03683_gb300 import autograd as pa
+
+    m = synth.make_config("window24")
+    ch = pb.Channels.from_model(m)
+    ids = ch.state_ids()
+    eps = torch.tensor(m.eps.reshape(-1)[ids], device="cuda")
+    grads = {}
+    for v in ("ff", "g32"):
+        dev = pb.Device(ch, variant=v)
+        f0 = torch.tensor(m.f_hot().reshape(-1)[ids], device="cuda", requires_grad=True)
+        g2 = pa.g2_tensor(ch).requires_grad_(True)
+        (eps * pa.trajectory(dev, f0, g2, 1.0, 200, 20)).sum().backward()
+        grads[v] = (f0.grad.cpu().numpy(), g2.grad.cpu().numpy())
+        dev.close()
+    ef = nrel(grads["g32"][0], grads["ff"][0])
+    eg = nrel(grads["g32"][1], grads["ff"][1])
+    print(f"fp32 trajectory gradient errors: f0 {ef:.2e}, g2 {eg:.2e}")
+    assert ef <= 1e-4 and eg <= 1e-4

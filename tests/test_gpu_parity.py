@@ -111,6 +111,34 @@ def test_rk4_tiny_workload(pb, variant):
     assert np.array_equal(out, ft.cpu().numpy())
 
 
+@pytest.mark.parametrize("name", ["tiny5", "win12", "win16", "tiny8"])
+def test_paper_layout_collision_and_rk4(pb, name):
+    """The paper's own layout (half list + sc_col + signed target gather) reaches the oracle."""
+    m, o, dev = setup_case(pb, name, "paper")
+    for f in (np.random.default_rng(7).uniform(0, 1, o.nstate), o.window_values(m.f_hot())):
+        ref, ab = o.collision(f, with_abs=True)
+        check_I(dev.collision(T(f)).cpu().numpy(), ref, ab)
+    if name == "tiny8":
+        f0 = o.window_values(m.f_hot())
+        ft = T(f0)
+        dev.rk4(ft, 1.0, 10)
+        assert nrel(ft.cpu().numpy(), o.rk4(f0, 1.0, 10)) <= TOL
+
+
+@pytest.mark.parametrize("variant", ["ff", "paper", "literal"])
+def test_cutoffs_on(pb, variant):
+    """The paper's |g| and delta cutoffs switched on: the pruned list, every layout, the
+    identically pruned oracle."""
+    m = synth.make_window4(16)
+    ch = pb.Channels.from_model(m, g2_min=5e-4, delta_nsigma=4.0)
+    o = oracle.Oracle(m, g2_min=5e-4, delta_nsigma=4.0)
+    dev = pb.Device(ch, variant=variant)
+    assert dev.nchannels == o.count_channels()
+    f = np.random.default_rng(12).uniform(0, 1, o.nstate)
+    ref, ab = o.collision(f, with_abs=True)
+    check_I(dev.collision(T(f)).cpu().numpy(), ref, ab)
+
+
 @pytest.mark.parametrize("item_channels", [64, 256, 4096])
 def test_item_split_is_invisible(pb, item_channels):
     """Rows split into many small items (ragged tails, several tiles per row) or few large
