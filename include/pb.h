@@ -56,7 +56,7 @@ enum {
   PB_ECUDA = 3,       /* a CUDA runtime call failed; message holds cudaGetErrorString */
   PB_ENOTCLOSED = 4,  /* a channel's reverse channel is missing or has a different |g|^2 */
   PB_ENOCONV = 5,     /* pb_iter_transport reached maxit above tol */
-  PB_ETIMEOUT = 6,    /* reserved: a bounded device-side wait gave up */
+  PB_ETIMEOUT = 6,    /* a bounded device-side wait gave up (reported by pb_dev_check) */
   PB_ECALLBACK = 7,   /* the |g|^2 callback returned non-zero or a negative/non-finite value */
   PB_EDEVICE = 8      /* no usable CUDA device, or it is not an sm_103 part */
 };
@@ -157,7 +157,9 @@ typedef struct pb_dev_opts {
   int32_t transport_ctas;    /* resident 256-thread transport CTAs per SM, 1..8 (0 = 8 with L1 gathers) */
   int32_t channel_per_lane;  /* FP32/BF16 sweep lane mapping: 0 automatic (= 1), 1 one channel per lane,
                                 2 four-channel groups per lane */
-  int32_t reserved;
+  int32_t stream_mode;       /* FF collision sweep: 0 automatic (= 1), 1 vector loads from global memory,
+                                2 TMA bulk copies (cp.async.bulk) into a shared-memory ring (FF variant,
+                                nstate <= 65536); its bounded waits report through pb_dev_check */
 } pb_dev_opts;
 
 typedef struct pb_dev pb_dev; /* opaque host handle describing device-resident data */
@@ -172,6 +174,10 @@ int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, void *arena, s
                   pb_dev **out);
 
 void pb_dev_destroy(pb_dev *dev);
+
+/* Synchronise `stream` and report PB_ETIMEOUT if a bounded device-side wait of an earlier
+ * launch gave up (the TMA bulk-copy sweep); PB_OK otherwise. */
+int pb_dev_check(pb_dev *dev, void *stream);
 
 typedef struct pb_dev_info {
   int64_t nstate, nchannels, nchannels_padded, nitems;

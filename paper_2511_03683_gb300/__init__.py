@@ -55,7 +55,8 @@ class _ChInfo(ctypes.Structure):
 class _DevOpts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("item_channels", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("transport", ctypes.c_int32), ("transport_gather", ctypes.c_int32),
-                ("transport_ctas", ctypes.c_int32), ("channel_per_lane", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("transport_ctas", ctypes.c_int32), ("channel_per_lane", ctypes.c_int32),
+                ("stream_mode", ctypes.c_int32)]
 
 
 class _DevInfo(ctypes.Structure):
@@ -107,6 +108,7 @@ def lib() -> ctypes.CDLL:
         "pb_dev_arena_bytes": [vp, ctypes.POINTER(_DevOpts), ctypes.POINTER(ctypes.c_size_t)],
         "pb_dev_create": [vp, ctypes.POINTER(_DevOpts), vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
         "pb_dev_get_info": [vp, ctypes.POINTER(_DevInfo)],
+        "pb_dev_check": [vp, vp],
         "pb_collision": [vp, vp, vp, vp],
         "pb_collision_static": [vp, vp, vp, vp],
         "pb_scatter_rates": [vp, vp, vp, vp],
@@ -272,7 +274,7 @@ class Device:
 
     def __init__(self, channels: Channels, variant: str = "ff", item_channels: int = 0, ctas_per_sm: int = 0,
                  transport: bool = False, transport_gather: int = 0, transport_ctas: int = 0,
-                 channel_per_lane: int = 0, stream=None):
+                 channel_per_lane: int = 0, stream_mode: int = 0, stream=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -280,7 +282,7 @@ class Device:
         self.channels = channels
         self.variant = variant
         o = _DevOpts(VARIANTS[variant], int(item_channels), int(ctas_per_sm), 1 if transport else 0,
-                     int(transport_gather), int(transport_ctas), int(channel_per_lane), 0)
+                     int(transport_gather), int(transport_ctas), int(channel_per_lane), int(stream_mode))
         nbytes = ctypes.c_size_t(0)
         _check(lib().pb_dev_arena_bytes(channels._h, ctypes.byref(o), ctypes.byref(nbytes)))
         self.arena = torch.empty(int(nbytes.value), dtype=torch.uint8, device="cuda")
@@ -309,6 +311,10 @@ class Device:
         out = self._new(self.nstate) if out is None else out
         _check(lib().pb_collision(self._h, fp, _dev_vec(out, self.nstate, "out"), _stream_ptr(stream)))
         return out
+
+    def check(self, stream=None):
+        """Synchronise and raise PBError(PB_ETIMEOUT) if a bounded device wait gave up."""
+        _check(lib().pb_dev_check(self._h, _stream_ptr(stream)))
 
     def collision_static(self, f, out, stream=None):
         """pb_collision_static: the same integral with scratch in the library's fixed

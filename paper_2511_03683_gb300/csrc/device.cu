@@ -26,7 +26,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct Layout {
   size_t rp, item_ptr, items, col, coefA, coefB, g2, wt, eps, kc, R, omega, tab, part, acc, y, yff, fstage, Fa, Fb,
       Fff, tau, invtau, red, scal, obs, g2lo, gstate, tab32, col16, rp_real, vjpG, vecs, hcol, hg2, hA, hB, sc,
-      entries, hitems, titems, t_item_ptr, total;
+      entries, hitems, titems, t_item_ptr, err, total;
 };
 
 struct Plan {
@@ -138,6 +138,7 @@ Layout make_layout(const pb_channels *ch, const Plan &P, int variant, bool trans
   L.red = take(sizeof(double2) * (size_t)nfin_blocks);
   L.scal = take(sizeof(double) * 8);
   L.obs = take(sizeof(double) * 8);
+  L.err = take(sizeof(int) * 4);
   const bool mixed = variant == PB_VARIANT_G32 || variant == PB_VARIANT_G16;
   L.g2lo = take(mixed ? (variant == PB_VARIANT_G32 ? 4 : 2) * nchp : 0);
   L.gstate = take(mixed ? 16 * ns : 0);
@@ -215,6 +216,10 @@ struct pb_dev {
   double *tau = nullptr, *invtau = nullptr;
   double2 *red = nullptr;
   double *scal = nullptr, *obs = nullptr;
+  int *err = nullptr;       // device error word (bounded waits that gave up)
+  bool bulk = false;        // collision sweep through TMA bulk copies
+  int bulk_cap = 0;         // largest work item (channels), the bulk stage capacity
+  size_t bulk_smem = 0;
   void *g2lo = nullptr;     // |g|^2 in FP32 or BF16 (mixed-precision variants)
   uint4 *gstate = nullptr;  // per-state records of the mixed-precision sweep
   float4 *tab32 = nullptr;  // padded-grid (hbar w hi, hbar w lo, N, 0) in FP32
@@ -298,12 +303,14 @@ int resolve_opts(const pb_channels *ch, const pb_dev_opts *opts, int sm_count, p
     return set_error(PB_EINVAL, "pb_dev: variant %d is not available in this build", d.variant);
   if (d.ctas_per_sm <= 0) d.ctas_per_sm = 3;  // measured best on GB300 for the coefficient sweeps
   if (d.ctas_per_sm > 8) return set_error(PB_EINVAL, "pb_dev: ctas_per_sm must be <= 8");
+  if (d.stream_mode < 0 || d.stream_mode > 2) return set_error(PB_EINVAL, "pb_dev: stream_mode must be 0..2");
   if (d.channel_per_lane < 0 || d.channel_per_lane > 2)
     return set_error(PB_EINVAL, "pb_dev: channel_per_lane must be 0..2");
   if (d.transport_gather < 0 || d.transport_gather > 3 || d.transport_ctas < 0 || d.transport_ctas > 8)
     return set_error(PB_EINVAL, "pb_dev: transport_gather must be 0..3 and transport_ctas 0..8");
   if (d.item_channels < 0 || d.item_channels % 64 != 0)
     return set_error(PB_EINVAL, "pb_dev: item_channels must be a non-negative multiple of 64");
+  if (d.item_channels == 0 && d.stream_mode == 2) d.item_channels = 2048;  // bulk ring fits shared memory
   if (d.item_channels == 0) {
     int64_t nchp = 0;
     for (int64_t r = 0; r < ch->nstate; ++r)
@@ -514,6 +521,7 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->red = (double2 *)(A + L.red);
   d->scal = (double *)(A + L.scal);
   d->obs = (double *)(A + L.obs);
+  d->err = (int *)(A + L.err);
   d->g2lo = A + L.g2lo;
   d->gstate = (uint4 *)(A + L.gstate);
   d->tab32 = (float4 *)(A + L.tab32);
@@ -560,6 +568,25 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->smem_F = (o.transport_gather == 1 && F_fits) ? Fbytes : 0;
   d->tr_lane = o.transport_gather != 2;  // 2 = L1 gathers with 4-channel groups per lane
   d->g_lane = o.channel_per_lane != 2;   // 2 = 4-channel groups per lane in the mixed-precision sweep
+  if (o.stream_mode == 2) {
+    if (d->variant != PB_VARIANT_FF || d->ns > 65536) {
+      delete d;
+      return set_error(PB_EINVAL, "pb_dev_create: the bulk-copy sweep needs the FF variant and nstate <= 65536");
+    }
+    int cap = 8;
+    for (const Item &it : P.items) cap = std::max(cap, it.len);
+    const size_t fb = ((size_t)d->ns * sizeof(float2) + 127) / 128 * 128;
+    const size_t sb = ((size_t)cap * (2 * sizeof(float2) + sizeof(uint16_t)) + 127) / 128 * 128;
+    const size_t need = fb + dev::kBulkStages * sb + (dev::kBulkStages + 1) * 8 + dev::kBulkStages * sizeof(Item) +
+                        2 * 32 * sizeof(double);
+    if (need > (size_t)smem_optin) {
+      delete d;
+      return set_error(PB_EINVAL, "pb_dev_create: bulk-copy sweep needs %zu bytes of shared memory", need);
+    }
+    d->bulk = true;
+    d->bulk_cap = cap;
+    d->bulk_smem = need;
+  }
   if (o.transport_gather == 1 && !F_fits) {
     delete d;
     return set_error(PB_EINVAL, "pb_dev_create: F of %lld states does not fit in shared memory", (long long)ch->nstate);
@@ -600,6 +627,13 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
     }                                                                                \
   } while (0)
     do {
+      {
+        cudaError_t e_ = cudaMemsetAsync(d->err, 0, sizeof(int) * 4, st);
+        if (e_ != cudaSuccess) {
+          status = cuda_fail(e_, "clear error word");
+          break;
+        }
+      }
       UP(d->rp, P.rp.data(), sizeof(int64_t) * (d->ns + 1));
       UP(d->rp_real, ch->row_ptr.data(), sizeof(int64_t) * (d->ns + 1));
       UP(d->item_ptr, P.item_ptr.data(), sizeof(int32_t) * (d->ns + 1));
@@ -665,6 +699,8 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
     delete d;
     return status;
   }
+  if (d->bulk)
+    cudaFuncSetAttribute(dev::k_stream_ff_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->bulk_smem);
   if (d->smem_f > 48 * 1024) {
     set_stream_smem<uint32_t>((int)d->smem_f);
     set_stream_smem<uint16_t>((int)d->smem_f);
@@ -701,6 +737,17 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   }
   cudaGetLastError();
   *out = d;
+  return PB_OK;
+}
+
+extern "C" int pb_dev_check(pb_dev *d, void *stream) {
+  clear_error();
+  if (!d) return set_error(PB_EINVAL, "pb_dev_check: null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  int h = 0;
+  PB_CUDA(cudaMemcpyAsync(&h, d->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PB_CUDA(cudaStreamSynchronize(st));
+  if (h) return set_error(PB_ETIMEOUT, "a bounded device-side wait gave up (error word %d)", h);
   return PB_OK;
 }
 
@@ -747,7 +794,12 @@ int launch_stream_t(pb_dev *d, int mode, const double *fd, const float2 *fff, co
   const int n = (int)d->nitems;
   const int ns = (int)d->ns;
   const bool coll = mode == dev::MODE_COLL;
-  if (d->variant == PB_VARIANT_FF) {
+  if (d->variant == PB_VARIANT_FF && coll && d->bulk) {
+    const int gb = (int)std::max<int64_t>(1, std::min<int64_t>(d->nitems, (int64_t)d->sm_count));
+    dev::k_stream_ff_bulk<<<gb, dev::kBlock, d->bulk_smem, st>>>(d->items, n, (const float2 *)d->coefA,
+                                                                 (const float2 *)d->coefB, d->col16, fff, ns,
+                                                                 d->bulk_cap, part, d->err);
+  } else if (d->variant == PB_VARIANT_FF) {
     const float4 *A4 = (const float4 *)d->coefA, *B4 = (const float4 *)d->coefB;
     if (d->smem_f) {
       if (coll) dev::k_stream_ff<dev::MODE_COLL, true, IDX><<<grid, dev::kBlock, d->smem_f, st>>>(d->items, n, A4, B4, colp, fff, ns, part);

@@ -284,6 +284,160 @@ __global__ void __launch_bounds__(kBlock) k_stream_ff(const Item *__restrict__ i
   }
 }
 
+// ------------------------------------------------------------ TMA bulk-copy form of the sweep
+//
+// The same float-float collision sweep with the stream staged through shared memory by the
+// Tensor Memory Accelerator: one thread issues 1D bulk copies (cp.async.bulk, completion
+// counted in bytes on an mbarrier) of each work item's P_in, D and 16-bit index slices into
+// a ring of NSTAGE buffers; the whole CTA consumes a buffer, reduces the item, and the buffer
+// is refilled.  Each CTA owns a contiguous range of items.  Every wait is bounded: when it
+// gives up the kernel records the failure in *err, waits (bounded) for its own copies and
+// returns; the host reads *err.
+
+constexpr int kBulkStages = 4;
+constexpr unsigned kWaitLimit = 1u << 26;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; false when the limit was reached
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+  for (unsigned i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Dynamic shared memory: f table (ns float2), then NSTAGE x [P_in | D | idx] buffers of
+// `cap` channels, then NSTAGE mbarriers and the reduction scratch.
+__global__ void __launch_bounds__(kBlock) k_stream_ff_bulk(const Item *__restrict__ items, int nitems,
+                                                           const float2 *__restrict__ A, const float2 *__restrict__ B,
+                                                           const uint16_t *__restrict__ col16,
+                                                           const float2 *__restrict__ fg, int ns, int cap,
+                                                           Part4 *__restrict__ part, int *__restrict__ err) {
+  extern __shared__ __align__(128) unsigned char bsm[];
+  float2 *fs = (float2 *)bsm;
+  const size_t fbytes = ((size_t)ns * sizeof(float2) + 127) / 128 * 128;
+  const size_t sbytes = ((size_t)cap * (2 * sizeof(float2) + sizeof(uint16_t)) + 127) / 128 * 128;
+  unsigned char *stage0 = bsm + fbytes;
+  unsigned long long *bars = (unsigned long long *)(stage0 + kBulkStages * sbytes);
+  unsigned long long *fbar = bars + kBulkStages;
+  Item *sitem = (Item *)(bars + kBulkStages + 1);   // descriptors of the items in flight
+  double *red = (double *)(sitem + kBulkStages);    // [2 * warps]
+
+  const int per = (nitems + gridDim.x - 1) / gridDim.x;
+  const int ib = blockIdx.x * per;
+  const int ie = min(nitems, ib + per);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+
+  if (tid == 0) {
+    for (int k = 0; k <= kBulkStages; ++k) mbar_init(bars + k, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  int issued = 0;  // copies issued by thread 0 (stage uses), for the drain on failure
+  auto issue = [&](const Item &I, int s) {
+    unsigned char *buf = stage0 + (size_t)s * sbytes;
+    const unsigned n8 = (unsigned)I.len * sizeof(float2), n2 = (unsigned)I.len * sizeof(uint16_t);
+    sitem[s] = I;
+    mbar_expect_tx(bars + s, 2 * n8 + n2);
+    bulk_g2s(buf, A + I.start, n8, bars + s);
+    bulk_g2s(buf + (size_t)cap * sizeof(float2), B + I.start, n8, bars + s);
+    bulk_g2s(buf + (size_t)cap * 2 * sizeof(float2), col16 + I.start, n2, bars + s);
+  };
+  // the f table, rounded up to a 16-byte multiple (the source region is padded to 256 bytes)
+  const unsigned fcopy = (unsigned)(((size_t)ns * sizeof(float2) + 15) / 16 * 16);
+  if (tid == 0) {
+    mbar_expect_tx(fbar, fcopy);
+    bulk_g2s(fs, fg, fcopy, fbar);
+    for (int it = ib; it < ie && it < ib + kBulkStages; ++it, ++issued) issue(items[it], (it - ib) % kBulkStages);
+  }
+  // every give-up decision is taken by the whole CTA at once (__syncthreads_and), so no thread
+  // is left waiting at a barrier another thread has abandoned
+  // thread 0 waits on the mbarrier (acquire); the CTA barrier then orders the staged data for
+  // every other thread, so the rest of the CTA sleeps at __syncthreads instead of spinning
+  bool ok = __syncthreads_and(tid == 0 ? mbar_wait(fbar, 0) : true);
+  for (int it = ib; it < ie && ok; ++it) {
+    const int s = (it - ib) % kBulkStages;
+    const unsigned parity = (unsigned)(((it - ib) / kBulkStages) & 1);
+    // thread 0 fetches the descriptor of the item that will refill this stage while it waits
+    Item nextI;
+    const bool refill = it + kBulkStages < ie;
+    if (tid == 0 && refill) nextI = items[it + kBulkStages];
+    if (!__syncthreads_and(tid == 0 ? mbar_wait(bars + s, parity) : true)) {
+      ok = false;
+      break;
+    }
+    const int len = sitem[s].len;
+    const unsigned char *buf = stage0 + (size_t)s * sbytes;
+    const float2 *pa = (const float2 *)buf;
+    const float2 *pd = (const float2 *)(buf + (size_t)cap * sizeof(float2));
+    const uint16_t *pc = (const uint16_t *)(buf + (size_t)cap * 2 * sizeof(float2));
+    float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;
+    for (int j = tid; j < len; j += blockDim.x) {
+      const float2 fp = fs[pc[j]];
+      const float2 a = pa[j], b = pd[j];
+      ff_mac(ah, al, fp, a.x, a.y);
+      ff_mac(bh, bl, fp, b.x, b.y);
+    }
+    double Ax = warp_sum(ff_to_double(ah, al)), Bx = warp_sum(ff_to_double(bh, bl));
+    if (lane == 0) {
+      red[2 * wid] = Ax;
+      red[2 * wid + 1] = Bx;
+    }
+    __syncthreads();  // every thread is done with buffer s and has posted its warp sums
+    if (tid == 0) {
+      if (refill) {
+        fence_proxy_async();  // order the generic-proxy reads of buffer s before the async refill
+        issue(nextI, s);
+        ++issued;
+      }
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < nw; ++w) {
+        a += red[2 * w];
+        b += red[2 * w + 1];
+      }
+      part[it] = make_part4(a, b, 0.0, 0.0);
+    }
+  }
+  if (!ok) {
+    *err = 1;
+    // drain: wait (bounded) for every copy this CTA issued before leaving
+    if (tid == 0) {
+      for (int k = 0; k < kBulkStages; ++k) {
+        const int uses = issued / kBulkStages + (k < issued % kBulkStages ? 1 : 0);
+        if (uses > 0) mbar_wait(bars + k, (unsigned)((uses - 1) & 1));
+      }
+      mbar_wait(fbar, 0);
+    }
+  }
+}
+
 // Same coefficient stream held as doubles, with native FP64 FMAs (f gathered as double).
 template <int MODE, bool SMEM, typename IDX>
 __global__ void __launch_bounds__(kBlock) k_stream_f64(const Item *__restrict__ items, int nitems,

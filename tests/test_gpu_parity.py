@@ -139,6 +139,21 @@ def test_cutoffs_on(pb, variant):
     check_I(dev.collision(T(f)).cpu().numpy(), ref, ab)
 
 
+@pytest.mark.parametrize("name", ["tiny5", "win16", "tiny8"])
+def test_bulk_copy_sweep(pb, name):
+    """The collision sweep staged by TMA bulk copies reaches the oracle; no bounded wait gave up."""
+    m, o, dev = setup_case(pb, name, "ff", stream_mode=2)
+    for f in (np.random.default_rng(7).uniform(0, 1, o.nstate), o.window_values(m.f_hot())):
+        ref, ab = o.collision(f, with_abs=True)
+        check_I(dev.collision(T(f)).cpu().numpy(), ref, ab)
+    if name == "tiny8":
+        f0 = o.window_values(m.f_hot())
+        ft = T(f0)
+        dev.rk4(ft, 1.0, 10)
+        assert nrel(ft.cpu().numpy(), o.rk4(f0, 1.0, 10)) <= TOL
+    dev.check()
+
+
 @pytest.mark.parametrize("item_channels", [64, 256, 4096])
 def test_item_split_is_invisible(pb, item_channels):
     """Rows split into many small items (ragged tails, several tiles per row) or few large
@@ -271,6 +286,16 @@ def test_full_size_mixed_precision(pb, big, variant):
     I = dev.collision(T(f)).cpu().numpy()
     check_I(I, ref, ab, tol=MIXED_TOL[variant], abs_tol=MIXED_TOL[variant])
     print(f"{variant}: normwise df/dt error {np.abs(I - ref).max() / np.abs(ref).max():.3e}")
+
+
+def test_full_size_bulk_copy_sweep(pb, big):
+    m, o, dev = big
+    bulk = pb.Device(dev.channels, variant="ff", stream_mode=2)
+    f = o.window_values(m.f_hot())
+    rows = np.unique(np.concatenate([np.arange(0, o.nstate, 53), [o.nstate - 1]]))
+    ref, ab = o.collision(f, rows=rows, with_abs=True)
+    check_I(bulk.collision(T(f)).cpu().numpy()[rows], ref, ab)
+    bulk.check()
 
 
 def test_full_size_transport_map_sampled(big):
