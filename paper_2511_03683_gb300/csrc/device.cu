@@ -247,9 +247,6 @@ struct pb_dev {
   cudaGraphExec_t rk_exec = nullptr;
   double *rk_f = nullptr;
   double rk_dt = 0.0;
-  // transport weights cache
-  const double *wt_f0 = nullptr;
-  bool wt_valid = false;
   pb::dev::ChanGeom geom() const {
     pb::dev::ChanGeom g;
     g.col = col;
