@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-ablation", action="store_true")
     ap.add_argument("--batched-instances", type=int, default=64)
-    ap.add_argument("--batched-steps", type=int, default=20)
+    ap.add_argument("--batched-steps", type=int, default=500)
     return ap.parse_args()
 
 

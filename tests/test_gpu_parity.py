@@ -307,3 +307,42 @@ def test_full_size_transport_map_sampled(big):
     rows = np.arange(5, o.nstate, 211)
     ref, _ = o.transport_map(f0, v, Fin, rows=rows)
     assert np.abs(out[rows] - ref).max() <= TOL * np.abs(ref).max()
+
+
+def test_full_size_1000_steps_two_arithmetics(pb, big):
+    """The 40^3 workload's dynamics: 1000 RK4 steps of 1 fs with the float-float default and
+    with native FP64 FMAs (independent arithmetic) agree, and the particle number sum_s f_s is
+    conserved to rounding (sum_s I_s = 0 for the closed channel list)."""
+    m, o, dev = big
+    f0 = o.window_values(m.f_hot())
+    a = T(f0)
+    dev.rk4(a, 1.0, 1000)
+    d64 = pb.Device(dev.channels, variant="f64")
+    b = T(f0)
+    d64.rk4(b, 1.0, 1000)
+    fa, fb = a.cpu().numpy(), b.cpu().numpy()
+    assert nrel(fa, fb) <= 1e-11
+    assert abs(fa.sum() - f0.sum()) <= 1e-12 * f0.sum()
+    assert fa.min() >= -1e-12 and fa.max() <= 1.0
+    # the hot carriers cool towards the lattice: carrier energy decreases
+    e = o.window_values(m.eps)
+    assert (e * fa).sum() < (e * f0).sum()
+
+
+def test_full_size_transport_solve_matches_oracle(pb, big):
+    """pb_iter_transport on the 40^3 workload for x, y, z to 1e-10 against the oracle's own
+    iteration: same iteration count (+-1), conductivity-like tensor and isotropy."""
+    m, o, dev = big
+    f0 = o.window_values(m.f_fermi(m.emin() - 0.2))
+    v = o.window_values(m.vel)
+    F, it, res, ok = dev.transport(T(f0), T(v), tol=1e-10, maxit=1000)
+    Fr, itr, resr, okr = o.transport(f0, v, tol=1e-10, maxit=1000)
+    assert ok and okr and abs(it - itr) <= 1
+    F = F.cpu().numpy()
+    w = (f0 * (1 - f0))[:, None, None]
+    S = (w * v[:, :, None] * F[:, None, :]).sum(0)
+    Sr = (w * v[:, :, None] * Fr[:, None, :]).sum(0)
+    assert np.abs(S - Sr).max() <= 1e-9 * np.abs(np.diag(Sr)).max()
+    assert nrel(F, Fr) <= 1e-8
+    d = np.diag(S)
+    assert np.abs(d - d.mean()).max() <= 1e-9 * abs(d.mean())
