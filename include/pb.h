@@ -158,8 +158,10 @@ typedef struct pb_dev_opts {
   int32_t transport_gather;  /* transport F gather: 0 automatic (= 3), 1 shared memory, 2 through L1 with
                                 4-channel groups per lane, 3 through L1 with one channel per lane */
   int32_t transport_ctas;    /* resident 256-thread transport CTAs per SM, 1..8 (0 = 8 with L1 gathers) */
-  int32_t channel_per_lane;  /* FP32/BF16 sweep lane mapping: 0 automatic (= 1), 1 one channel per lane,
-                                2 four-channel groups per lane */
+  int32_t channel_per_lane;  /* FP32/BF16 sweep shape: 0 automatic (= 4); one channel per lane in
+                                512-thread CTAs, three per SM: 1 plain, 3 with an L2 prefetch of the stream
+                                two 128-channel trips ahead; 2 four-channel groups per lane; 4 one channel
+                                per lane in one 1024-thread CTA per SM, next trip's stream in registers */
   int32_t stream_mode;       /* FF collision sweep: 0 automatic (= 1), 1 vector loads from global memory,
                                 2 TMA bulk copies (cp.async.bulk) into a shared-memory ring (FF variant,
                                 nstate <= 65536); its bounded waits report through pb_dev_check */

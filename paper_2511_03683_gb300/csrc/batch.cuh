@@ -14,7 +14,7 @@ namespace pb {
 namespace dev {
 
 struct BInst {
-  const float4 *tab;  // this instance's padded phonon table
+  const float2 *tab;  // this instance's padded phonon table
   int cpad;           // L(N1,N2,N3) * nmodes of the instance
   float k2;           // -log2(e) / (2 sigma^2)
   int soff;           // first global state of the instance
@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(512) k_stream_gbatch(const Item *__restrict__ 
     g.cpad = B.cpad;
     g.k2 = B.k2;
     const uint4 ss = __ldg(gstate + I.row);
-    const int base = B.cpad - (int)ss.w;
+    const int base = B.cpad - rec_lnm(ss);
     const uint4 *__restrict__ gsi = gstate + B.soff;
     const long long g0 = I.start >> 2;
     const int ng = I.len >> 2;
@@ -110,7 +110,7 @@ __global__ void k_fin_gbatch(const int *__restrict__ item_ptr, const Part4 *__re
     f[r] = yn;
   }
   y[r] = yn;
-  ((float *)gstate)[4 * r + 2] = __double2float_rn(yn);
+  rec_set_f(gstate + r, yn);
 }
 
 }  // namespace dev
@@ -131,7 +131,7 @@ struct pb_batch {
   uint32_t *col = nullptr;
   float *g2 = nullptr;
   uint4 *gstate = nullptr;
-  float4 *tabs = nullptr;
+  float2 *tabs = nullptr;
   pb::dev::BInst *inst = nullptr;
   double *cs = nullptr;
   Part4 *part = nullptr;
@@ -205,7 +205,7 @@ BatchLayout batch_layout(const pb_channels *const *chs, int n, int64_t ns, int64
   for (int i = 0; i < n; ++i) {
     size_t r = 1;
     for (int a = 0; a < 3; ++a) r *= (size_t)(chs[i]->nk[a] > 1 ? 2 * chs[i]->nk[a] : 1);
-    tab += align_up(sizeof(float4) * r * chs[i]->nmodes);
+    tab += align_up(sizeof(float2) * r * chs[i]->nmodes);
     maxq = std::max(maxq, (size_t)chs[i]->nq * chs[i]->nmodes);
     maxs = std::max(maxs, (size_t)chs[i]->nstate);
   }
@@ -364,7 +364,7 @@ extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const p
     b->col = (uint32_t *)(A + L.col);
     b->g2 = (float *)(A + L.g2);
     b->gstate = (uint4 *)(A + L.gstate);
-    b->tabs = (float4 *)(A + L.tabs);
+    b->tabs = (float2 *)(A + L.tabs);
     b->inst = (pb::dev::BInst *)(A + L.inst);
     b->cs = (double *)(A + L.cs);
     b->part = (Part4 *)(A + L.part);
@@ -380,7 +380,7 @@ extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const p
     std::vector<double> hcs((size_t)ns);
     std::vector<uint32_t> hcol((size_t)nchp);
     std::vector<float> hg2((size_t)nchp, 0.f);
-    size_t tab_off = 0;  // in float4
+    size_t tab_off = 0;  // in float2
     int64_t coff = 0;
     for (int i = 0; i < n && status == PB_OK; ++i) {
       const pb_channels *ch = chs[i];
@@ -391,7 +391,8 @@ extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const p
         r *= (size_t)rad[a];
       }
       const int64_t nt = (int64_t)r * ch->nmodes;
-      if ((double)nt >= 2147483647.0) status = set_error(PB_EINVAL, "pb_batch_create: instance %d table too large", i);
+      if ((double)nt >= (double)(1 << dev::kRecLnmBits))
+        status = set_error(PB_EINVAL, "pb_batch_create: instance %d needs (2 N1)(2 N2)(2 N3) nmodes < 2^27", i);
       if (ch->nk[0] > 32767 || ch->nk[1] > 32767 || ch->nk[2] > 32767)
         status = set_error(PB_EINVAL, "pb_batch_create: instance %d grid dimension above 32767", i);
       if (status) break;
@@ -439,7 +440,7 @@ extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const p
         status = cuda_fail(e, "pb_batch_create: instance setup");
         break;
       }
-      tab_off += align_up(sizeof(float4) * (size_t)nt) / sizeof(float4);
+      tab_off += align_up(sizeof(float2) * (size_t)nt) / sizeof(float2);
     }
     if (status == PB_OK) {
       cudaError_t e = cudaMemcpyAsync(b->inst, hin.data(), sizeof(pb::dev::BInst) * n, cudaMemcpyHostToDevice, st);

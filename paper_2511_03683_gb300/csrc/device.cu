@@ -143,7 +143,7 @@ Layout make_layout(const pb_channels *ch, const Plan &P, int variant, bool trans
   L.g2lo = take(mixed ? (variant == PB_VARIANT_G32 ? 4 : 2) * nchp : 0);
   L.gstate = take(mixed ? 16 * ns : 0);
   auto rad = [](int n) { return (size_t)(n > 1 ? 2 * n : 1); };
-  L.tab32 = take(mixed ? sizeof(float4) * rad(ch->nk[0]) * rad(ch->nk[1]) * rad(ch->nk[2]) * ch->nmodes : 0);
+  L.tab32 = take(mixed ? sizeof(float2) * rad(ch->nk[0]) * rad(ch->nk[1]) * rad(ch->nk[2]) * ch->nmodes : 0);
   L.col16 = take(ns <= 65536 ? sizeof(uint16_t) * nchp : 0);
   PaperSizes z;
   if (variant == PB_VARIANT_PAPER) z = paper_sizes(ch);
@@ -181,6 +181,45 @@ int cuda_fail(cudaError_t e, const char *what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, what);          \
   } while (0)
 
+}  // namespace
+
+namespace {
+// Mixed-precision lane-sweep shapes (pb_dev_opts.channel_per_lane): 1 = 512 threads, three
+// CTAs per SM; 3 = the same with an L2 prefetch two trips ahead; 4 = one 1024-thread CTA per
+// SM with the next trip's stream words in registers.
+template <typename G2T>
+void set_lane_smem(int bytes) {
+  using namespace pb::dev;
+  const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaFuncSetAttribute(k_stream_g_lane<MODE_COLL, G2T, 0, 512, false>, A, bytes);
+  cudaFuncSetAttribute(k_stream_g_lane<MODE_RATE, G2T, 0, 512, false>, A, bytes);
+  cudaFuncSetAttribute(k_stream_g_lane<MODE_COLL, G2T, 2, 512, false>, A, bytes);
+  cudaFuncSetAttribute(k_stream_g_lane<MODE_RATE, G2T, 2, 512, false>, A, bytes);
+  cudaFuncSetAttribute(k_stream_g_lane<MODE_COLL, G2T, 0, 1024, true>, A, bytes);
+  cudaFuncSetAttribute(k_stream_g_lane<MODE_RATE, G2T, 0, 1024, true>, A, bytes);
+}
+
+template <int PF, int NT, bool RP, typename G2T>
+void launch_g_lane_t(bool coll, int grid, size_t smem, cudaStream_t st, const pb::dev::Item *items, int n,
+                     const pb::dev::GGeom &g, const G2T *g2, const uint4 *gstate, int ns, pb::dev::Part4 *part) {
+  using namespace pb::dev;
+  if (coll) k_stream_g_lane<MODE_COLL, G2T, PF, NT, RP><<<grid, NT, smem, st>>>(items, n, g, g2, gstate, ns, part);
+  else      k_stream_g_lane<MODE_RATE, G2T, PF, NT, RP><<<grid, NT, smem, st>>>(items, n, g, g2, gstate, ns, part);
+}
+
+// grid512: the grid of 512-thread CTAs; the 1024-thread shape runs one CTA per SM
+template <typename G2T>
+void launch_g_lane(int shape, bool coll, int grid512, int sm_count, size_t smem, cudaStream_t st,
+                   const pb::dev::Item *items, int n, const pb::dev::GGeom &g, const G2T *g2, const uint4 *gstate,
+                   int ns, pb::dev::Part4 *part) {
+  if (shape == 4)
+    launch_g_lane_t<0, 1024, true>(coll, std::max(1, std::min(sm_count, (n * 32 + 1023) / 1024)), smem, st, items, n,
+                                   g, g2, gstate, ns, part);
+  else if (shape == 3)
+    launch_g_lane_t<2, 512, false>(coll, grid512, smem, st, items, n, g, g2, gstate, ns, part);
+  else
+    launch_g_lane_t<0, 512, false>(coll, grid512, smem, st, items, n, g, g2, gstate, ns, part);
+}
 }  // namespace
 
 struct pb_dev {
@@ -221,8 +260,9 @@ struct pb_dev {
   int bulk_cap = 0;         // largest work item (channels), the bulk stage capacity
   size_t bulk_smem = 0;
   void *g2lo = nullptr;     // |g|^2 in FP32 or BF16 (mixed-precision variants)
-  uint4 *gstate = nullptr;  // per-state records of the mixed-precision sweep
-  float4 *tab32 = nullptr;  // padded-grid (hbar w hi, hbar w lo, N, 0) in FP32
+  uint4 *gstate = nullptr;  // per-state records of the mixed-precision sweep (eps, f, grid index)
+  bool vjp_g_ok = false;    // the mixed-precision adjoint's 20 bytes per state fit in shared memory
+  float2 *tab32 = nullptr;  // padded-grid (hbar w, N) in FP32
   uint16_t *col16 = nullptr;  // 16-bit partner indices (nstate <= 65536), else null
   int64_t *rp_real = nullptr;  // unpadded CSR row offsets [ns+1]
   float2 *vjpG = nullptr;      // adjoint gather table [ns][3]
@@ -242,6 +282,7 @@ struct pb_dev {
   size_t smem_G = 0;      // dynamic smem of the adjoint gather table
   bool tr_lane = true;    // L1-gather transport with consecutive lanes on consecutive channels
   bool g_lane = true;     // mixed-precision sweep with consecutive lanes on consecutive channels
+  int g_shape = 1;        // its launch shape (pb_dev_opts.channel_per_lane: 1, 3 or 4)
   // RK4 graph cache
   cudaStream_t cap = nullptr;
   cudaGraphExec_t rk_exec = nullptr;
@@ -301,8 +342,8 @@ int resolve_opts(const pb_channels *ch, const pb_dev_opts *opts, int sm_count, p
   if (d.ctas_per_sm <= 0) d.ctas_per_sm = 3;  // measured best on GB300 for the coefficient sweeps
   if (d.ctas_per_sm > 8) return set_error(PB_EINVAL, "pb_dev: ctas_per_sm must be <= 8");
   if (d.stream_mode < 0 || d.stream_mode > 2) return set_error(PB_EINVAL, "pb_dev: stream_mode must be 0..2");
-  if (d.channel_per_lane < 0 || d.channel_per_lane > 2)
-    return set_error(PB_EINVAL, "pb_dev: channel_per_lane must be 0..2");
+  if (d.channel_per_lane < 0 || d.channel_per_lane > 4)
+    return set_error(PB_EINVAL, "pb_dev: channel_per_lane must be 0..4");
   if (d.transport_gather < 0 || d.transport_gather > 3 || d.transport_ctas < 0 || d.transport_ctas > 8)
     return set_error(PB_EINVAL, "pb_dev: transport_gather must be 0..3 and transport_ctas 0..8");
   if (d.item_channels < 0 || d.item_channels % 64 != 0)
@@ -521,7 +562,7 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->err = (int *)(A + L.err);
   d->g2lo = A + L.g2lo;
   d->gstate = (uint4 *)(A + L.gstate);
-  d->tab32 = (float4 *)(A + L.tab32);
+  d->tab32 = (float2 *)(A + L.tab32);
   d->col16 = d->ns <= 65536 ? (uint16_t *)(A + L.col16) : nullptr;
   d->rp_real = (int64_t *)(A + L.rp_real);
   d->vjpG = (float2 *)(A + L.vjpG);
@@ -549,9 +590,10 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
                                   "%lld states exceed it", (long long)ch->nstate);
     }
     for (int i = 0; i < 3; ++i) d->rad[i] = ch->nk[i] > 1 ? 2 * ch->nk[i] : 1;
-    if ((double)d->rad[0] * d->rad[1] * d->rad[2] * ch->nmodes >= 2147483647.0) {
+    if ((double)d->rad[0] * d->rad[1] * d->rad[2] * ch->nmodes >= (double)(1 << dev::kRecLnmBits)) {
       delete d;
-      return set_error(PB_EINVAL, "pb_dev_create: padded phonon table too large for 32-bit indices");
+      return set_error(PB_EINVAL, "pb_dev_create: the FP32/BF16 variants need (2 N1)(2 N2)(2 N3) nmodes < 2^27 "
+                                  "(padded phonon table index in the state records)");
     }
     d->ctas = (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(228 * 1024) / (fbytes + 1024)));  // of 512 threads
   }
@@ -565,6 +607,9 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->smem_F = (o.transport_gather == 1 && F_fits) ? Fbytes : 0;
   d->tr_lane = o.transport_gather != 2;  // 2 = L1 gathers with 4-channel groups per lane
   d->g_lane = o.channel_per_lane != 2;   // 2 = 4-channel groups per lane in the mixed-precision sweep
+  // automatic: one 1024-thread CTA per SM with register prefetch (measured fastest on GB300
+  // for both FP32 and BF16 |g|^2 at 40^3: 0.29 ms against 0.35-0.38 ms for the 512-thread shapes)
+  d->g_shape = o.channel_per_lane == 0 ? 4 : o.channel_per_lane >= 3 ? o.channel_per_lane : 1;
   if (o.stream_mode == 2) {
     if (d->variant != PB_VARIANT_FF || d->ns > 65536) {
       delete d;
@@ -716,17 +761,16 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
     d->smem_G = gb + 1024 <= (size_t)smem_optin ? gb : 0;
   }
   if (d->mixed()) {
-    const int vb = (int)((sizeof(uint4) + sizeof(float)) * (size_t)d->ns);
-    if (vb > 48 * 1024) {
-      cudaFuncSetAttribute(dev::k_stream_g_vjp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, vb);
-      cudaFuncSetAttribute(dev::k_stream_g_vjp<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, vb);
+    const size_t vb = (sizeof(uint4) + sizeof(float)) * (size_t)d->ns;
+    d->vjp_g_ok = vb + 1024 <= (size_t)smem_optin;
+    if (vb > 48 * 1024 && d->vjp_g_ok) {
+      cudaFuncSetAttribute(dev::k_stream_g_vjp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vb);
+      cudaFuncSetAttribute(dev::k_stream_g_vjp<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vb);
     }
   }
   if (d->mixed() && d->smem_f > 48 * 1024) {
-    cudaFuncSetAttribute(dev::k_stream_g_lane<dev::MODE_COLL, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
-    cudaFuncSetAttribute(dev::k_stream_g_lane<dev::MODE_RATE, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
-    cudaFuncSetAttribute(dev::k_stream_g_lane<dev::MODE_COLL, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
-    cudaFuncSetAttribute(dev::k_stream_g_lane<dev::MODE_RATE, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
+    set_lane_smem<float>((int)d->smem_f);
+    set_lane_smem<__nv_bfloat16>((int)d->smem_f);
     cudaFuncSetAttribute(dev::k_stream_g<dev::MODE_COLL, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
     cudaFuncSetAttribute(dev::k_stream_g<dev::MODE_RATE, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
     cudaFuncSetAttribute(dev::k_stream_g<dev::MODE_COLL, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
@@ -833,13 +877,11 @@ int launch_stream_t(pb_dev *d, int mode, const double *fd, const float2 *fff, co
     const float *g32 = (const float *)d->g2lo;
     const __nv_bfloat16 *g16 = (const __nv_bfloat16 *)d->g2lo;
     if (d->g_lane) {
-      if (d->variant == PB_VARIANT_G32) {
-        if (coll) dev::k_stream_g_lane<dev::MODE_COLL, float><<<gg, 512, d->smem_f, st>>>(d->items, n, g, g32, d->gstate, ns, part);
-        else      dev::k_stream_g_lane<dev::MODE_RATE, float><<<gg, 512, d->smem_f, st>>>(d->items, n, g, g32, d->gstate, ns, part);
-      } else {
-        if (coll) dev::k_stream_g_lane<dev::MODE_COLL, __nv_bfloat16><<<gg, 512, d->smem_f, st>>>(d->items, n, g, g16, d->gstate, ns, part);
-        else      dev::k_stream_g_lane<dev::MODE_RATE, __nv_bfloat16><<<gg, 512, d->smem_f, st>>>(d->items, n, g, g16, d->gstate, ns, part);
-      }
+      if (d->variant == PB_VARIANT_G32)
+        launch_g_lane<float>(d->g_shape, coll, gg, d->sm_count, d->smem_f, st, d->items, n, g, g32, d->gstate, ns, part);
+      else
+        launch_g_lane<__nv_bfloat16>(d->g_shape, coll, gg, d->sm_count, d->smem_f, st, d->items, n, g, g16, d->gstate,
+                                     ns, part);
     } else if (d->variant == PB_VARIANT_G32) {
       if (coll) dev::k_stream_g<dev::MODE_COLL, float><<<gg, 512, d->smem_f, st>>>(d->items, n, g, g32, d->gstate, ns, part);
       else      dev::k_stream_g<dev::MODE_RATE, float><<<gg, 512, d->smem_f, st>>>(d->items, n, g, g32, d->gstate, ns, part);
@@ -1145,6 +1187,9 @@ int coef_setup(pb_dev *d, cudaStream_t st) {
 int vjp_launch_mixed(pb_dev *d, const double *f, const double *lam, double *grad_f, double *grad_g2,
                      cudaStream_t st) {
   const int ns = (int)d->ns, n = (int)d->nitems;
+  if (!d->vjp_g_ok)
+    return set_error(PB_EINVAL, "pb_collision_vjp: the FP32/BF16 adjoint stages 20 bytes per state in shared "
+                                "memory; %d states exceed it", ns);
   int rc = stage_input(d, f, st);
   if (rc) return rc;
   float *lam32 = (float *)d->vjpG;  // ns floats fit in the [ns][3] float2 table

@@ -628,11 +628,17 @@ __global__ void __launch_bounds__(kBlock) k_stream_tr_lane(const Item *__restric
 // ------------------------------------------------------------ mixed precision (FP32 / BF16 |g|^2)
 //
 // The literal per-channel form of Eq. 2 in FP32: stream |g|^2 (FP32 or BF16) and the packed
-// (partner, branch) word; gather the partner's record (energy as a float-float pair,
-// occupation in FP32, padded grid index) from shared memory and (hbar w hi, hbar w lo, N)
-// from an FP32 table in L2; evaluate the two Gaussians with ex2 and F_abs / F_em in
+// (partner, branch) word; gather the partner's 16-byte record (energy and occupation, each as
+// a hi + lo pair, and its padded grid index) from shared memory and (hbar w, N) from an FP32
+// table in L2; evaluate the two Gaussians with ex2 and F_abs / F_em in
 // registers; accumulate each lane with Kahan compensation.  Partials, finalisers, RK4 and
 // transport stay FP64.
+//
+// The occupations enter at FP32 precision plus a first-order correction from their low
+// parts.  Rounding f to FP32 alone would perturb every term of a row by the same relative
+// amount (and every term with partner p likewise), an error that does not average out over
+// the row: d I_s / d f_s = -1/tau_s is large while I_s itself shrinks as f relaxes.  The
+// correction removes it at the cost of a few FMAs per channel.
 //
 // Phonon table index without a modulo: the table is laid out on a padded grid of radix
 // R_i = 2 N_i (R_i = 1 when N_i = 1), indexed by D_i = j_p,i - j_s,i + N_i in [1, 2 N_i).
@@ -642,10 +648,29 @@ __global__ void __launch_bounds__(kBlock) k_stream_tr_lane(const Item *__restric
 
 struct GGeom {
   const uint32_t *col;
-  const float4 *tabp;  // padded [R1 R2 R3][nmodes] (w hi, w lo, N, 0)
+  const float2 *tabp;  // padded [R1 R2 R3][nmodes] (hbar w, N)
   int cpad;            // L(N1, N2, N3) * nmodes
   float k2;            // -log2(e) / (2 sigma^2)
 };
+
+// Per-state record of the mixed-precision sweeps (16 bytes, one shared-memory load):
+//   .x  eps hi (FP32)
+//   .y  eps lo rounded to 12 significand bits; its low 11 bits hold bits 16..26 of L * nmodes
+//   .z  f hi (FP32)
+//   .w  high half: f lo as BF16; low half: bits 0..15 of L * nmodes
+// eps lo keeps eps to about 2^-36 relative (1e-11 eV at 1 eV, far inside sigma^2 / |x +- w|)
+// and f lo keeps f to about 2^-33; L * nmodes must stay below 2^27.
+constexpr int kRecLnmBits = 27;
+__device__ __forceinline__ int rec_lnm(uint4 r) { return (int)((r.w & 0xFFFFu) | ((r.y & 0x7FFu) << 16)); }
+__device__ __forceinline__ float rec_eps_lo(uint4 r) { return __uint_as_float(r.y & 0xFFFFF800u); }
+__device__ __forceinline__ float rec_f_lo(uint4 r) { return __uint_as_float(r.w & 0xFFFF0000u); }
+// f hi and the BF16 f lo; the grid-index bits in the low half of .w are left in place
+__device__ __forceinline__ void rec_set_f(uint4 *rec, double f) {
+  const float h = __double2float_rn(f);
+  const float l = __double2float_rn(f - (double)h);
+  reinterpret_cast<float *>(rec)[2] = h;
+  reinterpret_cast<unsigned short *>(rec)[7] = __bfloat16_as_ushort(__float2bfloat16_rn(l));
+}
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
@@ -661,28 +686,36 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float t) {
 }
 
 // One channel: g2 * [G_a F_abs + G_e F_em] (MODE_COLL) or g2 * [G_a (N+f_p) + G_e (N+1-f_p)]
-// without the Gaussian normalisation.  ss/sp: row and partner records; base = cpad - L_s nm.
+// without the Gaussian normalisation.  ss/sp: row and partner records; base = cpad - L_s nmodes.
 template <int MODE>
 __device__ __forceinline__ float g_term(const GGeom &g, uint4 ss, uint4 sp, uint32_t cw, int base, float g2) {
-  const float4 t = __ldg(g.tabp + (base + (int)sp.w + (int)(cw >> 24)));
+  const float2 t = __ldg(g.tabp + (base + rec_lnm(sp) + (int)(cw >> 24)));
   const float dh = __fsub_rn(__uint_as_float(ss.x), __uint_as_float(sp.x));
-  const float dl = __fsub_rn(__uint_as_float(ss.y), __uint_as_float(sp.y));
-  const float a = (dh + t.x) + (dl + t.y);  // x + w
-  const float e = (dh - t.x) + (dl - t.y);  // x - w
+  const float dl = __fsub_rn(rec_eps_lo(ss), rec_eps_lo(sp));
+  const float a = (dh + t.x) + dl;  // x + w
+  const float e = (dh - t.x) + dl;  // x - w
   const float Ga = ex2_approx(a * a * g.k2);
   const float Ge = ex2_approx(e * e * g.k2);
-  const float fs = __uint_as_float(ss.z), fp = __uint_as_float(sp.z), N = t.z;
+  const float fs = __uint_as_float(ss.z), fp = __uint_as_float(sp.z), N = t.y;
+  const float fpl = rec_f_lo(sp);
+  const float S = Ga + Ge, Dg = Ga - Ge, GN = S * N;
   if (MODE == MODE_COLL) {
+    // u = f_s [GN + G_e] - f_p [GN + G_a] + f_s f_p (G_a - G_e), evaluated as
     // F_abs = (f_s - f_p) N - B,  F_em = (f_s - f_p) N + A,  A = f_s (1-f_p), B = (1-f_s) f_p
     const float P = fs * fp;
     const float A = fs - P, B = fp - P;
     const float DN = (fs - fp) * N;
-    float u = (Ga + Ge) * DN;
+    float u = S * DN;
     u = fmaf(Ge, A, u);
     u = fmaf(-Ga, B, u);
+    // low parts of f: du/df_s = GN + G_e + f_p (G_a - G_e), du/df_p = -(GN + G_a) + f_s (G_a - G_e)
+    const float Xc = fmaf(fp, Dg, GN + Ge);
+    const float Yc = fmaf(-fs, Dg, GN + Ga);
+    u = fmaf(rec_f_lo(ss), Xc, u);
+    u = fmaf(-fpl, Yc, u);
     return g2 * u;
   }
-  return g2 * fmaf(Ga - Ge, fp, (Ga + Ge) * N + Ge);
+  return g2 * fmaf(Dg, fpl, fmaf(Dg, fp, GN + Ge));
 }
 
 // four consecutive |g|^2 values as FP32 (a 16-byte FP32 load or an 8-byte BF16 load)
@@ -709,7 +742,7 @@ __global__ void __launch_bounds__(512) k_stream_g(const Item *__restrict__ items
   for (int it = warp; it < nitems; it += nwarps) {
     const Item I = items[it];
     const uint4 ss = gs[I.row];
-    const int base = g.cpad - (int)ss.w;
+    const int base = g.cpad - rec_lnm(ss);
     const long long g0 = I.start >> 2;
     const int ng = I.len >> 2;
     float sum = 0.f, comp = 0.f;
@@ -756,10 +789,42 @@ __device__ __forceinline__ float g2_at<__nv_bfloat16>(const __nv_bfloat16 *__res
   return __uint_as_float((unsigned)__ldcs((const unsigned short *)g2v + i) << 16);
 }
 
-template <int MODE, typename G2T>
-__global__ void __launch_bounds__(512) k_stream_g_lane(const Item *__restrict__ items, int nitems, GGeom g,
-                                                       const G2T *__restrict__ g2v, const uint4 *__restrict__ gstate,
-                                                       int ns, Part4 *__restrict__ part) {
+// L2 prefetch of the 128-channel trip that starts at channel c (inside the item): lanes 0-3
+// take the four 128-byte lines of the index words, the next lanes those of |g|^2.
+template <typename G2T>
+__device__ __forceinline__ void prefetch_trip(const uint32_t *__restrict__ col, const G2T *__restrict__ g2v,
+                                              long long c, int avail, int lane) {
+  constexpr int kG2Lines = (int)(128 * sizeof(G2T) / 128);
+  const void *a = nullptr;
+  if (lane < 4) {
+    if (32 * lane < avail) a = col + c + 32 * lane;
+  } else if (lane < 4 + kG2Lines) {
+    const int k = lane - 4, per = 128 / (int)sizeof(G2T);
+    if (per * k < avail) a = g2v + c + per * k;
+  }
+  if (a) asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
+// Stream words and |g|^2 of one 128-channel trip (lane takes channels j, j+32, j+64, j+96).
+template <typename G2T>
+__device__ __forceinline__ void load_trip(const uint32_t *__restrict__ col, const G2T *__restrict__ g2v, long long c,
+                                          unsigned (&cw)[4], float (&gv)[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    cw[k] = __ldcs(col + c + 32 * k);
+    gv[k] = g2_at(g2v, c + 32 * k);
+  }
+}
+
+// PF > 0: each trip first prefetches, into L2, the trip PF ahead in the same item.
+// RP: the next trip's stream words are loaded into registers before this trip's gathers and
+// arithmetic, so that their HBM latency overlaps this trip (used with NT = 1024: one CTA per
+// SM, which leaves most of L1 to the phonon-table gathers and 64 registers per thread).
+template <int MODE, typename G2T, int PF, int NT, bool RP>
+__global__ void __launch_bounds__(NT, NT == 512 ? 3 : 1) k_stream_g_lane(const Item *__restrict__ items, int nitems, GGeom g,
+                                                         const G2T *__restrict__ g2v,
+                                                         const uint4 *__restrict__ gstate, int ns,
+                                                         Part4 *__restrict__ part) {
   extern __shared__ uint4 gsl[];
   for (int i = threadIdx.x; i < ns; i += blockDim.x) gsl[i] = gstate[i];
   __syncthreads();
@@ -769,27 +834,48 @@ __global__ void __launch_bounds__(512) k_stream_g_lane(const Item *__restrict__ 
   for (int it = warp; it < nitems; it += nwarps) {
     const Item I = items[it];
     const uint4 ss = gsl[I.row];
-    const int base = g.cpad - (int)ss.w;
+    const int base = g.cpad - rec_lnm(ss);
     const long long c0 = I.start;
     float sum = 0.f, comp = 0.f;
+    if (PF > 0)
+      for (int k = 1; k < PF; ++k)
+        if (128 * k < I.len) prefetch_trip(g.col, g2v, c0 + 128 * k, I.len - 128 * k, lane);
     int j = lane;
-    for (; j + 96 < I.len; j += 128) {
-      unsigned cw[4];
-      float gv[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        cw[k] = __ldcs(g.col + c0 + j + 32 * k);
-        gv[k] = g2_at(g2v, c0 + j + 32 * k);
+    bool full = j + 96 < I.len;
+    unsigned cw[4] = {0u, 0u, 0u, 0u};
+    float gv[4] = {0.f, 0.f, 0.f, 0.f};
+    if (RP && full) load_trip(g.col, g2v, c0 + j, cw, gv);
+    while (full) {
+      if (PF > 0) {
+        const int nx = j - lane + 128 * PF;
+        if (nx < I.len) prefetch_trip(g.col, g2v, c0 + nx, I.len - nx, lane);
+      }
+      const bool nfull = j + 128 + 96 < I.len;
+      unsigned cn[4];
+      float gn[4];
+      if (RP) {
+        if (nfull) load_trip(g.col, g2v, c0 + j + 128, cn, gn);
+      } else {
+        load_trip(g.col, g2v, c0 + j, cw, gv);
       }
       float t[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) t[k] = g_term<MODE>(g, ss, gsl[cw[k] & 0xFFFFFFu], cw[k], base, gv[k]);
+      // one compensated add per trip; the four-term partial sum rounds like any term
+      kahan_add(sum, comp, (t[0] + t[1]) + (t[2] + t[3]));
+      if (RP && nfull) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) kahan_add(sum, comp, t[k]);
+        for (int k = 0; k < 4; ++k) {
+          cw[k] = cn[k];
+          gv[k] = gn[k];
+        }
+      }
+      j += 128;
+      full = nfull;
     }
     for (; j < I.len; j += 32) {
-      const unsigned cw = __ldcs(g.col + c0 + j);
-      kahan_add(sum, comp, g_term<MODE>(g, ss, gsl[cw & 0xFFFFFFu], cw, base, g2_at(g2v, c0 + j)));
+      const unsigned c = __ldcs(g.col + c0 + j);
+      kahan_add(sum, comp, g_term<MODE>(g, ss, gsl[c & 0xFFFFFFu], c, base, g2_at(g2v, c0 + j)));
     }
     const double v = warp_sum((double)sum - (double)comp);
     if (lane == 0) part[it] = make_part4(v, 0.0, 0.0, 0.0);
@@ -819,7 +905,7 @@ __global__ void __launch_bounds__(512) k_stream_g_vjp(const Item *__restrict__ i
     const Item I = items[it];
     const uint4 ss = gsv[I.row];
     const float ls = lsm[I.row];
-    const int base = g.cpad - (int)ss.w;
+    const int base = g.cpad - rec_lnm(ss);
     float sum = 0.f, comp = 0.f;
     for (int j = lane; j < I.len; j += 32) {
       const unsigned cw = __ldcs(g.col + I.start + j);
@@ -847,7 +933,7 @@ __global__ void __launch_bounds__(kBlock) k_g2grad_g(const Item *__restrict__ it
     const Item I = items[it];
     const int r = I.row;
     const uint4 ss = __ldg(gstate + r);
-    const int base = g.cpad - (int)ss.w;
+    const int base = g.cpad - rec_lnm(ss);
     const long long off = I.start - rp_pad[r];
     const long long real_len = rp_real[r + 1] - rp_real[r];
     const double sl = scale * lam[r];
@@ -855,7 +941,8 @@ __global__ void __launch_bounds__(kBlock) k_g2grad_g(const Item *__restrict__ it
       const long long k = off + j;
       if (k >= real_len) continue;
       const unsigned cw = g.col[I.start + j];
-      const float t = g_term<MODE_COLL>(g, ss, __ldg(gstate + (cw & 0xFFFFFFu)), cw, base, 1.0f);
+      const unsigned p = cw & 0xFFFFFFu;
+      const float t = g_term<MODE_COLL>(g, ss, __ldg(gstate + p), cw, base, 1.0f);
       grad[rp_real[r] + k] += sl * (double)t;
     }
   }
@@ -877,21 +964,24 @@ __global__ void k_cvt_g2(const double *__restrict__ g2, long long n, G2T *__rest
   }
 }
 
-// Per-state records of the mixed-precision sweep: eps as a float-float pair, padded grid
-// index times nmodes.
+// Per-state records of the mixed-precision sweep (layout above rec_lnm); f is written per stage.
 __global__ void k_gstate_init(const double *__restrict__ eps, const short4 *__restrict__ kc, int n, int R2, int R3,
                               int nmodes, uint4 *__restrict__ gstate) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float2 e = ff_split(eps[i]);
   const short4 k = kc[i];
-  const int L = ((int)k.x * R2 + (int)k.y) * R3 + (int)k.z;
-  gstate[i] = make_uint4(__float_as_uint(e.x), __float_as_uint(e.y), 0u, (unsigned)(L * nmodes));
+  const unsigned L = (unsigned)((((int)k.x * R2 + (int)k.y) * R3 + (int)k.z) * nmodes);
+  const unsigned lo = (__float_as_uint(e.y) + 0x400u) & 0xFFFFF800u;  // 12 significand bits, rounded
+  gstate[i] = make_uint4(__float_as_uint(e.x), lo | ((L >> 16) & 0x7FFu), 0u, L & 0xFFFFu);
 }
 
-// Padded phonon table: entry (D1, D2, D3, nu) holds q = (D_i - N_i) mod N_i.
+// Padded phonon table: entry (D1, D2, D3, nu) holds (hbar w, N) in FP32 for
+// q = (D_i - N_i) mod N_i.  The energy needs no low part: its FP32 rounding (below 2e-9 eV
+// for hbar w < 0.06 eV) perturbs each Gaussian by under 1e-6 of itself, pseudo-randomly
+// across (q, nu), well below the FP32 error of the terms.
 __global__ void k_tab_padded(const double2 *__restrict__ tab, int N1, int N2, int N3, int R1, int R2, int R3,
-                             int nmodes, float4 *__restrict__ out) {
+                             int nmodes, float2 *__restrict__ out) {
   const long long n = (long long)R1 * R2 * R3 * nmodes;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const int nu = (int)(i % nmodes);
@@ -904,15 +994,14 @@ __global__ void k_tab_padded(const double2 *__restrict__ tab, int N1, int N2, in
     const int q2 = ((D2 - (R2 > 1 ? N2 : 0)) % N2 + N2) % N2;
     const int q3 = ((D3 - (R3 > 1 ? N3 : 0)) % N3 + N3) % N3;
     const double2 wN = tab[((long long)(q1 * N2 + q2) * N3 + q3) * nmodes + nu];
-    const float wh = __double2float_rn(wN.x);
-    out[i] = make_float4(wh, __double2float_rn(wN.x - (double)wh), __double2float_rn(wN.y), 0.f);
+    out[i] = make_float2(__double2float_rn(wN.x), __double2float_rn(wN.y));
   }
 }
 
-// gstate.z = (float) f  (the stage input of the mixed-precision sweep)
+// f into the records (the stage input of the mixed-precision sweep)
 __global__ void k_gstate_f(const double *__restrict__ f, int n, uint4 *__restrict__ gstate) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) ((float *)gstate)[4 * i + 2] = __double2float_rn(f[i]);
+  if (i < n) rec_set_f(gstate + i, f[i]);
 }
 
 // ------------------------------------------------------------ adjoint (reverse mode)
@@ -1199,7 +1288,7 @@ __global__ void k_fin_coll(const int *__restrict__ item_ptr, const Part4 *__rest
   }
   y[r] = yn;
   if (GSTATE)
-    ((float *)yff)[4 * r + 2] = __double2float_rn(yn);  // yff points at the uint4 gstate array
+    rec_set_f(reinterpret_cast<uint4 *>(yff) + r, yn);  // yff points at the uint4 record array
   else
     yff[r] = ff_split(yn);
 }
