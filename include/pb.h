@@ -155,8 +155,11 @@ typedef struct pb_dev_opts {
   int32_t item_channels;     /* channels per work item (multiple of 64; 0 = automatic, 256..4096) */
   int32_t ctas_per_sm;       /* resident CTAs per SM for the coefficient sweeps (0 = 3) */
   int32_t transport;         /* nonzero: reserve transport buffers (weights and F) */
-  int32_t transport_gather;  /* transport F gather: 0 automatic (= 3), 1 shared memory, 2 through L1 with
-                                4-channel groups per lane, 3 through L1 with one channel per lane */
+  int32_t transport_gather;  /* transport F gather: 0 automatic (= 4), 1 shared memory, 2 through L1 with
+                                4-channel groups per lane, 3 through L1 with one channel per lane;
+                                one channel per lane with lazily renormalised float-float sums: 4 one
+                                1024-thread CTA per SM with F in shared memory (5 if F does not fit) and
+                                the next trip in registers, 5 the same through L1, 6 = 3 with lazy sums */
   int32_t transport_ctas;    /* resident 256-thread transport CTAs per SM, 1..8 (0 = 8 with L1 gathers) */
   int32_t channel_per_lane;  /* FP32/BF16 sweep shape: 0 automatic (= 4); one channel per lane in
                                 512-thread CTAs, three per SM: 1 plain, 3 with an L2 prefetch of the stream

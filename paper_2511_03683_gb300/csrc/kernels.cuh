@@ -579,48 +579,103 @@ __global__ void __launch_bounds__(kBlock) k_stream_tr(const Item *__restrict__ i
   }
 }
 
+// (h, l) += x * (ah + al) like ff_mac, but without renormalising (h, l) after every term: h
+// takes the exact TwoSum and l collects the rounding errors and cross products in FP32.  Over
+// the ~64 terms a lane adds per work item, l stays within about 64 ulp(h), so its own rounding
+// costs about 2^-18 ulp(h): the pair is still exact to about 2^-42 relative, at 11 operations
+// per term instead of 15.
+__device__ __forceinline__ void ff_mac_lazy(float &h, float &l, float2 x, float ah, float al) {
+  const float p = __fmul_rn(x.x, ah);
+  float e = __fmaf_rn(x.x, ah, -p);
+  e = __fmaf_rn(x.x, al, e);
+  e = __fmaf_rn(x.y, ah, e);
+  const float s = __fadd_rn(h, p);
+  const float bb = __fsub_rn(s, h);
+  const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  l = __fadd_rn(l, __fadd_rn(err, e));
+  h = s;
+}
+
+template <bool LAZY, bool GLOBAL>
+__device__ __forceinline__ void tr_mac3(float (&acc)[6], const float2 *Fp, float2 w) {
+  const float2 fx = GLOBAL ? __ldg(Fp) : Fp[0], fy = GLOBAL ? __ldg(Fp + 1) : Fp[1], fz = GLOBAL ? __ldg(Fp + 2) : Fp[2];
+  if (LAZY) {
+    ff_mac_lazy(acc[0], acc[1], fx, w.x, w.y);
+    ff_mac_lazy(acc[2], acc[3], fy, w.x, w.y);
+    ff_mac_lazy(acc[4], acc[5], fz, w.x, w.y);
+  } else {
+    ff_mac(acc[0], acc[1], fx, w.x, w.y);
+    ff_mac(acc[2], acc[3], fy, w.x, w.y);
+    ff_mac(acc[4], acc[5], fz, w.x, w.y);
+  }
+}
+
 // Transport sweep with consecutive lanes on consecutive channels: a warp's 32 channels share
-// about 32/nmodes partners, so each F gather touches few L1 sectors; weights (8 B) and 16-bit
-// indices stay fully coalesced across the warp.  Four channels per lane per trip.
-template <typename IDX>
-__global__ void __launch_bounds__(kBlock) k_stream_tr_lane(const Item *__restrict__ items, int nitems,
-                                                           const float2 *__restrict__ W, const IDX *__restrict__ colp,
-                                                           const float2 *__restrict__ F, Part4 *__restrict__ part) {
+// about 32/nmodes partners, so each F gather touches few L1 sectors or shared-memory banks;
+// weights (8 B) and indices stay fully coalesced across the warp.  Four channels per lane per
+// trip.  Shapes: NT = 256 with F gathered through L1 (eight CTAs per SM), or NT = 1024 (one
+// CTA per SM) with F staged in shared memory (SMEMF) and the next trip's weights and indices
+// loaded into registers before this trip's gathers (RP).
+template <typename IDX, int NT, bool SMEMF, bool RP, bool LAZY>
+__global__ void __launch_bounds__(NT, NT == 1024 ? 1 : 8) k_stream_tr_lane(const Item *__restrict__ items, int nitems,
+                                                          const float2 *__restrict__ W,
+                                                          const IDX *__restrict__ colp,
+                                                          const float2 *__restrict__ F, int ns,
+                                                          Part4 *__restrict__ part) {
+  extern __shared__ float2 Fs[];
+  if (SMEMF) {
+    for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) Fs[i] = F[i];
+    __syncthreads();
+  }
+  const float2 *__restrict__ Fg = SMEMF ? Fs : F;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int it = warp; it < nitems; it += nwarps) {
     const Item I = items[it];
     const long long c0 = I.start;
-    float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f, zh = 0.f, zl = 0.f;
+    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int j = lane;
-    for (; j + 96 < I.len; j += 128) {
-      float2 w[4];
-      unsigned p[4];
+    bool full = j + 96 < I.len;
+    float2 w[4];
+    unsigned p[4];
+    auto load = [&](int at, float2 (&wv)[4], unsigned (&pv)[4]) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        w[k] = __ldcs(W + c0 + j + 32 * k);
-        p[k] = (unsigned)__ldcs(colp + c0 + j + 32 * k) & 0xFFFFFFu;
+        wv[k] = __ldcs(W + c0 + at + 32 * k);
+        pv[k] = (unsigned)__ldcs(colp + c0 + at + 32 * k) & 0xFFFFFFu;
+      }
+    };
+    if (RP && full) load(j, w, p);
+    while (full) {
+      const bool nfull = j + 128 + 96 < I.len;
+      float2 wn[4];
+      unsigned pn[4];
+      if (RP) {
+        if (nfull) load(j + 128, wn, pn);
+      } else {
+        load(j, w, p);
       }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float2 *Fp = F + 3 * p[k];
-        ff_mac(xh, xl, __ldg(Fp), w[k].x, w[k].y);
-        ff_mac(yh, yl, __ldg(Fp + 1), w[k].x, w[k].y);
-        ff_mac(zh, zl, __ldg(Fp + 2), w[k].x, w[k].y);
+      for (int k = 0; k < 4; ++k) tr_mac3<LAZY, !SMEMF>(acc, Fg + 3 * p[k], w[k]);
+      if (RP && nfull) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          w[k] = wn[k];
+          p[k] = pn[k];
+        }
       }
+      j += 128;
+      full = nfull;
     }
     for (; j < I.len; j += 32) {
       const float2 wk = __ldcs(W + c0 + j);
       const unsigned pk = (unsigned)__ldcs(colp + c0 + j) & 0xFFFFFFu;
-      const float2 *Fp = F + 3 * pk;
-      ff_mac(xh, xl, __ldg(Fp), wk.x, wk.y);
-      ff_mac(yh, yl, __ldg(Fp + 1), wk.x, wk.y);
-      ff_mac(zh, zl, __ldg(Fp + 2), wk.x, wk.y);
+      tr_mac3<LAZY, !SMEMF>(acc, Fg + 3 * pk, wk);
     }
-    const double X = warp_sum(ff_to_double(xh, xl));
-    const double Y = warp_sum(ff_to_double(yh, yl));
-    const double Z = warp_sum(ff_to_double(zh, zl));
+    const double X = warp_sum((double)acc[0] + (double)acc[1]);
+    const double Y = warp_sum((double)acc[2] + (double)acc[3]);
+    const double Z = warp_sum((double)acc[4] + (double)acc[5]);
     if (lane == 0) part[it] = make_part4(X, Y, Z, 0.0);
   }
 }

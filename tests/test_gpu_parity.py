@@ -164,6 +164,21 @@ def test_item_split_is_invisible(pb, item_channels):
     check_I(dev.collision(T(f)).cpu().numpy(), ref, ab)
 
 
+@pytest.mark.parametrize("gather", [1, 2, 3, 4, 5, 6])
+def test_transport_sweep_shapes(pb, gather):
+    """Every transport sweep shape (shared-memory or L1 gathers, 256- or 1024-thread CTAs,
+    eager or lazily renormalised float-float sums) on a ragged case: rows of many lengths
+    split into 256-channel items, so full trips and tails both occur."""
+    m = synth.make_window4(16)
+    o = oracle.Oracle(m)
+    dev = pb.Device(pb.Channels.from_model(m), transport=True, transport_gather=gather, item_channels=256)
+    f0 = o.window_values(m.f_fermi(m.emin() - 0.2))
+    v = o.window_values(m.vel)
+    Fin = np.random.default_rng(6).normal(size=(o.nstate, 3))
+    ref, _ = o.transport_map(f0, v, Fin)
+    assert nrel(dev.transport_map(T(f0), T(v), T(Fin)).cpu().numpy(), ref) <= TOL
+
+
 def test_transport_map_and_solve(pb):
     m = synth.make_tiny(4).with_(sigma=0.01)
     o = oracle.Oracle(m)
