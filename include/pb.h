@@ -168,6 +168,10 @@ typedef struct pb_dev_opts {
   int32_t stream_mode;       /* FF collision sweep: 0 automatic (= 1), 1 vector loads from global memory,
                                 2 TMA bulk copies (cp.async.bulk) into a shared-memory ring (FF variant,
                                 nstate <= 65536); its bounded waits report through pb_dev_check */
+  int32_t merge_branches;    /* FF and F64: 0 automatic (= 1); 1 sum the coefficients of the branches nu of
+                                every state pair (s, p) once at setup and stream one entry per pair (Eq. 2
+                                depends on nu only through |g|^2, N and the deltas, all fixed with eps,
+                                omega, sigma and T); 2 stream one entry per channel */
 } pb_dev_opts;
 
 typedef struct pb_dev pb_dev; /* opaque host handle describing device-resident data */

@@ -26,7 +26,8 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct Layout {
   size_t rp, item_ptr, items, col, coefA, coefB, g2, wt, eps, kc, R, omega, tab, part, acc, y, yff, fstage, Fa, Fb,
       Fff, tau, invtau, red, scal, obs, g2lo, gstate, tab32, col16, rp_real, vjpG, vecs, hcol, hg2, hA, hB, sc,
-      entries, hitems, titems, t_item_ptr, err, total;
+      entries, hitems, titems, t_item_ptr, err, citems, citem_ptr, cpart, ccoefA, ccoefB, sidx16, sidx32, pcstart,
+      pcnt, total;
 };
 
 struct Plan {
@@ -38,11 +39,36 @@ struct Plan {
 };
 
 int default_item_channels(int64_t nchp, int sm_count, int ctas) {
+  // (entries: channels, or state pairs of the branch-merged sweep)
   // enough items for ~4 per resident warp, 256..4096 channels each, multiple of 64
   const int64_t warps = (int64_t)sm_count * ctas * (dev::kBlock / 32);
   int64_t ic = nchp / std::max<int64_t>(1, warps * 4);
   ic = std::max<int64_t>(256, std::min<int64_t>(4096, ic));
   return (int)(ic / 64 * 64);
+}
+
+void plan_items(const std::vector<int64_t> &rp, int item_ch, std::vector<Item> &items, std::vector<int32_t> &ptr);
+
+// Branch-merged sweep (FF and F64): one entry per state pair (s, p) = per run of equal partner
+// in the CSR row, rows padded to kRowPad entries.  rp: padded entry offsets [ns+1].
+void pair_rows(const pb_channels *ch, std::vector<int64_t> &rp) {
+  const int64_t ns = ch->nstate;
+  rp.assign(ns + 1, 0);
+  for (int64_t r = 0; r < ns; ++r) {
+    int64_t runs = 0;
+    for (int64_t c = ch->row_ptr[r]; c < ch->row_ptr[r + 1]; ++c)
+      if (c == ch->row_ptr[r] || ch->col[c] != ch->col[c - 1]) ++runs;
+    rp[r + 1] = rp[r] + (runs + kRowPad - 1) / kRowPad * kRowPad;
+  }
+}
+
+void plan_from_rp(const std::vector<int64_t> &rp, int item_ch, Plan &P) {
+  P.ns = (int64_t)rp.size() - 1;
+  P.item_ch = item_ch;
+  P.rp = rp;
+  plan_items(P.rp, item_ch, P.items, P.item_ptr);
+  P.nchp = P.rp[P.ns];
+  P.nitems = (int64_t)P.items.size();
 }
 
 void make_plan(const pb_channels *ch, int item_ch, Plan &P) {
@@ -104,7 +130,10 @@ size_t coef_bytes(int variant) {
   }
 }
 
-Layout make_layout(const pb_channels *ch, const Plan &P, int variant, bool transport, int nfin_blocks) {
+// P: the channel plan; S: the sweep plan of the branch-merged variants (null: the sweep runs
+// over channels and the channel-only regions are empty).
+Layout make_layout(const pb_channels *ch, const Plan &P, const Plan *S, int variant, bool transport,
+                   int nfin_blocks) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -113,14 +142,25 @@ Layout make_layout(const pb_channels *ch, const Plan &P, int variant, bool trans
     return at;
   };
   const size_t ns = (size_t)P.ns, nchp = (size_t)P.nchp;
+  const Plan &W = S ? *S : P;  // the sweep plan
+  const size_t nsw = (size_t)W.nchp;
   L.rp = take(sizeof(int64_t) * (ns + 1));
   L.item_ptr = take(sizeof(int32_t) * (ns + 1));
-  L.items = take(sizeof(Item) * P.nitems);
+  L.items = take(sizeof(Item) * W.nitems);
+  L.citem_ptr = take(S ? sizeof(int32_t) * (ns + 1) : 0);
+  L.citems = take(S ? sizeof(Item) * P.nitems : 0);
+  L.cpart = take(S ? sizeof(Part4) * P.nitems : 0);
   L.col = take(sizeof(uint32_t) * nchp);
   L.g2 = take(sizeof(double) * nchp);
-  L.coefA = take(coef_bytes(variant) * nchp);
-  L.coefB = take(coef_bytes(variant) * nchp);
-  L.wt = take(transport ? sizeof(float2) * nchp : 0);
+  L.coefA = take(coef_bytes(variant) * nsw);
+  L.coefB = take(coef_bytes(variant) * nsw);
+  L.ccoefA = take(S ? coef_bytes(variant) * nchp : 0);
+  L.ccoefB = take(S ? coef_bytes(variant) * nchp : 0);
+  L.sidx16 = take(S && ns <= 65536 ? sizeof(uint16_t) * nsw : 0);
+  L.sidx32 = take(S && ns > 65536 ? sizeof(uint32_t) * nsw : 0);
+  L.pcstart = take(S ? sizeof(int64_t) * nsw : 0);
+  L.pcnt = take(S ? nsw : 0);
+  L.wt = take(transport ? sizeof(float2) * nsw : 0);
   L.eps = take(sizeof(double) * ns);
   L.kc = take(sizeof(short4) * ns);
   L.R = take(sizeof(double) * ns);
@@ -157,7 +197,7 @@ Layout make_layout(const pb_channels *ch, const Plan &P, int variant, bool trans
   L.hitems = take(sizeof(Item) * nhi);
   L.titems = take(sizeof(Item) * ((variant == PB_VARIANT_PAPER) ? z.nentp / kRowPad + (int64_t)ns : 0));
   L.t_item_ptr = take(sizeof(int32_t) * (ns + 1));
-  L.part = take(sizeof(Part4) * std::max<int64_t>(P.nitems, (variant == PB_VARIANT_PAPER) ? z.nentp / kRowPad + (int64_t)ns : 0));
+  L.part = take(sizeof(Part4) * std::max<int64_t>(W.nitems, (variant == PB_VARIANT_PAPER) ? z.nentp / kRowPad + (int64_t)ns : 0));
   L.rp_real = take(sizeof(int64_t) * (ns + 1));
   L.vjpG = take(sizeof(float2) * 3 * ns);
   L.vecs = take(sizeof(double) * 8 * ns);
@@ -264,6 +304,19 @@ struct pb_dev {
   bool vjp_g_ok = false;    // the mixed-precision adjoint's 20 bytes per state fit in shared memory
   float2 *tab32 = nullptr;  // padded-grid (hbar w, N) in FP32
   uint16_t *col16 = nullptr;  // 16-bit partner indices (nstate <= 65536), else null
+  // branch-merged sweep (FF, F64): items/item_ptr/part/coefA/coefB/wt above are per state
+  // pair; the per-channel plan and coefficients below feed the setup and the |g|^2 gradient.
+  // Without merging the c* views alias the sweep's and sidx* alias col16/col.
+  bool merged = false;
+  int64_t ncitems = 0, nsw = 0;   // channel-plan items; sweep entries (padded)
+  Item *citems = nullptr;
+  int32_t *citem_ptr = nullptr;
+  Part4 *cpart = nullptr;
+  void *ccoefA = nullptr, *ccoefB = nullptr;
+  uint16_t *sidx16 = nullptr;     // sweep partner indices (16-bit when nstate <= 65536)
+  uint32_t *sidx32 = nullptr;
+  int64_t *pcstart = nullptr;     // first channel of each sweep entry
+  uint8_t *pcnt = nullptr;        // channels of each sweep entry
   int64_t *rp_real = nullptr;  // unpadded CSR row offsets [ns+1]
   float2 *vjpG = nullptr;      // adjoint gather table [ns][3]
   double *vecs = nullptr;      // 8 scratch vectors of nstate doubles (adjoint stages)
@@ -320,6 +373,10 @@ struct pb_dev {
     const int64_t need = (nitems * 32 + dev::kBlock - 1) / dev::kBlock;
     return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sm_count * per_sm));
   }
+  int chan_grid(int per_sm) const {
+    const int64_t need = (ncitems * 32 + dev::kBlock - 1) / dev::kBlock;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sm_count * per_sm));
+  }
 };
 
 namespace {
@@ -344,6 +401,7 @@ int resolve_opts(const pb_channels *ch, const pb_dev_opts *opts, int sm_count, p
   if (d.ctas_per_sm <= 0) d.ctas_per_sm = 3;  // measured best on GB300 for the coefficient sweeps
   if (d.ctas_per_sm > 8) return set_error(PB_EINVAL, "pb_dev: ctas_per_sm must be <= 8");
   if (d.stream_mode < 0 || d.stream_mode > 2) return set_error(PB_EINVAL, "pb_dev: stream_mode must be 0..2");
+  if (d.merge_branches < 0 || d.merge_branches > 2) return set_error(PB_EINVAL, "pb_dev: merge_branches must be 0..2");
   if (d.channel_per_lane < 0 || d.channel_per_lane > 4)
     return set_error(PB_EINVAL, "pb_dev: channel_per_lane must be 0..4");
   if (d.transport_gather < 0 || d.transport_gather > 6 || d.transport_ctas < 0 || d.transport_ctas > 8)
@@ -359,6 +417,27 @@ int resolve_opts(const pb_channels *ch, const pb_dev_opts *opts, int sm_count, p
   }
   o = d;
   return PB_OK;
+}
+
+bool merge_for(const pb_dev_opts &o) {
+  return (o.variant == PB_VARIANT_FF || o.variant == PB_VARIANT_F64) && o.merge_branches != 2;
+}
+
+// work-item size of the branch-merged sweep: the caller's, the bulk ring's, or the default
+int sweep_item_size(const pb_dev_opts *user, const pb_dev_opts &o, int64_t nsw, int sm) {
+  if (user && user->item_channels > 0) return user->item_channels;
+  if (o.stream_mode == 2) return 2048;
+  return default_item_channels(nsw, sm, o.ctas_per_sm);
+}
+
+// channel plan P and, for the branch-merged variants, the sweep plan S
+bool make_plans(const pb_channels *ch, const pb_dev_opts *user, const pb_dev_opts &o, int sm, Plan &P, Plan &S) {
+  make_plan(ch, o.item_channels, P);
+  if (!merge_for(o)) return false;
+  std::vector<int64_t> rp;
+  pair_rows(ch, rp);
+  plan_from_rp(rp, sweep_item_size(user, o, rp.back(), sm), S);
+  return true;
 }
 
 }  // namespace
@@ -474,11 +553,19 @@ extern "C" int pb_dev_arena_bytes(const pb_channels *ch, const pb_dev_opts *opts
   pb_dev_opts o;
   int rc = resolve_opts(ch, opts, sm, o);
   if (rc) return rc;
-  Plan P;
-  make_plan(ch, o.item_channels, P);
-  const int nfin = (int)((P.ns + kFinBlock - 1) / kFinBlock);
-  *bytes = make_layout(ch, P, o.variant, o.transport != 0, nfin).total;
+  Plan P, S;
+  try {
+    const bool merged = make_plans(ch, opts, o, sm, P, S);
+    const int nfin = (int)((P.ns + kFinBlock - 1) / kFinBlock);
+    *bytes = make_layout(ch, P, merged ? &S : nullptr, o.variant, o.transport != 0, nfin).total;
+  } catch (const std::bad_alloc &) {
+    return set_error(PB_ENOMEM, "pb_dev_arena_bytes: out of host memory");
+  }
   return PB_OK;
+}
+
+namespace {
+int coef_setup(pb_dev *d, cudaStream_t st);
 }
 
 extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, void *arena, size_t arena_bytes,
@@ -498,14 +585,16 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
 
   pb_dev *d = new (std::nothrow) pb_dev();
   if (!d) return set_error(PB_ENOMEM, "pb_dev_create: out of host memory");
-  Plan P;
+  Plan P, S;
+  bool merged = false;
   try {
-    make_plan(ch, o.item_channels, P);
+    merged = make_plans(ch, opts, o, sm, P, S);
   } catch (const std::bad_alloc &) {
     delete d;
     return set_error(PB_ENOMEM, "pb_dev_create: out of host memory");
   }
-  if (P.nitems > INT32_MAX) {
+  const Plan &W = merged ? S : P;  // the sweep plan
+  if (P.nitems > INT32_MAX || W.nitems > INT32_MAX) {
     delete d;
     return set_error(PB_EINVAL, "pb_dev_create: too many work items");
   }
@@ -513,7 +602,10 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->ns = ch->nstate;
   d->nch = ch->nch;
   d->nchp = P.nchp;
-  d->nitems = P.nitems;
+  d->nitems = W.nitems;
+  d->merged = merged;
+  d->ncitems = P.nitems;
+  d->nsw = W.nchp;
   for (int i = 0; i < 3; ++i) d->nk[i] = ch->nk[i];
   d->nmodes = ch->nmodes;
   d->nq = ch->nq;
@@ -525,7 +617,7 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->item_ch = o.item_channels;
   d->transport = o.transport != 0;
   d->nfin_blocks = (int)((d->ns + kFinBlock - 1) / kFinBlock);
-  d->L = make_layout(ch, P, o.variant, d->transport, d->nfin_blocks);
+  d->L = make_layout(ch, P, merged ? &S : nullptr, o.variant, d->transport, d->nfin_blocks);
   if (arena_bytes < d->L.total) {
     const size_t need = d->L.total;
     delete d;
@@ -578,6 +670,25 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->hitems = (Item *)(A + L.hitems);
   d->titems = (Item *)(A + L.titems);
   d->t_item_ptr = (int32_t *)(A + L.t_item_ptr);
+  if (merged) {
+    d->citems = (Item *)(A + L.citems);
+    d->citem_ptr = (int32_t *)(A + L.citem_ptr);
+    d->cpart = (Part4 *)(A + L.cpart);
+    d->ccoefA = A + L.ccoefA;
+    d->ccoefB = A + L.ccoefB;
+    d->sidx16 = d->ns <= 65536 ? (uint16_t *)(A + L.sidx16) : nullptr;
+    d->sidx32 = d->ns <= 65536 ? nullptr : (uint32_t *)(A + L.sidx32);
+    d->pcstart = (int64_t *)(A + L.pcstart);
+    d->pcnt = (uint8_t *)(A + L.pcnt);
+  } else {
+    d->citems = d->items;
+    d->citem_ptr = d->item_ptr;
+    d->cpart = d->part;
+    d->ccoefA = d->coefA;
+    d->ccoefB = d->coefB;
+    d->sidx16 = d->col16;
+    d->sidx32 = d->col;
+  }
 
   // shared-memory staging sizes
   int devid = 0, smem_optin = 0;
@@ -623,7 +734,7 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
       return set_error(PB_EINVAL, "pb_dev_create: the bulk-copy sweep needs the FF variant and nstate <= 65536");
     }
     int cap = 8;
-    for (const Item &it : P.items) cap = std::max(cap, it.len);
+    for (const Item &it : W.items) cap = std::max(cap, it.len);
     const size_t fb = ((size_t)d->ns * sizeof(float2) + 127) / 128 * 128;
     const size_t sb = ((size_t)cap * (2 * sizeof(float2) + sizeof(uint16_t)) + 127) / 128 * 128;
     const size_t need = fb + dev::kBulkStages * sb + (dev::kBulkStages + 1) * 8 + dev::kBulkStages * sizeof(Item) +
@@ -685,8 +796,12 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
       }
       UP(d->rp, P.rp.data(), sizeof(int64_t) * (d->ns + 1));
       UP(d->rp_real, ch->row_ptr.data(), sizeof(int64_t) * (d->ns + 1));
-      UP(d->item_ptr, P.item_ptr.data(), sizeof(int32_t) * (d->ns + 1));
-      UP(d->items, P.items.data(), sizeof(Item) * P.nitems);
+      UP(d->item_ptr, W.item_ptr.data(), sizeof(int32_t) * (d->ns + 1));
+      UP(d->items, W.items.data(), sizeof(Item) * W.nitems);
+      if (merged) {
+        UP(d->citem_ptr, P.item_ptr.data(), sizeof(int32_t) * (d->ns + 1));
+        UP(d->citems, P.items.data(), sizeof(Item) * P.nitems);
+      }
       UP(d->col, colp.data(), sizeof(uint32_t) * P.nchp);
       if (d->col16) {
         std::vector<uint16_t> c16((size_t)P.nchp);
@@ -694,6 +809,41 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
         UP(d->col16, c16.data(), sizeof(uint16_t) * P.nchp);  // pageable source: staged before return
       }
       UP(d->g2, g2p.data(), sizeof(double) * P.nchp);
+      if (merged) {
+        // one entry per run of equal partner in each row; padding entries: self, no channels
+        std::vector<uint32_t> sidx((size_t)S.nchp);
+        std::vector<int64_t> cst((size_t)S.nchp, 0);
+        std::vector<uint8_t> cn((size_t)S.nchp, 0);
+        for (int64_t r = 0; r < d->ns; ++r) {
+          const int64_t a = ch->row_ptr[r], len = ch->row_ptr[r + 1] - a;
+          int64_t e = S.rp[r];
+          for (int64_t i = 0; i < len; ++i) {
+            if (i > 0 && ch->col[a + i] == ch->col[a + i - 1]) {
+              ++cn[e - 1];
+              continue;
+            }
+            sidx[e] = (uint32_t)ch->col[a + i];
+            cst[e] = P.rp[r] + i;
+            cn[e] = 1;
+            ++e;
+          }
+          for (; e < S.rp[r + 1]; ++e) sidx[e] = (uint32_t)r;
+        }
+        if (d->sidx16) {
+          std::vector<uint16_t> s16((size_t)S.nchp);
+          for (int64_t i = 0; i < S.nchp; ++i) s16[i] = (uint16_t)sidx[i];
+          UP(d->sidx16, s16.data(), sizeof(uint16_t) * S.nchp);
+        } else {
+          UP(d->sidx32, sidx.data(), sizeof(uint32_t) * S.nchp);
+        }
+        UP(d->pcstart, cst.data(), sizeof(int64_t) * S.nchp);
+        UP(d->pcnt, cn.data(), S.nchp);
+        cudaError_t e_ = cudaStreamSynchronize(st);  // pageable sources above go out of scope
+        if (e_ != cudaSuccess) {
+          status = cuda_fail(e_, "upload");
+          break;
+        }
+      }
       UP(d->eps, ch->eps.data(), sizeof(double) * d->ns);
       UP(d->kc, kc.data(), sizeof(short4) * d->ns);
       UP(d->omega, ch->omega.data(), sizeof(double) * (size_t)ch->nq * ch->nmodes);
@@ -705,30 +855,9 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) status = cuda_fail(e, "k_table");
     }
-    if (status == PB_OK) {
-      // per-channel coefficients (and R_s) for the coefficient variants
-      const int grid = d->stream_grid(8);
-      const dev::ChanGeom g = d->geom();
-      if (d->variant == PB_VARIANT_FF)
-        dev::k_coef<true><<<grid, dev::kBlock, 0, st>>>(d->items, (int)d->nitems, g, d->coefA, d->coefB, d->part);
-      else if (d->variant == PB_VARIANT_F64)
-        dev::k_coef<false><<<grid, dev::kBlock, 0, st>>>(d->items, (int)d->nitems, g, d->coefA, d->coefB, d->part);
-      cudaError_t e = cudaGetLastError();
-      if (e != cudaSuccess) status = cuda_fail(e, "k_coef");
-      if (status == PB_OK && d->variant != PB_VARIANT_LITERAL) {
-        dev::k_rowsum<<<(int)((d->ns + 255) / 256), 256, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->R);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) status = cuda_fail(e, "k_rowsum");
-      }
-    }
+    if (status == PB_OK) status = coef_setup(d, st);  // coefficients and R_s of the FF/F64 variants
     if (status == PB_OK && d->variant == PB_VARIANT_PAPER) status = paper_setup(d, ch, o.item_channels, st);
     if (status == PB_OK && d->mixed()) {
-      const long long n = (long long)P.nchp;
-      const int cg = (int)std::min<long long>((n + 255) / 256, 8192);
-      if (d->variant == PB_VARIANT_G32)
-        dev::k_cvt_g2<float><<<cg, 256, 0, st>>>(d->g2, n, (float *)d->g2lo);
-      else
-        dev::k_cvt_g2<__nv_bfloat16><<<cg, 256, 0, st>>>(d->g2, n, (__nv_bfloat16 *)d->g2lo);
       dev::k_gstate_init<<<(int)((d->ns + 255) / 256), 256, 0, st>>>(d->eps, d->kc, (int)d->ns, d->rad[1], d->rad[2],
                                                                       ch->nmodes, d->gstate);
       const long long nt = (long long)d->rad[0] * d->rad[1] * d->rad[2] * ch->nmodes;
@@ -823,8 +952,13 @@ extern "C" int pb_dev_get_info(const pb_dev *d, pb_dev_info *info) {
   info->sm_count = d->sm_count;
   info->c = d->c;
   switch (d->variant) {
-    case PB_VARIANT_FF: info->bytes_per_channel = 2 * sizeof(float2) + (d->col16 ? 2 : 4); break;
-    case PB_VARIANT_F64: info->bytes_per_channel = 2 * sizeof(double) + (d->col16 ? 2 : 4); break;
+    // streamed bytes per physical channel: per sweep entry (state pair when branch-merged)
+    case PB_VARIANT_FF:
+      info->bytes_per_channel = (2 * sizeof(float2) + (d->sidx16 ? 2 : 4)) * (d->merged ? (double)d->nsw / (double)d->nch : 1.0);
+      break;
+    case PB_VARIANT_F64:
+      info->bytes_per_channel = (2 * sizeof(double) + (d->sidx16 ? 2 : 4)) * (d->merged ? (double)d->nsw / (double)d->nch : 1.0);
+      break;
     case PB_VARIANT_G32: info->bytes_per_channel = sizeof(float) + sizeof(uint32_t); break;
     case PB_VARIANT_G16: info->bytes_per_channel = 2 + sizeof(uint32_t); break;
     case PB_VARIANT_PAPER:  // step 2: P_in, D, index, sc_col write; step 3: entry + sc_col gather
@@ -850,7 +984,7 @@ int launch_stream_t(pb_dev *d, int mode, const double *fd, const float2 *fff, co
   if (d->variant == PB_VARIANT_FF && coll && d->bulk) {
     const int gb = (int)std::max<int64_t>(1, std::min<int64_t>(d->nitems, (int64_t)d->sm_count));
     dev::k_stream_ff_bulk<<<gb, dev::kBlock, d->bulk_smem, st>>>(d->items, n, (const float2 *)d->coefA,
-                                                                 (const float2 *)d->coefB, d->col16, fff, ns,
+                                                                 (const float2 *)d->coefB, d->sidx16, fff, ns,
                                                                  d->bulk_cap, part, d->err);
   } else if (d->variant == PB_VARIANT_FF) {
     const float4 *A4 = (const float4 *)d->coefA, *B4 = (const float4 *)d->coefB;
@@ -912,8 +1046,8 @@ int launch_stream_t(pb_dev *d, int mode, const double *fd, const float2 *fff, co
 }
 
 int launch_stream_to(pb_dev *d, int mode, const double *fd, const float2 *fff, Part4 *part, cudaStream_t st) {
-  if (d->col16) return launch_stream_t<uint16_t>(d, mode, fd, fff, d->col16, part, st);
-  return launch_stream_t<uint32_t>(d, mode, fd, fff, d->col, part, st);
+  if (d->sidx16) return launch_stream_t<uint16_t>(d, mode, fd, fff, d->sidx16, part, st);
+  return launch_stream_t<uint32_t>(d, mode, fd, fff, d->sidx32, part, st);
 }
 
 int launch_stream(pb_dev *d, int mode, const double *fd, const float2 *fff, cudaStream_t st) {
@@ -1003,7 +1137,20 @@ int ensure_rk_graph(pb_dev *d, double *f, double dt) {
 int ensure_weights(pb_dev *d, const double *f0, cudaStream_t st) {
   if (!d->transport) return set_error(PB_EINVAL, "transport buffers were not reserved (pb_dev_opts.transport = 0)");
   const int grid = d->stream_grid(8);
-  dev::k_weights<<<grid, dev::kBlock, 0, st>>>(d->items, (int)d->nitems, d->geom(), f0, d->c, d->wt, d->part);
+  if (d->variant == PB_VARIANT_FF || d->variant == PB_VARIANT_F64) {
+    // from the coefficient arrays (per state pair when branch-merged)
+    const bool ff = d->variant == PB_VARIANT_FF;
+    const int n = (int)d->nitems;
+    if (d->sidx16) {
+      if (ff) dev::k_weights_coef<true, uint16_t><<<grid, dev::kBlock, 0, st>>>(d->items, n, d->coefA, d->coefB, d->sidx16, f0, d->c, d->wt, d->part);
+      else    dev::k_weights_coef<false, uint16_t><<<grid, dev::kBlock, 0, st>>>(d->items, n, d->coefA, d->coefB, d->sidx16, f0, d->c, d->wt, d->part);
+    } else {
+      if (ff) dev::k_weights_coef<true, uint32_t><<<grid, dev::kBlock, 0, st>>>(d->items, n, d->coefA, d->coefB, d->sidx32, f0, d->c, d->wt, d->part);
+      else    dev::k_weights_coef<false, uint32_t><<<grid, dev::kBlock, 0, st>>>(d->items, n, d->coefA, d->coefB, d->sidx32, f0, d->c, d->wt, d->part);
+    }
+  } else {
+    dev::k_weights<<<grid, dev::kBlock, 0, st>>>(d->items, (int)d->nitems, d->geom(), f0, d->c, d->wt, d->part);
+  }
   PB_LAUNCHED("k_weights");
   dev::k_rowsum<<<(int)((d->ns + 255) / 256), 256, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->invtau);
   PB_LAUNCHED("k_rowsum");
@@ -1045,14 +1192,14 @@ int transport_pass(pb_dev *d, const float2 *Fin_ff, const double *vel3, const do
   const int64_t need = (d->nitems * 32 + dev::kBlock - 1) / dev::kBlock;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)d->sm_count * d->ctas_tr));
   if (d->smem_F) {
-    if (d->col16) dev::k_stream_tr<true, uint16_t><<<grid, dev::kBlock, d->smem_F, st>>>(d->items, n, W4, d->col16, Fin_ff, (int)d->ns, d->part);
-    else          dev::k_stream_tr<true, uint32_t><<<grid, dev::kBlock, d->smem_F, st>>>(d->items, n, W4, d->col, Fin_ff, (int)d->ns, d->part);
+    if (d->sidx16) dev::k_stream_tr<true, uint16_t><<<grid, dev::kBlock, d->smem_F, st>>>(d->items, n, W4, d->sidx16, Fin_ff, (int)d->ns, d->part);
+    else           dev::k_stream_tr<true, uint32_t><<<grid, dev::kBlock, d->smem_F, st>>>(d->items, n, W4, d->sidx32, Fin_ff, (int)d->ns, d->part);
   } else if (d->tr_lane) {
-    if (d->col16) launch_tr_lane<uint16_t>(d, d->col16, Fin_ff, st);
-    else          launch_tr_lane<uint32_t>(d, d->col, Fin_ff, st);
+    if (d->sidx16) launch_tr_lane<uint16_t>(d, d->sidx16, Fin_ff, st);
+    else           launch_tr_lane<uint32_t>(d, d->sidx32, Fin_ff, st);
   } else {
-    if (d->col16) dev::k_stream_tr<false, uint16_t><<<grid, dev::kBlock, 0, st>>>(d->items, n, W4, d->col16, Fin_ff, (int)d->ns, d->part);
-    else          dev::k_stream_tr<false, uint32_t><<<grid, dev::kBlock, 0, st>>>(d->items, n, W4, d->col, Fin_ff, (int)d->ns, d->part);
+    if (d->sidx16) dev::k_stream_tr<false, uint16_t><<<grid, dev::kBlock, 0, st>>>(d->items, n, W4, d->sidx16, Fin_ff, (int)d->ns, d->part);
+    else           dev::k_stream_tr<false, uint32_t><<<grid, dev::kBlock, 0, st>>>(d->items, n, W4, d->sidx32, Fin_ff, (int)d->ns, d->part);
   }
   PB_LAUNCHED("k_stream_tr");
   dev::k_fin_tr<<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->tau, vel3, Fold, Fnew,
@@ -1198,16 +1345,24 @@ extern "C" int pb_observables(pb_dev *d, const double *f, double *out3, void *st
 namespace {
 
 int coef_setup(pb_dev *d, cudaStream_t st) {
-  const int grid = d->stream_grid(8);
-  const dev::ChanGeom g = d->geom();
-  if (d->variant == PB_VARIANT_FF)
-    dev::k_coef<true><<<grid, dev::kBlock, 0, st>>>(d->items, (int)d->nitems, g, d->coefA, d->coefB, d->part);
-  else if (d->variant == PB_VARIANT_F64)
-    dev::k_coef<false><<<grid, dev::kBlock, 0, st>>>(d->items, (int)d->nitems, g, d->coefA, d->coefB, d->part);
-  PB_LAUNCHED("k_coef");
   if (d->variant == PB_VARIANT_FF || d->variant == PB_VARIANT_F64) {
-    dev::k_rowsum<<<(int)((d->ns + 255) / 256), 256, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->R);
+    // per-channel coefficients and R_s on the channel plan, then (branch-merged) the sums
+    // over the branches of every state pair
+    const int grid = d->chan_grid(8);
+    const dev::ChanGeom g = d->geom();
+    const bool ff = d->variant == PB_VARIANT_FF;
+    if (ff) dev::k_coef<true><<<grid, dev::kBlock, 0, st>>>(d->citems, (int)d->ncitems, g, d->ccoefA, d->ccoefB, d->cpart);
+    else    dev::k_coef<false><<<grid, dev::kBlock, 0, st>>>(d->citems, (int)d->ncitems, g, d->ccoefA, d->ccoefB, d->cpart);
+    PB_LAUNCHED("k_coef");
+    dev::k_rowsum<<<(int)((d->ns + 255) / 256), 256, 0, st>>>(d->citem_ptr, d->cpart, (int)d->ns, d->R);
     PB_LAUNCHED("k_rowsum");
+    if (d->merged && d->nsw > 0) {
+      const int pg = (int)std::min<int64_t>((d->nsw + 255) / 256, 8192);
+      const long long* cs = (const long long *)d->pcstart;
+      if (ff) dev::k_pair_coef<true><<<pg, 256, 0, st>>>(cs, d->pcnt, (long long)d->nsw, d->ccoefA, d->ccoefB, d->coefA, d->coefB);
+      else    dev::k_pair_coef<false><<<pg, 256, 0, st>>>(cs, d->pcnt, (long long)d->nsw, d->ccoefA, d->ccoefB, d->coefA, d->coefB);
+      PB_LAUNCHED("k_pair_coef");
+    }
   }
   if (d->mixed()) {
     const long long n = (long long)d->nchp;
@@ -1263,23 +1418,23 @@ int vjp_launch(pb_dev *d, const double *f, const double *lam, double *grad_f, do
   const int grid = d->stream_grid(d->smem_G ? std::max(1, std::min(d->ctas, (int)((228 * 1024) / (d->smem_G + 1024)))) : d->ctas);
   const float4 *A4 = (const float4 *)d->coefA, *B4 = (const float4 *)d->coefB;
   if (d->smem_G) {
-    if (d->col16) dev::k_stream_vjp<true, uint16_t><<<grid, dev::kBlock, d->smem_G, st>>>(d->items, n, A4, B4, d->col16, d->vjpG, ns, d->part);
-    else          dev::k_stream_vjp<true, uint32_t><<<grid, dev::kBlock, d->smem_G, st>>>(d->items, n, A4, B4, d->col, d->vjpG, ns, d->part);
+    if (d->sidx16) dev::k_stream_vjp<true, uint16_t><<<grid, dev::kBlock, d->smem_G, st>>>(d->items, n, A4, B4, d->sidx16, d->vjpG, ns, d->part);
+    else           dev::k_stream_vjp<true, uint32_t><<<grid, dev::kBlock, d->smem_G, st>>>(d->items, n, A4, B4, d->sidx32, d->vjpG, ns, d->part);
   } else {
-    if (d->col16) dev::k_stream_vjp<false, uint16_t><<<grid, dev::kBlock, 0, st>>>(d->items, n, A4, B4, d->col16, d->vjpG, ns, d->part);
-    else          dev::k_stream_vjp<false, uint32_t><<<grid, dev::kBlock, 0, st>>>(d->items, n, A4, B4, d->col, d->vjpG, ns, d->part);
+    if (d->sidx16) dev::k_stream_vjp<false, uint16_t><<<grid, dev::kBlock, 0, st>>>(d->items, n, A4, B4, d->sidx16, d->vjpG, ns, d->part);
+    else           dev::k_stream_vjp<false, uint32_t><<<grid, dev::kBlock, 0, st>>>(d->items, n, A4, B4, d->sidx32, d->vjpG, ns, d->part);
   }
   PB_LAUNCHED("k_stream_vjp");
   dev::k_fin_vjp<<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, ns, d->c, d->R, lam, grad_f);
   PB_LAUNCHED("k_fin_vjp");
   if (grad_g2) {
-    const int gg = d->stream_grid(8);
-    const float2 *A = (const float2 *)d->coefA, *B = (const float2 *)d->coefB;
+    const int gg = d->chan_grid(8), nc = (int)d->ncitems;
+    const float2 *A = (const float2 *)d->ccoefA, *B = (const float2 *)d->ccoefB;
     if (d->col16)
-      dev::k_g2grad<uint16_t><<<gg, dev::kBlock, 0, st>>>(d->items, n, (const long long *)d->rp, (const long long *)d->rp_real,
+      dev::k_g2grad<uint16_t><<<gg, dev::kBlock, 0, st>>>(d->citems, nc, (const long long *)d->rp, (const long long *)d->rp_real,
                                                           A, B, d->col16, d->g2, f, lam, d->c, grad_g2);
     else
-      dev::k_g2grad<uint32_t><<<gg, dev::kBlock, 0, st>>>(d->items, n, (const long long *)d->rp, (const long long *)d->rp_real,
+      dev::k_g2grad<uint32_t><<<gg, dev::kBlock, 0, st>>>(d->citems, nc, (const long long *)d->rp, (const long long *)d->rp_real,
                                                           A, B, d->col, d->g2, f, lam, d->c, grad_g2);
     PB_LAUNCHED("k_g2grad");
   }
@@ -1340,7 +1495,7 @@ extern "C" int pb_dev_set_g2(pb_dev *d, const double *g2, void *stream) {
   clear_error();
   if (!d || !g2) return set_error(PB_EINVAL, "pb_dev_set_g2: null argument");
   cudaStream_t st = (cudaStream_t)stream;
-  dev::k_set_g2<<<d->stream_grid(8), dev::kBlock, 0, st>>>(d->items, (int)d->nitems, (const long long *)d->rp,
+  dev::k_set_g2<<<d->chan_grid(8), dev::kBlock, 0, st>>>(d->citems, (int)d->ncitems, (const long long *)d->rp,
                                                            (const long long *)d->rp_real, g2, d->g2);
   PB_LAUNCHED("k_set_g2");
   return coef_setup(d, st);

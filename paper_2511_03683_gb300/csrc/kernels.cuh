@@ -159,6 +159,75 @@ __global__ void __launch_bounds__(kBlock) k_coef(const Item *__restrict__ items,
   }
 }
 
+// Branch-merged coefficients.  For fixed eps, omega, sigma and T every branch nu of a state
+// pair (s, p) enters Eq. 2 through the same f_s and f_p, so the coefficient form only needs
+// the sums over nu:  P_in(s,p) = sum_nu P_in(s,p,nu),  D(s,p) = sum_nu D(s,p,nu).  Entry k
+// sums the cnt[k] consecutive channels from cstart[k] in FP64 (ascending nu) and stores the
+// result in the sweep's format; padding entries (cnt 0) become zero.
+template <bool FF>
+__global__ void k_pair_coef(const long long *__restrict__ cstart, const uint8_t *__restrict__ cnt, long long n,
+                            const void *__restrict__ cA, const void *__restrict__ cB, void *__restrict__ pA,
+                            void *__restrict__ pB) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const long long s = cstart[k];
+    const int m = cnt[k];
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < m; ++i) {
+      if (FF) {
+        const float2 x = ((const float2 *)cA)[s + i], y = ((const float2 *)cB)[s + i];
+        a += ff_to_double(x.x, x.y);
+        b += ff_to_double(y.x, y.y);
+      } else {
+        a += ((const double *)cA)[s + i];
+        b += ((const double *)cB)[s + i];
+      }
+    }
+    if (FF) {
+      ((float2 *)pA)[k] = ff_split(a);
+      ((float2 *)pB)[k] = ff_split(b);
+    } else {
+      ((double *)pA)[k] = a;
+      ((double *)pB)[k] = b;
+    }
+  }
+}
+
+// Transport weights from the coefficient arrays: W = c (P_in + (1 - f0_p) D), which equals
+// c g2 [G_a (N + f0_p) + G_e (N + 1 - f0_p)] summed over the entry's channels; stored
+// float-float; part[item].x = sum of W over the item.
+template <bool FF, typename IDX>
+__global__ void __launch_bounds__(kBlock) k_weights_coef(const Item *__restrict__ items, int nitems,
+                                                         const void *__restrict__ cA, const void *__restrict__ cB,
+                                                         const IDX *__restrict__ colp, const double *__restrict__ f0,
+                                                         double cpref, float2 *__restrict__ wt,
+                                                         Part4 *__restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    double acc = 0.0;
+    for (int j = lane; j < I.len; j += 32) {
+      const long long c = I.start + j;
+      double a, b;
+      if (FF) {
+        const float2 x = ((const float2 *)cA)[c], y = ((const float2 *)cB)[c];
+        a = ff_to_double(x.x, x.y);
+        b = ff_to_double(y.x, y.y);
+      } else {
+        a = ((const double *)cA)[c];
+        b = ((const double *)cB)[c];
+      }
+      const unsigned p = (unsigned)colp[c] & 0xFFFFFFu;
+      const double W = cpref * (a + (1.0 - f0[p]) * b);
+      wt[c] = ff_split(W);
+      acc += W;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) part[it] = make_part4(acc, 0.0, 0.0, 0.0);
+  }
+}
+
 // Transport weights W_c = c g2 [G_a (N + f0_p) + G_e (N + 1 - f0_p)] stored float-float;
 // part[item].x = sum of W over the item (for 1/tau_s at f0).
 __global__ void __launch_bounds__(kBlock) k_weights(const Item *__restrict__ items, int nitems, ChanGeom g,

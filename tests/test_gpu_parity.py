@@ -164,6 +164,38 @@ def test_item_split_is_invisible(pb, item_channels):
     check_I(dev.collision(T(f)).cpu().numpy(), ref, ab)
 
 
+@pytest.mark.parametrize("variant", ["ff", "f64"])
+@pytest.mark.parametrize("merge", [1, 2])
+@pytest.mark.parametrize("name", ["tiny5", "win16"])
+def test_branch_merged_and_per_channel_sweeps(pb, name, variant, merge):
+    """The coefficient sweeps with one entry per state pair (branches summed at setup) and
+    with one entry per channel: collision, rates, RK4 and the transport map all meet the
+    oracle; the two layouts agree with each other to rounding."""
+    m = SMALL[name]()
+    o = oracle.Oracle(m)
+    ch = pb.Channels.from_model(m)
+    dev = pb.Device(ch, variant=variant, merge_branches=merge, transport=True, item_channels=256)
+    rng = np.random.default_rng(21)
+    f = rng.uniform(0, 1, o.nstate)
+    ref, ab = o.collision(f, with_abs=True)
+    I = dev.collision(T(f)).cpu().numpy()
+    check_I(I, ref, ab)
+    assert nrel(dev.rates(T(f)).cpu().numpy(), o.rates(f)) <= TOL
+    f0 = o.window_values(m.f_hot())
+    ft = T(f0)
+    dev.rk4(ft, 1.0, 3)
+    assert nrel(ft.cpu().numpy(), o.rk4(f0, 1.0, 3)) <= TOL
+    v = o.window_values(m.vel)
+    Fin = rng.normal(size=(o.nstate, 3))
+    fe = o.window_values(m.f_fermi(m.emin() - 0.2))
+    Fr, _ = o.transport_map(fe, v, Fin)
+    assert nrel(dev.transport_map(T(fe), T(v), T(Fin)).cpu().numpy(), Fr) <= TOL
+    other = pb.Device(ch, variant=variant, merge_branches=3 - merge)
+    assert np.abs(other.collision(T(f)).cpu().numpy() - I).max() <= 1e-14 * ab.max()
+    if merge == 1:
+        assert dev.bytes_per_channel < other.bytes_per_channel
+
+
 @pytest.mark.parametrize("gather", [1, 2, 3, 4, 5, 6])
 def test_transport_sweep_shapes(pb, gather):
     """Every transport sweep shape (shared-memory or L1 gathers, 256- or 1024-thread CTAs,

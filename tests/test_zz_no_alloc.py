@@ -62,7 +62,8 @@ def test_static_refuses_problems_beyond_its_array(pb):
     import torch
 
     m = synth.make_config("window28")
-    dev = pb.Device(pb.Channels.from_model(m), item_channels=64)  # ~2.3e5 items: > 4 MiB of partials
+    # one entry per channel in 64-channel items: ~2.3e5 items, > 4 MiB of partials
+    dev = pb.Device(pb.Channels.from_model(m), item_channels=64, merge_branches=2)
     f = torch.full((dev.nstate,), 0.1, dtype=torch.float64, device="cuda")
     out = torch.empty_like(f)
     rc = _call_static(pb, dev, f, out)
