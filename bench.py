@@ -556,10 +556,12 @@ def run_ours(args):
             b.record(stream)
         torch.cuda.synchronize()
         rates_ms = statistics.mean(a.elapsed_time(b) for a, b in evs[:10])
+    # the sweep kernel alone: CUDA events on this stream around back-to-back launches of it
+    sweep_ms = dev.time_sweep(f, 50, stream=stream)
     clk = clocks.stop()
 
     bytes_launch = dev.bytes_per_channel * nch
-    achieved = bytes_launch / (coll_ms * 1e-3) / 1e9
+    achieved = bytes_launch / (sweep_ms * 1e-3) / 1e9
     peak, peak_src = measured_hbm()
     traffic = ncu_traffic(args.workload, args.variant, bytes_launch)
 
@@ -632,8 +634,11 @@ def run_ours(args):
             "rk4_steps_per_s": nrk / (rk_ms * 1e-3), "transport_iters_per_s": ntr / (tr_ms * 1e-3),
             "collision_ms": coll_ms, "rates_ms": rates_ms,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": traffic, "kernel": f"collision sweep ({args.variant} variant) via pb_collision",
+                         "traffic": traffic, "kernel": f"collision sweep ({args.variant} variant), its own launches",
+                         "kernel_ms": sweep_ms, "call_ms": coll_ms,
+                         "call_gb_s": bytes_launch / (coll_ms * 1e-3) / 1e9,
                          "bytes_per_channel": dev.bytes_per_channel, "bytes_per_launch": bytes_launch,
+                         "layout": "one entry per state pair (branches merged)" if dev.merged else "one entry per channel",
                          "peak_source": peak_src},
             "cpu_baseline": base, "e2e": e2e, "gpu_launches": LAUNCHES_PER_STEP * args.steps,
             "clocks": clk, "setup": {"build_channels_s": build_s, "device_create_s": create_s},

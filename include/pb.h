@@ -203,6 +203,13 @@ int pb_dev_get_info(const pb_dev *dev, pb_dev_info *info);
 /* Eq. 2: dfdt[s] = I_s[f] for every window state.  f, dfdt: device double[nstate]. */
 int pb_collision(pb_dev *dev, const double *f, double *dfdt, void *stream);
 
+/* Measurement aid (the paper has no counterpart): the average device duration of the
+ * collision sweep kernel alone, from CUDA events recorded on `stream` around `nlaunch`
+ * back-to-back launches of it on f (device double[nstate]); the stage-input conversion runs
+ * once before the first event and no finaliser runs.  Leaves the partial sums of the last
+ * launch in the handle's scratch; synchronises `stream`.  nlaunch in 1..10000. */
+int pb_dev_time_sweep(pb_dev *dev, const double *f, int32_t nlaunch, float *avg_ms, void *stream);
+
 /* Scattering rates 1/tau_s = -dI_s/df_s
  *   = (2pi/hbar)(1/N_q) sum |g|^2 [G(x+w)(N+f_p) + G(x-w)(N+1-f_p)],  x = eps_s - eps_p.
  * f, inv_tau: device double[nstate]. */

@@ -109,6 +109,7 @@ def lib() -> ctypes.CDLL:
         "pb_dev_create": [vp, ctypes.POINTER(_DevOpts), vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
         "pb_dev_get_info": [vp, ctypes.POINTER(_DevInfo)],
         "pb_dev_check": [vp, vp],
+        "pb_dev_time_sweep": [vp, vp, i32, ctypes.POINTER(ctypes.c_float), vp],
         "pb_collision": [vp, vp, vp, vp],
         "pb_collision_static": [vp, vp, vp, vp],
         "pb_scatter_rates": [vp, vp, vp, vp],
@@ -281,6 +282,8 @@ class Device:
             raise PBError(PB_EDEVICE, "no CUDA device is visible")
         self.channels = channels
         self.variant = variant
+        # FF/F64 stream one entry per state pair unless merge_branches == 2
+        self.merged = variant in ("ff", "f64") and int(merge_branches) != 2
         o = _DevOpts(VARIANTS[variant], int(item_channels), int(ctas_per_sm), 1 if transport else 0,
                      int(transport_gather), int(transport_ctas), int(channel_per_lane), int(stream_mode),
                      int(merge_branches))
@@ -323,6 +326,14 @@ class Device:
         _check(lib().pb_collision_static(self._h, _dev_vec(f, self.nstate, "f"), _dev_vec(out, self.nstate, "out"),
                                          _stream_ptr(stream)))
         return out
+
+    def time_sweep(self, f, nlaunch: int = 20, stream=None) -> float:
+        """Average device milliseconds of the collision sweep kernel alone (CUDA events on
+        the stream around nlaunch back-to-back launches)."""
+        ms = ctypes.c_float(0.0)
+        _check(lib().pb_dev_time_sweep(self._h, _dev_vec(f, self.nstate, "f"), int(nlaunch), ctypes.byref(ms),
+                                       _stream_ptr(stream)))
+        return float(ms.value)
 
     def rates(self, f, out=None, stream=None):
         """Scattering rates 1/tau_s (1/fs)."""

@@ -398,10 +398,13 @@ int resolve_opts(const pb_channels *ch, const pb_dev_opts *opts, int sm_count, p
   if (opts) d = *opts;
   if (d.variant < PB_VARIANT_FF || d.variant > PB_VARIANT_PAPER)
     return set_error(PB_EINVAL, "pb_dev: variant %d is not available in this build", d.variant);
-  if (d.ctas_per_sm <= 0) d.ctas_per_sm = 3;  // measured best on GB300 for the coefficient sweeps
+  if (d.merge_branches < 0 || d.merge_branches > 2) return set_error(PB_EINVAL, "pb_dev: merge_branches must be 0..2");
+  // measured best on GB300 at 40^3: 3 CTAs per SM for one entry per channel, 4 for the
+  // branch-merged sweep (whose stream is six times shorter)
+  const bool merged = (d.variant == PB_VARIANT_FF || d.variant == PB_VARIANT_F64) && d.merge_branches != 2;
+  if (d.ctas_per_sm <= 0) d.ctas_per_sm = merged ? 4 : 3;
   if (d.ctas_per_sm > 8) return set_error(PB_EINVAL, "pb_dev: ctas_per_sm must be <= 8");
   if (d.stream_mode < 0 || d.stream_mode > 2) return set_error(PB_EINVAL, "pb_dev: stream_mode must be 0..2");
-  if (d.merge_branches < 0 || d.merge_branches > 2) return set_error(PB_EINVAL, "pb_dev: merge_branches must be 0..2");
   if (d.channel_per_lane < 0 || d.channel_per_lane > 4)
     return set_error(PB_EINVAL, "pb_dev: channel_per_lane must be 0..4");
   if (d.transport_gather < 0 || d.transport_gather > 6 || d.transport_ctas < 0 || d.transport_ctas > 8)
@@ -427,7 +430,12 @@ bool merge_for(const pb_dev_opts &o) {
 int sweep_item_size(const pb_dev_opts *user, const pb_dev_opts &o, int64_t nsw, int sm) {
   if (user && user->item_channels > 0) return user->item_channels;
   if (o.stream_mode == 2) return 2048;
-  return default_item_channels(nsw, sm, o.ctas_per_sm);
+  // about two items per resident warp, 256..4096 entries: the per-item reduction and the
+  // finaliser's partial sums cost more than the tail of the last wave at this stream length
+  const int64_t warps = (int64_t)sm * o.ctas_per_sm * (dev::kBlock / 32);
+  int64_t ic = nsw / std::max<int64_t>(1, warps * 2);
+  ic = std::max<int64_t>(256, std::min<int64_t>(4096, ic));
+  return (int)(ic / 64 * 64);
 }
 
 // channel plan P and, for the branch-merged variants, the sweep plan S
@@ -1079,7 +1087,8 @@ int to_ff(pb_dev *d, const double *x, int64_t n, float2 *out, cudaStream_t st) {
   return PB_OK;
 }
 
-// Stage-input conversion the streaming kernel of this variant reads.
+// Stage-input conversion the streaming kernel of this variant reads (once per call: splitting
+// f inside every CTA of the sweep instead costs more, FP64 being slow on this part).
 int stage_input(pb_dev *d, const double *f, cudaStream_t st) {
   if (d->variant == PB_VARIANT_FF || d->variant == PB_VARIANT_PAPER) return to_ff(d, f, d->ns, d->yff, st);
   if (d->mixed()) {
@@ -1221,6 +1230,33 @@ extern "C" int pb_collision(pb_dev *d, const double *f, double *dfdt, void *stre
   if ((rc = launch_stream(d, dev::MODE_COLL, f, d->yff, st))) return rc;
   launch_fin<-1>(d, f, dfdt, nullptr, 0.0, st);
   PB_LAUNCHED("k_fin_coll");
+  return PB_OK;
+}
+
+extern "C" int pb_dev_time_sweep(pb_dev *d, const double *f, int32_t nlaunch, float *avg_ms, void *stream) {
+  clear_error();
+  if (!d || !f || !avg_ms) return set_error(PB_EINVAL, "pb_dev_time_sweep: null argument");
+  if (nlaunch < 1 || nlaunch > 10000) return set_error(PB_EINVAL, "pb_dev_time_sweep: nlaunch must be 1..10000");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc;
+  if ((rc = stage_input(d, f, st))) return rc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  PB_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return set_error(PB_ECUDA, "pb_dev_time_sweep: cudaEventCreate");
+  }
+  cudaError_t e = cudaEventRecord(e0, st);
+  for (int i = 0; i < nlaunch && e == cudaSuccess && rc == PB_OK; ++i) rc = launch_stream(d, dev::MODE_COLL, f, d->yff, st);
+  if (e == cudaSuccess && rc == PB_OK) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess && rc == PB_OK) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess && rc == PB_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "pb_dev_time_sweep");
+  *avg_ms = ms / (float)nlaunch;
   return PB_OK;
 }
 

@@ -196,6 +196,19 @@ def test_branch_merged_and_per_channel_sweeps(pb, name, variant, merge):
         assert dev.bytes_per_channel < other.bytes_per_channel
 
 
+def test_time_sweep_measures_without_changing_results(pb):
+    m = SMALL["win12"]()
+    o = oracle.Oracle(m)
+    dev = pb.Device(pb.Channels.from_model(m))
+    f = np.random.default_rng(8).uniform(0, 1, o.nstate)
+    before = dev.collision(T(f)).cpu().numpy()
+    ms = dev.time_sweep(T(f), 5)
+    assert 0.0 < ms < 100.0
+    assert np.array_equal(dev.collision(T(f)).cpu().numpy(), before)
+    with pytest.raises(pb.PBError):
+        dev.time_sweep(T(f), 0)
+
+
 @pytest.mark.parametrize("gather", [1, 2, 3, 4, 5, 6])
 def test_transport_sweep_shapes(pb, gather):
     """Every transport sweep shape (shared-memory or L1 gathers, 256- or 1024-thread CTAs,
