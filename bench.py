@@ -354,6 +354,27 @@ def batched_report(pb, ninst, nsteps, stream):
     ms_ffc, _ = sequential("ff", merge_branches=2)
     ms_g, _ = sequential("g32")
     b.close()
+
+    # the same batch on the FP64-accurate branch-merged stream
+    bf = pb.Batch(chs, precision="ff")
+    item_f, ctas_f, tune_f = bf.autotune(f)
+    g = f.clone()
+    bf.rk4(g, 1.0, 3)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    bf.rk4(g, 1.0, nsteps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_bf = e0.elapsed_time(e1)
+    If = bf.collision(f).cpu().numpy()
+    err_f = 0.0
+    for i, (c, x) in enumerate(zip(chs, fs)):
+        d = pb.Device(c)
+        ref = d.collision(torch.tensor(x, device="cuda")).cpu().numpy()
+        d.close()
+        a, e = bf.offsets[i], bf.offsets[i + 1]
+        err_f = max(err_f, float(np.abs(If[a:e] - ref).max() / max(np.abs(ref).max(), 1e-300)))
+    bf.close()
     return {"instances": ninst, "states": b.nstate, "channels": nch, "build_channels_s": build_s,
             "autotuned": {"item_channels": item, "ctas_per_sm": ctas, "sweep_ms": tune_ms},
             "rk4_steps": nsteps, "batched_ms": ms_b,
@@ -362,6 +383,12 @@ def batched_report(pb, ninst, nsteps, stream):
             "sequential_ff_ms": ms_ff, "sequential_ff_per_channel_ms": ms_ffc, "sequential_g32_ms": ms_g,
             "speedup_vs_sequential_fp32": ms_g / ms_b, "speedup_vs_sequential_ff": ms_ff / ms_b,
             "speedup_vs_sequential_ff_per_channel": ms_ffc / ms_b,
+            "ff_batch": {"autotuned": {"item_entries": item_f, "ctas_per_sm": ctas_f, "sweep_ms": tune_f},
+                         "batched_ms": ms_bf, "batched_rk4_steps_per_s": nsteps / (ms_bf * 1e-3),
+                         "batched_channels_per_s": 4 * nch * nsteps / (ms_bf * 1e-3),
+                         "speedup_vs_sequential_ff": ms_ff / ms_bf,
+                         "speedup_vs_sequential_ff_per_channel": ms_ffc / ms_bf,
+                         "dfdt_err_vs_unbatched_ff_max_over_instances": err_f},
             "dfdt_err_vs_fp64_max_over_instances": err}
 
 

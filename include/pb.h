@@ -282,17 +282,24 @@ int pb_dev_set_g2(pb_dev *dev, const double *g2, void *stream);
 /* ---------------------------------------------------------------- batched rt-BTE */
 
 /* Many independent systems (different grids, bands, modes, temperatures) advanced together:
- * one persistent launch per RK4 stage sweeps every instance's channels in the literal
- * per-channel form of Eq. 2 with |g|^2 stored in FP32 (rounded on the host), FP32
- * per-channel arithmetic with Kahan lane sums and FP64 states; a CUDA graph replays the
- * eight launches of a step.  Device vectors are the instances' state vectors concatenated
- * in instance order (offsets from pb_batch_get_info). */
+ * one persistent launch per RK4 stage sweeps every instance, followed by one epilogue
+ * launch; a CUDA graph replays the eight launches of a step.  Precision 0 (default): the
+ * literal per-channel form of Eq. 2 with |g|^2 stored in FP32 (rounded on the host), FP32
+ * per-channel arithmetic with Kahan lane sums and FP64 states.  Precision 1: the
+ * FP64-accurate branch-merged coefficient stream of the FF variant, each instance's
+ * prefactor folded into its coefficients.  Device vectors are the instances' state vectors
+ * concatenated in instance order (offsets from pb_batch_get_info). */
 typedef struct pb_batch pb_batch;
 
 typedef struct pb_batch_opts {
-  int32_t item_channels;  /* channels per work item (0 = 2048; else a multiple of 64, >= 1024) */
-  int32_t ctas_per_sm;    /* resident 512-thread CTAs per SM (0 = 2) */
-  int32_t reserved[2];
+  int32_t item_channels;  /* sweep entries per work item (0 = 2048; else a multiple of 64, >= 1024) */
+  int32_t ctas_per_sm;    /* resident CTAs per SM: 512-thread (precision 0, default 2) or 256-thread
+                             (precision 1, default 4); 0..4 */
+  int32_t precision;      /* 0: |g|^2 in FP32, the literal per-channel form of Eq. 2 in FP32 (one entry per
+                             channel); 1: FP64-accurate: each instance's coefficients computed in FP64,
+                             summed over the branches of every state pair, stored float-float (one entry
+                             per state pair) */
+  int32_t reserved;
 } pb_batch_opts;
 
 int pb_batch_arena_bytes(const pb_channels *const *chs, int32_t n, const pb_batch_opts *opts, size_t *bytes);
@@ -314,7 +321,7 @@ int pb_batch_collision(pb_batch *batch, const double *f, double *dfdt, void *str
 /* nsteps classic RK4 steps of every instance, in place on f (device double[nstate total]). */
 int pb_batch_rk4_step(pb_batch *batch, double *f, double dt, int32_t nsteps, void *stream);
 
-/* Time candidate launch shapes (work-item sizes 1024/2048/4096 channels x 2/3/4 CTAs per SM)
+/* Time candidate launch shapes (work-item sizes 1024/2048/4096 entries x 2/3/4 CTAs per SM)
  * on collision sweeps at f and keep the fastest; reports it (any pointer may be NULL).
  * Synchronises `stream`. */
 int pb_batch_autotune(pb_batch *batch, const double *f, void *stream, int32_t *best_item_channels,

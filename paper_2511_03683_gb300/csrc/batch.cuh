@@ -9,6 +9,12 @@
 // Eq. 2 in FP32 with Kahan lane sums, and one finaliser applies each state's prefactor and
 // the FP64 RK4 stage arithmetic.  A CUDA graph of the 8 launches replays each step.  The item
 // size and CTAs per SM come from a small autotuner that times candidate launch shapes.
+//
+// With pb_batch_opts.precision = 1 the batch streams FP64-accurate coefficients instead:
+// every instance's per-channel P_in and D are computed once in FP64 (its own grid, bands,
+// phonons, T and sigma), summed over the branches of each state pair and scaled by the
+// instance's 2 pi / (hbar N_q), then concatenated; the sweep and the RK4 stage epilogues are
+// the single-system float-float kernels run over all instances at once.
 
 namespace pb {
 namespace dev {
@@ -136,6 +142,12 @@ struct pb_batch {
   double *cs = nullptr;
   Part4 *part = nullptr;
   double *acc = nullptr, *y = nullptr;
+  // precision 1 (FP64-accurate, branch-merged): per-entry coefficients and global partner
+  // indices, per-state R (with the instance's prefactor folded in) and float-float stage input
+  int prec = 0;
+  float2 *pA = nullptr, *pB = nullptr, *yff = nullptr;
+  uint32_t *pidx = nullptr;
+  double *Rg = nullptr;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
   double *rk_f = nullptr;
@@ -229,6 +241,83 @@ BatchLayout batch_layout(const pb_channels *const *chs, int n, int64_t ns, int64
   return L;
 }
 
+// Sweep entries per row of the FP64-accurate batch: one per run of equal partner (state pair),
+// padded to kRowPad.
+std::vector<int64_t> batch_pair_lenp(const pb_channels *const *chs, int32_t n) {
+  std::vector<int64_t> lenp;
+  for (int i = 0; i < n; ++i)
+    for (int64_t r = 0; r < chs[i]->nstate; ++r) {
+      int64_t runs = 0;
+      for (int64_t c = chs[i]->row_ptr[r]; c < chs[i]->row_ptr[r + 1]; ++c)
+        if (c == chs[i]->row_ptr[r] || chs[i]->col[c] != chs[i]->col[c - 1]) ++runs;
+      lenp.push_back((runs + kRowPad - 1) / kRowPad * kRowPad);
+    }
+  return lenp;
+}
+
+struct BatchLayoutFF {
+  size_t items, item_inst, item_ptr, pA, pB, pidx, Rg, yff, part, acc, y, tcol, tg2, tcA, tcB, titems, titem_ptr, tpart,
+      tR, tpcst, tpcnt, omega_tmp, tab_tmp, eps_tmp, kc_tmp, total;
+};
+
+constexpr int kBatchSetupItem = 2048;  // channels per work item of the per-instance coefficient setup
+
+BatchLayoutFF batch_layout_ff(const pb_channels *const *chs, int n, int64_t ns, int64_t nent, int64_t nitems_cap) {
+  BatchLayoutFF L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + std::max<size_t>(bytes, 1));
+    return at;
+  };
+  size_t maxq = 0, maxs = 0, maxc = 0, maxp = 0, maxi = 0;
+  for (int i = 0; i < n; ++i) {
+    const pb_channels *ch = chs[i];
+    size_t c = 0, p = 0, it = 0;
+    for (int64_t r = 0; r < ch->nstate; ++r) {
+      const int64_t len = ch->row_ptr[r + 1] - ch->row_ptr[r], lp = (len + kRowPad - 1) / kRowPad * kRowPad;
+      c += (size_t)lp;
+      if (lp > 0) it += (size_t)std::max<int64_t>(1, (lp + kBatchSetupItem - 1) / kBatchSetupItem);
+      int64_t runs = 0;
+      for (int64_t k = ch->row_ptr[r]; k < ch->row_ptr[r + 1]; ++k)
+        if (k == ch->row_ptr[r] || ch->col[k] != ch->col[k - 1]) ++runs;
+      p += (size_t)((runs + kRowPad - 1) / kRowPad * kRowPad);
+    }
+    maxq = std::max(maxq, (size_t)ch->nq * ch->nmodes);
+    maxs = std::max(maxs, (size_t)ch->nstate);
+    maxc = std::max(maxc, c);
+    maxp = std::max(maxp, p);
+    maxi = std::max(maxi, it);
+  }
+  L.items = take(sizeof(Item) * nitems_cap);
+  L.item_inst = take(sizeof(int32_t) * nitems_cap);
+  L.item_ptr = take(sizeof(int32_t) * (ns + 1));
+  L.pA = take(sizeof(float2) * nent);
+  L.pB = take(sizeof(float2) * nent);
+  L.pidx = take(sizeof(uint32_t) * nent);
+  L.Rg = take(sizeof(double) * ns);
+  L.yff = take(sizeof(float2) * ns);
+  L.part = take(sizeof(Part4) * nitems_cap);
+  L.acc = take(sizeof(double) * ns);
+  L.y = take(sizeof(double) * ns);
+  L.tcol = take(sizeof(uint32_t) * maxc);
+  L.tg2 = take(sizeof(double) * maxc);
+  L.tcA = take(sizeof(float2) * maxc);
+  L.tcB = take(sizeof(float2) * maxc);
+  L.titems = take(sizeof(Item) * maxi);
+  L.titem_ptr = take(sizeof(int32_t) * (maxs + 1));
+  L.tpart = take(sizeof(Part4) * maxi);
+  L.tR = take(sizeof(double) * maxs);
+  L.tpcst = take(sizeof(int64_t) * maxp);
+  L.tpcnt = take(maxp);
+  L.omega_tmp = take(sizeof(double) * maxq);
+  L.tab_tmp = take(sizeof(double2) * maxq);
+  L.eps_tmp = take(sizeof(double) * maxs);
+  L.kc_tmp = take(sizeof(short4) * maxs);
+  L.total = o;
+  return L;
+}
+
 int batch_check(const pb_channels *const *chs, int32_t n, int64_t *ns, int64_t *nchp) {
   if (!chs || n <= 0) return set_error(PB_EINVAL, "pb_batch: need at least one channel list");
   int64_t s = 0, c = 0;
@@ -271,6 +360,14 @@ int batch_upload_plan(pb_batch *b, int item_ch, cudaStream_t st) {
 }
 
 int batch_sweep(pb_batch *b, cudaStream_t st) {
+  if (b->prec == 1) {
+    const int64_t need = (b->nitems * 32 + dev::kBlock - 1) / dev::kBlock;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)b->sm_count * b->ctas));
+    pb::dev::k_stream_ff<dev::MODE_COLL, false, uint32_t><<<grid, dev::kBlock, 0, st>>>(
+        b->items, (int)b->nitems, (const float4 *)b->pA, (const float4 *)b->pB, b->pidx, b->yff, (int)b->ns, b->part);
+    PB_LAUNCHED("k_stream_ff (batch)");
+    return PB_OK;
+  }
   const int64_t need = (b->nitems * 32 + 511) / 512;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)b->sm_count * b->ctas));
   pb::dev::k_stream_gbatch<dev::MODE_COLL><<<grid, 512, 0, st>>>(b->items, b->item_inst, (int)b->nitems, b->inst,
@@ -279,8 +376,16 @@ int batch_sweep(pb_batch *b, cudaStream_t st) {
   return PB_OK;
 }
 
+// src: the stage input (f for STAGE <= 0, y after), read by the FP64-accurate epilogue
 template <int STAGE>
-int batch_fin(pb_batch *b, double *out, double *f, double dt, cudaStream_t st) {
+int batch_fin(pb_batch *b, double *out, double *f, double dt, cudaStream_t st, const double *src) {
+  if (b->prec == 1) {
+    pb::dev::k_fin_coll<false, STAGE><<<(int)((b->ns + 255) / 256), 256, 0, st>>>(
+        b->item_ptr, b->part, (int)b->ns, 1.0, b->Rg, src, out, f, b->acc, b->y, b->yff, dt);
+    PB_LAUNCHED("k_fin_coll (batch)");
+    return PB_OK;
+  }
+  (void)src;
   pb::dev::k_fin_gbatch<STAGE><<<(int)((b->ns + 255) / 256), 256, 0, st>>>(b->item_ptr, b->part, (int)b->ns, b->cs,
                                                                             nullptr, out, f, b->acc, b->y, b->gstate, dt);
   PB_LAUNCHED("k_fin_gbatch");
@@ -288,6 +393,12 @@ int batch_fin(pb_batch *b, double *out, double *f, double dt, cudaStream_t st) {
 }
 
 int batch_stage_input(pb_batch *b, const double *f, cudaStream_t st) {
+  if (b->prec == 1) {
+    dev::k_to_ff<<<(int)std::max<int64_t>(1, std::min<int64_t>((b->ns + 255) / 256, 1024)), 256, 0, st>>>(
+        f, (long long)b->ns, b->yff);
+    PB_LAUNCHED("k_to_ff (batch)");
+    return PB_OK;
+  }
   dev::k_gstate_f<<<(int)((b->ns + 255) / 256), 256, 0, st>>>(f, (int)b->ns, b->gstate);
   PB_LAUNCHED("k_gstate_f");
   return PB_OK;
@@ -295,10 +406,133 @@ int batch_stage_input(pb_batch *b, const double *f, cudaStream_t st) {
 
 int batch_rk4_launches(pb_batch *b, double *f, double dt, cudaStream_t st) {
   int rc;
-  if ((rc = batch_sweep(b, st)) || (rc = batch_fin<0>(b, nullptr, f, dt, st))) return rc;
-  if ((rc = batch_sweep(b, st)) || (rc = batch_fin<1>(b, nullptr, f, dt, st))) return rc;
-  if ((rc = batch_sweep(b, st)) || (rc = batch_fin<2>(b, nullptr, f, dt, st))) return rc;
-  if ((rc = batch_sweep(b, st)) || (rc = batch_fin<3>(b, nullptr, f, dt, st))) return rc;
+  if ((rc = batch_sweep(b, st)) || (rc = batch_fin<0>(b, nullptr, f, dt, st, f))) return rc;
+  if ((rc = batch_sweep(b, st)) || (rc = batch_fin<1>(b, nullptr, f, dt, st, b->y))) return rc;
+  if ((rc = batch_sweep(b, st)) || (rc = batch_fin<2>(b, nullptr, f, dt, st, b->y))) return rc;
+  if ((rc = batch_sweep(b, st)) || (rc = batch_fin<3>(b, nullptr, f, dt, st, b->y))) return rc;
+  return PB_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Precision 1: per instance, the per-channel coefficients in FP64 on its own geometry
+// (k_coef over temporaries), R_s, the branch sums scaled by its prefactor into the shared
+// arrays, and the global partner indices.
+int batch_setup_ff(pb_batch *b, const pb_channels *const *chs, int n, const BatchLayoutFF &L, cudaStream_t st) {
+  char *A = b->arena;
+  uint32_t *tcol = (uint32_t *)(A + L.tcol);
+  double *tg2 = (double *)(A + L.tg2);
+  float2 *tcA = (float2 *)(A + L.tcA), *tcB = (float2 *)(A + L.tcB);
+  Item *titems = (Item *)(A + L.titems);
+  int32_t *titem_ptr = (int32_t *)(A + L.titem_ptr);
+  Part4 *tpart = (Part4 *)(A + L.tpart);
+  double *tR = (double *)(A + L.tR);
+  int64_t *tpcst = (int64_t *)(A + L.tpcst);
+  uint8_t *tpcnt = (uint8_t *)(A + L.tpcnt);
+  double *om = (double *)(A + L.omega_tmp);
+  double2 *tt = (double2 *)(A + L.tab_tmp);
+  double *ep = (double *)(A + L.eps_tmp);
+  short4 *kc = (short4 *)(A + L.kc_tmp);
+  int64_t poff = 0;  // first sweep entry of the instance
+  for (int i = 0; i < n; ++i) {
+    const pb_channels *ch = chs[i];
+    const int64_t ns_i = ch->nstate, so = b->soff[i];
+    if (ch->nk[0] > 32767 || ch->nk[1] > 32767 || ch->nk[2] > 32767)
+      return set_error(PB_EINVAL, "pb_batch_create: instance %d grid dimension above 32767", i);
+    // host: padded channel layout, setup items, pair entries
+    std::vector<int64_t> rp((size_t)ns_i + 1, 0);
+    for (int64_t r = 0; r < ns_i; ++r)
+      rp[r + 1] = rp[r] + (ch->row_ptr[r + 1] - ch->row_ptr[r] + kRowPad - 1) / kRowPad * kRowPad;
+    const int64_t nc = rp[ns_i];
+    std::vector<uint32_t> hcol((size_t)nc);
+    std::vector<double> hg2((size_t)nc, 0.0);
+    const int64_t np = [&] {
+      int64_t t = 0;
+      for (int64_t r = 0; r < ns_i; ++r) t += b->lenp[so + r];
+      return t;
+    }();
+    std::vector<uint32_t> hpidx((size_t)np);
+    std::vector<int64_t> hcst((size_t)np, 0);
+    std::vector<uint8_t> hcnt((size_t)np, 0);
+    int64_t e = 0;
+    for (int64_t r = 0; r < ns_i; ++r) {
+      const int64_t a = ch->row_ptr[r], len = ch->row_ptr[r + 1] - a;
+      for (int64_t k = 0; k < len; ++k) {
+        hcol[rp[r] + k] = (uint32_t)ch->col[a + k] | ((uint32_t)ch->nu[a + k] << kPartnerBits);
+        hg2[rp[r] + k] = ch->g2[a + k];
+      }
+      for (int64_t k = len; k < rp[r + 1] - rp[r]; ++k) hcol[rp[r] + k] = (uint32_t)r;
+      const int64_t e0 = e;
+      for (int64_t k = 0; k < len; ++k) {
+        if (k > 0 && ch->col[a + k] == ch->col[a + k - 1]) {
+          ++hcnt[e - 1];
+          continue;
+        }
+        hpidx[e] = (uint32_t)(so + ch->col[a + k]);
+        hcst[e] = rp[r] + k;
+        hcnt[e] = 1;
+        ++e;
+      }
+      for (; e < e0 + b->lenp[so + r]; ++e) hpidx[e] = (uint32_t)(so + r);
+    }
+    std::vector<Item> hit;
+    std::vector<int32_t> hptr;
+    plan_items(rp, kBatchSetupItem, hit, hptr);
+    std::vector<short4> hkc((size_t)ns_i);
+    const int N2 = ch->nk[1], N3 = ch->nk[2];
+    for (int64_t r = 0; r < ns_i; ++r) {
+      const int ik = ch->kidx[r];
+      hkc[r] = make_short4((short)(ik / (N2 * N3)), (short)((ik / N3) % N2), (short)(ik % N3), 0);
+    }
+    const size_t nq = (size_t)ch->nq * ch->nmodes;
+    PB_CUDA(cudaMemcpyAsync(tcol, hcol.data(), sizeof(uint32_t) * nc, cudaMemcpyHostToDevice, st));
+    PB_CUDA(cudaMemcpyAsync(tg2, hg2.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, st));
+    PB_CUDA(cudaMemcpyAsync(titems, hit.data(), sizeof(Item) * hit.size(), cudaMemcpyHostToDevice, st));
+    PB_CUDA(cudaMemcpyAsync(titem_ptr, hptr.data(), sizeof(int32_t) * hptr.size(), cudaMemcpyHostToDevice, st));
+    PB_CUDA(cudaMemcpyAsync(tpcst, hcst.data(), sizeof(int64_t) * np, cudaMemcpyHostToDevice, st));
+    PB_CUDA(cudaMemcpyAsync(tpcnt, hcnt.data(), np, cudaMemcpyHostToDevice, st));
+    PB_CUDA(cudaMemcpyAsync(b->pidx + poff, hpidx.data(), sizeof(uint32_t) * np, cudaMemcpyHostToDevice, st));
+    PB_CUDA(cudaMemcpyAsync(om, ch->omega.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, st));
+    PB_CUDA(cudaMemcpyAsync(ep, ch->eps.data(), sizeof(double) * ns_i, cudaMemcpyHostToDevice, st));
+    PB_CUDA(cudaMemcpyAsync(kc, hkc.data(), sizeof(short4) * ns_i, cudaMemcpyHostToDevice, st));
+    dev::k_table<<<(int)std::min<size_t>((nq + 255) / 256, 4096), 256, 0, st>>>(om, (long long)nq, kBoltz * ch->T, tt);
+    PB_LAUNCHED("k_table (batch)");
+    dev::ChanGeom g;
+    g.col = tcol;
+    g.g2 = tg2;
+    g.eps = ep;
+    g.kc = kc;
+    g.tab = tt;
+    g.N1 = ch->nk[0];
+    g.N2 = ch->nk[1];
+    g.N3 = ch->nk[2];
+    g.nmodes = ch->nmodes;
+    g.inv2s2 = 1.0 / (2.0 * ch->sigma * ch->sigma);
+    g.norm = 1.0 / (std::sqrt(2.0 * kPi) * ch->sigma);
+    const int nit = (int)hit.size();
+    if (nit > 0) {
+      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)nit * 32 + dev::kBlock - 1) / dev::kBlock,
+                                                                   (int64_t)b->sm_count * 8));
+      dev::k_coef<true><<<grid, dev::kBlock, 0, st>>>(titems, nit, g, tcA, tcB, tpart);
+      PB_LAUNCHED("k_coef (batch)");
+    }
+    const double c = 2.0 * kPi / (kHbar * (double)ch->nq);
+    if (ns_i > 0) {
+      dev::k_rowsum<<<(int)((ns_i + 255) / 256), 256, 0, st>>>(titem_ptr, tpart, (int)ns_i, tR);
+      PB_LAUNCHED("k_rowsum (batch)");
+      dev::k_scale_copy<<<(int)((ns_i + 255) / 256), 256, 0, st>>>(tR, (int)ns_i, c, b->Rg + so);
+      PB_LAUNCHED("k_scale_copy (batch)");
+    }
+    if (np > 0) {
+      dev::k_pair_coef<true><<<(int)std::min<int64_t>((np + 255) / 256, 8192), 256, 0, st>>>(
+          (const long long *)tpcst, tpcnt, (long long)np, tcA, tcB, b->pA + poff, b->pB + poff, c);
+      PB_LAUNCHED("k_pair_coef (batch)");
+    }
+    PB_CUDA(cudaStreamSynchronize(st));  // the temporaries are reused by the next instance
+    poff += np;
+  }
   return PB_OK;
 }
 
@@ -307,13 +541,24 @@ int batch_rk4_launches(pb_batch *b, double *f, double dt, cudaStream_t st) {
 extern "C" int pb_batch_arena_bytes(const pb_channels *const *chs, int32_t n, const pb_batch_opts *opts,
                                     size_t *bytes) {
   clear_error();
-  (void)opts;
   if (!bytes) return set_error(PB_EINVAL, "pb_batch_arena_bytes: null argument");
   int64_t ns = 0, nchp = 0;
   int rc = batch_check(chs, n, &ns, &nchp);
   if (rc) return rc;
-  const int64_t cap = batch_items_count(batch_lenp(chs, n), kBatchMinItem);
-  *bytes = batch_layout(chs, n, ns, nchp, cap).total;
+  const int prec = opts ? opts->precision : 0;
+  if (prec < 0 || prec > 1) return set_error(PB_EINVAL, "pb_batch: precision must be 0 or 1");
+  try {
+    if (prec == 1) {
+      const std::vector<int64_t> lenp = batch_pair_lenp(chs, n);
+      int64_t nent = 0;
+      for (int64_t l : lenp) nent += l;
+      *bytes = batch_layout_ff(chs, n, ns, nent, batch_items_count(lenp, kBatchMinItem)).total;
+    } else {
+      *bytes = batch_layout(chs, n, ns, nchp, batch_items_count(batch_lenp(chs, n), kBatchMinItem)).total;
+    }
+  } catch (const std::bad_alloc &) {
+    return set_error(PB_ENOMEM, "pb_batch_arena_bytes: out of host memory");
+  }
   return PB_OK;
 }
 
@@ -333,6 +578,7 @@ extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const p
   if (o.item_channels < 0 || (o.item_channels && (o.item_channels % 64 || o.item_channels < kBatchMinItem)))
     return set_error(PB_EINVAL, "pb_batch_create: item_channels must be 0 or a multiple of 64 >= %d", kBatchMinItem);
   if (o.ctas_per_sm < 0 || o.ctas_per_sm > 4) return set_error(PB_EINVAL, "pb_batch_create: ctas_per_sm must be 0..4");
+  if (o.precision < 0 || o.precision > 1) return set_error(PB_EINVAL, "pb_batch: precision must be 0 or 1");
   cudaStream_t st = (cudaStream_t)stream;
   pb_batch *b = new (std::nothrow) pb_batch();
   if (!b) return set_error(PB_ENOMEM, "pb_batch_create: out of host memory");
@@ -342,13 +588,49 @@ extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const p
     b->ns = ns;
     b->nchp = nchp;
     b->sm_count = sm;
-    b->lenp = batch_lenp(chs, n);
+    b->prec = o.precision;
+    b->lenp = b->prec == 1 ? batch_pair_lenp(chs, n) : batch_lenp(chs, n);
     b->nitems_cap = batch_items_count(b->lenp, kBatchMinItem);
     b->soff.assign(n + 1, 0);
     for (int i = 0; i < n; ++i) {
       b->soff[i + 1] = b->soff[i] + chs[i]->nstate;
       b->nch.push_back(chs[i]->nch);
       for (int64_t r = 0; r < chs[i]->nstate; ++r) b->row_inst.push_back(i);
+    }
+    if (b->prec == 1) {
+      int64_t nent = 0;
+      for (int64_t l : b->lenp) nent += l;
+      const BatchLayoutFF LF = batch_layout_ff(chs, n, ns, nent, b->nitems_cap);
+      if (bytes < LF.total) {
+        delete b;
+        return set_error(PB_ENOMEM, "pb_batch_create: arena of %zu bytes is smaller than the %zu needed", bytes,
+                         LF.total);
+      }
+      char *A = (char *)arena;
+      b->arena = A;
+      b->bytes = bytes;
+      b->items = (Item *)(A + LF.items);
+      b->item_inst = (int32_t *)(A + LF.item_inst);
+      b->item_ptr = (int32_t *)(A + LF.item_ptr);
+      b->pA = (float2 *)(A + LF.pA);
+      b->pB = (float2 *)(A + LF.pB);
+      b->pidx = (uint32_t *)(A + LF.pidx);
+      b->Rg = (double *)(A + LF.Rg);
+      b->yff = (float2 *)(A + LF.yff);
+      b->part = (Part4 *)(A + LF.part);
+      b->acc = (double *)(A + LF.acc);
+      b->y = (double *)(A + LF.y);
+      status = batch_setup_ff(b, chs, n, LF, st);
+      if (status == PB_OK) {
+        b->ctas = o.ctas_per_sm ? o.ctas_per_sm : 4;  // of 256 threads
+        status = batch_upload_plan(b, o.item_channels ? o.item_channels : 2048, st);
+      }
+      if (status != PB_OK) {
+        delete b;
+        return status;
+      }
+      *out = b;
+      return PB_OK;
     }
     const BatchLayout L = batch_layout(chs, n, ns, nchp, b->nitems_cap);
     if (bytes < L.total) {
@@ -494,7 +776,7 @@ extern "C" int pb_batch_collision(pb_batch *b, const double *f, double *dfdt, vo
   cudaStream_t st = (cudaStream_t)stream;
   int rc;
   if ((rc = batch_stage_input(b, f, st)) || (rc = batch_sweep(b, st))) return rc;
-  return batch_fin<-1>(b, dfdt, nullptr, 0.0, st);
+  return batch_fin<-1>(b, dfdt, nullptr, 0.0, st, f);
 }
 
 extern "C" int pb_batch_rk4_step(pb_batch *b, double *f, double dt, int32_t nsteps, void *stream) {

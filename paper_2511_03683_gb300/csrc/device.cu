@@ -1395,8 +1395,8 @@ int coef_setup(pb_dev *d, cudaStream_t st) {
     if (d->merged && d->nsw > 0) {
       const int pg = (int)std::min<int64_t>((d->nsw + 255) / 256, 8192);
       const long long* cs = (const long long *)d->pcstart;
-      if (ff) dev::k_pair_coef<true><<<pg, 256, 0, st>>>(cs, d->pcnt, (long long)d->nsw, d->ccoefA, d->ccoefB, d->coefA, d->coefB);
-      else    dev::k_pair_coef<false><<<pg, 256, 0, st>>>(cs, d->pcnt, (long long)d->nsw, d->ccoefA, d->ccoefB, d->coefA, d->coefB);
+      if (ff) dev::k_pair_coef<true><<<pg, 256, 0, st>>>(cs, d->pcnt, (long long)d->nsw, d->ccoefA, d->ccoefB, d->coefA, d->coefB, 1.0);
+      else    dev::k_pair_coef<false><<<pg, 256, 0, st>>>(cs, d->pcnt, (long long)d->nsw, d->ccoefA, d->ccoefB, d->coefA, d->coefB, 1.0);
       PB_LAUNCHED("k_pair_coef");
     }
   }

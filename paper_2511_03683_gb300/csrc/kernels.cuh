@@ -162,12 +162,12 @@ __global__ void __launch_bounds__(kBlock) k_coef(const Item *__restrict__ items,
 // Branch-merged coefficients.  For fixed eps, omega, sigma and T every branch nu of a state
 // pair (s, p) enters Eq. 2 through the same f_s and f_p, so the coefficient form only needs
 // the sums over nu:  P_in(s,p) = sum_nu P_in(s,p,nu),  D(s,p) = sum_nu D(s,p,nu).  Entry k
-// sums the cnt[k] consecutive channels from cstart[k] in FP64 (ascending nu) and stores the
-// result in the sweep's format; padding entries (cnt 0) become zero.
+// sums the cnt[k] consecutive channels from cstart[k] in FP64 (ascending nu), multiplies by
+// scale and stores the result in the sweep's format; padding entries (cnt 0) become zero.
 template <bool FF>
 __global__ void k_pair_coef(const long long *__restrict__ cstart, const uint8_t *__restrict__ cnt, long long n,
                             const void *__restrict__ cA, const void *__restrict__ cB, void *__restrict__ pA,
-                            void *__restrict__ pB) {
+                            void *__restrict__ pB, double scale) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
     const long long s = cstart[k];
     const int m = cnt[k];
@@ -182,6 +182,8 @@ __global__ void k_pair_coef(const long long *__restrict__ cstart, const uint8_t 
         b += ((const double *)cB)[s + i];
       }
     }
+    a *= scale;
+    b *= scale;
     if (FF) {
       ((float2 *)pA)[k] = ff_split(a);
       ((float2 *)pB)[k] = ff_split(b);
@@ -190,6 +192,12 @@ __global__ void k_pair_coef(const long long *__restrict__ cstart, const uint8_t 
       ((double *)pB)[k] = b;
     }
   }
+}
+
+// dst[i] = scale * src[i]
+__global__ void k_scale_copy(const double *__restrict__ src, int n, double scale, double *__restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = scale * src[i];
 }
 
 // Transport weights from the coefficient arrays: W = c (P_in + (1 - f0_p) D), which equals

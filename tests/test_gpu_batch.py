@@ -83,3 +83,57 @@ def test_batch_autotune_keeps_results(pb, batch):
     assert item in (1024, 2048, 4096) and ctas in (2, 3, 4) and ms > 0
     after = b.collision(ft).cpu().numpy()
     assert np.abs(after - before).max() <= 1e-6 * np.abs(before).max()
+
+
+# ------------------------------------------------------------------ FP64-accurate batch (precision "ff")
+
+@pytest.fixture(scope="module")
+def batch_ff(pb, batch):
+    inst, chs, _, f = batch
+    return pb.Batch(chs, precision="ff")
+
+
+def test_ff_batch_collision_matches_oracle_and_unbatched(pb, batch, batch_ff):
+    """The branch-merged float-float batch: every instance's df/dt meets its FP64 oracle at
+    the FF bound and agrees with the same instance on its own device to rounding."""
+    import torch
+
+    inst, chs, _, _ = batch
+    b = batch_ff
+    rng = np.random.default_rng(19)
+    fr = rng.uniform(0, 1, b.nstate)
+    I = b.collision(torch.tensor(fr, device="cuda")).cpu().numpy()
+    for i, ((m, _), ch) in enumerate(zip(inst, chs)):
+        a, e = b.offsets[i], b.offsets[i + 1]
+        ref, ab = oracle.Oracle(m).collision(fr[a:e], with_abs=True)
+        d = np.abs(I[a:e] - ref).max()
+        assert d <= 1e-13 * ab.max()
+        if np.abs(ref).max() >= 1e-2 * ab.max():
+            assert d <= 1e-12 * np.abs(ref).max()
+        own = pb.Device(ch).collision(torch.tensor(fr[a:e], device="cuda")).cpu().numpy()
+        assert np.abs(I[a:e] - own).max() <= 1e-14 * ab.max()
+
+
+def test_ff_batch_rk4_matches_oracle(pb, batch, batch_ff):
+    import torch
+
+    inst, chs, _, f = batch
+    ft = torch.tensor(f, device="cuda")
+    batch_ff.rk4(ft, 1.0, 5)
+    got = ft.cpu().numpy()
+    for i, ((m, _), ch) in enumerate(zip(inst[:4], chs[:4])):
+        a, e = batch_ff.offsets[i], batch_ff.offsets[i + 1]
+        ref = oracle.Oracle(m).rk4(f[a:e], 1.0, 5)
+        assert np.abs(got[a:e] - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_ff_batch_autotune_keeps_results(pb, batch, batch_ff):
+    import torch
+
+    _, _, _, f = batch
+    ft = torch.tensor(f, device="cuda")
+    before = batch_ff.collision(ft).cpu().numpy()
+    item, ctas, ms = batch_ff.autotune(ft)
+    assert item in (1024, 2048, 4096) and ctas in (2, 3, 4) and ms > 0
+    after = batch_ff.collision(ft).cpu().numpy()
+    assert np.abs(after - before).max() <= 1e-12 * np.abs(before).max()
