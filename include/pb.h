@@ -172,6 +172,10 @@ typedef struct pb_dev_opts {
                                 every state pair (s, p) once at setup and stream one entry per pair (Eq. 2
                                 depends on nu only through |g|^2, N and the deltas, all fixed with eps,
                                 omega, sigma and T); 2 stream one entry per channel */
+  int32_t dense_rows;        /* FF, branch-merged: 0 automatic (= 1); 1 when every row holds every window
+                                state in order (no cutoffs), the collision, rate and transport sweeps take
+                                each entry's partner from its position and stream no index (16 instead of
+                                18 bytes per entry); 2 always stream the index */
 } pb_dev_opts;
 
 typedef struct pb_dev pb_dev; /* opaque host handle describing device-resident data */

@@ -12,6 +12,8 @@
 #include "kernels.cuh"
 #include "pb_internal.h"
 
+static_assert(pb::kRowPad == pb::dev::kEntryPad, "host row padding and the kernels' entry padding must agree");
+
 using namespace pb;
 using pb::dev::Item;
 using pb::dev::Part4;
@@ -27,7 +29,7 @@ struct Layout {
   size_t rp, item_ptr, items, col, coefA, coefB, g2, wt, eps, kc, R, omega, tab, part, acc, y, yff, fstage, Fa, Fb,
       Fff, tau, invtau, red, scal, obs, g2lo, gstate, tab32, col16, rp_real, vjpG, vecs, hcol, hg2, hA, hB, sc,
       entries, hitems, titems, t_item_ptr, err, citems, citem_ptr, cpart, ccoefA, ccoefB, sidx16, sidx32, pcstart,
-      pcnt, total;
+      pcnt, srp, total;
 };
 
 struct Plan {
@@ -50,16 +52,20 @@ int default_item_channels(int64_t nchp, int sm_count, int ctas) {
 void plan_items(const std::vector<int64_t> &rp, int item_ch, std::vector<Item> &items, std::vector<int32_t> &ptr);
 
 // Branch-merged sweep (FF and F64): one entry per state pair (s, p) = per run of equal partner
-// in the CSR row, rows padded to kRowPad entries.  rp: padded entry offsets [ns+1].
-void pair_rows(const pb_channels *ch, std::vector<int64_t> &rp) {
+// in the CSR row, rows padded to kRowPad entries.  rp: padded entry offsets [ns+1].  Returns
+// whether every row is complete (its partners are all nstate window states, in order).
+bool pair_rows(const pb_channels *ch, std::vector<int64_t> &rp) {
   const int64_t ns = ch->nstate;
   rp.assign(ns + 1, 0);
+  bool complete = true;
   for (int64_t r = 0; r < ns; ++r) {
     int64_t runs = 0;
     for (int64_t c = ch->row_ptr[r]; c < ch->row_ptr[r + 1]; ++c)
       if (c == ch->row_ptr[r] || ch->col[c] != ch->col[c - 1]) ++runs;
+    complete = complete && runs == ns;
     rp[r + 1] = rp[r] + (runs + kRowPad - 1) / kRowPad * kRowPad;
   }
+  return complete;
 }
 
 void plan_from_rp(const std::vector<int64_t> &rp, int item_ch, Plan &P) {
@@ -160,6 +166,7 @@ Layout make_layout(const pb_channels *ch, const Plan &P, const Plan *S, int vari
   L.sidx32 = take(S && ns > 65536 ? sizeof(uint32_t) * nsw : 0);
   L.pcstart = take(S ? sizeof(int64_t) * nsw : 0);
   L.pcnt = take(S ? nsw : 0);
+  L.srp = take(S ? sizeof(int64_t) * (ns + 1) : 0);
   L.wt = take(transport ? sizeof(float2) * nsw : 0);
   L.eps = take(sizeof(double) * ns);
   L.kc = take(sizeof(short4) * ns);
@@ -317,6 +324,10 @@ struct pb_dev {
   uint32_t *sidx32 = nullptr;
   int64_t *pcstart = nullptr;     // first channel of each sweep entry
   uint8_t *pcnt = nullptr;        // channels of each sweep entry
+  // complete rows (every row holds every window state, in order): the FF collision and the
+  // transport sweeps take each entry's partner from its position and stream no index
+  bool dense = false;
+  int64_t *srp = nullptr;         // first sweep entry of every row [ns+1]
   int64_t *rp_real = nullptr;  // unpadded CSR row offsets [ns+1]
   float2 *vjpG = nullptr;      // adjoint gather table [ns][3]
   double *vecs = nullptr;      // 8 scratch vectors of nstate doubles (adjoint stages)
@@ -399,6 +410,7 @@ int resolve_opts(const pb_channels *ch, const pb_dev_opts *opts, int sm_count, p
   if (d.variant < PB_VARIANT_FF || d.variant > PB_VARIANT_PAPER)
     return set_error(PB_EINVAL, "pb_dev: variant %d is not available in this build", d.variant);
   if (d.merge_branches < 0 || d.merge_branches > 2) return set_error(PB_EINVAL, "pb_dev: merge_branches must be 0..2");
+  if (d.dense_rows < 0 || d.dense_rows > 2) return set_error(PB_EINVAL, "pb_dev: dense_rows must be 0..2");
   // measured best on GB300 at 40^3: 3 CTAs per SM for one entry per channel, 4 for the
   // branch-merged sweep (whose stream is six times shorter)
   const bool merged = (d.variant == PB_VARIANT_FF || d.variant == PB_VARIANT_F64) && d.merge_branches != 2;
@@ -427,24 +439,34 @@ bool merge_for(const pb_dev_opts &o) {
 }
 
 // work-item size of the branch-merged sweep: the caller's, the bulk ring's, or the default
-int sweep_item_size(const pb_dev_opts *user, const pb_dev_opts &o, int64_t nsw, int sm) {
+int sweep_item_size(const pb_dev_opts *user, const pb_dev_opts &o, const std::vector<int64_t> &rp, int sm) {
   if (user && user->item_channels > 0) return user->item_channels;
   if (o.stream_mode == 2) return 2048;
-  // about two items per resident warp, 256..4096 entries: the per-item reduction and the
-  // finaliser's partial sums cost more than the tail of the last wave at this stream length
+  // about two items per resident warp, each row cut into equal pieces (256..4096 entries):
+  // the per-item reduction and the finaliser's partial sums cost more than the tail of the
+  // last wave at this stream length
+  const int64_t ns = (int64_t)rp.size() - 1, nsw = rp.back();
+  int64_t rows = 0;
+  for (int64_t r = 0; r < ns; ++r) rows += rp[r + 1] > rp[r];
+  if (rows == 0) return 256;
   const int64_t warps = (int64_t)sm * o.ctas_per_sm * (dev::kBlock / 32);
-  int64_t ic = nsw / std::max<int64_t>(1, warps * 2);
-  ic = std::max<int64_t>(256, std::min<int64_t>(4096, ic));
-  return (int)(ic / 64 * 64);
+  const int64_t per_row = std::max<int64_t>(1, (2 * warps + rows / 2) / rows);  // pieces per row
+  int64_t ic = (nsw / rows + per_row - 1) / per_row;
+  ic = std::max<int64_t>(256, std::min<int64_t>(4096, (ic + 63) / 64 * 64));
+  return (int)ic;
 }
 
-// channel plan P and, for the branch-merged variants, the sweep plan S
-bool make_plans(const pb_channels *ch, const pb_dev_opts *user, const pb_dev_opts &o, int sm, Plan &P, Plan &S) {
+// channel plan P and, for the branch-merged variants, the sweep plan S (complete: every row
+// holds every window state)
+bool make_plans(const pb_channels *ch, const pb_dev_opts *user, const pb_dev_opts &o, int sm, Plan &P, Plan &S,
+                bool *complete = nullptr) {
   make_plan(ch, o.item_channels, P);
+  if (complete) *complete = false;
   if (!merge_for(o)) return false;
   std::vector<int64_t> rp;
-  pair_rows(ch, rp);
-  plan_from_rp(rp, sweep_item_size(user, o, rp.back(), sm), S);
+  const bool c = pair_rows(ch, rp);
+  if (complete) *complete = c;
+  plan_from_rp(rp, sweep_item_size(user, o, rp, sm), S);
   return true;
 }
 
@@ -543,6 +565,8 @@ template <typename IDX>
 void set_stream_smem(int bytes) {
   cudaFuncSetAttribute(dev::k_stream_ff<dev::MODE_COLL, true, IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   cudaFuncSetAttribute(dev::k_stream_ff<dev::MODE_RATE, true, IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(dev::k_stream_ff<dev::MODE_COLL, true, IDX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(dev::k_stream_ff<dev::MODE_RATE, true, IDX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   cudaFuncSetAttribute(dev::k_stream_f64<dev::MODE_COLL, true, IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   cudaFuncSetAttribute(dev::k_stream_f64<dev::MODE_RATE, true, IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
@@ -594,9 +618,9 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   pb_dev *d = new (std::nothrow) pb_dev();
   if (!d) return set_error(PB_ENOMEM, "pb_dev_create: out of host memory");
   Plan P, S;
-  bool merged = false;
+  bool merged = false, complete = false;
   try {
-    merged = make_plans(ch, opts, o, sm, P, S);
+    merged = make_plans(ch, opts, o, sm, P, S, &complete);
   } catch (const std::bad_alloc &) {
     delete d;
     return set_error(PB_ENOMEM, "pb_dev_create: out of host memory");
@@ -688,6 +712,7 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
     d->sidx32 = d->ns <= 65536 ? nullptr : (uint32_t *)(A + L.sidx32);
     d->pcstart = (int64_t *)(A + L.pcstart);
     d->pcnt = (uint8_t *)(A + L.pcnt);
+    d->srp = (int64_t *)(A + L.srp);
   } else {
     d->citems = d->items;
     d->citem_ptr = d->item_ptr;
@@ -702,7 +727,8 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   int devid = 0, smem_optin = 0;
   cudaGetDevice(&devid);
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, devid);
-  size_t fbytes = (d->variant == PB_VARIANT_F64 ? sizeof(double) : sizeof(float2)) * (size_t)d->ns;
+  const size_t ns8 = (size_t)((d->ns + kRowPad - 1) / kRowPad * kRowPad);  // zero-padded for complete rows
+  size_t fbytes = d->variant == PB_VARIANT_F64 ? sizeof(double) * (size_t)d->ns : sizeof(float2) * ns8;
   if (d->mixed()) {
     fbytes = sizeof(uint4) * (size_t)d->ns;
     if (fbytes + 1024 > (size_t)smem_optin) {
@@ -721,7 +747,7 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   const size_t per_cta_budget = (size_t)(228 * 1024) / (size_t)d->ctas - 1024;
   d->smem_f = (fbytes <= per_cta_budget && fbytes <= (size_t)smem_optin) ? fbytes : 0;
   if (d->mixed()) d->smem_f = fbytes;
-  const size_t Fbytes = sizeof(float2) * 3 * (size_t)d->ns;
+  const size_t Fbytes = sizeof(float2) * 3 * ns8;
   const bool F_fits = Fbytes <= (size_t)smem_optin - 1024;
   // automatic: gather F through L1 (measured faster on GB300 than shared-memory staging,
   // which limits residency to one 512-thread CTA per SM at 40^3)
@@ -759,6 +785,8 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
     delete d;
     return set_error(PB_EINVAL, "pb_dev_create: F of %lld states does not fit in shared memory", (long long)ch->nstate);
   }
+  // complete rows: the FF sweeps take partners from entry positions (needs f in shared memory)
+  d->dense = merged && complete && o.dense_rows != 2 && d->variant == PB_VARIANT_FF && d->smem_f && !d->bulk;
   d->ctas_tr = d->smem_F ? (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(228 * 1024) / (d->smem_F + 1024))) : 8;
   if (o.transport_ctas > 0) d->ctas_tr = std::min(d->ctas_tr, o.transport_ctas);
   if (!d->smem_F && o.transport_ctas > 0) d->ctas_tr = o.transport_ctas;
@@ -846,6 +874,7 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
         }
         UP(d->pcstart, cst.data(), sizeof(int64_t) * S.nchp);
         UP(d->pcnt, cn.data(), S.nchp);
+        UP(d->srp, S.rp.data(), sizeof(int64_t) * (d->ns + 1));
         cudaError_t e_ = cudaStreamSynchronize(st);  // pageable sources above go out of scope
         if (e_ != cudaSuccess) {
           status = cuda_fail(e_, "upload");
@@ -900,6 +929,8 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaFuncSetAttribute(dev::k_stream_tr_lane<uint32_t, 1024, true, true, true>, A, (int)d->smem_F1k);
     cudaFuncSetAttribute(dev::k_stream_tr_lane<uint16_t, 1024, true, true, true>, A, (int)d->smem_F1k);
+    cudaFuncSetAttribute(dev::k_stream_tr_lane<uint32_t, 1024, true, true, true, true>, A, (int)d->smem_F1k);
+    cudaFuncSetAttribute(dev::k_stream_tr_lane<uint16_t, 1024, true, true, true, true>, A, (int)d->smem_F1k);
   }
   {
     const size_t gb = sizeof(float2) * 3 * (size_t)d->ns;
@@ -962,7 +993,8 @@ extern "C" int pb_dev_get_info(const pb_dev *d, pb_dev_info *info) {
   switch (d->variant) {
     // streamed bytes per physical channel: per sweep entry (state pair when branch-merged)
     case PB_VARIANT_FF:
-      info->bytes_per_channel = (2 * sizeof(float2) + (d->sidx16 ? 2 : 4)) * (d->merged ? (double)d->nsw / (double)d->nch : 1.0);
+      info->bytes_per_channel = (2 * sizeof(float2) + (d->dense ? 0 : d->sidx16 ? 2 : 4)) *
+                                (d->merged ? (double)d->nsw / (double)d->nch : 1.0);
       break;
     case PB_VARIANT_F64:
       info->bytes_per_channel = (2 * sizeof(double) + (d->sidx16 ? 2 : 4)) * (d->merged ? (double)d->nsw / (double)d->nch : 1.0);
@@ -996,7 +1028,11 @@ int launch_stream_t(pb_dev *d, int mode, const double *fd, const float2 *fff, co
                                                                  d->bulk_cap, part, d->err);
   } else if (d->variant == PB_VARIANT_FF) {
     const float4 *A4 = (const float4 *)d->coefA, *B4 = (const float4 *)d->coefB;
-    if (d->smem_f) {
+    const long long *srp = (const long long *)d->srp;
+    if (d->dense) {
+      if (coll) dev::k_stream_ff<dev::MODE_COLL, true, IDX, true><<<grid, dev::kBlock, d->smem_f, st>>>(d->items, n, A4, B4, colp, fff, ns, part, srp);
+      else      dev::k_stream_ff<dev::MODE_RATE, true, IDX, true><<<grid, dev::kBlock, d->smem_f, st>>>(d->items, n, A4, B4, colp, fff, ns, part, srp);
+    } else if (d->smem_f) {
       if (coll) dev::k_stream_ff<dev::MODE_COLL, true, IDX><<<grid, dev::kBlock, d->smem_f, st>>>(d->items, n, A4, B4, colp, fff, ns, part);
       else      dev::k_stream_ff<dev::MODE_RATE, true, IDX><<<grid, dev::kBlock, d->smem_f, st>>>(d->items, n, A4, B4, colp, fff, ns, part);
     } else {
@@ -1181,7 +1217,11 @@ void launch_tr_lane(pb_dev *d, const IDX *col, const float2 *Fin, cudaStream_t s
   const int grid1k = (int)std::max<int64_t>(1, std::min<int64_t>((d->nitems * 32 + 1023) / 1024, d->sm_count));
   switch (d->tr_shape) {
     case 4:
-      k_stream_tr_lane<IDX, 1024, true, true, true><<<grid1k, 1024, d->smem_F1k, st>>>(d->items, n, d->wt, col, Fin, ns, d->part);
+      if (d->dense)
+        k_stream_tr_lane<IDX, 1024, true, true, true, true><<<grid1k, 1024, d->smem_F1k, st>>>(
+            d->items, n, d->wt, col, Fin, ns, d->part, (const long long *)d->srp);
+      else
+        k_stream_tr_lane<IDX, 1024, true, true, true><<<grid1k, 1024, d->smem_F1k, st>>>(d->items, n, d->wt, col, Fin, ns, d->part);
       break;
     case 5:
       k_stream_tr_lane<IDX, 1024, false, true, true><<<grid1k, 1024, 0, st>>>(d->items, n, d->wt, col, Fin, ns, d->part);

@@ -31,6 +31,7 @@ struct Item {
 };
 
 constexpr int kBlock = 256;  // threads per CTA of the streaming kernels
+constexpr int kEntryPad = 8;  // rows of every stream are padded to a multiple of this many entries
 
 // Per-item partial sums (up to three accumulators plus one spare), 32-byte aligned.
 struct alignas(32) Part4 {
@@ -295,18 +296,45 @@ __device__ __forceinline__ uint4 partners4<uint16_t>(const uint16_t *__restrict_
 // ------------------------------------------------------------ streaming kernels
 enum { MODE_COLL = 0, MODE_RATE = 1 };
 
-// Float-float coefficient stream.  Channel c: coefA[c] = P_in (hi,lo), coefB[c] = D (hi,lo),
-// col4 = packed partner index.  One warp per item, each lane two 4-channel groups per trip.
+// The four occupations (float-float) of the entries of group q (4 consecutive entries): gathered
+// through their partner indices, or, for complete rows (DENSE: the row's entries are its
+// partners 0, 1, 2, ... in order), read as two 16-byte words from shared memory at pe, the
+// partner of the group's first entry.
+template <bool DENSE, typename IDX>
+__device__ __forceinline__ void group_f(const float2 *__restrict__ fv, const IDX *__restrict__ colp, long long q,
+                                        int pe, float2 &f0, float2 &f1, float2 &f2, float2 &f3) {
+  if (DENSE) {
+    const float4 x = ((const float4 *)fv)[pe >> 1], y = ((const float4 *)fv)[(pe >> 1) + 1];
+    f0 = make_float2(x.x, x.y);
+    f1 = make_float2(x.z, x.w);
+    f2 = make_float2(y.x, y.y);
+    f3 = make_float2(y.z, y.w);
+  } else {
+    const uint4 c = partners4(colp, q);
+    f0 = fv[c.x];
+    f1 = fv[c.y];
+    f2 = fv[c.z];
+    f3 = fv[c.w];
+  }
+}
+
+// Float-float coefficient stream.  Entry c (a channel, or a state pair of the branch-merged
+// sweep): coefA[c] = P_in (hi,lo), coefB[c] = D (hi,lo), colp = partner index.  One warp per
+// item, each lane two 4-entry groups per trip.
 // part[item] = (A, B) where A = sum f_p P_in, B = sum f_p D (MODE_RATE: only B).
-template <int MODE, bool SMEM, typename IDX>
+// DENSE (with SMEM only): complete rows, no index stream; srp holds the rows' first entries
+// and the shared-memory copy of f is zero-padded to a multiple of kEntryPad states.
+template <int MODE, bool SMEM, typename IDX, bool DENSE = false>
 __global__ void __launch_bounds__(kBlock) k_stream_ff(const Item *__restrict__ items, int nitems,
                                                       const float4 *__restrict__ A4, const float4 *__restrict__ B4,
                                                       const IDX *__restrict__ colp,
                                                       const float2 *__restrict__ fg, int ns,
-                                                      Part4 *__restrict__ part) {
+                                                      Part4 *__restrict__ part,
+                                                      const long long *__restrict__ srp = nullptr) {
   extern __shared__ float2 fsm[];
   if (SMEM) {
-    for (int i = threadIdx.x; i < ns; i += blockDim.x) fsm[i] = fg[i];
+    const int nsp = DENSE ? (ns + kEntryPad - 1) / kEntryPad * kEntryPad : ns;
+    for (int i = threadIdx.x; i < nsp; i += blockDim.x) fsm[i] = i < ns ? fg[i] : make_float2(0.f, 0.f);
     __syncthreads();
   }
   const float2 *__restrict__ fv = SMEM ? fsm : fg;
@@ -317,11 +345,14 @@ __global__ void __launch_bounds__(kBlock) k_stream_ff(const Item *__restrict__ i
     const Item I = items[it];
     const long long g0 = I.start >> 2;
     const int ng = I.len >> 2;
+    const int pb0 = DENSE ? (int)(I.start - srp[I.row]) : 0;  // partner of the item's first entry
     float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;
     int g = lane;
     for (; g + 32 < ng; g += 64) {
       const long long q0 = g0 + g, q1 = q0 + 32;
-      const uint4 c0 = partners4(colp, q0), c1 = partners4(colp, q1);
+      float2 f0, f1, f2, f3, f4, f5, f6, f7;
+      group_f<DENSE>(fv, colp, q0, pb0 + 4 * g, f0, f1, f2, f3);
+      group_f<DENSE>(fv, colp, q1, pb0 + 4 * g + 128, f4, f5, f6, f7);
       float4 a00, a01, a10, a11;
       if (MODE == MODE_COLL) {
         a00 = __ldcs(A4 + 2 * q0); a01 = __ldcs(A4 + 2 * q0 + 1);
@@ -329,8 +360,6 @@ __global__ void __launch_bounds__(kBlock) k_stream_ff(const Item *__restrict__ i
       }
       const float4 b00 = __ldcs(B4 + 2 * q0), b01 = __ldcs(B4 + 2 * q0 + 1);
       const float4 b10 = __ldcs(B4 + 2 * q1), b11 = __ldcs(B4 + 2 * q1 + 1);
-      const float2 f0 = fv[c0.x], f1 = fv[c0.y], f2 = fv[c0.z], f3 = fv[c0.w];
-      const float2 f4 = fv[c1.x], f5 = fv[c1.y], f6 = fv[c1.z], f7 = fv[c1.w];
       if (MODE == MODE_COLL) {
         ff_mac(ah, al, f0, a00.x, a00.y); ff_mac(ah, al, f1, a00.z, a00.w);
         ff_mac(ah, al, f2, a01.x, a01.y); ff_mac(ah, al, f3, a01.z, a01.w);
@@ -344,8 +373,8 @@ __global__ void __launch_bounds__(kBlock) k_stream_ff(const Item *__restrict__ i
     }
     if (g < ng) {
       const long long q0 = g0 + g;
-      const uint4 c0 = partners4(colp, q0);
-      const float2 f0 = fv[c0.x], f1 = fv[c0.y], f2 = fv[c0.z], f3 = fv[c0.w];
+      float2 f0, f1, f2, f3;
+      group_f<DENSE>(fv, colp, q0, pb0 + 4 * g, f0, f1, f2, f3);
       if (MODE == MODE_COLL) {
         const float4 a00 = __ldcs(A4 + 2 * q0), a01 = __ldcs(A4 + 2 * q0 + 1);
         ff_mac(ah, al, f0, a00.x, a00.y); ff_mac(ah, al, f1, a00.z, a00.w);
@@ -692,16 +721,20 @@ __device__ __forceinline__ void tr_mac3(float (&acc)[6], const float2 *Fp, float
 // weights (8 B) and indices stay fully coalesced across the warp.  Four channels per lane per
 // trip.  Shapes: NT = 256 with F gathered through L1 (eight CTAs per SM), or NT = 1024 (one
 // CTA per SM) with F staged in shared memory (SMEMF) and the next trip's weights and indices
-// loaded into registers before this trip's gathers (RP).
-template <typename IDX, int NT, bool SMEMF, bool RP, bool LAZY>
+// loaded into registers before this trip's gathers (RP).  DENSE (with SMEMF only): complete
+// rows, the partner of entry j is the entry's position in its row (srp: the rows' first
+// entries), no index stream; F in shared memory is zero-padded to a multiple of kEntryPad states.
+template <typename IDX, int NT, bool SMEMF, bool RP, bool LAZY, bool DENSE = false>
 __global__ void __launch_bounds__(NT, NT == 1024 ? 1 : 8) k_stream_tr_lane(const Item *__restrict__ items, int nitems,
                                                           const float2 *__restrict__ W,
                                                           const IDX *__restrict__ colp,
                                                           const float2 *__restrict__ F, int ns,
-                                                          Part4 *__restrict__ part) {
+                                                          Part4 *__restrict__ part,
+                                                          const long long *__restrict__ srp = nullptr) {
   extern __shared__ float2 Fs[];
   if (SMEMF) {
-    for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) Fs[i] = F[i];
+    const int nsp = DENSE ? (ns + kEntryPad - 1) / kEntryPad * kEntryPad : ns;
+    for (int i = threadIdx.x; i < 3 * nsp; i += blockDim.x) Fs[i] = i < 3 * ns ? F[i] : make_float2(0.f, 0.f);
     __syncthreads();
   }
   const float2 *__restrict__ Fg = SMEMF ? Fs : F;
@@ -711,6 +744,7 @@ __global__ void __launch_bounds__(NT, NT == 1024 ? 1 : 8) k_stream_tr_lane(const
   for (int it = warp; it < nitems; it += nwarps) {
     const Item I = items[it];
     const long long c0 = I.start;
+    const int pb0 = DENSE ? (int)(c0 - srp[I.row]) : 0;  // partner of the item's first entry
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int j = lane;
     bool full = j + 96 < I.len;
@@ -720,7 +754,7 @@ __global__ void __launch_bounds__(NT, NT == 1024 ? 1 : 8) k_stream_tr_lane(const
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         wv[k] = __ldcs(W + c0 + at + 32 * k);
-        pv[k] = (unsigned)__ldcs(colp + c0 + at + 32 * k) & 0xFFFFFFu;
+        pv[k] = DENSE ? (unsigned)(pb0 + at + 32 * k) : (unsigned)__ldcs(colp + c0 + at + 32 * k) & 0xFFFFFFu;
       }
     };
     if (RP && full) load(j, w, p);
@@ -747,7 +781,7 @@ __global__ void __launch_bounds__(NT, NT == 1024 ? 1 : 8) k_stream_tr_lane(const
     }
     for (; j < I.len; j += 32) {
       const float2 wk = __ldcs(W + c0 + j);
-      const unsigned pk = (unsigned)__ldcs(colp + c0 + j) & 0xFFFFFFu;
+      const unsigned pk = DENSE ? (unsigned)(pb0 + j) : (unsigned)__ldcs(colp + c0 + j) & 0xFFFFFFu;
       tr_mac3<LAZY, !SMEMF>(acc, Fg + 3 * pk, wk);
     }
     const double X = warp_sum((double)acc[0] + (double)acc[1]);

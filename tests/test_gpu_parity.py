@@ -165,16 +165,17 @@ def test_item_split_is_invisible(pb, item_channels):
 
 
 @pytest.mark.parametrize("variant", ["ff", "f64"])
-@pytest.mark.parametrize("merge", [1, 2])
+@pytest.mark.parametrize("merge,dense", [(1, 0), (1, 2), (2, 0)], ids=["merged", "merged-indexed", "per-channel"])
 @pytest.mark.parametrize("name", ["tiny5", "win16"])
-def test_branch_merged_and_per_channel_sweeps(pb, name, variant, merge):
-    """The coefficient sweeps with one entry per state pair (branches summed at setup) and
+def test_branch_merged_and_per_channel_sweeps(pb, name, variant, merge, dense):
+    """The coefficient sweeps with one entry per state pair (branches summed at setup; on
+    these complete rows the FF sweeps take partners from entry positions unless dense=2) and
     with one entry per channel: collision, rates, RK4 and the transport map all meet the
-    oracle; the two layouts agree with each other to rounding."""
+    oracle; the layouts agree with each other to rounding."""
     m = SMALL[name]()
     o = oracle.Oracle(m)
     ch = pb.Channels.from_model(m)
-    dev = pb.Device(ch, variant=variant, merge_branches=merge, transport=True, item_channels=256)
+    dev = pb.Device(ch, variant=variant, merge_branches=merge, dense_rows=dense, transport=True, item_channels=256)
     rng = np.random.default_rng(21)
     f = rng.uniform(0, 1, o.nstate)
     ref, ab = o.collision(f, with_abs=True)
@@ -194,6 +195,10 @@ def test_branch_merged_and_per_channel_sweeps(pb, name, variant, merge):
     assert np.abs(other.collision(T(f)).cpu().numpy() - I).max() <= 1e-14 * ab.max()
     if merge == 1:
         assert dev.bytes_per_channel < other.bytes_per_channel
+    if merge == 1 and variant == "ff":
+        indexed = pb.Device(ch, variant="ff", dense_rows=2 if dense == 0 else 0)
+        assert np.abs(indexed.collision(T(f)).cpu().numpy() - I).max() <= 1e-14 * ab.max()
+        assert (dev.bytes_per_channel < indexed.bytes_per_channel) == (dense == 0)
 
 
 def test_time_sweep_measures_without_changing_results(pb):
