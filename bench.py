@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--mixed-steps", type=int, default=1000)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-ablation", action="store_true")
     ap.add_argument("--batched-instances", type=int, default=64)
     ap.add_argument("--batched-steps", type=int, default=500)
@@ -296,6 +297,48 @@ def time_calls(fn, n, stream):
         b.record(stream)
     torch.cuda.synchronize()
     return statistics.mean(a.elapsed_time(b) for a, b in evs)
+
+
+def adjoint_report(pb, stream):
+    """The adjoint workload: 24^3, 4 bands, 6 modes; loss = carrier energy after 200 RK4
+    steps of 1 fs; gradient with respect to f0 and every stored |g|^2 through checkpoints
+    every 20 steps (forward + backward), FP64-accurate (FF) and FP32 (G32) devices."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2511_03683_gb300 import autograd as pa
+
+    m = synth.make_config("window24")
+    ch = pb.Channels.from_model(m)
+    ids = ch.state_ids()
+    eps = torch.tensor(m.eps.reshape(-1)[ids], device="cuda")
+    out = {"workload": "24^3, 4 bands, 6 modes, 200 RK4 steps of 1 fs, checkpoints every 20",
+           "channels": ch.nchannels}
+    grads = {}
+    for v in ("ff", "g32"):
+        dev = pb.Device(ch, variant=v)
+        g2 = pa.g2_tensor(ch)
+        times = []
+        for rep in range(3):
+            f0 = torch.tensor(m.f_hot().reshape(-1)[ids], device="cuda", requires_grad=True)
+            g2r = g2.clone().requires_grad_(True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            (eps * pa.trajectory(dev, f0, g2r, 1.0, 200, 20)).sum().backward()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        grads[v] = (f0.grad.cpu().numpy(), g2r.grad.cpu().numpy())
+        out[v] = {"forward_backward_ms": min(times), "forward_steps": 200, "recomputed_steps": 200,
+                  "adjoint_steps": 200}
+        dev.close()
+    out["g32_grad_err_vs_ff"] = {
+        "f0": float(np.abs(grads["g32"][0] - grads["ff"][0]).max() / np.abs(grads["ff"][0]).max()),
+        "g2": float(np.abs(grads["g32"][1] - grads["ff"][1]).max() / np.abs(grads["ff"][1]).max())}
+    ch.close()
+    return out
 
 
 def batched_report(pb, ninst, nsteps, stream):
@@ -636,6 +679,10 @@ def run_ours(args):
     if not args.no_ablation and ws == 1:
         ablation = ablation_report(pb, m, ch, stream)
 
+    adjoint = None
+    if not args.no_adjoint and ws == 1 and args.workload == "window40":
+        adjoint = adjoint_report(pb, stream)
+
     batched = None
     if not args.no_batched and ws == 1:
         dev.close()
@@ -670,6 +717,7 @@ def run_ours(args):
             "cpu_baseline": base, "e2e": e2e, "gpu_launches": LAUNCHES_PER_STEP * args.steps,
             "clocks": clk, "setup": {"build_channels_s": build_s, "device_create_s": create_s},
             "transport_solve": solve, "variants": variants, "batched": batched, "paper_layout": ablation,
+            "adjoint": adjoint,
         })
     if ws > 1:
         import torch.distributed as tdist
