@@ -172,10 +172,14 @@ typedef struct pb_dev_opts {
                                 every state pair (s, p) once at setup and stream one entry per pair (Eq. 2
                                 depends on nu only through |g|^2, N and the deltas, all fixed with eps,
                                 omega, sigma and T); 2 stream one entry per channel */
-  int32_t dense_rows;        /* FF, branch-merged: 0 automatic (= 1); 1 when every row holds every window
-                                state in order (no cutoffs), the collision, rate and transport sweeps take
-                                each entry's partner from its position and stream no index (16 instead of
-                                18 bytes per entry); 2 always stream the index */
+  int32_t dense_rows;        /* FF, branch-merged, when every row holds every window state in order (no
+                                cutoffs): 0 automatic (= 3); 1 the collision, rate and transport sweeps take
+                                each entry's partner from its position and stream no index (16 instead of 18
+                                bytes per entry); 3 as 1, and the collision and rate sweeps stream the upper
+                                block triangle of the pair matrix as 64 x 64 tiles of (P_in, P_out), adding
+                                each tile to its rows and, through the reverse channels (P_in(p,s) =
+                                P_out(s,p)), to its columns: about 8 bytes per state pair; 2 always stream
+                                the index */
 } pb_dev_opts;
 
 typedef struct pb_dev pb_dev; /* opaque host handle describing device-resident data */
@@ -279,7 +283,9 @@ int pb_collision_vjp(pb_dev *dev, const double *f, const double *lam, double *gr
 int pb_rtbte_rk4_vjp(pb_dev *dev, const double *f, double *lam, double dt, double *grad_g2, void *stream);
 
 /* Replace the device |g|^2 (device double[nchannels], CSR order of pb_channels_export) and
- * recompute the per-channel coefficients.  Transport weights are not refreshed: call
+ * recompute the per-channel coefficients.  The two stored copies of a channel (under each of
+ * its states) may be given different values, so the device stops using the symmetric tiles
+ * (dense_rows 3) and streams rows from then on.  Transport weights are not refreshed: call
  * pb_transport_setup again before iterating. */
 int pb_dev_set_g2(pb_dev *dev, const double *g2, void *stream);
 

@@ -381,7 +381,7 @@ template <int STAGE>
 int batch_fin(pb_batch *b, double *out, double *f, double dt, cudaStream_t st, const double *src) {
   if (b->prec == 1) {
     pb::dev::k_fin_coll<false, STAGE><<<(int)((b->ns + 255) / 256), 256, 0, st>>>(
-        b->item_ptr, b->part, (int)b->ns, 1.0, b->Rg, src, out, f, b->acc, b->y, b->yff, dt);
+        pb::dev::ItemSrc{b->item_ptr, b->part}, (int)b->ns, 1.0, b->Rg, src, out, f, b->acc, b->y, b->yff, dt);
     PB_LAUNCHED("k_fin_coll (batch)");
     return PB_OK;
   }

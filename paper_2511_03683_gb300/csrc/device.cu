@@ -29,7 +29,7 @@ struct Layout {
   size_t rp, item_ptr, items, col, coefA, coefB, g2, wt, eps, kc, R, omega, tab, part, acc, y, yff, fstage, Fa, Fb,
       Fff, tau, invtau, red, scal, obs, g2lo, gstate, tab32, col16, rp_real, vjpG, vecs, hcol, hg2, hA, hB, sc,
       entries, hitems, titems, t_item_ptr, err, citems, citem_ptr, cpart, ccoefA, ccoefB, sidx16, sidx32, pcstart,
-      pcnt, srp, total;
+      pcnt, srp, tiles, tcoef, tpart, total;
 };
 
 struct Plan {
@@ -138,8 +138,20 @@ size_t coef_bytes(int variant) {
 
 // P: the channel plan; S: the sweep plan of the branch-merged variants (null: the sweep runs
 // over channels and the channel-only regions are empty).
+// symmetric tiles of the complete-row FF sweep: nb blocks of kTile states, nt = nb(nb+1)/2 tiles
+struct TileDims {
+  int nb = 0, nt = 0, nsp = 0;
+};
+TileDims tile_dims(int64_t ns) {
+  TileDims t;
+  t.nb = (int)((ns + dev::kTile - 1) / dev::kTile);
+  t.nt = t.nb * (t.nb + 1) / 2;
+  t.nsp = t.nb * dev::kTile;
+  return t;
+}
+
 Layout make_layout(const pb_channels *ch, const Plan &P, const Plan *S, int variant, bool transport,
-                   int nfin_blocks) {
+                   int nfin_blocks, bool sym = false) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -167,6 +179,10 @@ Layout make_layout(const pb_channels *ch, const Plan &P, const Plan *S, int vari
   L.pcstart = take(S ? sizeof(int64_t) * nsw : 0);
   L.pcnt = take(S ? nsw : 0);
   L.srp = take(S ? sizeof(int64_t) * (ns + 1) : 0);
+  const TileDims td = tile_dims((int64_t)ns);
+  L.tiles = take(sym ? sizeof(int2) * td.nt : 0);
+  L.tcoef = take(sym ? sizeof(float4) * (size_t)td.nt * dev::kTile * dev::kTile : 0);
+  L.tpart = take(sym ? sizeof(double2) * (size_t)td.nb * td.nsp : 0);
   L.wt = take(transport ? sizeof(float2) * nsw : 0);
   L.eps = take(sizeof(double) * ns);
   L.kc = take(sizeof(short4) * ns);
@@ -328,6 +344,13 @@ struct pb_dev {
   // transport sweeps take each entry's partner from its position and stream no index
   bool dense = false;
   int64_t *srp = nullptr;         // first sweep entry of every row [ns+1]
+  // symmetric tiles (complete rows, FF): the collision and rate sweeps stream the upper block
+  // triangle of the pair matrix once and add each tile to its rows and to its columns
+  bool sym = false;
+  TileDims td;
+  int2 *tiles = nullptr;
+  float4 *tcoef = nullptr;
+  double2 *tpart = nullptr;
   int64_t *rp_real = nullptr;  // unpadded CSR row offsets [ns+1]
   float2 *vjpG = nullptr;      // adjoint gather table [ns][3]
   double *vecs = nullptr;      // 8 scratch vectors of nstate doubles (adjoint stages)
@@ -410,7 +433,7 @@ int resolve_opts(const pb_channels *ch, const pb_dev_opts *opts, int sm_count, p
   if (d.variant < PB_VARIANT_FF || d.variant > PB_VARIANT_PAPER)
     return set_error(PB_EINVAL, "pb_dev: variant %d is not available in this build", d.variant);
   if (d.merge_branches < 0 || d.merge_branches > 2) return set_error(PB_EINVAL, "pb_dev: merge_branches must be 0..2");
-  if (d.dense_rows < 0 || d.dense_rows > 2) return set_error(PB_EINVAL, "pb_dev: dense_rows must be 0..2");
+  if (d.dense_rows < 0 || d.dense_rows > 3) return set_error(PB_EINVAL, "pb_dev: dense_rows must be 0..3");
   // measured best on GB300 at 40^3: 3 CTAs per SM for one entry per channel, 4 for the
   // branch-merged sweep (whose stream is six times shorter)
   const bool merged = (d.variant == PB_VARIANT_FF || d.variant == PB_VARIANT_F64) && d.merge_branches != 2;
@@ -436,6 +459,12 @@ int resolve_opts(const pb_channels *ch, const pb_dev_opts *opts, int sm_count, p
 
 bool merge_for(const pb_dev_opts &o) {
   return (o.variant == PB_VARIANT_FF || o.variant == PB_VARIANT_F64) && o.merge_branches != 2;
+}
+
+// symmetric tiles: FF, branch-merged, complete rows, dense_rows automatic or 3
+bool sym_for(const pb_dev_opts &o, bool merged, bool complete) {
+  return merged && complete && o.variant == PB_VARIANT_FF && (o.dense_rows == 0 || o.dense_rows == 3) &&
+         o.stream_mode != 2;
 }
 
 // work-item size of the branch-merged sweep: the caller's, the bulk ring's, or the default
@@ -587,9 +616,11 @@ extern "C" int pb_dev_arena_bytes(const pb_channels *ch, const pb_dev_opts *opts
   if (rc) return rc;
   Plan P, S;
   try {
-    const bool merged = make_plans(ch, opts, o, sm, P, S);
+    bool complete = false;
+    const bool merged = make_plans(ch, opts, o, sm, P, S, &complete);
     const int nfin = (int)((P.ns + kFinBlock - 1) / kFinBlock);
-    *bytes = make_layout(ch, P, merged ? &S : nullptr, o.variant, o.transport != 0, nfin).total;
+    *bytes = make_layout(ch, P, merged ? &S : nullptr, o.variant, o.transport != 0, nfin,
+                         sym_for(o, merged, complete)).total;
   } catch (const std::bad_alloc &) {
     return set_error(PB_ENOMEM, "pb_dev_arena_bytes: out of host memory");
   }
@@ -649,7 +680,9 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->item_ch = o.item_channels;
   d->transport = o.transport != 0;
   d->nfin_blocks = (int)((d->ns + kFinBlock - 1) / kFinBlock);
-  d->L = make_layout(ch, P, merged ? &S : nullptr, o.variant, d->transport, d->nfin_blocks);
+  d->sym = sym_for(o, merged, complete);
+  d->td = tile_dims(d->ns);
+  d->L = make_layout(ch, P, merged ? &S : nullptr, o.variant, d->transport, d->nfin_blocks, d->sym);
   if (arena_bytes < d->L.total) {
     const size_t need = d->L.total;
     delete d;
@@ -713,6 +746,11 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
     d->pcstart = (int64_t *)(A + L.pcstart);
     d->pcnt = (uint8_t *)(A + L.pcnt);
     d->srp = (int64_t *)(A + L.srp);
+    if (d->sym) {
+      d->tiles = (int2 *)(A + L.tiles);
+      d->tcoef = (float4 *)(A + L.tcoef);
+      d->tpart = (double2 *)(A + L.tpart);
+    }
   } else {
     d->citems = d->items;
     d->citem_ptr = d->item_ptr;
@@ -875,6 +913,17 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
         UP(d->pcstart, cst.data(), sizeof(int64_t) * S.nchp);
         UP(d->pcnt, cn.data(), S.nchp);
         UP(d->srp, S.rp.data(), sizeof(int64_t) * (d->ns + 1));
+        if (d->sym) {
+          std::vector<int2> tl;
+          for (int I = 0; I < d->td.nb; ++I)
+            for (int J = I; J < d->td.nb; ++J) tl.push_back(make_int2(I, J));
+          UP(d->tiles, tl.data(), sizeof(int2) * tl.size());
+          cudaError_t e2 = cudaStreamSynchronize(st);
+          if (e2 != cudaSuccess) {
+            status = cuda_fail(e2, "upload");
+            break;
+          }
+        }
         cudaError_t e_ = cudaStreamSynchronize(st);  // pageable sources above go out of scope
         if (e_ != cudaSuccess) {
           status = cuda_fail(e_, "upload");
@@ -993,8 +1042,11 @@ extern "C" int pb_dev_get_info(const pb_dev *d, pb_dev_info *info) {
   switch (d->variant) {
     // streamed bytes per physical channel: per sweep entry (state pair when branch-merged)
     case PB_VARIANT_FF:
-      info->bytes_per_channel = (2 * sizeof(float2) + (d->dense ? 0 : d->sidx16 ? 2 : 4)) *
-                                (d->merged ? (double)d->nsw / (double)d->nch : 1.0);
+      if (d->sym)
+        info->bytes_per_channel = (double)sizeof(float4) * d->td.nt * dev::kTile * dev::kTile / (double)d->nch;
+      else
+        info->bytes_per_channel = (2 * sizeof(float2) + (d->dense ? 0 : d->sidx16 ? 2 : 4)) *
+                                  (d->merged ? (double)d->nsw / (double)d->nch : 1.0);
       break;
     case PB_VARIANT_F64:
       info->bytes_per_channel = (2 * sizeof(double) + (d->sidx16 ? 2 : 4)) * (d->merged ? (double)d->nsw / (double)d->nch : 1.0);
@@ -1026,6 +1078,10 @@ int launch_stream_t(pb_dev *d, int mode, const double *fd, const float2 *fff, co
     dev::k_stream_ff_bulk<<<gb, dev::kBlock, d->bulk_smem, st>>>(d->items, n, (const float2 *)d->coefA,
                                                                  (const float2 *)d->coefB, d->sidx16, fff, ns,
                                                                  d->bulk_cap, part, d->err);
+  } else if (d->variant == PB_VARIANT_FF && d->sym && part == d->part) {
+    // symmetric tiles; the rate mode needs the same (A, B) partials
+    const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(d->td.nt, (int64_t)d->sm_count * 3));
+    dev::k_stream_sym<<<gs, 256, 0, st>>>(d->tiles, d->td.nt, d->tcoef, fff, ns, d->td.nsp, d->tpart);
   } else if (d->variant == PB_VARIANT_FF) {
     const float4 *A4 = (const float4 *)d->coefA, *B4 = (const float4 *)d->coefB;
     const long long *srp = (const long long *)d->srp;
@@ -1103,16 +1159,19 @@ int fin_grid(const pb_dev *d) { return d->nfin_blocks; }
 template <int STAGE>
 void launch_fin(pb_dev *d, const double *ysrc, double *out, double *f, double dt, cudaStream_t st) {
   if (d->mixed())
-    dev::k_fin_coll<true, STAGE, true><<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, (int)d->ns,
+    dev::k_fin_coll<true, STAGE, true><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->item_ptr, d->part}, (int)d->ns,
                                                                           d->c * d->gnorm(), d->R,
                                                                           ysrc, out, f, d->acc, d->y,
                                                                           (float2 *)d->gstate, dt);
   else if (d->variant == PB_VARIANT_LITERAL || d->variant == PB_VARIANT_PAPER)
     dev::k_fin_coll<true, STAGE><<<fin_grid(d), kFinBlock, 0, st>>>(
-        d->variant == PB_VARIANT_PAPER ? d->t_item_ptr : d->item_ptr, d->part, (int)d->ns, d->c, d->R, ysrc,
+        dev::ItemSrc{d->variant == PB_VARIANT_PAPER ? d->t_item_ptr : d->item_ptr, d->part}, (int)d->ns, d->c, d->R, ysrc,
                                                                     out, f, d->acc, d->y, d->yff, dt);
+  else if (d->sym)
+    dev::k_fin_tiles<STAGE><<<(int)((d->ns * 32 + 255) / 256), 256, 0, st>>>(
+        dev::TileSrc{d->tpart, d->td.nb, d->td.nsp}, (int)d->ns, d->c, d->R, ysrc, out, f, d->acc, d->y, d->yff, dt);
   else
-    dev::k_fin_coll<false, STAGE><<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->c, d->R, ysrc,
+    dev::k_fin_coll<false, STAGE><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->item_ptr, d->part}, (int)d->ns, d->c, d->R, ysrc,
                                                                      out, f, d->acc, d->y, d->yff, dt);
 }
 
@@ -1308,10 +1367,14 @@ extern "C" int pb_scatter_rates(pb_dev *d, const double *f, double *inv_tau, voi
   if ((rc = stage_input(d, f, st))) return rc;
   if ((rc = launch_stream(d, dev::MODE_RATE, f, d->yff, st))) return rc;
   if (d->variant == PB_VARIANT_LITERAL || d->mixed())
-    dev::k_fin_rate<true><<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, (int)d->ns,
+    dev::k_fin_rate<true><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->item_ptr, d->part}, (int)d->ns,
                                                              d->mixed() ? d->c * d->gnorm() : d->c, d->R, inv_tau);
+  else if (d->sym)
+    dev::k_fin_tiles<-1, true><<<(int)((d->ns * 32 + 255) / 256), 256, 0, st>>>(
+        dev::TileSrc{d->tpart, d->td.nb, d->td.nsp}, (int)d->ns, d->c, d->R, nullptr, inv_tau, nullptr, nullptr, nullptr,
+        nullptr, 0.0);
   else
-    dev::k_fin_rate<false><<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->c, d->R, inv_tau);
+    dev::k_fin_rate<false><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->item_ptr, d->part}, (int)d->ns, d->c, d->R, inv_tau);
   PB_LAUNCHED("k_fin_rate");
   return PB_OK;
 }
@@ -1439,6 +1502,13 @@ int coef_setup(pb_dev *d, cudaStream_t st) {
       else    dev::k_pair_coef<false><<<pg, 256, 0, st>>>(cs, d->pcnt, (long long)d->nsw, d->ccoefA, d->ccoefB, d->coefA, d->coefB, 1.0);
       PB_LAUNCHED("k_pair_coef");
     }
+    if (d->sym) {
+      const long long n = (long long)d->td.nt * dev::kTile * dev::kTile;
+      dev::k_tiles_fill<<<(int)std::min<long long>((n + 255) / 256, 8192), 256, 0, st>>>(
+          d->tiles, d->td.nt, (const float2 *)d->coefA, (const float2 *)d->coefB, (const long long *)d->srp,
+          (int)d->ns, d->tcoef);
+      PB_LAUNCHED("k_tiles_fill");
+    }
   }
   if (d->mixed()) {
     const long long n = (long long)d->nchp;
@@ -1474,7 +1544,7 @@ int vjp_launch_mixed(pb_dev *d, const double *f, const double *lam, double *grad
     dev::k_stream_g_vjp<__nv_bfloat16><<<grid, 512, smem, st>>>(d->items, n, g, (const __nv_bfloat16 *)d->g2lo, d->gstate,
                                                                 lam32, ns, d->part);
   PB_LAUNCHED("k_stream_g_vjp");
-  dev::k_fin_rate<true><<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, ns, -d->c * d->gnorm(), d->R, grad_f);
+  dev::k_fin_rate<true><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->item_ptr, d->part}, ns, -d->c * d->gnorm(), d->R, grad_f);
   PB_LAUNCHED("k_fin_rate (vjp)");
   if (grad_g2) {
     dev::k_g2grad_g<<<d->stream_grid(8), dev::kBlock, 0, st>>>(d->items, n, g, d->gstate, (const long long *)d->rp,
@@ -1574,6 +1644,15 @@ extern "C" int pb_dev_set_g2(pb_dev *d, const double *g2, void *stream) {
   dev::k_set_g2<<<d->chan_grid(8), dev::kBlock, 0, st>>>(d->citems, (int)d->ncitems, (const long long *)d->rp,
                                                            (const long long *)d->rp_real, g2, d->g2);
   PB_LAUNCHED("k_set_g2");
+  if (d->sym) {
+    // the caller may give the two stored copies of a channel different values: the symmetric
+    // tiles (which take a pair's reverse from its own entry) no longer apply; stream rows
+    d->sym = false;
+    if (d->rk_exec) {
+      cudaGraphExecDestroy(d->rk_exec);
+      d->rk_exec = nullptr;
+    }
+  }
   return coef_setup(d, st);
 }
 
@@ -1634,10 +1713,10 @@ extern "C" int pb_collision_static(pb_dev *d, const double *f, double *dfdt, voi
   if ((rc = launch_stream_to(d, dev::MODE_COLL, f, fff, part, st))) return rc;
   PB_LAUNCHED("pb_collision_static: stream kernel");
   if (d->variant == PB_VARIANT_LITERAL)
-    dev::k_fin_coll<true, -1><<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, part, (int)d->ns, d->c, d->R, f, dfdt,
+    dev::k_fin_coll<true, -1><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->item_ptr, part}, (int)d->ns, d->c, d->R, f, dfdt,
                                                                  nullptr, nullptr, nullptr, nullptr, 0.0);
   else
-    dev::k_fin_coll<false, -1><<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, part, (int)d->ns, d->c, d->R, f, dfdt,
+    dev::k_fin_coll<false, -1><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->item_ptr, part}, (int)d->ns, d->c, d->R, f, dfdt,
                                                                   nullptr, nullptr, nullptr, nullptr, 0.0);
   PB_LAUNCHED("pb_collision_static: k_fin_coll");
   return PB_OK;

@@ -1406,6 +1406,113 @@ __global__ void __launch_bounds__(kBlock) k_paper_gather(const Item *__restrict_
   }
 }
 
+// ------------------------------------------------------------ symmetric tiles (complete rows)
+//
+// When every row holds every window state, the branch-merged pair matrix is dense, and the
+// reverse channels fix its transpose: P_in(p,s) = P_out(s,p) and P_out(p,s) = P_in(s,p). It is
+// stored as 64 x 64 tiles of its upper block triangle, (P_in hi, P_in lo, P_out hi, P_out lo)
+// per entry. Each off-diagonal tile adds to its rows (partners = its columns) and to its
+// columns (partners = its rows):
+//   row s:  A += f_p P_in(s,p),   C += f_p P_out(s,p)
+//   col p:  A += f_s P_out(s,p),  C += f_s P_in(s,p)
+// so each state gets B = C - A = sum f D, as in the row stream. Diagonal tiles hold all
+// 64 x 64 entries and add to their rows only. Every tile writes one (A, B) per row and per
+// column into tp[partner block][state], so each state receives exactly one partial per block
+// of partner states; the epilogue adds them in block order (no atomics).
+
+constexpr int kTile = 64;
+
+// tc[t][i][j] from the branch-merged coefficients of complete rows (entry (s, p) of row s is
+// at srp[s] + p); zero outside the nstate states.
+__global__ void k_tiles_fill(const int2 *__restrict__ tiles, int nt, const float2 *__restrict__ coefA,
+                             const float2 *__restrict__ coefB, const long long *__restrict__ srp, int ns,
+                             float4 *__restrict__ tc) {
+  const long long n = (long long)nt * kTile * kTile;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int t = (int)(e / (kTile * kTile)), k = (int)(e % (kTile * kTile));
+    const int2 IJ = tiles[t];
+    const int s = IJ.x * kTile + k / kTile, p = IJ.y * kTile + k % kTile;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (s < ns && p < ns) {
+      const long long c = srp[s] + p;
+      const float2 a = coefA[c], b = coefB[c];
+      const double pin = ff_to_double(a.x, a.y), pout = pin + ff_to_double(b.x, b.y);
+      const float2 x = ff_split(pin), y = ff_split(pout);
+      v = make_float4(x.x, x.y, y.x, y.y);
+    }
+    tc[e] = v;
+  }
+}
+
+// One tile per CTA trip (grid-stride over tiles); thread (ti, tj) takes rows 4ti..4ti+3 and
+// columns 4tj..4tj+3 of the tile, so a warp reads two 1 KB row segments per step.  The four
+// terms a thread adds per row (per column) use lazily renormalised float-float sums; the 16
+// thread partials of a row (column) are then added with full float-float additions.
+__global__ void __launch_bounds__(256, 3) k_stream_sym(const int2 *__restrict__ tiles, int nt,
+                                                       const float4 *__restrict__ tc,
+                                                       const float2 *__restrict__ fg, int ns, int nsp,
+                                                       double2 *__restrict__ tp) {
+  __shared__ float2 fr[kTile], fc[kTile];
+  __shared__ float4 red[2][kTile][17];  // [rows | cols][state][thread] (A hi, A lo, C hi, C lo); 17: no bank clash
+  const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
+  for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+    const int2 IJ = tiles[t];
+    const bool diag = IJ.x == IJ.y;
+    const int r0 = IJ.x * kTile, c0 = IJ.y * kTile;
+    if (tid < kTile) fr[tid] = r0 + tid < ns ? fg[r0 + tid] : make_float2(0.f, 0.f);
+    else if (tid < 2 * kTile) fc[tid - kTile] = c0 + tid - kTile < ns ? fg[c0 + tid - kTile] : make_float2(0.f, 0.f);
+    __syncthreads();
+    float2 fcol[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) fcol[j] = fc[4 * tj + j];
+    float rA[4][2], rC[4][2], cA[4][2], cC[4][2];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      rA[k][0] = rA[k][1] = rC[k][0] = rC[k][1] = 0.f;
+      cA[k][0] = cA[k][1] = cC[k][0] = cC[k][1] = 0.f;
+    }
+    const float4 *__restrict__ base = tc + (long long)t * kTile * kTile + 4 * tj;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int s = 4 * ti + i;
+      const float2 fs = fr[s];
+      float4 e[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) e[j] = __ldcs(base + s * kTile + j);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        ff_mac_lazy(rA[i][0], rA[i][1], fcol[j], e[j].x, e[j].y);
+        ff_mac_lazy(rC[i][0], rC[i][1], fcol[j], e[j].z, e[j].w);
+        if (!diag) {
+          ff_mac_lazy(cA[j][0], cA[j][1], fs, e[j].z, e[j].w);
+          ff_mac_lazy(cC[j][0], cC[j][1], fs, e[j].x, e[j].y);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      red[0][4 * ti + k][tj] = make_float4(rA[k][0], rA[k][1], rC[k][0], rC[k][1]);
+      red[1][4 * tj + k][ti] = make_float4(cA[k][0], cA[k][1], cC[k][0], cC[k][1]);
+    }
+    __syncthreads();
+    if (tid < 2 * kTile && (tid < kTile || !diag)) {
+      const int side = tid >> 6, x = tid & (kTile - 1);
+      float2 A = make_float2(0.f, 0.f), C = make_float2(0.f, 0.f);
+#pragma unroll 4
+      for (int k = 0; k < 16; ++k) {
+        const float4 v = red[side][x][k];
+        A = ff_add(A, make_float2(v.x, v.y));
+        C = ff_add(C, make_float2(v.z, v.w));
+      }
+      const double a = ff_to_double(A.x, A.y), c = ff_to_double(C.x, C.y);
+      const int st = (side == 0 ? r0 : c0) + x;
+      const int blk = side == 0 ? IJ.y : IJ.x;
+      if (st < nsp) tp[(long long)blk * nsp + st] = make_double2(a, c - a);
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------ finalisers
 
 // Row totals of the (A, B) partials (coefficient variants) or of the literal sums.
@@ -1420,18 +1527,35 @@ __device__ __forceinline__ void row_partials(const int *__restrict__ item_ptr, c
   }
 }
 
+// Where a row's partial sums (A, B) come from: the work items of its row (one Part4 each)
+// or, for the symmetric tile sweep, one double2 per block of partner states.
+struct ItemSrc {
+  const int *item_ptr;
+  const Part4 *part;
+  __device__ __forceinline__ void get(int r, double &A, double &B) const { row_partials(item_ptr, part, r, A, B); }
+};
+struct TileSrc {
+  const double2 *tp;  // [nb][nsp]
+  int nb, nsp;
+  __device__ __forceinline__ void get(int r, double &A, double &B) const {
+    A = 0.0;
+    B = 0.0;
+    for (int k = 0; k < nb; ++k) {
+      const double2 v = tp[(long long)k * nsp + r];
+      A += v.x;
+      B += v.y;
+    }
+  }
+};
+
 // Collision epilogue fused with the RK4 stage arithmetic.
 //   STAGE < 0 : out[r] = I_r (plain pb_collision)
 //   STAGE 0..3: classic RK4 stage k_{STAGE+1} = I[y]; see the host driver for buffers.
-template <bool LIT, int STAGE, bool GSTATE = false>
-__global__ void k_fin_coll(const int *__restrict__ item_ptr, const Part4 *__restrict__ part, int ns, double c,
-                           const double *__restrict__ R, const double *__restrict__ ysrc, double *__restrict__ out,
-                           double *__restrict__ f, double *__restrict__ acc, double *__restrict__ y,
-                           float2 *__restrict__ yff, double dt) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= ns) return;
-  double A, B;
-  row_partials(item_ptr, part, r, A, B);
+template <bool LIT, int STAGE, bool GSTATE>
+__device__ __forceinline__ void fin_apply(int r, double A, double B, double c, const double *__restrict__ R,
+                                          const double *__restrict__ ysrc, double *__restrict__ out,
+                                          double *__restrict__ f, double *__restrict__ acc, double *__restrict__ y,
+                                          float2 *__restrict__ yff, double dt) {
   const double I = LIT ? -c * A : c * (A - ysrc[r] * (R[r] - B));
   if (STAGE < 0) {
     out[r] = I;
@@ -1459,13 +1583,47 @@ __global__ void k_fin_coll(const int *__restrict__ item_ptr, const Part4 *__rest
     yff[r] = ff_split(yn);
 }
 
-template <bool LIT>
-__global__ void k_fin_rate(const int *__restrict__ item_ptr, const Part4 *__restrict__ part, int ns, double c,
-                           const double *__restrict__ R, double *__restrict__ out) {
+template <bool LIT, int STAGE, bool GSTATE = false, typename SRC = ItemSrc>
+__global__ void k_fin_coll(SRC src, int ns, double c, const double *__restrict__ R, const double *__restrict__ ysrc,
+                           double *__restrict__ out, double *__restrict__ f, double *__restrict__ acc,
+                           double *__restrict__ y, float2 *__restrict__ yff, double dt) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= ns) return;
   double A, B;
-  row_partials(item_ptr, part, r, A, B);
+  src.get(r, A, B);
+  fin_apply<LIT, STAGE, GSTATE>(r, A, B, c, R, ysrc, out, f, acc, y, yff, dt);
+}
+
+// The same epilogue over symmetric-tile partials, one warp per state: lanes add the block
+// partials k = lane, lane + 32, ... and a fixed shuffle tree combines them.  RATE: 1/tau.
+template <int STAGE, bool RATE = false>
+__global__ void __launch_bounds__(256) k_fin_tiles(TileSrc src, int ns, double c, const double *__restrict__ R,
+                                                   const double *__restrict__ ysrc, double *__restrict__ out,
+                                                   double *__restrict__ f, double *__restrict__ acc,
+                                                   double *__restrict__ y, float2 *__restrict__ yff, double dt) {
+  const int r = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (r >= ns) return;
+  double A = 0.0, B = 0.0;
+  for (int k = lane; k < src.nb; k += 32) {
+    const double2 v = src.tp[(long long)k * src.nsp + r];
+    A += v.x;
+    B += v.y;
+  }
+  A = warp_sum(A);
+  B = warp_sum(B);
+  if (lane != 0) return;
+  if (RATE)
+    out[r] = c * (R[r] - B);
+  else
+    fin_apply<false, STAGE, false>(r, A, B, c, R, ysrc, out, f, acc, y, yff, dt);
+}
+
+template <bool LIT, typename SRC = ItemSrc>
+__global__ void k_fin_rate(SRC src, int ns, double c, const double *__restrict__ R, double *__restrict__ out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= ns) return;
+  double A, B;
+  src.get(r, A, B);
   out[r] = LIT ? c * A : c * (R[r] - B);
 }
 

@@ -165,13 +165,15 @@ def test_item_split_is_invisible(pb, item_channels):
 
 
 @pytest.mark.parametrize("variant", ["ff", "f64"])
-@pytest.mark.parametrize("merge,dense", [(1, 0), (1, 2), (2, 0)], ids=["merged", "merged-indexed", "per-channel"])
+@pytest.mark.parametrize("merge,dense", [(1, 0), (1, 1), (1, 2), (2, 0)],
+                         ids=["merged-tiles", "merged-positional", "merged-indexed", "per-channel"])
 @pytest.mark.parametrize("name", ["tiny5", "win16"])
 def test_branch_merged_and_per_channel_sweeps(pb, name, variant, merge, dense):
     """The coefficient sweeps with one entry per state pair (branches summed at setup; on
-    these complete rows the FF sweeps take partners from entry positions unless dense=2) and
-    with one entry per channel: collision, rates, RK4 and the transport map all meet the
-    oracle; the layouts agree with each other to rounding."""
+    these complete rows the FF collision sweep streams symmetric tiles of the pair matrix by
+    default, the row stream with positional partners with dense=1, with partner indices with
+    dense=2) and with one entry per channel: collision, rates, RK4 and the transport map all
+    meet the oracle; the layouts agree with each other to rounding."""
     m = SMALL[name]()
     o = oracle.Oracle(m)
     ch = pb.Channels.from_model(m)
@@ -196,9 +198,10 @@ def test_branch_merged_and_per_channel_sweeps(pb, name, variant, merge, dense):
     if merge == 1:
         assert dev.bytes_per_channel < other.bytes_per_channel
     if merge == 1 and variant == "ff":
-        indexed = pb.Device(ch, variant="ff", dense_rows=2 if dense == 0 else 0)
-        assert np.abs(indexed.collision(T(f)).cpu().numpy() - I).max() <= 1e-14 * ab.max()
-        assert (dev.bytes_per_channel < indexed.bytes_per_channel) == (dense == 0)
+        other_rows = pb.Device(ch, variant="ff", dense_rows=0 if dense == 2 else 2)
+        assert np.abs(other_rows.collision(T(f)).cpu().numpy() - I).max() <= 1e-14 * ab.max()
+        if dense != 2:  # tiles and positional partners stream fewer bytes than the index form
+            assert dev.bytes_per_channel < other_rows.bytes_per_channel
 
 
 def test_time_sweep_measures_without_changing_results(pb):
