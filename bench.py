@@ -145,7 +145,8 @@ def function_source(text: str, name: str) -> str:
     return "\n".join(out)
 
 
-HOT_FUNCTIONS = ("ff_split", "ff_to_double", "ff_mac", "warp_sum", "partners4", "k_stream_ff")
+HOT_FUNCTIONS = ("ff_split", "ff_to_double", "ff_mac", "ff_mac_lazy", "ff_add", "warp_sum", "partners4", "group_f",
+                 "k_stream_ff", "k_stream_sym")
 
 
 def kernel_source_hash(names=HOT_FUNCTIONS) -> str:

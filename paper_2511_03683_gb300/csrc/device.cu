@@ -182,7 +182,7 @@ Layout make_layout(const pb_channels *ch, const Plan &P, const Plan *S, int vari
   const TileDims td = tile_dims((int64_t)ns);
   L.tiles = take(sym ? sizeof(int2) * td.nt : 0);
   L.tcoef = take(sym ? sizeof(float4) * (size_t)td.nt * dev::kTile * dev::kTile : 0);
-  L.tpart = take(sym ? sizeof(double2) * (size_t)td.nb * td.nsp : 0);
+  L.tpart = take(sym ? sizeof(float4) * (size_t)td.nb * td.nsp : 0);
   L.wt = take(transport ? sizeof(float2) * nsw : 0);
   L.eps = take(sizeof(double) * ns);
   L.kc = take(sizeof(short4) * ns);
@@ -350,7 +350,7 @@ struct pb_dev {
   TileDims td;
   int2 *tiles = nullptr;
   float4 *tcoef = nullptr;
-  double2 *tpart = nullptr;
+  float4 *tpart = nullptr;
   int64_t *rp_real = nullptr;  // unpadded CSR row offsets [ns+1]
   float2 *vjpG = nullptr;      // adjoint gather table [ns][3]
   double *vecs = nullptr;      // 8 scratch vectors of nstate doubles (adjoint stages)
@@ -749,7 +749,7 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
     if (d->sym) {
       d->tiles = (int2 *)(A + L.tiles);
       d->tcoef = (float4 *)(A + L.tcoef);
-      d->tpart = (double2 *)(A + L.tpart);
+      d->tpart = (float4 *)(A + L.tpart);
     }
   } else {
     d->citems = d->items;
@@ -1081,7 +1081,7 @@ int launch_stream_t(pb_dev *d, int mode, const double *fd, const float2 *fff, co
   } else if (d->variant == PB_VARIANT_FF && d->sym && part == d->part) {
     // symmetric tiles; the rate mode needs the same (A, B) partials
     const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(d->td.nt, (int64_t)d->sm_count * 3));
-    dev::k_stream_sym<<<gs, 256, 0, st>>>(d->tiles, d->td.nt, d->tcoef, fff, ns, d->td.nsp, d->tpart);
+    dev::k_stream_sym<<<gs, 256, 0, st>>>(d->tiles, d->td.nt, d->tcoef, fff, ns, d->td.nb, d->tpart);
   } else if (d->variant == PB_VARIANT_FF) {
     const float4 *A4 = (const float4 *)d->coefA, *B4 = (const float4 *)d->coefB;
     const long long *srp = (const long long *)d->srp;

@@ -73,6 +73,33 @@ __device__ __forceinline__ void ff_mac(float &h, float &l, float2 x, float ah, f
   l = __fsub_rn(err, __fsub_rn(h, s));
 }
 
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float bb = __fsub_rn(s, a.x);
+  float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+  err = __fadd_rn(err, __fadd_rn(a.y, b.y));
+  const float h = __fadd_rn(s, err);
+  return make_float2(h, __fsub_rn(err, __fsub_rn(h, s)));
+}
+
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  const float h = __fadd_rn(p, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, p)));
+}
+
+// Sum over the warp of a float-float value with a fixed xor shuffle tree (FP32 only), then
+// one conversion: lane 0's result is reproducible run to run.
+__device__ __forceinline__ double warp_sum_ff(float2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = ff_add(v, make_float2(__shfl_xor_sync(0xFFFFFFFFu, v.x, o), __shfl_xor_sync(0xFFFFFFFFu, v.y, o)));
+  return ff_to_double(v.x, v.y);
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -384,8 +411,8 @@ __global__ void __launch_bounds__(kBlock) k_stream_ff(const Item *__restrict__ i
       ff_mac(bh, bl, f0, b00.x, b00.y); ff_mac(bh, bl, f1, b00.z, b00.w);
       ff_mac(bh, bl, f2, b01.x, b01.y); ff_mac(bh, bl, f3, b01.z, b01.w);
     }
-    const double A = warp_sum(MODE == MODE_COLL ? ff_to_double(ah, al) : 0.0);
-    const double B = warp_sum(ff_to_double(bh, bl));
+    const double A = MODE == MODE_COLL ? warp_sum_ff(make_float2(ah, al)) : 0.0;
+    const double B = warp_sum_ff(make_float2(bh, bl));
     if (lane == 0) part[it] = make_part4(A, B, 0.0, 0.0);
   }
 }
@@ -784,9 +811,9 @@ __global__ void __launch_bounds__(NT, NT == 1024 ? 1 : 8) k_stream_tr_lane(const
       const unsigned pk = DENSE ? (unsigned)(pb0 + j) : (unsigned)__ldcs(colp + c0 + j) & 0xFFFFFFu;
       tr_mac3<LAZY, !SMEMF>(acc, Fg + 3 * pk, wk);
     }
-    const double X = warp_sum((double)acc[0] + (double)acc[1]);
-    const double Y = warp_sum((double)acc[2] + (double)acc[3]);
-    const double Z = warp_sum((double)acc[4] + (double)acc[5]);
+    const double X = warp_sum_ff(make_float2(acc[0], acc[1]));
+    const double Y = warp_sum_ff(make_float2(acc[2], acc[3]));
+    const double Z = warp_sum_ff(make_float2(acc[4], acc[5]));
     if (lane == 0) part[it] = make_part4(X, Y, Z, 0.0);
   }
 }
@@ -1315,23 +1342,6 @@ __global__ void k_lincomb(int n, double a, const double *__restrict__ x, double 
 // over its target list (the signed stargets_sources), with no atomics.  It trades half the
 // coefficient storage for an extra write and read of sc_col and a scattered gather.
 
-__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
-  const float s = __fadd_rn(a.x, b.x);
-  const float bb = __fsub_rn(s, a.x);
-  float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
-  err = __fadd_rn(err, __fadd_rn(a.y, b.y));
-  const float h = __fadd_rn(s, err);
-  return make_float2(h, __fsub_rn(err, __fsub_rn(h, s)));
-}
-
-__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
-  const float p = __fmul_rn(a.x, b.x);
-  float e = __fmaf_rn(a.x, b.x, -p);
-  e = __fmaf_rn(a.x, b.y, e);
-  e = __fmaf_rn(a.y, b.x, e);
-  const float h = __fadd_rn(p, e);
-  return make_float2(h, __fsub_rn(e, __fsub_rn(h, p)));
-}
 
 // sc_col[c] = f_p (P_in + f_s D) - f_s P_out for each stored channel (orientation s -> p);
 // its contribution to I_p is -sc_col[c].
@@ -1417,8 +1427,8 @@ __global__ void __launch_bounds__(kBlock) k_paper_gather(const Item *__restrict_
 //   col p:  A += f_s P_out(s,p),  C += f_s P_in(s,p)
 // so each state gets B = C - A = sum f D, as in the row stream. Diagonal tiles hold all
 // 64 x 64 entries and add to their rows only. Every tile writes one (A, B) per row and per
-// column into tp[partner block][state], so each state receives exactly one partial per block
-// of partner states; the epilogue adds them in block order (no atomics).
+// column into tp[state][partner block], so each state receives exactly one partial per block
+// of partner states, stored contiguously; the epilogue adds them in block order (no atomics).
 
 constexpr int kTile = 64;
 
@@ -1450,8 +1460,8 @@ __global__ void k_tiles_fill(const int2 *__restrict__ tiles, int nt, const float
 // thread partials of a row (column) are then added with full float-float additions.
 __global__ void __launch_bounds__(256, 3) k_stream_sym(const int2 *__restrict__ tiles, int nt,
                                                        const float4 *__restrict__ tc,
-                                                       const float2 *__restrict__ fg, int ns, int nsp,
-                                                       double2 *__restrict__ tp) {
+                                                       const float2 *__restrict__ fg, int ns, int nb,
+                                                       float4 *__restrict__ tp) {
   __shared__ float2 fr[kTile], fc[kTile];
   __shared__ float4 red[2][kTile][17];  // [rows | cols][state][thread] (A hi, A lo, C hi, C lo); 17: no bank clash
   const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
@@ -1504,10 +1514,9 @@ __global__ void __launch_bounds__(256, 3) k_stream_sym(const int2 *__restrict__ 
         A = ff_add(A, make_float2(v.x, v.y));
         C = ff_add(C, make_float2(v.z, v.w));
       }
-      const double a = ff_to_double(A.x, A.y), c = ff_to_double(C.x, C.y);
       const int st = (side == 0 ? r0 : c0) + x;
       const int blk = side == 0 ? IJ.y : IJ.x;
-      if (st < nsp) tp[(long long)blk * nsp + st] = make_double2(a, c - a);
+      tp[(long long)st * nb + blk] = make_float4(A.x, A.y, C.x, C.y);
     }
     __syncthreads();
   }
@@ -1535,17 +1544,8 @@ struct ItemSrc {
   __device__ __forceinline__ void get(int r, double &A, double &B) const { row_partials(item_ptr, part, r, A, B); }
 };
 struct TileSrc {
-  const double2 *tp;  // [nb][nsp]
+  const float4 *tp;  // [nsp][nb]: state-major, one partial (A hi, A lo, C hi, C lo) per block of partner states
   int nb, nsp;
-  __device__ __forceinline__ void get(int r, double &A, double &B) const {
-    A = 0.0;
-    B = 0.0;
-    for (int k = 0; k < nb; ++k) {
-      const double2 v = tp[(long long)k * nsp + r];
-      A += v.x;
-      B += v.y;
-    }
-  }
 };
 
 // Collision epilogue fused with the RK4 stage arithmetic.
@@ -1595,7 +1595,9 @@ __global__ void k_fin_coll(SRC src, int ns, double c, const double *__restrict__
 }
 
 // The same epilogue over symmetric-tile partials, one warp per state: lanes add the block
-// partials k = lane, lane + 32, ... and a fixed shuffle tree combines them.  RATE: 1/tau.
+// partials k = lane, lane + 32, ... and a fixed shuffle tree combines them, all in float-float
+// (FP64 adds run at 1/64 of the FP32 rate on this part: 75 double partials per state and a
+// double shuffle tree made this epilogue cost as much as a fifth of the sweep).  RATE: 1/tau.
 template <int STAGE, bool RATE = false>
 __global__ void __launch_bounds__(256) k_fin_tiles(TileSrc src, int ns, double c, const double *__restrict__ R,
                                                    const double *__restrict__ ysrc, double *__restrict__ out,
@@ -1603,15 +1605,19 @@ __global__ void __launch_bounds__(256) k_fin_tiles(TileSrc src, int ns, double c
                                                    double *__restrict__ y, float2 *__restrict__ yff, double dt) {
   const int r = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (r >= ns) return;
-  double A = 0.0, B = 0.0;
+  float2 a = make_float2(0.f, 0.f), cc = make_float2(0.f, 0.f);
   for (int k = lane; k < src.nb; k += 32) {
-    const double2 v = src.tp[(long long)k * src.nsp + r];
-    A += v.x;
-    B += v.y;
+    const float4 v = src.tp[(long long)r * src.nb + k];  // one contiguous run per state
+    a = ff_add(a, make_float2(v.x, v.y));
+    cc = ff_add(cc, make_float2(v.z, v.w));
   }
-  A = warp_sum(A);
-  B = warp_sum(B);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a = ff_add(a, make_float2(__shfl_xor_sync(0xFFFFFFFFu, a.x, o), __shfl_xor_sync(0xFFFFFFFFu, a.y, o)));
+    cc = ff_add(cc, make_float2(__shfl_xor_sync(0xFFFFFFFFu, cc.x, o), __shfl_xor_sync(0xFFFFFFFFu, cc.y, o)));
+  }
   if (lane != 0) return;
+  const double A = ff_to_double(a.x, a.y), B = ff_to_double(cc.x, cc.y) - A;
   if (RATE)
     out[r] = c * (R[r] - B);
   else
