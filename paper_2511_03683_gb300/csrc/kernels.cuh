@@ -1551,29 +1551,46 @@ struct TileSrc {
 // Collision epilogue fused with the RK4 stage arithmetic.
 //   STAGE < 0 : out[r] = I_r (plain pb_collision)
 //   STAGE 0..3: classic RK4 stage k_{STAGE+1} = I[y]; see the host driver for buffers.
+// The per-state inputs of the epilogue, loaded before the partial sums so that their latency
+// overlaps the partials' (the epilogues are a chain of dependent loads otherwise).
+struct FinIn {
+  double R, y, f, acc;
+};
+template <bool LIT, int STAGE>
+__device__ __forceinline__ FinIn fin_load(int r, const double *__restrict__ R, const double *__restrict__ ysrc,
+                                          const double *__restrict__ f, const double *__restrict__ acc) {
+  FinIn v{0.0, 0.0, 0.0, 0.0};
+  if (!LIT) {
+    v.R = R[r];
+    v.y = ysrc[r];
+  }
+  if (STAGE >= 0) v.f = f[r];
+  if (STAGE >= 1) v.acc = acc[r];
+  return v;
+}
+
 template <bool LIT, int STAGE, bool GSTATE>
-__device__ __forceinline__ void fin_apply(int r, double A, double B, double c, const double *__restrict__ R,
-                                          const double *__restrict__ ysrc, double *__restrict__ out,
-                                          double *__restrict__ f, double *__restrict__ acc, double *__restrict__ y,
-                                          float2 *__restrict__ yff, double dt) {
-  const double I = LIT ? -c * A : c * (A - ysrc[r] * (R[r] - B));
+__device__ __forceinline__ void fin_apply(int r, double A, double B, double c, const FinIn &in,
+                                          double *__restrict__ out, double *__restrict__ f, double *__restrict__ acc,
+                                          double *__restrict__ y, float2 *__restrict__ yff, double dt) {
+  const double I = LIT ? -c * A : c * (A - in.y * (in.R - B));
   if (STAGE < 0) {
     out[r] = I;
     return;
   }
-  const double fr = f[r];
+  const double fr = in.f;
   double yn;
   if (STAGE == 0) {
     acc[r] = I;
     yn = fr + 0.5 * dt * I;
   } else if (STAGE == 1) {
-    acc[r] += 2.0 * I;
+    acc[r] = in.acc + 2.0 * I;
     yn = fr + 0.5 * dt * I;
   } else if (STAGE == 2) {
-    acc[r] += 2.0 * I;
+    acc[r] = in.acc + 2.0 * I;
     yn = fr + dt * I;
   } else {
-    yn = fr + dt / 6.0 * (acc[r] + I);
+    yn = fr + dt / 6.0 * (in.acc + I);
     f[r] = yn;
   }
   y[r] = yn;
@@ -1589,9 +1606,10 @@ __global__ void k_fin_coll(SRC src, int ns, double c, const double *__restrict__
                            double *__restrict__ y, float2 *__restrict__ yff, double dt) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= ns) return;
+  const FinIn in = fin_load<LIT, STAGE>(r, R, ysrc, f, acc);
   double A, B;
   src.get(r, A, B);
-  fin_apply<LIT, STAGE, GSTATE>(r, A, B, c, R, ysrc, out, f, acc, y, yff, dt);
+  fin_apply<LIT, STAGE, GSTATE>(r, A, B, c, in, out, f, acc, y, yff, dt);
 }
 
 // The same epilogue over symmetric-tile partials, one warp per state: lanes add the block
@@ -1605,11 +1623,29 @@ __global__ void __launch_bounds__(256) k_fin_tiles(TileSrc src, int ns, double c
                                                    double *__restrict__ y, float2 *__restrict__ yff, double dt) {
   const int r = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (r >= ns) return;
+  FinIn in{0.0, 0.0, 0.0, 0.0};
+  if (lane == 0) {
+    if (RATE) in.R = R[r];
+    else in = fin_load<false, STAGE>(r, R, ysrc, f, acc);
+  }
+  // the first three partials of every lane are loaded together (up to 96 partner blocks)
+  const float4 *__restrict__ row = src.tp + (long long)r * src.nb;
+  float4 v[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    const int k = lane + 32 * m;
+    v[m] = k < src.nb ? row[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
   float2 a = make_float2(0.f, 0.f), cc = make_float2(0.f, 0.f);
-  for (int k = lane; k < src.nb; k += 32) {
-    const float4 v = src.tp[(long long)r * src.nb + k];  // one contiguous run per state
-    a = ff_add(a, make_float2(v.x, v.y));
-    cc = ff_add(cc, make_float2(v.z, v.w));
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    a = ff_add(a, make_float2(v[m].x, v[m].y));
+    cc = ff_add(cc, make_float2(v[m].z, v[m].w));
+  }
+  for (int k = lane + 96; k < src.nb; k += 32) {
+    const float4 w = row[k];
+    a = ff_add(a, make_float2(w.x, w.y));
+    cc = ff_add(cc, make_float2(w.z, w.w));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -1619,18 +1655,19 @@ __global__ void __launch_bounds__(256) k_fin_tiles(TileSrc src, int ns, double c
   if (lane != 0) return;
   const double A = ff_to_double(a.x, a.y), B = ff_to_double(cc.x, cc.y) - A;
   if (RATE)
-    out[r] = c * (R[r] - B);
+    out[r] = c * (in.R - B);
   else
-    fin_apply<false, STAGE, false>(r, A, B, c, R, ysrc, out, f, acc, y, yff, dt);
+    fin_apply<false, STAGE, false>(r, A, B, c, in, out, f, acc, y, yff, dt);
 }
 
 template <bool LIT, typename SRC = ItemSrc>
 __global__ void k_fin_rate(SRC src, int ns, double c, const double *__restrict__ R, double *__restrict__ out) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= ns) return;
+  const double Rr = LIT ? 0.0 : R[r];
   double A, B;
   src.get(r, A, B);
-  out[r] = LIT ? c * A : c * (R[r] - B);
+  out[r] = LIT ? c * A : c * (Rr - B);
 }
 
 // F_new = tau (v + sum W F); ff copy for the next pass; per-block max |dF| and max |F|.
