@@ -527,7 +527,7 @@ int batch_setup_ff(pb_batch *b, const pb_channels *const *chs, int n, const Batc
     }
     if (np > 0) {
       dev::k_pair_coef<true><<<(int)std::min<int64_t>((np + 255) / 256, 8192), 256, 0, st>>>(
-          (const long long *)tpcst, tpcnt, (long long)np, tcA, tcB, b->pA + poff, b->pB + poff, c);
+          (const long long *)tpcst, tpcnt, (long long)np, tcA, tcB, b->pA + poff, b->pB + poff, c, nullptr);
       PB_LAUNCHED("k_pair_coef (batch)");
     }
     PB_CUDA(cudaStreamSynchronize(st));  // the temporaries are reused by the next instance

@@ -27,7 +27,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
   size_t rp, item_ptr, items, col, coefA, coefB, g2, wt, eps, kc, R, omega, tab, part, acc, y, yff, fstage, Fa, Fb,
-      Fff, tau, invtau, red, scal, obs, g2lo, gstate, tab32, col16, rp_real, vjpG, vecs, hcol, hg2, hA, hB, sc,
+      Fff, tau, invtau, red, scal, obs, g2lo, gstate, tab32, col16, rp_real, vjpG, g2tab, vecs, hcol, hg2, hA, hB, sc,
       entries, hitems, titems, t_item_ptr, err, citems, citem_ptr, cpart, ccoefA, ccoefB, sidx16, sidx32, pcstart,
       pcnt, srp, tiles, tcoef, tpart, total;
 };
@@ -223,6 +223,7 @@ Layout make_layout(const pb_channels *ch, const Plan &P, const Plan *S, int vari
   L.part = take(sizeof(Part4) * std::max<int64_t>(W.nitems, (variant == PB_VARIANT_PAPER) ? z.nentp / kRowPad + (int64_t)ns : 0));
   L.rp_real = take(sizeof(int64_t) * (ns + 1));
   L.vjpG = take(sizeof(float2) * 3 * ns);
+  L.g2tab = take(sizeof(float4) * 2 * 4 * ns);
   L.vecs = take(sizeof(double) * 8 * ns);
   L.total = o;
   return L;
@@ -353,6 +354,7 @@ struct pb_dev {
   float4 *tpart = nullptr;
   int64_t *rp_real = nullptr;  // unpadded CSR row offsets [ns+1]
   float2 *vjpG = nullptr;      // adjoint gather table [ns][3]
+  float4 *g2tab = nullptr;     // |g|^2-gradient stage table [4 stages][ns][2]
   double *vecs = nullptr;      // 8 scratch vectors of nstate doubles (adjoint stages)
   // paper layout (PB_VARIANT_PAPER)
   uint32_t *hcol = nullptr;
@@ -725,6 +727,7 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->col16 = d->ns <= 65536 ? (uint16_t *)(A + L.col16) : nullptr;
   d->rp_real = (int64_t *)(A + L.rp_real);
   d->vjpG = (float2 *)(A + L.vjpG);
+  d->g2tab = (float4 *)(A + L.g2tab);
   d->vecs = (double *)(A + L.vecs);
   d->hcol = (uint32_t *)(A + L.hcol);
   d->hg2 = (double *)(A + L.hg2);
@@ -1490,16 +1493,21 @@ int coef_setup(pb_dev *d, cudaStream_t st) {
     const int grid = d->chan_grid(8);
     const dev::ChanGeom g = d->geom();
     const bool ff = d->variant == PB_VARIANT_FF;
-    if (ff) dev::k_coef<true><<<grid, dev::kBlock, 0, st>>>(d->citems, (int)d->ncitems, g, d->ccoefA, d->ccoefB, d->cpart);
-    else    dev::k_coef<false><<<grid, dev::kBlock, 0, st>>>(d->citems, (int)d->ncitems, g, d->ccoefA, d->ccoefB, d->cpart);
+    // branch-merged: the per-channel arrays hold the coefficients without g2 (the branch
+    // sums multiply it back in; the |g|^2 gradient reads them as they are)
+    const bool kf = d->merged;
+    if (ff && kf)  dev::k_coef<true, true><<<grid, dev::kBlock, 0, st>>>(d->citems, (int)d->ncitems, g, d->ccoefA, d->ccoefB, d->cpart);
+    else if (ff)   dev::k_coef<true><<<grid, dev::kBlock, 0, st>>>(d->citems, (int)d->ncitems, g, d->ccoefA, d->ccoefB, d->cpart);
+    else if (kf)   dev::k_coef<false, true><<<grid, dev::kBlock, 0, st>>>(d->citems, (int)d->ncitems, g, d->ccoefA, d->ccoefB, d->cpart);
+    else           dev::k_coef<false><<<grid, dev::kBlock, 0, st>>>(d->citems, (int)d->ncitems, g, d->ccoefA, d->ccoefB, d->cpart);
     PB_LAUNCHED("k_coef");
     dev::k_rowsum<<<(int)((d->ns + 255) / 256), 256, 0, st>>>(d->citem_ptr, d->cpart, (int)d->ns, d->R);
     PB_LAUNCHED("k_rowsum");
     if (d->merged && d->nsw > 0) {
       const int pg = (int)std::min<int64_t>((d->nsw + 255) / 256, 8192);
       const long long* cs = (const long long *)d->pcstart;
-      if (ff) dev::k_pair_coef<true><<<pg, 256, 0, st>>>(cs, d->pcnt, (long long)d->nsw, d->ccoefA, d->ccoefB, d->coefA, d->coefB, 1.0);
-      else    dev::k_pair_coef<false><<<pg, 256, 0, st>>>(cs, d->pcnt, (long long)d->nsw, d->ccoefA, d->ccoefB, d->coefA, d->coefB, 1.0);
+      if (ff) dev::k_pair_coef<true><<<pg, 256, 0, st>>>(cs, d->pcnt, (long long)d->nsw, d->ccoefA, d->ccoefB, d->coefA, d->coefB, 1.0, d->g2);
+      else    dev::k_pair_coef<false><<<pg, 256, 0, st>>>(cs, d->pcnt, (long long)d->nsw, d->ccoefA, d->ccoefB, d->coefA, d->coefB, 1.0, d->g2);
       PB_LAUNCHED("k_pair_coef");
     }
     if (d->sym) {
@@ -1555,11 +1563,14 @@ int vjp_launch_mixed(pb_dev *d, const double *f, const double *lam, double *grad
   return PB_OK;
 }
 
-// grad_f = J(f)^T lam (FF coefficients); grad_g2 (unpadded CSR order) += dL/dg2 if not null
-int vjp_launch(pb_dev *d, const double *f, const double *lam, double *grad_f, double *grad_g2, cudaStream_t st) {
+// grad_f = J(f)^T lam.  Mixed variants: grad_g2 (unpadded CSR order) += dL/dg2 if not null.
+// FF: slot >= 0 writes stage slot of the |g|^2-gradient table, which g2grad_launch applies.
+int vjp_launch(pb_dev *d, const double *f, const double *lam, double *grad_f, double *grad_g2, int slot,
+               cudaStream_t st) {
   if (d->mixed()) return vjp_launch_mixed(d, f, lam, grad_f, grad_g2, st);
   const int ns = (int)d->ns, n = (int)d->nitems;
-  dev::k_vjp_prep<<<(ns + 255) / 256, 256, 0, st>>>(f, lam, ns, d->vjpG);
+  dev::k_vjp_prep<<<(ns + 255) / 256, 256, 0, st>>>(f, lam, ns, d->vjpG, -d->c,
+                                                    slot >= 0 ? d->g2tab + 2 * (size_t)slot * ns : nullptr);
   PB_LAUNCHED("k_vjp_prep");
   const int grid = d->stream_grid(d->smem_G ? std::max(1, std::min(d->ctas, (int)((228 * 1024) / (d->smem_G + 1024)))) : d->ctas);
   const float4 *A4 = (const float4 *)d->coefA, *B4 = (const float4 *)d->coefB;
@@ -1573,17 +1584,23 @@ int vjp_launch(pb_dev *d, const double *f, const double *lam, double *grad_f, do
   PB_LAUNCHED("k_stream_vjp");
   dev::k_fin_vjp<<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, ns, d->c, d->R, lam, grad_f);
   PB_LAUNCHED("k_fin_vjp");
-  if (grad_g2) {
-    const int gg = d->chan_grid(8), nc = (int)d->ncitems;
-    const float2 *A = (const float2 *)d->ccoefA, *B = (const float2 *)d->ccoefB;
-    if (d->col16)
-      dev::k_g2grad<uint16_t><<<gg, dev::kBlock, 0, st>>>(d->citems, nc, (const long long *)d->rp, (const long long *)d->rp_real,
-                                                          A, B, d->col16, d->g2, f, lam, d->c, grad_g2);
-    else
-      dev::k_g2grad<uint32_t><<<gg, dev::kBlock, 0, st>>>(d->citems, nc, (const long long *)d->rp, (const long long *)d->rp_real,
-                                                          A, B, d->col, d->g2, f, lam, d->c, grad_g2);
-    PB_LAUNCHED("k_g2grad");
+  return PB_OK;
+}
+
+// grad_g2 (unpadded CSR order) += dL/dg2 of the nst calls whose stages fill the table (FF)
+template <int NST>
+int g2grad_launch(pb_dev *d, double *grad_g2, cudaStream_t st) {
+  const int gg = d->chan_grid(8), nc = (int)d->ncitems, ns = (int)d->ns;
+  const float2 *A = (const float2 *)d->ccoefA, *B = (const float2 *)d->ccoefB;
+  const long long *rp = (const long long *)d->rp, *rr = (const long long *)d->rp_real;
+  if (d->merged) {
+    if (d->col16) dev::k_g2grad<NST, true, uint16_t><<<gg, dev::kBlock, 0, st>>>(d->citems, nc, rp, rr, A, B, d->col16, d->g2, d->g2tab, ns, grad_g2);
+    else          dev::k_g2grad<NST, true, uint32_t><<<gg, dev::kBlock, 0, st>>>(d->citems, nc, rp, rr, A, B, d->col, d->g2, d->g2tab, ns, grad_g2);
+  } else {
+    if (d->col16) dev::k_g2grad<NST, false, uint16_t><<<gg, dev::kBlock, 0, st>>>(d->citems, nc, rp, rr, A, B, d->col16, d->g2, d->g2tab, ns, grad_g2);
+    else          dev::k_g2grad<NST, false, uint32_t><<<gg, dev::kBlock, 0, st>>>(d->citems, nc, rp, rr, A, B, d->col, d->g2, d->g2tab, ns, grad_g2);
   }
+  PB_LAUNCHED("k_g2grad");
   return PB_OK;
 }
 
@@ -1601,7 +1618,11 @@ extern "C" int pb_collision_vjp(pb_dev *d, const double *f, const double *lam, d
   if (!d || !f || !lam || !grad_f) return set_error(PB_EINVAL, "pb_collision_vjp: null argument");
   if (d->variant != PB_VARIANT_FF && !d->mixed())
     return set_error(PB_EINVAL, "pb_collision_vjp: needs the FF, G32 or G16 variant");
-  return vjp_launch(d, f, lam, grad_f, grad_g2, (cudaStream_t)stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool tab = grad_g2 && !d->mixed();
+  const int rc = vjp_launch(d, f, lam, grad_f, grad_g2, tab ? 0 : -1, st);
+  if (rc || !tab) return rc;
+  return g2grad_launch<1>(d, grad_g2, st);
 }
 
 extern "C" int pb_rtbte_rk4_vjp(pb_dev *d, const double *f, double *lam, double dt, double *grad_g2, void *stream) {
@@ -1630,10 +1651,11 @@ extern "C" int pb_rtbte_rk4_vjp(pb_dev *d, const double *f, double *lam, double 
   if ((rc = lincomb(d, 1.0, lam, 0.0, nullptr, acc, st))) return rc;
   for (int j = 3; j >= 0; --j) {
     if ((rc = lincomb(d, wl[j], lam, wm[j], j == 3 ? nullptr : mprev, g, st))) return rc;
-    if ((rc = vjp_launch(d, U[j], g, mu, grad_g2, st))) return rc;
+    if ((rc = vjp_launch(d, U[j], g, mu, grad_g2, grad_g2 && !d->mixed() ? j : -1, st))) return rc;
     if ((rc = lincomb(d, 1.0, acc, 1.0, mu, acc, st))) return rc;
     if ((rc = lincomb(d, 1.0, mu, 0.0, nullptr, mprev, st))) return rc;
   }
+  if (grad_g2 && !d->mixed() && (rc = g2grad_launch<4>(d, grad_g2, st))) return rc;
   return lincomb(d, 1.0, acc, 0.0, nullptr, lam, st);
 }
 

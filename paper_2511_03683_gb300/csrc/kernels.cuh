@@ -155,8 +155,11 @@ __device__ __forceinline__ void channel_deltas(const ChanGeom &g, int r, uint32_
 }
 
 // Per-channel rate coefficients (P_in, D) in FP64, stored as float-float (FF=true) or
-// double; part[item].x = sum over the item of P_out (for R_s).
-template <bool FF>
+// double; part[item].x = sum over the item of P_out (for R_s).  KFORM stores them without
+// the factor |g|^2 (P_in / g2 = G_a (N+1) + G_e N, D / g2 = G_e - G_a): the branch-merged
+// devices keep that form per channel, for the branch sums (which multiply g2 back in) and
+// for the |g|^2 gradient (whose bracket is exactly that form).
+template <bool FF, bool KFORM = false>
 __global__ void __launch_bounds__(kBlock) k_coef(const Item *__restrict__ items, int nitems, ChanGeom g,
                                                  void *__restrict__ coefA, void *__restrict__ coefB,
                                                  Part4 *__restrict__ part) {
@@ -171,8 +174,9 @@ __global__ void __launch_bounds__(kBlock) k_coef(const Item *__restrict__ items,
       double g2, Ga, Ge, N;
       int p;
       channel_deltas(g, I.row, g.col[c], g2, Ga, Ge, N, p, c);
-      const double pin = g2 * (Ga * (N + 1.0) + Ge * N);
-      const double dd = g2 * (Ge - Ga);
+      const double kin = Ga * (N + 1.0) + Ge * N, kd = Ge - Ga;
+      const double pin = KFORM ? kin : g2 * kin;
+      const double dd = KFORM ? kd : g2 * kd;
       acc += g2 * (Ga * N + Ge * (N + 1.0));
       if (FF) {
         ((float2 *)coefA)[c] = ff_split(pin);
@@ -190,25 +194,33 @@ __global__ void __launch_bounds__(kBlock) k_coef(const Item *__restrict__ items,
 // Branch-merged coefficients.  For fixed eps, omega, sigma and T every branch nu of a state
 // pair (s, p) enters Eq. 2 through the same f_s and f_p, so the coefficient form only needs
 // the sums over nu:  P_in(s,p) = sum_nu P_in(s,p,nu),  D(s,p) = sum_nu D(s,p,nu).  Entry k
-// sums the cnt[k] consecutive channels from cstart[k] in FP64 (ascending nu), multiplies by
+// sums the cnt[k] consecutive channels from cstart[k] in FP64 (ascending nu), each times
+// w[channel] when w is given (the g2 of coefficients stored without it), multiplies by
 // scale and stores the result in the sweep's format; padding entries (cnt 0) become zero.
 template <bool FF>
 __global__ void k_pair_coef(const long long *__restrict__ cstart, const uint8_t *__restrict__ cnt, long long n,
                             const void *__restrict__ cA, const void *__restrict__ cB, void *__restrict__ pA,
-                            void *__restrict__ pB, double scale) {
+                            void *__restrict__ pB, double scale, const double *__restrict__ w) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
     const long long s = cstart[k];
     const int m = cnt[k];
     double a = 0.0, b = 0.0;
     for (int i = 0; i < m; ++i) {
+      double x, y;
       if (FF) {
-        const float2 x = ((const float2 *)cA)[s + i], y = ((const float2 *)cB)[s + i];
-        a += ff_to_double(x.x, x.y);
-        b += ff_to_double(y.x, y.y);
+        const float2 xf = ((const float2 *)cA)[s + i], yf = ((const float2 *)cB)[s + i];
+        x = ff_to_double(xf.x, xf.y);
+        y = ff_to_double(yf.x, yf.y);
       } else {
-        a += ((const double *)cA)[s + i];
-        b += ((const double *)cB)[s + i];
+        x = ((const double *)cA)[s + i];
+        y = ((const double *)cB)[s + i];
       }
+      if (w) {
+        x *= w[s + i];
+        y *= w[s + i];
+      }
+      a += x;
+      b += y;
     }
     a *= scale;
     b *= scale;
@@ -1206,14 +1218,23 @@ __global__ void k_gstate_f(const double *__restrict__ f, int n, uint4 *__restric
 //   B_x = sum_{row x} f_p D.
 // So the adjoint is another segmented gather over the same stream: no scatter, no atomics.
 
-// G[3i] = lam_i, G[3i+1] = lam_i f_i, G[3i+2] = f_i as float-float pairs
+// G[3i] = lam_i, G[3i+1] = lam_i f_i, G[3i+2] = f_i as float-float pairs.  With tab (one
+// stage of the |g|^2 gradient's table, see k_g2grad): tab[2i] = (a, b), tab[2i+1] =
+// (f_i, 1 - f_i), a = scale lam_i f_i, b = scale lam_i (1 - f_i), all float-float.
 __global__ void k_vjp_prep(const double *__restrict__ f, const double *__restrict__ lam, int n,
-                           float2 *__restrict__ G) {
+                           float2 *__restrict__ G, double scale, float4 *__restrict__ tab) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  G[3 * i] = ff_split(lam[i]);
-  G[3 * i + 1] = ff_split(lam[i] * f[i]);
-  G[3 * i + 2] = ff_split(f[i]);
+  const double fi = f[i], li = lam[i];
+  G[3 * i] = ff_split(li);
+  G[3 * i + 1] = ff_split(li * fi);
+  G[3 * i + 2] = ff_split(fi);
+  if (tab) {
+    const double gi = 1.0 - fi, sl = scale * li;
+    const float2 a = ff_split(sl * fi), b = ff_split(sl * gi), fs = ff_split(fi), gs = ff_split(gi);
+    tab[2 * i] = make_float4(a.x, a.y, b.x, b.y);
+    tab[2 * i + 1] = make_float4(fs.x, fs.y, gs.x, gs.y);
+  }
 }
 
 // part[item] = (sum lam_p P_in, sum lam_p D, sum lam_p f_p D, sum f_p D)
@@ -1274,16 +1295,23 @@ __global__ void k_fin_vjp(const int *__restrict__ item_ptr, const Part4 *__restr
   out[r] = c * ((S1 + S2 - S3) + lam[r] * (S4 - R[r]));
 }
 
-// grad_g2[c] += -c lam_s [G_a F_abs + G_e F_em] for every stored channel c (CSR order without
-// padding); the bracket is (f_s (1-f_p) P_out - (1-f_s) f_p P_in) / g2, P_out = P_in + D.
-template <typename IDX>
+// |g|^2 gradient of NST collision calls at once (one call, or the four stages of an RK4
+// step): grad_g2[c] += sum_j -c lam_s^j [G_a F_abs + G_e F_em](f^j) for every stored channel
+// c (CSR order without padding).  g2 times the bracket is f_s (1-f_p) P_out - (1-f_s) f_p P_in
+// with P_out = P_in + D, so with the stage table of k_vjp_prep (scale -c; per state x and
+// stage j: a_j(x), b_j(x), f_x^j and 1 - f_x^j)
+//   g2 * sum_j term_j = P_out u - P_in v,   u = sum_j a_j(s) (1 - f_p^j),   v = sum_j b_j(s) f_p^j.
+// KFORM: the channel coefficients hold P_in / g2 and D / g2 (branch-merged devices) and the
+// sum is the gradient itself, also for channels with g2 = 0; otherwise it is divided by g2
+// and channels with g2 = 0 are skipped.  Float-float arithmetic; FP64 only to update grad.
+template <int NST, bool KFORM, typename IDX>
 __global__ void __launch_bounds__(kBlock) k_g2grad(const Item *__restrict__ items, int nitems,
                                                    const long long *__restrict__ rp_pad,
                                                    const long long *__restrict__ rp_real,
                                                    const float2 *__restrict__ A, const float2 *__restrict__ B,
                                                    const IDX *__restrict__ colp, const double *__restrict__ g2,
-                                                   const double *__restrict__ f, const double *__restrict__ lam,
-                                                   double c, double *__restrict__ grad) {
+                                                   const float4 *__restrict__ tab, int ns,
+                                                   double *__restrict__ grad) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -1292,19 +1320,32 @@ __global__ void __launch_bounds__(kBlock) k_g2grad(const Item *__restrict__ item
     const int r = I.row;
     const long long off = I.start - rp_pad[r];
     const long long real_len = rp_real[r + 1] - rp_real[r];
-    const double fs = f[r], ls = lam[r];
-    for (int j = lane; j < I.len; j += 32) {
-      const long long k = off + j;
-      if (k >= real_len) continue;
-      const long long cpos = I.start + j;
-      const double gv = g2[cpos];
-      if (!(gv > 0.0)) continue;
-      const unsigned p = (unsigned)colp[cpos] & 0xFFFFFFu;
-      const double fp = f[p];
-      const double pin = ff_to_double(A[cpos].x, A[cpos].y);
-      const double dd = ff_to_double(B[cpos].x, B[cpos].y);
-      const double t = fs * (1.0 - fp) * (pin + dd) - (1.0 - fs) * fp * pin;
-      grad[rp_real[r] + k] += -c * ls * t / gv;
+    const long long len = real_len - off < I.len ? real_len - off : I.len;  // stored channels of the item
+    double *__restrict__ gr = grad + rp_real[r] + off;
+    float4 rc[NST];
+#pragma unroll
+    for (int j = 0; j < NST; ++j) rc[j] = tab[2 * ((long long)j * ns + r)];
+    for (int k = lane; k < len; k += 32) {
+      const long long c = I.start + k;
+      const unsigned p = (unsigned)colp[c] & 0xFFFFFFu;
+      float uh = 0.f, ul = 0.f, vh = 0.f, vl = 0.f;
+#pragma unroll
+      for (int j = 0; j < NST; ++j) {
+        const float4 q = __ldg(tab + 2 * ((long long)j * ns + p) + 1);
+        ff_mac_lazy(uh, ul, make_float2(rc[j].x, rc[j].y), q.z, q.w);
+        ff_mac_lazy(vh, vl, make_float2(rc[j].z, rc[j].w), q.x, q.y);
+      }
+      const float2 pin = A[c], pout = ff_add(pin, B[c]);
+      float th = 0.f, tl = 0.f;
+      ff_mac(th, tl, pout, uh, ul);
+      ff_mac(th, tl, make_float2(-pin.x, -pin.y), vh, vl);
+      double t = ff_to_double(th, tl);
+      if (!KFORM) {
+        const double gv = g2[c];
+        if (!(gv > 0.0)) continue;
+        t /= gv;
+      }
+      gr[k] += t;
     }
   }
 }
