@@ -1159,23 +1159,26 @@ int launch_stream(pb_dev *d, int mode, const double *fd, const float2 *fff, cuda
 
 int fin_grid(const pb_dev *d) { return d->nfin_blocks; }
 
+// ydst: where a stage writes the next stage's input (default d->y)
 template <int STAGE>
-void launch_fin(pb_dev *d, const double *ysrc, double *out, double *f, double dt, cudaStream_t st) {
+void launch_fin(pb_dev *d, const double *ysrc, double *out, double *f, double dt, cudaStream_t st,
+                double *ydst = nullptr) {
+  double *y = ydst ? ydst : d->y;
   if (d->mixed())
     dev::k_fin_coll<true, STAGE, true><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->item_ptr, d->part}, (int)d->ns,
                                                                           d->c * d->gnorm(), d->R,
-                                                                          ysrc, out, f, d->acc, d->y,
+                                                                          ysrc, out, f, d->acc, y,
                                                                           (float2 *)d->gstate, dt);
   else if (d->variant == PB_VARIANT_LITERAL || d->variant == PB_VARIANT_PAPER)
     dev::k_fin_coll<true, STAGE><<<fin_grid(d), kFinBlock, 0, st>>>(
         dev::ItemSrc{d->variant == PB_VARIANT_PAPER ? d->t_item_ptr : d->item_ptr, d->part}, (int)d->ns, d->c, d->R, ysrc,
-                                                                    out, f, d->acc, d->y, d->yff, dt);
+                                                                    out, f, d->acc, y, d->yff, dt);
   else if (d->sym)
     dev::k_fin_tiles<STAGE><<<(int)((d->ns * 32 + 255) / 256), 256, 0, st>>>(
-        dev::TileSrc{d->tpart, d->td.nb, d->td.nsp}, (int)d->ns, d->c, d->R, ysrc, out, f, d->acc, d->y, d->yff, dt);
+        dev::TileSrc{d->tpart, d->td.nb, d->td.nsp}, (int)d->ns, d->c, d->R, ysrc, out, f, d->acc, y, d->yff, dt);
   else
     dev::k_fin_coll<false, STAGE><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->item_ptr, d->part}, (int)d->ns, d->c, d->R, ysrc,
-                                                                     out, f, d->acc, d->y, d->yff, dt);
+                                                                     out, f, d->acc, y, d->yff, dt);
 }
 
 int to_ff(pb_dev *d, const double *x, int64_t n, float2 *out, cudaStream_t st) {
@@ -1531,8 +1534,8 @@ int coef_setup(pb_dev *d, cudaStream_t st) {
 }
 
 // Mixed-precision adjoint: FP32 per-channel terms, FP64 partials and output.
-int vjp_launch_mixed(pb_dev *d, const double *f, const double *lam, double *grad_f, double *grad_g2,
-                     cudaStream_t st) {
+int vjp_launch_mixed(pb_dev *d, const double *f, const double *lam, double wl, const double *mprev, double wm,
+                     double *mu, const double *acc_in, double *acc_out, int slot, cudaStream_t st) {
   const int ns = (int)d->ns, n = (int)d->nitems;
   if (!d->vjp_g_ok)
     return set_error(PB_EINVAL, "pb_collision_vjp: the FP32/BF16 adjoint stages 20 bytes per state in shared "
@@ -1540,8 +1543,9 @@ int vjp_launch_mixed(pb_dev *d, const double *f, const double *lam, double *grad
   int rc = stage_input(d, f, st);
   if (rc) return rc;
   float *lam32 = (float *)d->vjpG;  // ns floats fit in the [ns][3] float2 table
-  dev::k_to_f32<<<(ns + 255) / 256, 256, 0, st>>>(lam, ns, lam32);
-  PB_LAUNCHED("k_to_f32");
+  dev::k_vjp_prep32<<<(ns + 255) / 256, 256, 0, st>>>(f, lam, wl, mprev, wm, ns, lam32, -d->c * d->gnorm(),
+                                                      slot >= 0 ? d->g2tab + (size_t)slot * ns : nullptr);
+  PB_LAUNCHED("k_vjp_prep32");
   const dev::GGeom g = d->ggeom();
   const size_t smem = (sizeof(uint4) + sizeof(float)) * (size_t)ns;
   const int ctas = (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(228 * 1024) / (smem + 1024)));
@@ -1552,26 +1556,30 @@ int vjp_launch_mixed(pb_dev *d, const double *f, const double *lam, double *grad
     dev::k_stream_g_vjp<__nv_bfloat16><<<grid, 512, smem, st>>>(d->items, n, g, (const __nv_bfloat16 *)d->g2lo, d->gstate,
                                                                 lam32, ns, d->part);
   PB_LAUNCHED("k_stream_g_vjp");
-  dev::k_fin_rate<true><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->item_ptr, d->part}, ns, -d->c * d->gnorm(), d->R, grad_f);
+  dev::k_fin_rate<true><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->item_ptr, d->part}, ns, -d->c * d->gnorm(), d->R, mu);
   PB_LAUNCHED("k_fin_rate (vjp)");
-  if (grad_g2) {
-    dev::k_g2grad_g<<<d->stream_grid(8), dev::kBlock, 0, st>>>(d->items, n, g, d->gstate, (const long long *)d->rp,
-                                                               (const long long *)d->rp_real, lam,
-                                                               -d->c * d->gnorm(), grad_g2);
-    PB_LAUNCHED("k_g2grad_g");
+  if (acc_out) {
+    dev::k_lincomb<<<(ns + 255) / 256, 256, 0, st>>>(ns, 1.0, acc_in, 1.0, mu, acc_out);
+    PB_LAUNCHED("k_lincomb");
   }
   return PB_OK;
 }
 
-// grad_f = J(f)^T lam.  Mixed variants: grad_g2 (unpadded CSR order) += dL/dg2 if not null.
-// FF: slot >= 0 writes stage slot of the |g|^2-gradient table, which g2grad_launch applies.
-int vjp_launch(pb_dev *d, const double *f, const double *lam, double *grad_f, double *grad_g2, int slot,
-               cudaStream_t st) {
-  if (d->mixed()) return vjp_launch_mixed(d, f, lam, grad_f, grad_g2, st);
-  const int ns = (int)d->ns, n = (int)d->nitems;
-  dev::k_vjp_prep<<<(ns + 255) / 256, 256, 0, st>>>(f, lam, ns, d->vjpG, -d->c,
+// FF adjoint in three launches per call: vjp_prep_ff (the cotangent g = wl lam + wm mprev,
+// mprev may be null, and its gather table; slot >= 0 also writes that stage of the
+// |g|^2-gradient table), vjp_sweep_ff (k_stream_vjp) and vjp_fin_ff (mu = J(f)^T g, out = mu
+// if not null, acc_out = acc_in + mu if not null, and the next stage's prep if nx.f is set).
+int vjp_prep_ff(pb_dev *d, const double *f, const double *lam, double wl, const double *mprev, double wm,
+                 double *gbuf, int slot, cudaStream_t st) {
+  const int ns = (int)d->ns;
+  dev::k_vjp_prep<<<(ns + 255) / 256, 256, 0, st>>>(f, lam, wl, mprev, wm, ns, gbuf, d->vjpG, -d->c,
                                                     slot >= 0 ? d->g2tab + 2 * (size_t)slot * ns : nullptr);
   PB_LAUNCHED("k_vjp_prep");
+  return PB_OK;
+}
+
+int vjp_sweep_ff(pb_dev *d, cudaStream_t st) {
+  const int ns = (int)d->ns, n = (int)d->nitems;
   const int grid = d->stream_grid(d->smem_G ? std::max(1, std::min(d->ctas, (int)((228 * 1024) / (d->smem_G + 1024)))) : d->ctas);
   const float4 *A4 = (const float4 *)d->coefA, *B4 = (const float4 *)d->coefB;
   if (d->smem_G) {
@@ -1582,24 +1590,42 @@ int vjp_launch(pb_dev *d, const double *f, const double *lam, double *grad_f, do
     else           dev::k_stream_vjp<false, uint32_t><<<grid, dev::kBlock, 0, st>>>(d->items, n, A4, B4, d->sidx32, d->vjpG, ns, d->part);
   }
   PB_LAUNCHED("k_stream_vjp");
-  dev::k_fin_vjp<<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, ns, d->c, d->R, lam, grad_f);
+  return PB_OK;
+}
+
+int vjp_fin_ff(pb_dev *d, const double *gbuf, double *mu, const double *acc_in, double *acc_out,
+                const dev::VjpNext &nx, cudaStream_t st) {
+  const int ns = (int)d->ns;
+  dev::k_fin_vjp<<<(int)(((int64_t)ns * 32 + 255) / 256), 256, 0, st>>>(d->item_ptr, d->part, ns, d->c, d->R, gbuf, mu,
+                                                                         acc_in, acc_out, nx, d->vjpG, -d->c);
   PB_LAUNCHED("k_fin_vjp");
   return PB_OK;
 }
 
-// grad_g2 (unpadded CSR order) += dL/dg2 of the nst calls whose stages fill the table (FF)
+// grad_g2 (unpadded CSR order) += dL/dg2 of the NST calls whose stages fill the table
 template <int NST>
 int g2grad_launch(pb_dev *d, double *grad_g2, cudaStream_t st) {
-  const int gg = d->chan_grid(8), nc = (int)d->ncitems, ns = (int)d->ns;
-  const float2 *A = (const float2 *)d->ccoefA, *B = (const float2 *)d->ccoefB;
+  const int ns = (int)d->ns;
   const long long *rp = (const long long *)d->rp, *rr = (const long long *)d->rp_real;
-  if (d->merged) {
-    if (d->col16) dev::k_g2grad<NST, true, uint16_t><<<gg, dev::kBlock, 0, st>>>(d->citems, nc, rp, rr, A, B, d->col16, d->g2, d->g2tab, ns, grad_g2);
-    else          dev::k_g2grad<NST, true, uint32_t><<<gg, dev::kBlock, 0, st>>>(d->citems, nc, rp, rr, A, B, d->col, d->g2, d->g2tab, ns, grad_g2);
-  } else {
-    if (d->col16) dev::k_g2grad<NST, false, uint16_t><<<gg, dev::kBlock, 0, st>>>(d->citems, nc, rp, rr, A, B, d->col16, d->g2, d->g2tab, ns, grad_g2);
-    else          dev::k_g2grad<NST, false, uint32_t><<<gg, dev::kBlock, 0, st>>>(d->citems, nc, rp, rr, A, B, d->col, d->g2, d->g2tab, ns, grad_g2);
+  if (d->mixed()) {
+    dev::k_g2grad_g<NST><<<d->stream_grid(8), dev::kBlock, 0, st>>>(d->items, (int)d->nitems, d->ggeom(), d->gstate,
+                                                                    rp, rr, d->g2tab, ns, grad_g2);
+    PB_LAUNCHED("k_g2grad_g");
+    return PB_OK;
   }
+  const float2 *A = (const float2 *)d->ccoefA, *B = (const float2 *)d->ccoefB;
+  if (d->merged) {
+    // per state pair (the channel coefficients are stored without g2)
+    const int gg = d->stream_grid(8), n = (int)d->nitems;
+    const long long *pcs = (const long long *)d->pcstart;
+    if (d->sidx16) dev::k_g2grad_pairs<NST, uint16_t><<<gg, dev::kBlock, 0, st>>>(d->items, n, d->sidx16, pcs, d->pcnt, rp, rr, A, B, d->g2tab, ns, grad_g2);
+    else           dev::k_g2grad_pairs<NST, uint32_t><<<gg, dev::kBlock, 0, st>>>(d->items, n, d->sidx32, pcs, d->pcnt, rp, rr, A, B, d->g2tab, ns, grad_g2);
+    PB_LAUNCHED("k_g2grad_pairs");
+    return PB_OK;
+  }
+  const int gg = d->chan_grid(8), nc = (int)d->ncitems;
+  if (d->col16) dev::k_g2grad<NST, uint16_t><<<gg, dev::kBlock, 0, st>>>(d->citems, nc, rp, rr, A, B, d->col16, d->g2, d->g2tab, ns, grad_g2);
+  else          dev::k_g2grad<NST, uint32_t><<<gg, dev::kBlock, 0, st>>>(d->citems, nc, rp, rr, A, B, d->col, d->g2, d->g2tab, ns, grad_g2);
   PB_LAUNCHED("k_g2grad");
   return PB_OK;
 }
@@ -1619,9 +1645,17 @@ extern "C" int pb_collision_vjp(pb_dev *d, const double *f, const double *lam, d
   if (d->variant != PB_VARIANT_FF && !d->mixed())
     return set_error(PB_EINVAL, "pb_collision_vjp: needs the FF, G32 or G16 variant");
   cudaStream_t st = (cudaStream_t)stream;
-  const bool tab = grad_g2 && !d->mixed();
-  const int rc = vjp_launch(d, f, lam, grad_f, grad_g2, tab ? 0 : -1, st);
-  if (rc || !tab) return rc;
+  const int slot = grad_g2 ? 0 : -1;
+  if (d->mixed()) {
+    const int rc = vjp_launch_mixed(d, f, lam, 1.0, nullptr, 0.0, grad_f, nullptr, nullptr, slot, st);
+    if (rc || !grad_g2) return rc;
+  } else {
+    int rc;
+    if ((rc = vjp_prep_ff(d, f, lam, 1.0, nullptr, 0.0, d->vecs, slot, st))) return rc;
+    if ((rc = vjp_sweep_ff(d, st))) return rc;
+    if ((rc = vjp_fin_ff(d, d->vecs, grad_f, nullptr, nullptr, dev::VjpNext{}, st))) return rc;
+    if (!grad_g2) return PB_OK;
+  }
   return g2grad_launch<1>(d, grad_g2, st);
 }
 
@@ -1633,30 +1667,50 @@ extern "C" int pb_rtbte_rk4_vjp(pb_dev *d, const double *f, double *lam, double 
   if (!std::isfinite(dt)) return set_error(PB_EINVAL, "pb_rtbte_rk4_vjp: bad dt");
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t ns = d->ns;
-  double *u2 = d->vecs, *u3 = u2 + ns, *u4 = u3 + ns, *k = u4 + ns, *g = k + ns, *mu = g + ns, *acc = mu + ns,
-         *mprev = acc + ns;
+  double *u2 = d->vecs, *u3 = u2 + ns, *u4 = u3 + ns, *acc = u4 + ns, *ga = acc + ns, *gb = ga + ns, *mu0 = gb + ns,
+         *mu1 = mu0 + ns;
   int rc;
-  // forward stages (u1 = f)
-  if ((rc = pb_collision(d, f, k, stream))) return rc;
-  if ((rc = lincomb(d, 1.0, f, 0.5 * dt, k, u2, st))) return rc;
-  if ((rc = pb_collision(d, u2, k, stream))) return rc;
-  if ((rc = lincomb(d, 1.0, f, 0.5 * dt, k, u3, st))) return rc;
-  if ((rc = pb_collision(d, u3, k, stream))) return rc;
-  if ((rc = lincomb(d, 1.0, f, dt, k, u4, st))) return rc;
+  // forward stages u2, u3, u4 (u1 = f) through the RK4 stage finalisers
+  if ((rc = stage_input(d, f, st))) return rc;
+  double *fw = const_cast<double *>(f);  // stages 0..2 only read f
+  if ((rc = launch_stream(d, dev::MODE_COLL, f, d->yff, st))) return rc;
+  launch_fin<0>(d, f, nullptr, fw, dt, st, u2);
+  if ((rc = launch_stream(d, dev::MODE_COLL, u2, d->yff, st))) return rc;
+  launch_fin<1>(d, u2, nullptr, fw, dt, st, u3);
+  if ((rc = launch_stream(d, dev::MODE_COLL, u3, d->yff, st))) return rc;
+  launch_fin<2>(d, u3, nullptr, fw, dt, st, u4);
+  PB_LAUNCHED("rk4 vjp forward stages");
   // reverse: dL/dk4 = dt/6 lam; dL/dk3 = dt/3 lam + dt mu4; dL/dk2 = dt/3 lam + dt/2 mu3;
   // dL/dk1 = dt/6 lam + dt/2 mu2; dL/df = lam + mu1 + mu2 + mu3 + mu4, mu_i = J(u_i)^T dL/dk_i
   const double *U[4] = {f, u2, u3, u4};
   const double wl[4] = {dt / 6.0, dt / 3.0, dt / 3.0, dt / 6.0};
   const double wm[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
-  if ((rc = lincomb(d, 1.0, lam, 0.0, nullptr, acc, st))) return rc;
-  for (int j = 3; j >= 0; --j) {
-    if ((rc = lincomb(d, wl[j], lam, wm[j], j == 3 ? nullptr : mprev, g, st))) return rc;
-    if ((rc = vjp_launch(d, U[j], g, mu, grad_g2, grad_g2 && !d->mixed() ? j : -1, st))) return rc;
-    if ((rc = lincomb(d, 1.0, acc, 1.0, mu, acc, st))) return rc;
-    if ((rc = lincomb(d, 1.0, mu, 0.0, nullptr, mprev, st))) return rc;
+  if (d->mixed()) {
+    double *mu = mu0, *mprev = mu1;
+    for (int j = 3; j >= 0; --j) {
+      std::swap(mu, mprev);
+      const double *ain = j == 3 ? lam : acc;
+      double *aout = j == 0 ? lam : acc;  // the last stage writes dL/df over lam (lam is read first)
+      if ((rc = vjp_launch_mixed(d, U[j], lam, wl[j], j == 3 ? nullptr : mprev, wm[j], mu, ain, aout,
+                                 grad_g2 ? j : -1, st)))
+        return rc;
+    }
+  } else {
+    // each stage's finaliser prepares the next stage's cotangent (g alternates ga, gb)
+    double *gc = ga, *gn = gb;
+    if ((rc = vjp_prep_ff(d, U[3], lam, wl[3], nullptr, 0.0, gc, grad_g2 ? 3 : -1, st))) return rc;
+    for (int j = 3; j >= 0; --j) {
+      if ((rc = vjp_sweep_ff(d, st))) return rc;
+      dev::VjpNext nx{};
+      if (j > 0) nx = dev::VjpNext{U[j - 1], lam, wl[j - 1], wm[j - 1], gn,
+                                   grad_g2 ? d->g2tab + 2 * (size_t)(j - 1) * ns : nullptr};
+      // the last stage writes dL/df = lam + sum mu over lam (every read of lam precedes it)
+      if ((rc = vjp_fin_ff(d, gc, nullptr, j == 3 ? lam : acc, j == 0 ? lam : acc, nx, st))) return rc;
+      std::swap(gc, gn);
+    }
   }
-  if (grad_g2 && !d->mixed() && (rc = g2grad_launch<4>(d, grad_g2, st))) return rc;
-  return lincomb(d, 1.0, acc, 0.0, nullptr, lam, st);
+  if (grad_g2 && (rc = g2grad_launch<4>(d, grad_g2, st))) return rc;
+  return PB_OK;
 }
 
 extern "C" int pb_dev_set_g2(pb_dev *d, const double *g2, void *stream) {

@@ -93,11 +93,28 @@ __device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
 
 // Sum over the warp of a float-float value with a fixed xor shuffle tree (FP32 only), then
 // one conversion: lane 0's result is reproducible run to run.
-__device__ __forceinline__ double warp_sum_ff(float2 v) {
+__device__ __forceinline__ float2 warp_reduce_ff(float2 v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
     v = ff_add(v, make_float2(__shfl_xor_sync(0xFFFFFFFFu, v.x, o), __shfl_xor_sync(0xFFFFFFFFu, v.y, o)));
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum_ff(float2 v) {
+  v = warp_reduce_ff(v);
   return ff_to_double(v.x, v.y);
+}
+
+// Exact FP32 -> FP64 widening with integer operations, from the IEEE 754 binary32 and binary64
+// layouts: the exponent is rebiased by 1023 - 127 and the significand moves up 29 bits.  Zero
+// and subnormal inputs (below 2^-126 in magnitude) give a signed zero; Inf and NaN stay Inf and
+// NaN.  Keeps the conversions of float-float results off the FP64 pipe.
+__device__ __forceinline__ double widen_f32(float x) {
+  const unsigned b = __float_as_uint(x), m = b & 0x7FFFFFFFu, e = m >> 23;
+  unsigned hi = (m >> 3) + 0x38000000u, lo = b << 29;
+  if (e == 0u) hi = lo = 0u;
+  if (e == 0xFFu) hi |= 0x7FF00000u;
+  return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)lo);
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -1123,13 +1140,39 @@ __global__ void __launch_bounds__(512) k_stream_g_vjp(const Item *__restrict__ i
   }
 }
 
-// grad_g2[c] += scale * lam_s * [G_a F_abs + G_e F_em] (FP32 terms, FP64 accumulation), stored
-// channels in CSR order without padding; scale = -(2 pi / hbar N_q) / (sqrt(2 pi) sigma).
+// The cotangent g = wl lam + wm mprev (mprev may be null) in FP32 for k_stream_g_vjp.  With
+// tab (one stage of the mixed |g|^2-gradient table, see k_g2grad_g): tab[i] =
+// (scale g_i, f_i hi, f_i lo, 1 - f_i) in FP32.
+__global__ void k_vjp_prep32(const double *__restrict__ f, const double *__restrict__ lam, double wl,
+                             const double *__restrict__ mprev, double wm, int n, float *__restrict__ lam32,
+                             double scale, float4 *__restrict__ tab) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double li = wl * lam[i] + (mprev ? wm * mprev[i] : 0.0);
+  lam32[i] = __double2float_rn(li);
+  if (tab) {
+    const double fi = f[i];
+    const float2 fs = ff_split(fi);
+    tab[i] = make_float4(__double2float_rn(scale * li), fs.x, fs.y, __double2float_rn(1.0 - fi));
+  }
+}
+
+// Mixed-precision |g|^2 gradient of NST collision calls at once (one call, or the four stages
+// of an RK4 step): grad_g2[c] += sum_j scale lam_s^j [G_a F_abs + G_e F_em](f^j), stored
+// channels in CSR order without padding, scale = -(2 pi / hbar N_q) / (sqrt(2 pi) sigma) (the
+// Gaussians below are not normalised).  The bracket is
+// (G_a + G_e) N (f_s - f_p) + G_e f_s (1-f_p) - G_a (1-f_s) f_p, so with the stage table of
+// k_vjp_prep32 (c_j = scale lam^j and f^j per state) and c_j(s) summed over the stages,
+//   sum_j c_j [...] = GN W + G_e U - G_a V,  W = sum_j c_j (f_s^j - f_p^j),
+//   U = sum_j c_j f_s^j (1 - f_p^j),  V = sum_j c_j (1 - f_s^j) f_p^j,
+// with f_s - f_p from the high and low parts of f (it is small where the terms cancel): the
+// Gaussians once per channel, FP32 terms, one FP64 update of grad per channel.
+template <int NST>
 __global__ void __launch_bounds__(kBlock) k_g2grad_g(const Item *__restrict__ items, int nitems, GGeom g,
                                                      const uint4 *__restrict__ gstate,
                                                      const long long *__restrict__ rp_pad,
                                                      const long long *__restrict__ rp_real,
-                                                     const double *__restrict__ lam, double scale,
+                                                     const float4 *__restrict__ tab, int ns,
                                                      double *__restrict__ grad) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1141,21 +1184,39 @@ __global__ void __launch_bounds__(kBlock) k_g2grad_g(const Item *__restrict__ it
     const int base = g.cpad - rec_lnm(ss);
     const long long off = I.start - rp_pad[r];
     const long long real_len = rp_real[r + 1] - rp_real[r];
-    const double sl = scale * lam[r];
-    for (int j = lane; j < I.len; j += 32) {
-      const long long k = off + j;
-      if (k >= real_len) continue;
-      const unsigned cw = g.col[I.start + j];
+    const long long len = real_len - off < I.len ? real_len - off : I.len;  // stored channels of the item
+    double *__restrict__ gr = grad + rp_real[r] + off;
+    float4 rs[NST];  // (c, f hi, f lo, c f)
+    float rb[NST];   // c (1 - f)
+#pragma unroll
+    for (int j = 0; j < NST; ++j) {
+      const float4 t = tab[(long long)j * ns + r];
+      rs[j] = make_float4(t.x, t.y, t.z, t.x * t.y);
+      rb[j] = t.x * t.w;
+    }
+    for (int k = lane; k < len; k += 32) {
+      const unsigned cw = g.col[I.start + k];
       const unsigned p = cw & 0xFFFFFFu;
-      const float t = g_term<MODE_COLL>(g, ss, __ldg(gstate + p), cw, base, 1.0f);
-      grad[rp_real[r] + k] += sl * (double)t;
+      const uint4 sp = __ldg(gstate + p);
+      const float2 t = __ldg(g.tabp + (base + rec_lnm(sp) + (int)(cw >> 24)));
+      const float dh = __fsub_rn(__uint_as_float(ss.x), __uint_as_float(sp.x));
+      const float dl = __fsub_rn(rec_eps_lo(ss), rec_eps_lo(sp));
+      const float xa = (dh + t.x) + dl;  // x + w
+      const float xe = (dh - t.x) + dl;  // x - w
+      const float Ga = ex2_approx(xa * xa * g.k2);
+      const float Ge = ex2_approx(xe * xe * g.k2);
+      const float GN = (Ga + Ge) * t.y;
+      float W = 0.f, U = 0.f, V = 0.f;
+#pragma unroll
+      for (int j = 0; j < NST; ++j) {
+        const float4 q = __ldg(tab + (long long)j * ns + p);
+        W = fmaf(rs[j].x, __fsub_rn(rs[j].y, q.y) + __fsub_rn(rs[j].z, q.z), W);
+        U = fmaf(rs[j].w, q.w, U);
+        V = fmaf(rb[j], q.y, V);
+      }
+      gr[k] += (double)fmaf(GN, W, fmaf(Ge, U, -Ga * V));
     }
   }
-}
-
-__global__ void k_to_f32(const double *__restrict__ x, int n, float *__restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = __double2float_rn(x[i]);
 }
 
 // |g|^2 in the storage type of the mixed-precision variants (round to nearest)
@@ -1218,14 +1279,13 @@ __global__ void k_gstate_f(const double *__restrict__ f, int n, uint4 *__restric
 //   B_x = sum_{row x} f_p D.
 // So the adjoint is another segmented gather over the same stream: no scatter, no atomics.
 
-// G[3i] = lam_i, G[3i+1] = lam_i f_i, G[3i+2] = f_i as float-float pairs.  With tab (one
+// The cotangent of one call, g = wl lam + wm mprev (mprev may be null; an RK4 stage's), into
+// g and G: G[3i] = g_i, G[3i+1] = g_i f_i, G[3i+2] = f_i as float-float pairs.  With tab (one
 // stage of the |g|^2 gradient's table, see k_g2grad): tab[2i] = (a, b), tab[2i+1] =
-// (f_i, 1 - f_i), a = scale lam_i f_i, b = scale lam_i (1 - f_i), all float-float.
-__global__ void k_vjp_prep(const double *__restrict__ f, const double *__restrict__ lam, int n,
-                           float2 *__restrict__ G, double scale, float4 *__restrict__ tab) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double fi = f[i], li = lam[i];
+// (f_i, 1 - f_i), a = scale g_i f_i, b = scale g_i (1 - f_i), all float-float.
+__device__ __forceinline__ void vjp_prep_at(int i, double fi, double li, double *__restrict__ g,
+                                            float2 *__restrict__ G, double scale, float4 *__restrict__ tab) {
+  g[i] = li;
   G[3 * i] = ff_split(li);
   G[3 * i + 1] = ff_split(li * fi);
   G[3 * i + 2] = ff_split(fi);
@@ -1235,6 +1295,14 @@ __global__ void k_vjp_prep(const double *__restrict__ f, const double *__restric
     tab[2 * i] = make_float4(a.x, a.y, b.x, b.y);
     tab[2 * i + 1] = make_float4(fs.x, fs.y, gs.x, gs.y);
   }
+}
+
+__global__ void k_vjp_prep(const double *__restrict__ f, const double *__restrict__ lam, double wl,
+                           const double *__restrict__ mprev, double wm, int n, double *__restrict__ g,
+                           float2 *__restrict__ G, double scale, float4 *__restrict__ tab) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  vjp_prep_at(i, f[i], wl * lam[i] + (mprev ? wm * mprev[i] : 0.0), g, G, scale, tab);
 }
 
 // part[item] = (sum lam_p P_in, sum lam_p D, sum lam_p f_p D, sum f_p D)
@@ -1268,31 +1336,61 @@ __global__ void __launch_bounds__(kBlock) k_stream_vjp(const Item *__restrict__ 
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const float2 lp = Gv[3 * p[k]], mp = Gv[3 * p[k] + 1], fp = Gv[3 * p[k] + 2];
-        ff_mac(h1, l1, lp, ah[k], al[k]);
-        ff_mac(h2, l2, lp, bh[k], bl[k]);
-        ff_mac(h3, l3, mp, bh[k], bl[k]);
-        ff_mac(h4, l4, fp, bh[k], bl[k]);
+        ff_mac_lazy(h1, l1, lp, ah[k], al[k]);
+        ff_mac_lazy(h2, l2, lp, bh[k], bl[k]);
+        ff_mac_lazy(h3, l3, mp, bh[k], bl[k]);
+        ff_mac_lazy(h4, l4, fp, bh[k], bl[k]);
       }
     }
-    const double S1 = warp_sum(ff_to_double(h1, l1)), S2 = warp_sum(ff_to_double(h2, l2));
-    const double S3 = warp_sum(ff_to_double(h3, l3)), S4 = warp_sum(ff_to_double(h4, l4));
-    if (lane == 0) part[it] = make_part4(S1, S2, S3, S4);
+    // float-float partials (no FP64 here; the finaliser converts once per state)
+    const float2 S1 = warp_reduce_ff(make_float2(h1, l1)), S2 = warp_reduce_ff(make_float2(h2, l2));
+    const float2 S3 = warp_reduce_ff(make_float2(h3, l3)), S4 = warp_reduce_ff(make_float2(h4, l4));
+    if (lane == 0) {
+      float4 *q = reinterpret_cast<float4 *>(part + it);
+      q[0] = make_float4(S1.x, S1.y, S2.x, S2.y);
+      q[1] = make_float4(S3.x, S3.y, S4.x, S4.y);
+    }
   }
 }
 
-__global__ void k_fin_vjp(const int *__restrict__ item_ptr, const Part4 *__restrict__ part, int ns, double c,
-                          const double *__restrict__ R, const double *__restrict__ lam, double *__restrict__ out) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+// The next RK4 stage's cotangent, prepared by the finaliser of the current stage (f null: none):
+// g' = wl lam + wm mu with mu this stage's J^T g, into g, the gather table and tab (if not null).
+struct VjpNext {
+  const double *f, *lam;
+  double wl, wm;
+  double *g;
+  float4 *tab;
+};
+
+// mu = J^T g from the float-float partials of k_stream_vjp, one warp per state (lanes over the
+// state's work items, a fixed shuffle tree); out = mu if not null; with acc_out also
+// acc_out = acc_in + mu (the running sum of an RK4 step's stage cotangents); nx: see VjpNext.
+__global__ void __launch_bounds__(256) k_fin_vjp(const int *__restrict__ item_ptr, const Part4 *__restrict__ part,
+                                                 int ns, double c, const double *__restrict__ R,
+                                                 const double *__restrict__ g, double *__restrict__ out,
+                                                 const double *acc_in, double *acc_out,  // acc_in may be acc_out
+                                                 VjpNext nx, float2 *__restrict__ G, double scale) {
+  const int r = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (r >= ns) return;
-  double S1 = 0.0, S2 = 0.0, S3 = 0.0, S4 = 0.0;
-  for (int i = item_ptr[r]; i < item_ptr[r + 1]; ++i) {
-    const Part4 v = part[i];
-    S1 += v.x;
-    S2 += v.y;
-    S3 += v.z;
-    S4 += v.w;
+  float2 S1 = make_float2(0.f, 0.f), S2 = S1, S3 = S1, S4 = S1;
+  for (int i = item_ptr[r] + lane; i < item_ptr[r + 1]; i += 32) {
+    const float4 *q = reinterpret_cast<const float4 *>(part + i);
+    const float4 u = q[0], v = q[1];
+    S1 = ff_add(S1, make_float2(u.x, u.y));
+    S2 = ff_add(S2, make_float2(u.z, u.w));
+    S3 = ff_add(S3, make_float2(v.x, v.y));
+    S4 = ff_add(S4, make_float2(v.z, v.w));
   }
-  out[r] = c * ((S1 + S2 - S3) + lam[r] * (S4 - R[r]));
+  S1 = warp_reduce_ff(S1);
+  S2 = warp_reduce_ff(S2);
+  S3 = warp_reduce_ff(S3);
+  S4 = warp_reduce_ff(S4);
+  if (lane != 0) return;
+  const double mu = c * ((ff_to_double(S1.x, S1.y) + ff_to_double(S2.x, S2.y) - ff_to_double(S3.x, S3.y)) +
+                         g[r] * (ff_to_double(S4.x, S4.y) - R[r]));
+  if (out) out[r] = mu;
+  if (acc_out) acc_out[r] = acc_in[r] + mu;
+  if (nx.f) vjp_prep_at(r, nx.f[r], nx.wl * nx.lam[r] + nx.wm * mu, nx.g, G, scale, nx.tab);
 }
 
 // |g|^2 gradient of NST collision calls at once (one call, or the four stages of an RK4
@@ -1301,10 +1399,27 @@ __global__ void k_fin_vjp(const int *__restrict__ item_ptr, const Part4 *__restr
 // with P_out = P_in + D, so with the stage table of k_vjp_prep (scale -c; per state x and
 // stage j: a_j(x), b_j(x), f_x^j and 1 - f_x^j)
 //   g2 * sum_j term_j = P_out u - P_in v,   u = sum_j a_j(s) (1 - f_p^j),   v = sum_j b_j(s) f_p^j.
-// KFORM: the channel coefficients hold P_in / g2 and D / g2 (branch-merged devices) and the
-// sum is the gradient itself, also for channels with g2 = 0; otherwise it is divided by g2
-// and channels with g2 = 0 are skipped.  Float-float arithmetic; FP64 only to update grad.
-template <int NST, bool KFORM, typename IDX>
+// Here the channel coefficients include g2 (devices without branch merging), so the sum is
+// divided by it and channels with g2 = 0 are skipped (k_g2grad_pairs below serves the
+// branch-merged devices).  Float-float arithmetic; FP64 for the division and the update.
+template <int NST>
+__device__ __forceinline__ double g2grad_term(const float4 *__restrict__ rc, const float4 *__restrict__ tab, int ns,
+                                              unsigned p, float2 pin, float2 dd) {
+  float uh = 0.f, ul = 0.f, vh = 0.f, vl = 0.f;
+#pragma unroll
+  for (int j = 0; j < NST; ++j) {
+    const float4 q = __ldg(tab + 2 * (j * ns + (int)p) + 1);
+    ff_mac_lazy(uh, ul, make_float2(rc[j].x, rc[j].y), q.z, q.w);
+    ff_mac_lazy(vh, vl, make_float2(rc[j].z, rc[j].w), q.x, q.y);
+  }
+  const float2 pout = ff_add(pin, dd);
+  float th = 0.f, tl = 0.f;
+  ff_mac(th, tl, pout, uh, ul);
+  ff_mac(th, tl, make_float2(-pin.x, -pin.y), vh, vl);
+  return widen_f32(th) + widen_f32(tl);
+}
+
+template <int NST, typename IDX>
 __global__ void __launch_bounds__(kBlock) k_g2grad(const Item *__restrict__ items, int nitems,
                                                    const long long *__restrict__ rp_pad,
                                                    const long long *__restrict__ rp_real,
@@ -1320,32 +1435,97 @@ __global__ void __launch_bounds__(kBlock) k_g2grad(const Item *__restrict__ item
     const int r = I.row;
     const long long off = I.start - rp_pad[r];
     const long long real_len = rp_real[r + 1] - rp_real[r];
-    const long long len = real_len - off < I.len ? real_len - off : I.len;  // stored channels of the item
+    const int len = (int)(real_len - off < I.len ? real_len - off : I.len);  // stored channels of the item
     double *__restrict__ gr = grad + rp_real[r] + off;
+    const float2 *__restrict__ Ai = A + I.start, *__restrict__ Bi = B + I.start;
+    const IDX *__restrict__ ci = colp + I.start;
     float4 rc[NST];
 #pragma unroll
-    for (int j = 0; j < NST; ++j) rc[j] = tab[2 * ((long long)j * ns + r)];
-    for (int k = lane; k < len; k += 32) {
-      const long long c = I.start + k;
-      const unsigned p = (unsigned)colp[c] & 0xFFFFFFu;
-      float uh = 0.f, ul = 0.f, vh = 0.f, vl = 0.f;
+    for (int j = 0; j < NST; ++j) rc[j] = tab[2 * (j * ns + r)];
+    // two channels per lane per trip: their loads are issued together
+    for (int k = lane; k < len; k += 64) {
+      const int k1 = k + 32;
+      const bool two = k1 < len;
+      const unsigned p0 = (unsigned)ci[k] & 0xFFFFFFu, p1 = two ? (unsigned)ci[k1] & 0xFFFFFFu : p0;
+      const float2 a0 = Ai[k], b0 = Bi[k];
+      const float2 a1 = two ? Ai[k1] : a0, b1 = two ? Bi[k1] : b0;
+      const double o0 = gr[k], o1 = two ? gr[k1] : 0.0;
+      double t0 = g2grad_term<NST>(rc, tab, ns, p0, a0, b0);
+      double t1 = g2grad_term<NST>(rc, tab, ns, p1, a1, b1);
+      const double v0 = g2[I.start + k], v1 = two ? g2[I.start + k1] : 1.0;
+      t0 = v0 > 0.0 ? t0 / v0 : 0.0;
+      t1 = v1 > 0.0 ? t1 / v1 : 0.0;
+      gr[k] = o0 + t0;
+      if (two) gr[k1] = o1 + t1;
+    }
+  }
+}
+
+// The same gradient on branch-merged devices (coefficients stored without g2), with the
+// stage sums u, v computed once per state pair: a warp takes 32 consecutive sweep entries of a
+// row (one per lane; an entry is the run of pcnt >= 1 channels of one partner, from pcstart;
+// padding entries have none), whose channels form one contiguous range of the row.  The warp
+// walks that range with coalesced loads; each channel finds the lane of its entry by a
+// binary search over the lanes' first-channel offsets and takes u, v from it by shuffles.
+template <int NST, typename IDX>
+__global__ void __launch_bounds__(kBlock) k_g2grad_pairs(const Item *__restrict__ items, int nitems,
+                                                         const IDX *__restrict__ sidx,
+                                                         const long long *__restrict__ pcstart,
+                                                         const uint8_t *__restrict__ pcnt,
+                                                         const long long *__restrict__ rp_pad,
+                                                         const long long *__restrict__ rp_real,
+                                                         const float2 *__restrict__ A, const float2 *__restrict__ B,
+                                                         const float4 *__restrict__ tab, int ns,
+                                                         double *__restrict__ grad) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    const int r = I.row;
+    double *__restrict__ gr = grad + (rp_real[r] - rp_pad[r]);  // channel position -> unpadded index
+    float4 rc[NST];
 #pragma unroll
-      for (int j = 0; j < NST; ++j) {
-        const float4 q = __ldg(tab + 2 * ((long long)j * ns + p) + 1);
-        ff_mac_lazy(uh, ul, make_float2(rc[j].x, rc[j].y), q.z, q.w);
-        ff_mac_lazy(vh, vl, make_float2(rc[j].z, rc[j].w), q.x, q.y);
+    for (int j = 0; j < NST; ++j) rc[j] = tab[2 * (j * ns + r)];
+    for (int e0 = 0; e0 < I.len; e0 += 32) {
+      const long long q = I.start + e0 + lane;
+      const int m = e0 + lane < I.len ? (int)pcnt[q] : 0;
+      const unsigned any = __ballot_sync(0xFFFFFFFFu, m > 0);
+      if (!any) break;  // the rest of the row is padding
+      const long long cs = m ? pcstart[q] : 0;
+      float uh = 0.f, ul = 0.f, vh = 0.f, vl = 0.f;
+      if (m) {
+        const int p = (int)sidx[q];
+#pragma unroll
+        for (int j = 0; j < NST; ++j) {
+          const float4 t = __ldg(tab + 2 * (j * ns + p) + 1);
+          ff_mac_lazy(uh, ul, make_float2(rc[j].x, rc[j].y), t.z, t.w);
+          ff_mac_lazy(vh, vl, make_float2(rc[j].z, rc[j].w), t.x, t.y);
+        }
       }
-      const float2 pin = A[c], pout = ff_add(pin, B[c]);
-      float th = 0.f, tl = 0.f;
-      ff_mac(th, tl, pout, uh, ul);
-      ff_mac(th, tl, make_float2(-pin.x, -pin.y), vh, vl);
-      double t = ff_to_double(th, tl);
-      if (!KFORM) {
-        const double gv = g2[c];
-        if (!(gv > 0.0)) continue;
-        t /= gv;
+      // real entries precede the padding, so lane 0 holds the first channel of the chunk
+      const long long cb = __shfl_sync(0xFFFFFFFFu, cs, 0);
+      const int rs = m ? (int)(cs - cb) : 0x7FFFFFFF;  // first-channel offset (padding: never owns)
+      const int nch = __reduce_max_sync(0xFFFFFFFFu, m ? rs + m : 0);
+      for (int o0 = 0; o0 < nch; o0 += 32) {
+        const int o = o0 + lane;
+        int own = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int sc = __shfl_sync(0xFFFFFFFFu, rs, own + step);
+          if (sc <= o) own += step;
+        }
+        const float2 u = make_float2(__shfl_sync(0xFFFFFFFFu, uh, own), __shfl_sync(0xFFFFFFFFu, ul, own));
+        const float2 v = make_float2(__shfl_sync(0xFFFFFFFFu, vh, own), __shfl_sync(0xFFFFFFFFu, vl, own));
+        if (o < nch) {
+          const long long cpos = cb + o;
+          const float2 pin = A[cpos], pout = ff_add(pin, B[cpos]);
+          float th = 0.f, tl = 0.f;
+          ff_mac(th, tl, pout, u.x, u.y);
+          ff_mac(th, tl, make_float2(-pin.x, -pin.y), v.x, v.y);
+          gr[cpos] += widen_f32(th) + widen_f32(tl);
+        }
       }
-      gr[k] += t;
     }
   }
 }
@@ -1368,9 +1548,8 @@ __global__ void k_set_g2(const Item *__restrict__ items, int nitems, const long 
   }
 }
 
-// out = a x + b y (y may be null)
-__global__ void k_lincomb(int n, double a, const double *__restrict__ x, double b, const double *__restrict__ y,
-                          double *__restrict__ out) {
+// out = a x + b y (y may be null; out may be x or y)
+__global__ void k_lincomb(int n, double a, const double *x, double b, const double *y, double *out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = a * x[i] + (y ? b * y[i] : 0.0);
 }

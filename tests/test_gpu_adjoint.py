@@ -1,4 +1,4 @@
-"""GPU adjoint (NEXT-3): collision VJP, per-channel |g|^2 gradients and RK4 trajectory
+"""GPU adjoint: collision VJP, per-channel |g|^2 gradients and RK4 trajectory
 gradients, against the FP64 oracle's reverse mode and against central finite differences
 of the GPU forward map (h = 1e-6, random directions)."""
 import numpy as np
@@ -63,6 +63,53 @@ def test_rk4_step_adjoint_matches_oracle(pb):
     lam = T(eps)
     dev.rk4_vjp(T(f0), lam, 1.0)
     assert nrel(lam.cpu().numpy(), o.rk4_vjp(f0, 1.0, 1, eps)) <= 1e-11
+
+
+def _oracle_rk4_g2_grad(o, f, lam, dt, s, p, nu):
+    """dL/dg2 of one classic RK4 step from the oracle's collision, VJP and per-call |g|^2
+    gradient: stage states u_j, stage cotangents g_j by the chain rule, then the sum over the
+    four stages of g2_grad(u_j, g_j)."""
+    k1 = o.collision(f)
+    u2 = f + 0.5 * dt * k1
+    u3 = f + 0.5 * dt * o.collision(u2)
+    u4 = f + dt * o.collision(u3)
+    g4 = dt / 6.0 * lam
+    m4 = o.collision_vjp(u4, g4)
+    g3 = dt / 3.0 * lam + dt * m4
+    m3 = o.collision_vjp(u3, g3)
+    g2 = dt / 3.0 * lam + 0.5 * dt * m3
+    m2 = o.collision_vjp(u2, g2)
+    g1 = dt / 6.0 * lam + 0.5 * dt * m2
+    return sum(o.g2_grad(u, g, s, p, nu) for u, g in ((f, g1), (u2, g2), (u3, g3), (u4, g4)))
+
+
+@pytest.mark.parametrize("opts,tol", [({}, 1e-11), ({"dense_rows": 2}, 1e-11), ({"merge_branches": 2}, 1e-11),
+                                      ({"variant": "g32"}, 1e-5)],
+                         ids=["merged-tiles", "merged-indexed", "per-channel", "g32"])
+@pytest.mark.parametrize("model", [synth.make_window4(12), synth.make_tiny(4)], ids=["win12", "tiny4"])
+def test_rk4_step_g2_gradient_matches_oracle(pb, model, opts, tol):
+    """One RK4 step with grad_g2: the four stages' |g|^2 gradients accumulated in one pass over
+    the channels, against the oracle's stage-by-stage sum; dL/df against the oracle adjoint."""
+    import torch
+
+    ch = pb.Channels.from_model(model)
+    dev = pb.Device(ch, **opts)
+    o = oracle.Oracle(model)
+    rng = np.random.default_rng(7)
+    f = rng.uniform(0, 1, o.nstate)
+    lam0 = rng.normal(size=o.nstate)
+    dt = 2.0
+    gg2 = torch.zeros(dev.nchannels, dtype=torch.float64, device="cuda")
+    lam = T(lam0)
+    dev.rk4_vjp(T(f), lam, dt, grad_g2=gg2)
+    assert nrel(lam.cpu().numpy(), o.rk4_vjp(f, dt, 1, lam0)) <= tol
+    e = ch.export()
+    rows = np.repeat(np.arange(ch.nstate), np.diff(e["row_ptr"]))
+    pick = rng.choice(ch.nchannels, size=min(400, ch.nchannels), replace=False)
+    ref = _oracle_rk4_g2_grad(o, f, lam0, dt, rows[pick], e["col"][pick], e["nu"][pick])
+    err = nrel(gg2.cpu().numpy()[pick], ref)
+    print(f"{opts} rk4 g2-gradient normwise error {err:.2e}")
+    assert err <= tol
 
 
 def _carrier_energy_grad(pb, model, nsteps, every):

@@ -1,4 +1,4 @@
-"""Batched rt-BTE (NEXT-2): many instances of the batched workload in one launch per stage,
+"""Batched rt-BTE: many instances of the batched workload in one launch per stage,
 against the unbatched FP32 device and the FP64 oracle of each instance."""
 import numpy as np
 import pytest
