@@ -29,7 +29,7 @@ struct Layout {
   size_t rp, item_ptr, items, col, coefA, coefB, g2, wt, eps, kc, R, omega, tab, part, acc, y, yff, fstage, Fa, Fb,
       Fff, tau, invtau, red, scal, obs, g2lo, gstate, tab32, col16, rp_real, vjpG, g2tab, vecs, hcol, hg2, hA, hB, sc,
       entries, hitems, titems, t_item_ptr, err, citems, citem_ptr, cpart, ccoefA, ccoefB, sidx16, sidx32, pcstart,
-      pcnt, srp, tiles, tcoef, tpart, total;
+      pcnt, srp, gitems, tiles, tcoef, tpart, total;
 };
 
 struct Plan {
@@ -138,6 +138,17 @@ size_t coef_bytes(int variant) {
 
 // P: the channel plan; S: the sweep plan of the branch-merged variants (null: the sweep runs
 // over channels and the channel-only regions are empty).
+void plan_items(const std::vector<int64_t> &rp, int item_ch, std::vector<Item> &items, std::vector<int32_t> &ptr);
+
+// work items of the branch-merged |g|^2 gradient: the sweep rows in pieces of at most one warp
+// width of entries (plan_items never exceeds item_ch)
+int64_t grad_chunks(const std::vector<int64_t> &rp) {
+  std::vector<Item> it;
+  std::vector<int32_t> ptr;
+  plan_items(rp, dev::kWarpChunk, it, ptr);
+  return (int64_t)it.size();
+}
+
 // symmetric tiles of the complete-row FF sweep: nb blocks of kTile states, nt = nb(nb+1)/2 tiles
 struct TileDims {
   int nb = 0, nt = 0, nsp = 0;
@@ -179,6 +190,7 @@ Layout make_layout(const pb_channels *ch, const Plan &P, const Plan *S, int vari
   L.pcstart = take(S ? sizeof(int64_t) * nsw : 0);
   L.pcnt = take(S ? nsw : 0);
   L.srp = take(S ? sizeof(int64_t) * (ns + 1) : 0);
+  L.gitems = take(S ? sizeof(Item) * (size_t)grad_chunks(S->rp) : 0);
   const TileDims td = tile_dims((int64_t)ns);
   L.tiles = take(sym ? sizeof(int2) * td.nt : 0);
   L.tcoef = take(sym ? sizeof(float4) * (size_t)td.nt * dev::kTile * dev::kTile : 0);
@@ -345,6 +357,8 @@ struct pb_dev {
   // transport sweeps take each entry's partner from its position and stream no index
   bool dense = false;
   int64_t *srp = nullptr;         // first sweep entry of every row [ns+1]
+  Item *gitems = nullptr;         // the sweep rows in pieces of <= 32 entries (|g|^2 gradient)
+  int ngitems = 0;
   // symmetric tiles (complete rows, FF): the collision and rate sweeps stream the upper block
   // triangle of the pair matrix once and add each tile to its rows and to its columns
   bool sym = false;
@@ -749,6 +763,7 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
     d->pcstart = (int64_t *)(A + L.pcstart);
     d->pcnt = (uint8_t *)(A + L.pcnt);
     d->srp = (int64_t *)(A + L.srp);
+    d->gitems = (Item *)(A + L.gitems);
     if (d->sym) {
       d->tiles = (int2 *)(A + L.tiles);
       d->tcoef = (float4 *)(A + L.tcoef);
@@ -916,6 +931,13 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
         UP(d->pcstart, cst.data(), sizeof(int64_t) * S.nchp);
         UP(d->pcnt, cn.data(), S.nchp);
         UP(d->srp, S.rp.data(), sizeof(int64_t) * (d->ns + 1));
+        {
+          std::vector<Item> gi;
+          std::vector<int32_t> gptr;
+          plan_items(S.rp, dev::kWarpChunk, gi, gptr);
+          d->ngitems = (int)gi.size();
+          UP(d->gitems, gi.data(), sizeof(Item) * gi.size());
+        }
         if (d->sym) {
           std::vector<int2> tl;
           for (int I = 0; I < d->td.nb; ++I)
@@ -1615,11 +1637,12 @@ int g2grad_launch(pb_dev *d, double *grad_g2, cudaStream_t st) {
   }
   const float2 *A = (const float2 *)d->ccoefA, *B = (const float2 *)d->ccoefB;
   if (d->merged) {
-    // per state pair (the channel coefficients are stored without g2)
-    const int gg = d->stream_grid(8), n = (int)d->nitems;
+    // per state pair (the channel coefficients are stored without g2), on a persistent grid
+    const int n = d->ngitems;
+    const int gg = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, (int64_t)d->sm_count * dev::kGradCtas));
     const long long *pcs = (const long long *)d->pcstart;
-    if (d->sidx16) dev::k_g2grad_pairs<NST, uint16_t><<<gg, dev::kBlock, 0, st>>>(d->items, n, d->sidx16, pcs, d->pcnt, rp, rr, A, B, d->g2tab, ns, grad_g2);
-    else           dev::k_g2grad_pairs<NST, uint32_t><<<gg, dev::kBlock, 0, st>>>(d->items, n, d->sidx32, pcs, d->pcnt, rp, rr, A, B, d->g2tab, ns, grad_g2);
+    if (d->sidx16) dev::k_g2grad_pairs<NST, uint16_t><<<gg, dev::kBlock, 0, st>>>(d->gitems, n, d->sidx16, pcs, d->pcnt, rp, rr, A, B, d->g2tab, ns, grad_g2);
+    else           dev::k_g2grad_pairs<NST, uint32_t><<<gg, dev::kBlock, 0, st>>>(d->gitems, n, d->sidx32, pcs, d->pcnt, rp, rr, A, B, d->g2tab, ns, grad_g2);
     PB_LAUNCHED("k_g2grad_pairs");
     return PB_OK;
   }

@@ -1462,53 +1462,69 @@ __global__ void __launch_bounds__(kBlock) k_g2grad(const Item *__restrict__ item
 }
 
 // The same gradient on branch-merged devices (coefficients stored without g2), with the
-// stage sums u, v computed once per state pair: a warp takes 32 consecutive sweep entries of a
-// row (one per lane; an entry is the run of pcnt >= 1 channels of one partner, from pcstart;
-// padding entries have none), whose channels form one contiguous range of the row.  The warp
-// walks that range with coalesced loads; each channel finds the lane of its entry by a
-// binary search over the lanes' first-channel offsets and takes u, v from it by shuffles.
+// stage sums u, v computed once per state pair.  A work item is a piece of at most 32
+// consecutive sweep entries of a row, one per lane (an entry is the run of pcnt >= 1 channels of
+// one partner, from pcstart; padding entries have none), whose channels form one contiguous
+// range of the row.  The warp walks that range with coalesced loads, kUnr trips' loads issued
+// together; each channel finds the lane of its entry by a binary search over the lanes'
+// first-channel offsets and takes u, v from it by shuffles.
+constexpr int kWarpChunk = 32;
+constexpr int kGradCtas = 3;  // resident CTAs per SM of k_g2grad_pairs (its persistent grid)
 template <int NST, typename IDX>
-__global__ void __launch_bounds__(kBlock) k_g2grad_pairs(const Item *__restrict__ items, int nitems,
-                                                         const IDX *__restrict__ sidx,
-                                                         const long long *__restrict__ pcstart,
-                                                         const uint8_t *__restrict__ pcnt,
-                                                         const long long *__restrict__ rp_pad,
-                                                         const long long *__restrict__ rp_real,
-                                                         const float2 *__restrict__ A, const float2 *__restrict__ B,
-                                                         const float4 *__restrict__ tab, int ns,
-                                                         double *__restrict__ grad) {
+__global__ void __launch_bounds__(kBlock, kGradCtas) k_g2grad_pairs(const Item *__restrict__ items, int nitems,
+                                                                    const IDX *__restrict__ sidx,
+                                                                    const long long *__restrict__ pcstart,
+                                                                    const uint8_t *__restrict__ pcnt,
+                                                                    const long long *__restrict__ rp_pad,
+                                                                    const long long *__restrict__ rp_real,
+                                                                    const float2 *__restrict__ A,
+                                                                    const float2 *__restrict__ B,
+                                                                    const float4 *__restrict__ tab, int ns,
+                                                                    double *__restrict__ grad) {
+  constexpr int kUnr = 3;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int it = warp; it < nitems; it += nwarps) {
     const Item I = items[it];
     const int r = I.row;
+    const long long q = I.start + lane;
+    const int m = lane < I.len ? (int)pcnt[q] : 0;
+    if (!__any_sync(0xFFFFFFFFu, m > 0)) continue;  // padding only
     double *__restrict__ gr = grad + (rp_real[r] - rp_pad[r]);  // channel position -> unpadded index
-    float4 rc[NST];
+    const long long cs = m ? pcstart[q] : 0;
+    float uh = 0.f, ul = 0.f, vh = 0.f, vl = 0.f;
+    if (m) {
+      const int p = (int)sidx[q];
 #pragma unroll
-    for (int j = 0; j < NST; ++j) rc[j] = tab[2 * (j * ns + r)];
-    for (int e0 = 0; e0 < I.len; e0 += 32) {
-      const long long q = I.start + e0 + lane;
-      const int m = e0 + lane < I.len ? (int)pcnt[q] : 0;
-      const unsigned any = __ballot_sync(0xFFFFFFFFu, m > 0);
-      if (!any) break;  // the rest of the row is padding
-      const long long cs = m ? pcstart[q] : 0;
-      float uh = 0.f, ul = 0.f, vh = 0.f, vl = 0.f;
-      if (m) {
-        const int p = (int)sidx[q];
+      for (int j = 0; j < NST; ++j) {
+        const float4 rc = tab[2 * (j * ns + r)];
+        const float4 t = __ldg(tab + 2 * (j * ns + p) + 1);
+        ff_mac_lazy(uh, ul, make_float2(rc.x, rc.y), t.z, t.w);
+        ff_mac_lazy(vh, vl, make_float2(rc.z, rc.w), t.x, t.y);
+      }
+    }
+    // real entries precede the padding, so lane 0 holds the first channel of the piece
+    const long long cb = __shfl_sync(0xFFFFFFFFu, cs, 0);
+    const int rs = m ? (int)(cs - cb) : 0x7FFFFFFF;  // first-channel offset (padding: never owns)
+    const int nch = __reduce_max_sync(0xFFFFFFFFu, m ? rs + m : 0);
+    const float2 *__restrict__ Ab = A + cb, *__restrict__ Bb = B + cb;
+    double *__restrict__ gb = gr + cb;
+    for (int o0 = 0; o0 < nch; o0 += 32 * kUnr) {
+      float2 pin[kUnr], dd[kUnr];
+      double old[kUnr];
 #pragma unroll
-        for (int j = 0; j < NST; ++j) {
-          const float4 t = __ldg(tab + 2 * (j * ns + p) + 1);
-          ff_mac_lazy(uh, ul, make_float2(rc[j].x, rc[j].y), t.z, t.w);
-          ff_mac_lazy(vh, vl, make_float2(rc[j].z, rc[j].w), t.x, t.y);
+      for (int k = 0; k < kUnr; ++k) {
+        const int o = o0 + 32 * k + lane;
+        if (o < nch) {
+          pin[k] = Ab[o];
+          dd[k] = Bb[o];
+          old[k] = gb[o];
         }
       }
-      // real entries precede the padding, so lane 0 holds the first channel of the chunk
-      const long long cb = __shfl_sync(0xFFFFFFFFu, cs, 0);
-      const int rs = m ? (int)(cs - cb) : 0x7FFFFFFF;  // first-channel offset (padding: never owns)
-      const int nch = __reduce_max_sync(0xFFFFFFFFu, m ? rs + m : 0);
-      for (int o0 = 0; o0 < nch; o0 += 32) {
-        const int o = o0 + lane;
+#pragma unroll
+      for (int k = 0; k < kUnr; ++k) {
+        const int o = o0 + 32 * k + lane;
         int own = 0;
 #pragma unroll
         for (int step = 16; step > 0; step >>= 1) {
@@ -1518,12 +1534,11 @@ __global__ void __launch_bounds__(kBlock) k_g2grad_pairs(const Item *__restrict_
         const float2 u = make_float2(__shfl_sync(0xFFFFFFFFu, uh, own), __shfl_sync(0xFFFFFFFFu, ul, own));
         const float2 v = make_float2(__shfl_sync(0xFFFFFFFFu, vh, own), __shfl_sync(0xFFFFFFFFu, vl, own));
         if (o < nch) {
-          const long long cpos = cb + o;
-          const float2 pin = A[cpos], pout = ff_add(pin, B[cpos]);
+          const float2 pout = ff_add(pin[k], dd[k]);
           float th = 0.f, tl = 0.f;
           ff_mac(th, tl, pout, u.x, u.y);
-          ff_mac(th, tl, make_float2(-pin.x, -pin.y), v.x, v.y);
-          gr[cpos] += widen_f32(th) + widen_f32(tl);
+          ff_mac(th, tl, make_float2(-pin[k].x, -pin[k].y), v.x, v.y);
+          gb[o] = old[k] + (widen_f32(th) + widen_f32(tl));
         }
       }
     }
