@@ -180,6 +180,11 @@ typedef struct pb_dev_opts {
                                 each tile to its rows and, through the reverse channels (P_in(p,s) =
                                 P_out(s,p)), to its columns: about 8 bytes per state pair; 2 always stream
                                 the index */
+  int32_t tile_sweep;        /* the symmetric tile sweep (dense_rows 3): 0 automatic (= 2); 1 each thread
+                                loads its 4 x 4 entries of a tile from global memory (3 CTAs per SM);
+                                2 one persistent CTA per SM with 256 threads keeps three tiles in flight in
+                                shared memory through TMA bulk copies (cp.async.bulk, mbarrier-counted),
+                                its bounded waits reporting through pb_dev_check */
 } pb_dev_opts;
 
 typedef struct pb_dev pb_dev; /* opaque host handle describing device-resident data */

@@ -56,7 +56,8 @@ class _DevOpts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("item_channels", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("transport", ctypes.c_int32), ("transport_gather", ctypes.c_int32),
                 ("transport_ctas", ctypes.c_int32), ("channel_per_lane", ctypes.c_int32),
-                ("stream_mode", ctypes.c_int32), ("merge_branches", ctypes.c_int32), ("dense_rows", ctypes.c_int32)]
+                ("stream_mode", ctypes.c_int32), ("merge_branches", ctypes.c_int32), ("dense_rows", ctypes.c_int32),
+                ("tile_sweep", ctypes.c_int32)]
 
 
 class _DevInfo(ctypes.Structure):
@@ -276,7 +277,7 @@ class Device:
     def __init__(self, channels: Channels, variant: str = "ff", item_channels: int = 0, ctas_per_sm: int = 0,
                  transport: bool = False, transport_gather: int = 0, transport_ctas: int = 0,
                  channel_per_lane: int = 0, stream_mode: int = 0, merge_branches: int = 0, dense_rows: int = 0,
-                 stream=None):
+                 tile_sweep: int = 0, stream=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -287,7 +288,7 @@ class Device:
         self.merged = variant in ("ff", "f64") and int(merge_branches) != 2
         o = _DevOpts(VARIANTS[variant], int(item_channels), int(ctas_per_sm), 1 if transport else 0,
                      int(transport_gather), int(transport_ctas), int(channel_per_lane), int(stream_mode),
-                     int(merge_branches), int(dense_rows))
+                     int(merge_branches), int(dense_rows), int(tile_sweep))
         nbytes = ctypes.c_size_t(0)
         _check(lib().pb_dev_arena_bytes(channels._h, ctypes.byref(o), ctypes.byref(nbytes)))
         self.arena = torch.empty(int(nbytes.value), dtype=torch.uint8, device="cuda")

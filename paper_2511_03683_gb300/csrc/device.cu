@@ -362,6 +362,7 @@ struct pb_dev {
   // symmetric tiles (complete rows, FF): the collision and rate sweeps stream the upper block
   // triangle of the pair matrix once and add each tile to its rows and to its columns
   bool sym = false;
+  int sym_nt = 0;  // threads of the bulk-copy tile sweep's CTA (0: the global-load tile sweep)
   TileDims td;
   int2 *tiles = nullptr;
   float4 *tcoef = nullptr;
@@ -450,6 +451,8 @@ int resolve_opts(const pb_channels *ch, const pb_dev_opts *opts, int sm_count, p
     return set_error(PB_EINVAL, "pb_dev: variant %d is not available in this build", d.variant);
   if (d.merge_branches < 0 || d.merge_branches > 2) return set_error(PB_EINVAL, "pb_dev: merge_branches must be 0..2");
   if (d.dense_rows < 0 || d.dense_rows > 3) return set_error(PB_EINVAL, "pb_dev: dense_rows must be 0..3");
+  if (d.tile_sweep < 0 || d.tile_sweep > 2) return set_error(PB_EINVAL, "pb_dev: tile_sweep must be 0..2");
+  if (d.tile_sweep == 0) d.tile_sweep = 2;
   // measured best on GB300 at 40^3: 3 CTAs per SM for one entry per channel, 4 for the
   // branch-merged sweep (whose stream is six times shorter)
   const bool merged = (d.variant == PB_VARIANT_FF || d.variant == PB_VARIANT_F64) && d.merge_branches != 2;
@@ -697,6 +700,7 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->transport = o.transport != 0;
   d->nfin_blocks = (int)((d->ns + kFinBlock - 1) / kFinBlock);
   d->sym = sym_for(o, merged, complete);
+  d->sym_nt = d->sym && o.tile_sweep == 2 ? dev::kSymThreads : 0;
   d->td = tile_dims(d->ns);
   d->L = make_layout(ch, P, merged ? &S : nullptr, o.variant, d->transport, d->nfin_blocks, d->sym);
   if (arena_bytes < d->L.total) {
@@ -990,6 +994,12 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   }
   if (d->bulk)
     cudaFuncSetAttribute(dev::k_stream_ff_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->bulk_smem);
+  if (d->sym_nt) {
+    if (dev::kSymBulkSmem > (size_t)smem_optin)
+      d->sym_nt = 0;  // the global-load tile sweep needs no opt-in shared memory
+    else
+      cudaFuncSetAttribute(dev::k_stream_sym_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dev::kSymBulkSmem);
+  }
   if (d->smem_f > 48 * 1024) {
     set_stream_smem<uint32_t>((int)d->smem_f);
     set_stream_smem<uint16_t>((int)d->smem_f);
@@ -1105,8 +1115,14 @@ int launch_stream_t(pb_dev *d, int mode, const double *fd, const float2 *fff, co
                                                                  d->bulk_cap, part, d->err);
   } else if (d->variant == PB_VARIANT_FF && d->sym && part == d->part) {
     // symmetric tiles; the rate mode needs the same (A, B) partials
-    const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(d->td.nt, (int64_t)d->sm_count * 3));
-    dev::k_stream_sym<<<gs, 256, 0, st>>>(d->tiles, d->td.nt, d->tcoef, fff, ns, d->td.nb, d->tpart);
+    if (d->sym_nt && fff == d->yff) {  // the bulk copies read f from this padded arena buffer
+      const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(d->td.nt, (int64_t)d->sm_count));
+      dev::k_stream_sym_bulk<<<gs, dev::kSymThreads, dev::kSymBulkSmem, st>>>(d->tiles, d->td.nt, d->tcoef, fff, ns,
+                                                                              d->td.nb, d->tpart, d->err);
+    } else {
+      const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(d->td.nt, (int64_t)d->sm_count * 3));
+      dev::k_stream_sym<<<gs, 256, 0, st>>>(d->tiles, d->td.nt, d->tcoef, fff, ns, d->td.nb, d->tpart);
+    }
   } else if (d->variant == PB_VARIANT_FF) {
     const float4 *A4 = (const float4 *)d->coefA, *B4 = (const float4 *)d->coefB;
     const long long *srp = (const long long *)d->srp;

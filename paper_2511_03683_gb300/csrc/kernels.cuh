@@ -758,6 +758,28 @@ __device__ __forceinline__ void ff_mac_lazy(float &h, float &l, float2 x, float 
   h = s;
 }
 
+// (h, l) = x * (ah, al): the first term of a lazily accumulated float-float sum (no addition)
+__device__ __forceinline__ void ff_prod(float &h, float &l, float2 x, float ah, float al) {
+  h = __fmul_rn(x.x, ah);
+  float e = __fmaf_rn(x.x, ah, -h);
+  e = __fmaf_rn(x.x, al, e);
+  l = __fmaf_rn(x.y, ah, e);
+}
+
+// a + b without the final renormalisation (the high part is the rounded sum of the high parts,
+// the low part carries its exact error plus the low parts); renormalise with ff_norm
+__device__ __forceinline__ float2 ff_add_lazy(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float bb = __fsub_rn(s, a.x);
+  const float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+  return make_float2(s, __fadd_rn(err, __fadd_rn(a.y, b.y)));
+}
+
+__device__ __forceinline__ float2 ff_norm(float2 a) {
+  const float h = __fadd_rn(a.x, a.y);
+  return make_float2(h, __fsub_rn(a.y, __fsub_rn(h, a.x)));
+}
+
 template <bool LAZY, bool GLOBAL>
 __device__ __forceinline__ void tr_mac3(float (&acc)[6], const float2 *Fp, float2 w) {
   const float2 fx = GLOBAL ? __ldg(Fp) : Fp[0], fy = GLOBAL ? __ldg(Fp + 1) : Fp[1], fz = GLOBAL ? __ldg(Fp + 2) : Fp[2];
@@ -1754,6 +1776,208 @@ __global__ void __launch_bounds__(256, 3) k_stream_sym(const int2 *__restrict__ 
       tp[(long long)st * nb + blk] = make_float4(A.x, A.y, C.x, C.y);
     }
     __syncthreads();
+  }
+}
+
+// The same tile sweep with the tiles staged through shared memory by bulk copies
+// (cp.async.bulk, completion counted in bytes on an mbarrier): one persistent 256-thread CTA per
+// SM; thread 0 keeps kSymStages tiles in flight (each with the float-float f of its row and
+// column blocks) while the CTA adds the staged tile.  Thread (ti, tj) takes rows 4ti .. 4ti+3
+// and columns tj, tj+16, tj+32, tj+48, so a quarter-warp reads 128 contiguous bytes of a row
+// (no bank conflicts).  Row partials are reduced inside the warp by a float-float reduce-scatter
+// over the 16 lanes of a row; column partials by one shuffle level into a per-warp table that
+// the next iteration combines (double-buffered), so each tile costs one CTA barrier.  Every
+// wait is bounded: on a give-up the kernel records it in *err, waits (bounded) for its own
+// copies and returns.
+constexpr int kSymStages = 3;
+constexpr int kSymThreads = 256;
+constexpr unsigned kTileBytes = kTile * kTile * sizeof(float4);
+constexpr unsigned kSymStageBytes = kTileBytes + 2 * kTile * sizeof(float2);
+constexpr size_t kSymColBytes = (size_t)(kSymThreads / 32) * 2 * kTile * sizeof(float2);  // one column table
+constexpr size_t kSymBulkSmem = (size_t)kSymStages * kSymStageBytes + 64 + 2 * kSymColBytes;
+
+// reduce-scatter of NV float-float values over the 16 lanes sharing lane bits 0..3: at the end
+// v[0] holds, on every lane, the total of value index idx(lane) = bits 3, 2, .. of the lane (the
+// first log2 NV of them, most significant first), not renormalised
+template <int NV>
+__device__ __forceinline__ void ff_reduce_scatter16(float2 (&v)[NV], int lane) {
+  int n = NV;
+#pragma unroll
+  for (int mask = 8; mask > 0; mask >>= 1) {
+    if (n > 1) {
+      const bool up = lane & mask;
+      const int h = n >> 1;
+#pragma unroll
+      for (int k = 0; k < NV / 2; ++k) {
+        if (k < h) {
+          const float2 send = up ? v[k] : v[k + h], keep = up ? v[k + h] : v[k];
+          const float2 recv = make_float2(__shfl_xor_sync(0xFFFFFFFFu, send.x, mask),
+                                          __shfl_xor_sync(0xFFFFFFFFu, send.y, mask));
+          v[k] = ff_add_lazy(keep, recv);
+        }
+      }
+      n = h;
+    } else {
+      v[0] = ff_add_lazy(v[0], make_float2(__shfl_xor_sync(0xFFFFFFFFu, v[0].x, mask),
+                                           __shfl_xor_sync(0xFFFFFFFFu, v[0].y, mask)));
+    }
+  }
+}
+
+// the column partials of a finished off-diagonal tile: one (column, A | C) value per lane pair
+// (lanes l and l ^ 16 take warps 0-3 and 4-7), renormalised, into tp
+__device__ __forceinline__ void sym_columns_out(const float2 *__restrict__ colred, int2 IJ, int nb, int lane, int wid,
+                                                float4 *__restrict__ tp) {
+  constexpr int NW = kSymThreads / 32, WG = NW / 2;
+  const int g = lane >> 4;
+  const int q = (lane & 15) + 16 * wid;  // 0 .. 127
+  const int col = q & (kTile - 1), comp = q >> 6;
+  float2 acc = colred[((g * WG) * 2 + comp) * kTile + col];
+#pragma unroll
+  for (int w = 1; w < WG; ++w) acc = ff_add_lazy(acc, colred[((g * WG + w) * 2 + comp) * kTile + col]);
+  acc = ff_add_lazy(acc, make_float2(__shfl_xor_sync(0xFFFFFFFFu, acc.x, 16), __shfl_xor_sync(0xFFFFFFFFu, acc.y, 16)));
+  if (g == 0) ((float2 *)tp)[2 * ((long long)(IJ.y * kTile + col) * nb + IJ.x) + comp] = ff_norm(acc);
+}
+
+__global__ void __launch_bounds__(kSymThreads, 1) k_stream_sym_bulk(const int2 *__restrict__ tiles, int nt,
+                                                                     const float4 *__restrict__ tc,
+                                                                     const float2 *__restrict__ fg, int ns, int nb,
+                                                                     float4 *__restrict__ tp, int *__restrict__ err) {
+  constexpr int R = 4, NV = 2 * R;
+  extern __shared__ __align__(128) unsigned char ssm[];
+  unsigned long long *bars = (unsigned long long *)(ssm + kSymStages * kSymStageBytes);
+  int2 *stile = (int2 *)(bars + kSymStages);  // the tile held by each stage
+  float2 *colred0 = (float2 *)(ssm + kSymStages * kSymStageBytes + 64);  // 2 x [8 warps][A | C][64 columns]
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, tj = tid & 15, ti = tid >> 4;
+  const int G = (int)gridDim.x;
+  const int nloc = (int)blockIdx.x < nt ? (nt - 1 - (int)blockIdx.x) / G + 1 : 0;
+  // the f slices of every stage start as zeros (a copy of a last, partial block leaves the rest)
+  for (int i = tid; i < kSymStages * 2 * kTile; i += kSymThreads) {
+    float2 *fz = (float2 *)(ssm + (i / (2 * kTile)) * kSymStageBytes + kTileBytes);
+    fz[i % (2 * kTile)] = make_float2(0.f, 0.f);
+  }
+  if (tid == 0) {
+    for (int k = 0; k < kSymStages; ++k) mbar_init(bars + k, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_proxy_async();  // the zeroed f slices before any bulk write to them
+  __syncthreads();
+  int issued = 0;
+  auto issue = [&](int k, int2 IJ) {
+    const int s = k % kSymStages;
+    const int t = (int)blockIdx.x + k * G;
+    stile[s] = IJ;
+    unsigned char *buf = ssm + (size_t)s * kSymStageBytes;
+    const int nr = min(kTile, ns - IJ.x * kTile), nc = min(kTile, ns - IJ.y * kTile);
+    const unsigned br = (unsigned)(nr * sizeof(float2) + 15) / 16 * 16, bc = (unsigned)(nc * sizeof(float2) + 15) / 16 * 16;
+    mbar_expect_tx(bars + s, kTileBytes + br + bc);
+    const unsigned char *src = (const unsigned char *)(tc + (size_t)t * kTile * kTile);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) bulk_g2s(buf + q * (kTileBytes / 4), src + q * (kTileBytes / 4), kTileBytes / 4, bars + s);
+    bulk_g2s(buf + kTileBytes, fg + (size_t)IJ.x * kTile, br, bars + s);
+    bulk_g2s(buf + kTileBytes + kTile * sizeof(float2), fg + (size_t)IJ.y * kTile, bc, bars + s);
+  };
+  if (tid == 0)
+    for (; issued < kSymStages && issued < nloc; ++issued) issue(issued, tiles[(int)blockIdx.x + issued * G]);
+  int2 nextIJ = make_int2(0, 0);  // thread 0: descriptor of the next tile to issue, loaded a tile ahead
+  if (tid == 0 && issued < nloc) nextIJ = tiles[(int)blockIdx.x + issued * G];
+  int2 prevIJ = make_int2(0, 0);  // the previous tile (its columns are combined in this iteration)
+  bool ok = true;
+  for (int k = 0; k <= nloc; ++k) {
+    // thread 0 waits on the mbarrier of tile k (acquire); the CTA barrier publishes the stage
+    // to all, and marks the end of tile k-1 (its stage is free, its column table complete)
+    const bool have = k < nloc;
+    if (!__syncthreads_and(tid == 0 && have ? mbar_wait(bars + k % kSymStages, (unsigned)((k / kSymStages) & 1)) : true)) {
+      ok = false;
+      break;
+    }
+    if (tid == 0 && k >= 1 && issued < nloc) {
+      fence_proxy_async();  // order the generic reads of tile k-1's stage before its refill
+      issue(issued, nextIJ);
+      ++issued;
+      if (issued < nloc) nextIJ = tiles[(int)blockIdx.x + issued * G];
+    }
+    if (k >= 1 && prevIJ.x != prevIJ.y) sym_columns_out(colred0 + ((k - 1) & 1) * (kSymColBytes / sizeof(float2)), prevIJ, nb, lane, wid, tp);
+    if (!have) break;
+    const int s = k % kSymStages;
+    const int2 IJ = stile[s];
+    prevIJ = IJ;
+    const bool diag = IJ.x == IJ.y;
+    const float4 *__restrict__ T = (const float4 *)(ssm + (size_t)s * kSymStageBytes);
+    const float2 *__restrict__ fr = (const float2 *)(ssm + (size_t)s * kSymStageBytes + kTileBytes);
+    const float2 *__restrict__ fc = fr + kTile;
+    float2 fcol[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) fcol[j] = fc[tj + 16 * j];
+    // each accumulator's first term is a plain product (no zeroing, no addition)
+    float rA[R][2], rC[R][2], cA[4][2], cC[4][2];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int row = ti * R + i;
+      const float2 fs = fr[row];
+      float4 e[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) e[j] = T[row * kTile + tj + 16 * j];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (j == 0) {
+          ff_prod(rA[i][0], rA[i][1], fcol[j], e[j].x, e[j].y);
+          ff_prod(rC[i][0], rC[i][1], fcol[j], e[j].z, e[j].w);
+        } else {
+          ff_mac_lazy(rA[i][0], rA[i][1], fcol[j], e[j].x, e[j].y);
+          ff_mac_lazy(rC[i][0], rC[i][1], fcol[j], e[j].z, e[j].w);
+        }
+        if (!diag) {
+          if (i == 0) {
+            ff_prod(cA[j][0], cA[j][1], fs, e[j].z, e[j].w);
+            ff_prod(cC[j][0], cC[j][1], fs, e[j].x, e[j].y);
+          } else {
+            ff_mac_lazy(cA[j][0], cA[j][1], fs, e[j].z, e[j].w);
+            ff_mac_lazy(cC[j][0], cC[j][1], fs, e[j].x, e[j].y);
+          }
+        }
+      }
+    }
+    // rows: the 16 lanes of a half-warp share them; lane tj ends with value idx (row, A | C)
+    {
+      float2 v[NV];
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        v[2 * i] = make_float2(rA[i][0], rA[i][1]);
+        v[2 * i + 1] = make_float2(rC[i][0], rC[i][1]);
+      }
+      ff_reduce_scatter16<NV>(v, lane);
+      const int idx = ((tj >> 3) & 1) * 4 + ((tj >> 2) & 1) * 2 + ((tj >> 1) & 1);
+      if ((tj & 1) == 0) {  // lanes tj and tj ^ 1 hold the same total
+        const int row = IJ.x * kTile + ti * R + (idx >> 1);
+        ((float2 *)tp)[2 * ((long long)row * nb + IJ.y) + (idx & 1)] = ff_norm(v[0]);
+      }
+    }
+    if (!diag) {
+      // columns: lanes tj and tj + 16 share them (one level), then the warps (next iteration)
+      float2 *colred = colred0 + (k & 1) * (kSymColBytes / sizeof(float2));
+      const bool up = lane & 16;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int jk = m >> 1, jo = jk + 2;  // kept / sent column slot
+        const float2 a = (m & 1) ? make_float2(cC[jk][0], cC[jk][1]) : make_float2(cA[jk][0], cA[jk][1]);
+        const float2 c = (m & 1) ? make_float2(cC[jo][0], cC[jo][1]) : make_float2(cA[jo][0], cA[jo][1]);
+        const float2 send = up ? a : c, keep = up ? c : a;
+        const float2 w = ff_add_lazy(keep, make_float2(__shfl_xor_sync(0xFFFFFFFFu, send.x, 16),
+                                                       __shfl_xor_sync(0xFFFFFFFFu, send.y, 16)));
+        const int col = tj + 16 * ((up ? 2 : 0) + jk);
+        colred[(wid * 2 + (m & 1)) * kTile + col] = w;
+      }
+    }
+  }
+  if (!ok) {
+    *err = 2;
+    if (tid == 0) {  // drain: wait (bounded) for every copy this CTA issued
+      for (int k = 0; k < kSymStages; ++k) {
+        const int uses = issued / kSymStages + (k < issued % kSymStages ? 1 : 0);
+        if (uses > 0) mbar_wait(bars + k, (unsigned)((uses - 1) & 1));
+      }
+    }
   }
 }
 

@@ -53,12 +53,22 @@ def T(x):
     return torch.tensor(np.ascontiguousarray(x, dtype=np.float64), device="cuda")
 
 
+def _three_band_window():
+    w = np.array([[e - 1.0, e + 0.3] for e in (0.0, 0.2, 1.1, 1.3)])
+    w[3] = [-10.0, -9.0]
+    return w
+
+
 SMALL = {
     "tiny4": lambda: synth.make_tiny(4),
     "tiny5": lambda: synth.make_tiny(5),
     "win12": lambda: synth.make_window4(12),
     "win16": lambda: synth.make_window4(16),
     "tiny8": lambda: synth.make_config("tiny"),
+    # three bands (the fourth band's window is empty): 81 and 99 states, so the last
+    # 64-state block is ragged with an odd number of states (17, 35)
+    "odd81": lambda: synth.make_window4(11, win=_three_band_window()),
+    "odd99": lambda: synth.make_window4(13, win=_three_band_window()),
 }
 VARIANTS = ["ff", "f64", "literal"]
 
@@ -202,6 +212,31 @@ def test_branch_merged_and_per_channel_sweeps(pb, name, variant, merge, dense):
         assert np.abs(other_rows.collision(T(f)).cpu().numpy() - I).max() <= 1e-14 * ab.max()
         if dense != 2:  # tiles and positional partners stream fewer bytes than the index form
             assert dev.bytes_per_channel < other_rows.bytes_per_channel
+
+
+@pytest.mark.parametrize("tile_sweep", [1, 2], ids=["global-loads", "bulk-copies"])
+@pytest.mark.parametrize("name", ["odd81", "odd99", "win16", "tiny8"])
+def test_tile_sweep_shapes(pb, name, tile_sweep):
+    """The symmetric tile sweep with per-thread global loads and with the TMA bulk-copy ring:
+    collision, rates and RK4 against the oracle on complete rows whose
+    last 64-state block is ragged (odd for odd81 / odd99); the shapes agree to rounding."""
+    m = SMALL[name]()
+    o = oracle.Oracle(m)
+    ch = pb.Channels.from_model(m)
+    dev = pb.Device(ch, tile_sweep=tile_sweep)
+    rng = np.random.default_rng(33)
+    f = rng.uniform(0, 1, o.nstate)
+    ref, ab = o.collision(f, with_abs=True)
+    I = dev.collision(T(f)).cpu().numpy()
+    check_I(I, ref, ab)
+    assert nrel(dev.rates(T(f)).cpu().numpy(), o.rates(f)) <= TOL
+    f0 = o.window_values(m.f_hot())
+    ft = T(f0)
+    dev.rk4(ft, 1.0, 3)
+    assert nrel(ft.cpu().numpy(), o.rk4(f0, 1.0, 3)) <= TOL
+    dev.check()
+    other = pb.Device(ch, tile_sweep=1 if tile_sweep != 1 else 2)
+    assert np.abs(other.collision(T(f)).cpu().numpy() - I).max() <= 1e-14 * ab.max()
 
 
 def test_time_sweep_measures_without_changing_results(pb):
@@ -396,6 +431,22 @@ def test_full_size_bulk_copy_sweep(pb, big):
     ref, ab = o.collision(f, rows=rows, with_abs=True)
     check_I(bulk.collision(T(f)).cpu().numpy()[rows], ref, ab)
     bulk.check()
+
+
+def test_full_size_tile_sweep_shapes(pb, big):
+    """The global-load tile sweep at 40^3 against the full oracle and the default bulk-copy
+    ring (2850 tiles, about 19 per CTA of the persistent ring, so every stage is refilled many
+    times); no bounded wait gave up."""
+    tile_sweep = 1
+    m, o, dev = big
+    alt = pb.Device(dev.channels, variant="ff", tile_sweep=tile_sweep)
+    f = o.window_values(m.f_hot())
+    ref, ab = o.collision(f, with_abs=True)
+    I = alt.collision(T(f)).cpu().numpy()
+    check_I(I, ref, ab)
+    alt.check()
+    dev.check()
+    assert np.abs(dev.collision(T(f)).cpu().numpy() - I).max() <= 1e-14 * ab.max()
 
 
 def test_full_size_transport_map_sampled(big):
