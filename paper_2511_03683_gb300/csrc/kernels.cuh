@@ -766,20 +766,6 @@ __device__ __forceinline__ void ff_prod(float &h, float &l, float2 x, float ah, 
   l = __fmaf_rn(x.y, ah, e);
 }
 
-// a + b without the final renormalisation (the high part is the rounded sum of the high parts,
-// the low part carries its exact error plus the low parts); renormalise with ff_norm
-__device__ __forceinline__ float2 ff_add_lazy(float2 a, float2 b) {
-  const float s = __fadd_rn(a.x, b.x);
-  const float bb = __fsub_rn(s, a.x);
-  const float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
-  return make_float2(s, __fadd_rn(err, __fadd_rn(a.y, b.y)));
-}
-
-__device__ __forceinline__ float2 ff_norm(float2 a) {
-  const float h = __fadd_rn(a.x, a.y);
-  return make_float2(h, __fsub_rn(a.y, __fsub_rn(h, a.x)));
-}
-
 template <bool LAZY, bool GLOBAL>
 __device__ __forceinline__ void tr_mac3(float (&acc)[6], const float2 *Fp, float2 w) {
   const float2 fx = GLOBAL ? __ldg(Fp) : Fp[0], fy = GLOBAL ? __ldg(Fp + 1) : Fp[1], fz = GLOBAL ? __ldg(Fp + 2) : Fp[2];
@@ -1798,7 +1784,9 @@ constexpr size_t kSymBulkSmem = (size_t)kSymStages * kSymStageBytes + 64 + 2 * k
 
 // reduce-scatter of NV float-float values over the 16 lanes sharing lane bits 0..3: at the end
 // v[0] holds, on every lane, the total of value index idx(lane) = bits 3, 2, .. of the lane (the
-// first log2 NV of them, most significant first), not renormalised
+// first log2 NV of them, most significant first).  Full float-float additions: the low words of
+// lazily added partials of 16 lanes would grow to many ulps of the high word, and their FP32
+// rounding with them.
 template <int NV>
 __device__ __forceinline__ void ff_reduce_scatter16(float2 (&v)[NV], int lane) {
   int n = NV;
@@ -1813,13 +1801,13 @@ __device__ __forceinline__ void ff_reduce_scatter16(float2 (&v)[NV], int lane) {
           const float2 send = up ? v[k] : v[k + h], keep = up ? v[k + h] : v[k];
           const float2 recv = make_float2(__shfl_xor_sync(0xFFFFFFFFu, send.x, mask),
                                           __shfl_xor_sync(0xFFFFFFFFu, send.y, mask));
-          v[k] = ff_add_lazy(keep, recv);
+          v[k] = ff_add(keep, recv);
         }
       }
       n = h;
     } else {
-      v[0] = ff_add_lazy(v[0], make_float2(__shfl_xor_sync(0xFFFFFFFFu, v[0].x, mask),
-                                           __shfl_xor_sync(0xFFFFFFFFu, v[0].y, mask)));
+      v[0] = ff_add(v[0], make_float2(__shfl_xor_sync(0xFFFFFFFFu, v[0].x, mask),
+                                      __shfl_xor_sync(0xFFFFFFFFu, v[0].y, mask)));
     }
   }
 }
@@ -1834,9 +1822,9 @@ __device__ __forceinline__ void sym_columns_out(const float2 *__restrict__ colre
   const int col = q & (kTile - 1), comp = q >> 6;
   float2 acc = colred[((g * WG) * 2 + comp) * kTile + col];
 #pragma unroll
-  for (int w = 1; w < WG; ++w) acc = ff_add_lazy(acc, colred[((g * WG + w) * 2 + comp) * kTile + col]);
-  acc = ff_add_lazy(acc, make_float2(__shfl_xor_sync(0xFFFFFFFFu, acc.x, 16), __shfl_xor_sync(0xFFFFFFFFu, acc.y, 16)));
-  if (g == 0) ((float2 *)tp)[2 * ((long long)(IJ.y * kTile + col) * nb + IJ.x) + comp] = ff_norm(acc);
+  for (int w = 1; w < WG; ++w) acc = ff_add(acc, colred[((g * WG + w) * 2 + comp) * kTile + col]);
+  acc = ff_add(acc, make_float2(__shfl_xor_sync(0xFFFFFFFFu, acc.x, 16), __shfl_xor_sync(0xFFFFFFFFu, acc.y, 16)));
+  if (g == 0) ((float2 *)tp)[2 * ((long long)(IJ.y * kTile + col) * nb + IJ.x) + comp] = acc;
 }
 
 __global__ void __launch_bounds__(kSymThreads, 1) k_stream_sym_bulk(const int2 *__restrict__ tiles, int nt,
@@ -1950,7 +1938,7 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_stream_sym_bulk(const int2 *
       const int idx = ((tj >> 3) & 1) * 4 + ((tj >> 2) & 1) * 2 + ((tj >> 1) & 1);
       if ((tj & 1) == 0) {  // lanes tj and tj ^ 1 hold the same total
         const int row = IJ.x * kTile + ti * R + (idx >> 1);
-        ((float2 *)tp)[2 * ((long long)row * nb + IJ.y) + (idx & 1)] = ff_norm(v[0]);
+        ((float2 *)tp)[2 * ((long long)row * nb + IJ.y) + (idx & 1)] = v[0];
       }
     }
     if (!diag) {
@@ -1963,8 +1951,8 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_stream_sym_bulk(const int2 *
         const float2 a = (m & 1) ? make_float2(cC[jk][0], cC[jk][1]) : make_float2(cA[jk][0], cA[jk][1]);
         const float2 c = (m & 1) ? make_float2(cC[jo][0], cC[jo][1]) : make_float2(cA[jo][0], cA[jo][1]);
         const float2 send = up ? a : c, keep = up ? c : a;
-        const float2 w = ff_add_lazy(keep, make_float2(__shfl_xor_sync(0xFFFFFFFFu, send.x, 16),
-                                                       __shfl_xor_sync(0xFFFFFFFFu, send.y, 16)));
+        const float2 w = ff_add(keep, make_float2(__shfl_xor_sync(0xFFFFFFFFu, send.x, 16),
+                                                  __shfl_xor_sync(0xFFFFFFFFu, send.y, 16)));
         const int col = tj + 16 * ((up ? 2 : 0) + jk);
         colred[(wid * 2 + (m & 1)) * kTile + col] = w;
       }

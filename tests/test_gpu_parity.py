@@ -20,6 +20,7 @@ import synth
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-12
+MUTUAL = 3e-14  # agreement of two FP64-accurate layouts, relative to the gross scattering
 
 
 @pytest.fixture(scope="module")
@@ -203,13 +204,16 @@ def test_branch_merged_and_per_channel_sweeps(pb, name, variant, merge, dense):
     fe = o.window_values(m.f_fermi(m.emin() - 0.2))
     Fr, _ = o.transport_map(fe, v, Fin)
     assert nrel(dev.transport_map(T(fe), T(v), T(Fin)).cpu().numpy(), Fr) <= TOL
+    # two float-float evaluations that round the coefficients and order the sums differently:
+    # each carries about 16 roundings of 2^-48 relative to the gross scattering on the way to a
+    # partial, so they may differ by a few 1e-14 of it (the oracle bound is 1e-13)
     other = pb.Device(ch, variant=variant, merge_branches=3 - merge)
-    assert np.abs(other.collision(T(f)).cpu().numpy() - I).max() <= 1e-14 * ab.max()
+    assert np.abs(other.collision(T(f)).cpu().numpy() - I).max() <= MUTUAL * ab.max()
     if merge == 1:
         assert dev.bytes_per_channel < other.bytes_per_channel
     if merge == 1 and variant == "ff":
         other_rows = pb.Device(ch, variant="ff", dense_rows=0 if dense == 2 else 2)
-        assert np.abs(other_rows.collision(T(f)).cpu().numpy() - I).max() <= 1e-14 * ab.max()
+        assert np.abs(other_rows.collision(T(f)).cpu().numpy() - I).max() <= MUTUAL * ab.max()
         if dense != 2:  # tiles and positional partners stream fewer bytes than the index form
             assert dev.bytes_per_channel < other_rows.bytes_per_channel
 
@@ -236,7 +240,7 @@ def test_tile_sweep_shapes(pb, name, tile_sweep):
     assert nrel(ft.cpu().numpy(), o.rk4(f0, 1.0, 3)) <= TOL
     dev.check()
     other = pb.Device(ch, tile_sweep=1 if tile_sweep != 1 else 2)
-    assert np.abs(other.collision(T(f)).cpu().numpy() - I).max() <= 1e-14 * ab.max()
+    assert np.abs(other.collision(T(f)).cpu().numpy() - I).max() <= MUTUAL * ab.max()
 
 
 def test_time_sweep_measures_without_changing_results(pb):
@@ -446,7 +450,7 @@ def test_full_size_tile_sweep_shapes(pb, big):
     check_I(I, ref, ab)
     alt.check()
     dev.check()
-    assert np.abs(dev.collision(T(f)).cpu().numpy() - I).max() <= 1e-14 * ab.max()
+    assert np.abs(dev.collision(T(f)).cpu().numpy() - I).max() <= MUTUAL * ab.max()
 
 
 def test_full_size_transport_map_sampled(big):
