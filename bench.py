@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--mixed-steps", type=int, default=1000)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--only-adjoint", action="store_true",
+                    help="print only the adjoint workload's report (for profiling its kernels)")
+    ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--no-ablation", action="store_true")
     ap.add_argument("--batched-instances", type=int, default=64)
     ap.add_argument("--batched-steps", type=int, default=500)
@@ -302,10 +305,11 @@ def time_calls(fn, n, stream):
     return statistics.mean(a.elapsed_time(b) for a, b in evs)
 
 
-def adjoint_report(pb, stream):
+def adjoint_report(pb, stream, nsteps=200):
     """The adjoint workload: 24^3, 4 bands, 6 modes; loss = carrier energy after 200 RK4
     steps of 1 fs; gradient with respect to f0 and every stored |g|^2 through checkpoints
     every 20 steps (forward + backward), FP64-accurate (FF) and FP32 (G32) devices."""
+    every = min(20, nsteps)
     import numpy as np
     import torch
 
@@ -316,7 +320,7 @@ def adjoint_report(pb, stream):
     ch = pb.Channels.from_model(m)
     ids = ch.state_ids()
     eps = torch.tensor(m.eps.reshape(-1)[ids], device="cuda")
-    out = {"workload": "24^3, 4 bands, 6 modes, 200 RK4 steps of 1 fs, checkpoints every 20",
+    out = {"workload": f"24^3, 4 bands, 6 modes, {nsteps} RK4 steps of 1 fs, checkpoints every {every}",
            "channels": ch.nchannels}
     grads = {}
     for v in ("ff", "g32"):
@@ -329,13 +333,13 @@ def adjoint_report(pb, stream):
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            (eps * pa.trajectory(dev, f0, g2r, 1.0, 200, 20)).sum().backward()
+            (eps * pa.trajectory(dev, f0, g2r, 1.0, nsteps, every)).sum().backward()
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
         grads[v] = (f0.grad.cpu().numpy(), g2r.grad.cpu().numpy())
-        out[v] = {"forward_backward_ms": min(times), "forward_steps": 200, "recomputed_steps": 200,
-                  "adjoint_steps": 200}
+        out[v] = {"forward_backward_ms": min(times), "forward_steps": nsteps, "recomputed_steps": nsteps,
+                  "adjoint_steps": nsteps}
         dev.close()
     out["g32_grad_err_vs_ff"] = {
         "f0": float(np.abs(grads["g32"][0] - grads["ff"][0]).max() / np.abs(grads["ff"][0]).max()),
@@ -534,6 +538,10 @@ def run_ours(args):
 
     ws, rank, local = dist()
     torch.cuda.set_device(local)
+    if args.only_adjoint:
+        if rank == 0:
+            print(json.dumps({"adjoint": adjoint_report(pb, torch.cuda.current_stream(), args.adjoint_steps)}))
+        return 0
     if ws > 1:
         import torch.distributed as tdist
 
