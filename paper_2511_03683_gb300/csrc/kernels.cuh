@@ -117,6 +117,36 @@ __device__ __forceinline__ double widen_f32(float x) {
   return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)lo);
 }
 
+// reduce-scatter of NV float-float values over the 2 * TOP lanes that differ in lane bits
+// log2 TOP .. 0: at the end v[0] holds, on every lane, the total of value index idx(lane) = those
+// bits of the lane, most significant first (the first log2 NV of them).  Full float-float
+// additions: the low words of lazily added partials of many lanes would grow to many ulps of the
+// high word, and their FP32 rounding with them.
+template <int NV, int TOP>
+__device__ __forceinline__ void ff_reduce_scatter(float2 (&v)[NV], int lane) {
+  int n = NV;
+#pragma unroll
+  for (int mask = TOP; mask > 0; mask >>= 1) {
+    if (n > 1) {
+      const bool up = lane & mask;
+      const int h = n >> 1;
+#pragma unroll
+      for (int k = 0; k < NV / 2; ++k) {
+        if (k < h) {
+          const float2 send = up ? v[k] : v[k + h], keep = up ? v[k + h] : v[k];
+          const float2 recv = make_float2(__shfl_xor_sync(0xFFFFFFFFu, send.x, mask),
+                                          __shfl_xor_sync(0xFFFFFFFFu, send.y, mask));
+          v[k] = ff_add(keep, recv);
+        }
+      }
+      n = h;
+    } else {
+      v[0] = ff_add(v[0], make_float2(__shfl_xor_sync(0xFFFFFFFFu, v[0].x, mask),
+                                      __shfl_xor_sync(0xFFFFFFFFu, v[0].y, mask)));
+    }
+  }
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -1370,35 +1400,62 @@ struct VjpNext {
   float4 *tab;
 };
 
-// mu = J^T g from the float-float partials of k_stream_vjp, one warp per state (lanes over the
-// state's work items, a fixed shuffle tree); out = mu if not null; with acc_out also
-// acc_out = acc_in + mu (the running sum of an RK4 step's stage cotangents); nx: see VjpNext.
+// mu = J^T g from the float-float partials of k_stream_vjp; out = mu if not null; with acc_out
+// also acc_out = acc_in + mu (the running sum of an RK4 step's stage cotangents); nx: see
+// VjpNext.  A 256-thread CTA takes 32 states: each warp adds the item partials of 4 states
+// (lanes over the items, then one 32-lane float-float reduce-scatter of the 16 values), and warp
+// 0 does the FP64 arithmetic of the 32 states at once, one lane per state.
+constexpr int kFinVjpStates = 32;
 __global__ void __launch_bounds__(256) k_fin_vjp(const int *__restrict__ item_ptr, const Part4 *__restrict__ part,
                                                  int ns, double c, const double *__restrict__ R,
                                                  const double *__restrict__ g, double *__restrict__ out,
                                                  const double *acc_in, double *acc_out,  // acc_in may be acc_out
                                                  VjpNext nx, float2 *__restrict__ G, double scale) {
-  const int r = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  if (r >= ns) return;
-  float2 S1 = make_float2(0.f, 0.f), S2 = S1, S3 = S1, S4 = S1;
-  for (int i = item_ptr[r] + lane; i < item_ptr[r + 1]; i += 32) {
-    const float4 *q = reinterpret_cast<const float4 *>(part + i);
-    const float4 u = q[0], v = q[1];
-    S1 = ff_add(S1, make_float2(u.x, u.y));
-    S2 = ff_add(S2, make_float2(u.z, u.w));
-    S3 = ff_add(S3, make_float2(v.x, v.y));
-    S4 = ff_add(S4, make_float2(v.z, v.w));
+  __shared__ float2 tot[kFinVjpStates][4];  // S1..S4 per state
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int base = blockIdx.x * kFinVjpStates;
+  const int r0 = base + lane;
+  // warp 0 loads its state's inputs first, so that their latency overlaps the partials'
+  double gr = 0.0, Rr = 0.0, ai = 0.0, fn = 0.0, ln = 0.0;
+  if (wid == 0 && r0 < ns) {
+    gr = g[r0];
+    Rr = R[r0];
+    if (acc_out) ai = acc_in[r0];
+    if (nx.f) {
+      fn = nx.f[r0];
+      ln = nx.lam[r0];
+    }
   }
-  S1 = warp_reduce_ff(S1);
-  S2 = warp_reduce_ff(S2);
-  S3 = warp_reduce_ff(S3);
-  S4 = warp_reduce_ff(S4);
-  if (lane != 0) return;
+  float2 v[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = base + 4 * wid + q;
+    if (r < ns) {
+      for (int i = item_ptr[r] + lane; i < item_ptr[r + 1]; i += 32) {
+        const float4 *p = reinterpret_cast<const float4 *>(part + i);
+        const float4 a = p[0], b = p[1];
+        v[4 * q] = ff_add(v[4 * q], make_float2(a.x, a.y));
+        v[4 * q + 1] = ff_add(v[4 * q + 1], make_float2(a.z, a.w));
+        v[4 * q + 2] = ff_add(v[4 * q + 2], make_float2(b.x, b.y));
+        v[4 * q + 3] = ff_add(v[4 * q + 3], make_float2(b.z, b.w));
+      }
+    }
+  }
+  ff_reduce_scatter<16, 16>(v, lane);
+  if ((lane & 1) == 0) {
+    const int idx = (lane >> 1) & 15;  // lane bits 4..1: (state q, value)
+    tot[4 * wid + (idx >> 2)][idx & 3] = v[0];
+  }
+  __syncthreads();
+  if (wid != 0 || r0 >= ns) return;
+  const float2 S1 = tot[lane][0], S2 = tot[lane][1], S3 = tot[lane][2], S4 = tot[lane][3];
   const double mu = c * ((ff_to_double(S1.x, S1.y) + ff_to_double(S2.x, S2.y) - ff_to_double(S3.x, S3.y)) +
-                         g[r] * (ff_to_double(S4.x, S4.y) - R[r]));
-  if (out) out[r] = mu;
-  if (acc_out) acc_out[r] = acc_in[r] + mu;
-  if (nx.f) vjp_prep_at(r, nx.f[r], nx.wl * nx.lam[r] + nx.wm * mu, nx.g, G, scale, nx.tab);
+                         gr * (ff_to_double(S4.x, S4.y) - Rr));
+  if (out) out[r0] = mu;
+  if (acc_out) acc_out[r0] = ai + mu;
+  if (nx.f) vjp_prep_at(r0, fn, nx.wl * ln + nx.wm * mu, nx.g, G, scale, nx.tab);
 }
 
 // |g|^2 gradient of NST collision calls at once (one call, or the four stages of an RK4
@@ -1782,36 +1839,6 @@ constexpr unsigned kSymStageBytes = kTileBytes + 2 * kTile * sizeof(float2);
 constexpr size_t kSymColBytes = (size_t)(kSymThreads / 32) * 2 * kTile * sizeof(float2);  // one column table
 constexpr size_t kSymBulkSmem = (size_t)kSymStages * kSymStageBytes + 64 + 2 * kSymColBytes;
 
-// reduce-scatter of NV float-float values over the 16 lanes sharing lane bits 0..3: at the end
-// v[0] holds, on every lane, the total of value index idx(lane) = bits 3, 2, .. of the lane (the
-// first log2 NV of them, most significant first).  Full float-float additions: the low words of
-// lazily added partials of 16 lanes would grow to many ulps of the high word, and their FP32
-// rounding with them.
-template <int NV>
-__device__ __forceinline__ void ff_reduce_scatter16(float2 (&v)[NV], int lane) {
-  int n = NV;
-#pragma unroll
-  for (int mask = 8; mask > 0; mask >>= 1) {
-    if (n > 1) {
-      const bool up = lane & mask;
-      const int h = n >> 1;
-#pragma unroll
-      for (int k = 0; k < NV / 2; ++k) {
-        if (k < h) {
-          const float2 send = up ? v[k] : v[k + h], keep = up ? v[k + h] : v[k];
-          const float2 recv = make_float2(__shfl_xor_sync(0xFFFFFFFFu, send.x, mask),
-                                          __shfl_xor_sync(0xFFFFFFFFu, send.y, mask));
-          v[k] = ff_add(keep, recv);
-        }
-      }
-      n = h;
-    } else {
-      v[0] = ff_add(v[0], make_float2(__shfl_xor_sync(0xFFFFFFFFu, v[0].x, mask),
-                                      __shfl_xor_sync(0xFFFFFFFFu, v[0].y, mask)));
-    }
-  }
-}
-
 // the column partials of a finished off-diagonal tile: one (column, A | C) value per lane pair
 // (lanes l and l ^ 16 take warps 0-3 and 4-7), renormalised, into tp
 __device__ __forceinline__ void sym_columns_out(const float2 *__restrict__ colred, int2 IJ, int nb, int lane, int wid,
@@ -1934,7 +1961,7 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_stream_sym_bulk(const int2 *
         v[2 * i] = make_float2(rA[i][0], rA[i][1]);
         v[2 * i + 1] = make_float2(rC[i][0], rC[i][1]);
       }
-      ff_reduce_scatter16<NV>(v, lane);
+      ff_reduce_scatter<NV, 8>(v, lane);
       const int idx = ((tj >> 3) & 1) * 4 + ((tj >> 2) & 1) * 2 + ((tj >> 1) & 1);
       if ((tj & 1) == 0) {  // lanes tj and tj ^ 1 hold the same total
         const int row = IJ.x * kTile + ti * R + (idx >> 1);
@@ -2063,48 +2090,77 @@ __global__ void k_fin_coll(SRC src, int ns, double c, const double *__restrict__
 // partials k = lane, lane + 32, ... and a fixed shuffle tree combines them, all in float-float
 // (FP64 adds run at 1/64 of the FP32 rate on this part: 75 double partials per state and a
 // double shuffle tree made this epilogue cost as much as a fifth of the sweep).  RATE: 1/tau.
+// The epilogue of the symmetric tile sweep: a 256-thread CTA takes 32 states.  Each warp adds
+// the block partials of 4 states (lanes over the blocks, then one 32-lane float-float
+// reduce-scatter of the 8 values) into a shared table; warp 0 then applies Eq. 2 and the RK4
+// stage arithmetic in FP64 to the 32 states at once, one lane per state (FP64 instructions
+// cost the same with one active lane as with 32 on this part, so a lane-0-per-state epilogue
+// spent most of its time there).  RATE: 1/tau.
+constexpr int kFinTileStates = 32;
 template <int STAGE, bool RATE = false>
 __global__ void __launch_bounds__(256) k_fin_tiles(TileSrc src, int ns, double c, const double *__restrict__ R,
                                                    const double *__restrict__ ysrc, double *__restrict__ out,
                                                    double *__restrict__ f, double *__restrict__ acc,
                                                    double *__restrict__ y, float2 *__restrict__ yff, double dt) {
-  const int r = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  if (r >= ns) return;
+  __shared__ float4 tot[kFinTileStates];  // (A hi, A lo, C hi, C lo) per state
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int base = blockIdx.x * kFinTileStates;
+  // warp 0 loads its state's epilogue inputs first, so that their latency overlaps the partials'
+  const int r0 = base + lane;
   FinIn in{0.0, 0.0, 0.0, 0.0};
-  if (lane == 0) {
-    if (RATE) in.R = R[r];
-    else in = fin_load<false, STAGE>(r, R, ysrc, f, acc);
+  if (wid == 0 && r0 < ns) {
+    if (RATE) in.R = R[r0];
+    else in = fin_load<false, STAGE>(r0, R, ysrc, f, acc);
   }
-  // the first three partials of every lane are loaded together (up to 96 partner blocks)
-  const float4 *__restrict__ row = src.tp + (long long)r * src.nb;
-  float4 v[3];
+  // partials are stored for every padded state (r < nsp); the first three of every lane for
+  // the warp's 4 states are loaded together (up to 96 partner blocks), the rest after
+  const int nb = src.nb;
+  float4 w[4][3];
 #pragma unroll
-  for (int m = 0; m < 3; ++m) {
-    const int k = lane + 32 * m;
-    v[m] = k < src.nb ? row[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  float2 a = make_float2(0.f, 0.f), cc = make_float2(0.f, 0.f);
+  for (int q = 0; q < 4; ++q) {
+    const int r = base + 4 * wid + q;
+    const float4 *__restrict__ row = src.tp + (long long)r * nb;
 #pragma unroll
-  for (int m = 0; m < 3; ++m) {
-    a = ff_add(a, make_float2(v[m].x, v[m].y));
-    cc = ff_add(cc, make_float2(v[m].z, v[m].w));
+    for (int m = 0; m < 3; ++m) {
+      const int k = lane + 32 * m;
+      w[q][m] = r < src.nsp && k < nb ? row[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
   }
-  for (int k = lane + 96; k < src.nb; k += 32) {
-    const float4 w = row[k];
-    a = ff_add(a, make_float2(w.x, w.y));
-    cc = ff_add(cc, make_float2(w.z, w.w));
-  }
+  float2 v[8];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a = ff_add(a, make_float2(__shfl_xor_sync(0xFFFFFFFFu, a.x, o), __shfl_xor_sync(0xFFFFFFFFu, a.y, o)));
-    cc = ff_add(cc, make_float2(__shfl_xor_sync(0xFFFFFFFFu, cc.x, o), __shfl_xor_sync(0xFFFFFFFFu, cc.y, o)));
+  for (int q = 0; q < 4; ++q) {
+    v[2 * q] = make_float2(w[q][0].x, w[q][0].y);
+    v[2 * q + 1] = make_float2(w[q][0].z, w[q][0].w);
+#pragma unroll
+    for (int m = 1; m < 3; ++m) {
+      v[2 * q] = ff_add(v[2 * q], make_float2(w[q][m].x, w[q][m].y));
+      v[2 * q + 1] = ff_add(v[2 * q + 1], make_float2(w[q][m].z, w[q][m].w));
+    }
+    const int r = base + 4 * wid + q;
+    if (r < src.nsp) {
+      const float4 *__restrict__ row = src.tp + (long long)r * nb;
+      for (int k = lane + 96; k < nb; k += 32) {
+        const float4 x = row[k];
+        v[2 * q] = ff_add(v[2 * q], make_float2(x.x, x.y));
+        v[2 * q + 1] = ff_add(v[2 * q + 1], make_float2(x.z, x.w));
+      }
+    }
   }
-  if (lane != 0) return;
-  const double A = ff_to_double(a.x, a.y), B = ff_to_double(cc.x, cc.y) - A;
+  ff_reduce_scatter<8, 16>(v, lane);
+  if ((lane & 3) == 0) {
+    const int idx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);  // (state q, A | C)
+    float *t = reinterpret_cast<float *>(tot + 4 * wid + (idx >> 1)) + 2 * (idx & 1);
+    t[0] = v[0].x;
+    t[1] = v[0].y;
+  }
+  __syncthreads();
+  if (wid != 0 || r0 >= ns) return;
+  const float4 T = tot[lane];
+  const double A = ff_to_double(T.x, T.y), B = ff_to_double(T.z, T.w) - A;
   if (RATE)
-    out[r] = c * (in.R - B);
+    out[r0] = c * (in.R - B);
   else
-    fin_apply<false, STAGE, false>(r, A, B, c, in, out, f, acc, y, yff, dt);
+    fin_apply<false, STAGE, false>(r0, A, B, c, in, out, f, acc, y, yff, dt);
 }
 
 template <bool LIT, typename SRC = ItemSrc>
