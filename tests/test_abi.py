@@ -122,3 +122,22 @@ def test_builder_cutoffs_match_oracle_count(pb, g2_min, nsig):
     m = synth.make_window4(16)
     ch = pb.Channels.from_model(m, g2_min=g2_min, delta_nsigma=nsig)
     assert ch.nchannels == oracle.Oracle(m, g2_min=g2_min, delta_nsigma=nsig).count_channels()
+
+
+@pytest.mark.parametrize("field,bad", [("variant", 9), ("merge_branches", 3), ("dense_rows", 4), ("tile_sweep", 3),
+                                       ("tile_sweep", -1), ("stream_mode", 3), ("channel_per_lane", 5),
+                                       ("transport_gather", 7), ("ctas_per_sm", 9), ("item_channels", 100)])
+def test_device_options_are_checked_on_the_host(pb, field, bad):
+    """pb_dev_arena_bytes resolves and checks pb_dev_opts without touching a GPU: every field
+    out of its documented range is PB_EINVAL, and the defaults size an arena."""
+    import ctypes
+
+    ch = pb.Channels.from_model(synth.make_window4(12))
+    L = pb.lib()
+    nbytes = ctypes.c_size_t(0)
+    ok = pb._DevOpts()
+    assert L.pb_dev_arena_bytes(ch._h, ctypes.byref(ok), ctypes.byref(nbytes)) == pb.PB_OK
+    assert nbytes.value > 0
+    o = pb._DevOpts()
+    setattr(o, field, bad)
+    assert L.pb_dev_arena_bytes(ch._h, ctypes.byref(o), ctypes.byref(nbytes)) == pb.PB_EINVAL
