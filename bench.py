@@ -654,19 +654,24 @@ def run_ours(args):
         Fs, iters, resid, ok = dev.transport(f0, v, tol=1e-10, maxit=1000)
         solve = {"iterations": iters, "residual": resid, "converged": ok, "seconds": time.perf_counter() - t0}
 
-    # end to end through the host-buffer entry points: H2D of f and F, step, D2H of both
+    # end to end through the public API from pinned host buffers: every step copies f and F
+    # host -> device, runs the RK4 step and the transport iteration, copies both results back
+    # and waits for them (one stream synchronisation per step)
     e2e = None
     if not args.no_e2e:
         f_host = torch.tensor(fh).pin_memory()
         F_host = torch.zeros((ns, 3), dtype=torch.float64).pin_memory()
+        f_dev = torch.empty(ns, dtype=torch.float64, device="cuda")
         F_dev = torch.empty((ns, 3), dtype=torch.float64, device="cuda")
         F_out = torch.empty_like(F_dev)
         fnp = f_host.numpy()
 
         def e2e_step():
-            dev.rk4_host(f_host, dt, 1, out=f_host)
+            f_dev.copy_(f_host, non_blocking=True)
             F_dev.copy_(F_host, non_blocking=True)
+            dev.rk4(f_dev, dt, 1)
             dev.transport_iterate(v, F_dev, out=F_out)
+            f_host.copy_(f_dev, non_blocking=True)
             F_host.copy_(F_out, non_blocking=True)
             torch.cuda.current_stream().synchronize()
 
