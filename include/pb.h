@@ -201,8 +201,17 @@ int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, void *arena, s
 void pb_dev_destroy(pb_dev *dev);
 
 /* Synchronise `stream` and report PB_ETIMEOUT if a bounded device-side wait of an earlier
- * launch gave up (the TMA bulk-copy sweep); PB_OK otherwise. */
+ * launch gave up (the TMA bulk-copy sweeps); PB_OK otherwise.  The report clears the handle's
+ * error word, so the next check sees only later launches. */
 int pb_dev_check(pb_dev *dev, void *stream);
+
+/* Test of the bounded-wait machinery itself (the paper has no counterpart): one CTA issues a
+ * 1 KB bulk copy from the handle's arena into shared memory, then waits on an mbarrier that
+ * nothing ever completes, giving up after wait_us microseconds (1..2000000; the sweeps' own
+ * waits give up after 2 s); on the give-up it records the failure in the error word and waits
+ * (bounded) for its own copy before returning, as the sweeps do.  No fault and no hang: the
+ * next pb_dev_check reports PB_ETIMEOUT and the handle stays usable. */
+int pb_dev_selftest_wait(pb_dev *dev, int32_t wait_us, void *stream);
 
 typedef struct pb_dev_info {
   int64_t nstate, nchannels, nchannels_padded, nitems;

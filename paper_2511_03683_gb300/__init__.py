@@ -110,6 +110,7 @@ def lib() -> ctypes.CDLL:
         "pb_dev_create": [vp, ctypes.POINTER(_DevOpts), vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
         "pb_dev_get_info": [vp, ctypes.POINTER(_DevInfo)],
         "pb_dev_check": [vp, vp],
+        "pb_dev_selftest_wait": [vp, i32, vp],
         "pb_dev_time_sweep": [vp, vp, i32, ctypes.POINTER(ctypes.c_float), vp],
         "pb_collision": [vp, vp, vp, vp],
         "pb_collision_static": [vp, vp, vp, vp],
@@ -328,6 +329,11 @@ class Device:
         _check(lib().pb_collision_static(self._h, _dev_vec(f, self.nstate, "f"), _dev_vec(out, self.nstate, "out"),
                                          _stream_ptr(stream)))
         return out
+
+    def selftest_wait(self, wait_us: int = 1000, stream=None):
+        """Launch the bounded-wait self-test (a wait that nothing completes gives up after
+        wait_us microseconds); the next check() raises PBError(PB_ETIMEOUT) and clears it."""
+        _check(lib().pb_dev_selftest_wait(self._h, int(wait_us), _stream_ptr(stream)))
 
     def time_sweep(self, f, nlaunch: int = 20, stream=None) -> float:
         """Average device milliseconds of the collision sweep kernel alone (CUDA events on

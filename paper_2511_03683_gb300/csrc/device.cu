@@ -1052,7 +1052,22 @@ extern "C" int pb_dev_check(pb_dev *d, void *stream) {
   int h = 0;
   PB_CUDA(cudaMemcpyAsync(&h, d->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   PB_CUDA(cudaStreamSynchronize(st));
-  if (h) return set_error(PB_ETIMEOUT, "a bounded device-side wait gave up (error word %d)", h);
+  if (h) {
+    PB_CUDA(cudaMemsetAsync(d->err, 0, sizeof(int), st));  // reported once
+    PB_CUDA(cudaStreamSynchronize(st));
+    return set_error(PB_ETIMEOUT, "a bounded device-side wait gave up (error word %d)", h);
+  }
+  return PB_OK;
+}
+
+extern "C" int pb_dev_selftest_wait(pb_dev *d, int32_t wait_us, void *stream) {
+  clear_error();
+  if (!d) return set_error(PB_EINVAL, "pb_dev_selftest_wait: null argument");
+  if (wait_us < 1 || wait_us > 2000000) return set_error(PB_EINVAL, "pb_dev_selftest_wait: wait_us must be 1..2000000");
+  if (d->arena_bytes < 1024) return set_error(PB_EINVAL, "pb_dev_selftest_wait: the arena is smaller than the 1 KB copied");
+  cudaStream_t st = (cudaStream_t)stream;
+  dev::k_selftest_wait<<<1, 32, 0, st>>>((const float4 *)d->arena, 1000ull * (unsigned long long)wait_us, d->err);
+  PB_LAUNCHED("k_selftest_wait");
   return PB_OK;
 }
 

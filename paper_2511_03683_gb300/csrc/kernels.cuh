@@ -482,12 +482,19 @@ __global__ void __launch_bounds__(kBlock) k_stream_ff(const Item *__restrict__ i
 // Tensor Memory Accelerator: one thread issues 1D bulk copies (cp.async.bulk, completion
 // counted in bytes on an mbarrier) of each work item's P_in, D and 16-bit index slices into
 // a ring of NSTAGE buffers; the whole CTA consumes a buffer, reduces the item, and the buffer
-// is refilled.  Each CTA owns a contiguous range of items.  Every wait is bounded: when it
-// gives up the kernel records the failure in *err, waits (bounded) for its own copies and
-// returns; the host reads *err.
+// is refilled.  Each CTA owns a contiguous range of items.  Every wait is bounded in time (a
+// try_wait may suspend the thread for a while, so polls are not counted): when it gives up the
+// kernel records the failure in *err, waits (bounded) for its own copies and returns; the host
+// reads *err.
 
 constexpr int kBulkStages = 4;
-constexpr unsigned kWaitLimit = 1u << 26;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -509,11 +516,23 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
   return ok != 0;
 }
 
-// bounded wait; false when the limit was reached
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
-  for (unsigned i = 0; i < kWaitLimit; ++i)
+// wait of at most about ns nanoseconds; false when the limit was reached.  The first 1024 polls
+// read no clock (the usual waits end there); after them the clock is read every 64 polls, and
+// a cap on the polls bounds the loop even without the clock.
+constexpr unsigned kWaitPolls = 1u << 24;
+__device__ __forceinline__ bool mbar_wait_for(unsigned long long *bar, unsigned parity, unsigned long long ns) {
+  for (int i = 0; i < 1024; ++i)
     if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (unsigned i = 0; i < kWaitPolls; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63u) == 63u && globaltimer_ns() - t0 >= ns) return false;
+  }
   return false;
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+  return mbar_wait_for(bar, parity, kWaitNs);
 }
 
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
@@ -524,6 +543,29 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Test of the bounded waits: one CTA issues a 1 KB bulk copy (completing on bars[0]), then waits
+// on bars[1], which nothing arrives on, for at most `ns` nanoseconds; on the give-up it records
+// the failure in *err and waits (bounded) for its own copy, like the sweeps' failure path.
+__global__ void k_selftest_wait(const float4 *__restrict__ src, unsigned long long ns, int *__restrict__ err) {
+  __shared__ __align__(128) float4 buf[64];
+  __shared__ unsigned long long bars[2];
+  if (threadIdx.x == 0) {
+    mbar_init(bars, 1);
+    mbar_init(bars + 1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(bars, sizeof(buf));
+    bulk_g2s(buf, src, sizeof(buf), bars);
+    if (!mbar_wait_for(bars + 1, 0, ns)) {
+      *err = 4;
+      mbar_wait(bars, 0);  // drain the copy in flight
+    }
+  }
+  __syncthreads();
+}
 
 // Dynamic shared memory: f table (ns float2), then NSTAGE x [P_in | D | idx] buffers of
 // `cap` channels, then NSTAGE mbarriers and the reduction scratch.

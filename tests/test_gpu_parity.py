@@ -165,6 +165,29 @@ def test_bulk_copy_sweep(pb, name):
     dev.check()
 
 
+def test_bounded_wait_gives_up_and_the_device_stays_usable(pb):
+    """The bounded-wait machinery of the bulk-copy sweeps, exercised without a fault: a wait on
+    an mbarrier that nothing completes gives up after its limit (20 ms here), the error word
+    reaches the host as PB_ETIMEOUT once, and the handle keeps computing the same integral."""
+    import time
+
+    m = SMALL["win16"]()
+    dev = pb.Device(pb.Channels.from_model(m))
+    f = np.random.default_rng(5).uniform(0, 1, dev.nstate)
+    I0 = dev.collision(T(f)).cpu().numpy()
+    dev.check()
+    t0 = time.perf_counter()
+    dev.selftest_wait(20000)
+    with pytest.raises(pb.PBError) as ei:
+        dev.check()
+    dt = time.perf_counter() - t0
+    assert ei.value.code == pb.PB_ETIMEOUT
+    assert 0.015 <= dt < 2.0, dt
+    dev.check()  # reported once
+    assert np.array_equal(dev.collision(T(f)).cpu().numpy(), I0)
+    dev.check()
+
+
 @pytest.mark.parametrize("item_channels", [64, 256, 4096])
 def test_item_split_is_invisible(pb, item_channels):
     """Rows split into many small items (ragged tails, several tiles per row) or few large
