@@ -161,10 +161,15 @@ typedef struct pb_dev_opts {
                                 1024-thread CTA per SM with F in shared memory (5 if F does not fit) and
                                 the next trip in registers, 5 the same through L1, 6 = 3 with lazy sums */
   int32_t transport_ctas;    /* resident 256-thread transport CTAs per SM, 1..8 (0 = 8 with L1 gathers) */
-  int32_t channel_per_lane;  /* FP32/BF16 sweep shape: 0 automatic (= 4); one channel per lane in
-                                512-thread CTAs, three per SM: 1 plain, 3 with an L2 prefetch of the stream
-                                two 128-channel trips ahead; 2 four-channel groups per lane; 4 one channel
-                                per lane in one 1024-thread CTA per SM, next trip's stream in registers */
+  int32_t channel_per_lane;  /* FP32/BF16 sweep shape: 0 automatic (= 5 when the channel list fills at
+                                least 85% of the (state, branch, partner) slots, else 4); one channel per
+                                lane in 512-thread CTAs, three per SM: 1 plain, 3 with an L2 prefetch of the
+                                stream two 128-channel trips ahead; 2 four-channel groups per lane; 4 one
+                                channel per lane in one 1024-thread CTA per SM, next trip's stream in
+                                registers; 5 dense pair-major: |g|^2 in one slot per (state, branch,
+                                partner), zero where no channel exists, no index streamed, one partner per
+                                lane with its branches in turn (the forward sweeps; the adjoint keeps the
+                                channel list) */
   int32_t stream_mode;       /* FF collision sweep: 0 automatic (= 1), 1 vector loads from global memory,
                                 2 TMA bulk copies (cp.async.bulk) into a shared-memory ring (FF variant,
                                 nstate <= 65536); its bounded waits report through pb_dev_check */

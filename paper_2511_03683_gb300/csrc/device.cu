@@ -29,7 +29,7 @@ struct Layout {
   size_t rp, item_ptr, items, col, coefA, coefB, g2, wt, eps, kc, R, omega, tab, part, acc, y, yff, fstage, Fa, Fb,
       Fff, tau, invtau, red, scal, obs, g2lo, gstate, tab32, col16, rp_real, vjpG, g2tab, vecs, hcol, hg2, hA, hB, sc,
       entries, hitems, titems, t_item_ptr, err, citems, citem_ptr, cpart, ccoefA, ccoefB, sidx16, sidx32, pcstart,
-      pcnt, srp, gitems, tiles, tcoef, tpart, total;
+      pcnt, srp, gitems, tiles, tcoef, tpart, g2d, gditems, gdptr, total;
 };
 
 struct Plan {
@@ -140,6 +140,36 @@ size_t coef_bytes(int variant) {
 // over channels and the channel-only regions are empty).
 void plan_items(const std::vector<int64_t> &rp, int item_ch, std::vector<Item> &items, std::vector<int32_t> &ptr);
 
+// Dense pair-major form of the mixed-precision sweep (pb_dev_opts.channel_per_lane 5, or 0 when
+// the channel list fills at least 85% of the (row, branch, partner) slots): |g|^2 in one slot
+// per (row, branch, partner), rows of npp partner slots (nstate rounded up to 32), items of
+// `item` partners, about two per resident warp.
+struct GDense {
+  bool on = false;
+  int npp = 0, nm = 0, item = 0;
+  int64_t nitems = 0;
+  size_t bytes = 0;
+};
+GDense gdense_for(const pb_channels *ch, const pb_dev_opts &o, int sm) {
+  GDense g;
+  const bool mixed = o.variant == PB_VARIANT_G32 || o.variant == PB_VARIANT_G16;
+  if (!mixed || (o.channel_per_lane != 0 && o.channel_per_lane != 5)) return g;
+  const int64_t ns = ch->nstate, nm = ch->nmodes;
+  if (ns == 0 || nm == 0) return g;
+  const int64_t npp = (ns + 31) / 32 * 32;
+  const double slots = (double)ns * (double)nm * (double)npp;
+  if (o.channel_per_lane == 0 && (double)ch->row_ptr[ns] < 0.85 * slots) return g;
+  g.on = true;
+  g.npp = (int)npp;
+  g.nm = (int)nm;
+  const int64_t warps = (int64_t)sm * 32;
+  const int64_t item = (ns * npp / (2 * warps) + 31) / 32 * 32;
+  g.item = (int)std::max<int64_t>(256, std::min<int64_t>(item, npp));
+  g.nitems = ns * std::max<int64_t>(1, (npp + g.item - 1) / g.item);
+  g.bytes = (size_t)(o.variant == PB_VARIANT_G32 ? 4 : 2) * (size_t)slots;
+  return g;
+}
+
 // work items of the branch-merged |g|^2 gradient: the sweep rows in pieces of at most one warp
 // width of entries (plan_items never exceeds item_ch)
 int64_t grad_chunks(const std::vector<int64_t> &rp) {
@@ -162,7 +192,7 @@ TileDims tile_dims(int64_t ns) {
 }
 
 Layout make_layout(const pb_channels *ch, const Plan &P, const Plan *S, int variant, bool transport,
-                   int nfin_blocks, bool sym = false) {
+                   int nfin_blocks, bool sym = false, const GDense &gd = GDense()) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -232,7 +262,11 @@ Layout make_layout(const pb_channels *ch, const Plan &P, const Plan *S, int vari
   L.hitems = take(sizeof(Item) * nhi);
   L.titems = take(sizeof(Item) * ((variant == PB_VARIANT_PAPER) ? z.nentp / kRowPad + (int64_t)ns : 0));
   L.t_item_ptr = take(sizeof(int32_t) * (ns + 1));
-  L.part = take(sizeof(Part4) * std::max<int64_t>(W.nitems, (variant == PB_VARIANT_PAPER) ? z.nentp / kRowPad + (int64_t)ns : 0));
+  L.part = take(sizeof(Part4) * std::max<int64_t>(std::max<int64_t>(W.nitems, gd.nitems),
+                                                  (variant == PB_VARIANT_PAPER) ? z.nentp / kRowPad + (int64_t)ns : 0));
+  L.g2d = take(gd.on ? gd.bytes : 0);
+  L.gditems = take(gd.on ? sizeof(Item) * (size_t)gd.nitems : 0);
+  L.gdptr = take(gd.on ? sizeof(int32_t) * (ns + 1) : 0);
   L.rp_real = take(sizeof(int64_t) * (ns + 1));
   L.vjpG = take(sizeof(float2) * 3 * ns);
   L.g2tab = take(sizeof(float4) * 2 * 4 * ns);
@@ -336,6 +370,13 @@ struct pb_dev {
   int bulk_cap = 0;         // largest work item (channels), the bulk stage capacity
   size_t bulk_smem = 0;
   void *g2lo = nullptr;     // |g|^2 in FP32 or BF16 (mixed-precision variants)
+  // dense pair-major mixed-precision sweep (GDense)
+  bool gdense = false;
+  int gd_npp = 0, gd_nitems = 0;
+  size_t gd_bytes = 0;
+  void *g2d = nullptr;
+  Item *gd_items = nullptr;
+  int32_t *gd_item_ptr = nullptr;
   uint4 *gstate = nullptr;  // per-state records of the mixed-precision sweep (eps, f, grid index)
   bool vjp_g_ok = false;    // the mixed-precision adjoint's 20 bytes per state fit in shared memory
   float2 *tab32 = nullptr;  // padded-grid (hbar w, N) in FP32
@@ -410,6 +451,8 @@ struct pb_dev {
     return g;
   }
   bool mixed() const { return variant == PB_VARIANT_G32 || variant == PB_VARIANT_G16; }
+  // the work items whose partials the forward sweeps write (collision, rates, RK4 stages)
+  const int32_t *fwd_item_ptr() const { return gdense ? gd_item_ptr : item_ptr; }
   pb::dev::GGeom ggeom() const {
     pb::dev::GGeom g;
     g.col = col;
@@ -459,8 +502,8 @@ int resolve_opts(const pb_channels *ch, const pb_dev_opts *opts, int sm_count, p
   if (d.ctas_per_sm <= 0) d.ctas_per_sm = merged ? 4 : 3;
   if (d.ctas_per_sm > 8) return set_error(PB_EINVAL, "pb_dev: ctas_per_sm must be <= 8");
   if (d.stream_mode < 0 || d.stream_mode > 2) return set_error(PB_EINVAL, "pb_dev: stream_mode must be 0..2");
-  if (d.channel_per_lane < 0 || d.channel_per_lane > 4)
-    return set_error(PB_EINVAL, "pb_dev: channel_per_lane must be 0..4");
+  if (d.channel_per_lane < 0 || d.channel_per_lane > 5)
+    return set_error(PB_EINVAL, "pb_dev: channel_per_lane must be 0..5");
   if (d.transport_gather < 0 || d.transport_gather > 6 || d.transport_ctas < 0 || d.transport_ctas > 8)
     return set_error(PB_EINVAL, "pb_dev: transport_gather must be 0..6 and transport_ctas 0..8");
   if (d.item_channels < 0 || d.item_channels % 64 != 0)
@@ -639,7 +682,7 @@ extern "C" int pb_dev_arena_bytes(const pb_channels *ch, const pb_dev_opts *opts
     const bool merged = make_plans(ch, opts, o, sm, P, S, &complete);
     const int nfin = (int)((P.ns + kFinBlock - 1) / kFinBlock);
     *bytes = make_layout(ch, P, merged ? &S : nullptr, o.variant, o.transport != 0, nfin,
-                         sym_for(o, merged, complete)).total;
+                         sym_for(o, merged, complete), gdense_for(ch, o, sm)).total;
   } catch (const std::bad_alloc &) {
     return set_error(PB_ENOMEM, "pb_dev_arena_bytes: out of host memory");
   }
@@ -702,7 +745,12 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->sym = sym_for(o, merged, complete);
   d->sym_nt = d->sym && o.tile_sweep == 2 ? dev::kSymThreads : 0;
   d->td = tile_dims(d->ns);
-  d->L = make_layout(ch, P, merged ? &S : nullptr, o.variant, d->transport, d->nfin_blocks, d->sym);
+  const GDense gd = gdense_for(ch, o, sm);
+  d->gdense = gd.on;
+  d->gd_npp = gd.npp;
+  d->gd_nitems = (int)gd.nitems;
+  d->gd_bytes = gd.bytes;
+  d->L = make_layout(ch, P, merged ? &S : nullptr, o.variant, d->transport, d->nfin_blocks, d->sym, gd);
   if (arena_bytes < d->L.total) {
     const size_t need = d->L.total;
     delete d;
@@ -740,6 +788,11 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->obs = (double *)(A + L.obs);
   d->err = (int *)(A + L.err);
   d->g2lo = A + L.g2lo;
+  if (d->gdense) {
+    d->g2d = A + L.g2d;
+    d->gd_items = (Item *)(A + L.gditems);
+    d->gd_item_ptr = (int32_t *)(A + L.gdptr);
+  }
   d->gstate = (uint4 *)(A + L.gstate);
   d->tab32 = (float2 *)(A + L.tab32);
   d->col16 = d->ns <= 65536 ? (uint16_t *)(A + L.col16) : nullptr;
@@ -891,6 +944,15 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
         }
       }
       UP(d->rp, P.rp.data(), sizeof(int64_t) * (d->ns + 1));
+      if (d->gdense) {
+        std::vector<int64_t> rpd((size_t)d->ns + 1);
+        for (int64_t r = 0; r <= d->ns; ++r) rpd[r] = r * gd.npp;
+        std::vector<Item> gi;
+        std::vector<int32_t> gp;
+        plan_items(rpd, gd.item, gi, gp);
+        UP(d->gd_items, gi.data(), sizeof(Item) * gi.size());
+        UP(d->gd_item_ptr, gp.data(), sizeof(int32_t) * gp.size());
+      }
       UP(d->rp_real, ch->row_ptr.data(), sizeof(int64_t) * (d->ns + 1));
       UP(d->item_ptr, W.item_ptr.data(), sizeof(int32_t) * (d->ns + 1));
       UP(d->items, W.items.data(), sizeof(Item) * W.nitems);
@@ -1035,6 +1097,10 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   if (d->mixed() && d->smem_f > 48 * 1024) {
     set_lane_smem<float>((int)d->smem_f);
     set_lane_smem<__nv_bfloat16>((int)d->smem_f);
+    cudaFuncSetAttribute(dev::k_stream_g_dense<dev::MODE_COLL, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
+    cudaFuncSetAttribute(dev::k_stream_g_dense<dev::MODE_RATE, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
+    cudaFuncSetAttribute(dev::k_stream_g_dense<dev::MODE_COLL, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
+    cudaFuncSetAttribute(dev::k_stream_g_dense<dev::MODE_RATE, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
     cudaFuncSetAttribute(dev::k_stream_g<dev::MODE_COLL, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
     cudaFuncSetAttribute(dev::k_stream_g<dev::MODE_RATE, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
     cudaFuncSetAttribute(dev::k_stream_g<dev::MODE_COLL, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
@@ -1101,8 +1167,12 @@ extern "C" int pb_dev_get_info(const pb_dev *d, pb_dev_info *info) {
     case PB_VARIANT_F64:
       info->bytes_per_channel = (2 * sizeof(double) + (d->sidx16 ? 2 : 4)) * (d->merged ? (double)d->nsw / (double)d->nch : 1.0);
       break;
-    case PB_VARIANT_G32: info->bytes_per_channel = sizeof(float) + sizeof(uint32_t); break;
-    case PB_VARIANT_G16: info->bytes_per_channel = 2 + sizeof(uint32_t); break;
+    case PB_VARIANT_G32:
+    case PB_VARIANT_G16:
+      // dense pair-major: the (state, partner, branch) slots, zeros included; else |g|^2 + word
+      info->bytes_per_channel = d->gdense ? (d->nch ? (double)d->gd_bytes / (double)d->nch : 0.0)
+                                          : (d->variant == PB_VARIANT_G32 ? 4.0 : 2.0) + sizeof(uint32_t);
+      break;
     case PB_VARIANT_PAPER:  // step 2: P_in, D, index, sc_col write; step 3: entry + sc_col gather
       info->bytes_per_channel = d->nch ? (28.0 * (double)d->nh + 12.0 * (double)d->nent) / (double)d->nch : 0.0;
       break;
@@ -1178,7 +1248,20 @@ int launch_stream_t(pb_dev *d, int mode, const double *fd, const float2 *fff, co
     const int gg = (int)std::max<int64_t>(1, std::min<int64_t>((d->nitems * 32 + 511) / 512, (int64_t)d->sm_count * d->ctas));
     const float *g32 = (const float *)d->g2lo;
     const __nv_bfloat16 *g16 = (const __nv_bfloat16 *)d->g2lo;
-    if (d->g_lane) {
+    if (d->gdense) {
+      const int gdg = (int)std::max<int64_t>(
+          1, std::min<int64_t>(((int64_t)d->gd_nitems * 32 + dev::kDenseThreads - 1) / dev::kDenseThreads, d->sm_count));
+      const int nd = d->gd_nitems, npp = d->gd_npp, nm = d->nmodes;
+      if (d->variant == PB_VARIANT_G32) {
+        const float *gd = (const float *)d->g2d;
+        if (coll) dev::k_stream_g_dense<dev::MODE_COLL, float><<<gdg, dev::kDenseThreads, d->smem_f, st>>>(d->gd_items, nd, g, gd, npp, nm, d->gstate, ns, part);
+        else      dev::k_stream_g_dense<dev::MODE_RATE, float><<<gdg, dev::kDenseThreads, d->smem_f, st>>>(d->gd_items, nd, g, gd, npp, nm, d->gstate, ns, part);
+      } else {
+        const __nv_bfloat16 *gd = (const __nv_bfloat16 *)d->g2d;
+        if (coll) dev::k_stream_g_dense<dev::MODE_COLL, __nv_bfloat16><<<gdg, dev::kDenseThreads, d->smem_f, st>>>(d->gd_items, nd, g, gd, npp, nm, d->gstate, ns, part);
+        else      dev::k_stream_g_dense<dev::MODE_RATE, __nv_bfloat16><<<gdg, dev::kDenseThreads, d->smem_f, st>>>(d->gd_items, nd, g, gd, npp, nm, d->gstate, ns, part);
+      }
+    } else if (d->g_lane) {
       if (d->variant == PB_VARIANT_G32)
         launch_g_lane<float>(d->g_shape, coll, gg, d->sm_count, d->smem_f, st, d->items, n, g, g32, d->gstate, ns, part);
       else
@@ -1218,7 +1301,7 @@ void launch_fin(pb_dev *d, const double *ysrc, double *out, double *f, double dt
                 double *ydst = nullptr) {
   double *y = ydst ? ydst : d->y;
   if (d->mixed())
-    dev::k_fin_coll<true, STAGE, true><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->item_ptr, d->part}, (int)d->ns,
+    dev::k_fin_coll<true, STAGE, true><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->fwd_item_ptr(), d->part}, (int)d->ns,
                                                                           d->c * d->gnorm(), d->R,
                                                                           ysrc, out, f, d->acc, y,
                                                                           (float2 *)d->gstate, dt);
@@ -1426,7 +1509,7 @@ extern "C" int pb_scatter_rates(pb_dev *d, const double *f, double *inv_tau, voi
   if ((rc = stage_input(d, f, st))) return rc;
   if ((rc = launch_stream(d, dev::MODE_RATE, f, d->yff, st))) return rc;
   if (d->variant == PB_VARIANT_LITERAL || d->mixed())
-    dev::k_fin_rate<true><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->item_ptr, d->part}, (int)d->ns,
+    dev::k_fin_rate<true><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->fwd_item_ptr(), d->part}, (int)d->ns,
                                                              d->mixed() ? d->c * d->gnorm() : d->c, d->R, inv_tau);
   else if (d->sym)
     dev::k_fin_tiles<-1, true><<<(int)((d->ns + dev::kFinTileStates - 1) / dev::kFinTileStates), 256, 0, st>>>(
@@ -1582,6 +1665,17 @@ int coef_setup(pb_dev *d, cudaStream_t st) {
     else
       dev::k_cvt_g2<__nv_bfloat16><<<cg, 256, 0, st>>>(d->g2, n, (__nv_bfloat16 *)d->g2lo);
     PB_LAUNCHED("k_cvt_g2");
+    if (d->gdense) {
+      PB_CUDA(cudaMemsetAsync(d->g2d, 0, d->gd_bytes, st));
+      const long long *rp = (const long long *)d->rp, *rr = (const long long *)d->rp_real;
+      if (d->variant == PB_VARIANT_G32)
+        dev::k_dense_g2<float><<<d->chan_grid(8), dev::kBlock, 0, st>>>(d->items, (int)d->nitems, rp, rr, d->col, d->g2,
+                                                                        d->nmodes, d->gd_npp, (float *)d->g2d);
+      else
+        dev::k_dense_g2<__nv_bfloat16><<<d->chan_grid(8), dev::kBlock, 0, st>>>(
+            d->items, (int)d->nitems, rp, rr, d->col, d->g2, d->nmodes, d->gd_npp, (__nv_bfloat16 *)d->g2d);
+      PB_LAUNCHED("k_dense_g2");
+    }
   }
   return PB_OK;
 }

@@ -1184,6 +1184,147 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 3 : 1) k_stream_g_lane(const I
   }
 }
 
+// Dense pair-major form of the mixed-precision sweep.  |g|^2 is stored in one slot per
+// (row s, partner p, branch nu): g2d[(s * npp + p) * nm + nu], zero where the channel does not
+// exist, so no index is streamed; a pair's branches are contiguous (a few vector loads at fixed
+// offsets) and a warp's 32 partners one contiguous run.  A lane takes one partner at a time:
+// the partner record, the energy difference and the occupation products once per pair, then
+// the nm branches with their (hbar w, N) from the table row of q = k_p - k_s.  g_term's bracket
+// with its first-order low-part corrections is bilinear in (G_a, G_e); collected per pair it is
+//   u = G_a (N alpha - gamma') + G_e (N alpha + beta'),   alpha = (f_s - f_p) + (f_s,lo - f_p,lo),
+//   delta = f_s,lo f_p + f_p,lo f_s,  beta' = A + f_s,lo - delta,  gamma' = B + f_p,lo - delta
+// (A = f_s (1 - f_p), B = (1 - f_s) f_p as g_term forms them), and the rate summand is
+// G_a (N + f_p) + G_e (N + 1 - f_p) with f_p = hi + lo: a few operations per branch besides the
+// Gaussians.  A lane's nm terms are summed and added to its compensated sum once per pair.  An
+// item is a run of partners of one row (I.start = s * npp + first partner); its partial goes to
+// part[item].x.
+constexpr int kDenseBranches = 6;  // branches whose loads a lane issues together (more: one at a time)
+constexpr int kDenseThreads = 1024;  // one CTA per SM (768 threads without spills measured slower)
+template <int MODE, typename G2T>
+__global__ void __launch_bounds__(kDenseThreads, 1) k_stream_g_dense(const Item *__restrict__ items, int nitems, GGeom g,
+                                                            const G2T *__restrict__ g2d, int npp, int nm,
+                                                            const uint4 *__restrict__ gstate, int ns,
+                                                            Part4 *__restrict__ part) {
+  extern __shared__ uint4 gsd[];
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) gsd[i] = gstate[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    const int s = I.row;
+    const uint4 ss = gsd[s];
+    const int base = g.cpad - rec_lnm(ss);
+    const int p0 = (int)(I.start - (long long)s * npp);
+    const G2T *__restrict__ gr = g2d + (size_t)s * npp * nm;
+    const float fs = __uint_as_float(ss.z), fsl = rec_f_lo(ss), es = __uint_as_float(ss.x), esl = rec_eps_lo(ss);
+    float sum = 0.f, comp = 0.f;
+    for (int j = lane; j < I.len; j += 32) {
+      const int p = p0 + j;
+      if (p >= ns) break;  // the row's padding slots (zero |g|^2, no record)
+      const uint4 sp = gsd[p];
+      const float dh = __fsub_rn(es, __uint_as_float(sp.x));
+      const float dl = __fsub_rn(esl, rec_eps_lo(sp));
+      const float fp = __uint_as_float(sp.z), fpl = rec_f_lo(sp);
+      float alpha, betap, gammap;  // pair constants of the collision bracket (or of the rate summand)
+      if (MODE == MODE_COLL) {
+        const float P = fs * fp, A = fs - P, B = fp - P;
+        const float delta = fmaf(fsl, fp, fpl * fs);
+        alpha = (fs - fp) + (fsl - fpl);
+        betap = (A + fsl) - delta;
+        gammap = (B + fpl) - delta;
+      } else {
+        alpha = fp + fpl;  // f_p
+        betap = 1.f - alpha;
+        gammap = 0.f;
+      }
+      const float2 *__restrict__ tr = g.tabp + (base + rec_lnm(sp));
+      auto term = [&](float gv, float2 t) {
+        const float a = (dh + t.x) + dl;  // x + w
+        const float e = (dh - t.x) + dl;  // x - w
+        const float Ga = ex2_approx(a * a * g.k2);
+        const float Ge = ex2_approx(e * e * g.k2);
+        float u;
+        if (MODE == MODE_COLL) {
+          const float na = alpha * t.y;
+          u = fmaf(Ge, na + betap, Ga * (na - gammap));
+        } else {
+          u = fmaf(Ge, t.y + betap, Ga * (t.y + alpha));
+        }
+        return gv * u;
+      };
+      float acc = 0.f;
+      const G2T *__restrict__ gq = gr + (size_t)p * nm;  // the pair's nm slots
+      if (nm <= kDenseBranches) {
+        // all of the pair's loads first (|g|^2 from HBM, (hbar w, N) from L1/L2), then the terms
+        float gv[kDenseBranches];
+        float2 tv[kDenseBranches];
+        if ((nm & 1) == 0) {  // even nm: the slots of a pair start 8-byte (FP32) / 4-byte (BF16) aligned
+#pragma unroll
+          for (int k = 0; k < kDenseBranches / 2; ++k)
+            if (2 * k < nm) {
+              if (sizeof(G2T) == 4) {
+                const float2 v = __ldcs(reinterpret_cast<const float2 *>(gq) + k);
+                gv[2 * k] = v.x;
+                gv[2 * k + 1] = v.y;
+              } else {
+                const unsigned w = __ldcs(reinterpret_cast<const unsigned *>(gq) + k);
+                gv[2 * k] = __uint_as_float(w << 16);
+                gv[2 * k + 1] = __uint_as_float(w & 0xFFFF0000u);
+              }
+            }
+        } else {
+#pragma unroll
+          for (int nu = 0; nu < kDenseBranches; ++nu)
+            if (nu < nm) gv[nu] = g2_at(gq, nu);
+        }
+#pragma unroll
+        for (int nu = 0; nu < kDenseBranches; ++nu)
+          if (nu < nm) tv[nu] = __ldg(tr + nu);
+#pragma unroll
+        for (int nu = 0; nu < kDenseBranches; ++nu)
+          if (nu < nm) acc += term(gv[nu], tv[nu]);
+      } else {
+        for (int nu = 0; nu < nm; ++nu) acc += term(g2_at(gq, nu), __ldg(tr + nu));
+      }
+      kahan_add(sum, comp, acc);
+    }
+    // float-float tree of (sum, -comp), then one conversion
+    const double v = warp_sum_ff(make_float2(sum, -comp));
+    if (lane == 0) part[it] = make_part4(v, 0.0, 0.0, 0.0);
+  }
+}
+
+// g2d[(r * npp + p) * nm + nu] = |g|^2 of the stored channel (r, p, nu) in the storage type
+// (round to nearest); the array is cleared before, so missing channels keep zero slots
+template <typename G2T>
+__global__ void __launch_bounds__(kBlock) k_dense_g2(const Item *__restrict__ items, int nitems,
+                                                     const long long *__restrict__ rp_pad,
+                                                     const long long *__restrict__ rp_real,
+                                                     const uint32_t *__restrict__ col, const double *__restrict__ g2,
+                                                     int nm, int npp, G2T *__restrict__ g2d) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    const int r = I.row;
+    const long long off = I.start - rp_pad[r];
+    const long long real_len = rp_real[r + 1] - rp_real[r];
+    for (int j = lane; j < I.len; j += 32) {
+      if (off + j >= real_len) break;
+      const long long c = I.start + j;
+      const unsigned cw = col[c];
+      const size_t slot = ((size_t)r * npp + (cw & 0xFFFFFFu)) * (size_t)nm + (cw >> 24);
+      if (sizeof(G2T) == 4)
+        ((float *)g2d)[slot] = __double2float_rn(g2[c]);
+      else
+        ((__nv_bfloat16 *)g2d)[slot] = __double2bfloat16(g2[c]);
+    }
+  }
+}
+
 // FP32 adjoint of the mixed-precision sweep.  With w_c(f_p) = g2 [G_a (N+f_p) + G_e (N+1-f_p)]
 // (the rate summand) the VJP of Eq. 2 is  (J^T lam)_x = -c sum_{row x} (lam_x - lam_p) w_c(f_p):
 // the coefficient form's c [sum lam_p (P_in + (1-f_p) D) - lam_x sum W] written per channel.

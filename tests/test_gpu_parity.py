@@ -359,11 +359,12 @@ def test_mixed_precision_collision_and_rates(pb, name, variant):
         assert nrel(dev.rates(T(f)).cpu().numpy(), o.rates(f)) <= tol
 
 
-@pytest.mark.parametrize("shape", [1, 2, 3, 4])
+@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("variant", ["g32", "g16"])
 def test_mixed_precision_sweep_shapes(pb, variant, shape):
     """Every launch shape of the FP32/BF16 sweep on a ragged case (rows of many lengths,
-    items split inside rows) meets the same bound against the oracle."""
+    items split inside rows; 5: the dense pair-major form) meets the same bound against the
+    oracle."""
     m = synth.make_window4(16)
     o = oracle.Oracle(m)
     dev = pb.Device(pb.Channels.from_model(m), variant=variant, channel_per_lane=shape, item_channels=256)
@@ -371,6 +372,21 @@ def test_mixed_precision_sweep_shapes(pb, variant, shape):
     ref, ab = o.collision(f, with_abs=True)
     check_I(dev.collision(T(f)).cpu().numpy(), ref, ab, tol=MIXED_TOL[variant], abs_tol=MIXED_TOL[variant])
     assert nrel(dev.rates(T(f)).cpu().numpy(), o.rates(f)) <= MIXED_TOL[variant]
+
+
+@pytest.mark.parametrize("shape", [0, 5])
+def test_mixed_precision_with_cutoffs(pb, shape):
+    """With the |g| and delta cutoffs on, the channel list fills few (row, branch, partner)
+    slots: the automatic shape keeps the per-channel sweep, and the dense pair-major form
+    (forced) still meets the oracle with zeros in the missing slots."""
+    m = synth.make_window4(16)
+    ch = pb.Channels.from_model(m, g2_min=5e-4, delta_nsigma=4.0)
+    o = oracle.Oracle(m, g2_min=5e-4, delta_nsigma=4.0)
+    dev = pb.Device(ch, variant="g32", channel_per_lane=shape)
+    f = np.random.default_rng(12).uniform(0, 1, o.nstate)
+    ref, ab = o.collision(f, with_abs=True)
+    check_I(dev.collision(T(f)).cpu().numpy(), ref, ab, tol=MIXED_TOL["g32"], abs_tol=MIXED_TOL["g32"])
+    assert nrel(dev.rates(T(f)).cpu().numpy(), o.rates(f)) <= MIXED_TOL["g32"]
 
 
 @pytest.mark.parametrize("variant", ["g32", "g16"])
