@@ -1092,6 +1092,9 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
     if (vb > 48 * 1024 && d->vjp_g_ok) {
       cudaFuncSetAttribute(dev::k_stream_g_vjp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vb);
       cudaFuncSetAttribute(dev::k_stream_g_vjp<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vb);
+      cudaFuncSetAttribute(dev::k_stream_g_dense<dev::MODE_VJP, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vb);
+      cudaFuncSetAttribute(dev::k_stream_g_dense<dev::MODE_VJP, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)vb);
     }
   }
   if (d->mixed() && d->smem_f > 48 * 1024) {
@@ -1697,13 +1700,26 @@ int vjp_launch_mixed(pb_dev *d, const double *f, const double *lam, double wl, c
   const size_t smem = (sizeof(uint4) + sizeof(float)) * (size_t)ns;
   const int ctas = (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(228 * 1024) / (smem + 1024)));
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((d->nitems * 32 + 511) / 512, (int64_t)d->sm_count * ctas));
-  if (d->variant == PB_VARIANT_G32)
-    dev::k_stream_g_vjp<float><<<grid, 512, smem, st>>>(d->items, n, g, (const float *)d->g2lo, d->gstate, lam32, ns, d->part);
-  else
-    dev::k_stream_g_vjp<__nv_bfloat16><<<grid, 512, smem, st>>>(d->items, n, g, (const __nv_bfloat16 *)d->g2lo, d->gstate,
-                                                                lam32, ns, d->part);
-  PB_LAUNCHED("k_stream_g_vjp");
-  dev::k_fin_rate<true><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->item_ptr, d->part}, ns, -d->c * d->gnorm(), d->R, mu);
+  if (d->gdense) {
+    // the dense pair-major sweep with the rate summands weighted by lam_s - lam_p
+    const int gdg = (int)std::max<int64_t>(
+        1, std::min<int64_t>(((int64_t)d->gd_nitems * 32 + dev::kDenseThreads - 1) / dev::kDenseThreads, d->sm_count));
+    if (d->variant == PB_VARIANT_G32)
+      dev::k_stream_g_dense<dev::MODE_VJP, float><<<gdg, dev::kDenseThreads, smem, st>>>(
+          d->gd_items, d->gd_nitems, g, (const float *)d->g2d, d->gd_npp, d->nmodes, d->gstate, ns, d->part, lam32);
+    else
+      dev::k_stream_g_dense<dev::MODE_VJP, __nv_bfloat16><<<gdg, dev::kDenseThreads, smem, st>>>(
+          d->gd_items, d->gd_nitems, g, (const __nv_bfloat16 *)d->g2d, d->gd_npp, d->nmodes, d->gstate, ns, d->part, lam32);
+    PB_LAUNCHED("k_stream_g_dense (vjp)");
+  } else {
+    if (d->variant == PB_VARIANT_G32)
+      dev::k_stream_g_vjp<float><<<grid, 512, smem, st>>>(d->items, n, g, (const float *)d->g2lo, d->gstate, lam32, ns, d->part);
+    else
+      dev::k_stream_g_vjp<__nv_bfloat16><<<grid, 512, smem, st>>>(d->items, n, g, (const __nv_bfloat16 *)d->g2lo, d->gstate,
+                                                                  lam32, ns, d->part);
+    PB_LAUNCHED("k_stream_g_vjp");
+  }
+  dev::k_fin_rate<true><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->fwd_item_ptr(), d->part}, ns, -d->c * d->gnorm(), d->R, mu);
   PB_LAUNCHED("k_fin_rate (vjp)");
   if (acc_out) {
     dev::k_lincomb<<<(ns + 255) / 256, 256, 0, st>>>(ns, 1.0, acc_in, 1.0, mu, acc_out);

@@ -380,7 +380,7 @@ __device__ __forceinline__ uint4 partners4<uint16_t>(const uint16_t *__restrict_
 }
 
 // ------------------------------------------------------------ streaming kernels
-enum { MODE_COLL = 0, MODE_RATE = 1 };
+enum { MODE_COLL = 0, MODE_RATE = 1, MODE_VJP = 2 };  // MODE_VJP: the dense mixed-precision sweep only
 
 // The four occupations (float-float) of the entries of group q (4 consecutive entries): gathered
 // through their partner indices, or, for complete rows (DENSE: the row's entries are its
@@ -1197,16 +1197,22 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 3 : 1) k_stream_g_lane(const I
 // G_a (N + f_p) + G_e (N + 1 - f_p) with f_p = hi + lo: a few operations per branch besides the
 // Gaussians.  A lane's nm terms are summed and added to its compensated sum once per pair.  An
 // item is a run of partners of one row (I.start = s * npp + first partner); its partial goes to
-// part[item].x.
+// part[item].x.  MODE_VJP: the FP32 adjoint's sum, the rate summands of each pair weighted by
+// lam_s - lam_p (lam in FP32 after the records in shared memory; see k_stream_g_vjp).
 constexpr int kDenseBranches = 6;  // branches whose loads a lane issues together (more: one at a time)
 constexpr int kDenseThreads = 1024;  // one CTA per SM (768 threads without spills measured slower)
 template <int MODE, typename G2T>
 __global__ void __launch_bounds__(kDenseThreads, 1) k_stream_g_dense(const Item *__restrict__ items, int nitems, GGeom g,
                                                             const G2T *__restrict__ g2d, int npp, int nm,
                                                             const uint4 *__restrict__ gstate, int ns,
-                                                            Part4 *__restrict__ part) {
+                                                            Part4 *__restrict__ part,
+                                                            const float *__restrict__ lam32 = nullptr) {
   extern __shared__ uint4 gsd[];
-  for (int i = threadIdx.x; i < ns; i += blockDim.x) gsd[i] = gstate[i];
+  float *lsm = reinterpret_cast<float *>(gsd + ns);  // MODE_VJP
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+    gsd[i] = gstate[i];
+    if (MODE == MODE_VJP) lsm[i] = lam32[i];
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1219,6 +1225,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_stream_g_dense(const Item 
     const int p0 = (int)(I.start - (long long)s * npp);
     const G2T *__restrict__ gr = g2d + (size_t)s * npp * nm;
     const float fs = __uint_as_float(ss.z), fsl = rec_f_lo(ss), es = __uint_as_float(ss.x), esl = rec_eps_lo(ss);
+    const float ls = MODE == MODE_VJP ? lsm[s] : 0.f;
     float sum = 0.f, comp = 0.f;
     for (int j = lane; j < I.len; j += 32) {
       const int p = p0 + j;
@@ -1288,7 +1295,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_stream_g_dense(const Item 
       } else {
         for (int nu = 0; nu < nm; ++nu) acc += term(g2_at(gq, nu), __ldg(tr + nu));
       }
-      kahan_add(sum, comp, acc);
+      kahan_add(sum, comp, MODE == MODE_VJP ? (ls - lsm[p]) * acc : acc);
     }
     // float-float tree of (sum, -comp), then one conversion
     const double v = warp_sum_ff(make_float2(sum, -comp));
