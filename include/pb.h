@@ -328,7 +328,10 @@ typedef struct pb_batch_opts {
                              channel); 1: FP64-accurate: each instance's coefficients computed in FP64,
                              summed over the branches of every state pair, stored float-float (one entry
                              per state pair) */
-  int32_t reserved;
+  int32_t layout;         /* precision 0: 0 automatic (the dense pair-major form when the stored channels
+                             fill at least 85% of the instances' (state, partner, branch) slots: |g|^2 in
+                             one FP32 slot each, zero where no channel exists, no index streamed; work
+                             items of item_channels / 4 partners); 1 one entry per channel */
 } pb_batch_opts;
 
 int pb_batch_arena_bytes(const pb_channels *const *chs, int32_t n, const pb_batch_opts *opts, size_t *bytes);

@@ -444,7 +444,7 @@ class Device:
 
 class _BatchOpts(ctypes.Structure):
     _fields_ = [("item_channels", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("layout", ctypes.c_int32)]
 
 
 class Batch:
@@ -454,14 +454,15 @@ class Batch:
 
     PRECISIONS = {"fp32": 0, "ff": 1}
 
-    def __init__(self, channels, item_channels: int = 0, ctas_per_sm: int = 0, precision: str = "fp32", stream=None):
+    def __init__(self, channels, item_channels: int = 0, ctas_per_sm: int = 0, precision: str = "fp32", layout: int = 0,
+                 stream=None):
         import torch
 
         self.channels = list(channels)
         arr = (ctypes.c_void_p * len(self.channels))(*[c._h.value for c in self.channels])
         self._arr = arr
         self.precision = precision
-        o = _BatchOpts(int(item_channels), int(ctas_per_sm), Batch.PRECISIONS[precision], 0)
+        o = _BatchOpts(int(item_channels), int(ctas_per_sm), Batch.PRECISIONS[precision], int(layout))
         nbytes = ctypes.c_size_t(0)
         _check(lib().pb_batch_arena_bytes(arr, len(self.channels), ctypes.byref(o), ctypes.byref(nbytes)))
         self.arena = torch.empty(int(nbytes.value), dtype=torch.uint8, device="cuda")

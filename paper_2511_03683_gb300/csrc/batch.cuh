@@ -24,7 +24,9 @@ struct BInst {
   int cpad;           // L(N1,N2,N3) * nmodes of the instance
   float k2;           // -log2(e) / (2 sigma^2)
   int soff;           // first global state of the instance
-  int pad;
+  int ns;             // states of the instance
+  long long doff;     // dense form: first (state, partner, branch) slot of the instance
+  int npp, nm;        // dense form: partner slots per state (ns rounded up to 32), branches
 };
 
 template <int MODE>
@@ -83,6 +85,111 @@ __global__ void __launch_bounds__(512) k_stream_gbatch(const Item *__restrict__ 
   }
 }
 
+// Dense pair-major form of the FP32 batch sweep (as k_stream_g_dense, per instance): every
+// instance keeps |g|^2 in one slot per (state, partner, branch), g2d[doff + (s * npp + p) * nm
+// + nu], zero where no channel exists, so no index is streamed.  An item is a run of partners
+// [I.start, I.start + I.len) of the global row I.row; partner records come through L1 (each CTA
+// takes a contiguous item range, mostly of one instance).  The per-pair arithmetic is
+// k_stream_g_dense's (the bracket collected per pair).
+__global__ void __launch_bounds__(512, 2) k_stream_gbatch_dense(const Item *__restrict__ items,
+                                                             const int *__restrict__ item_inst, int nitems,
+                                                             const BInst *__restrict__ inst,
+                                                             const float *__restrict__ g2d,
+                                                             const uint4 *__restrict__ gstate,
+                                                             Part4 *__restrict__ part) {
+  const int per = (nitems + gridDim.x - 1) / gridDim.x;
+  const int begin = blockIdx.x * per;
+  const int end = min(nitems, begin + per);
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int it = begin + wib; it < end; it += nw) {
+    const Item I = items[it];
+    const BInst B = inst[item_inst[it]];
+    const uint4 ss = __ldg(gstate + I.row);
+    const int base = B.cpad - rec_lnm(ss);
+    const uint4 *__restrict__ gsi = gstate + B.soff;
+    const int nm = B.nm;
+    const float *__restrict__ gr = g2d + B.doff + (long long)(I.row - B.soff) * B.npp * nm;
+    const float fs = __uint_as_float(ss.z), fsl = rec_f_lo(ss), es = __uint_as_float(ss.x), esl = rec_eps_lo(ss);
+    float sum = 0.f, comp = 0.f;
+    for (int j = lane; j < I.len; j += 32) {
+      const int p = (int)I.start + j;
+      if (p >= B.ns) break;
+      const uint4 sp = __ldg(gsi + p);
+      const float dh = __fsub_rn(es, __uint_as_float(sp.x));
+      const float dl = __fsub_rn(esl, rec_eps_lo(sp));
+      const float fp = __uint_as_float(sp.z), fpl = rec_f_lo(sp);
+      const float P = fs * fp, A = fs - P, Bq = fp - P;
+      const float delta = fmaf(fsl, fp, fpl * fs);
+      const float alpha = (fs - fp) + (fsl - fpl);
+      const float betap = (A + fsl) - delta, gammap = (Bq + fpl) - delta;
+      const float2 *__restrict__ tr = B.tab + (base + rec_lnm(sp));
+      const float *__restrict__ gq = gr + (long long)p * nm;
+      auto term = [&](float gv, float2 t) {
+        const float a = (dh + t.x) + dl;  // x + w
+        const float e = (dh - t.x) + dl;  // x - w
+        const float Ga = ex2_approx(a * a * B.k2);
+        const float Ge = ex2_approx(e * e * B.k2);
+        const float na = alpha * t.y;
+        return gv * fmaf(Ge, na + betap, Ga * (na - gammap));
+      };
+      float acc = 0.f;
+      if (nm <= kDenseBranches) {
+        // the pair's loads first; even nm: slot offsets are even (npp is a multiple of 32)
+        float gv[kDenseBranches];
+        float2 tv[kDenseBranches];
+        if ((nm & 1) == 0) {
+#pragma unroll
+          for (int k = 0; k < kDenseBranches / 2; ++k)
+            if (2 * k < nm) {
+              const float2 v = __ldcs(reinterpret_cast<const float2 *>(gq) + k);
+              gv[2 * k] = v.x;
+              gv[2 * k + 1] = v.y;
+            }
+        } else {
+#pragma unroll
+          for (int nu = 0; nu < kDenseBranches; ++nu)
+            if (nu < nm) gv[nu] = __ldcs(gq + nu);
+        }
+#pragma unroll
+        for (int nu = 0; nu < kDenseBranches; ++nu)
+          if (nu < nm) tv[nu] = __ldg(tr + nu);
+#pragma unroll
+        for (int nu = 0; nu < kDenseBranches; ++nu)
+          if (nu < nm) acc += term(gv[nu], tv[nu]);
+      } else {
+        for (int nu = 0; nu < nm; ++nu) acc += term(__ldcs(gq + nu), __ldg(tr + nu));
+      }
+      kahan_add(sum, comp, acc);
+    }
+    const double v = warp_sum_ff(make_float2(sum, -comp));
+    if (lane == 0) part[it] = make_part4(v, 0.0, 0.0, 0.0);
+  }
+}
+
+// g2d slots of every stored channel of the batch (the array is cleared before)
+__global__ void __launch_bounds__(kBlock) k_dense_g2_batch(const Item *__restrict__ items,
+                                                           const int *__restrict__ item_inst, int nitems,
+                                                           const BInst *__restrict__ inst,
+                                                           const uint32_t *__restrict__ col,
+                                                           const float *__restrict__ g2, float *__restrict__ g2d) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    const BInst B = inst[item_inst[it]];
+    float *__restrict__ gr = g2d + B.doff + (long long)(I.row - B.soff) * B.npp * B.nm;
+    for (int j = lane; j < I.len; j += 32) {
+      const long long c = I.start + j;
+      const float v = g2[c];
+      if (v == 0.f) continue;  // row padding (and channels with |g|^2 = 0, whose slot stays 0)
+      const unsigned cw = col[c];
+      gr[(long long)(cw & 0xFFFFFFu) * B.nm + (cw >> 24)] = v;
+    }
+  }
+}
+
 // I_r = -cs[r] * (row sum); cs = (2 pi / hbar N_q) / (sqrt(2 pi) sigma) of the row's instance.
 // STAGE < 0 writes I; STAGE 0..3 does the RK4 stage arithmetic as k_fin_coll does.
 template <int STAGE>
@@ -130,6 +237,10 @@ struct pb_batch {
   std::vector<int64_t> lenp;       // padded length of every global row
   std::vector<int32_t> row_inst;   // instance of every global row
   std::vector<int64_t> nch;        // [n] stored channels per instance
+  // dense pair-major FP32 form (precision 0): |g|^2 in (state, partner, branch) slots
+  bool dense = false;
+  float *g2d = nullptr;
+  std::vector<int32_t> npp;        // [n] partner slots per state of each instance
   char *arena = nullptr;
   size_t bytes = 0;
   Item *items = nullptr;
@@ -161,14 +272,16 @@ struct BatchPlan {
   std::vector<int32_t> item_inst, item_ptr;
 };
 
-void batch_plan(const pb_batch *b, int item_ch, BatchPlan &P) {
+// dense: rows of npp partner slots, items of item_ch partners, Item.start = first partner
+void batch_plan(const pb_batch *b, int item_ch, BatchPlan &P, bool dense = false) {
   P.items.clear();
   P.item_inst.clear();
   P.item_ptr.assign(b->ns + 1, 0);
   int64_t off = 0;
   for (int64_t r = 0; r < b->ns; ++r) {
     P.item_ptr[r] = (int32_t)P.items.size();
-    const int64_t lenp = b->lenp[r];
+    const int64_t lenp = dense ? b->npp[b->row_inst[r]] : b->lenp[r];
+    if (dense) off = 0;
     if (lenp > 0) {
       const int64_t chunks = lenp / kRowPad;
       const int64_t np = std::max<int64_t>(1, (lenp + item_ch - 1) / item_ch);
@@ -198,14 +311,38 @@ int64_t batch_items_count(const std::vector<int64_t> &lenp, int item_ch) {
   return n;
 }
 
+// Dense pair-major FP32 batch (pb_batch_opts.layout 0 with precision 0): used when the stored
+// channels fill at least 85% of all instances' (state, partner, branch) slots; npp = nstate
+// rounded up to 32.  A dense work item takes item_ch / 4 partners (at least 32).
+int batch_npp(const pb_channels *ch) { return (int)((ch->nstate + 31) / 32 * 32); }
+int64_t batch_dense_slots(const pb_channels *const *chs, int32_t n) {
+  int64_t s = 0;
+  for (int i = 0; i < n; ++i) s += chs[i]->nstate * (int64_t)batch_npp(chs[i]) * chs[i]->nmodes;
+  return s;
+}
+bool batch_dense_for(const pb_channels *const *chs, int32_t n, const pb_batch_opts &o) {
+  if (o.precision != 0 || o.layout != 0) return false;
+  int64_t nch = 0;
+  for (int i = 0; i < n; ++i) nch += chs[i]->nch;
+  return (double)nch >= 0.85 * (double)batch_dense_slots(chs, n);
+}
+int batch_dense_part(int item_ch) { return std::max(32, item_ch / 4 / 8 * 8); }
+std::vector<int64_t> batch_dense_lenp(const pb_channels *const *chs, int32_t n) {
+  std::vector<int64_t> lenp;
+  for (int i = 0; i < n; ++i)
+    for (int64_t r = 0; r < chs[i]->nstate; ++r) lenp.push_back(batch_npp(chs[i]));
+  return lenp;
+}
+
 constexpr int kBatchMinItem = 1024;  // smallest item size the arena is planned for
 
 struct BatchLayout {
   size_t items, item_inst, item_ptr, col, g2, gstate, tabs, inst, cs, part, acc, y, omega_tmp, tab_tmp, eps_tmp,
-      kc_tmp, total;
+      kc_tmp, g2d, total;
 };
 
-BatchLayout batch_layout(const pb_channels *const *chs, int n, int64_t ns, int64_t nchp, int64_t nitems_cap) {
+BatchLayout batch_layout(const pb_channels *const *chs, int n, int64_t ns, int64_t nchp, int64_t nitems_cap,
+                         int64_t dense_slots = 0) {
   BatchLayout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -237,6 +374,7 @@ BatchLayout batch_layout(const pb_channels *const *chs, int n, int64_t ns, int64
   L.tab_tmp = take(sizeof(double2) * maxq);
   L.eps_tmp = take(sizeof(double) * maxs);
   L.kc_tmp = take(sizeof(short4) * maxs);
+  L.g2d = take(sizeof(float) * (size_t)dense_slots);
   L.total = o;
   return L;
 }
@@ -341,9 +479,10 @@ std::vector<int64_t> batch_lenp(const pb_channels *const *chs, int32_t n) {
   return lenp;
 }
 
-int batch_upload_plan(pb_batch *b, int item_ch, cudaStream_t st) {
+int batch_upload_plan(pb_batch *b, int item_ch, cudaStream_t st, bool csr = false) {
   BatchPlan P;
-  batch_plan(b, item_ch, P);
+  const bool dense = b->dense && !csr;
+  batch_plan(b, dense ? batch_dense_part(item_ch) : item_ch, P, dense);
   if ((int64_t)P.items.size() > b->nitems_cap)
     return set_error(PB_EINVAL, "pb_batch: item size %d needs more items than the arena holds", item_ch);
   PB_CUDA(cudaMemcpyAsync(b->items, P.items.data(), sizeof(Item) * P.items.size(), cudaMemcpyHostToDevice, st));
@@ -370,6 +509,12 @@ int batch_sweep(pb_batch *b, cudaStream_t st) {
   }
   const int64_t need = (b->nitems * 32 + 511) / 512;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)b->sm_count * b->ctas));
+  if (b->dense) {
+    pb::dev::k_stream_gbatch_dense<<<grid, 512, 0, st>>>(b->items, b->item_inst, (int)b->nitems, b->inst, b->g2d,
+                                                          b->gstate, b->part);
+    PB_LAUNCHED("k_stream_gbatch_dense");
+    return PB_OK;
+  }
   pb::dev::k_stream_gbatch<dev::MODE_COLL><<<grid, 512, 0, st>>>(b->items, b->item_inst, (int)b->nitems, b->inst,
                                                                  b->col, b->g2, b->gstate, b->part);
   PB_LAUNCHED("k_stream_gbatch");
@@ -554,7 +699,12 @@ extern "C" int pb_batch_arena_bytes(const pb_channels *const *chs, int32_t n, co
       for (int64_t l : lenp) nent += l;
       *bytes = batch_layout_ff(chs, n, ns, nent, batch_items_count(lenp, kBatchMinItem)).total;
     } else {
-      *bytes = batch_layout(chs, n, ns, nchp, batch_items_count(batch_lenp(chs, n), kBatchMinItem)).total;
+      pb_batch_opts o{};
+      if (opts) o = *opts;
+      const bool dense = batch_dense_for(chs, n, o);
+      const int64_t cap = std::max(batch_items_count(batch_lenp(chs, n), kBatchMinItem),
+                                   dense ? batch_items_count(batch_dense_lenp(chs, n), batch_dense_part(kBatchMinItem)) : 0);
+      *bytes = batch_layout(chs, n, ns, nchp, cap, dense ? batch_dense_slots(chs, n) : 0).total;
     }
   } catch (const std::bad_alloc &) {
     return set_error(PB_ENOMEM, "pb_batch_arena_bytes: out of host memory");
@@ -579,6 +729,7 @@ extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const p
     return set_error(PB_EINVAL, "pb_batch_create: item_channels must be 0 or a multiple of 64 >= %d", kBatchMinItem);
   if (o.ctas_per_sm < 0 || o.ctas_per_sm > 4) return set_error(PB_EINVAL, "pb_batch_create: ctas_per_sm must be 0..4");
   if (o.precision < 0 || o.precision > 1) return set_error(PB_EINVAL, "pb_batch: precision must be 0 or 1");
+  if (o.layout < 0 || o.layout > 1) return set_error(PB_EINVAL, "pb_batch: layout must be 0 or 1");
   cudaStream_t st = (cudaStream_t)stream;
   pb_batch *b = new (std::nothrow) pb_batch();
   if (!b) return set_error(PB_ENOMEM, "pb_batch_create: out of host memory");
@@ -591,6 +742,11 @@ extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const p
     b->prec = o.precision;
     b->lenp = b->prec == 1 ? batch_pair_lenp(chs, n) : batch_lenp(chs, n);
     b->nitems_cap = batch_items_count(b->lenp, kBatchMinItem);
+    b->dense = batch_dense_for(chs, n, o);
+    if (b->dense)
+      b->nitems_cap = std::max(b->nitems_cap,
+                               batch_items_count(batch_dense_lenp(chs, n), batch_dense_part(kBatchMinItem)));
+    for (int i = 0; i < n; ++i) b->npp.push_back(batch_npp(chs[i]));
     b->soff.assign(n + 1, 0);
     for (int i = 0; i < n; ++i) {
       b->soff[i + 1] = b->soff[i] + chs[i]->nstate;
@@ -632,7 +788,7 @@ extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const p
       *out = b;
       return PB_OK;
     }
-    const BatchLayout L = batch_layout(chs, n, ns, nchp, b->nitems_cap);
+    const BatchLayout L = batch_layout(chs, n, ns, nchp, b->nitems_cap, b->dense ? batch_dense_slots(chs, n) : 0);
     if (bytes < L.total) {
       delete b;
       return set_error(PB_ENOMEM, "pb_batch_create: arena of %zu bytes is smaller than the %zu needed", bytes, L.total);
@@ -652,6 +808,7 @@ extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const p
     b->part = (Part4 *)(A + L.part);
     b->acc = (double *)(A + L.acc);
     b->y = (double *)(A + L.y);
+    if (b->dense) b->g2d = (float *)(A + L.g2d);
     double *om = (double *)(A + L.omega_tmp);
     double2 *tt = (double2 *)(A + L.tab_tmp);
     double *ep = (double *)(A + L.eps_tmp);
@@ -685,7 +842,10 @@ extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const p
       hin[i].cpad = ((n1 * rad[1] + n2) * rad[2] + n3) * ch->nmodes;
       hin[i].k2 = (float)(-1.4426950408889634 / (2.0 * ch->sigma * ch->sigma));
       hin[i].soff = (int)b->soff[i];
-      hin[i].pad = 0;
+      hin[i].ns = (int)ch->nstate;
+      hin[i].npp = batch_npp(ch);
+      hin[i].nm = ch->nmodes;
+      hin[i].doff = i == 0 ? 0 : hin[i - 1].doff + (long long)chs[i - 1]->nstate * hin[i - 1].npp * hin[i - 1].nm;
       for (int64_t s = 0; s < ch->nstate; ++s) hcs[b->soff[i] + s] = c * norm;
       for (int64_t s = 0; s < ch->nstate; ++s) {
         const int64_t a = ch->row_ptr[s], len = ch->row_ptr[s + 1] - a, lp = b->lenp[b->soff[i] + s];
@@ -731,6 +891,21 @@ extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const p
       if (e == cudaSuccess) e = cudaMemcpyAsync(b->g2, hg2.data(), sizeof(float) * nchp, cudaMemcpyHostToDevice, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) status = cuda_fail(e, "pb_batch_create: upload");
+    }
+    if (status == PB_OK && b->dense) {
+      // the dense slots from the channel list (through the channel plan), then the dense plan
+      cudaError_t e = cudaMemsetAsync(b->g2d, 0, sizeof(float) * (size_t)batch_dense_slots(chs, n), st);
+      if (e != cudaSuccess) status = cuda_fail(e, "pb_batch_create: clear dense slots");
+      if (status == PB_OK) status = batch_upload_plan(b, 2048, st, true);
+      if (status == PB_OK) {
+        const int64_t need = (b->nitems * 32 + dev::kBlock - 1) / dev::kBlock;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)b->sm_count * 8));
+        dev::k_dense_g2_batch<<<grid, dev::kBlock, 0, st>>>(b->items, b->item_inst, (int)b->nitems, b->inst, b->col,
+                                                            b->g2, b->g2d);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) status = cuda_fail(e, "k_dense_g2_batch");
+      }
     }
     if (status == PB_OK) {
       b->ctas = o.ctas_per_sm ? o.ctas_per_sm : 2;

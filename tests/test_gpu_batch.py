@@ -60,6 +60,19 @@ def test_batch_collision_matches_unbatched_and_oracle(pb, batch):
             assert d <= 1e-6 * np.abs(ref).max()
 
 
+def test_batch_layouts_agree(pb, batch):
+    """The dense pair-major FP32 batch (the default on these complete rows) and the form with
+    one entry per channel (layout 1) give the same integral to FP32 rounding."""
+    import torch
+
+    inst, chs, b, f = batch
+    per_channel = pb.Batch(chs, layout=1)
+    ft = torch.tensor(f, device="cuda")
+    a = b.collision(ft).cpu().numpy()
+    c = per_channel.collision(ft).cpu().numpy()
+    assert np.abs(a - c).max() <= 1e-6 * np.abs(c).max()
+
+
 def test_batch_rk4_matches_oracle(pb, batch):
     import torch
 
