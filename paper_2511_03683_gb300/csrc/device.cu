@@ -1313,8 +1313,12 @@ void launch_fin(pb_dev *d, const double *ysrc, double *out, double *f, double dt
         dev::ItemSrc{d->variant == PB_VARIANT_PAPER ? d->t_item_ptr : d->item_ptr, d->part}, (int)d->ns, d->c, d->R, ysrc,
                                                                     out, f, d->acc, y, d->yff, dt);
   else if (d->sym)
-    dev::k_fin_tiles<STAGE><<<(int)((d->ns + dev::kFinTileStates - 1) / dev::kFinTileStates), 256, 0, st>>>(
-        dev::TileSrc{d->tpart, d->td.nb, d->td.nsp}, (int)d->ns, d->c, d->R, ysrc, out, f, d->acc, y, d->yff, dt);
+    if (d->ns <= 2048)  // few states: more, smaller CTAs
+      dev::k_fin_tiles<STAGE, false, 8><<<(int)((d->ns + 7) / 8), 256, 0, st>>>(
+          dev::TileSrc{d->tpart, d->td.nb, d->td.nsp}, (int)d->ns, d->c, d->R, ysrc, out, f, d->acc, y, d->yff, dt);
+    else
+      dev::k_fin_tiles<STAGE><<<(int)((d->ns + 31) / 32), 256, 0, st>>>(
+          dev::TileSrc{d->tpart, d->td.nb, d->td.nsp}, (int)d->ns, d->c, d->R, ysrc, out, f, d->acc, y, d->yff, dt);
   else
     dev::k_fin_coll<false, STAGE><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->item_ptr, d->part}, (int)d->ns, d->c, d->R, ysrc,
                                                                      out, f, d->acc, y, d->yff, dt);
@@ -1515,7 +1519,7 @@ extern "C" int pb_scatter_rates(pb_dev *d, const double *f, double *inv_tau, voi
     dev::k_fin_rate<true><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->fwd_item_ptr(), d->part}, (int)d->ns,
                                                              d->mixed() ? d->c * d->gnorm() : d->c, d->R, inv_tau);
   else if (d->sym)
-    dev::k_fin_tiles<-1, true><<<(int)((d->ns + dev::kFinTileStates - 1) / dev::kFinTileStates), 256, 0, st>>>(
+    dev::k_fin_tiles<-1, true><<<(int)((d->ns + 31) / 32), 256, 0, st>>>(
         dev::TileSrc{d->tpart, d->td.nb, d->td.nsp}, (int)d->ns, d->c, d->R, nullptr, inv_tau, nullptr, nullptr, nullptr,
         nullptr, 0.0);
   else
@@ -1759,8 +1763,12 @@ int vjp_sweep_ff(pb_dev *d, cudaStream_t st) {
 int vjp_fin_ff(pb_dev *d, const double *gbuf, double *mu, const double *acc_in, double *acc_out,
                 const dev::VjpNext &nx, cudaStream_t st) {
   const int ns = (int)d->ns;
-  dev::k_fin_vjp<<<(ns + dev::kFinVjpStates - 1) / dev::kFinVjpStates, 256, 0, st>>>(d->item_ptr, d->part, ns, d->c, d->R, gbuf, mu,
-                                                                         acc_in, acc_out, nx, d->vjpG, -d->c);
+  if (ns <= 2048)  // few states: more, smaller CTAs
+    dev::k_fin_vjp<8><<<(ns + 7) / 8, 256, 0, st>>>(d->item_ptr, d->part, ns, d->c, d->R, gbuf, mu, acc_in, acc_out, nx,
+                                                   d->vjpG, -d->c);
+  else
+    dev::k_fin_vjp<32><<<(ns + 31) / 32, 256, 0, st>>>(d->item_ptr, d->part, ns, d->c, d->R, gbuf, mu, acc_in, acc_out,
+                                                      nx, d->vjpG, -d->c);
   PB_LAUNCHED("k_fin_vjp");
   return PB_OK;
 }

@@ -1592,22 +1592,24 @@ struct VjpNext {
 
 // mu = J^T g from the float-float partials of k_stream_vjp; out = mu if not null; with acc_out
 // also acc_out = acc_in + mu (the running sum of an RK4 step's stage cotangents); nx: see
-// VjpNext.  A 256-thread CTA takes 32 states: each warp adds the item partials of 4 states
-// (lanes over the items, then one 32-lane float-float reduce-scatter of the 16 values), and warp
-// 0 does the FP64 arithmetic of the 32 states at once, one lane per state.
-constexpr int kFinVjpStates = 32;
+// VjpNext.  A 256-thread CTA takes SPC states (8 or 32): each warp adds the item partials of
+// SPC / 8 states (lanes over the items, then one 32-lane float-float reduce-scatter of their
+// 4 values each), and warp 0 does the FP64 arithmetic of the SPC states at once, one lane per
+// state.  Few states (small problems) take SPC = 8 for more CTAs in flight.
+template <int SPC>
 __global__ void __launch_bounds__(256) k_fin_vjp(const int *__restrict__ item_ptr, const Part4 *__restrict__ part,
                                                  int ns, double c, const double *__restrict__ R,
                                                  const double *__restrict__ g, double *__restrict__ out,
                                                  const double *acc_in, double *acc_out,  // acc_in may be acc_out
                                                  VjpNext nx, float2 *__restrict__ G, double scale) {
-  __shared__ float2 tot[kFinVjpStates][4];  // S1..S4 per state
+  constexpr int SPW = SPC / 8, NV = 4 * SPW, LPV = 32 / NV;  // states per warp, values, lanes per value
+  __shared__ float2 tot[SPC][4];  // S1..S4 per state
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int base = blockIdx.x * kFinVjpStates;
+  const int base = blockIdx.x * SPC;
   const int r0 = base + lane;
   // warp 0 loads its state's inputs first, so that their latency overlaps the partials'
   double gr = 0.0, Rr = 0.0, ai = 0.0, fn = 0.0, ln = 0.0;
-  if (wid == 0 && r0 < ns) {
+  if (wid == 0 && lane < SPC && r0 < ns) {
     gr = g[r0];
     Rr = R[r0];
     if (acc_out) ai = acc_in[r0];
@@ -1616,12 +1618,12 @@ __global__ void __launch_bounds__(256) k_fin_vjp(const int *__restrict__ item_pt
       ln = nx.lam[r0];
     }
   }
-  float2 v[16];
+  float2 v[NV];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = make_float2(0.f, 0.f);
+  for (int q = 0; q < NV; ++q) v[q] = make_float2(0.f, 0.f);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int r = base + 4 * wid + q;
+  for (int q = 0; q < SPW; ++q) {
+    const int r = base + SPW * wid + q;
     if (r < ns) {
       for (int i = item_ptr[r] + lane; i < item_ptr[r + 1]; i += 32) {
         const float4 *p = reinterpret_cast<const float4 *>(part + i);
@@ -1633,13 +1635,13 @@ __global__ void __launch_bounds__(256) k_fin_vjp(const int *__restrict__ item_pt
       }
     }
   }
-  ff_reduce_scatter<16, 16>(v, lane);
-  if ((lane & 1) == 0) {
-    const int idx = (lane >> 1) & 15;  // lane bits 4..1: (state q, value)
-    tot[4 * wid + (idx >> 2)][idx & 3] = v[0];
+  ff_reduce_scatter<NV, 16>(v, lane);
+  if ((lane & (LPV - 1)) == 0) {
+    const int idx = lane / LPV;  // the top lane bits: (state q, value)
+    tot[SPW * wid + (idx >> 2)][idx & 3] = v[0];
   }
   __syncthreads();
-  if (wid != 0 || r0 >= ns) return;
+  if (wid != 0 || lane >= SPC || r0 >= ns) return;
   const float2 S1 = tot[lane][0], S2 = tot[lane][1], S3 = tot[lane][2], S4 = tot[lane][3];
   const double mu = c * ((ff_to_double(S1.x, S1.y) + ff_to_double(S2.x, S2.y) - ff_to_double(S3.x, S3.y)) +
                          gr * (ff_to_double(S4.x, S4.y) - Rr));
@@ -2286,29 +2288,30 @@ __global__ void k_fin_coll(SRC src, int ns, double c, const double *__restrict__
 // stage arithmetic in FP64 to the 32 states at once, one lane per state (FP64 instructions
 // cost the same with one active lane as with 32 on this part, so a lane-0-per-state epilogue
 // spent most of its time there).  RATE: 1/tau.
-constexpr int kFinTileStates = 32;
-template <int STAGE, bool RATE = false>
+// SPC states per CTA (8 or 32; few states take 8, for more CTAs in flight)
+template <int STAGE, bool RATE = false, int SPC = 32>
 __global__ void __launch_bounds__(256) k_fin_tiles(TileSrc src, int ns, double c, const double *__restrict__ R,
                                                    const double *__restrict__ ysrc, double *__restrict__ out,
                                                    double *__restrict__ f, double *__restrict__ acc,
                                                    double *__restrict__ y, float2 *__restrict__ yff, double dt) {
-  __shared__ float4 tot[kFinTileStates];  // (A hi, A lo, C hi, C lo) per state
+  constexpr int SPW = SPC / 8, NV = 2 * SPW, LPV = 32 / NV;  // states per warp, values, lanes per value
+  __shared__ float4 tot[SPC];  // (A hi, A lo, C hi, C lo) per state
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int base = blockIdx.x * kFinTileStates;
+  const int base = blockIdx.x * SPC;
   // warp 0 loads its state's epilogue inputs first, so that their latency overlaps the partials'
   const int r0 = base + lane;
   FinIn in{0.0, 0.0, 0.0, 0.0};
-  if (wid == 0 && r0 < ns) {
+  if (wid == 0 && lane < SPC && r0 < ns) {
     if (RATE) in.R = R[r0];
     else in = fin_load<false, STAGE>(r0, R, ysrc, f, acc);
   }
   // partials are stored for every padded state (r < nsp); the first three of every lane for
-  // the warp's 4 states are loaded together (up to 96 partner blocks), the rest after
+  // the warp's states are loaded together (up to 96 partner blocks), the rest after
   const int nb = src.nb;
-  float4 w[4][3];
+  float4 w[SPW][3];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int r = base + 4 * wid + q;
+  for (int q = 0; q < SPW; ++q) {
+    const int r = base + SPW * wid + q;
     const float4 *__restrict__ row = src.tp + (long long)r * nb;
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
@@ -2316,9 +2319,9 @@ __global__ void __launch_bounds__(256) k_fin_tiles(TileSrc src, int ns, double c
       w[q][m] = r < src.nsp && k < nb ? row[k] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
-  float2 v[8];
+  float2 v[NV];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < SPW; ++q) {
     v[2 * q] = make_float2(w[q][0].x, w[q][0].y);
     v[2 * q + 1] = make_float2(w[q][0].z, w[q][0].w);
 #pragma unroll
@@ -2326,7 +2329,7 @@ __global__ void __launch_bounds__(256) k_fin_tiles(TileSrc src, int ns, double c
       v[2 * q] = ff_add(v[2 * q], make_float2(w[q][m].x, w[q][m].y));
       v[2 * q + 1] = ff_add(v[2 * q + 1], make_float2(w[q][m].z, w[q][m].w));
     }
-    const int r = base + 4 * wid + q;
+    const int r = base + SPW * wid + q;
     if (r < src.nsp) {
       const float4 *__restrict__ row = src.tp + (long long)r * nb;
       for (int k = lane + 96; k < nb; k += 32) {
@@ -2336,15 +2339,15 @@ __global__ void __launch_bounds__(256) k_fin_tiles(TileSrc src, int ns, double c
       }
     }
   }
-  ff_reduce_scatter<8, 16>(v, lane);
-  if ((lane & 3) == 0) {
-    const int idx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);  // (state q, A | C)
-    float *t = reinterpret_cast<float *>(tot + 4 * wid + (idx >> 1)) + 2 * (idx & 1);
+  ff_reduce_scatter<NV, 16>(v, lane);
+  if ((lane & (LPV - 1)) == 0) {
+    const int idx = lane / LPV;  // the top lane bits: (state q, A | C)
+    float *t = reinterpret_cast<float *>(tot + SPW * wid + (idx >> 1)) + 2 * (idx & 1);
     t[0] = v[0].x;
     t[1] = v[0].y;
   }
   __syncthreads();
-  if (wid != 0 || r0 >= ns) return;
+  if (wid != 0 || lane >= SPC || r0 >= ns) return;
   const float4 T = tot[lane];
   const double A = ff_to_double(T.x, T.y), B = ff_to_double(T.z, T.w) - A;
   if (RATE)
