@@ -374,6 +374,26 @@ def test_mixed_precision_sweep_shapes(pb, variant, shape):
     assert nrel(dev.rates(T(f)).cpu().numpy(), o.rates(f)) <= MIXED_TOL[variant]
 
 
+@pytest.mark.parametrize("variant", ["g32", "g16"])
+def test_mixed_precision_set_g2_refreshes_dense_slots(pb, variant):
+    """pb_dev_set_g2 on a dense pair-major device rewrites the (state, partner, branch) slots:
+    Eq. 2 is linear in |g|^2, so doubling every |g|^2 doubles the integral (a factor of two
+    commutes with rounding to FP32 and BF16, so only the summation order differs)."""
+    import torch
+
+    m = SMALL["win16"]()
+    ch = pb.Channels.from_model(m)
+    dev = pb.Device(ch, variant=variant)
+    f = T(np.random.default_rng(4).uniform(0, 1, dev.nstate))
+    I0 = dev.collision(f).cpu().numpy()
+    g2 = torch.tensor(ch.export()["g2"], dtype=torch.float64, device="cuda")
+    dev.set_g2(2.0 * g2)
+    I1 = dev.collision(f).cpu().numpy()
+    assert np.abs(I1 - 2.0 * I0).max() <= 1e-6 * np.abs(I0).max()
+    dev.set_g2(g2)
+    assert np.abs(dev.collision(f).cpu().numpy() - I0).max() <= 1e-7 * np.abs(I0).max()
+
+
 @pytest.mark.parametrize("shape", [0, 5])
 def test_mixed_precision_with_cutoffs(pb, shape):
     """With the |g| and delta cutoffs on, the channel list fills few (row, branch, partner)
