@@ -190,6 +190,9 @@ typedef struct pb_dev_opts {
                                 2 one persistent CTA per SM with 256 threads keeps three tiles in flight in
                                 shared memory through TMA bulk copies (cp.async.bulk, mbarrier-counted),
                                 its bounded waits reporting through pb_dev_check */
+  int32_t adjoint;           /* nonzero: reserve one float-float accumulator pair per state pair (16 bytes)
+                                for the deferred |g|^2 gradient of pb_rtbte_rk4_vjp_defer (FF variant,
+                                branch-merged; ignored otherwise) */
 } pb_dev_opts;
 
 typedef struct pb_dev pb_dev; /* opaque host handle describing device-resident data */
@@ -300,6 +303,17 @@ int pb_collision_vjp(pb_dev *dev, const double *f, const double *lam, double *gr
  * dL/df_{n+1}, on return dL/df_n; grad_g2 (or NULL) accumulates dL/dg2 as above.  The four
  * stage inputs are recomputed from f. */
 int pb_rtbte_rk4_vjp(pb_dev *dev, const double *f, double *lam, double dt, double *grad_g2, void *stream);
+
+/* The same RK4 adjoint step with the |g|^2 gradient deferred: instead of updating every stored
+ * channel, the step adds the two stage sums that the gradient of a state pair needs (the
+ * pair's branches share them) into the handle's per-pair accumulators; pb_dev_g2grad_flush
+ * applies them.  Needs a device created with pb_dev_opts.adjoint on the FF variant with
+ * branch merging (PB_EINVAL otherwise). */
+int pb_rtbte_rk4_vjp_defer(pb_dev *dev, const double *f, double *lam, double dt, void *stream);
+
+/* grad_g2 (device double[nchannels], CSR order) += the |g|^2 gradient accumulated by
+ * pb_rtbte_rk4_vjp_defer since the last flush; the accumulators are cleared. */
+int pb_dev_g2grad_flush(pb_dev *dev, double *grad_g2, void *stream);
 
 /* Replace the device |g|^2 (device double[nchannels], CSR order of pb_channels_export) and
  * recompute the per-channel coefficients.  The two stored copies of a channel (under each of

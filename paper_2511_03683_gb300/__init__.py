@@ -57,7 +57,7 @@ class _DevOpts(ctypes.Structure):
                 ("transport", ctypes.c_int32), ("transport_gather", ctypes.c_int32),
                 ("transport_ctas", ctypes.c_int32), ("channel_per_lane", ctypes.c_int32),
                 ("stream_mode", ctypes.c_int32), ("merge_branches", ctypes.c_int32), ("dense_rows", ctypes.c_int32),
-                ("tile_sweep", ctypes.c_int32)]
+                ("tile_sweep", ctypes.c_int32), ("adjoint", ctypes.c_int32)]
 
 
 class _DevInfo(ctypes.Structure):
@@ -131,6 +131,8 @@ def lib() -> ctypes.CDLL:
         "pb_batch_rk4_step": [vp, vp, dbl, i32, vp],
         "pb_batch_autotune": [vp, vp, vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(dbl)],
         "pb_rtbte_rk4_vjp": [vp, vp, vp, dbl, vp, vp],
+        "pb_rtbte_rk4_vjp_defer": [vp, vp, vp, dbl, vp],
+        "pb_dev_g2grad_flush": [vp, vp, vp],
         "pb_dev_set_g2": [vp, vp, vp],
     }
     for name, args in sig.items():
@@ -278,7 +280,7 @@ class Device:
     def __init__(self, channels: Channels, variant: str = "ff", item_channels: int = 0, ctas_per_sm: int = 0,
                  transport: bool = False, transport_gather: int = 0, transport_ctas: int = 0,
                  channel_per_lane: int = 0, stream_mode: int = 0, merge_branches: int = 0, dense_rows: int = 0,
-                 tile_sweep: int = 0, stream=None):
+                 tile_sweep: int = 0, adjoint: bool = False, stream=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -287,9 +289,11 @@ class Device:
         self.variant = variant
         # FF/F64 stream one entry per state pair unless merge_branches == 2
         self.merged = variant in ("ff", "f64") and int(merge_branches) != 2
+        # per-pair accumulators of the deferred |g|^2 gradient (rk4_vjp_defer / g2grad_flush)
+        self.deferred = bool(adjoint) and variant == "ff" and self.merged
         o = _DevOpts(VARIANTS[variant], int(item_channels), int(ctas_per_sm), 1 if transport else 0,
                      int(transport_gather), int(transport_ctas), int(channel_per_lane), int(stream_mode),
-                     int(merge_branches), int(dense_rows), int(tile_sweep))
+                     int(merge_branches), int(dense_rows), int(tile_sweep), 1 if adjoint else 0)
         nbytes = ctypes.c_size_t(0)
         _check(lib().pb_dev_arena_bytes(channels._h, ctypes.byref(o), ctypes.byref(nbytes)))
         self.arena = torch.empty(int(nbytes.value), dtype=torch.uint8, device="cuda")
@@ -418,6 +422,19 @@ class Device:
         _check(lib().pb_rtbte_rk4_vjp(self._h, _dev_vec(f, self.nstate, "f"), _dev_vec(lam, self.nstate, "lam"),
                                       float(dt), gp, _stream_ptr(stream)))
         return lam
+
+    def rk4_vjp_defer(self, f, lam, dt, stream=None):
+        """rk4_vjp whose |g|^2 gradient goes to the device's per-pair accumulators (a device
+        made with adjoint=True); g2grad_flush adds it to a gradient vector."""
+        _check(lib().pb_rtbte_rk4_vjp_defer(self._h, _dev_vec(f, self.nstate, "f"),
+                                            _dev_vec(lam, self.nstate, "lam"), float(dt), _stream_ptr(stream)))
+        return lam
+
+    def g2grad_flush(self, grad_g2, stream=None):
+        """grad_g2 (CUDA double[nchannels], CSR order) += the deferred |g|^2 gradient; clears it."""
+        _check(lib().pb_dev_g2grad_flush(self._h, _dev_vec(grad_g2, self.nchannels, "grad_g2"),
+                                         _stream_ptr(stream)))
+        return grad_g2
 
     def set_g2(self, g2, stream=None):
         """Replace |g|^2 (CUDA double[nchannels], CSR order) and recompute the coefficients."""

@@ -5,7 +5,9 @@ df/dt = I[f] (Eq. 2, Eq. 1 with no field) as a differentiable function of the in
 occupations f0 and of the couplings |g|^2 (one entry per stored channel, in the CSR order
 of ``Channels.export``).  The forward pass keeps f every ``every`` steps; the backward pass
 recomputes each segment from its checkpoint and applies ``pb_rtbte_rk4_vjp`` step by step
-in reverse.  Every arithmetic step runs in libpb.so; this module only orders the calls.
+in reverse.  On a device made with adjoint=True the steps only accumulate the two stage sums
+per state pair that dL/d|g|^2 needs, and one flush at the end spreads them over the channels.
+Every arithmetic step runs in libpb.so; this module only orders the calls.
 """
 from __future__ import annotations
 
@@ -41,7 +43,12 @@ class _Trajectory(torch.autograd.Function):
                 dev.rk4(y, dt, 1)
                 states.append(y.clone())
             for k in reversed(range(m)):
-                dev.rk4_vjp(states[k], lam, dt, grad_g2=gg2)
+                if gg2 is not None and dev.deferred:
+                    dev.rk4_vjp_defer(states[k], lam, dt)
+                else:
+                    dev.rk4_vjp(states[k], lam, dt, grad_g2=gg2)
+        if gg2 is not None and dev.deferred:
+            dev.g2grad_flush(gg2)
         return lam, gg2, None, None, None, None
 
 

@@ -29,7 +29,7 @@ struct Layout {
   size_t rp, item_ptr, items, col, coefA, coefB, g2, wt, eps, kc, R, omega, tab, part, acc, y, yff, fstage, Fa, Fb,
       Fff, tau, invtau, red, scal, obs, g2lo, gstate, tab32, col16, rp_real, vjpG, g2tab, vecs, hcol, hg2, hA, hB, sc,
       entries, hitems, titems, t_item_ptr, err, citems, citem_ptr, cpart, ccoefA, ccoefB, sidx16, sidx32, pcstart,
-      pcnt, srp, gitems, tiles, tcoef, tpart, g2d, gditems, gdptr, total;
+      pcnt, srp, gitems, tiles, tcoef, tpart, g2d, gditems, gdptr, gacc, total;
 };
 
 struct Plan {
@@ -192,7 +192,7 @@ TileDims tile_dims(int64_t ns) {
 }
 
 Layout make_layout(const pb_channels *ch, const Plan &P, const Plan *S, int variant, bool transport,
-                   int nfin_blocks, bool sym = false, const GDense &gd = GDense()) {
+                   int nfin_blocks, bool sym = false, const GDense &gd = GDense(), bool gacc = false) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -221,6 +221,7 @@ Layout make_layout(const pb_channels *ch, const Plan &P, const Plan *S, int vari
   L.pcnt = take(S ? nsw : 0);
   L.srp = take(S ? sizeof(int64_t) * (ns + 1) : 0);
   L.gitems = take(S ? sizeof(Item) * (size_t)grad_chunks(S->rp) : 0);
+  L.gacc = take(S && gacc ? sizeof(float4) * nsw : 0);
   const TileDims td = tile_dims((int64_t)ns);
   L.tiles = take(sym ? sizeof(int2) * td.nt : 0);
   L.tcoef = take(sym ? sizeof(float4) * (size_t)td.nt * dev::kTile * dev::kTile : 0);
@@ -399,6 +400,7 @@ struct pb_dev {
   bool dense = false;
   int64_t *srp = nullptr;         // first sweep entry of every row [ns+1]
   Item *gitems = nullptr;         // the sweep rows in pieces of <= 32 entries (|g|^2 gradient)
+  float4 *gacc = nullptr;         // deferred |g|^2 gradient: (u, v) float-float per sweep entry
   int ngitems = 0;
   // symmetric tiles (complete rows, FF): the collision and rate sweeps stream the upper block
   // triangle of the pair matrix once and add each tile to its rows and to its columns
@@ -495,6 +497,7 @@ int resolve_opts(const pb_channels *ch, const pb_dev_opts *opts, int sm_count, p
   if (d.merge_branches < 0 || d.merge_branches > 2) return set_error(PB_EINVAL, "pb_dev: merge_branches must be 0..2");
   if (d.dense_rows < 0 || d.dense_rows > 3) return set_error(PB_EINVAL, "pb_dev: dense_rows must be 0..3");
   if (d.tile_sweep < 0 || d.tile_sweep > 2) return set_error(PB_EINVAL, "pb_dev: tile_sweep must be 0..2");
+  if (d.adjoint < 0 || d.adjoint > 1) return set_error(PB_EINVAL, "pb_dev: adjoint must be 0 or 1");
   if (d.tile_sweep == 0) d.tile_sweep = 2;
   // measured best on GB300 at 40^3: 3 CTAs per SM for one entry per channel, 4 for the
   // branch-merged sweep (whose stream is six times shorter)
@@ -682,7 +685,8 @@ extern "C" int pb_dev_arena_bytes(const pb_channels *ch, const pb_dev_opts *opts
     const bool merged = make_plans(ch, opts, o, sm, P, S, &complete);
     const int nfin = (int)((P.ns + kFinBlock - 1) / kFinBlock);
     *bytes = make_layout(ch, P, merged ? &S : nullptr, o.variant, o.transport != 0, nfin,
-                         sym_for(o, merged, complete), gdense_for(ch, o, sm)).total;
+                         sym_for(o, merged, complete), gdense_for(ch, o, sm),
+                         o.adjoint != 0 && o.variant == PB_VARIANT_FF).total;
   } catch (const std::bad_alloc &) {
     return set_error(PB_ENOMEM, "pb_dev_arena_bytes: out of host memory");
   }
@@ -750,7 +754,8 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->gd_npp = gd.npp;
   d->gd_nitems = (int)gd.nitems;
   d->gd_bytes = gd.bytes;
-  d->L = make_layout(ch, P, merged ? &S : nullptr, o.variant, d->transport, d->nfin_blocks, d->sym, gd);
+  d->L = make_layout(ch, P, merged ? &S : nullptr, o.variant, d->transport, d->nfin_blocks, d->sym, gd,
+                     o.adjoint != 0 && o.variant == PB_VARIANT_FF);
   if (arena_bytes < d->L.total) {
     const size_t need = d->L.total;
     delete d;
@@ -821,6 +826,7 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
     d->pcnt = (uint8_t *)(A + L.pcnt);
     d->srp = (int64_t *)(A + L.srp);
     d->gitems = (Item *)(A + L.gitems);
+    if (d->variant == PB_VARIANT_FF && o.adjoint) d->gacc = (float4 *)(A + L.gacc);
     if (d->sym) {
       d->tiles = (int2 *)(A + L.tiles);
       d->tcoef = (float4 *)(A + L.tcoef);
@@ -944,6 +950,13 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
         }
       }
       UP(d->rp, P.rp.data(), sizeof(int64_t) * (d->ns + 1));
+      if (d->gacc) {
+        cudaError_t e_ = cudaMemsetAsync(d->gacc, 0, sizeof(float4) * (size_t)d->nsw, st);
+        if (e_ != cudaSuccess) {
+          status = cuda_fail(e_, "clear the gradient accumulators");
+          break;
+        }
+      }
       if (d->gdense) {
         std::vector<int64_t> rpd((size_t)d->ns + 1);
         for (int64_t r = 0; r <= d->ns; ++r) rpd[r] = r * gd.npp;
@@ -1790,8 +1803,8 @@ int g2grad_launch(pb_dev *d, double *grad_g2, cudaStream_t st) {
     const int n = d->ngitems;
     const int gg = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, (int64_t)d->sm_count * dev::kGradCtas));
     const long long *pcs = (const long long *)d->pcstart;
-    if (d->sidx16) dev::k_g2grad_pairs<NST, uint16_t><<<gg, dev::kBlock, 0, st>>>(d->gitems, n, d->sidx16, pcs, d->pcnt, rp, rr, A, B, d->g2tab, ns, grad_g2);
-    else           dev::k_g2grad_pairs<NST, uint32_t><<<gg, dev::kBlock, 0, st>>>(d->gitems, n, d->sidx32, pcs, d->pcnt, rp, rr, A, B, d->g2tab, ns, grad_g2);
+    if (d->sidx16) dev::k_g2grad_pairs<NST, uint16_t><<<gg, dev::kBlock, 0, st>>>(d->gitems, n, d->sidx16, pcs, d->pcnt, rp, rr, A, B, d->g2tab, ns, grad_g2, d->gacc);
+    else           dev::k_g2grad_pairs<NST, uint32_t><<<gg, dev::kBlock, 0, st>>>(d->gitems, n, d->sidx32, pcs, d->pcnt, rp, rr, A, B, d->g2tab, ns, grad_g2, d->gacc);
     PB_LAUNCHED("k_g2grad_pairs");
     return PB_OK;
   }
@@ -1799,6 +1812,29 @@ int g2grad_launch(pb_dev *d, double *grad_g2, cudaStream_t st) {
   if (d->col16) dev::k_g2grad<NST, uint16_t><<<gg, dev::kBlock, 0, st>>>(d->citems, nc, rp, rr, A, B, d->col16, d->g2, d->g2tab, ns, grad_g2);
   else          dev::k_g2grad<NST, uint32_t><<<gg, dev::kBlock, 0, st>>>(d->citems, nc, rp, rr, A, B, d->col, d->g2, d->g2tab, ns, grad_g2);
   PB_LAUNCHED("k_g2grad");
+  return PB_OK;
+}
+
+// the deferred form: the NST stages' pair sums into the accumulators (branch-merged FF devices)
+template <int NST>
+int g2acc_launch(pb_dev *d, cudaStream_t st) {
+  const int n = d->ngitems, ns = (int)d->ns;
+  const int gg = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, (int64_t)d->sm_count * 8));
+  if (d->sidx16) dev::k_g2acc_pairs<NST, uint16_t><<<gg, dev::kBlock, 0, st>>>(d->gitems, n, d->sidx16, d->pcnt, d->g2tab, ns, d->gacc);
+  else           dev::k_g2acc_pairs<NST, uint32_t><<<gg, dev::kBlock, 0, st>>>(d->gitems, n, d->sidx32, d->pcnt, d->g2tab, ns, d->gacc);
+  PB_LAUNCHED("k_g2acc_pairs");
+  return PB_OK;
+}
+
+// grad_g2 += the accumulated pair sums applied to the pairs' channels (accumulators cleared)
+int g2flush_launch(pb_dev *d, double *grad_g2, cudaStream_t st) {
+  const int n = d->ngitems, ns = (int)d->ns;
+  const int gg = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, (int64_t)d->sm_count * dev::kGradCtas));
+  const long long *rp = (const long long *)d->rp, *rr = (const long long *)d->rp_real, *pcs = (const long long *)d->pcstart;
+  const float2 *A = (const float2 *)d->ccoefA, *B = (const float2 *)d->ccoefB;
+  if (d->sidx16) dev::k_g2grad_pairs<0, uint16_t><<<gg, dev::kBlock, 0, st>>>(d->gitems, n, d->sidx16, pcs, d->pcnt, rp, rr, A, B, d->g2tab, ns, grad_g2, d->gacc);
+  else           dev::k_g2grad_pairs<0, uint32_t><<<gg, dev::kBlock, 0, st>>>(d->gitems, n, d->sidx32, pcs, d->pcnt, rp, rr, A, B, d->g2tab, ns, grad_g2, d->gacc);
+  PB_LAUNCHED("k_g2grad_pairs");
   return PB_OK;
 }
 
@@ -1831,13 +1867,11 @@ extern "C" int pb_collision_vjp(pb_dev *d, const double *f, const double *lam, d
   return g2grad_launch<1>(d, grad_g2, st);
 }
 
-extern "C" int pb_rtbte_rk4_vjp(pb_dev *d, const double *f, double *lam, double dt, double *grad_g2, void *stream) {
-  clear_error();
-  if (!d || !f || !lam) return set_error(PB_EINVAL, "pb_rtbte_rk4_vjp: null argument");
-  if (d->variant != PB_VARIANT_FF && !d->mixed())
-    return set_error(PB_EINVAL, "pb_rtbte_rk4_vjp: needs the FF, G32 or G16 variant");
-  if (!std::isfinite(dt)) return set_error(PB_EINVAL, "pb_rtbte_rk4_vjp: bad dt");
+namespace {
+// one RK4 adjoint step; defer: the |g|^2 gradient goes to the pair accumulators (FF merged)
+int rk4_vjp_impl(pb_dev *d, const double *f, double *lam, double dt, double *grad_g2, bool defer, void *stream) {
   cudaStream_t st = (cudaStream_t)stream;
+  const bool want_g2 = grad_g2 || defer;
   const int64_t ns = d->ns;
   double *u2 = d->vecs, *u3 = u2 + ns, *u4 = u3 + ns, *acc = u4 + ns, *ga = acc + ns, *gb = ga + ns, *mu0 = gb + ns,
          *mu1 = mu0 + ns;
@@ -1870,19 +1904,49 @@ extern "C" int pb_rtbte_rk4_vjp(pb_dev *d, const double *f, double *lam, double 
   } else {
     // each stage's finaliser prepares the next stage's cotangent (g alternates ga, gb)
     double *gc = ga, *gn = gb;
-    if ((rc = vjp_prep_ff(d, U[3], lam, wl[3], nullptr, 0.0, gc, grad_g2 ? 3 : -1, st))) return rc;
+    if ((rc = vjp_prep_ff(d, U[3], lam, wl[3], nullptr, 0.0, gc, want_g2 ? 3 : -1, st))) return rc;
     for (int j = 3; j >= 0; --j) {
       if ((rc = vjp_sweep_ff(d, st))) return rc;
       dev::VjpNext nx{};
       if (j > 0) nx = dev::VjpNext{U[j - 1], lam, wl[j - 1], wm[j - 1], gn,
-                                   grad_g2 ? d->g2tab + 2 * (size_t)(j - 1) * ns : nullptr};
+                                   want_g2 ? d->g2tab + 2 * (size_t)(j - 1) * ns : nullptr};
       // the last stage writes dL/df = lam + sum mu over lam (every read of lam precedes it)
       if ((rc = vjp_fin_ff(d, gc, nullptr, j == 3 ? lam : acc, j == 0 ? lam : acc, nx, st))) return rc;
       std::swap(gc, gn);
     }
   }
+  if (defer) return g2acc_launch<4>(d, st);
   if (grad_g2 && (rc = g2grad_launch<4>(d, grad_g2, st))) return rc;
   return PB_OK;
+}
+
+int rk4_vjp_check(pb_dev *d, const double *f, const double *lam, double dt, const char *who) {
+  if (!d || !f || !lam) return set_error(PB_EINVAL, "%s: null argument", who);
+  if (d->variant != PB_VARIANT_FF && !d->mixed())
+    return set_error(PB_EINVAL, "%s: needs the FF, G32 or G16 variant", who);
+  if (!std::isfinite(dt)) return set_error(PB_EINVAL, "%s: bad dt", who);
+  return PB_OK;
+}
+}  // namespace
+
+extern "C" int pb_rtbte_rk4_vjp(pb_dev *d, const double *f, double *lam, double dt, double *grad_g2, void *stream) {
+  clear_error();
+  if (int rc = rk4_vjp_check(d, f, lam, dt, "pb_rtbte_rk4_vjp")) return rc;
+  return rk4_vjp_impl(d, f, lam, dt, grad_g2, false, stream);
+}
+
+extern "C" int pb_rtbte_rk4_vjp_defer(pb_dev *d, const double *f, double *lam, double dt, void *stream) {
+  clear_error();
+  if (int rc = rk4_vjp_check(d, f, lam, dt, "pb_rtbte_rk4_vjp_defer")) return rc;
+  if (!d->gacc) return set_error(PB_EINVAL, "pb_rtbte_rk4_vjp_defer: needs a branch-merged FF device created with adjoint = 1");
+  return rk4_vjp_impl(d, f, lam, dt, nullptr, true, stream);
+}
+
+extern "C" int pb_dev_g2grad_flush(pb_dev *d, double *grad_g2, void *stream) {
+  clear_error();
+  if (!d || !grad_g2) return set_error(PB_EINVAL, "pb_dev_g2grad_flush: null argument");
+  if (!d->gacc) return set_error(PB_EINVAL, "pb_dev_g2grad_flush: the device keeps no gradient accumulators");
+  return g2flush_launch(d, grad_g2, (cudaStream_t)stream);
 }
 
 extern "C" int pb_dev_set_g2(pb_dev *d, const double *g2, void *stream) {

@@ -1724,7 +1724,8 @@ __global__ void __launch_bounds__(kBlock) k_g2grad(const Item *__restrict__ item
 // one partner, from pcstart; padding entries have none), whose channels form one contiguous
 // range of the row.  The warp walks that range with coalesced loads, kUnr trips' loads issued
 // together; each channel finds the lane of its entry by a binary search over the lanes'
-// first-channel offsets and takes u, v from it by shuffles.
+// first-channel offsets and takes u, v from it by shuffles.  NST = 0: u, v come from the pair
+// accumulators of the deferred gradient (k_g2acc_pairs), which are cleared once read.
 constexpr int kWarpChunk = 32;
 constexpr int kGradCtas = 3;  // resident CTAs per SM of k_g2grad_pairs (its persistent grid)
 template <int NST, typename IDX>
@@ -1737,7 +1738,8 @@ __global__ void __launch_bounds__(kBlock, kGradCtas) k_g2grad_pairs(const Item *
                                                                     const float2 *__restrict__ A,
                                                                     const float2 *__restrict__ B,
                                                                     const float4 *__restrict__ tab, int ns,
-                                                                    double *__restrict__ grad) {
+                                                                    double *__restrict__ grad,
+                                                                    float4 *__restrict__ gacc = nullptr) {
   constexpr int kUnr = 3;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1751,7 +1753,14 @@ __global__ void __launch_bounds__(kBlock, kGradCtas) k_g2grad_pairs(const Item *
     double *__restrict__ gr = grad + (rp_real[r] - rp_pad[r]);  // channel position -> unpadded index
     const long long cs = m ? pcstart[q] : 0;
     float uh = 0.f, ul = 0.f, vh = 0.f, vl = 0.f;
-    if (m) {
+    if (m && NST == 0) {
+      const float4 a = gacc[q];
+      uh = a.x;
+      ul = a.y;
+      vh = a.z;
+      vl = a.w;
+      gacc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else if (m) {
       const int p = (int)sidx[q];
 #pragma unroll
       for (int j = 0; j < NST; ++j) {
@@ -1799,6 +1808,38 @@ __global__ void __launch_bounds__(kBlock, kGradCtas) k_g2grad_pairs(const Item *
         }
       }
     }
+  }
+}
+
+// Deferred |g|^2 gradient of branch-merged devices: the NST stages' sums u, v of every state
+// pair (as k_g2grad_pairs forms them) added into the pair's float-float accumulators
+// gacc[q] = (u hi, u lo, v hi, v lo); k_g2grad_pairs<0> later applies the accumulated sums to
+// the pair's channels once and clears them.  Lane per sweep entry of a piece (padding: none).
+template <int NST, typename IDX>
+__global__ void __launch_bounds__(kBlock) k_g2acc_pairs(const Item *__restrict__ items, int nitems,
+                                                        const IDX *__restrict__ sidx, const uint8_t *__restrict__ pcnt,
+                                                        const float4 *__restrict__ tab, int ns,
+                                                        float4 *__restrict__ gacc) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    const long long q = I.start + lane;
+    if (lane >= I.len || pcnt[q] == 0) continue;
+    const int r = I.row, p = (int)sidx[q];
+    float uh = 0.f, ul = 0.f, vh = 0.f, vl = 0.f;
+#pragma unroll
+    for (int j = 0; j < NST; ++j) {
+      const float4 rc = tab[2 * (j * ns + r)];
+      const float4 t = __ldg(tab + 2 * (j * ns + p) + 1);
+      ff_mac_lazy(uh, ul, make_float2(rc.x, rc.y), t.z, t.w);
+      ff_mac_lazy(vh, vl, make_float2(rc.z, rc.w), t.x, t.y);
+    }
+    float4 a = gacc[q];
+    const float2 u = ff_add(make_float2(a.x, a.y), make_float2(uh, ul));
+    const float2 v = ff_add(make_float2(a.z, a.w), make_float2(vh, vl));
+    gacc[q] = make_float4(u.x, u.y, v.x, v.y);
   }
 }
 

@@ -126,7 +126,8 @@ def test_builder_cutoffs_match_oracle_count(pb, g2_min, nsig):
 
 @pytest.mark.parametrize("field,bad", [("variant", 9), ("merge_branches", 3), ("dense_rows", 4), ("tile_sweep", 3),
                                        ("tile_sweep", -1), ("stream_mode", 3), ("channel_per_lane", 6),
-                                       ("transport_gather", 7), ("ctas_per_sm", 9), ("item_channels", 100)])
+                                       ("transport_gather", 7), ("ctas_per_sm", 9), ("item_channels", 100),
+                                       ("adjoint", 2)])
 def test_device_options_are_checked_on_the_host(pb, field, bad):
     """pb_dev_arena_bytes resolves and checks pb_dev_opts without touching a GPU: every field
     out of its documented range is PB_EINVAL, and the defaults size an arena."""
@@ -141,3 +142,25 @@ def test_device_options_are_checked_on_the_host(pb, field, bad):
     o = pb._DevOpts()
     setattr(o, field, bad)
     assert L.pb_dev_arena_bytes(ch._h, ctypes.byref(o), ctypes.byref(nbytes)) == pb.PB_EINVAL
+
+
+def test_adjoint_accumulators_are_sized_per_state_pair(pb):
+    """adjoint = 1 reserves one float-float (u, v) accumulator of 16 bytes per sweep entry on a
+    branch-merged FF device, and nothing on the per-channel or FP32 forms."""
+    import ctypes
+
+    ch = pb.Channels.from_model(synth.make_window4(12))
+    L = pb.lib()
+
+    def arena(**kw):
+        o = pb._DevOpts()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        n = ctypes.c_size_t(0)
+        assert L.pb_dev_arena_bytes(ch._h, ctypes.byref(o), ctypes.byref(n)) == pb.PB_OK
+        return n.value
+
+    grow = arena(adjoint=1) - arena()
+    assert 16 * ch.nchannels // 8 <= grow <= 16 * ch.nchannels + 4096
+    assert arena(adjoint=1, merge_branches=2) == arena(merge_branches=2)
+    assert arena(adjoint=1, variant=pb.VARIANTS["g32"]) == arena(variant=pb.VARIANTS["g32"])

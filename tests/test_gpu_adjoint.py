@@ -227,3 +227,70 @@ def test_fp32_trajectory_gradient_against_fp64(pb):
     eg = nrel(grads["g32"][1], grads["ff"][1])
     print(f"fp32 trajectory gradient errors: f0 {ef:.2e}, g2 {eg:.2e}")
     assert ef <= 1e-4 and eg <= 1e-4
+
+
+@pytest.mark.parametrize("opts", [{}, {"dense_rows": 2}], ids=["merged-tiles", "merged-indexed"])
+def test_deferred_g2_gradient_matches_per_step(pb, opts):
+    """Three RK4 adjoint steps with the |g|^2 gradient deferred to per-pair accumulators and
+    flushed once, against the same steps applying it to every channel per step: dL/df is the
+    same arithmetic (bit-equal); dL/dg2 differs only in where the stage sums are rounded.  A
+    second flush adds nothing (the accumulators are cleared)."""
+    import torch
+
+    m = synth.make_window4(12)
+    ch = pb.Channels.from_model(m)
+    dev = pb.Device(ch, adjoint=True, **opts)
+    assert dev.deferred
+    rng = np.random.default_rng(11)
+    fs = [T(rng.uniform(0, 1, dev.nstate)) for _ in range(3)]
+    lam0 = rng.normal(size=dev.nstate)
+    ref = torch.zeros(dev.nchannels, dtype=torch.float64, device="cuda")
+    lam_ref = T(lam0)
+    for f in fs:
+        dev.rk4_vjp(f, lam_ref, 1.5, grad_g2=ref)
+    got = torch.zeros_like(ref)
+    lam = T(lam0)
+    for f in fs:
+        dev.rk4_vjp_defer(f, lam, 1.5)
+    dev.g2grad_flush(got)
+    assert torch.equal(lam, lam_ref)
+    err = nrel(got.cpu().numpy(), ref.cpu().numpy())
+    print(f"{opts} deferred g2-gradient normwise difference {err:.2e}")
+    assert err <= 1e-12
+    again = got.clone()
+    dev.g2grad_flush(again)
+    assert torch.equal(again, got)
+
+
+def test_deferred_trajectory_gradient_matches(pb):
+    """autograd.trajectory on an adjoint=True device (deferred |g|^2 gradient) against the
+    per-step form on the 8^3 workload."""
+    import torch
+    from paper_2511_03683_gb300 import autograd as pa
+
+    m = synth.make_config("tiny")
+    ch = pb.Channels.from_model(m)
+    ids = ch.state_ids()
+    eps = torch.tensor(m.eps.reshape(-1)[ids], device="cuda")
+    out = []
+    for adj in (False, True):
+        dev = pb.Device(ch, adjoint=adj)
+        f0 = torch.tensor(m.f_hot().reshape(-1)[ids], device="cuda", requires_grad=True)
+        g2 = pa.g2_tensor(ch).requires_grad_(True)
+        (eps * pa.trajectory(dev, f0, g2, 1.0, 10, 4)).sum().backward()
+        out.append((f0.grad.cpu().numpy(), g2.grad.cpu().numpy()))
+        dev.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert nrel(out[1][1], out[0][1]) <= 1e-12
+
+
+def test_deferred_entry_points_need_accumulators(pb):
+    import torch
+
+    ch = pb.Channels.from_model(synth.make_window4(12))
+    dev = pb.Device(ch)
+    z = torch.zeros(dev.nstate, dtype=torch.float64, device="cuda")
+    with pytest.raises(pb.PBError):
+        dev.rk4_vjp_defer(z, z.clone(), 1.0)
+    with pytest.raises(pb.PBError):
+        dev.g2grad_flush(torch.zeros(dev.nchannels, dtype=torch.float64, device="cuda"))
