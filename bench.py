@@ -324,8 +324,8 @@ def adjoint_report(pb, stream, nsteps=200):
            "channels": ch.nchannels}
     grads = {}
     for v in ("ff", "g32"):
-        # FF: the |g|^2 gradient is deferred to per-pair accumulators and flushed once
-        dev = pb.Device(ch, variant=v, adjoint=(v == "ff"))
+        # the |g|^2 gradient is deferred to per-pair accumulators and flushed once
+        dev = pb.Device(ch, variant=v, adjoint=True)
         g2 = pa.g2_tensor(ch)
         times = []
         for rep in range(3):

@@ -190,9 +190,10 @@ typedef struct pb_dev_opts {
                                 2 one persistent CTA per SM with 256 threads keeps three tiles in flight in
                                 shared memory through TMA bulk copies (cp.async.bulk, mbarrier-counted),
                                 its bounded waits reporting through pb_dev_check */
-  int32_t adjoint;           /* nonzero: reserve one float-float accumulator pair per state pair (16 bytes)
-                                for the deferred |g|^2 gradient of pb_rtbte_rk4_vjp_defer (FF variant,
-                                branch-merged; ignored otherwise) */
+  int32_t adjoint;           /* 1: reserve the accumulators of the deferred |g|^2 gradient
+                                (pb_rtbte_rk4_vjp_defer): FF with branch merging, one float-float
+                                (u, v) per stored state pair (16 bytes); G32/G16, three doubles per
+                                (state, partner) pair (24 nstate^2 bytes); ignored otherwise */
 } pb_dev_opts;
 
 typedef struct pb_dev pb_dev; /* opaque host handle describing device-resident data */
@@ -305,10 +306,10 @@ int pb_collision_vjp(pb_dev *dev, const double *f, const double *lam, double *gr
 int pb_rtbte_rk4_vjp(pb_dev *dev, const double *f, double *lam, double dt, double *grad_g2, void *stream);
 
 /* The same RK4 adjoint step with the |g|^2 gradient deferred: instead of updating every stored
- * channel, the step adds the two stage sums that the gradient of a state pair needs (the
- * pair's branches share them) into the handle's per-pair accumulators; pb_dev_g2grad_flush
- * applies them.  Needs a device created with pb_dev_opts.adjoint on the FF variant with
- * branch merging (PB_EINVAL otherwise). */
+ * channel, the step adds the stage sums that the gradient of a state pair needs (the pair's
+ * branches and modes share them) into the handle's per-pair accumulators; pb_dev_g2grad_flush
+ * applies them.  Needs a device created with pb_dev_opts.adjoint = 1 on the FF variant with
+ * branch merging or on G32/G16 (PB_EINVAL otherwise). */
 int pb_rtbte_rk4_vjp_defer(pb_dev *dev, const double *f, double *lam, double dt, void *stream);
 
 /* grad_g2 (device double[nchannels], CSR order) += the |g|^2 gradient accumulated by

@@ -290,7 +290,7 @@ class Device:
         # FF/F64 stream one entry per state pair unless merge_branches == 2
         self.merged = variant in ("ff", "f64") and int(merge_branches) != 2
         # per-pair accumulators of the deferred |g|^2 gradient (rk4_vjp_defer / g2grad_flush)
-        self.deferred = bool(adjoint) and variant == "ff" and self.merged
+        self.deferred = bool(adjoint) and ((variant == "ff" and self.merged) or variant in ("g32", "g16"))
         o = _DevOpts(VARIANTS[variant], int(item_channels), int(ctas_per_sm), 1 if transport else 0,
                      int(transport_gather), int(transport_ctas), int(channel_per_lane), int(stream_mode),
                      int(merge_branches), int(dense_rows), int(tile_sweep), 1 if adjoint else 0)

@@ -29,7 +29,7 @@ struct Layout {
   size_t rp, item_ptr, items, col, coefA, coefB, g2, wt, eps, kc, R, omega, tab, part, acc, y, yff, fstage, Fa, Fb,
       Fff, tau, invtau, red, scal, obs, g2lo, gstate, tab32, col16, rp_real, vjpG, g2tab, vecs, hcol, hg2, hA, hB, sc,
       entries, hitems, titems, t_item_ptr, err, citems, citem_ptr, cpart, ccoefA, ccoefB, sidx16, sidx32, pcstart,
-      pcnt, srp, gitems, tiles, tcoef, tpart, g2d, gditems, gdptr, gacc, total;
+      pcnt, srp, gitems, tiles, tcoef, tpart, g2d, gditems, gdptr, gacc, gaccg, total;
 };
 
 struct Plan {
@@ -221,7 +221,8 @@ Layout make_layout(const pb_channels *ch, const Plan &P, const Plan *S, int vari
   L.pcnt = take(S ? nsw : 0);
   L.srp = take(S ? sizeof(int64_t) * (ns + 1) : 0);
   L.gitems = take(S ? sizeof(Item) * (size_t)grad_chunks(S->rp) : 0);
-  L.gacc = take(S && gacc ? sizeof(float4) * nsw : 0);
+  L.gacc = take(S && gacc && variant == PB_VARIANT_FF ? sizeof(float4) * nsw : 0);
+  L.gaccg = take(gacc && (variant == PB_VARIANT_G32 || variant == PB_VARIANT_G16) ? 3 * sizeof(double) * (size_t)ns * (size_t)ns : 0);
   const TileDims td = tile_dims((int64_t)ns);
   L.tiles = take(sym ? sizeof(int2) * td.nt : 0);
   L.tcoef = take(sym ? sizeof(float4) * (size_t)td.nt * dev::kTile * dev::kTile : 0);
@@ -401,6 +402,8 @@ struct pb_dev {
   int64_t *srp = nullptr;         // first sweep entry of every row [ns+1]
   Item *gitems = nullptr;         // the sweep rows in pieces of <= 32 entries (|g|^2 gradient)
   float4 *gacc = nullptr;         // deferred |g|^2 gradient: (u, v) float-float per sweep entry
+  double *gaccg = nullptr;        // deferred mixed |g|^2 gradient: W, U, V per (state, partner), FP64
+  size_t gaccg_bytes() const { return 3 * sizeof(double) * (size_t)ns * (size_t)ns; }
   int ngitems = 0;
   // symmetric tiles (complete rows, FF): the collision and rate sweeps stream the upper block
   // triangle of the pair matrix once and add each tile to its rows and to its columns
@@ -686,7 +689,7 @@ extern "C" int pb_dev_arena_bytes(const pb_channels *ch, const pb_dev_opts *opts
     const int nfin = (int)((P.ns + kFinBlock - 1) / kFinBlock);
     *bytes = make_layout(ch, P, merged ? &S : nullptr, o.variant, o.transport != 0, nfin,
                          sym_for(o, merged, complete), gdense_for(ch, o, sm),
-                         o.adjoint != 0 && o.variant == PB_VARIANT_FF).total;
+                         o.adjoint != 0).total;
   } catch (const std::bad_alloc &) {
     return set_error(PB_ENOMEM, "pb_dev_arena_bytes: out of host memory");
   }
@@ -755,7 +758,7 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->gd_nitems = (int)gd.nitems;
   d->gd_bytes = gd.bytes;
   d->L = make_layout(ch, P, merged ? &S : nullptr, o.variant, d->transport, d->nfin_blocks, d->sym, gd,
-                     o.adjoint != 0 && o.variant == PB_VARIANT_FF);
+                     o.adjoint != 0);
   if (arena_bytes < d->L.total) {
     const size_t need = d->L.total;
     delete d;
@@ -804,6 +807,7 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->rp_real = (int64_t *)(A + L.rp_real);
   d->vjpG = (float2 *)(A + L.vjpG);
   d->g2tab = (float4 *)(A + L.g2tab);
+  if (d->mixed() && o.adjoint) d->gaccg = (double *)(A + L.gaccg);
   d->vecs = (double *)(A + L.vecs);
   d->hcol = (uint32_t *)(A + L.hcol);
   d->hg2 = (double *)(A + L.hg2);
@@ -950,8 +954,9 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
         }
       }
       UP(d->rp, P.rp.data(), sizeof(int64_t) * (d->ns + 1));
-      if (d->gacc) {
-        cudaError_t e_ = cudaMemsetAsync(d->gacc, 0, sizeof(float4) * (size_t)d->nsw, st);
+      if (d->gacc || d->gaccg) {
+        cudaError_t e_ = d->gacc ? cudaMemsetAsync(d->gacc, 0, sizeof(float4) * (size_t)d->nsw, st)
+                                 : cudaMemsetAsync(d->gaccg, 0, d->gaccg_bytes(), st);
         if (e_ != cudaSuccess) {
           status = cuda_fail(e_, "clear the gradient accumulators");
           break;
@@ -1828,6 +1833,14 @@ int g2acc_launch(pb_dev *d, cudaStream_t st) {
 
 // grad_g2 += the accumulated pair sums applied to the pairs' channels (accumulators cleared)
 int g2flush_launch(pb_dev *d, double *grad_g2, cudaStream_t st) {
+  if (d->gaccg) {
+    const long long *rp = (const long long *)d->rp, *rr = (const long long *)d->rp_real;
+    dev::k_g2grad_g<0><<<d->stream_grid(8), dev::kBlock, 0, st>>>(d->items, (int)d->nitems, d->ggeom(), d->gstate,
+                                                                   rp, rr, d->g2tab, (int)d->ns, grad_g2, d->gaccg);
+    PB_LAUNCHED("k_g2grad_g");
+    const cudaError_t e = cudaMemsetAsync(d->gaccg, 0, d->gaccg_bytes(), st);
+    return e == cudaSuccess ? PB_OK : cuda_fail(e, "clear the gradient accumulators");
+  }
   const int n = d->ngitems, ns = (int)d->ns;
   const int gg = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, (int64_t)d->sm_count * dev::kGradCtas));
   const long long *rp = (const long long *)d->rp, *rr = (const long long *)d->rp_real, *pcs = (const long long *)d->pcstart;
@@ -1835,6 +1848,17 @@ int g2flush_launch(pb_dev *d, double *grad_g2, cudaStream_t st) {
   if (d->sidx16) dev::k_g2grad_pairs<0, uint16_t><<<gg, dev::kBlock, 0, st>>>(d->gitems, n, d->sidx16, pcs, d->pcnt, rp, rr, A, B, d->g2tab, ns, grad_g2, d->gacc);
   else           dev::k_g2grad_pairs<0, uint32_t><<<gg, dev::kBlock, 0, st>>>(d->gitems, n, d->sidx32, pcs, d->pcnt, rp, rr, A, B, d->g2tab, ns, grad_g2, d->gacc);
   PB_LAUNCHED("k_g2grad_pairs");
+  return PB_OK;
+}
+
+// the mixed deferred form: the NST stages' W, U, V of every (state, partner) pair
+template <int NST>
+int g2accg_launch(pb_dev *d, cudaStream_t st) {
+  const int ns = (int)d->ns;
+  if (ns == 0) return PB_OK;
+  const dim3 grid((unsigned)((ns + dev::kBlock - 1) / dev::kBlock), (unsigned)std::min(ns, 65535));
+  dev::k_g2acc_g<NST><<<grid, dev::kBlock, 0, st>>>(d->g2tab, ns, d->gaccg);
+  PB_LAUNCHED("k_g2acc_g");
   return PB_OK;
 }
 
@@ -1898,7 +1922,7 @@ int rk4_vjp_impl(pb_dev *d, const double *f, double *lam, double dt, double *gra
       const double *ain = j == 3 ? lam : acc;
       double *aout = j == 0 ? lam : acc;  // the last stage writes dL/df over lam (lam is read first)
       if ((rc = vjp_launch_mixed(d, U[j], lam, wl[j], j == 3 ? nullptr : mprev, wm[j], mu, ain, aout,
-                                 grad_g2 ? j : -1, st)))
+                                 want_g2 ? j : -1, st)))
         return rc;
     }
   } else {
@@ -1915,7 +1939,7 @@ int rk4_vjp_impl(pb_dev *d, const double *f, double *lam, double dt, double *gra
       std::swap(gc, gn);
     }
   }
-  if (defer) return g2acc_launch<4>(d, st);
+  if (defer) return d->mixed() ? g2accg_launch<4>(d, st) : g2acc_launch<4>(d, st);
   if (grad_g2 && (rc = g2grad_launch<4>(d, grad_g2, st))) return rc;
   return PB_OK;
 }
@@ -1938,14 +1962,15 @@ extern "C" int pb_rtbte_rk4_vjp(pb_dev *d, const double *f, double *lam, double 
 extern "C" int pb_rtbte_rk4_vjp_defer(pb_dev *d, const double *f, double *lam, double dt, void *stream) {
   clear_error();
   if (int rc = rk4_vjp_check(d, f, lam, dt, "pb_rtbte_rk4_vjp_defer")) return rc;
-  if (!d->gacc) return set_error(PB_EINVAL, "pb_rtbte_rk4_vjp_defer: needs a branch-merged FF device created with adjoint = 1");
+  if (!d->gacc && !d->gaccg)
+    return set_error(PB_EINVAL, "pb_rtbte_rk4_vjp_defer: needs a device created with adjoint = 1 (FF branch-merged, G32 or G16)");
   return rk4_vjp_impl(d, f, lam, dt, nullptr, true, stream);
 }
 
 extern "C" int pb_dev_g2grad_flush(pb_dev *d, double *grad_g2, void *stream) {
   clear_error();
   if (!d || !grad_g2) return set_error(PB_EINVAL, "pb_dev_g2grad_flush: null argument");
-  if (!d->gacc) return set_error(PB_EINVAL, "pb_dev_g2grad_flush: the device keeps no gradient accumulators");
+  if (!d->gacc && !d->gaccg) return set_error(PB_EINVAL, "pb_dev_g2grad_flush: the device keeps no gradient accumulators");
   return g2flush_launch(d, grad_g2, (cudaStream_t)stream);
 }
 

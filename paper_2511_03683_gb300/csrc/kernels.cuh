@@ -1394,14 +1394,17 @@ __global__ void k_vjp_prep32(const double *__restrict__ f, const double *__restr
 //   sum_j c_j [...] = GN W + G_e U - G_a V,  W = sum_j c_j (f_s^j - f_p^j),
 //   U = sum_j c_j f_s^j (1 - f_p^j),  V = sum_j c_j (1 - f_s^j) f_p^j,
 // with f_s - f_p from the high and low parts of f (it is small where the terms cancel): the
-// Gaussians once per channel, FP32 terms, one FP64 update of grad per channel.
+// Gaussians once per channel, FP32 terms, one FP64 update of grad per channel.  NST = 0: W, U, V
+// are the FP64 sums over many calls that k_g2acc_g keeps per (state, partner) pair,
+// acc[0..2][s ns + p], and the bracket is formed in FP64.
 template <int NST>
 __global__ void __launch_bounds__(kBlock) k_g2grad_g(const Item *__restrict__ items, int nitems, GGeom g,
                                                      const uint4 *__restrict__ gstate,
                                                      const long long *__restrict__ rp_pad,
                                                      const long long *__restrict__ rp_real,
                                                      const float4 *__restrict__ tab, int ns,
-                                                     double *__restrict__ grad) {
+                                                     double *__restrict__ grad,
+                                                     const double *__restrict__ acc = nullptr) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -1414,8 +1417,8 @@ __global__ void __launch_bounds__(kBlock) k_g2grad_g(const Item *__restrict__ it
     const long long real_len = rp_real[r + 1] - rp_real[r];
     const long long len = real_len - off < I.len ? real_len - off : I.len;  // stored channels of the item
     double *__restrict__ gr = grad + rp_real[r] + off;
-    float4 rs[NST];  // (c, f hi, f lo, c f)
-    float rb[NST];   // c (1 - f)
+    float4 rs[NST > 0 ? NST : 1];  // (c, f hi, f lo, c f)
+    float rb[NST > 0 ? NST : 1];   // c (1 - f)
 #pragma unroll
     for (int j = 0; j < NST; ++j) {
       const float4 t = tab[(long long)j * ns + r];
@@ -1434,6 +1437,11 @@ __global__ void __launch_bounds__(kBlock) k_g2grad_g(const Item *__restrict__ it
       const float Ga = ex2_approx(xa * xa * g.k2);
       const float Ge = ex2_approx(xe * xe * g.k2);
       const float GN = (Ga + Ge) * t.y;
+      if (NST == 0) {
+        const long long npair = (long long)ns * ns, q = (long long)r * ns + p;
+        gr[k] += fma((double)GN, acc[q], fma((double)Ge, acc[npair + q], -(double)Ga * acc[2 * npair + q]));
+        continue;
+      }
       float W = 0.f, U = 0.f, V = 0.f;
 #pragma unroll
       for (int j = 0; j < NST; ++j) {
@@ -1443,6 +1451,39 @@ __global__ void __launch_bounds__(kBlock) k_g2grad_g(const Item *__restrict__ it
         V = fmaf(rb[j], q.y, V);
       }
       gr[k] += (double)fmaf(GN, W, fmaf(Ge, U, -Ga * V));
+    }
+  }
+}
+
+// Deferred mixed-precision |g|^2 gradient: the NST stages' W, U, V of k_g2grad_g (the same FP32
+// terms) for every (state s, partner p) pair, added into FP64 accumulators acc[0..2][s ns + p];
+// k_g2grad_g<0> applies them to the channels.  Rows over blockIdx.y, partners over x.
+template <int NST>
+__global__ void __launch_bounds__(kBlock) k_g2acc_g(const float4 *__restrict__ tab, int ns,
+                                                    double *__restrict__ acc) {
+  const long long npair = (long long)ns * ns;
+  for (int s = blockIdx.y; s < ns; s += gridDim.y) {
+    float4 rs[NST];
+    float rb[NST];
+#pragma unroll
+    for (int j = 0; j < NST; ++j) {
+      const float4 t = tab[(long long)j * ns + s];
+      rs[j] = make_float4(t.x, t.y, t.z, t.x * t.y);
+      rb[j] = t.x * t.w;
+    }
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < ns; p += gridDim.x * blockDim.x) {
+      float W = 0.f, U = 0.f, V = 0.f;
+#pragma unroll
+      for (int j = 0; j < NST; ++j) {
+        const float4 q = __ldg(tab + (long long)j * ns + p);
+        W = fmaf(rs[j].x, __fsub_rn(rs[j].y, q.y) + __fsub_rn(rs[j].z, q.z), W);
+        U = fmaf(rs[j].w, q.w, U);
+        V = fmaf(rb[j], q.y, V);
+      }
+      const long long i = (long long)s * ns + p;
+      acc[i] += (double)W;
+      acc[npair + i] += (double)U;
+      acc[2 * npair + i] += (double)V;
     }
   }
 }

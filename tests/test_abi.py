@@ -146,7 +146,8 @@ def test_device_options_are_checked_on_the_host(pb, field, bad):
 
 def test_adjoint_accumulators_are_sized_per_state_pair(pb):
     """adjoint = 1 reserves one float-float (u, v) accumulator of 16 bytes per sweep entry on a
-    branch-merged FF device, and nothing on the per-channel or FP32 forms."""
+    branch-merged FF device, three doubles per (state, partner) pair on G32, and nothing on
+    the per-channel FF form."""
     import ctypes
 
     ch = pb.Channels.from_model(synth.make_window4(12))
@@ -163,4 +164,6 @@ def test_adjoint_accumulators_are_sized_per_state_pair(pb):
     grow = arena(adjoint=1) - arena()
     assert 16 * ch.nchannels // 8 <= grow <= 16 * ch.nchannels + 4096
     assert arena(adjoint=1, merge_branches=2) == arena(merge_branches=2)
-    assert arena(adjoint=1, variant=pb.VARIANTS["g32"]) == arena(variant=pb.VARIANTS["g32"])
+    g32 = pb.VARIANTS["g32"]
+    grow = arena(adjoint=1, variant=g32) - arena(variant=g32)
+    assert abs(grow - 24 * ch.nstate ** 2) <= 4096  # up to the alignment of the arena regions
