@@ -265,10 +265,13 @@ def test_deferred_g2_gradient_matches_per_step(pb, opts, tol):
     assert torch.equal(again, got)
 
 
-@pytest.mark.parametrize("variant,tol", [("ff", 1e-12), ("g32", 1e-6)])
-def test_deferred_trajectory_gradient_matches(pb, variant, tol):
-    """autograd.trajectory on an adjoint=True device (deferred |g|^2 gradient) against the
-    per-step form on the 8^3 workload."""
+def test_deferred_trajectory_gradient_matches(pb):
+    """autograd.trajectory on adjoint=True devices (deferred |g|^2 gradient) on the 8^3
+    workload, 10 steps: dL/df0 bit-equal to the per-step form of the same variant; dL/dg2
+    against the FF per-step gradient at the FP64 (1e-11) and FP32 (1e-4) trajectory bounds.
+    This gradient is ill-conditioned (its terms cancel: the two FF forms differ by ~1e-12 here
+    against ~5e-15 for three random steps), so the forms are compared with the FP64-accurate
+    one rather than with each other."""
     import torch
     from paper_2511_03683_gb300 import autograd as pa
 
@@ -276,19 +279,22 @@ def test_deferred_trajectory_gradient_matches(pb, variant, tol):
     ch = pb.Channels.from_model(m)
     ids = ch.state_ids()
     eps = torch.tensor(m.eps.reshape(-1)[ids], device="cuda")
-    out = []
-    for adj in (False, True):
-        dev = pb.Device(ch, variant=variant, adjoint=adj)
-        assert dev.deferred == adj
-        f0 = torch.tensor(m.f_hot().reshape(-1)[ids], device="cuda", requires_grad=True)
-        g2 = pa.g2_tensor(ch).requires_grad_(True)
-        (eps * pa.trajectory(dev, f0, g2, 1.0, 10, 4)).sum().backward()
-        out.append((f0.grad.cpu().numpy(), g2.grad.cpu().numpy()))
-        dev.close()
-    assert np.array_equal(out[0][0], out[1][0])
-    err = nrel(out[1][1], out[0][1])
-    print(f"{variant} deferred trajectory g2-gradient difference {err:.2e}")
-    assert err <= tol
+    out = {}
+    for variant in ("ff", "g32"):
+        for adj in (False, True):
+            dev = pb.Device(ch, variant=variant, adjoint=adj)
+            assert dev.deferred == adj
+            f0 = torch.tensor(m.f_hot().reshape(-1)[ids], device="cuda", requires_grad=True)
+            g2 = pa.g2_tensor(ch).requires_grad_(True)
+            (eps * pa.trajectory(dev, f0, g2, 1.0, 10, 4)).sum().backward()
+            out[variant, adj] = (f0.grad.cpu().numpy(), g2.grad.cpu().numpy())
+            dev.close()
+    ref = out["ff", False][1]
+    for variant, tol in (("ff", 1e-11), ("g32", 1e-4)):
+        assert np.array_equal(out[variant, False][0], out[variant, True][0])
+        e_step, e_def = nrel(out[variant, False][1], ref), nrel(out[variant, True][1], ref)
+        print(f"{variant} trajectory g2-gradient vs FF per-step: per-step {e_step:.2e}, deferred {e_def:.2e}")
+        assert e_def <= tol
 
 
 def test_deferred_entry_points_need_accumulators(pb):
