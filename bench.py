@@ -87,6 +87,12 @@ class Clocks:
         except (OSError, FileNotFoundError):
             self.proc = None
 
+    def has_sample(self) -> bool:
+        try:
+            return self.proc is not None and os.path.getsize(self.path) > 0
+        except OSError:
+            return False
+
     def stop(self):
         if not self.proc:
             return None
@@ -588,8 +594,16 @@ def run_ours(args):
     clocks = Clocks(local)
     for i in range(args.warmup):
         step(Fa, Fb) if i % 2 == 0 else step(Fb, Fa)
-    barrier()
     clocks.start()
+    # keep the GPU busy with further untimed steps until the sampler has taken its first
+    # sample (at most 3 s), so that its samples cover the timed region
+    t_wait = time.time()
+    i = 0
+    while clocks.proc is not None and not clocks.has_sample() and time.time() - t_wait < 3.0:
+        step(Fa, Fb) if i % 2 == 0 else step(Fb, Fa)
+        i += 1
+        torch.cuda.synchronize()
+    barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for i in range(args.steps):
