@@ -492,7 +492,7 @@ def compare_variants(pb, ch, dev_ff, fh, ff_ms, mixed_steps, stream):
     out = {}
     ms = {"ff": ff_ms}
     devs = {}
-    for v in ("ff_per_channel", "f64", "f64_per_channel", "literal", "g32", "g16"):
+    for v in ("ff_per_channel", "f64", "f64_per_channel", "literal", "g32", "g16", "h16"):
         kw = {"merge_branches": 2} if v.endswith("_per_channel") else {}
         d = pb.Device(ch, variant=v.replace("_per_channel", ""), **kw)
         o = torch.empty(d.nstate, dtype=torch.float64, device="cuda")
@@ -502,7 +502,7 @@ def compare_variants(pb, ch, dev_ff, fh, ff_ms, mixed_steps, stream):
                   "hbm_gb_s": d.bytes_per_channel * d.nchannels / (ms[v] * 1e-3) / 1e9,
                   "bytes_per_channel": d.bytes_per_channel, "speedup_vs_ff": ff_ms / ms[v],
                   "dfdt_err_vs_fp64": err}
-        if v in ("g32", "g16"):
+        if v in ("g32", "g16", "h16"):
             devs[v] = d
         else:
             d.close()
@@ -734,7 +734,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"ff": "f32x2", "paper": "f32x2", "f64": "f64", "literal": "f64", "g32": "f32",
-                      "g16": "f32 (bf16 |g|^2)"}.get(args.variant, args.variant),
+                      "g16": "f32 (bf16 |g|^2)", "h16": "f32 (fp16 |g|^2 x 2^k)"}.get(args.variant, args.variant),
             "data": "synthetic", "config": cfg,
             "rk4_steps_per_s": nrk / (rk_ms * 1e-3), "transport_iters_per_s": ntr / (tr_ms * 1e-3),
             "collision_ms": coll_ms, "rates_ms": rates_ms,

@@ -143,12 +143,16 @@ void pb_channels_free(pb_channels *ch);
  *  PB_VARIANT_G32     |g|^2 stored FP32, per-channel arithmetic in FP32, compensated
  *                     (Kahan) accumulation, FP64 state.
  *  PB_VARIANT_G16     as G32 with |g|^2 stored BF16.
+ *  PB_VARIANT_H16     as G32 with |g|^2 stored FP16 times a power of two chosen at creation (the
+ *                     largest value maps into [2^9, 2^10)): the same 2 bytes as BF16 with 11
+ *                     significand bits instead of 8.  pb_dev_set_g2 values above 63 times the
+ *                     largest value at creation overflow: pb_dev_check then returns PB_EINVAL.
  *  PB_VARIANT_PAPER   the paper's own layout (Sec. "Optimized GPU algorithm", Fig. 2), for
  *                     comparison: every channel stored once, per-channel contributions written
  *                     to sc_col (step 2), then gathered with signs by each state's target list
  *                     (step 3).  Collision integral and RK4 only (no scattering rates). */
 enum { PB_VARIANT_FF = 0, PB_VARIANT_F64 = 1, PB_VARIANT_LITERAL = 2, PB_VARIANT_G32 = 3, PB_VARIANT_G16 = 4,
-       PB_VARIANT_PAPER = 5 };
+       PB_VARIANT_PAPER = 5, PB_VARIANT_H16 = 6 };
 
 typedef struct pb_dev_opts {
   int32_t variant;           /* PB_VARIANT_* */
@@ -210,8 +214,9 @@ int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, void *arena, s
 void pb_dev_destroy(pb_dev *dev);
 
 /* Synchronise `stream` and report PB_ETIMEOUT if a bounded device-side wait of an earlier
- * launch gave up (the TMA bulk-copy sweeps); PB_OK otherwise.  The report clears the handle's
- * error word, so the next check sees only later launches. */
+ * launch gave up (the TMA bulk-copy sweeps), or PB_EINVAL if a |g|^2 value overflowed the
+ * scaled FP16 storage of a PB_VARIANT_H16 device; PB_OK otherwise.  The report clears the
+ * handle's error word, so the next check sees only later launches. */
 int pb_dev_check(pb_dev *dev, void *stream);
 
 /* Test of the bounded-wait machinery itself (the paper has no counterpart): one CTA issues a

@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_PKG, "lib", "libpb.so")
 PB_OK, PB_EINVAL, PB_ENOMEM, PB_ECUDA, PB_ENOTCLOSED, PB_ENOCONV, PB_ETIMEOUT, PB_ECALLBACK, PB_EDEVICE = range(9)
 _CODES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCLOSED", 5: "ENOCONV", 6: "ETIMEOUT", 7: "ECALLBACK",
           8: "EDEVICE"}
-VARIANTS = {"ff": 0, "f64": 1, "literal": 2, "g32": 3, "g16": 4, "paper": 5}
+VARIANTS = {"ff": 0, "f64": 1, "literal": 2, "g32": 3, "g16": 4, "paper": 5, "h16": 6}
 
 
 class PBError(RuntimeError):
@@ -290,7 +290,7 @@ class Device:
         # FF/F64 stream one entry per state pair unless merge_branches == 2
         self.merged = variant in ("ff", "f64") and int(merge_branches) != 2
         # per-pair accumulators of the deferred |g|^2 gradient (rk4_vjp_defer / g2grad_flush)
-        self.deferred = bool(adjoint) and ((variant == "ff" and self.merged) or variant in ("g32", "g16"))
+        self.deferred = bool(adjoint) and ((variant == "ff" and self.merged) or variant in ("g32", "g16", "h16"))
         o = _DevOpts(VARIANTS[variant], int(item_channels), int(ctas_per_sm), 1 if transport else 0,
                      int(transport_gather), int(transport_ctas), int(channel_per_lane), int(stream_mode),
                      int(merge_branches), int(dense_rows), int(tile_sweep), 1 if adjoint else 0)
@@ -324,7 +324,8 @@ class Device:
         return out
 
     def check(self, stream=None):
-        """Synchronise and raise PBError(PB_ETIMEOUT) if a bounded device wait gave up."""
+        """Synchronise and raise PBError(PB_ETIMEOUT) if a bounded device wait gave up, or
+        PBError(PB_EINVAL) if a |g|^2 value overflowed the scaled FP16 storage (h16)."""
         _check(lib().pb_dev_check(self._h, _stream_ptr(stream)))
 
     def collision_static(self, f, out, stream=None):

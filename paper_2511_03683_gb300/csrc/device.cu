@@ -7,6 +7,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "kernels.cuh"
@@ -152,7 +153,7 @@ struct GDense {
 };
 GDense gdense_for(const pb_channels *ch, const pb_dev_opts &o, int sm) {
   GDense g;
-  const bool mixed = o.variant == PB_VARIANT_G32 || o.variant == PB_VARIANT_G16;
+  const bool mixed = o.variant == PB_VARIANT_G32 || o.variant == PB_VARIANT_G16 || o.variant == PB_VARIANT_H16;
   if (!mixed || (o.channel_per_lane != 0 && o.channel_per_lane != 5)) return g;
   const int64_t ns = ch->nstate, nm = ch->nmodes;
   if (ns == 0 || nm == 0) return g;
@@ -222,7 +223,7 @@ Layout make_layout(const pb_channels *ch, const Plan &P, const Plan *S, int vari
   L.srp = take(S ? sizeof(int64_t) * (ns + 1) : 0);
   L.gitems = take(S ? sizeof(Item) * (size_t)grad_chunks(S->rp) : 0);
   L.gacc = take(S && gacc && variant == PB_VARIANT_FF ? sizeof(float4) * nsw : 0);
-  L.gaccg = take(gacc && (variant == PB_VARIANT_G32 || variant == PB_VARIANT_G16) ? 3 * sizeof(double) * (size_t)ns * (size_t)ns : 0);
+  L.gaccg = take(gacc && (variant == PB_VARIANT_G32 || variant == PB_VARIANT_G16 || variant == PB_VARIANT_H16) ? 3 * sizeof(double) * (size_t)ns * (size_t)ns : 0);
   const TileDims td = tile_dims((int64_t)ns);
   L.tiles = take(sym ? sizeof(int2) * td.nt : 0);
   L.tcoef = take(sym ? sizeof(float4) * (size_t)td.nt * dev::kTile * dev::kTile : 0);
@@ -246,7 +247,7 @@ Layout make_layout(const pb_channels *ch, const Plan &P, const Plan *S, int vari
   L.scal = take(sizeof(double) * 8);
   L.obs = take(sizeof(double) * 8);
   L.err = take(sizeof(int) * 4);
-  const bool mixed = variant == PB_VARIANT_G32 || variant == PB_VARIANT_G16;
+  const bool mixed = variant == PB_VARIANT_G32 || variant == PB_VARIANT_G16 || variant == PB_VARIANT_H16;
   L.g2lo = take(mixed ? (variant == PB_VARIANT_G32 ? 4 : 2) * nchp : 0);
   L.gstate = take(mixed ? 16 * ns : 0);
   auto rad = [](int n) { return (size_t)(n > 1 ? 2 * n : 1); };
@@ -296,6 +297,14 @@ int cuda_fail(cudaError_t e, const char *what) {
 }  // namespace
 
 namespace {
+// fn(T *) with T the |g|^2 storage type of a mixed-precision variant
+template <typename F>
+void with_g2t(int variant, F &&fn) {
+  if (variant == PB_VARIANT_G32) fn((float *)nullptr);
+  else if (variant == PB_VARIANT_G16) fn((__nv_bfloat16 *)nullptr);
+  else fn((__half *)nullptr);
+}
+
 // Mixed-precision lane-sweep shapes (pb_dev_opts.channel_per_lane): 1 = 512 threads, three
 // CTAs per SM; 3 = the same with an L2 prefetch two trips ahead; 4 = one 1024-thread CTA per
 // SM with the next trip's stream words in registers.
@@ -455,7 +464,11 @@ struct pb_dev {
     g.norm = 1.0 / (std::sqrt(2.0 * kPi) * sigma);
     return g;
   }
-  bool mixed() const { return variant == PB_VARIANT_G32 || variant == PB_VARIANT_G16; }
+  bool mixed() const { return variant == PB_VARIANT_G32 || variant == PB_VARIANT_G16 || variant == PB_VARIANT_H16; }
+  // mixed variants: the stored |g|^2 is s2 |g|^2 (a power of two; 1 but for FP16), so the
+  // prefactor of their sums is c gnorm / s2
+  double g2s = 1.0;
+  double gscale() const { return c * gnorm() / g2s; }
   // the work items whose partials the forward sweeps write (collision, rates, RK4 stages)
   const int32_t *fwd_item_ptr() const { return gdense ? gd_item_ptr : item_ptr; }
   pb::dev::GGeom ggeom() const {
@@ -495,7 +508,7 @@ int check_device(int *sm_count) {
 int resolve_opts(const pb_channels *ch, const pb_dev_opts *opts, int sm_count, pb_dev_opts &o) {
   pb_dev_opts d{};
   if (opts) d = *opts;
-  if (d.variant < PB_VARIANT_FF || d.variant > PB_VARIANT_PAPER)
+  if (d.variant < PB_VARIANT_FF || d.variant > PB_VARIANT_H16)
     return set_error(PB_EINVAL, "pb_dev: variant %d is not available in this build", d.variant);
   if (d.merge_branches < 0 || d.merge_branches > 2) return set_error(PB_EINVAL, "pb_dev: merge_branches must be 0..2");
   if (d.dense_rows < 0 || d.dense_rows > 3) return set_error(PB_EINVAL, "pb_dev: dense_rows must be 0..3");
@@ -744,6 +757,13 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->T = ch->T;
   d->sigma = ch->sigma;
   d->c = 2.0 * kPi / (kHbar * (double)ch->nq);
+  if (o.variant == PB_VARIANT_H16) {
+    // FP16 |g|^2: the largest value at creation maps into [2^9, 2^10), so values down to 2^-24
+    // of it stay normal (11 significand bits) and pb_dev_set_g2 may raise them up to 63-fold
+    double gmax = 0.0;
+    for (const double v : ch->g2) gmax = std::max(gmax, std::fabs(v));
+    if (gmax > 0.0 && std::isfinite(gmax)) d->g2s = std::ldexp(1.0, 10 - std::ilogb(gmax) - 1);
+  }
   d->sm_count = sm;
   d->ctas = o.ctas_per_sm;
   d->item_ch = o.item_channels;
@@ -1107,26 +1127,23 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   if (d->mixed()) {
     const size_t vb = (sizeof(uint4) + sizeof(float)) * (size_t)d->ns;
     d->vjp_g_ok = vb + 1024 <= (size_t)smem_optin;
-    if (vb > 48 * 1024 && d->vjp_g_ok) {
-      cudaFuncSetAttribute(dev::k_stream_g_vjp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vb);
-      cudaFuncSetAttribute(dev::k_stream_g_vjp<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vb);
-      cudaFuncSetAttribute(dev::k_stream_g_dense<dev::MODE_VJP, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vb);
-      cudaFuncSetAttribute(dev::k_stream_g_dense<dev::MODE_VJP, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)vb);
-    }
+    if (vb > 48 * 1024 && d->vjp_g_ok)
+      with_g2t(d->variant, [&](auto tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        cudaFuncSetAttribute(dev::k_stream_g_vjp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vb);
+        cudaFuncSetAttribute(dev::k_stream_g_dense<dev::MODE_VJP, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vb);
+      });
   }
-  if (d->mixed() && d->smem_f > 48 * 1024) {
-    set_lane_smem<float>((int)d->smem_f);
-    set_lane_smem<__nv_bfloat16>((int)d->smem_f);
-    cudaFuncSetAttribute(dev::k_stream_g_dense<dev::MODE_COLL, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
-    cudaFuncSetAttribute(dev::k_stream_g_dense<dev::MODE_RATE, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
-    cudaFuncSetAttribute(dev::k_stream_g_dense<dev::MODE_COLL, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
-    cudaFuncSetAttribute(dev::k_stream_g_dense<dev::MODE_RATE, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
-    cudaFuncSetAttribute(dev::k_stream_g<dev::MODE_COLL, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
-    cudaFuncSetAttribute(dev::k_stream_g<dev::MODE_RATE, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
-    cudaFuncSetAttribute(dev::k_stream_g<dev::MODE_COLL, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
-    cudaFuncSetAttribute(dev::k_stream_g<dev::MODE_RATE, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_f);
-  }
+  if (d->mixed() && d->smem_f > 48 * 1024)
+    with_g2t(d->variant, [&](auto tag) {
+      using T = std::remove_pointer_t<decltype(tag)>;
+      const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+      set_lane_smem<T>((int)d->smem_f);
+      cudaFuncSetAttribute(dev::k_stream_g_dense<dev::MODE_COLL, T>, A, (int)d->smem_f);
+      cudaFuncSetAttribute(dev::k_stream_g_dense<dev::MODE_RATE, T>, A, (int)d->smem_f);
+      cudaFuncSetAttribute(dev::k_stream_g<dev::MODE_COLL, T>, A, (int)d->smem_f);
+      cudaFuncSetAttribute(dev::k_stream_g<dev::MODE_RATE, T>, A, (int)d->smem_f);
+    });
   cudaGetLastError();
   *out = d;
   return PB_OK;
@@ -1142,6 +1159,9 @@ extern "C" int pb_dev_check(pb_dev *d, void *stream) {
   if (h) {
     PB_CUDA(cudaMemsetAsync(d->err, 0, sizeof(int), st));  // reported once
     PB_CUDA(cudaStreamSynchronize(st));
+    if (h == dev::kErrG2Range)
+      return set_error(PB_EINVAL, "a |g|^2 value overflowed the FP16 storage (more than 63 times the largest value "
+                                  "at device creation)");
     return set_error(PB_ETIMEOUT, "a bounded device-side wait gave up (error word %d)", h);
   }
   return PB_OK;
@@ -1190,6 +1210,7 @@ extern "C" int pb_dev_get_info(const pb_dev *d, pb_dev_info *info) {
       break;
     case PB_VARIANT_G32:
     case PB_VARIANT_G16:
+    case PB_VARIANT_H16:
       // dense pair-major: the (state, partner, branch) slots, zeros included; else |g|^2 + word
       info->bytes_per_channel = d->gdense ? (d->nch ? (double)d->gd_bytes / (double)d->nch : 0.0)
                                           : (d->variant == PB_VARIANT_G32 ? 4.0 : 2.0) + sizeof(uint32_t);
@@ -1267,34 +1288,23 @@ int launch_stream_t(pb_dev *d, int mode, const double *fd, const float2 *fff, co
   } else if (d->mixed()) {
     const dev::GGeom g = d->ggeom();
     const int gg = (int)std::max<int64_t>(1, std::min<int64_t>((d->nitems * 32 + 511) / 512, (int64_t)d->sm_count * d->ctas));
-    const float *g32 = (const float *)d->g2lo;
-    const __nv_bfloat16 *g16 = (const __nv_bfloat16 *)d->g2lo;
-    if (d->gdense) {
-      const int gdg = (int)std::max<int64_t>(
-          1, std::min<int64_t>(((int64_t)d->gd_nitems * 32 + dev::kDenseThreads - 1) / dev::kDenseThreads, d->sm_count));
-      const int nd = d->gd_nitems, npp = d->gd_npp, nm = d->nmodes;
-      if (d->variant == PB_VARIANT_G32) {
-        const float *gd = (const float *)d->g2d;
-        if (coll) dev::k_stream_g_dense<dev::MODE_COLL, float><<<gdg, dev::kDenseThreads, d->smem_f, st>>>(d->gd_items, nd, g, gd, npp, nm, d->gstate, ns, part);
-        else      dev::k_stream_g_dense<dev::MODE_RATE, float><<<gdg, dev::kDenseThreads, d->smem_f, st>>>(d->gd_items, nd, g, gd, npp, nm, d->gstate, ns, part);
+    with_g2t(d->variant, [&](auto tag) {
+      using T = std::remove_pointer_t<decltype(tag)>;
+      const T *gl = (const T *)d->g2lo;
+      if (d->gdense) {
+        const int gdg = (int)std::max<int64_t>(
+            1, std::min<int64_t>(((int64_t)d->gd_nitems * 32 + dev::kDenseThreads - 1) / dev::kDenseThreads, d->sm_count));
+        const int nd = d->gd_nitems, npp = d->gd_npp, nm = d->nmodes;
+        const T *gd = (const T *)d->g2d;
+        if (coll) dev::k_stream_g_dense<dev::MODE_COLL, T><<<gdg, dev::kDenseThreads, d->smem_f, st>>>(d->gd_items, nd, g, gd, npp, nm, d->gstate, ns, part);
+        else      dev::k_stream_g_dense<dev::MODE_RATE, T><<<gdg, dev::kDenseThreads, d->smem_f, st>>>(d->gd_items, nd, g, gd, npp, nm, d->gstate, ns, part);
+      } else if (d->g_lane) {
+        launch_g_lane<T>(d->g_shape, coll, gg, d->sm_count, d->smem_f, st, d->items, n, g, gl, d->gstate, ns, part);
       } else {
-        const __nv_bfloat16 *gd = (const __nv_bfloat16 *)d->g2d;
-        if (coll) dev::k_stream_g_dense<dev::MODE_COLL, __nv_bfloat16><<<gdg, dev::kDenseThreads, d->smem_f, st>>>(d->gd_items, nd, g, gd, npp, nm, d->gstate, ns, part);
-        else      dev::k_stream_g_dense<dev::MODE_RATE, __nv_bfloat16><<<gdg, dev::kDenseThreads, d->smem_f, st>>>(d->gd_items, nd, g, gd, npp, nm, d->gstate, ns, part);
+        if (coll) dev::k_stream_g<dev::MODE_COLL, T><<<gg, 512, d->smem_f, st>>>(d->items, n, g, gl, d->gstate, ns, part);
+        else      dev::k_stream_g<dev::MODE_RATE, T><<<gg, 512, d->smem_f, st>>>(d->items, n, g, gl, d->gstate, ns, part);
       }
-    } else if (d->g_lane) {
-      if (d->variant == PB_VARIANT_G32)
-        launch_g_lane<float>(d->g_shape, coll, gg, d->sm_count, d->smem_f, st, d->items, n, g, g32, d->gstate, ns, part);
-      else
-        launch_g_lane<__nv_bfloat16>(d->g_shape, coll, gg, d->sm_count, d->smem_f, st, d->items, n, g, g16, d->gstate,
-                                     ns, part);
-    } else if (d->variant == PB_VARIANT_G32) {
-      if (coll) dev::k_stream_g<dev::MODE_COLL, float><<<gg, 512, d->smem_f, st>>>(d->items, n, g, g32, d->gstate, ns, part);
-      else      dev::k_stream_g<dev::MODE_RATE, float><<<gg, 512, d->smem_f, st>>>(d->items, n, g, g32, d->gstate, ns, part);
-    } else {
-      if (coll) dev::k_stream_g<dev::MODE_COLL, __nv_bfloat16><<<gg, 512, d->smem_f, st>>>(d->items, n, g, g16, d->gstate, ns, part);
-      else      dev::k_stream_g<dev::MODE_RATE, __nv_bfloat16><<<gg, 512, d->smem_f, st>>>(d->items, n, g, g16, d->gstate, ns, part);
-    }
+    });
   } else {
     const dev::ChanGeom g = d->geom();
     const int lgrid = d->stream_grid(8);
@@ -1323,7 +1333,7 @@ void launch_fin(pb_dev *d, const double *ysrc, double *out, double *f, double dt
   double *y = ydst ? ydst : d->y;
   if (d->mixed())
     dev::k_fin_coll<true, STAGE, true><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->fwd_item_ptr(), d->part}, (int)d->ns,
-                                                                          d->c * d->gnorm(), d->R,
+                                                                          d->gscale(), d->R,
                                                                           ysrc, out, f, d->acc, y,
                                                                           (float2 *)d->gstate, dt);
   else if (d->variant == PB_VARIANT_LITERAL || d->variant == PB_VARIANT_PAPER)
@@ -1535,7 +1545,7 @@ extern "C" int pb_scatter_rates(pb_dev *d, const double *f, double *inv_tau, voi
   if ((rc = launch_stream(d, dev::MODE_RATE, f, d->yff, st))) return rc;
   if (d->variant == PB_VARIANT_LITERAL || d->mixed())
     dev::k_fin_rate<true><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->fwd_item_ptr(), d->part}, (int)d->ns,
-                                                             d->mixed() ? d->c * d->gnorm() : d->c, d->R, inv_tau);
+                                                             d->mixed() ? d->gscale() : d->c, d->R, inv_tau);
   else if (d->sym)
     dev::k_fin_tiles<-1, true><<<(int)((d->ns + 31) / 32), 256, 0, st>>>(
         dev::TileSrc{d->tpart, d->td.nb, d->td.nsp}, (int)d->ns, d->c, d->R, nullptr, inv_tau, nullptr, nullptr, nullptr,
@@ -1685,20 +1695,19 @@ int coef_setup(pb_dev *d, cudaStream_t st) {
   if (d->mixed()) {
     const long long n = (long long)d->nchp;
     const int cg = (int)std::min<long long>((n + 255) / 256, 8192);
-    if (d->variant == PB_VARIANT_G32)
-      dev::k_cvt_g2<float><<<cg, 256, 0, st>>>(d->g2, n, (float *)d->g2lo);
-    else
-      dev::k_cvt_g2<__nv_bfloat16><<<cg, 256, 0, st>>>(d->g2, n, (__nv_bfloat16 *)d->g2lo);
+    with_g2t(d->variant, [&](auto tag) {
+      using T = std::remove_pointer_t<decltype(tag)>;
+      dev::k_cvt_g2<T><<<cg, 256, 0, st>>>(d->g2, n, (T *)d->g2lo, d->g2s, d->err);
+    });
     PB_LAUNCHED("k_cvt_g2");
     if (d->gdense) {
       PB_CUDA(cudaMemsetAsync(d->g2d, 0, d->gd_bytes, st));
       const long long *rp = (const long long *)d->rp, *rr = (const long long *)d->rp_real;
-      if (d->variant == PB_VARIANT_G32)
-        dev::k_dense_g2<float><<<d->chan_grid(8), dev::kBlock, 0, st>>>(d->items, (int)d->nitems, rp, rr, d->col, d->g2,
-                                                                        d->nmodes, d->gd_npp, (float *)d->g2d);
-      else
-        dev::k_dense_g2<__nv_bfloat16><<<d->chan_grid(8), dev::kBlock, 0, st>>>(
-            d->items, (int)d->nitems, rp, rr, d->col, d->g2, d->nmodes, d->gd_npp, (__nv_bfloat16 *)d->g2d);
+      with_g2t(d->variant, [&](auto tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        dev::k_dense_g2<T><<<d->chan_grid(8), dev::kBlock, 0, st>>>(d->items, (int)d->nitems, rp, rr, d->col, d->g2,
+                                                                    d->nmodes, d->gd_npp, (T *)d->g2d, d->g2s);
+      });
       PB_LAUNCHED("k_dense_g2");
     }
   }
@@ -1726,22 +1735,20 @@ int vjp_launch_mixed(pb_dev *d, const double *f, const double *lam, double wl, c
     // the dense pair-major sweep with the rate summands weighted by lam_s - lam_p
     const int gdg = (int)std::max<int64_t>(
         1, std::min<int64_t>(((int64_t)d->gd_nitems * 32 + dev::kDenseThreads - 1) / dev::kDenseThreads, d->sm_count));
-    if (d->variant == PB_VARIANT_G32)
-      dev::k_stream_g_dense<dev::MODE_VJP, float><<<gdg, dev::kDenseThreads, smem, st>>>(
-          d->gd_items, d->gd_nitems, g, (const float *)d->g2d, d->gd_npp, d->nmodes, d->gstate, ns, d->part, lam32);
-    else
-      dev::k_stream_g_dense<dev::MODE_VJP, __nv_bfloat16><<<gdg, dev::kDenseThreads, smem, st>>>(
-          d->gd_items, d->gd_nitems, g, (const __nv_bfloat16 *)d->g2d, d->gd_npp, d->nmodes, d->gstate, ns, d->part, lam32);
+    with_g2t(d->variant, [&](auto tag) {
+      using T = std::remove_pointer_t<decltype(tag)>;
+      dev::k_stream_g_dense<dev::MODE_VJP, T><<<gdg, dev::kDenseThreads, smem, st>>>(
+          d->gd_items, d->gd_nitems, g, (const T *)d->g2d, d->gd_npp, d->nmodes, d->gstate, ns, d->part, lam32);
+    });
     PB_LAUNCHED("k_stream_g_dense (vjp)");
   } else {
-    if (d->variant == PB_VARIANT_G32)
-      dev::k_stream_g_vjp<float><<<grid, 512, smem, st>>>(d->items, n, g, (const float *)d->g2lo, d->gstate, lam32, ns, d->part);
-    else
-      dev::k_stream_g_vjp<__nv_bfloat16><<<grid, 512, smem, st>>>(d->items, n, g, (const __nv_bfloat16 *)d->g2lo, d->gstate,
-                                                                  lam32, ns, d->part);
+    with_g2t(d->variant, [&](auto tag) {
+      using T = std::remove_pointer_t<decltype(tag)>;
+      dev::k_stream_g_vjp<T><<<grid, 512, smem, st>>>(d->items, n, g, (const T *)d->g2lo, d->gstate, lam32, ns, d->part);
+    });
     PB_LAUNCHED("k_stream_g_vjp");
   }
-  dev::k_fin_rate<true><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->fwd_item_ptr(), d->part}, ns, -d->c * d->gnorm(), d->R, mu);
+  dev::k_fin_rate<true><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->fwd_item_ptr(), d->part}, ns, -d->gscale(), d->R, mu);
   PB_LAUNCHED("k_fin_rate (vjp)");
   if (acc_out) {
     dev::k_lincomb<<<(ns + 255) / 256, 256, 0, st>>>(ns, 1.0, acc_in, 1.0, mu, acc_out);

@@ -19,6 +19,7 @@
 
 #include <cstdint>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace pb {
@@ -1020,13 +1021,37 @@ __device__ __forceinline__ float g_term(const GGeom &g, uint4 ss, uint4 sp, uint
   return g2 * fmaf(Dg, fpl, fmaf(Dg, fp, GN + Ge));
 }
 
-// four consecutive |g|^2 values as FP32 (a 16-byte FP32 load or an 8-byte BF16 load)
+// 16-bit |g|^2 storage: BF16, or FP16 holding |g|^2 times a power of two (the H16 variant;
+// the factor is taken out with the collision prefactor).  Two packed values (the lower
+// address in the low half) as FP32:
+template <typename G2T>
+__device__ __forceinline__ float2 g2_pair16(unsigned w) {
+  return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u));
+}
+template <>
+__device__ __forceinline__ float2 g2_pair16<__half>(unsigned w) {
+  return make_float2(__half2float(__ushort_as_half((unsigned short)(w & 0xFFFFu))),
+                     __half2float(__ushort_as_half((unsigned short)(w >> 16))));
+}
+// |g|^2 (times the storage factor) in the storage type, rounded to nearest
+template <typename G2T>
+__device__ __forceinline__ void g2_store(G2T *__restrict__ out, size_t i, double v);
+template <>
+__device__ __forceinline__ void g2_store<float>(float *__restrict__ out, size_t i, double v) { out[i] = __double2float_rn(v); }
+template <>
+__device__ __forceinline__ void g2_store<__nv_bfloat16>(__nv_bfloat16 *__restrict__ out, size_t i, double v) {
+  out[i] = __double2bfloat16(v);
+}
+template <>
+__device__ __forceinline__ void g2_store<__half>(__half *__restrict__ out, size_t i, double v) { out[i] = __double2half(v); }
+
+// four consecutive |g|^2 values as FP32 (a 16-byte FP32 load or an 8-byte 16-bit load)
 template <typename G2T>
 __device__ __forceinline__ float4 load_g2x4(const G2T *__restrict__ g2v, long long q) {
   if (sizeof(G2T) == 4) return __ldcs((const float4 *)g2v + q);
   const uint2 v = __ldcs((const uint2 *)g2v + q);
-  return make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xFFFF0000u), __uint_as_float(v.y << 16),
-                     __uint_as_float(v.y & 0xFFFF0000u));
+  const float2 a = g2_pair16<G2T>(v.x), b = g2_pair16<G2T>(v.y);
+  return make_float4(a.x, a.y, b.x, b.y);
 }
 
 // part[item].x = sum over the item of the channel terms above.
@@ -1089,6 +1114,10 @@ __device__ __forceinline__ float g2_at<float>(const float *__restrict__ g2v, lon
 template <>
 __device__ __forceinline__ float g2_at<__nv_bfloat16>(const __nv_bfloat16 *__restrict__ g2v, long long i) {
   return __uint_as_float((unsigned)__ldcs((const unsigned short *)g2v + i) << 16);
+}
+template <>
+__device__ __forceinline__ float g2_at<__half>(const __half *__restrict__ g2v, long long i) {
+  return __half2float(__ushort_as_half(__ldcs((const unsigned short *)g2v + i)));
 }
 
 // L2 prefetch of the 128-channel trip that starts at channel c (inside the item): lanes 0-3
@@ -1276,9 +1305,9 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_stream_g_dense(const Item 
                 gv[2 * k] = v.x;
                 gv[2 * k + 1] = v.y;
               } else {
-                const unsigned w = __ldcs(reinterpret_cast<const unsigned *>(gq) + k);
-                gv[2 * k] = __uint_as_float(w << 16);
-                gv[2 * k + 1] = __uint_as_float(w & 0xFFFF0000u);
+                const float2 v = g2_pair16<G2T>(__ldcs(reinterpret_cast<const unsigned *>(gq) + k));
+                gv[2 * k] = v.x;
+                gv[2 * k + 1] = v.y;
               }
             }
         } else {
@@ -1303,14 +1332,15 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_stream_g_dense(const Item 
   }
 }
 
-// g2d[(r * npp + p) * nm + nu] = |g|^2 of the stored channel (r, p, nu) in the storage type
-// (round to nearest); the array is cleared before, so missing channels keep zero slots
+// g2d[(r * npp + p) * nm + nu] = s2 |g|^2 of the stored channel (r, p, nu) in the storage type
+// (round to nearest; s2 a power of two); the array is cleared before, so missing channels keep
+// zero slots
 template <typename G2T>
 __global__ void __launch_bounds__(kBlock) k_dense_g2(const Item *__restrict__ items, int nitems,
                                                      const long long *__restrict__ rp_pad,
                                                      const long long *__restrict__ rp_real,
                                                      const uint32_t *__restrict__ col, const double *__restrict__ g2,
-                                                     int nm, int npp, G2T *__restrict__ g2d) {
+                                                     int nm, int npp, G2T *__restrict__ g2d, double s2) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -1324,10 +1354,7 @@ __global__ void __launch_bounds__(kBlock) k_dense_g2(const Item *__restrict__ it
       const long long c = I.start + j;
       const unsigned cw = col[c];
       const size_t slot = ((size_t)r * npp + (cw & 0xFFFFFFu)) * (size_t)nm + (cw >> 24);
-      if (sizeof(G2T) == 4)
-        ((float *)g2d)[slot] = __double2float_rn(g2[c]);
-      else
-        ((__nv_bfloat16 *)g2d)[slot] = __double2bfloat16(g2[c]);
+      g2_store(g2d, slot, s2 * g2[c]);
     }
   }
 }
@@ -1488,14 +1515,16 @@ __global__ void __launch_bounds__(kBlock) k_g2acc_g(const float4 *__restrict__ t
   }
 }
 
-// |g|^2 in the storage type of the mixed-precision variants (round to nearest)
+// s2 |g|^2 in the storage type of the mixed-precision variants (round to nearest; s2 is a
+// power of two, 1 but for FP16).  A value that overflows FP16 sets *err = kErrG2Range.
+constexpr int kErrG2Range = 16;
 template <typename G2T>
-__global__ void k_cvt_g2(const double *__restrict__ g2, long long n, G2T *__restrict__ out) {
+__global__ void k_cvt_g2(const double *__restrict__ g2, long long n, G2T *__restrict__ out, double s2,
+                         int *__restrict__ err) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    if (sizeof(G2T) == 4)
-      ((float *)out)[i] = __double2float_rn(g2[i]);
-    else
-      ((__nv_bfloat16 *)out)[i] = __double2bfloat16(g2[i]);
+    const double v = s2 * g2[i];
+    g2_store(out, (size_t)i, v);
+    if (sizeof(G2T) == 2 && fabs(v) >= 65520.0) *err = kErrG2Range;  // rounds to FP16 infinity
   }
 }
 
