@@ -181,12 +181,15 @@ def test_trajectory_gradient_finite_differences_24cubed(pb):
 
 # ------------------------------------------------------------------ FP32 adjoint (G32 variant)
 
-def test_fp32_collision_vjp_against_fp64_oracle(pb):
+@pytest.mark.parametrize("variant,vjp_tol", [("g32", 1e-5), ("h16", 1e-3)])
+def test_fp32_collision_vjp_against_fp64_oracle(pb, variant, vjp_tol):
+    """FP32 adjoint against the FP64 oracle; with FP16 |g|^2 (h16) the VJP carries the 2^-11
+    rounding of |g|^2 while the |g|^2 gradient (whose bracket has no |g|^2) keeps FP32 accuracy."""
     import torch
 
     m = synth.make_window4(16)
     ch = pb.Channels.from_model(m)
-    dev = pb.Device(ch, variant="g32")
+    dev = pb.Device(ch, variant=variant)
     o = oracle.Oracle(m)
     rng = np.random.default_rng(31)
     f = rng.uniform(0, 1, o.nstate)
@@ -194,14 +197,14 @@ def test_fp32_collision_vjp_against_fp64_oracle(pb):
     gg2 = torch.zeros(dev.nchannels, dtype=torch.float64, device="cuda")
     g = dev.collision_vjp(T(f), T(lam), grad_g2=gg2).cpu().numpy()
     err = nrel(g, o.collision_vjp(f, lam))
-    print(f"fp32 vjp normwise error {err:.2e}")
-    assert err <= 1e-5
+    print(f"{variant} vjp normwise error {err:.2e}")
+    assert err <= vjp_tol
     e = ch.export()
     rows = np.repeat(np.arange(ch.nstate), np.diff(e["row_ptr"]))
     pick = rng.choice(ch.nchannels, size=500, replace=False)
     ref = o.g2_grad(f, lam, rows[pick], e["col"][pick], e["nu"][pick])
     err2 = nrel(gg2.cpu().numpy()[pick], ref)
-    print(f"fp32 g2-gradient normwise error {err2:.2e}")
+    print(f"{variant} g2-gradient normwise error {err2:.2e}")
     assert err2 <= 1e-5
 
 
