@@ -266,6 +266,30 @@ def test_tile_sweep_shapes(pb, name, tile_sweep):
     assert np.abs(other.collision(T(f)).cpu().numpy() - I).max() <= MUTUAL * ab.max()
 
 
+@pytest.mark.parametrize("name", ["odd81", "win16"])
+def test_tile_sweep_signed_inputs(pb, name):
+    """The bulk-copy tile sweep takes cheaper sums where a tile's occupations and every
+    coefficient are non-negative (the coefficients always are on this path: the builder
+    rejects negative |g|^2, and pb_dev_set_g2 leaves the tiles for the row stream).
+    Occupations of both signs (tiles of either kind in one launch) still meet the oracle, and
+    so do their absolute values (the cheaper sums throughout)."""
+    m = SMALL[name]()
+    o = oracle.Oracle(m)
+    ch = pb.Channels.from_model(m)
+    dev = pb.Device(ch, tile_sweep=2)
+    rng = np.random.default_rng(35)
+    f = rng.uniform(0, 1, o.nstate)
+    f[rng.choice(o.nstate, size=o.nstate // 10, replace=False)] *= -0.5
+    ref, ab = o.collision(f, with_abs=True)
+    I = dev.collision(T(f)).cpu().numpy()
+    check_I(I, ref, ab)
+    fp = np.abs(f)
+    refp, abp = o.collision(fp, with_abs=True)
+    Ip = dev.collision(T(fp)).cpu().numpy()
+    check_I(Ip, refp, abp)
+    dev.check()
+
+
 def test_time_sweep_measures_without_changing_results(pb):
     m = SMALL["win12"]()
     o = oracle.Oracle(m)
