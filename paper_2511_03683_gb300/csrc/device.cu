@@ -1686,10 +1686,9 @@ int coef_setup(pb_dev *d, cudaStream_t st) {
     }
     if (d->sym) {
       const long long n = (long long)d->td.nt * dev::kTile * dev::kTile;
-      PB_CUDA(cudaMemsetAsync(d->err + 1, 0, sizeof(int), st));  // the negative-coefficient flag
       dev::k_tiles_fill<<<(int)std::min<long long>((n + 255) / 256, 8192), 256, 0, st>>>(
           d->tiles, d->td.nt, (const float2 *)d->coefA, (const float2 *)d->coefB, (const long long *)d->srp,
-          (int)d->ns, d->tcoef, d->err + 1);
+          (int)d->ns, d->tcoef);
       PB_LAUNCHED("k_tiles_fill");
     }
   }

@@ -831,21 +831,6 @@ __device__ __forceinline__ void ff_mac_lazy(float &h, float &l, float2 x, float 
   h = s;
 }
 
-// ff_mac_lazy for a sum of non-negative terms (x.x >= 0, ah >= 0, so h >= 0 and every product
-// x.x * ah >= 0): the larger of h and the product is the first operand of a Fast2Sum, whose
-// error term is then exact (two min/max and three additions instead of six additions)
-__device__ __forceinline__ void ff_mac_nn(float &h, float &l, float2 x, float ah, float al) {
-  const float p = __fmul_rn(x.x, ah);
-  float e = __fmaf_rn(x.x, ah, -p);
-  e = __fmaf_rn(x.x, al, e);
-  e = __fmaf_rn(x.y, ah, e);
-  const float s = __fadd_rn(h, p);
-  const float a = fmaxf(h, p), b = fminf(h, p);
-  const float err = __fsub_rn(b, __fsub_rn(s, a));
-  l = __fadd_rn(l, __fadd_rn(err, e));
-  h = s;
-}
-
 // (h, l) = x * (ah, al): the first term of a lazily accumulated float-float sum (no addition)
 __device__ __forceinline__ void ff_prod(float &h, float &l, float2 x, float ah, float al) {
   h = __fmul_rn(x.x, ah);
@@ -2051,12 +2036,10 @@ __global__ void __launch_bounds__(kBlock) k_paper_gather(const Item *__restrict_
 constexpr int kTile = 64;
 
 // tc[t][i][j] from the branch-merged coefficients of complete rows (entry (s, p) of row s is
-// at srp[s] + p); zero outside the nstate states.  *neg = 1 if a high word is negative, which
-// non-negative |g|^2 excludes (the tiles are built from the channel list, whose builder rejects
-// negative values); the tile sweep would then keep its general float-float sums.
+// at srp[s] + p); zero outside the nstate states.
 __global__ void k_tiles_fill(const int2 *__restrict__ tiles, int nt, const float2 *__restrict__ coefA,
                              const float2 *__restrict__ coefB, const long long *__restrict__ srp, int ns,
-                             float4 *__restrict__ tc, int *__restrict__ neg) {
+                             float4 *__restrict__ tc) {
   const long long n = (long long)nt * kTile * kTile;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const int t = (int)(e / (kTile * kTile)), k = (int)(e % (kTile * kTile));
@@ -2069,7 +2052,6 @@ __global__ void k_tiles_fill(const int2 *__restrict__ tiles, int nt, const float
       const double pin = ff_to_double(a.x, a.y), pout = pin + ff_to_double(b.x, b.y);
       const float2 x = ff_split(pin), y = ff_split(pout);
       v = make_float4(x.x, x.y, y.x, y.y);
-      if (x.x < 0.f || y.x < 0.f) *neg = 1;
     }
     tc[e] = v;
   }
@@ -2150,10 +2132,8 @@ __global__ void __launch_bounds__(256, 3) k_stream_sym(const int2 *__restrict__ 
 // and columns tj, tj+16, tj+32, tj+48, so a quarter-warp reads 128 contiguous bytes of a row
 // (no bank conflicts).  Row partials are reduced inside the warp by a float-float reduce-scatter
 // over the 16 lanes of a row; column partials by one shuffle level into a per-warp table that
-// the next iteration combines (double-buffered), so each tile costs one CTA barrier.  Where the
-// tile's occupations and (flag err[1] == 0, set by k_tiles_fill) all coefficients are
-// non-negative, the float-float sums take the cheaper non-negative form (ff_mac_nn).  Every
-// wait is bounded: on a give-up the kernel records it in err[0], waits (bounded) for its own
+// the next iteration combines (double-buffered), so each tile costs one CTA barrier.  Every
+// wait is bounded: on a give-up the kernel records it in *err, waits (bounded) for its own
 // copies and returns.
 constexpr int kSymStages = 3;
 constexpr int kSymThreads = 256;
@@ -2177,47 +2157,6 @@ __device__ __forceinline__ void sym_columns_out(const float2 *__restrict__ colre
   if (g == 0) ((float2 *)tp)[2 * ((long long)(IJ.y * kTile + col) * nb + IJ.x) + comp] = acc;
 }
 
-// the 4 x R products of thread (ti, tj) in one staged tile: each accumulator's first term is a
-// plain product (no zeroing, no addition); NN: every term is non-negative
-template <int R, bool NN>
-__device__ __forceinline__ void sym_tile_macs(const float4 *__restrict__ T, int ti, int tj, bool diag,
-                                              const float2 (&fcol)[4], const float2 (&frow)[R], float (&rA)[R][2],
-                                              float (&rC)[R][2], float (&cA)[4][2], float (&cC)[4][2]) {
-#pragma unroll
-  for (int i = 0; i < R; ++i) {
-    const int row = ti * R + i;
-    const float2 fs = frow[i];
-    float4 e[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) e[j] = T[row * kTile + tj + 16 * j];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (j == 0) {
-        ff_prod(rA[i][0], rA[i][1], fcol[j], e[j].x, e[j].y);
-        ff_prod(rC[i][0], rC[i][1], fcol[j], e[j].z, e[j].w);
-      } else if (NN) {
-        ff_mac_nn(rA[i][0], rA[i][1], fcol[j], e[j].x, e[j].y);
-        ff_mac_nn(rC[i][0], rC[i][1], fcol[j], e[j].z, e[j].w);
-      } else {
-        ff_mac_lazy(rA[i][0], rA[i][1], fcol[j], e[j].x, e[j].y);
-        ff_mac_lazy(rC[i][0], rC[i][1], fcol[j], e[j].z, e[j].w);
-      }
-      if (!diag) {
-        if (i == 0) {
-          ff_prod(cA[j][0], cA[j][1], fs, e[j].z, e[j].w);
-          ff_prod(cC[j][0], cC[j][1], fs, e[j].x, e[j].y);
-        } else if (NN) {
-          ff_mac_nn(cA[j][0], cA[j][1], fs, e[j].z, e[j].w);
-          ff_mac_nn(cC[j][0], cC[j][1], fs, e[j].x, e[j].y);
-        } else {
-          ff_mac_lazy(cA[j][0], cA[j][1], fs, e[j].z, e[j].w);
-          ff_mac_lazy(cC[j][0], cC[j][1], fs, e[j].x, e[j].y);
-        }
-      }
-    }
-  }
-}
-
 __global__ void __launch_bounds__(kSymThreads, 1) k_stream_sym_bulk(const int2 *__restrict__ tiles, int nt,
                                                                      const float4 *__restrict__ tc,
                                                                      const float2 *__restrict__ fg, int ns, int nb,
@@ -2229,7 +2168,6 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_stream_sym_bulk(const int2 *
   float2 *colred0 = (float2 *)(ssm + kSymStages * kSymStageBytes + 64);  // 2 x [8 warps][A | C][64 columns]
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, tj = tid & 15, ti = tid >> 4;
   const int G = (int)gridDim.x;
-  const bool coef_nn = err[1] == 0;  // k_tiles_fill found no negative coefficient
   const int nloc = (int)blockIdx.x < nt ? (nt - 1 - (int)blockIdx.x) / G + 1 : 0;
   // the f slices of every stage start as zeros (a copy of a last, partial block leaves the rest)
   for (int i = tid; i < kSymStages * 2 * kTile; i += kSymThreads) {
@@ -2286,23 +2224,38 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_stream_sym_bulk(const int2 *
     const float4 *__restrict__ T = (const float4 *)(ssm + (size_t)s * kSymStageBytes);
     const float2 *__restrict__ fr = (const float2 *)(ssm + (size_t)s * kSymStageBytes + kTileBytes);
     const float2 *__restrict__ fc = fr + kTile;
-    float2 fcol[4], frow[R];
+    float2 fcol[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) fcol[j] = fc[tj + 16 * j];
-#pragma unroll
-    for (int i = 0; i < R; ++i) frow[i] = fr[ti * R + i];
-    // non-negative occupations and coefficients (the physical case) take the cheaper
-    // non-negative sums; the choice is warp-uniform and per tile
-    bool nn = coef_nn;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) nn = nn && fcol[j].x >= 0.f;
-#pragma unroll
-    for (int i = 0; i < R; ++i) nn = nn && frow[i].x >= 0.f;
+    // each accumulator's first term is a plain product (no zeroing, no addition)
     float rA[R][2], rC[R][2], cA[4][2], cC[4][2];
-    if (__all_sync(0xFFFFFFFFu, nn))
-      sym_tile_macs<R, true>(T, ti, tj, diag, fcol, frow, rA, rC, cA, cC);
-    else
-      sym_tile_macs<R, false>(T, ti, tj, diag, fcol, frow, rA, rC, cA, cC);
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int row = ti * R + i;
+      const float2 fs = fr[row];
+      float4 e[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) e[j] = T[row * kTile + tj + 16 * j];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (j == 0) {
+          ff_prod(rA[i][0], rA[i][1], fcol[j], e[j].x, e[j].y);
+          ff_prod(rC[i][0], rC[i][1], fcol[j], e[j].z, e[j].w);
+        } else {
+          ff_mac_lazy(rA[i][0], rA[i][1], fcol[j], e[j].x, e[j].y);
+          ff_mac_lazy(rC[i][0], rC[i][1], fcol[j], e[j].z, e[j].w);
+        }
+        if (!diag) {
+          if (i == 0) {
+            ff_prod(cA[j][0], cA[j][1], fs, e[j].z, e[j].w);
+            ff_prod(cC[j][0], cC[j][1], fs, e[j].x, e[j].y);
+          } else {
+            ff_mac_lazy(cA[j][0], cA[j][1], fs, e[j].z, e[j].w);
+            ff_mac_lazy(cC[j][0], cC[j][1], fs, e[j].x, e[j].y);
+          }
+        }
+      }
+    }
     // rows: the 16 lanes of a half-warp share them; lane tj ends with value idx (row, A | C)
     {
       float2 v[NV];

@@ -268,11 +268,9 @@ def test_tile_sweep_shapes(pb, name, tile_sweep):
 
 @pytest.mark.parametrize("name", ["odd81", "win16"])
 def test_tile_sweep_signed_inputs(pb, name):
-    """The bulk-copy tile sweep takes cheaper sums where a tile's occupations and every
-    coefficient are non-negative (the coefficients always are on this path: the builder
-    rejects negative |g|^2, and pb_dev_set_g2 leaves the tiles for the row stream).
-    Occupations of both signs (tiles of either kind in one launch) still meet the oracle, and
-    so do their absolute values (the cheaper sums throughout)."""
+    """The bulk-copy tile sweep with occupations of both signs (outside the physical [0, 1]:
+    products and partial sums of either sign in the float-float tile sums) and with their
+    absolute values, against the oracle."""
     m = SMALL[name]()
     o = oracle.Oracle(m)
     ch = pb.Channels.from_model(m)
