@@ -165,7 +165,7 @@ typedef struct pb_dev_opts {
                                 1024-thread CTA per SM with F in shared memory (5 if F does not fit) and
                                 the next trip in registers, 5 the same through L1, 6 = 3 with lazy sums */
   int32_t transport_ctas;    /* resident 256-thread transport CTAs per SM, 1..8 (0 = 8 with L1 gathers) */
-  int32_t channel_per_lane;  /* FP32/BF16 sweep shape: 0 automatic (= 5 when the channel list fills at
+  int32_t channel_per_lane;  /* FP32/BF16/FP16 sweep shape: 0 automatic (= 5 when the channel list fills at
                                 least 85% of the (state, branch, partner) slots, else 4); one channel per
                                 lane in 512-thread CTAs, three per SM: 1 plain, 3 with an L2 prefetch of the
                                 stream two 128-channel trips ahead; 2 four-channel groups per lane; 4 one
@@ -196,7 +196,7 @@ typedef struct pb_dev_opts {
                                 its bounded waits reporting through pb_dev_check */
   int32_t adjoint;           /* 1: reserve the accumulators of the deferred |g|^2 gradient
                                 (pb_rtbte_rk4_vjp_defer): FF with branch merging, one float-float
-                                (u, v) per stored state pair (16 bytes); G32/G16, three doubles per
+                                (u, v) per stored state pair (16 bytes); G32/G16/H16, three doubles per
                                 (state, partner) pair (24 nstate^2 bytes); ignored otherwise */
 } pb_dev_opts;
 
@@ -301,7 +301,7 @@ int pb_transport_map(pb_dev *dev, const double *f0, const double *vel3, const do
  * shared |g|^2 of a channel and its reverse is the sum of the two entries.  The transposed
  * sum is evaluated as a gather over each state's own row (the list is closed under
  * s <-> p), so no atomic updates are needed.  Needs a PB_VARIANT_FF device (FP64-accurate) or a
- * PB_VARIANT_G32 / G16 device (FP32 per-channel terms, FP64 accumulation). */
+ * PB_VARIANT_G32 / G16 / H16 device (FP32 per-channel terms, FP64 accumulation). */
 int pb_collision_vjp(pb_dev *dev, const double *f, const double *lam, double *grad_f, double *grad_g2,
                      void *stream);
 
@@ -314,7 +314,7 @@ int pb_rtbte_rk4_vjp(pb_dev *dev, const double *f, double *lam, double dt, doubl
  * channel, the step adds the stage sums that the gradient of a state pair needs (the pair's
  * branches and modes share them) into the handle's per-pair accumulators; pb_dev_g2grad_flush
  * applies them.  Needs a device created with pb_dev_opts.adjoint = 1 on the FF variant with
- * branch merging or on G32/G16 (PB_EINVAL otherwise). */
+ * branch merging or on G32/G16/H16 (PB_EINVAL otherwise). */
 int pb_rtbte_rk4_vjp_defer(pb_dev *dev, const double *f, double *lam, double dt, void *stream);
 
 /* grad_g2 (device double[nchannels], CSR order) += the |g|^2 gradient accumulated by

@@ -876,13 +876,13 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
     fbytes = sizeof(uint4) * (size_t)d->ns;
     if (fbytes + 1024 > (size_t)smem_optin) {
       delete d;
-      return set_error(PB_EINVAL, "pb_dev_create: the FP32/BF16 variants stage 16 bytes per state in shared memory; "
+      return set_error(PB_EINVAL, "pb_dev_create: the FP32/BF16/FP16 variants stage 16 bytes per state in shared memory; "
                                   "%lld states exceed it", (long long)ch->nstate);
     }
     for (int i = 0; i < 3; ++i) d->rad[i] = ch->nk[i] > 1 ? 2 * ch->nk[i] : 1;
     if ((double)d->rad[0] * d->rad[1] * d->rad[2] * ch->nmodes >= (double)(1 << dev::kRecLnmBits)) {
       delete d;
-      return set_error(PB_EINVAL, "pb_dev_create: the FP32/BF16 variants need (2 N1)(2 N2)(2 N3) nmodes < 2^27 "
+      return set_error(PB_EINVAL, "pb_dev_create: the FP32/BF16/FP16 variants need (2 N1)(2 N2)(2 N3) nmodes < 2^27 "
                                   "(padded phonon table index in the state records)");
     }
     d->ctas = (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(228 * 1024) / (fbytes + 1024)));  // of 512 threads
@@ -1719,7 +1719,7 @@ int vjp_launch_mixed(pb_dev *d, const double *f, const double *lam, double wl, c
                      double *mu, const double *acc_in, double *acc_out, int slot, cudaStream_t st) {
   const int ns = (int)d->ns, n = (int)d->nitems;
   if (!d->vjp_g_ok)
-    return set_error(PB_EINVAL, "pb_collision_vjp: the FP32/BF16 adjoint stages 20 bytes per state in shared "
+    return set_error(PB_EINVAL, "pb_collision_vjp: the FP32/BF16/FP16 adjoint stages 20 bytes per state in shared "
                                 "memory; %d states exceed it", ns);
   int rc = stage_input(d, f, st);
   if (rc) return rc;
@@ -1882,7 +1882,7 @@ extern "C" int pb_collision_vjp(pb_dev *d, const double *f, const double *lam, d
   clear_error();
   if (!d || !f || !lam || !grad_f) return set_error(PB_EINVAL, "pb_collision_vjp: null argument");
   if (d->variant != PB_VARIANT_FF && !d->mixed())
-    return set_error(PB_EINVAL, "pb_collision_vjp: needs the FF, G32 or G16 variant");
+    return set_error(PB_EINVAL, "pb_collision_vjp: needs the FF, G32, G16 or H16 variant");
   cudaStream_t st = (cudaStream_t)stream;
   const int slot = grad_g2 ? 0 : -1;
   if (d->mixed()) {
@@ -1954,7 +1954,7 @@ int rk4_vjp_impl(pb_dev *d, const double *f, double *lam, double dt, double *gra
 int rk4_vjp_check(pb_dev *d, const double *f, const double *lam, double dt, const char *who) {
   if (!d || !f || !lam) return set_error(PB_EINVAL, "%s: null argument", who);
   if (d->variant != PB_VARIANT_FF && !d->mixed())
-    return set_error(PB_EINVAL, "%s: needs the FF, G32 or G16 variant", who);
+    return set_error(PB_EINVAL, "%s: needs the FF, G32, G16 or H16 variant", who);
   if (!std::isfinite(dt)) return set_error(PB_EINVAL, "%s: bad dt", who);
   return PB_OK;
 }
