@@ -1970,7 +1970,7 @@ extern "C" int pb_rtbte_rk4_vjp_defer(pb_dev *d, const double *f, double *lam, d
   clear_error();
   if (int rc = rk4_vjp_check(d, f, lam, dt, "pb_rtbte_rk4_vjp_defer")) return rc;
   if (!d->gacc && !d->gaccg)
-    return set_error(PB_EINVAL, "pb_rtbte_rk4_vjp_defer: needs a device created with adjoint = 1 (FF branch-merged, G32 or G16)");
+    return set_error(PB_EINVAL, "pb_rtbte_rk4_vjp_defer: needs a device created with adjoint = 1 (FF branch-merged, G32, G16 or H16)");
   return rk4_vjp_impl(d, f, lam, dt, nullptr, true, stream);
 }
 
