@@ -2128,13 +2128,11 @@ __global__ void __launch_bounds__(256, 3) k_stream_sym(const int2 *__restrict__ 
 // The same tile sweep with the tiles staged through shared memory by bulk copies
 // (cp.async.bulk, completion counted in bytes on an mbarrier): one persistent 256-thread CTA per
 // SM; thread 0 keeps kSymStages tiles in flight (each with the float-float f of its row and
-// column blocks).  The CTA copies the staged tile into registers (16 entries per thread) and
-// hands its stage back to the copies at once, so all kSymStages stages are in flight while the
-// tile is added.  Thread (ti, tj) takes rows 4ti .. 4ti+3 and columns tj, tj+16, tj+32, tj+48,
-// so a quarter-warp reads 128 contiguous bytes of a row (no bank conflicts).  Row partials are
-// reduced inside the warp by a float-float reduce-scatter over the 16 lanes of a row; column
-// partials by one shuffle level into a per-warp table that the next iteration combines
-// (double-buffered); each tile costs two CTA barriers.  Every
+// column blocks) while the CTA adds the staged tile.  Thread (ti, tj) takes rows 4ti .. 4ti+3
+// and columns tj, tj+16, tj+32, tj+48, so a quarter-warp reads 128 contiguous bytes of a row
+// (no bank conflicts).  Row partials are reduced inside the warp by a float-float reduce-scatter
+// over the 16 lanes of a row; column partials by one shuffle level into a per-warp table that
+// the next iteration combines (double-buffered), so each tile costs one CTA barrier.  Every
 // wait is bounded: on a give-up the kernel records it in *err, waits (bounded) for its own
 // copies and returns.
 constexpr int kSymStages = 3;
@@ -2205,11 +2203,17 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_stream_sym_bulk(const int2 *
   bool ok = true;
   for (int k = 0; k <= nloc; ++k) {
     // thread 0 waits on the mbarrier of tile k (acquire); the CTA barrier publishes the stage
-    // to all, and marks the end of tile k-1 (its column table complete)
+    // to all, and marks the end of tile k-1 (its stage is free, its column table complete)
     const bool have = k < nloc;
     if (!__syncthreads_and(tid == 0 && have ? mbar_wait(bars + k % kSymStages, (unsigned)((k / kSymStages) & 1)) : true)) {
       ok = false;
       break;
+    }
+    if (tid == 0 && k >= 1 && issued < nloc) {
+      fence_proxy_async();  // order the generic reads of tile k-1's stage before its refill
+      issue(issued, nextIJ);
+      ++issued;
+      if (issued < nloc) nextIJ = tiles[(int)blockIdx.x + issued * G];
     }
     if (k >= 1 && prevIJ.x != prevIJ.y) sym_columns_out(colred0 + ((k - 1) & 1) * (kSymColBytes / sizeof(float2)), prevIJ, nb, lane, wid, tp);
     if (!have) break;
@@ -2220,32 +2224,18 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_stream_sym_bulk(const int2 *
     const float4 *__restrict__ T = (const float4 *)(ssm + (size_t)s * kSymStageBytes);
     const float2 *__restrict__ fr = (const float2 *)(ssm + (size_t)s * kSymStageBytes + kTileBytes);
     const float2 *__restrict__ fc = fr + kTile;
-    // the thread's entries and occupations of tile k into registers; once every thread holds
-    // them the stage takes tile k + kSymStages, so kSymStages copies stay in flight while the
-    // tile is added
-    float2 fcol[4], frow[R];
-    float4 E[R][4];
+    float2 fcol[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) fcol[j] = fc[tj + 16 * j];
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-      frow[i] = fr[ti * R + i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) E[i][j] = T[(ti * R + i) * kTile + tj + 16 * j];
-    }
-    __syncthreads();
-    if (tid == 0 && issued < nloc) {
-      fence_proxy_async();  // order the generic reads of tile k's stage before its refill
-      issue(issued, nextIJ);
-      ++issued;
-      if (issued < nloc) nextIJ = tiles[(int)blockIdx.x + issued * G];
-    }
     // each accumulator's first term is a plain product (no zeroing, no addition)
     float rA[R][2], rC[R][2], cA[4][2], cC[4][2];
 #pragma unroll
     for (int i = 0; i < R; ++i) {
-      const float2 fs = frow[i];
-      const float4 *e = E[i];
+      const int row = ti * R + i;
+      const float2 fs = fr[row];
+      float4 e[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) e[j] = T[row * kTile + tj + 16 * j];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         if (j == 0) {
