@@ -167,3 +167,22 @@ def test_adjoint_accumulators_are_sized_per_state_pair(pb):
     g32 = pb.VARIANTS["g32"]
     grow = arena(adjoint=1, variant=g32) - arena(variant=g32)
     assert abs(grow - 24 * ch.nstate ** 2) <= 4096  # up to the alignment of the arena regions
+
+
+def test_fp16_variant_sizes_like_bf16(pb):
+    """The FP16 |g|^2 variant (h16) keeps 2 bytes per value like BF16 (g16): the same arena."""
+    import ctypes
+
+    ch = pb.Channels.from_model(synth.make_window4(12))
+    L = pb.lib()
+    sizes = []
+    for v in ("g16", "h16"):
+        o = pb._DevOpts()
+        o.variant = pb.VARIANTS[v]
+        n = ctypes.c_size_t(0)
+        assert L.pb_dev_arena_bytes(ch._h, ctypes.byref(o), ctypes.byref(n)) == pb.PB_OK
+        sizes.append(n.value)
+    assert sizes[0] == sizes[1]
+    o = pb._DevOpts()
+    o.variant = 7
+    assert L.pb_dev_arena_bytes(ch._h, ctypes.byref(o), ctypes.byref(ctypes.c_size_t(0))) == pb.PB_EINVAL
