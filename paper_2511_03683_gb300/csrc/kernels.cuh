@@ -18,6 +18,8 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -1524,7 +1526,7 @@ __global__ void k_cvt_g2(const double *__restrict__ g2, long long n, G2T *__rest
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double v = s2 * g2[i];
     g2_store(out, (size_t)i, v);
-    if (sizeof(G2T) == 2 && fabs(v) >= 65520.0) *err = kErrG2Range;  // rounds to FP16 infinity
+    if (std::is_same<G2T, __half>::value && fabs(v) >= 65520.0) *err = kErrG2Range;  // rounds to FP16 infinity
   }
 }
 

@@ -459,6 +459,23 @@ def test_fp16_storage_overflow_is_reported(pb):
     assert np.abs(dev.collision(f).cpu().numpy() - I0).max() <= 1e-7 * np.abs(I0).max()
 
 
+def test_bf16_storage_takes_large_values(pb):
+    """The FP16 range check is the H16 variant's alone: BF16 storage (FP32 range) takes |g|^2
+    a million times larger without a report, and the integral scales with it."""
+    import torch
+
+    m = SMALL["win16"]()
+    ch = pb.Channels.from_model(m)
+    dev = pb.Device(ch, variant="g16")
+    f = T(np.random.default_rng(6).uniform(0, 1, dev.nstate))
+    I0 = dev.collision(f).cpu().numpy()
+    g2 = torch.tensor(ch.export()["g2"], dtype=torch.float64, device="cuda")
+    dev.set_g2(2.0 ** 20 * g2)
+    I1 = dev.collision(f).cpu().numpy()
+    dev.check()
+    assert np.abs(I1 - 2.0 ** 20 * I0).max() <= 1e-6 * 2.0 ** 20 * np.abs(I0).max()
+
+
 @pytest.mark.parametrize("variant", ["g32", "g16", "h16"])
 def test_mixed_precision_rk4(pb, variant):
     m, o, dev = setup_case(pb, "tiny8", variant)
