@@ -310,15 +310,21 @@ int pb_collision_vjp(pb_dev *dev, const double *f, const double *lam, double *gr
  * stage inputs are recomputed from f. */
 int pb_rtbte_rk4_vjp(pb_dev *dev, const double *f, double *lam, double dt, double *grad_g2, void *stream);
 
-/* The same RK4 adjoint step with the |g|^2 gradient deferred: instead of updating every stored
- * channel, the step adds the stage sums that the gradient of a state pair needs (the pair's
- * branches and modes share them) into the handle's per-pair accumulators; pb_dev_g2grad_flush
- * applies them.  Needs a device created with pb_dev_opts.adjoint = 1 on the FF variant with
- * branch merging or on G32/G16/H16 (PB_EINVAL otherwise). */
+/* The same RK4 adjoint step with the |g|^2 gradient deferred.  Eq. 2 is linear in each
+ * |g|^2, and the derivative of a channel's term depends on f only through two sums per state
+ * pair (shared by the pair's branches and modes) and on the channel only through fixed
+ * coefficients; so instead of updating every stored channel, the step adds its stage sums into
+ * the handle's per-pair accumulators and pb_dev_g2grad_flush applies them later, once.  f, lam:
+ * device double[nstate] as in pb_rtbte_rk4_vjp (lam in/out; dL/df_n on return).  Needs a device
+ * created with pb_dev_opts.adjoint = 1 on the FF variant with branch merging or on G32/G16/H16:
+ * PB_EINVAL otherwise, and for a null pointer or a non-finite dt.  Asynchronous on `stream`;
+ * the accumulators belong to the handle (in its arena). */
 int pb_rtbte_rk4_vjp_defer(pb_dev *dev, const double *f, double *lam, double dt, void *stream);
 
-/* grad_g2 (device double[nchannels], CSR order) += the |g|^2 gradient accumulated by
- * pb_rtbte_rk4_vjp_defer since the last flush; the accumulators are cleared. */
+/* grad_g2 (caller's device double[nchannels], CSR order of pb_channels_export) += the |g|^2
+ * gradient accumulated by pb_rtbte_rk4_vjp_defer since the last flush; the accumulators are
+ * cleared.  PB_EINVAL for a null pointer or a device without accumulators.  Asynchronous on
+ * `stream`. */
 int pb_dev_g2grad_flush(pb_dev *dev, double *grad_g2, void *stream);
 
 /* Replace the device |g|^2 (device double[nchannels], CSR order of pb_channels_export) and
