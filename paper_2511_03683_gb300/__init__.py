@@ -275,7 +275,13 @@ def _dev_vec(t, n, name, cols=None):
 
 
 class Device:
-    """Device-resident channel list and tables (pb_dev_create) in one torch arena."""
+    """Device-resident channel list and tables (pb_dev_create) in one torch arena.
+
+    ``variant``: "ff" (default, FP64-accurate float-float), "f64", "literal", "g32", "g16"
+    (BF16 |g|^2), "h16" (FP16 |g|^2 times a power of two) or "paper"; the other keywords are
+    the fields of pb_dev_opts.  ``adjoint=True`` reserves the accumulators of the deferred
+    |g|^2 gradient (``rk4_vjp_defer`` / ``g2grad_flush``); ``deferred`` tells whether this
+    device has them (FF with branch merging, G32, G16, H16)."""
 
     def __init__(self, channels: Channels, variant: str = "ff", item_channels: int = 0, ctas_per_sm: int = 0,
                  transport: bool = False, transport_gather: int = 0, transport_ctas: int = 0,
