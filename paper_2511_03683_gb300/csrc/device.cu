@@ -1244,23 +1244,8 @@ int launch_stream_t(pb_dev *d, int mode, const double *fd, const float2 *fff, co
     // symmetric tiles; the rate mode needs the same (A, B) partials
     if (d->sym_nt && fff == d->yff) {  // the bulk copies read f from this padded arena buffer
       const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(d->td.nt, (int64_t)d->sm_count));
-      // programmatic serialization: the sweep stages its first tiles while the kernel before
-      // it (the f conversion or the previous stage's epilogue) finishes; it waits for that
-      // kernel before it reads f or writes partials
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3((unsigned)gs);
-      cfg.blockDim = dim3((unsigned)dev::kSymThreads);
-      cfg.dynamicSmemBytes = dev::kSymBulkSmem;
-      cfg.stream = st;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-      attr[0].val.programmaticStreamSerializationAllowed = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      const cudaError_t le = cudaLaunchKernelEx(&cfg, dev::k_stream_sym_bulk, (const int2 *)d->tiles, (int)d->td.nt,
-                                                (const float4 *)d->tcoef, (const float2 *)fff, (int)ns, (int)d->td.nb,
-                                                d->tpart, d->err);
-      if (le != cudaSuccess) return cuda_fail(le, "k_stream_sym_bulk");
+      dev::k_stream_sym_bulk<<<gs, dev::kSymThreads, dev::kSymBulkSmem, st>>>(d->tiles, d->td.nt, d->tcoef, fff, ns,
+                                                                              d->td.nb, d->tpart, d->err);
     } else {
       const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(d->td.nt, (int64_t)d->sm_count * 3));
       dev::k_stream_sym<<<gs, 256, 0, st>>>(d->tiles, d->td.nt, d->tcoef, fff, ns, d->td.nb, d->tpart);

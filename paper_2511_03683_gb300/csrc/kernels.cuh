@@ -176,15 +176,7 @@ __global__ void k_table(const double *__restrict__ omega, long long n, double kT
   }
 }
 
-// Programmatic dependent launch: a kernel launched with programmatic stream serialization may
-// start once every CTA of the kernel before it has called grid_dep_release() (or exited);
-// grid_dep_wait() then blocks until that kernel has completed and its writes are visible (it
-// returns at once after a normal launch).
-__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void grid_dep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
 __global__ void k_to_ff(const double *__restrict__ x, long long n, float2 *__restrict__ out) {
-  grid_dep_release();  // the tile sweep after it may stage its tiles meanwhile
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] = ff_split(x[i]);
 }
@@ -2191,9 +2183,7 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_stream_sym_bulk(const int2 *
   fence_proxy_async();  // the zeroed f slices before any bulk write to them
   __syncthreads();
   int issued = 0;
-  // the tile (written once at setup) and, separately, the f slices of its row and column blocks
-  // (written by the kernel before this one); one byte count on the stage's mbarrier for both
-  auto issue_tile = [&](int k, int2 IJ) {
+  auto issue = [&](int k, int2 IJ) {
     const int s = k % kSymStages;
     const int t = (int)blockIdx.x + k * G;
     stile[s] = IJ;
@@ -2204,26 +2194,11 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_stream_sym_bulk(const int2 *
     const unsigned char *src = (const unsigned char *)(tc + (size_t)t * kTile * kTile);
 #pragma unroll
     for (int q = 0; q < 4; ++q) bulk_g2s(buf + q * (kTileBytes / 4), src + q * (kTileBytes / 4), kTileBytes / 4, bars + s);
-  };
-  auto issue_f = [&](int k, int2 IJ) {
-    const int s = k % kSymStages;
-    unsigned char *buf = ssm + (size_t)s * kSymStageBytes;
-    const int nr = min(kTile, ns - IJ.x * kTile), nc = min(kTile, ns - IJ.y * kTile);
-    const unsigned br = (unsigned)(nr * sizeof(float2) + 15) / 16 * 16, bc = (unsigned)(nc * sizeof(float2) + 15) / 16 * 16;
     bulk_g2s(buf + kTileBytes, fg + (size_t)IJ.x * kTile, br, bars + s);
     bulk_g2s(buf + kTileBytes + kTile * sizeof(float2), fg + (size_t)IJ.y * kTile, bc, bars + s);
   };
-  auto issue = [&](int k, int2 IJ) {
-    issue_tile(k, IJ);
-    issue_f(k, IJ);
-  };
   if (tid == 0)
-    for (; issued < kSymStages && issued < nloc; ++issued) issue_tile(issued, tiles[(int)blockIdx.x + issued * G]);
-  // f and the partials that the previous kernel reads belong to it: wait for it (launched with
-  // programmatic serialization, this kernel may have started while it ran)
-  grid_dep_wait();
-  if (tid == 0)
-    for (int k = 0; k < issued; ++k) issue_f(k, stile[k]);
+    for (; issued < kSymStages && issued < nloc; ++issued) issue(issued, tiles[(int)blockIdx.x + issued * G]);
   int2 nextIJ = make_int2(0, 0);  // thread 0: descriptor of the next tile to issue, loaded a tile ahead
   if (tid == 0 && issued < nloc) nextIJ = tiles[(int)blockIdx.x + issued * G];
   int2 prevIJ = make_int2(0, 0);  // the previous tile (its columns are combined in this iteration)
@@ -2434,7 +2409,6 @@ __global__ void __launch_bounds__(256) k_fin_tiles(TileSrc src, int ns, double c
                                                    double *__restrict__ y, float2 *__restrict__ yff, double dt) {
   constexpr int SPW = SPC / 8, NV = 2 * SPW, LPV = 32 / NV;  // states per warp, values, lanes per value
   __shared__ float4 tot[SPC];  // (A hi, A lo, C hi, C lo) per state
-  grid_dep_release();  // the next stage's tile sweep may stage its tiles meanwhile
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int base = blockIdx.x * SPC;
   // warp 0 loads its state's epilogue inputs first, so that their latency overlaps the partials'
