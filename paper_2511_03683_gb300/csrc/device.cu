@@ -297,12 +297,13 @@ int cuda_fail(cudaError_t e, const char *what) {
 }  // namespace
 
 namespace {
-// fn(T *) with T the |g|^2 storage type of a mixed-precision variant
+// fn(T *) with T the |g|^2 storage type of a mixed-precision variant (G32, G16, H16; the
+// callers check pb_dev::mixed() first, and other variants call nothing)
 template <typename F>
 void with_g2t(int variant, F &&fn) {
   if (variant == PB_VARIANT_G32) fn((float *)nullptr);
   else if (variant == PB_VARIANT_G16) fn((__nv_bfloat16 *)nullptr);
-  else fn((__half *)nullptr);
+  else if (variant == PB_VARIANT_H16) fn((__half *)nullptr);
 }
 
 // Mixed-precision lane-sweep shapes (pb_dev_opts.channel_per_lane): 1 = 512 threads, three
