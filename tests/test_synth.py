@@ -57,3 +57,20 @@ def test_named_configs():
     assert m1.nk == (40, 40, 40) and m1.nbands == 4 and m1.nmodes == 6 and m1.sigma == 0.008
     assert np.allclose(m1.omega[:, 3:].max(axis=0), [0.035, 0.0475, 0.06])
     assert abs(m1.omega[:, :3].max() - 0.025) < 1e-12 and m1.omega[0, :3].max() == 0.0
+
+
+def test_fp16_storage_range_covers_the_lognormal_couplings():
+    """The FP16 |g|^2 storage (one power-of-two factor that maps the largest value into
+    [2^9, 2^10)) keeps every coupling of the 24^3 workload a normal FP16 number, so each is
+    rounded by at most 2^-11 relative: the premise of the 16-bit variant's error bound.  numpy's
+    float16 conversion stands in for the device's round-to-nearest."""
+    import paper_2511_03683_gb300 as pb
+
+    g2 = pb.Channels.from_model(synth.make_config("window24")).export()["g2"]
+    scale = 2.0 ** (9 - np.floor(np.log2(g2.max())))
+    assert 2.0 ** 9 <= g2.max() * scale < 2.0 ** 10
+    h = (g2 * scale).astype(np.float16)
+    assert np.all(np.isfinite(h)) and h.min() >= np.float16(2.0 ** -14)
+    rel = np.abs(h.astype(np.float64) / scale - g2) / g2
+    assert rel.max() <= 2.0 ** -11
+    print(f"span max/min = 2^{np.log2(g2.max() / g2.min()):.1f}, max relative rounding {rel.max():.2e}")
