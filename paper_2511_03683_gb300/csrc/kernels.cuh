@@ -930,9 +930,9 @@ __global__ void __launch_bounds__(NT, NT == 1024 ? 1 : 8) k_stream_tr_lane(const
   }
 }
 
-// ------------------------------------------------------------ mixed precision (FP32 / BF16 |g|^2)
+// ------------------------------------------------------------ mixed precision (FP32 / BF16 / FP16 |g|^2)
 //
-// The literal per-channel form of Eq. 2 in FP32: stream |g|^2 (FP32 or BF16) and the packed
+// The literal per-channel form of Eq. 2 in FP32: stream |g|^2 (FP32, BF16 or scaled FP16) and the packed
 // (partner, branch) word; gather the partner's 16-byte record (energy and occupation, each as
 // a hi + lo pair, and its padded grid index) from shared memory and (hbar w, N) from an FP32
 // table in L2; evaluate the two Gaussians with ex2 and F_abs / F_em in
@@ -1298,7 +1298,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_stream_g_dense(const Item 
         // all of the pair's loads first (|g|^2 from HBM, (hbar w, N) from L1/L2), then the terms
         float gv[kDenseBranches];
         float2 tv[kDenseBranches];
-        if ((nm & 1) == 0) {  // even nm: the slots of a pair start 8-byte (FP32) / 4-byte (BF16) aligned
+        if ((nm & 1) == 0) {  // even nm: the slots of a pair start 8-byte (FP32) / 4-byte (16-bit) aligned
 #pragma unroll
           for (int k = 0; k < kDenseBranches / 2; ++k)
             if (2 * k < nm) {
