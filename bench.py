@@ -492,7 +492,8 @@ def compare_variants(pb, ch, dev_ff, fh, ff_ms, mixed_steps, stream):
     out = {}
     ms = {"ff": ff_ms}
     devs = {}
-    for v in ("ff_per_channel", "f64", "f64_per_channel", "literal", "g32", "g16", "h16"):
+    peak, _ = measured_hbm()
+    for v in ("ff_per_channel", "f64", "f64_per_channel", "literal", "g32", "g16", "h16", "c32"):
         kw = {"merge_branches": 2} if v.endswith("_per_channel") else {}
         d = pb.Device(ch, variant=v.replace("_per_channel", ""), **kw)
         o = torch.empty(d.nstate, dtype=torch.float64, device="cuda")
@@ -502,7 +503,14 @@ def compare_variants(pb, ch, dev_ff, fh, ff_ms, mixed_steps, stream):
                   "hbm_gb_s": d.bytes_per_channel * d.nchannels / (ms[v] * 1e-3) / 1e9,
                   "bytes_per_channel": d.bytes_per_channel, "speedup_vs_ff": ff_ms / ms[v],
                   "dfdt_err_vs_fp64": err}
-        if v in ("g32", "g16", "h16"):
+        if v in ("c32", "g32", "g16", "h16", "f64"):
+            # the sweep kernel alone (CUDA events around back-to-back launches on this stream)
+            k_ms = d.time_sweep(f, 50, stream=stream)
+            gbs = d.bytes_per_channel * d.nchannels / (k_ms * 1e-3) / 1e9
+            out[v]["sweep_kernel"] = {"ms": k_ms, "algorithmic_gb_s": gbs, "frac_of_hbm": gbs / peak}
+            rv = torch.empty_like(o)
+            out[v]["rates_ms"] = time_calls(lambda: d.rates(f, out=rv), 10, stream)
+        if v in ("g32", "g16", "h16", "c32"):
             devs[v] = d
         else:
             d.close()
@@ -734,7 +742,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"ff": "f32x2", "paper": "f32x2", "f64": "f64", "literal": "f64", "g32": "f32",
-                      "g16": "f32 (bf16 |g|^2)", "h16": "f32 (fp16 |g|^2 x 2^k)"}.get(args.variant, args.variant),
+                      "g16": "f32 (bf16 |g|^2)", "h16": "f32 (fp16 |g|^2 x 2^k)",
+                      "c32": "f32 (fp32 coefficient tiles)"}.get(args.variant, args.variant),
             "data": "synthetic", "config": cfg,
             "rk4_steps_per_s": nrk / (rk_ms * 1e-3), "transport_iters_per_s": ntr / (tr_ms * 1e-3),
             "collision_ms": coll_ms, "rates_ms": rates_ms,

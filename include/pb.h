@@ -145,14 +145,27 @@ void pb_channels_free(pb_channels *ch);
  *  PB_VARIANT_G16     as G32 with |g|^2 stored BF16.
  *  PB_VARIANT_H16     as G32 with |g|^2 stored FP16 times a power of two chosen at creation (the
  *                     largest value maps into [2^9, 2^10)): the same 2 bytes as BF16 with 11
- *                     significand bits instead of 8.  pb_dev_set_g2 values above 63 times the
- *                     largest value at creation overflow: pb_dev_check then returns PB_EINVAL.
+ *                     significand bits instead of 8.  Values from 2^-23 of the largest value at
+ *                     creation up to 63 times it are normal FP16 numbers; a value above that range
+ *                     (overflow) or a nonzero value below it (fewer significand bits) makes
+ *                     pb_dev_check return PB_EINVAL.
  *  PB_VARIANT_PAPER   the paper's own layout (Sec. "Optimized GPU algorithm", Fig. 2), for
  *                     comparison: every channel stored once, per-channel contributions written
  *                     to sc_col (step 2), then gathered with signs by each state's target list
- *                     (step 3).  Collision integral and RK4 only (no scattering rates). */
+ *                     (step 3).  Collision integral and RK4 only (no scattering rates).
+ *  PB_VARIANT_C32     the FF device whose collision, rate and RK4 sweeps stream the symmetric
+ *                     tiles (dense_rows 3) of the branch-merged coefficients in FP32: 8 bytes per
+ *                     state pair, half the float-float tiles.  Each (P_in, P_out) pair is rounded
+ *                     with its ratio kept; every tile entry forms its net term
+ *                     P_in f_p (1-f_s) - P_out f_s (1-f_p) in FP32 with the larger product made
+ *                     exact by an FMA, plus first-order terms in the low part of the float-float
+ *                     f; FP64 for the per-state combination and the RK4 update.  df/dt within
+ *                     about 1e-6 of Eq. 2 (normwise).  Needs complete rows (no cutoffs), branch
+ *                     merging and tile_sweep 0/2 (PB_EINVAL otherwise).  Transport, the
+ *                     no-allocation call and, after pb_dev_set_g2, every sweep run the FF rows;
+ *                     the adjoint calls return PB_EINVAL. */
 enum { PB_VARIANT_FF = 0, PB_VARIANT_F64 = 1, PB_VARIANT_LITERAL = 2, PB_VARIANT_G32 = 3, PB_VARIANT_G16 = 4,
-       PB_VARIANT_PAPER = 5, PB_VARIANT_H16 = 6 };
+       PB_VARIANT_PAPER = 5, PB_VARIANT_H16 = 6, PB_VARIANT_C32 = 7 };
 
 typedef struct pb_dev_opts {
   int32_t variant;           /* PB_VARIANT_* */
@@ -214,8 +227,8 @@ int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, void *arena, s
 void pb_dev_destroy(pb_dev *dev);
 
 /* Synchronise `stream` and report PB_ETIMEOUT if a bounded device-side wait of an earlier
- * launch gave up (the TMA bulk-copy sweeps), or PB_EINVAL if a |g|^2 value overflowed the
- * scaled FP16 storage of a PB_VARIANT_H16 device; PB_OK otherwise.  The report clears the
+ * launch gave up (the TMA bulk-copy sweeps), or PB_EINVAL if a |g|^2 value fell outside the
+ * normal range of the scaled FP16 storage of a PB_VARIANT_H16 device; PB_OK otherwise.  The report clears the
  * handle's error word, so the next check sees only later launches. */
 int pb_dev_check(pb_dev *dev, void *stream);
 

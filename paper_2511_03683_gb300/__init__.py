@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_PKG, "lib", "libpb.so")
 PB_OK, PB_EINVAL, PB_ENOMEM, PB_ECUDA, PB_ENOTCLOSED, PB_ENOCONV, PB_ETIMEOUT, PB_ECALLBACK, PB_EDEVICE = range(9)
 _CODES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCLOSED", 5: "ENOCONV", 6: "ETIMEOUT", 7: "ECALLBACK",
           8: "EDEVICE"}
-VARIANTS = {"ff": 0, "f64": 1, "literal": 2, "g32": 3, "g16": 4, "paper": 5, "h16": 6}
+VARIANTS = {"ff": 0, "f64": 1, "literal": 2, "g32": 3, "g16": 4, "paper": 5, "h16": 6, "c32": 7}
 
 
 class PBError(RuntimeError):
@@ -278,7 +278,8 @@ class Device:
     """Device-resident channel list and tables (pb_dev_create) in one torch arena.
 
     ``variant``: "ff" (default, FP64-accurate float-float), "f64", "literal", "g32", "g16"
-    (BF16 |g|^2), "h16" (FP16 |g|^2 times a power of two) or "paper"; the other keywords are
+    (BF16 |g|^2), "h16" (FP16 |g|^2 times a power of two), "c32" (the FF coefficients in FP32
+    symmetric tiles) or "paper"; the other keywords are
     the fields of pb_dev_opts.  ``adjoint=True`` reserves the accumulators of the deferred
     |g|^2 gradient (``rk4_vjp_defer`` / ``g2grad_flush``); ``deferred`` tells whether this
     device has them (FF with branch merging, G32, G16, H16)."""
@@ -316,6 +317,7 @@ class Device:
         self.bytes_per_channel = float(info.bytes_per_channel)
         self.sm_count = int(info.sm_count)
         self.c = float(info.c)
+        self._g2 = None  # the device's |g|^2 when set through set_g2 (None: the channel list's)
 
     def _new(self, *shape):
         import torch
@@ -446,6 +448,16 @@ class Device:
     def set_g2(self, g2, stream=None):
         """Replace |g|^2 (CUDA double[nchannels], CSR order) and recompute the coefficients."""
         _check(lib().pb_dev_set_g2(self._h, _dev_vec(g2, self.nchannels, "g2"), _stream_ptr(stream)))
+        self._g2 = g2.detach().clone()
+
+    def g2_values(self):
+        """The |g|^2 the device computes with (CUDA double[nchannels], CSR order): the channel
+        list's couplings, or the last values given to set_g2."""
+        import torch
+
+        if self._g2 is None:
+            self._g2 = torch.tensor(self.channels.export()["g2"], dtype=torch.float64, device="cuda")
+        return self._g2
 
     def observables(self, f, out=None, stream=None):
         """(sum f, sum eps f, sum I[f]) as a CUDA tensor of 3 doubles."""

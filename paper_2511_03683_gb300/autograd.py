@@ -17,6 +17,14 @@ import torch
 class _Trajectory(torch.autograd.Function):
     @staticmethod
     def forward(ctx, f0, g2, dev, dt, nsteps, every):
+        if g2.numel() > 0:
+            # the trajectory (and so its gradient) is taken at the couplings given: push them to
+            # the device when they differ from the ones it holds
+            if g2.numel() != dev.nchannels:
+                raise ValueError(f"g2 has {g2.numel()} values; the device stores {dev.nchannels} channels")
+            g2d = g2.detach()
+            if not torch.equal(dev.g2_values(), g2d):
+                dev.set_g2(g2d.to(dtype=torch.float64).contiguous())
         f = f0.detach().clone().contiguous()
         ckpts = []
         n = 0
@@ -53,9 +61,11 @@ class _Trajectory(torch.autograd.Function):
 
 
 def trajectory(dev, f0, g2=None, dt=1.0, nsteps=1, every=20):
-    """Differentiable RK4 trajectory on ``dev`` (a Device of the FF variant).  ``g2`` is a
-    CUDA float64 tensor of the stored couplings (its values must be those on the device,
-    e.g. from ``g2_tensor``); pass it with requires_grad to get dL/dg2."""
+    """Differentiable RK4 trajectory on ``dev`` (a Device of the FF, G32, G16 or H16 variant).
+    ``g2`` is a CUDA float64 tensor of the stored couplings (CSR order, e.g. from ``g2_tensor``);
+    the trajectory is computed at these values (they are pushed to the device with
+    ``Device.set_g2`` when they differ from the ones it holds).  Pass it with requires_grad to
+    get dL/dg2."""
     if g2 is None:
         g2 = torch.zeros(0, dtype=torch.float64, device=f0.device)
     return _Trajectory.apply(f0, g2, dev, dt, int(nsteps), int(every))

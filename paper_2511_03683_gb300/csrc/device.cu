@@ -1,5 +1,6 @@
 // Device runtime of libpb.so: arena layout, upload, coefficient setup and the host
 // drivers of the public compute calls (include/pb.h).  Kernels are in kernels.cuh.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -12,6 +13,7 @@
 
 #include "kernels.cuh"
 #include "pb_internal.h"
+#include "tiles32.cuh"
 
 static_assert(pb::kRowPad == pb::dev::kEntryPad, "host row padding and the kernels' entry padding must agree");
 
@@ -23,6 +25,9 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int kFinBlock = 256;
+// launch shape of the FP32 tile sweep: stages per CTA and resident CTAs per SM
+constexpr int kC32Stages = 2;
+constexpr int kC32Ctas = 2;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -192,8 +197,10 @@ TileDims tile_dims(int64_t ns) {
   return t;
 }
 
+// tile_entry: bytes per pair of the symmetric tiles (16 float-float, 8 for the FP32 tiles of C32)
 Layout make_layout(const pb_channels *ch, const Plan &P, const Plan *S, int variant, bool transport,
-                   int nfin_blocks, bool sym = false, const GDense &gd = GDense(), bool gacc = false) {
+                   int nfin_blocks, bool sym = false, const GDense &gd = GDense(), bool gacc = false,
+                   size_t tile_entry = sizeof(float4)) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -226,7 +233,7 @@ Layout make_layout(const pb_channels *ch, const Plan &P, const Plan *S, int vari
   L.gaccg = take(gacc && (variant == PB_VARIANT_G32 || variant == PB_VARIANT_G16 || variant == PB_VARIANT_H16) ? 3 * sizeof(double) * (size_t)ns * (size_t)ns : 0);
   const TileDims td = tile_dims((int64_t)ns);
   L.tiles = take(sym ? sizeof(int2) * td.nt : 0);
-  L.tcoef = take(sym ? sizeof(float4) * (size_t)td.nt * dev::kTile * dev::kTile : 0);
+  L.tcoef = take(sym ? tile_entry * (size_t)td.nt * dev::kTile * dev::kTile : 0);
   L.tpart = take(sym ? sizeof(float4) * (size_t)td.nb * td.nsp : 0);
   L.wt = take(transport ? sizeof(float2) * nsw : 0);
   L.eps = take(sizeof(double) * ns);
@@ -423,6 +430,10 @@ struct pb_dev {
   int2 *tiles = nullptr;
   float4 *tcoef = nullptr;
   float4 *tpart = nullptr;
+  // PB_VARIANT_C32: the FF device whose tiles hold FP32 (P_in, P_out) (tiles32.cuh); its
+  // partials in tpart are (N, Bd, L, Ld) per (state, block)
+  bool c32 = false;
+  float2 *tc32 = nullptr;
   int64_t *rp_real = nullptr;  // unpadded CSR row offsets [ns+1]
   float2 *vjpG = nullptr;      // adjoint gather table [ns][3]
   float4 *g2tab = nullptr;     // |g|^2-gradient stage table [4 stages][ns][2]
@@ -509,16 +520,22 @@ int check_device(int *sm_count) {
 int resolve_opts(const pb_channels *ch, const pb_dev_opts *opts, int sm_count, pb_dev_opts &o) {
   pb_dev_opts d{};
   if (opts) d = *opts;
-  if (d.variant < PB_VARIANT_FF || d.variant > PB_VARIANT_H16)
+  if (d.variant < PB_VARIANT_FF || d.variant > PB_VARIANT_C32)
     return set_error(PB_EINVAL, "pb_dev: variant %d is not available in this build", d.variant);
   if (d.merge_branches < 0 || d.merge_branches > 2) return set_error(PB_EINVAL, "pb_dev: merge_branches must be 0..2");
   if (d.dense_rows < 0 || d.dense_rows > 3) return set_error(PB_EINVAL, "pb_dev: dense_rows must be 0..3");
   if (d.tile_sweep < 0 || d.tile_sweep > 2) return set_error(PB_EINVAL, "pb_dev: tile_sweep must be 0..2");
   if (d.adjoint < 0 || d.adjoint > 1) return set_error(PB_EINVAL, "pb_dev: adjoint must be 0 or 1");
   if (d.tile_sweep == 0) d.tile_sweep = 2;
+  if (d.variant == PB_VARIANT_C32 && (d.tile_sweep != 2 || d.stream_mode == 2 || d.merge_branches == 2 ||
+                                      d.dense_rows == 1 || d.dense_rows == 2))
+    return set_error(PB_EINVAL, "pb_dev: the FP32 coefficient tiles (C32) need branch merging and the symmetric "
+                                "bulk-copy tile sweep (merge_branches 0/1, dense_rows 0/3, tile_sweep 0/2, "
+                                "stream_mode 0/1)");
   // measured best on GB300 at 40^3: 3 CTAs per SM for one entry per channel, 4 for the
   // branch-merged sweep (whose stream is six times shorter)
-  const bool merged = (d.variant == PB_VARIANT_FF || d.variant == PB_VARIANT_F64) && d.merge_branches != 2;
+  const bool merged = (d.variant == PB_VARIANT_FF || d.variant == PB_VARIANT_F64 || d.variant == PB_VARIANT_C32) &&
+                      d.merge_branches != 2;
   if (d.ctas_per_sm <= 0) d.ctas_per_sm = merged ? 4 : 3;
   if (d.ctas_per_sm > 8) return set_error(PB_EINVAL, "pb_dev: ctas_per_sm must be <= 8");
   if (d.stream_mode < 0 || d.stream_mode > 2) return set_error(PB_EINVAL, "pb_dev: stream_mode must be 0..2");
@@ -696,14 +713,19 @@ extern "C" int pb_dev_arena_bytes(const pb_channels *ch, const pb_dev_opts *opts
   pb_dev_opts o;
   int rc = resolve_opts(ch, opts, sm, o);
   if (rc) return rc;
+  const bool c32 = o.variant == PB_VARIANT_C32;
+  if (c32) o.variant = PB_VARIANT_FF;  // the FF device with FP32 tiles
   Plan P, S;
   try {
     bool complete = false;
     const bool merged = make_plans(ch, opts, o, sm, P, S, &complete);
     const int nfin = (int)((P.ns + kFinBlock - 1) / kFinBlock);
-    *bytes = make_layout(ch, P, merged ? &S : nullptr, o.variant, o.transport != 0, nfin,
-                         sym_for(o, merged, complete), gdense_for(ch, o, sm),
-                         o.adjoint != 0).total;
+    const bool sym = sym_for(o, merged, complete);
+    if (c32 && !sym)
+      return set_error(PB_EINVAL, "pb_dev: the FP32 coefficient tiles (C32) need complete rows (every window state "
+                                  "a partner of every other: no |g| or delta cutoffs)");
+    *bytes = make_layout(ch, P, merged ? &S : nullptr, o.variant, o.transport != 0, nfin, sym,
+                         gdense_for(ch, o, sm), o.adjoint != 0, c32 ? sizeof(float2) : sizeof(float4)).total;
   } catch (const std::bad_alloc &) {
     return set_error(PB_ENOMEM, "pb_dev_arena_bytes: out of host memory");
   }
@@ -726,6 +748,8 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   pb_dev_opts o;
   rc = resolve_opts(ch, opts, sm, o);
   if (rc) return rc;
+  const bool c32 = o.variant == PB_VARIANT_C32;
+  if (c32) o.variant = PB_VARIANT_FF;  // the FF device with FP32 tiles
   if (ch->nstate > INT32_MAX / 4) return set_error(PB_EINVAL, "pb_dev_create: too many states");
   cudaStream_t st = (cudaStream_t)stream;
 
@@ -759,8 +783,9 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->sigma = ch->sigma;
   d->c = 2.0 * kPi / (kHbar * (double)ch->nq);
   if (o.variant == PB_VARIANT_H16) {
-    // FP16 |g|^2: the largest value at creation maps into [2^9, 2^10), so values down to 2^-24
-    // of it stay normal (11 significand bits) and pb_dev_set_g2 may raise them up to 63-fold
+    // FP16 |g|^2: the largest value at creation maps into [2^9, 2^10), so every value down to
+    // 2^-23 of it stays a normal FP16 number (11 significand bits; FP16's smallest normal is
+    // 2^-14) and pb_dev_set_g2 may raise them up to 63-fold
     double gmax = 0.0;
     for (const double v : ch->g2) gmax = std::max(gmax, std::fabs(v));
     if (gmax > 0.0 && std::isfinite(gmax)) d->g2s = std::ldexp(1.0, 10 - std::ilogb(gmax) - 1);
@@ -771,6 +796,12 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->transport = o.transport != 0;
   d->nfin_blocks = (int)((d->ns + kFinBlock - 1) / kFinBlock);
   d->sym = sym_for(o, merged, complete);
+  if (c32 && !d->sym) {
+    delete d;
+    return set_error(PB_EINVAL, "pb_dev: the FP32 coefficient tiles (C32) need complete rows (every window state a "
+                                "partner of every other: no |g| or delta cutoffs)");
+  }
+  d->c32 = c32;
   d->sym_nt = d->sym && o.tile_sweep == 2 ? dev::kSymThreads : 0;
   d->td = tile_dims(d->ns);
   const GDense gd = gdense_for(ch, o, sm);
@@ -779,7 +810,7 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->gd_nitems = (int)gd.nitems;
   d->gd_bytes = gd.bytes;
   d->L = make_layout(ch, P, merged ? &S : nullptr, o.variant, d->transport, d->nfin_blocks, d->sym, gd,
-                     o.adjoint != 0);
+                     o.adjoint != 0, c32 ? sizeof(float2) : sizeof(float4));
   if (arena_bytes < d->L.total) {
     const size_t need = d->L.total;
     delete d;
@@ -855,6 +886,7 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
     if (d->sym) {
       d->tiles = (int2 *)(A + L.tiles);
       d->tcoef = (float4 *)(A + L.tcoef);
+      d->tc32 = (float2 *)(A + L.tcoef);
       d->tpart = (float4 *)(A + L.tpart);
     }
   } else {
@@ -971,6 +1003,13 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
         cudaError_t e_ = cudaMemsetAsync(d->err, 0, sizeof(int) * 4, st);
         if (e_ != cudaSuccess) {
           status = cuda_fail(e_, "clear error word");
+          break;
+        }
+        // the tile sweeps copy the float-float f of a ragged last block rounded up to 16 bytes:
+        // the padding after the nstate values must hold zeros (it multiplies zero coefficients)
+        e_ = cudaMemsetAsync(d->yff, 0, align_up(sizeof(float2) * (size_t)d->ns), st);
+        if (e_ != cudaSuccess) {
+          status = cuda_fail(e_, "clear the stage input");
           break;
         }
       }
@@ -1101,6 +1140,12 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
     else
       cudaFuncSetAttribute(dev::k_stream_sym_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dev::kSymBulkSmem);
   }
+  if (d->c32) {
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    const int sm32 = (int)dev::c32_smem<kC32Stages>();
+    cudaFuncSetAttribute(dev::k_stream_c32<dev::MODE_COLL, kC32Stages, kC32Ctas>, A, sm32);
+    cudaFuncSetAttribute(dev::k_stream_c32<dev::MODE_RATE, kC32Stages, kC32Ctas>, A, sm32);
+  }
   if (d->smem_f > 48 * 1024) {
     set_stream_smem<uint32_t>((int)d->smem_f);
     set_stream_smem<uint16_t>((int)d->smem_f);
@@ -1163,6 +1208,9 @@ extern "C" int pb_dev_check(pb_dev *d, void *stream) {
     if (h == dev::kErrG2Range)
       return set_error(PB_EINVAL, "a |g|^2 value overflowed the FP16 storage (more than 63 times the largest value "
                                   "at device creation)");
+    if (h == dev::kErrG2Small)
+      return set_error(PB_EINVAL, "a nonzero |g|^2 value is too small for the scaled FP16 storage (below 2^-23 of "
+                                  "the largest value at device creation, it would keep fewer than 11 significand bits)");
     return set_error(PB_ETIMEOUT, "a bounded device-side wait gave up (error word %d)", h);
   }
   return PB_OK;
@@ -1194,14 +1242,15 @@ extern "C" int pb_dev_get_info(const pb_dev *d, pb_dev_info *info) {
   info->nchannels = d->nch;
   info->nchannels_padded = d->nchp;
   info->nitems = d->nitems;
-  info->variant = d->variant;
+  info->variant = d->c32 ? PB_VARIANT_C32 : d->variant;
   info->sm_count = d->sm_count;
   info->c = d->c;
   switch (d->variant) {
     // streamed bytes per physical channel: per sweep entry (state pair when branch-merged)
     case PB_VARIANT_FF:
       if (d->sym)
-        info->bytes_per_channel = (double)sizeof(float4) * d->td.nt * dev::kTile * dev::kTile / (double)d->nch;
+        info->bytes_per_channel = (double)(d->c32 ? sizeof(float2) : sizeof(float4)) * d->td.nt * dev::kTile *
+                                  dev::kTile / (double)d->nch;
       else
         info->bytes_per_channel = (2 * sizeof(float2) + (d->dense ? 0 : d->sidx16 ? 2 : 4)) *
                                   (d->merged ? (double)d->nsw / (double)d->nch : 1.0);
@@ -1241,7 +1290,18 @@ int launch_stream_t(pb_dev *d, int mode, const double *fd, const float2 *fff, co
     dev::k_stream_ff_bulk<<<gb, dev::kBlock, d->bulk_smem, st>>>(d->items, n, (const float2 *)d->coefA,
                                                                  (const float2 *)d->coefB, d->sidx16, fff, ns,
                                                                  d->bulk_cap, part, d->err);
-  } else if (d->variant == PB_VARIANT_FF && d->sym && part == d->part) {
+  } else if (d->variant == PB_VARIANT_FF && d->sym && d->c32 && part == d->part && fff == d->yff) {
+    // FP32 coefficient tiles through the bulk-copy ring (tiles32.cuh)
+    const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(d->td.nt, (int64_t)d->sm_count * kC32Ctas));
+    const size_t sm32 = dev::c32_smem<kC32Stages>();
+    float *tp = (float *)d->tpart;
+    if (coll)
+      dev::k_stream_c32<dev::MODE_COLL, kC32Stages, kC32Ctas><<<gs, dev::kC32Threads, sm32, st>>>(
+          d->tiles, d->td.nt, d->tc32, fff, ns, d->td.nb, tp, d->err);
+    else
+      dev::k_stream_c32<dev::MODE_RATE, kC32Stages, kC32Ctas><<<gs, dev::kC32Threads, sm32, st>>>(
+          d->tiles, d->td.nt, d->tc32, fff, ns, d->td.nb, tp, d->err);
+  } else if (d->variant == PB_VARIANT_FF && d->sym && !d->c32 && part == d->part) {
     // symmetric tiles; the rate mode needs the same (A, B) partials
     if (d->sym_nt && fff == d->yff) {  // the bulk copies read f from this padded arena buffer
       const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(d->td.nt, (int64_t)d->sm_count));
@@ -1341,6 +1401,13 @@ void launch_fin(pb_dev *d, const double *ysrc, double *out, double *f, double dt
     dev::k_fin_coll<true, STAGE><<<fin_grid(d), kFinBlock, 0, st>>>(
         dev::ItemSrc{d->variant == PB_VARIANT_PAPER ? d->t_item_ptr : d->item_ptr, d->part}, (int)d->ns, d->c, d->R, ysrc,
                                                                     out, f, d->acc, y, d->yff, dt);
+  else if (d->sym && d->c32)
+    if (d->ns <= 2048)
+      dev::k_fin_c32<STAGE, false, 8><<<(int)((d->ns + 7) / 8), 256, 0, st>>>(
+          d->tpart, d->td.nb, d->td.nsp, (int)d->ns, d->c, d->R, ysrc, out, f, d->acc, y, d->yff, dt);
+    else
+      dev::k_fin_c32<STAGE><<<(int)((d->ns + 31) / 32), 256, 0, st>>>(
+          d->tpart, d->td.nb, d->td.nsp, (int)d->ns, d->c, d->R, ysrc, out, f, d->acc, y, d->yff, dt);
   else if (d->sym)
     if (d->ns <= 2048)  // few states: more, smaller CTAs
       dev::k_fin_tiles<STAGE, false, 8><<<(int)((d->ns + 7) / 8), 256, 0, st>>>(
@@ -1547,6 +1614,10 @@ extern "C" int pb_scatter_rates(pb_dev *d, const double *f, double *inv_tau, voi
   if (d->variant == PB_VARIANT_LITERAL || d->mixed())
     dev::k_fin_rate<true><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->fwd_item_ptr(), d->part}, (int)d->ns,
                                                              d->mixed() ? d->gscale() : d->c, d->R, inv_tau);
+  else if (d->sym && d->c32)
+    dev::k_fin_c32<-1, true><<<(int)((d->ns + 31) / 32), 256, 0, st>>>(d->tpart, d->td.nb, d->td.nsp, (int)d->ns, d->c,
+                                                                       d->R, nullptr, inv_tau, nullptr, nullptr,
+                                                                       nullptr, nullptr, 0.0);
   else if (d->sym)
     dev::k_fin_tiles<-1, true><<<(int)((d->ns + 31) / 32), 256, 0, st>>>(
         dev::TileSrc{d->tpart, d->td.nb, d->td.nsp}, (int)d->ns, d->c, d->R, nullptr, inv_tau, nullptr, nullptr, nullptr,
@@ -1687,9 +1758,15 @@ int coef_setup(pb_dev *d, cudaStream_t st) {
     }
     if (d->sym) {
       const long long n = (long long)d->td.nt * dev::kTile * dev::kTile;
-      dev::k_tiles_fill<<<(int)std::min<long long>((n + 255) / 256, 8192), 256, 0, st>>>(
-          d->tiles, d->td.nt, (const float2 *)d->coefA, (const float2 *)d->coefB, (const long long *)d->srp,
-          (int)d->ns, d->tcoef);
+      const int grid = (int)std::min<long long>((n + 255) / 256, 8192);
+      if (d->c32)
+        dev::k_tiles_fill_c32<<<grid, 256, 0, st>>>(d->tiles, d->td.nt, (const float2 *)d->coefA,
+                                                    (const float2 *)d->coefB, (const long long *)d->srp, (int)d->ns,
+                                                    d->tc32);
+      else
+        dev::k_tiles_fill<<<grid, 256, 0, st>>>(d->tiles, d->td.nt, (const float2 *)d->coefA,
+                                                (const float2 *)d->coefB, (const long long *)d->srp, (int)d->ns,
+                                                d->tcoef);
       PB_LAUNCHED("k_tiles_fill");
     }
   }
@@ -1882,7 +1959,7 @@ extern "C" int pb_collision_vjp(pb_dev *d, const double *f, const double *lam, d
                                 void *stream) {
   clear_error();
   if (!d || !f || !lam || !grad_f) return set_error(PB_EINVAL, "pb_collision_vjp: null argument");
-  if (d->variant != PB_VARIANT_FF && !d->mixed())
+  if ((d->variant != PB_VARIANT_FF && !d->mixed()) || d->c32)
     return set_error(PB_EINVAL, "pb_collision_vjp: needs the FF, G32, G16 or H16 variant");
   cudaStream_t st = (cudaStream_t)stream;
   const int slot = grad_g2 ? 0 : -1;
@@ -1954,7 +2031,7 @@ int rk4_vjp_impl(pb_dev *d, const double *f, double *lam, double dt, double *gra
 
 int rk4_vjp_check(pb_dev *d, const double *f, const double *lam, double dt, const char *who) {
   if (!d || !f || !lam) return set_error(PB_EINVAL, "%s: null argument", who);
-  if (d->variant != PB_VARIANT_FF && !d->mixed())
+  if ((d->variant != PB_VARIANT_FF && !d->mixed()) || d->c32)
     return set_error(PB_EINVAL, "%s: needs the FF, G32, G16 or H16 variant", who);
   if (!std::isfinite(dt)) return set_error(PB_EINVAL, "%s: bad dt", who);
   return PB_OK;
@@ -2015,7 +2092,41 @@ namespace {
 
 constexpr int kMaxStaticDevices = 64;
 std::mutex g_static_mu;
-void *g_static_addr[kMaxStaticDevices] = {};
+// per device: the context the address was looked up in (its process-unique id) and the address
+struct StaticAddr {
+  unsigned long long ctx = 0;
+  void *addr = nullptr;
+};
+StaticAddr g_static_addr[kMaxStaticDevices];
+
+// The unique id of the calling thread's current context (cuCtxGetCurrent + cuCtxGetId, reached
+// through the runtime's driver entry points so that the library does not link the driver
+// library); 0 when there is none or the lookup is unavailable.  A device reset or a new primary
+// context gets a new id, and with it a new lookup of the array's address.
+typedef CUresult(CUDAAPI *CtxGetCurrentFn)(CUcontext *);
+typedef CUresult(CUDAAPI *CtxGetIdFn)(CUcontext, unsigned long long *);
+unsigned long long current_ctx_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (CtxGetCurrentFn)p;
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (CtxGetIdFn)p;
+    cudaGetLastError();
+  });
+  if (!get_current || !get_id) return 0;
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 int static_scratch_address(void **out) {
   int devid = 0;
@@ -2024,13 +2135,16 @@ int static_scratch_address(void **out) {
     return set_error(PB_EDEVICE, "pb_collision_static: device %d is beyond the %d devices it tracks", devid,
                      kMaxStaticDevices);
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_addr[devid]) {
+  StaticAddr &a = g_static_addr[devid];
+  const unsigned long long ctx = current_ctx_id();
+  if (!a.addr || ctx == 0 || ctx != a.ctx) {
     void *p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, pb_static_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "pb_collision_static: cudaGetSymbolAddress");
-    g_static_addr[devid] = p;
+    a.addr = p;
+    a.ctx = current_ctx_id();  // the lookup made the device's primary context current if none was
   }
-  *out = g_static_addr[devid];
+  *out = a.addr;
   return PB_OK;
 }
 

@@ -1518,15 +1518,21 @@ __global__ void __launch_bounds__(kBlock) k_g2acc_g(const float4 *__restrict__ t
 }
 
 // s2 |g|^2 in the storage type of the mixed-precision variants (round to nearest; s2 is a
-// power of two, 1 but for FP16).  A value that overflows FP16 sets *err = kErrG2Range.
+// power of two, 1 but for FP16).  For FP16, a value that overflows sets *err = kErrG2Range and
+// a nonzero value below FP16's smallest normal number (2^-14: it would keep fewer than 11
+// significand bits, or none) sets *err = kErrG2Small.
 constexpr int kErrG2Range = 16;
+constexpr int kErrG2Small = 17;
 template <typename G2T>
 __global__ void k_cvt_g2(const double *__restrict__ g2, long long n, G2T *__restrict__ out, double s2,
                          int *__restrict__ err) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double v = s2 * g2[i];
     g2_store(out, (size_t)i, v);
-    if (std::is_same<G2T, __half>::value && fabs(v) >= 65520.0) *err = kErrG2Range;  // rounds to FP16 infinity
+    if (std::is_same<G2T, __half>::value) {
+      if (fabs(v) >= 65520.0) *err = kErrG2Range;  // rounds to FP16 infinity
+      else if (v != 0.0 && fabs(v) < 0x1p-14) *err = kErrG2Small;  // subnormal or zero in FP16
+    }
   }
 }
 
@@ -2348,11 +2354,11 @@ __device__ __forceinline__ FinIn fin_load(int r, const double *__restrict__ R, c
   return v;
 }
 
-template <bool LIT, int STAGE, bool GSTATE>
-__device__ __forceinline__ void fin_apply(int r, double A, double B, double c, const FinIn &in,
-                                          double *__restrict__ out, double *__restrict__ f, double *__restrict__ acc,
-                                          double *__restrict__ y, float2 *__restrict__ yff, double dt) {
-  const double I = LIT ? -c * A : c * (A - in.y * (in.R - B));
+// out[r] = I (STAGE < 0), or the RK4 stage arithmetic with k_{STAGE+1} = I
+template <int STAGE, bool GSTATE>
+__device__ __forceinline__ void fin_stage(int r, double I, const FinIn &in, double *__restrict__ out,
+                                          double *__restrict__ f, double *__restrict__ acc, double *__restrict__ y,
+                                          float2 *__restrict__ yff, double dt) {
   if (STAGE < 0) {
     out[r] = I;
     return;
@@ -2377,6 +2383,13 @@ __device__ __forceinline__ void fin_apply(int r, double A, double B, double c, c
     rec_set_f(reinterpret_cast<uint4 *>(yff) + r, yn);  // yff points at the uint4 record array
   else
     yff[r] = ff_split(yn);
+}
+
+template <bool LIT, int STAGE, bool GSTATE>
+__device__ __forceinline__ void fin_apply(int r, double A, double B, double c, const FinIn &in,
+                                          double *__restrict__ out, double *__restrict__ f, double *__restrict__ acc,
+                                          double *__restrict__ y, float2 *__restrict__ yff, double dt) {
+  fin_stage<STAGE, GSTATE>(r, LIT ? -c * A : c * (A - in.y * (in.R - B)), in, out, f, acc, y, yff, dt);
 }
 
 template <bool LIT, int STAGE, bool GSTATE = false, typename SRC = ItemSrc>

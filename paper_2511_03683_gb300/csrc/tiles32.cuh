@@ -1,0 +1,333 @@
+// FP32 coefficient tiles (PB_VARIANT_C32): the collision sweep of Eq. 2 over the upper block
+// triangle of the branch-merged pair matrix, stored as 64 x 64 tiles of FP32 (P_in, P_out),
+// 8 bytes per state pair: half the bytes of the float-float tiles.  Included by device.cu after
+// kernels.cuh (it uses the tile, mbarrier and bulk-copy helpers there).
+//
+// Why a per-entry net term.  The pair (s, p) adds
+//     n(s,p) = P_in f_p (1 - f_s) - P_out f_s (1 - f_p)
+// to I_s / c and -n(s,p) to I_p / c (the reverse channel swaps P_in and P_out).  Near a steady
+// state the two products are much larger than their difference, so sums of them (the A and C
+// sums of the float-float sweep) rounded to FP32 carry errors of 2^-24 of the gross scattering,
+// which the closing difference turns into 1e-6 of df/dt and more along a 1000-step trajectory.
+// Here every entry forms n(s,p) itself, with the larger product made exact by an FMA error term:
+//     n = P_in f_p - P_out f_s - d f_s f_p,   d = P_in - P_out,
+//     u = fl(P_in f_p),  e = P_in f_p - u (exact, one FMA),  v = fl(P_out f_s - u) (one FMA),
+//     n = fl(-d fl(f_s f_p) + (e - v)),
+// so the rounding left in n is relative to n, and the sums over a row are sums of net terms.
+// The occupations are float-float (f = f_h + f_l); the sweep uses f_h and adds the first-order
+// terms in f_l from four sums per state:
+//     N_s  = sum_p n(s,p)                       (at f_h)
+//     Bd_s = sum_p f_h,p d(s,p),   L_s = sum_p f_l,p P_in(s,p),   Ld_s = sum_p f_l,p d(s,p),
+//     I_s  = c [ N_s + L_s - f_s Ld_s - f_l,s (R_s + Bd_s) ],   R_s = sum_p P_out(s,p),
+// (dn/df_p = P_in - f_s d, dn/df_s = -(P_out + f_p d)); the second-order term f_l,s f_l,p d is
+// below 2^-48 of the products.
+//
+// Why the coefficients are rounded together.  Rounding P_in and P_out independently perturbs
+// the two products of n by different relative amounts, an error of 2^-24 of the gross terms
+// again.  A common relative error scales n itself.  So each entry stores the pair (a, b) that
+// keeps the ratio P_out / P_in best: a is taken within kC32RatioUlps units in the last place of
+// P_in, b = fl(a P_out / P_in), and the candidate whose b / a is closest to P_out / P_in wins
+// (the choice of a scales the entry by a relative amount of at most about 2.5 ulp).
+namespace pb {
+namespace dev {
+
+constexpr int kC32Threads = 256;
+constexpr int kC32RatioUlps = 2;
+constexpr unsigned kC32TileBytes = kTile * kTile * sizeof(float2);
+constexpr unsigned kC32StageBytes = kC32TileBytes + 2 * kTile * sizeof(float2);
+constexpr size_t kC32ColFloats = (size_t)(kC32Threads / 32) * 4 * kTile;  // [8 warps][4 sums][64 columns]
+template <int NST>
+constexpr size_t c32_smem() {
+  return (size_t)NST * kC32StageBytes + 128 + 2 * kC32ColFloats * sizeof(float);
+}
+
+// (a, b) ~ (P_in, P_out) in FP32 with the ratio kept (see above); zero stays zero.
+__device__ __forceinline__ float2 c32_round_pair(double pin, double pout) {
+  const float a0 = __double2float_rn(pin);
+  if (!(a0 > 0.f) || !(pout > 0.0)) return make_float2(a0, __double2float_rn(pout));
+  const double r = pout / pin;
+  float ba = a0, bb = __double2float_rn((double)a0 * r);
+  double be = fabs((double)bb / (double)ba - r);
+  for (int k = -kC32RatioUlps; k <= kC32RatioUlps; ++k) {
+    if (k == 0) continue;
+    const float a = __int_as_float(__float_as_int(a0) + k);
+    if (!(a > 0.f) || isinf(a)) continue;
+    const float b = __double2float_rn((double)a * r);
+    if (!(b > 0.f) || isinf(b)) continue;
+    const double e = fabs((double)b / (double)a - r);
+    if (e < be) {
+      be = e;
+      ba = a;
+      bb = b;
+    }
+  }
+  return make_float2(ba, bb);
+}
+
+// tc[t][i][j] = rounded (P_in, P_out) of pair (64 I + i, 64 J + j) from the branch-merged
+// float-float coefficients of complete rows (entry (s, p) of row s is at srp[s] + p); zero
+// outside the nstate states.
+__global__ void k_tiles_fill_c32(const int2 *__restrict__ tiles, int nt, const float2 *__restrict__ coefA,
+                                 const float2 *__restrict__ coefB, const long long *__restrict__ srp, int ns,
+                                 float2 *__restrict__ tc) {
+  const long long n = (long long)nt * kTile * kTile;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int t = (int)(e / (kTile * kTile)), k = (int)(e % (kTile * kTile));
+    const int2 IJ = tiles[t];
+    const int s = IJ.x * kTile + k / kTile, p = IJ.y * kTile + k % kTile;
+    float2 v = make_float2(0.f, 0.f);
+    if (s < ns && p < ns) {
+      const long long c = srp[s] + p;
+      const float2 a = coefA[c], b = coefB[c];
+      const double pin = ff_to_double(a.x, a.y), pout = pin + ff_to_double(b.x, b.y);
+      v = c32_round_pair(pin, pout);
+    }
+    tc[e] = v;
+  }
+}
+
+// reduce-scatter of NV floats over the 2 * TOP lanes that differ in lane bits log2 TOP .. 0: at
+// the end v[0] holds the total of value index idx(lane) = those bits of the lane, most
+// significant first (the float-float version is ff_reduce_scatter)
+template <int NV, int TOP>
+__device__ __forceinline__ void f32_reduce_scatter(float (&v)[NV], int lane) {
+  int n = NV;
+#pragma unroll
+  for (int mask = TOP; mask > 0; mask >>= 1) {
+    if (n > 1) {
+      const bool up = lane & mask;
+      const int h = n >> 1;
+#pragma unroll
+      for (int k = 0; k < NV / 2; ++k) {
+        if (k < h) {
+          const float send = up ? v[k] : v[k + h], keep = up ? v[k + h] : v[k];
+          v[k] = __fadd_rn(keep, __shfl_xor_sync(0xFFFFFFFFu, send, mask));
+        }
+      }
+      n = h;
+    } else {
+      v[0] = __fadd_rn(v[0], __shfl_xor_sync(0xFFFFFFFFu, v[0], mask));
+    }
+  }
+}
+
+// the column sums of a finished off-diagonal tile: thread (sum, column) adds the 8 warps' values
+// and writes them to the column state's partial for block IJ.x
+__device__ __forceinline__ void c32_columns_out(const float *__restrict__ colred, int2 IJ, int nb, int tid,
+                                                float *__restrict__ tp) {
+  const int comp = tid >> 6, col = tid & (kTile - 1);
+  float acc = colred[comp * kTile + col];
+#pragma unroll
+  for (int w = 1; w < kC32Threads / 32; ++w) acc = __fadd_rn(acc, colred[(w * 4 + comp) * kTile + col]);
+  tp[((long long)(IJ.y * kTile + col) * nb + IJ.x) * 4 + comp] = acc;
+}
+
+// One persistent 256-thread CTA (CPS per SM) streams its share of the tiles through NST
+// shared-memory stages filled by bulk copies (thread 0 issues, completion counted in bytes on
+// one mbarrier per stage, every wait bounded), as k_stream_sym_bulk does for the float-float
+// tiles.  Thread (ti, tj) takes rows 4 ti .. 4 ti + 3 and columns tj + 16 j.  Partials per
+// (state, block of partner states): MODE_COLL (N, Bd, L, Ld) as above; MODE_RATE (rate sum,
+// its f_l term, 0, 0) with the summand P_out + f_p d of 1/tau_s.
+template <int MODE, int NST, int CPS>
+__global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32(const int2 *__restrict__ tiles, int nt,
+                                                                  const float2 *__restrict__ tc,
+                                                                  const float2 *__restrict__ fg, int ns, int nb,
+                                                                  float *__restrict__ tp, int *__restrict__ err) {
+  constexpr int R = 4;
+  extern __shared__ __align__(128) unsigned char ssm[];
+  unsigned long long *bars = (unsigned long long *)(ssm + NST * kC32StageBytes);
+  int2 *stile = (int2 *)(bars + NST);
+  float *colred0 = (float *)(ssm + NST * kC32StageBytes + 128);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, tj = tid & 15, ti = tid >> 4;
+  const int G = (int)gridDim.x;
+  const int nloc = (int)blockIdx.x < nt ? (nt - 1 - (int)blockIdx.x) / G + 1 : 0;
+  for (int i = tid; i < NST * 2 * kTile; i += kC32Threads) {
+    float2 *fz = (float2 *)(ssm + (i / (2 * kTile)) * kC32StageBytes + kC32TileBytes);
+    fz[i % (2 * kTile)] = make_float2(0.f, 0.f);
+  }
+  if (tid == 0) {
+    for (int k = 0; k < NST; ++k) mbar_init(bars + k, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_proxy_async();
+  __syncthreads();
+  int issued = 0;
+  auto issue = [&](int k, int2 IJ) {
+    const int s = k % NST;
+    const int t = (int)blockIdx.x + k * G;
+    stile[s] = IJ;
+    unsigned char *buf = ssm + (size_t)s * kC32StageBytes;
+    const int nr = min(kTile, ns - IJ.x * kTile), nc = min(kTile, ns - IJ.y * kTile);
+    const unsigned br = (unsigned)(nr * sizeof(float2) + 15) / 16 * 16, bc = (unsigned)(nc * sizeof(float2) + 15) / 16 * 16;
+    mbar_expect_tx(bars + s, kC32TileBytes + br + bc);
+    const unsigned char *src = (const unsigned char *)(tc + (size_t)t * kTile * kTile);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) bulk_g2s(buf + q * (kC32TileBytes / 2), src + q * (kC32TileBytes / 2), kC32TileBytes / 2, bars + s);
+    bulk_g2s(buf + kC32TileBytes, fg + (size_t)IJ.x * kTile, br, bars + s);
+    bulk_g2s(buf + kC32TileBytes + kTile * sizeof(float2), fg + (size_t)IJ.y * kTile, bc, bars + s);
+  };
+  if (tid == 0)
+    for (; issued < NST && issued < nloc; ++issued) issue(issued, tiles[(int)blockIdx.x + issued * G]);
+  int2 nextIJ = make_int2(0, 0);
+  if (tid == 0 && issued < nloc) nextIJ = tiles[(int)blockIdx.x + issued * G];
+  int2 prevIJ = make_int2(0, 0);
+  bool ok = true;
+  for (int k = 0; k <= nloc; ++k) {
+    const bool have = k < nloc;
+    if (!__syncthreads_and(tid == 0 && have ? mbar_wait(bars + k % NST, (unsigned)((k / NST) & 1)) : true)) {
+      ok = false;
+      break;
+    }
+    if (tid == 0 && k >= 1 && issued < nloc) {
+      fence_proxy_async();  // the generic reads of tile k-1's stage before its refill
+      issue(issued, nextIJ);
+      ++issued;
+      if (issued < nloc) nextIJ = tiles[(int)blockIdx.x + issued * G];
+    }
+    if (k >= 1 && prevIJ.x != prevIJ.y) c32_columns_out(colred0 + ((k - 1) & 1) * kC32ColFloats, prevIJ, nb, tid, tp);
+    if (!have) break;
+    const int s = k % NST;
+    const int2 IJ = stile[s];
+    prevIJ = IJ;
+    const bool diag = IJ.x == IJ.y;
+    const float2 *__restrict__ T = (const float2 *)(ssm + (size_t)s * kC32StageBytes);
+    const float2 *__restrict__ fr = (const float2 *)(ssm + (size_t)s * kC32StageBytes + kC32TileBytes);
+    const float2 *__restrict__ fc = fr + kTile;
+    float2 fcol[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) fcol[j] = fc[tj + 16 * j];
+    float rv[4 * R], cv[16];  // [sum][row], [sum][column slot]
+#pragma unroll
+    for (int i = 0; i < 16; ++i) rv[i] = cv[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int row = ti * R + i;
+      const float2 fs = fr[row];
+      float2 e[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) e[j] = T[row * kTile + tj + 16 * j];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float a = e[j].x, b = e[j].y, fp = fcol[j].x, flp = fcol[j].y;
+        const float d = __fsub_rn(a, b);
+        if (MODE == MODE_COLL) {
+          const float u = __fmul_rn(a, fp);
+          const float ex = __fmaf_rn(a, fp, -u);
+          const float v = __fmaf_rn(b, fs.x, -u);
+          const float w = __fmul_rn(fs.x, fp);
+          const float n = __fmaf_rn(-d, w, __fsub_rn(ex, v));
+          rv[0 * R + i] = __fadd_rn(rv[0 * R + i], n);
+          rv[1 * R + i] = __fmaf_rn(fp, d, rv[1 * R + i]);
+          rv[2 * R + i] = __fmaf_rn(flp, a, rv[2 * R + i]);
+          rv[3 * R + i] = __fmaf_rn(flp, d, rv[3 * R + i]);
+          if (!diag) {
+            cv[0 * 4 + j] = __fsub_rn(cv[0 * 4 + j], n);
+            cv[1 * 4 + j] = __fmaf_rn(-fs.x, d, cv[1 * 4 + j]);
+            cv[2 * 4 + j] = __fmaf_rn(fs.y, b, cv[2 * 4 + j]);
+            cv[3 * 4 + j] = __fmaf_rn(-fs.y, d, cv[3 * 4 + j]);
+          }
+        } else {  // 1/tau summands: row s: P_out + f_p d; column p (reverse channel): P_in - f_s d
+          rv[0 * R + i] = __fadd_rn(rv[0 * R + i], __fmaf_rn(fp, d, b));
+          rv[1 * R + i] = __fmaf_rn(flp, d, rv[1 * R + i]);
+          if (!diag) {
+            cv[0 * 4 + j] = __fadd_rn(cv[0 * 4 + j], __fmaf_rn(-fs.x, d, a));
+            cv[1 * 4 + j] = __fmaf_rn(-fs.y, d, cv[1 * 4 + j]);
+          }
+        }
+      }
+    }
+    // rows: the 16 lanes of a half-warp share them; lane tj ends with sum tj >> 2 of row tj & 3
+    f32_reduce_scatter<16, 8>(rv, lane);
+    {
+      const int row = IJ.x * kTile + ti * R + (tj & 3);
+      tp[((long long)row * nb + IJ.y) * 4 + (tj >> 2)] = rv[0];
+    }
+    if (!diag) {
+      // columns: lanes tj and tj + 16 share them (one level), then the 8 warps (next iteration)
+      float *colred = colred0 + (k & 1) * kC32ColFloats;
+      const bool up = lane & 16;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int comp = m >> 1, jk = m & 1, jo = jk + 2;  // kept / sent column slot
+        const float kept = up ? cv[comp * 4 + jo] : cv[comp * 4 + jk];
+        const float sent = up ? cv[comp * 4 + jk] : cv[comp * 4 + jo];
+        const float w = __fadd_rn(kept, __shfl_xor_sync(0xFFFFFFFFu, sent, 16));
+        const int col = tj + 16 * ((up ? 2 : 0) + jk);
+        colred[(wid * 4 + comp) * kTile + col] = w;
+      }
+    }
+  }
+  if (!ok) {
+    *err = 2;
+    if (tid == 0) {
+      for (int k = 0; k < NST; ++k) {
+        const int uses = issued / NST + (k < issued % NST ? 1 : 0);
+        if (uses > 0) mbar_wait(bars + k, (unsigned)((uses - 1) & 1));
+      }
+    }
+  }
+}
+
+// Epilogue of the C32 sweep: a 256-thread CTA takes SPC states; each warp adds the block
+// partials of SPC / 8 states (lanes over the blocks, N in float-float, the three correction sums
+// in FP32, then a 32-lane butterfly), and warp 0 applies the combination above and the RK4 stage
+// arithmetic in FP64, one lane per state.  RATE: 1/tau = c (rate sum + its f_l term).
+template <int STAGE, bool RATE = false, int SPC = 32>
+__global__ void __launch_bounds__(256) k_fin_c32(const float4 *__restrict__ tp, int nb, int nsp, int ns, double c,
+                                                 const double *__restrict__ R, const double *__restrict__ ysrc,
+                                                 double *__restrict__ out, double *__restrict__ f,
+                                                 double *__restrict__ acc, double *__restrict__ y,
+                                                 float2 *__restrict__ yff, double dt) {
+  constexpr int SPW = SPC / 8;
+  __shared__ float4 tot[SPC];  // (N hi, N lo, Bd, L)
+  __shared__ float totd[SPC];  // Ld
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int base = blockIdx.x * SPC;
+  const int r0 = base + lane;
+  FinIn in{0.0, 0.0, 0.0, 0.0};
+  if (wid == 0 && lane < SPC && r0 < ns) {
+    if (RATE) in.R = 0.0;
+    else in = fin_load<false, STAGE>(r0, R, ysrc, f, acc);
+  }
+#pragma unroll
+  for (int q = 0; q < SPW; ++q) {
+    const int r = base + SPW * wid + q;
+    float2 N = make_float2(0.f, 0.f);
+    float B = 0.f, L = 0.f, D = 0.f;
+    if (r < nsp) {
+      const float4 *__restrict__ row = tp + (long long)r * nb;
+      for (int k = lane; k < nb; k += 32) {
+        const float4 x = row[k];
+        N = ff_add(N, make_float2(x.x, 0.f));
+        B = __fadd_rn(B, x.y);
+        L = __fadd_rn(L, x.z);
+        D = __fadd_rn(D, x.w);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      N = ff_add(N, make_float2(__shfl_xor_sync(0xFFFFFFFFu, N.x, o), __shfl_xor_sync(0xFFFFFFFFu, N.y, o)));
+      B = __fadd_rn(B, __shfl_xor_sync(0xFFFFFFFFu, B, o));
+      L = __fadd_rn(L, __shfl_xor_sync(0xFFFFFFFFu, L, o));
+      D = __fadd_rn(D, __shfl_xor_sync(0xFFFFFFFFu, D, o));
+    }
+    if (lane == 0) {
+      tot[SPW * wid + q] = make_float4(N.x, N.y, B, L);
+      totd[SPW * wid + q] = D;
+    }
+  }
+  __syncthreads();
+  if (wid != 0 || lane >= SPC || r0 >= ns) return;
+  const float4 Tt = tot[lane];
+  const double Nsum = ff_to_double(Tt.x, Tt.y);
+  if (RATE) {
+    out[r0] = c * (Nsum + (double)Tt.z);
+    return;
+  }
+  const double ys = in.y, yl = ys - (double)__double2float_rn(ys);
+  const double I = c * (Nsum + (double)Tt.w - ys * (double)totd[lane] - yl * (in.R + (double)Tt.z));
+  fin_stage<STAGE, false>(r0, I, in, out, f, acc, y, yff, dt);
+}
+
+}  // namespace dev
+}  // namespace pb

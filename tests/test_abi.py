@@ -184,5 +184,36 @@ def test_fp16_variant_sizes_like_bf16(pb):
         sizes.append(n.value)
     assert sizes[0] == sizes[1]
     o = pb._DevOpts()
-    o.variant = 7
+    o.variant = 8
     assert L.pb_dev_arena_bytes(ch._h, ctypes.byref(o), ctypes.byref(ctypes.c_size_t(0))) == pb.PB_EINVAL
+
+
+def test_c32_arena_and_options(pb):
+    """The FP32 coefficient tiles (c32) hold 8 bytes per state pair of the upper block triangle
+    instead of 16: the arena is the FF arena less 8 * tiles * 64^2 bytes (up to region
+    alignment).  They need complete rows and the bulk-copy tile sweep: PB_EINVAL otherwise."""
+    import ctypes
+
+    m = synth.make_window4(12)
+    ch = pb.Channels.from_model(m)
+    L = pb.lib()
+
+    def arena(chs, **kw):
+        o = pb._DevOpts()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        n = ctypes.c_size_t(0)
+        rc = L.pb_dev_arena_bytes(chs._h, ctypes.byref(o), ctypes.byref(n))
+        return rc, n.value
+
+    nb = (ch.nstate + 63) // 64
+    nt = nb * (nb + 1) // 2
+    rc_ff, ff = arena(ch)
+    rc_32, c32 = arena(ch, variant=pb.VARIANTS["c32"])
+    assert rc_ff == rc_32 == pb.PB_OK
+    assert abs((ff - c32) - 8 * nt * 64 * 64) <= 256
+    for kw in ({"tile_sweep": 1}, {"merge_branches": 2}, {"stream_mode": 2}, {"dense_rows": 2}):
+        assert arena(ch, variant=pb.VARIANTS["c32"], **kw)[0] == pb.PB_EINVAL
+    cut = pb.Channels.from_model(m, g2_min=5e-4, delta_nsigma=4.0)
+    assert arena(cut, variant=pb.VARIANTS["c32"])[0] == pb.PB_EINVAL
+    assert "complete rows" in L.pb_last_error().decode()

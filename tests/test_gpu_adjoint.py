@@ -136,6 +136,30 @@ def test_trajectory_gradient_matches_oracle_adjoint(pb):
     assert nrel(f0.grad.cpu().numpy(), ref) <= 1e-10
 
 
+def test_trajectory_at_given_couplings(pb):
+    """trajectory() takes the couplings it is given: with every |g|^2 doubled (not yet on the
+    device) the f0 gradient is the oracle adjoint of the model whose couplings are doubled
+    (log-normal mean raised by ln 2), and the device then holds the doubled values."""
+    import torch
+    from paper_2511_03683_gb300 import autograd as pa
+
+    m = synth.make_config("tiny")
+    ch = pb.Channels.from_model(m)
+    dev = pb.Device(ch)
+    ids = ch.state_ids()
+    f0 = torch.tensor(m.f_hot().reshape(-1)[ids], device="cuda", requires_grad=True)
+    eps = torch.tensor(m.eps.reshape(-1)[ids], device="cuda")
+    g2 = (2.0 * pa.g2_tensor(ch)).requires_grad_(True)
+    (eps * pa.trajectory(dev, f0, g2, 1.0, 6, 4)).sum().backward()
+    m2 = m.with_(g2_mu=m.g2_mu + np.log(2.0))
+    o2 = oracle.Oracle(m2)
+    ref = o2.rk4_vjp(o2.window_values(m2.f_hot()), 1.0, 6, o2.window_values(m2.eps))
+    assert nrel(f0.grad.cpu().numpy(), ref) <= 1e-10
+    assert torch.equal(dev.g2_values(), g2.detach())
+    with pytest.raises(ValueError):
+        pa.trajectory(dev, f0, g2[:-1], 1.0, 1, 1)
+
+
 def test_trajectory_gradient_finite_differences_24cubed(pb):
     """The adjoint workload: 24^3 grids, 4 bands, 6 modes, loss = carrier energy after
     200 RK4 steps of 1 fs, checkpoints every 20 steps; 50 random directions in f0 and 5 in

@@ -364,11 +364,13 @@ def test_single_state(pb):
 
 # ------------------------------------------------------------------ mixed precision
 # |g|^2 stored FP32 / BF16 / FP16 (times a power of two), per-channel arithmetic in FP32, Kahan
-# lane sums, FP64 state.  Bounds on df/dt (normwise): 1e-6 for FP32.  BF16 rounds each |g|^2
-# by up to 2^-8 (3.9e-3 relative); on coarse grids one channel can dominate a row, so the bound
-# is 2.5e-3 here (the 1e-3 target holds on the 40^3 workload's initial state, see the design
-# notes).  FP16 rounds by up to 2^-11 (4.9e-4): the error is at most 2^-11 of the gross
-# scattering plus the FP32 terms' 1e-6, so 5e-4 holds even where one channel dominates.
+# lane sums, FP64 state.  Bounds on df/dt (normwise) on the small grids below: 1e-6 for FP32.
+# BF16 rounds each |g|^2 by up to 2^-9 relative; on these coarse grids one channel can dominate a
+# row, so the bound here is 2.5e-3.  The 40^3 workload (the mixed-precision configuration) is
+# held to the 1e-3 target itself (FULL_TOL below): met at the hot start, missed along the
+# 1000-step trajectory (2.08e-3, an expected failure there).  FP16 rounds by up to 2^-11: the
+# error is at most 2^-11 of the gross scattering plus the FP32 terms' 1e-6, so 5e-4 holds even
+# where one channel dominates.
 MIXED_TOL = {"g32": 1e-6, "g16": 2.5e-3, "h16": 5e-4}
 
 
@@ -459,6 +461,30 @@ def test_fp16_storage_overflow_is_reported(pb):
     assert np.abs(dev.collision(f).cpu().numpy() - I0).max() <= 1e-7 * np.abs(I0).max()
 
 
+def test_fp16_storage_underflow_is_reported(pb):
+    """Scaled FP16 |g|^2 keeps 11 significand bits only down to 2^-23 of the largest value at
+    creation: values set 2^30 times smaller fall below FP16's smallest normal number, the
+    conversion flags it and pb_dev_check returns PB_EINVAL; a factor of 2^-8 stays inside the
+    range and is exact."""
+    import torch
+
+    m = SMALL["win16"]()
+    ch = pb.Channels.from_model(m)
+    dev = pb.Device(ch, variant="h16")
+    f = T(np.random.default_rng(8).uniform(0, 1, dev.nstate))
+    I0 = dev.collision(f).cpu().numpy()
+    g2 = torch.tensor(ch.export()["g2"], dtype=torch.float64, device="cuda")
+    dev.set_g2(2.0 ** -8 * g2)
+    assert np.abs(dev.collision(f).cpu().numpy() - 2.0 ** -8 * I0).max() <= 1e-6 * 2.0 ** -8 * np.abs(I0).max()
+    dev.check()
+    dev.set_g2(2.0 ** -30 * g2)
+    with pytest.raises(pb.PBError) as e:
+        dev.check()
+    assert e.value.code == pb.PB_EINVAL and "too small" in str(e.value)
+    dev.set_g2(g2)
+    dev.check()
+
+
 def test_bf16_storage_takes_large_values(pb):
     """The FP16 range check is the H16 variant's alone: BF16 storage (FP32 range) takes |g|^2
     a million times larger without a report, and the integral scales with it."""
@@ -483,6 +509,77 @@ def test_mixed_precision_rk4(pb, variant):
     ft = T(f0)
     dev.rk4(ft, 1.0, 10)
     assert nrel(ft.cpu().numpy(), o.rk4(f0, 1.0, 10)) <= MIXED_TOL[variant]
+
+
+# ------------------------------------------------------------------ FP32 coefficient tiles (C32)
+# The branch-merged coefficients in FP32 symmetric tiles with the ratio P_out / P_in kept, each
+# entry's net term formed in FP32 with an exact leading product, first-order terms in the low
+# part of f, FP64 per-state combination: df/dt within 1e-6 normwise (the FP32 target of Eq. 2's
+# reduced-precision forms), rates within 1e-6, particle number conserved to 1e-6 of the gross
+# scattering.
+C32_TOL = 1e-6
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_c32_collision_rates_conservation(pb, name):
+    m, o, dev = setup_case(pb, name, "c32")
+    assert dev.bytes_per_channel > 0
+    for f in (np.random.default_rng(7).uniform(0, 1, o.nstate), o.window_values(m.f_hot())):
+        ref, ab = o.collision(f, with_abs=True)
+        I = dev.collision(T(f)).cpu().numpy()
+        check_I(I, ref, ab, tol=C32_TOL, abs_tol=C32_TOL)
+        assert abs(I.sum()) <= C32_TOL * ab.sum()
+        assert nrel(dev.rates(T(f)).cpu().numpy(), o.rates(f)) <= C32_TOL
+    dev.check()
+
+
+def test_c32_signed_inputs(pb):
+    """The net-term arithmetic holds for occupations of either sign (as the adjoint and
+    finite-difference probes use them): random f in [-1, 1] on the ragged 99-state case."""
+    m, o, dev = setup_case(pb, "odd99", "c32")
+    f = np.random.default_rng(21).uniform(-1, 1, o.nstate)
+    ref, ab = o.collision(f, with_abs=True)
+    check_I(dev.collision(T(f)).cpu().numpy(), ref, ab, tol=C32_TOL, abs_tol=C32_TOL)
+
+
+def test_c32_rk4(pb):
+    m, o, dev = setup_case(pb, "tiny8", "c32")
+    f0 = o.window_values(m.f_hot())
+    ft = T(f0)
+    dev.rk4(ft, 1.0, 10)
+    assert nrel(ft.cpu().numpy(), o.rk4(f0, 1.0, 10)) <= C32_TOL
+    dev.check()
+
+
+def test_c32_needs_complete_rows_and_the_tile_sweep(pb):
+    m = synth.make_window4(16)
+    ch = pb.Channels.from_model(m, g2_min=5e-4, delta_nsigma=4.0)
+    with pytest.raises(pb.PBError) as e:
+        pb.Device(ch, variant="c32")
+    assert e.value.code == pb.PB_EINVAL
+    full = pb.Channels.from_model(m)
+    for kw in ({"tile_sweep": 1}, {"merge_branches": 2}, {"stream_mode": 2}, {"dense_rows": 2}):
+        with pytest.raises(pb.PBError) as e:
+            pb.Device(full, variant="c32", **kw)
+        assert e.value.code == pb.PB_EINVAL
+
+
+def test_c32_adjoint_is_refused_and_set_g2_streams_rows(pb):
+    """A C32 device has no FP32 adjoint (PB_EINVAL); after pb_dev_set_g2 it streams the
+    float-float rows, so doubling |g|^2 doubles the integral to FP64 accuracy."""
+    import torch
+
+    m, o, dev0 = setup_case(pb, "win12", "c32")
+    ch = pb.Channels.from_model(m)
+    dev = pb.Device(ch, variant="c32")
+    f = np.random.default_rng(9).uniform(0, 1, dev.nstate)
+    with pytest.raises(pb.PBError) as e:
+        dev.collision_vjp(T(f), T(f))
+    assert e.value.code == pb.PB_EINVAL
+    g2 = torch.tensor(ch.export()["g2"], dtype=torch.float64, device="cuda")
+    dev.set_g2(2.0 * g2)
+    ref, ab = o.collision(f, with_abs=True)
+    check_I(dev.collision(T(f)).cpu().numpy(), 2.0 * ref, 2.0 * ab)
 
 
 # ------------------------------------------------------------------ full size (40^3)
@@ -524,23 +621,35 @@ def test_full_size_rk4_two_steps(big):
     assert nrel(ft.cpu().numpy(), o.rk4(f0, 1.0, 2)) <= TOL
 
 
-@pytest.mark.parametrize("variant", ["g32", "g16", "h16"])
+# the 40^3 workload (the mixed-precision configuration): the targets themselves
+FULL_TOL = {"g32": 1e-6, "g16": 1e-3, "h16": 5e-4, "c32": C32_TOL}
+
+
+@pytest.mark.parametrize("variant", ["g32", "g16", "h16", "c32"])
 def test_full_size_mixed_precision(pb, big, variant):
     m, o, _ = big
-    dev = pb.Device(pb.Channels.from_model(m), variant=variant)
+    dev = pb.Device(big[2].channels, variant=variant)
     f = o.window_values(m.f_hot())
     ref, ab = o.collision(f, with_abs=True)
     I = dev.collision(T(f)).cpu().numpy()
-    check_I(I, ref, ab, tol=MIXED_TOL[variant], abs_tol=MIXED_TOL[variant])
+    check_I(I, ref, ab, tol=FULL_TOL[variant], abs_tol=FULL_TOL[variant])
     print(f"{variant}: normwise df/dt error {np.abs(I - ref).max() / np.abs(ref).max():.3e}")
+    rows = np.arange(3, o.nstate, 151)
+    assert nrel(dev.rates(T(f)).cpu().numpy()[rows], o.rates(f, rows=rows)) <= FULL_TOL[variant]
+    dev.check()
+    dev.close()
 
 
-@pytest.mark.parametrize("variant,bound", [("g32", 1e-6), ("h16", 1e-3)])
+@pytest.mark.parametrize("variant,bound", [
+    ("g32", 1e-6), ("h16", 1e-3), ("c32", C32_TOL),
+    pytest.param("g16", 1e-3, marks=pytest.mark.xfail(
+        strict=True, reason="BF16 rounds each |g|^2 by up to 2^-9: measured 2.08e-3 at the worst of the 1000 "
+                            "steps; the 16-bit form that meets 1e-3 is h16 (FP16 x 2^k)"))])
 def test_full_size_mixed_error_along_trajectory(pb, big, variant, bound):
-    """FP32 (FP16) |g|^2 and FP32 per-channel terms along 1000 RK4 steps of the 40^3 hot
-    start: the df/dt error against the FP64-accurate sweep (itself held to the oracle at
-    1e-12) stays within the 1e-6 (1e-3) target normwise at every 100th step, while max|df/dt|
-    shrinks as f relaxes."""
+    """Reduced-precision forms along 1000 RK4 steps of the 40^3 hot start (FP32 |g|^2, FP16 and
+    BF16 |g|^2 with FP32 per-channel terms; the FP32 coefficient tiles): the df/dt error against
+    the FP64-accurate sweep (itself held to the oracle at 1e-12) at every 100th step, normwise,
+    against the 1e-6 (FP32) and 1e-3 (16-bit) targets, while max|df/dt| shrinks as f relaxes."""
     m, o, dev = big
     mixed = pb.Device(dev.channels, variant=variant)
     f = T(o.window_values(m.f_hot()))

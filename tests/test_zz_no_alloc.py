@@ -39,13 +39,14 @@ def _call_static(pb, dev, f, out):
     return pb.lib().pb_collision_static(dev._h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(out.data_ptr()), stream)
 
 
-@pytest.mark.parametrize("name,variant", [("tiny", "ff"), ("window16", "ff"), ("window24", "ff"),
-                                          ("window16", "f64"), ("window16", "literal")])
-def test_static_matches_regular_on_two_calls(pb, name, variant):
+@pytest.mark.parametrize("name,variant,opts", [("tiny", "ff", {}), ("window16", "ff", {}), ("window24", "ff", {}),
+                                               ("window16", "ff", {"stream_mode": 2}), ("window16", "f64", {}),
+                                               ("window16", "literal", {})])
+def test_static_matches_regular_on_two_calls(pb, name, variant, opts):
     import torch
 
     m = synth.make_config(name)
-    dev = pb.Device(pb.Channels.from_model(m), variant=variant)
+    dev = pb.Device(pb.Channels.from_model(m), variant=variant, **opts)
     rng = np.random.default_rng(17)
     out = torch.empty(dev.nstate, dtype=torch.float64, device="cuda")
     for call in range(2):
@@ -56,6 +57,26 @@ def test_static_matches_regular_on_two_calls(pb, name, variant):
         got = out.cpu().numpy()
         err = np.abs(got - ref).max() / np.abs(ref).max()
         assert err <= TOL, f"call {call}: normwise error {err:.3e}"
+    dev.check()  # no bounded wait of the bulk-copy sweep gave up
+
+
+def test_static_call_allocates_nothing(pb):
+    """After a first call (which looks up the array's address and loads the kernels), further
+    calls leave both torch's allocator and the device's free memory exactly as they were."""
+    import torch
+
+    m = synth.make_config("window16")
+    dev = pb.Device(pb.Channels.from_model(m))
+    f = torch.tensor(np.random.default_rng(3).uniform(0.0, 1.0, dev.nstate), device="cuda")
+    out = torch.empty_like(f)
+    assert _call_static(pb, dev, f, out) == pb.PB_OK
+    torch.cuda.synchronize()
+    before = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved(), torch.cuda.mem_get_info()[0])
+    for _ in range(3):
+        assert _call_static(pb, dev, f, out) == pb.PB_OK
+    torch.cuda.synchronize()
+    after = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved(), torch.cuda.mem_get_info()[0])
+    assert after == before
 
 
 def test_static_refuses_problems_beyond_its_array(pb):
