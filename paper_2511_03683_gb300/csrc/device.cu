@@ -25,9 +25,19 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int kFinBlock = 256;
-// launch shape of the FP32 tile sweep: stages per CTA and resident CTAs per SM
-constexpr int kC32Stages = 2;
-constexpr int kC32Ctas = 2;
+// launch shapes of the FP32 tile sweep (pb_dev_opts.tile_sweep 2..6): stages per CTA and
+// resident CTAs per SM
+template <typename F>
+void with_c32_shape(int shape, F &&fn) {
+  using std::integral_constant;
+  switch (shape) {
+    case 3: fn(integral_constant<int, 3>(), integral_constant<int, 2>()); break;
+    case 4: fn(integral_constant<int, 2>(), integral_constant<int, 2>()); break;
+    case 5: fn(integral_constant<int, 4>(), integral_constant<int, 1>()); break;
+    case 6: fn(integral_constant<int, 6>(), integral_constant<int, 1>()); break;
+    default: fn(integral_constant<int, 2>(), integral_constant<int, 3>()); break;
+  }
+}
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -433,6 +443,7 @@ struct pb_dev {
   // PB_VARIANT_C32: the FF device whose tiles hold FP32 (P_in, P_out) (tiles32.cuh); its
   // partials in tpart are (N, Bd, L, Ld) per (state, block)
   bool c32 = false;
+  int c32_shape = 2;  // pb_dev_opts.tile_sweep: the launch shape (with_c32_shape)
   float2 *tc32 = nullptr;
   int64_t *rp_real = nullptr;  // unpadded CSR row offsets [ns+1]
   float2 *vjpG = nullptr;      // adjoint gather table [ns][3]
@@ -524,13 +535,14 @@ int resolve_opts(const pb_channels *ch, const pb_dev_opts *opts, int sm_count, p
     return set_error(PB_EINVAL, "pb_dev: variant %d is not available in this build", d.variant);
   if (d.merge_branches < 0 || d.merge_branches > 2) return set_error(PB_EINVAL, "pb_dev: merge_branches must be 0..2");
   if (d.dense_rows < 0 || d.dense_rows > 3) return set_error(PB_EINVAL, "pb_dev: dense_rows must be 0..3");
-  if (d.tile_sweep < 0 || d.tile_sweep > 2) return set_error(PB_EINVAL, "pb_dev: tile_sweep must be 0..2");
+  if (d.tile_sweep < 0 || d.tile_sweep > 6 || (d.tile_sweep > 2 && d.variant != PB_VARIANT_C32))
+    return set_error(PB_EINVAL, "pb_dev: tile_sweep must be 0..2 (0..6 for the FP32 coefficient tiles)");
   if (d.adjoint < 0 || d.adjoint > 1) return set_error(PB_EINVAL, "pb_dev: adjoint must be 0 or 1");
   if (d.tile_sweep == 0) d.tile_sweep = 2;
-  if (d.variant == PB_VARIANT_C32 && (d.tile_sweep != 2 || d.stream_mode == 2 || d.merge_branches == 2 ||
+  if (d.variant == PB_VARIANT_C32 && (d.tile_sweep == 1 || d.stream_mode == 2 || d.merge_branches == 2 ||
                                       d.dense_rows == 1 || d.dense_rows == 2))
     return set_error(PB_EINVAL, "pb_dev: the FP32 coefficient tiles (C32) need branch merging and the symmetric "
-                                "bulk-copy tile sweep (merge_branches 0/1, dense_rows 0/3, tile_sweep 0/2, "
+                                "bulk-copy tile sweep (merge_branches 0/1, dense_rows 0/3, tile_sweep 0/2..6, "
                                 "stream_mode 0/1)");
   // measured best on GB300 at 40^3: 3 CTAs per SM for one entry per channel, 4 for the
   // branch-merged sweep (whose stream is six times shorter)
@@ -802,6 +814,7 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
                                 "partner of every other: no |g| or delta cutoffs)");
   }
   d->c32 = c32;
+  d->c32_shape = o.tile_sweep;
   d->sym_nt = d->sym && o.tile_sweep == 2 ? dev::kSymThreads : 0;
   d->td = tile_dims(d->ns);
   const GDense gd = gdense_for(ch, o, sm);
@@ -1140,12 +1153,13 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
     else
       cudaFuncSetAttribute(dev::k_stream_sym_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dev::kSymBulkSmem);
   }
-  if (d->c32) {
-    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    const int sm32 = (int)dev::c32_smem<kC32Stages>();
-    cudaFuncSetAttribute(dev::k_stream_c32<dev::MODE_COLL, kC32Stages, kC32Ctas>, A, sm32);
-    cudaFuncSetAttribute(dev::k_stream_c32<dev::MODE_RATE, kC32Stages, kC32Ctas>, A, sm32);
-  }
+  if (d->c32)
+    with_c32_shape(d->c32_shape, [&](auto nst, auto cps) {
+      const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+      const int sm32 = (int)dev::c32_smem<nst()>();
+      cudaFuncSetAttribute(dev::k_stream_c32<dev::MODE_COLL, nst(), cps()>, A, sm32);
+      cudaFuncSetAttribute(dev::k_stream_c32<dev::MODE_RATE, nst(), cps()>, A, sm32);
+    });
   if (d->smem_f > 48 * 1024) {
     set_stream_smem<uint32_t>((int)d->smem_f);
     set_stream_smem<uint16_t>((int)d->smem_f);
@@ -1292,15 +1306,17 @@ int launch_stream_t(pb_dev *d, int mode, const double *fd, const float2 *fff, co
                                                                  d->bulk_cap, part, d->err);
   } else if (d->variant == PB_VARIANT_FF && d->sym && d->c32 && part == d->part && fff == d->yff) {
     // FP32 coefficient tiles through the bulk-copy ring (tiles32.cuh)
-    const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(d->td.nt, (int64_t)d->sm_count * kC32Ctas));
-    const size_t sm32 = dev::c32_smem<kC32Stages>();
     float *tp = (float *)d->tpart;
-    if (coll)
-      dev::k_stream_c32<dev::MODE_COLL, kC32Stages, kC32Ctas><<<gs, dev::kC32Threads, sm32, st>>>(
-          d->tiles, d->td.nt, d->tc32, fff, ns, d->td.nb, tp, d->err);
-    else
-      dev::k_stream_c32<dev::MODE_RATE, kC32Stages, kC32Ctas><<<gs, dev::kC32Threads, sm32, st>>>(
-          d->tiles, d->td.nt, d->tc32, fff, ns, d->td.nb, tp, d->err);
+    with_c32_shape(d->c32_shape, [&](auto nst, auto cps) {
+      const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(d->td.nt, (int64_t)d->sm_count * cps()));
+      const size_t sm32 = dev::c32_smem<nst()>();
+      if (coll)
+        dev::k_stream_c32<dev::MODE_COLL, nst(), cps()><<<gs, dev::kC32Threads, sm32, st>>>(
+            d->tiles, d->td.nt, d->tc32, fff, ns, d->td.nb, tp, d->err);
+      else
+        dev::k_stream_c32<dev::MODE_RATE, nst(), cps()><<<gs, dev::kC32Threads, sm32, st>>>(
+            d->tiles, d->td.nt, d->tc32, fff, ns, d->td.nb, tp, d->err);
+    });
   } else if (d->variant == PB_VARIANT_FF && d->sym && !d->c32 && part == d->part) {
     // symmetric tiles; the rate mode needs the same (A, B) partials
     if (d->sym_nt && fff == d->yff) {  // the bulk copies read f from this padded arena buffer
@@ -1404,10 +1420,10 @@ void launch_fin(pb_dev *d, const double *ysrc, double *out, double *f, double dt
   else if (d->sym && d->c32)
     if (d->ns <= 2048)
       dev::k_fin_c32<STAGE, false, 8><<<(int)((d->ns + 7) / 8), 256, 0, st>>>(
-          d->tpart, d->td.nb, d->td.nsp, (int)d->ns, d->c, d->R, ysrc, out, f, d->acc, y, d->yff, dt);
+          (const float *)d->tpart, d->td.nb, d->td.nsp, (int)d->ns, d->c, ysrc, out, f, d->acc, y, d->yff, dt);
     else
       dev::k_fin_c32<STAGE><<<(int)((d->ns + 31) / 32), 256, 0, st>>>(
-          d->tpart, d->td.nb, d->td.nsp, (int)d->ns, d->c, d->R, ysrc, out, f, d->acc, y, d->yff, dt);
+          (const float *)d->tpart, d->td.nb, d->td.nsp, (int)d->ns, d->c, ysrc, out, f, d->acc, y, d->yff, dt);
   else if (d->sym)
     if (d->ns <= 2048)  // few states: more, smaller CTAs
       dev::k_fin_tiles<STAGE, false, 8><<<(int)((d->ns + 7) / 8), 256, 0, st>>>(
@@ -1615,9 +1631,9 @@ extern "C" int pb_scatter_rates(pb_dev *d, const double *f, double *inv_tau, voi
     dev::k_fin_rate<true><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->fwd_item_ptr(), d->part}, (int)d->ns,
                                                              d->mixed() ? d->gscale() : d->c, d->R, inv_tau);
   else if (d->sym && d->c32)
-    dev::k_fin_c32<-1, true><<<(int)((d->ns + 31) / 32), 256, 0, st>>>(d->tpart, d->td.nb, d->td.nsp, (int)d->ns, d->c,
-                                                                       d->R, nullptr, inv_tau, nullptr, nullptr,
-                                                                       nullptr, nullptr, 0.0);
+    dev::k_fin_c32<-1, true><<<(int)((d->ns + 31) / 32), 256, 0, st>>>((const float *)d->tpart, d->td.nb, d->td.nsp,
+                                                                       (int)d->ns, d->c, nullptr, inv_tau, nullptr,
+                                                                       nullptr, nullptr, nullptr, 0.0);
   else if (d->sym)
     dev::k_fin_tiles<-1, true><<<(int)((d->ns + 31) / 32), 256, 0, st>>>(
         dev::TileSrc{d->tpart, d->td.nb, d->td.nsp}, (int)d->ns, d->c, d->R, nullptr, inv_tau, nullptr, nullptr, nullptr,

@@ -13,21 +13,13 @@
 //     n = P_in f_p - P_out f_s - d f_s f_p,   d = P_in - P_out,
 //     u = fl(P_in f_p),  e = P_in f_p - u (exact, one FMA),  v = fl(P_out f_s - u) (one FMA),
 //     n = fl(-d fl(f_s f_p) + (e - v)),
-// so the rounding left in n is relative to n, and the sums over a row are sums of net terms.
-// The occupations are float-float (f = f_h + f_l); the sweep uses f_h and adds the first-order
-// terms in f_l from four sums per state:
-//     N_s  = sum_p n(s,p)                       (at f_h)
-//     Bd_s = sum_p f_h,p d(s,p),   L_s = sum_p f_l,p P_in(s,p),   Ld_s = sum_p f_l,p d(s,p),
-//     I_s  = c [ N_s + L_s - f_s Ld_s - f_l,s (R_s + Bd_s) ],   R_s = sum_p P_out(s,p),
-// (dn/df_p = P_in - f_s d, dn/df_s = -(P_out + f_p d)); the second-order term f_l,s f_l,p d is
-// below 2^-48 of the products.
+// so the rounding left in n is relative to n.  The occupations are float-float (f = f_h + f_l);
+// n is taken at f_h and the entry adds its first-order change in f_l,
+//     t(s,p) = n + f_l,p (P_in - f_s d) - f_l,s (P_out + f_p d)
+// (dn/df_p = P_in - f_s d, dn/df_s = -(P_out + f_p d); the second-order term f_l,s f_l,p d is
+// below 2^-48 of the products).  t(p,s) = -t(s,p) for every f, so the row of s adds t and the
+// row of p subtracts the same FP32 value: each state needs one sum, I_s = c sum_p t(s,p).
 //
-// Why the coefficients are rounded together.  Rounding P_in and P_out independently perturbs
-// the two products of n by different relative amounts, an error of 2^-24 of the gross terms
-// again.  A common relative error scales n itself.  So each entry stores the pair (a, b) that
-// keeps the ratio P_out / P_in best: a is taken within kC32RatioUlps units in the last place of
-// P_in, b = fl(a P_out / P_in), and the candidate whose b / a is closest to P_out / P_in wins
-// (the choice of a scales the entry by a relative amount of at most about 2.5 ulp).
 namespace pb {
 namespace dev {
 
@@ -35,7 +27,8 @@ constexpr int kC32Threads = 256;
 constexpr int kC32RatioUlps = 2;
 constexpr unsigned kC32TileBytes = kTile * kTile * sizeof(float2);
 constexpr unsigned kC32StageBytes = kC32TileBytes + 2 * kTile * sizeof(float2);
-constexpr size_t kC32ColFloats = (size_t)(kC32Threads / 32) * 4 * kTile;  // [8 warps][4 sums][64 columns]
+constexpr size_t kC32ColFloats = (size_t)(kC32Threads / 32) * kTile;  // [8 warps][64 columns]
+// dynamic shared memory of a launch shape with NST stages (and the double-buffered column table)
 template <int NST>
 constexpr size_t c32_smem() {
   return (size_t)NST * kC32StageBytes + 128 + 2 * kC32ColFloats * sizeof(float);
@@ -111,28 +104,33 @@ __device__ __forceinline__ void f32_reduce_scatter(float (&v)[NV], int lane) {
   }
 }
 
-// the column sums of a finished off-diagonal tile: thread (sum, column) adds the 8 warps' values
-// and writes them to the column state's partial for block IJ.x
+// the column sums of a finished off-diagonal tile: threads 0..63 add the 8 warps' values of
+// one column each and write them to the column state's partial for block IJ.x
 __device__ __forceinline__ void c32_columns_out(const float *__restrict__ colred, int2 IJ, int nb, int tid,
                                                 float *__restrict__ tp) {
-  const int comp = tid >> 6, col = tid & (kTile - 1);
-  float acc = colred[comp * kTile + col];
+  if (tid >= kTile) return;
+  float acc = colred[tid];
 #pragma unroll
-  for (int w = 1; w < kC32Threads / 32; ++w) acc = __fadd_rn(acc, colred[(w * 4 + comp) * kTile + col]);
-  tp[((long long)(IJ.y * kTile + col) * nb + IJ.x) * 4 + comp] = acc;
+  for (int w = 1; w < kC32Threads / 32; ++w) acc = __fadd_rn(acc, colred[w * kTile + tid]);
+  tp[(long long)(IJ.y * kTile + tid) * nb + IJ.x] = acc;
 }
 
 // One persistent 256-thread CTA (CPS per SM) streams its share of the tiles through NST
 // shared-memory stages filled by bulk copies (thread 0 issues, completion counted in bytes on
 // one mbarrier per stage, every wait bounded), as k_stream_sym_bulk does for the float-float
-// tiles.  Thread (ti, tj) takes rows 4 ti .. 4 ti + 3 and columns tj + 16 j.  Partials per
-// (state, block of partner states): MODE_COLL (N, Bd, L, Ld) as above; MODE_RATE (rate sum,
-// its f_l term, 0, 0) with the summand P_out + f_p d of 1/tau_s.
+// tiles.  Thread (ti, tj) takes rows 4 ti .. 4 ti + 3 and columns tj + 16 j.  One FP32 partial
+// per (state, block of partner states): MODE_COLL the sum of t above; MODE_RATE the sum of the
+// 1/tau_s summands P_out + f_p d (row s) and P_in - f_s d (column p, the reverse channel), each
+// with its f_l term.  The per-warp column table is double buffered and combined in the next
+// iteration, so a tile costs one CTA barrier.
 template <int MODE, int NST, int CPS>
 __global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32(const int2 *__restrict__ tiles, int nt,
                                                                   const float2 *__restrict__ tc,
                                                                   const float2 *__restrict__ fg, int ns, int nb,
                                                                   float *__restrict__ tp, int *__restrict__ err) {
+  // the stage of tile k - 1 is refilled (with tile k - 1 + NST) only after the wait for tile k, so
+  // one stage would wait for a copy not yet issued
+  static_assert(NST >= 2 && NST <= 8, "the ring needs 2..8 stages");
   constexpr int R = 4;
   extern __shared__ __align__(128) unsigned char ssm[];
   unsigned long long *bars = (unsigned long long *)(ssm + NST * kC32StageBytes);
@@ -196,9 +194,9 @@ __global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32(const int2 *__r
     float2 fcol[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) fcol[j] = fc[tj + 16 * j];
-    float rv[4 * R], cv[16];  // [sum][row], [sum][column slot]
+    float rv[R], cv[4];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) rv[i] = cv[i] = 0.f;
+    for (int i = 0; i < 4; ++i) rv[i] = cv[i] = 0.f;
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       const int row = ti * R + i;
@@ -215,45 +213,29 @@ __global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32(const int2 *__r
           const float ex = __fmaf_rn(a, fp, -u);
           const float v = __fmaf_rn(b, fs.x, -u);
           const float w = __fmul_rn(fs.x, fp);
-          const float n = __fmaf_rn(-d, w, __fsub_rn(ex, v));
-          rv[0 * R + i] = __fadd_rn(rv[0 * R + i], n);
-          rv[1 * R + i] = __fmaf_rn(fp, d, rv[1 * R + i]);
-          rv[2 * R + i] = __fmaf_rn(flp, a, rv[2 * R + i]);
-          rv[3 * R + i] = __fmaf_rn(flp, d, rv[3 * R + i]);
-          if (!diag) {
-            cv[0 * 4 + j] = __fsub_rn(cv[0 * 4 + j], n);
-            cv[1 * 4 + j] = __fmaf_rn(-fs.x, d, cv[1 * 4 + j]);
-            cv[2 * 4 + j] = __fmaf_rn(fs.y, b, cv[2 * 4 + j]);
-            cv[3 * 4 + j] = __fmaf_rn(-fs.y, d, cv[3 * 4 + j]);
-          }
+          float t = __fmaf_rn(-d, w, __fsub_rn(ex, v));
+          t = __fmaf_rn(flp, __fmaf_rn(-fs.x, d, a), t);
+          t = __fmaf_rn(-fs.y, __fmaf_rn(fp, d, b), t);
+          rv[i] = __fadd_rn(rv[i], t);
+          if (!diag) cv[j] = __fsub_rn(cv[j], t);
         } else {  // 1/tau summands: row s: P_out + f_p d; column p (reverse channel): P_in - f_s d
-          rv[0 * R + i] = __fadd_rn(rv[0 * R + i], __fmaf_rn(fp, d, b));
-          rv[1 * R + i] = __fmaf_rn(flp, d, rv[1 * R + i]);
-          if (!diag) {
-            cv[0 * 4 + j] = __fadd_rn(cv[0 * 4 + j], __fmaf_rn(-fs.x, d, a));
-            cv[1 * 4 + j] = __fmaf_rn(-fs.y, d, cv[1 * 4 + j]);
-          }
+          rv[i] = __fadd_rn(rv[i], __fmaf_rn(flp, d, __fmaf_rn(fp, d, b)));
+          if (!diag) cv[j] = __fadd_rn(cv[j], __fmaf_rn(-fs.y, d, __fmaf_rn(-fs.x, d, a)));
         }
       }
     }
-    // rows: the 16 lanes of a half-warp share them; lane tj ends with sum tj >> 2 of row tj & 3
-    f32_reduce_scatter<16, 8>(rv, lane);
-    {
-      const int row = IJ.x * kTile + ti * R + (tj & 3);
-      tp[((long long)row * nb + IJ.y) * 4 + (tj >> 2)] = rv[0];
-    }
+    // rows: the 16 lanes of a half-warp share them; lanes 4i .. 4i + 3 end with the total of row i
+    f32_reduce_scatter<R, 8>(rv, lane);
+    if ((tj & 3) == 0) tp[(long long)(IJ.x * kTile + ti * R + (tj >> 2)) * nb + IJ.y] = rv[0];
     if (!diag) {
       // columns: lanes tj and tj + 16 share them (one level), then the 8 warps (next iteration)
       float *colred = colred0 + (k & 1) * kC32ColFloats;
       const bool up = lane & 16;
 #pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        const int comp = m >> 1, jk = m & 1, jo = jk + 2;  // kept / sent column slot
-        const float kept = up ? cv[comp * 4 + jo] : cv[comp * 4 + jk];
-        const float sent = up ? cv[comp * 4 + jk] : cv[comp * 4 + jo];
-        const float w = __fadd_rn(kept, __shfl_xor_sync(0xFFFFFFFFu, sent, 16));
-        const int col = tj + 16 * ((up ? 2 : 0) + jk);
-        colred[(wid * 4 + comp) * kTile + col] = w;
+      for (int jk = 0; jk < 2; ++jk) {
+        const int jo = jk + 2;  // kept / sent column slot
+        const float kept = up ? cv[jo] : cv[jk], sent = up ? cv[jk] : cv[jo];
+        colred[wid * kTile + tj + 16 * ((up ? 2 : 0) + jk)] = __fadd_rn(kept, __shfl_xor_sync(0xFFFFFFFFu, sent, 16));
       }
     }
   }
@@ -269,63 +251,44 @@ __global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32(const int2 *__r
 }
 
 // Epilogue of the C32 sweep: a 256-thread CTA takes SPC states; each warp adds the block
-// partials of SPC / 8 states (lanes over the blocks, N in float-float, the three correction sums
-// in FP32, then a 32-lane butterfly), and warp 0 applies the combination above and the RK4 stage
-// arithmetic in FP64, one lane per state.  RATE: 1/tau = c (rate sum + its f_l term).
+// partials of SPC / 8 states (lanes over the blocks, float-float, then a 32-lane butterfly), and
+// warp 0 applies the prefactor and the RK4 stage arithmetic in FP64, one lane per state.
 template <int STAGE, bool RATE = false, int SPC = 32>
-__global__ void __launch_bounds__(256) k_fin_c32(const float4 *__restrict__ tp, int nb, int nsp, int ns, double c,
-                                                 const double *__restrict__ R, const double *__restrict__ ysrc,
-                                                 double *__restrict__ out, double *__restrict__ f,
-                                                 double *__restrict__ acc, double *__restrict__ y,
-                                                 float2 *__restrict__ yff, double dt) {
+__global__ void __launch_bounds__(256) k_fin_c32(const float *__restrict__ tp, int nb, int nsp, int ns, double c,
+                                                 const double *__restrict__ ysrc, double *__restrict__ out,
+                                                 double *__restrict__ f, double *__restrict__ acc,
+                                                 double *__restrict__ y, float2 *__restrict__ yff, double dt) {
   constexpr int SPW = SPC / 8;
-  __shared__ float4 tot[SPC];  // (N hi, N lo, Bd, L)
-  __shared__ float totd[SPC];  // Ld
+  __shared__ float2 tot[SPC];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int base = blockIdx.x * SPC;
   const int r0 = base + lane;
   FinIn in{0.0, 0.0, 0.0, 0.0};
-  if (wid == 0 && lane < SPC && r0 < ns) {
-    if (RATE) in.R = 0.0;
-    else in = fin_load<false, STAGE>(r0, R, ysrc, f, acc);
+  if (!RATE && wid == 0 && lane < SPC && r0 < ns) {
+    if (STAGE >= 0) in.f = f[r0];
+    if (STAGE >= 1) in.acc = acc[r0];
   }
 #pragma unroll
   for (int q = 0; q < SPW; ++q) {
     const int r = base + SPW * wid + q;
     float2 N = make_float2(0.f, 0.f);
-    float B = 0.f, L = 0.f, D = 0.f;
     if (r < nsp) {
-      const float4 *__restrict__ row = tp + (long long)r * nb;
-      for (int k = lane; k < nb; k += 32) {
-        const float4 x = row[k];
-        N = ff_add(N, make_float2(x.x, 0.f));
-        B = __fadd_rn(B, x.y);
-        L = __fadd_rn(L, x.z);
-        D = __fadd_rn(D, x.w);
-      }
+      const float *__restrict__ row = tp + (long long)r * nb;
+      for (int k = lane; k < nb; k += 32) N = ff_add(N, make_float2(row[k], 0.f));
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = 16; o > 0; o >>= 1)
       N = ff_add(N, make_float2(__shfl_xor_sync(0xFFFFFFFFu, N.x, o), __shfl_xor_sync(0xFFFFFFFFu, N.y, o)));
-      B = __fadd_rn(B, __shfl_xor_sync(0xFFFFFFFFu, B, o));
-      L = __fadd_rn(L, __shfl_xor_sync(0xFFFFFFFFu, L, o));
-      D = __fadd_rn(D, __shfl_xor_sync(0xFFFFFFFFu, D, o));
-    }
-    if (lane == 0) {
-      tot[SPW * wid + q] = make_float4(N.x, N.y, B, L);
-      totd[SPW * wid + q] = D;
-    }
+    if (lane == 0) tot[SPW * wid + q] = N;
   }
   __syncthreads();
   if (wid != 0 || lane >= SPC || r0 >= ns) return;
-  const float4 Tt = tot[lane];
-  const double Nsum = ff_to_double(Tt.x, Tt.y);
+  const float2 Tt = tot[lane];
+  const double I = c * ff_to_double(Tt.x, Tt.y);
   if (RATE) {
-    out[r0] = c * (Nsum + (double)Tt.z);
+    out[r0] = I;
     return;
   }
-  const double ys = in.y, yl = ys - (double)__double2float_rn(ys);
-  const double I = c * (Nsum + (double)Tt.w - ys * (double)totd[lane] - yl * (in.R + (double)Tt.z));
   fin_stage<STAGE, false>(r0, I, in, out, f, acc, y, yff, dt);
 }
 
