@@ -35,6 +35,8 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--repeats", type=int, default=5,
+                    help="timed blocks of --steps steps each; value and ms_per_step are their median")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="window40")
     ap.add_argument("--variant", default="ff")
@@ -432,6 +434,27 @@ def batched_report(pb, ninst, nsteps, stream):
         a, e = bf.offsets[i], bf.offsets[i + 1]
         err_f = max(err_f, float(np.abs(If[a:e] - ref).max() / max(np.abs(ref).max(), 1e-300)))
     bf.close()
+
+    # the same batch with the FP32 pair coefficients (net terms per entry)
+    bc = pb.Batch(chs, precision="c32")
+    item_c, ctas_c, tune_c = bc.autotune(f)
+    g = f.clone()
+    bc.rk4(g, 1.0, 3)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    bc.rk4(g, 1.0, nsteps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_bc = e0.elapsed_time(e1)
+    Ic = bc.collision(f).cpu().numpy()
+    err_c = 0.0
+    for i, (c, x) in enumerate(zip(chs, fs)):
+        d = pb.Device(c)
+        ref = d.collision(torch.tensor(x, device="cuda")).cpu().numpy()
+        d.close()
+        a, e = bc.offsets[i], bc.offsets[i + 1]
+        err_c = max(err_c, float(np.abs(Ic[a:e] - ref).max() / max(np.abs(ref).max(), 1e-300)))
+    bc.close()
     return {"instances": ninst, "states": b.nstate, "channels": nch, "build_channels_s": build_s,
             "autotuned": {"item_channels": item, "ctas_per_sm": ctas, "sweep_ms": tune_ms},
             "rk4_steps": nsteps, "batched_ms": ms_b,
@@ -446,6 +469,12 @@ def batched_report(pb, ninst, nsteps, stream):
                          "speedup_vs_sequential_ff": ms_ff / ms_bf,
                          "speedup_vs_sequential_ff_per_channel": ms_ffc / ms_bf,
                          "dfdt_err_vs_unbatched_ff_max_over_instances": err_f},
+            "c32_batch": {"autotuned": {"item_entries": item_c, "ctas_per_sm": ctas_c, "sweep_ms": tune_c},
+                          "batched_ms": ms_bc, "batched_rk4_steps_per_s": nsteps / (ms_bc * 1e-3),
+                          "batched_channels_per_s": 4 * nch * nsteps / (ms_bc * 1e-3),
+                          "speedup_vs_sequential_ff": ms_ff / ms_bc, "speedup_vs_ff_batch": ms_bf / ms_bc,
+                          "speedup_vs_sequential_fp32": ms_g / ms_bc,
+                          "dfdt_err_vs_fp64_max_over_instances": err_c},
             "dfdt_err_vs_fp64_max_over_instances": err}
 
 
@@ -611,15 +640,18 @@ def run_ours(args):
         step(Fa, Fb) if i % 2 == 0 else step(Fb, Fa)
         i += 1
         torch.cuda.synchronize()
-    barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for i in range(args.steps):
-        step(Fa, Fb) if i % 2 == 0 else step(Fb, Fa)
-    e1.record(stream)
-    barrier()
-    ms = e0.elapsed_time(e1)
-    ms_max = rank_max(ms)
+    block_ms = []
+    for _ in range(max(1, args.repeats)):
+        # each block: exactly --steps steps, a barrier and a device synchronisation on both sides
+        barrier()
+        e0.record(stream)
+        for i in range(args.steps):
+            step(Fa, Fb) if i % 2 == 0 else step(Fb, Fa)
+        e1.record(stream)
+        barrier()
+        block_ms.append(rank_max(e0.elapsed_time(e1)))
+    ms_max = statistics.median(block_ms)
     value = whole_job_value(SWEEPS_PER_STEP * nch * args.steps, ws, ms_max * 1e-3)
 
     # rt-BTE RK4 steps per second (one call, graph replay)
@@ -677,28 +709,21 @@ def run_ours(args):
         Fs, iters, resid, ok = dev.transport(f0, v, tol=1e-10, maxit=1000)
         solve = {"iterations": iters, "residual": resid, "converged": ok, "seconds": time.perf_counter() - t0}
 
-    # end to end through the public API from pinned host buffers: every step copies f and F
-    # host -> device, runs the RK4 step and the transport iteration, copies both results back
-    # and waits for them (one stream synchronisation per step)
+    # end to end through the C ABI's host-buffer calls from pinned host memory: every step is
+    # pb_rtbte_rk4_host (f host -> device, one RK4 step, f device -> host, synchronise) and
+    # pb_transport_iterate_host (F host -> device, one transport pass, F device -> host,
+    # synchronise), so the host holds both results after every step
     e2e = None
     if not args.no_e2e:
         f_host = torch.tensor(fh).pin_memory()
         F_host = torch.zeros((ns, 3), dtype=torch.float64).pin_memory()
-        f_dev = torch.empty(ns, dtype=torch.float64, device="cuda")
-        F_dev = torch.empty((ns, 3), dtype=torch.float64, device="cuda")
-        F_out = torch.empty_like(F_dev)
-        fnp = f_host.numpy()
+        fnp, Fnp = f_host.numpy(), F_host.numpy()
 
         def e2e_step():
-            f_dev.copy_(f_host, non_blocking=True)
-            F_dev.copy_(F_host, non_blocking=True)
-            dev.rk4(f_dev, dt, 1)
-            dev.transport_iterate(v, F_dev, out=F_out)
-            f_host.copy_(f_dev, non_blocking=True)
-            F_host.copy_(F_out, non_blocking=True)
-            torch.cuda.current_stream().synchronize()
+            dev.rk4_host(f_host, dt, 1, out=f_host)
+            dev.transport_iterate_host(v, F_host, out=F_host)
 
-        for _ in range(min(args.warmup, 3)):
+        for _ in range(max(3, min(args.warmup, 5))):
             e2e_step()
         barrier()
         t0 = time.perf_counter()
@@ -706,9 +731,10 @@ def run_ours(args):
             e2e_step()
         torch.cuda.synchronize()
         e2e_s = rank_max(time.perf_counter() - t0)
-        assert np.isfinite(fnp).all()
+        assert np.isfinite(fnp).all() and np.isfinite(Fnp).all()
         e2e = {"value": ws * SWEEPS_PER_STEP * nch * args.steps / e2e_s, "unit": "channels/s",
-               "h2d_bytes_per_step": 8 * ns + 24 * ns, "d2h_bytes_per_step": 8 * ns + 24 * ns}
+               "h2d_bytes_per_step": 8 * ns + 24 * ns, "d2h_bytes_per_step": 8 * ns + 24 * ns,
+               "calls": "pb_rtbte_rk4_host + pb_transport_iterate_host per step (pinned host buffers)"}
 
     variants = None
     if not args.no_variants and ws == 1:
@@ -755,6 +781,14 @@ def run_ours(args):
                          "layout": "one entry per state pair (branches merged)" if dev.merged else "one entry per channel",
                          "peak_source": peak_src},
             "cpu_baseline": base, "e2e": e2e, "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+            "repeats": {"blocks": len(block_ms), "steps_per_block": args.steps, "ms_per_step": [b / args.steps for b in block_ms],
+                        "median": ms_max / args.steps, "min": min(block_ms) / args.steps,
+                        "max": max(block_ms) / args.steps},
+            "state_pairs": {"per_sweep": ns * ns, "per_s": whole_job_value(SWEEPS_PER_STEP * ns * ns * args.steps, ws, ms_max * 1e-3),
+                            "channels_per_pair": nch / (ns * ns),
+                            "note": "the sweeps stream coefficients summed once per state pair (branches merged at "
+                                    "setup); value counts the physical channels those pairs carry"},
+            "setup_ms": create_s * 1e3, "setup_in_steps": create_s * 1e3 / (ms_max / args.steps),
             "clocks": clk, "setup": {"build_channels_s": build_s, "device_create_s": create_s},
             "transport_solve": solve, "variants": variants, "batched": batched, "paper_layout": ablation,
             "adjoint": adjoint,

@@ -299,6 +299,16 @@ int pb_transport_setup(pb_dev *dev, const double *f0, void *stream);
 int pb_transport_iterate(pb_dev *dev, const double *vel3, const double *F3in, double *F3out, double *resid3,
                          void *stream);
 
+/* Same as pb_transport_iterate with the iterates in HOST buffers: copies F3in_host
+ * (double[nstate][3]) to the device, runs one pass with the weights of the last
+ * pb_transport_setup, copies the new iterate to F3out_host (which may equal F3in_host) and, if
+ * resid3_host is not NULL, the three residual numbers of pb_transport_iterate to it, then
+ * synchronises `stream`.  vel3 is a device vector as there.  The host buffers should be pinned
+ * for asynchronous copies; pageable memory works.  Needs opts.transport != 0 (the copies use the
+ * handle's own iterate buffers). */
+int pb_transport_iterate_host(pb_dev *dev, const double *vel3, const double *F3in_host, double *F3out_host,
+                              double *resid3_host, void *stream);
+
 /* One transport map application without the convergence loop: F3out = tau (v + W F3in)
  * with W, tau at f0 (pb_transport_setup followed by pb_transport_iterate). */
 int pb_transport_map(pb_dev *dev, const double *f0, const double *vel3, const double *F3in, double *F3out,
@@ -355,7 +365,8 @@ int pb_dev_set_g2(pb_dev *dev, const double *g2, void *stream);
  * literal per-channel form of Eq. 2 with |g|^2 stored in FP32 (rounded on the host), FP32
  * per-channel arithmetic with Kahan lane sums and FP64 states.  Precision 1: the
  * FP64-accurate branch-merged coefficient stream of the FF variant, each instance's
- * prefactor folded into its coefficients.  Device vectors are the instances' state vectors
+ * prefactor folded into its coefficients.  Precision 2: those coefficients as FP32 pairs
+ * (the PB_VARIANT_C32 arithmetic on rows).  Device vectors are the instances' state vectors
  * concatenated in instance order (offsets from pb_batch_get_info). */
 typedef struct pb_batch pb_batch;
 
@@ -366,7 +377,10 @@ typedef struct pb_batch_opts {
   int32_t precision;      /* 0: |g|^2 in FP32, the literal per-channel form of Eq. 2 in FP32 (one entry per
                              channel); 1: FP64-accurate: each instance's coefficients computed in FP64,
                              summed over the branches of every state pair, stored float-float (one entry
-                             per state pair) */
+                             per state pair); 2: the coefficients of 1 rounded once to FP32 pairs
+                             (P_in, P_out) with their ratio kept (8 bytes per state pair), each entry's
+                             net term in FP32 with an exact leading product and first-order terms in the
+                             low part of f, as PB_VARIANT_C32 (df/dt within about 1e-6) */
   int32_t layout;         /* precision 0: 0 automatic (the dense pair-major form when the stored channels
                              fill at least 85% of the instances' (state, partner, branch) slots: |g|^2 in
                              one FP32 slot each, zero where no channel exists, no index streamed; work

@@ -121,6 +121,7 @@ def lib() -> ctypes.CDLL:
         "pb_transport_map": [vp, vp, vp, vp, vp, vp],
         "pb_transport_setup": [vp, vp, vp],
         "pb_transport_iterate": [vp, vp, vp, vp, vp, vp],
+        "pb_transport_iterate_host": [vp, vp, vp, vp, vp, vp],
         "pb_observables": [vp, vp, vp, vp],
         "pb_collision_vjp": [vp, vp, vp, vp, vp, vp],
         "pb_batch_arena_bytes": [vp, i32, vp, ctypes.POINTER(ctypes.c_size_t)],
@@ -395,6 +396,20 @@ class Device:
             _check(rc)
         return out, int(it.value), float(res.value), rc == PB_OK
 
+    def transport_iterate_host(self, vel3, F_in, out=None, resid=None, stream=None):
+        """pb_transport_iterate_host: one pass with the iterates in host memory (numpy arrays
+        or pinned CPU torch tensors of shape [nstate, 3]); synchronous.  ``resid`` (3 doubles in
+        host memory) receives the residual numbers if given."""
+        def ptr(a):
+            return ctypes.c_void_p(a.data_ptr()) if hasattr(a, "data_ptr") else ctypes.c_void_p(a.ctypes.data)
+
+        src = F_in if hasattr(F_in, "data_ptr") else np.ascontiguousarray(F_in, dtype=np.float64)
+        if out is None:
+            out = np.empty((self.nstate, 3))
+        _check(lib().pb_transport_iterate_host(self._h, _dev_vec(vel3, self.nstate, "vel3", 3), ptr(src), ptr(out),
+                                               None if resid is None else ptr(resid), _stream_ptr(stream)))
+        return out
+
     def transport_map(self, f0, vel3, F_in, out=None, stream=None):
         out = self._new(self.nstate, 3) if out is None else out
         _check(lib().pb_transport_map(self._h, _dev_vec(f0, self.nstate, "f0"), _dev_vec(vel3, self.nstate, "vel3", 3),
@@ -485,10 +500,11 @@ class _BatchOpts(ctypes.Structure):
 
 class Batch:
     """Many channel lists advanced together (pb_batch_*), one sweep launch per stage:
-    precision "fp32" (|g|^2 in FP32, literal per-channel form) or "ff" (FP64-accurate
-    branch-merged coefficients)."""
+    precision "fp32" (|g|^2 in FP32, literal per-channel form), "ff" (FP64-accurate
+    branch-merged coefficients) or "c32" (those coefficients as FP32 pairs with the net-term
+    arithmetic of the c32 device variant)."""
 
-    PRECISIONS = {"fp32": 0, "ff": 1}
+    PRECISIONS = {"fp32": 0, "ff": 1, "c32": 2}
 
     def __init__(self, channels, item_channels: int = 0, ctas_per_sm: int = 0, precision: str = "fp32", layout: int = 0,
                  stream=None):

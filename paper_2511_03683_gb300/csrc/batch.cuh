@@ -15,6 +15,11 @@
 // phonons, T and sigma), summed over the branches of each state pair and scaled by the
 // instance's 2 pi / (hbar N_q), then concatenated; the sweep and the RK4 stage epilogues are
 // the single-system float-float kernels run over all instances at once.
+//
+// With precision = 2 the same branch-merged coefficients are rounded once to FP32 pairs
+// (P_in, P_out) with their ratio kept, 8 bytes per state pair, and the row stream forms each
+// entry's net term in FP32 with an exact leading product and the first-order terms in the low
+// part of f (tiles32.cuh): df/dt within about 1e-6 of Eq. 2.
 
 namespace pb {
 namespace dev {
@@ -257,6 +262,7 @@ struct pb_batch {
   // indices, per-state R (with the instance's prefactor folded in) and float-float stage input
   int prec = 0;
   float2 *pA = nullptr, *pB = nullptr, *yff = nullptr;
+  float2 *pC = nullptr;  // precision 2: rounded FP32 (P_in, P_out) per entry
   uint32_t *pidx = nullptr;
   double *Rg = nullptr;
   cudaStream_t cap = nullptr;
@@ -394,13 +400,15 @@ std::vector<int64_t> batch_pair_lenp(const pb_channels *const *chs, int32_t n) {
 }
 
 struct BatchLayoutFF {
-  size_t items, item_inst, item_ptr, pA, pB, pidx, Rg, yff, part, acc, y, tcol, tg2, tcA, tcB, titems, titem_ptr, tpart,
-      tR, tpcst, tpcnt, omega_tmp, tab_tmp, eps_tmp, kc_tmp, total;
+  size_t items, item_inst, item_ptr, pA, pB, pC, pidx, Rg, yff, part, acc, y, tcol, tg2, tcA, tcB, titems, titem_ptr,
+      tpart, tR, tpcst, tpcnt, omega_tmp, tab_tmp, eps_tmp, kc_tmp, total;
 };
 
 constexpr int kBatchSetupItem = 2048;  // channels per work item of the per-instance coefficient setup
 
-BatchLayoutFF batch_layout_ff(const pb_channels *const *chs, int n, int64_t ns, int64_t nent, int64_t nitems_cap) {
+// c32: also the rounded FP32 pairs of precision 2
+BatchLayoutFF batch_layout_ff(const pb_channels *const *chs, int n, int64_t ns, int64_t nent, int64_t nitems_cap,
+                              bool c32 = false) {
   BatchLayoutFF L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -432,6 +440,7 @@ BatchLayoutFF batch_layout_ff(const pb_channels *const *chs, int n, int64_t ns, 
   L.item_ptr = take(sizeof(int32_t) * (ns + 1));
   L.pA = take(sizeof(float2) * nent);
   L.pB = take(sizeof(float2) * nent);
+  L.pC = take(c32 ? sizeof(float2) * nent : 0);
   L.pidx = take(sizeof(uint32_t) * nent);
   L.Rg = take(sizeof(double) * ns);
   L.yff = take(sizeof(float2) * ns);
@@ -499,6 +508,15 @@ int batch_upload_plan(pb_batch *b, int item_ch, cudaStream_t st, bool csr = fals
 }
 
 int batch_sweep(pb_batch *b, cudaStream_t st) {
+  if (b->prec == 2) {
+    const int64_t need = (b->nitems * 32 + dev::kBlock - 1) / dev::kBlock;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)b->sm_count * b->ctas));
+    pb::dev::k_stream_c32_rows<uint32_t><<<grid, dev::kBlock, 0, st>>>(b->items, (int)b->nitems,
+                                                                        (const float4 *)b->pC, b->pidx, b->yff,
+                                                                        b->part);
+    PB_LAUNCHED("k_stream_c32_rows (batch)");
+    return PB_OK;
+  }
   if (b->prec == 1) {
     const int64_t need = (b->nitems * 32 + dev::kBlock - 1) / dev::kBlock;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)b->sm_count * b->ctas));
@@ -524,6 +542,14 @@ int batch_sweep(pb_batch *b, cudaStream_t st) {
 // src: the stage input (f for STAGE <= 0, y after), read by the FP64-accurate epilogue
 template <int STAGE>
 int batch_fin(pb_batch *b, double *out, double *f, double dt, cudaStream_t st, const double *src) {
+  if (b->prec == 2) {
+    // the partials are sums of t (prefactors folded in): the plain-sum epilogue with c = -1 gives
+    // I = -c A = A; it writes the next stage's float-float input like the FF batch
+    pb::dev::k_fin_coll<true, STAGE><<<(int)((b->ns + 255) / 256), 256, 0, st>>>(
+        pb::dev::ItemSrc{b->item_ptr, b->part}, (int)b->ns, -1.0, nullptr, src, out, f, b->acc, b->y, b->yff, dt);
+    PB_LAUNCHED("k_fin_coll (batch, FP32 pairs)");
+    return PB_OK;
+  }
   if (b->prec == 1) {
     pb::dev::k_fin_coll<false, STAGE><<<(int)((b->ns + 255) / 256), 256, 0, st>>>(
         pb::dev::ItemSrc{b->item_ptr, b->part}, (int)b->ns, 1.0, b->Rg, src, out, f, b->acc, b->y, b->yff, dt);
@@ -538,7 +564,7 @@ int batch_fin(pb_batch *b, double *out, double *f, double dt, cudaStream_t st, c
 }
 
 int batch_stage_input(pb_batch *b, const double *f, cudaStream_t st) {
-  if (b->prec == 1) {
+  if (b->prec >= 1) {
     dev::k_to_ff<<<(int)std::max<int64_t>(1, std::min<int64_t>((b->ns + 255) / 256, 1024)), 256, 0, st>>>(
         f, (long long)b->ns, b->yff);
     PB_LAUNCHED("k_to_ff (batch)");
@@ -691,13 +717,13 @@ extern "C" int pb_batch_arena_bytes(const pb_channels *const *chs, int32_t n, co
   int rc = batch_check(chs, n, &ns, &nchp);
   if (rc) return rc;
   const int prec = opts ? opts->precision : 0;
-  if (prec < 0 || prec > 1) return set_error(PB_EINVAL, "pb_batch: precision must be 0 or 1");
+  if (prec < 0 || prec > 2) return set_error(PB_EINVAL, "pb_batch: precision must be 0, 1 or 2");
   try {
-    if (prec == 1) {
+    if (prec >= 1) {
       const std::vector<int64_t> lenp = batch_pair_lenp(chs, n);
       int64_t nent = 0;
       for (int64_t l : lenp) nent += l;
-      *bytes = batch_layout_ff(chs, n, ns, nent, batch_items_count(lenp, kBatchMinItem)).total;
+      *bytes = batch_layout_ff(chs, n, ns, nent, batch_items_count(lenp, kBatchMinItem), prec == 2).total;
     } else {
       pb_batch_opts o{};
       if (opts) o = *opts;
@@ -728,7 +754,7 @@ extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const p
   if (o.item_channels < 0 || (o.item_channels && (o.item_channels % 64 || o.item_channels < kBatchMinItem)))
     return set_error(PB_EINVAL, "pb_batch_create: item_channels must be 0 or a multiple of 64 >= %d", kBatchMinItem);
   if (o.ctas_per_sm < 0 || o.ctas_per_sm > 4) return set_error(PB_EINVAL, "pb_batch_create: ctas_per_sm must be 0..4");
-  if (o.precision < 0 || o.precision > 1) return set_error(PB_EINVAL, "pb_batch: precision must be 0 or 1");
+  if (o.precision < 0 || o.precision > 2) return set_error(PB_EINVAL, "pb_batch: precision must be 0, 1 or 2");
   if (o.layout < 0 || o.layout > 1) return set_error(PB_EINVAL, "pb_batch: layout must be 0 or 1");
   cudaStream_t st = (cudaStream_t)stream;
   pb_batch *b = new (std::nothrow) pb_batch();
@@ -740,7 +766,7 @@ extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const p
     b->nchp = nchp;
     b->sm_count = sm;
     b->prec = o.precision;
-    b->lenp = b->prec == 1 ? batch_pair_lenp(chs, n) : batch_lenp(chs, n);
+    b->lenp = b->prec >= 1 ? batch_pair_lenp(chs, n) : batch_lenp(chs, n);
     b->nitems_cap = batch_items_count(b->lenp, kBatchMinItem);
     b->dense = batch_dense_for(chs, n, o);
     if (b->dense)
@@ -753,10 +779,10 @@ extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const p
       b->nch.push_back(chs[i]->nch);
       for (int64_t r = 0; r < chs[i]->nstate; ++r) b->row_inst.push_back(i);
     }
-    if (b->prec == 1) {
+    if (b->prec >= 1) {
       int64_t nent = 0;
       for (int64_t l : b->lenp) nent += l;
-      const BatchLayoutFF LF = batch_layout_ff(chs, n, ns, nent, b->nitems_cap);
+      const BatchLayoutFF LF = batch_layout_ff(chs, n, ns, nent, b->nitems_cap, b->prec == 2);
       if (bytes < LF.total) {
         delete b;
         return set_error(PB_ENOMEM, "pb_batch_create: arena of %zu bytes is smaller than the %zu needed", bytes,
@@ -770,6 +796,7 @@ extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const p
       b->item_ptr = (int32_t *)(A + LF.item_ptr);
       b->pA = (float2 *)(A + LF.pA);
       b->pB = (float2 *)(A + LF.pB);
+      if (b->prec == 2) b->pC = (float2 *)(A + LF.pC);
       b->pidx = (uint32_t *)(A + LF.pidx);
       b->Rg = (double *)(A + LF.Rg);
       b->yff = (float2 *)(A + LF.yff);
@@ -777,6 +804,13 @@ extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const p
       b->acc = (double *)(A + LF.acc);
       b->y = (double *)(A + LF.y);
       status = batch_setup_ff(b, chs, n, LF, st);
+      if (status == PB_OK && b->prec == 2 && nent > 0) {
+        dev::k_pairs_c32<<<(int)std::min<int64_t>((nent + 255) / 256, 8192), 256, 0, st>>>(b->pA, b->pB,
+                                                                                           (long long)nent, b->pC);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) status = cuda_fail(e, "k_pairs_c32 (batch)");
+      }
       if (status == PB_OK) {
         b->ctas = o.ctas_per_sm ? o.ctas_per_sm : 4;  // of 256 threads
         status = batch_upload_plan(b, o.item_channels ? o.item_channels : 2048, st);

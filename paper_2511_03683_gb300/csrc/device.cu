@@ -1690,6 +1690,23 @@ extern "C" int pb_transport_iterate(pb_dev *d, const double *vel3, const double 
   return PB_OK;
 }
 
+extern "C" int pb_transport_iterate_host(pb_dev *d, const double *vel3, const double *F3in_host, double *F3out_host,
+                                         double *resid3_host, void *stream) {
+  clear_error();
+  if (!d || !vel3 || !F3in_host || !F3out_host) return set_error(PB_EINVAL, "pb_transport_iterate_host: null argument");
+  if (!d->transport) return set_error(PB_EINVAL, "transport buffers were not reserved (pb_dev_opts.transport = 0)");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double) * 3 * (size_t)d->ns;
+  PB_CUDA(cudaMemcpyAsync(d->Fa, F3in_host, bytes, cudaMemcpyHostToDevice, st));
+  int rc;
+  if ((rc = to_ff(d, d->Fa, 3 * d->ns, d->Fff, st))) return rc;
+  if ((rc = transport_pass(d, d->Fff, vel3, d->Fa, d->Fb, d->Fff, st))) return rc;
+  PB_CUDA(cudaMemcpyAsync(F3out_host, d->Fb, bytes, cudaMemcpyDeviceToHost, st));
+  if (resid3_host) PB_CUDA(cudaMemcpyAsync(resid3_host, d->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  PB_CUDA(cudaStreamSynchronize(st));
+  return PB_OK;
+}
+
 extern "C" int pb_transport_map(pb_dev *d, const double *f0, const double *vel3, const double *F3in, double *F3out,
                                 void *stream) {
   clear_error();

@@ -79,6 +79,19 @@ __global__ void k_tiles_fill_c32(const int2 *__restrict__ tiles, int nt, const f
   }
 }
 
+// t(s, p) above from the entry's rounded (P_in, P_out) = (a, b) and the float-float occupations
+// fs of s and fp of p
+__device__ __forceinline__ float c32_term(float a, float b, float2 fs, float2 fp) {
+  const float d = __fsub_rn(a, b);
+  const float u = __fmul_rn(a, fp.x);
+  const float ex = __fmaf_rn(a, fp.x, -u);
+  const float v = __fmaf_rn(b, fs.x, -u);
+  const float w = __fmul_rn(fs.x, fp.x);
+  float t = __fmaf_rn(-d, w, __fsub_rn(ex, v));
+  t = __fmaf_rn(fp.y, __fmaf_rn(-fs.x, d, a), t);
+  return __fmaf_rn(-fs.y, __fmaf_rn(fp.x, d, b), t);
+}
+
 // reduce-scatter of NV floats over the 2 * TOP lanes that differ in lane bits log2 TOP .. 0: at
 // the end v[0] holds the total of value index idx(lane) = those bits of the lane, most
 // significant first (the float-float version is ff_reduce_scatter)
@@ -207,18 +220,12 @@ __global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32(const int2 *__r
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const float a = e[j].x, b = e[j].y, fp = fcol[j].x, flp = fcol[j].y;
-        const float d = __fsub_rn(a, b);
         if (MODE == MODE_COLL) {
-          const float u = __fmul_rn(a, fp);
-          const float ex = __fmaf_rn(a, fp, -u);
-          const float v = __fmaf_rn(b, fs.x, -u);
-          const float w = __fmul_rn(fs.x, fp);
-          float t = __fmaf_rn(-d, w, __fsub_rn(ex, v));
-          t = __fmaf_rn(flp, __fmaf_rn(-fs.x, d, a), t);
-          t = __fmaf_rn(-fs.y, __fmaf_rn(fp, d, b), t);
+          const float t = c32_term(a, b, fs, fcol[j]);
           rv[i] = __fadd_rn(rv[i], t);
           if (!diag) cv[j] = __fsub_rn(cv[j], t);
         } else {  // 1/tau summands: row s: P_out + f_p d; column p (reverse channel): P_in - f_s d
+          const float d = __fsub_rn(a, b);
           rv[i] = __fadd_rn(rv[i], __fmaf_rn(flp, d, __fmaf_rn(fp, d, b)));
           if (!diag) cv[j] = __fadd_rn(cv[j], __fmaf_rn(-fs.y, d, __fmaf_rn(-fs.x, d, a)));
         }
@@ -247,6 +254,65 @@ __global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32(const int2 *__r
         if (uses > 0) mbar_wait(bars + k, (unsigned)((uses - 1) & 1));
       }
     }
+  }
+}
+
+// The same FP32 pair coefficients as a row stream, for the batched rt-BTE (precision 2): entry
+// e of the branch-merged rows holds C[e] = rounded (P_in, P_out) of (row state, partner colp[e]);
+// one warp per item (a piece of one row), each lane two 4-entry groups per trip, partners'
+// float-float f gathered through L1; part[item].x = sum of t(s, p) over the item.
+template <typename IDX>
+__global__ void __launch_bounds__(kBlock) k_stream_c32_rows(const Item *__restrict__ items, int nitems,
+                                                            const float4 *__restrict__ C4,
+                                                            const IDX *__restrict__ colp,
+                                                            const float2 *__restrict__ fg,
+                                                            Part4 *__restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < nitems; it += nwarps) {
+    const Item I = items[it];
+    const long long g0 = I.start >> 2;
+    const int ng = I.len >> 2;
+    const float2 fs = fg[I.row];
+    float acc = 0.f, acc2 = 0.f;
+    int g = lane;
+    for (; g + 32 < ng; g += 64) {
+      const long long q0 = g0 + g, q1 = q0 + 32;
+      const uint4 c0 = partners4(colp, q0), c1 = partners4(colp, q1);
+      const float4 x0 = __ldcs(C4 + 2 * q0), y0 = __ldcs(C4 + 2 * q0 + 1);
+      const float4 x1 = __ldcs(C4 + 2 * q1), y1 = __ldcs(C4 + 2 * q1 + 1);
+      acc = __fadd_rn(acc, c32_term(x0.x, x0.y, fs, fg[c0.x]));
+      acc2 = __fadd_rn(acc2, c32_term(x1.x, x1.y, fs, fg[c1.x]));
+      acc = __fadd_rn(acc, c32_term(x0.z, x0.w, fs, fg[c0.y]));
+      acc2 = __fadd_rn(acc2, c32_term(x1.z, x1.w, fs, fg[c1.y]));
+      acc = __fadd_rn(acc, c32_term(y0.x, y0.y, fs, fg[c0.z]));
+      acc2 = __fadd_rn(acc2, c32_term(y1.x, y1.y, fs, fg[c1.z]));
+      acc = __fadd_rn(acc, c32_term(y0.z, y0.w, fs, fg[c0.w]));
+      acc2 = __fadd_rn(acc2, c32_term(y1.z, y1.w, fs, fg[c1.w]));
+    }
+    if (g < ng) {
+      const long long q0 = g0 + g;
+      const uint4 c0 = partners4(colp, q0);
+      const float4 x0 = __ldcs(C4 + 2 * q0), y0 = __ldcs(C4 + 2 * q0 + 1);
+      acc = __fadd_rn(acc, c32_term(x0.x, x0.y, fs, fg[c0.x]));
+      acc = __fadd_rn(acc, c32_term(x0.z, x0.w, fs, fg[c0.y]));
+      acc = __fadd_rn(acc, c32_term(y0.x, y0.y, fs, fg[c0.z]));
+      acc = __fadd_rn(acc, c32_term(y0.z, y0.w, fs, fg[c0.w]));
+    }
+    acc = __fadd_rn(acc, acc2);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(0xFFFFFFFFu, acc, o));
+    if (lane == 0) part[it] = make_part4((double)acc, 0.0, 0.0, 0.0);
+  }
+}
+
+// C[e] = rounded (P_in, P_out) of n branch-merged float-float entries (A = P_in, B = D)
+__global__ void k_pairs_c32(const float2 *__restrict__ A, const float2 *__restrict__ B, long long n,
+                            float2 *__restrict__ C) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double pin = ff_to_double(A[e].x, A[e].y);
+    C[e] = c32_round_pair(pin, pin + ff_to_double(B[e].x, B[e].y));
   }
 }
 

@@ -150,3 +150,81 @@ def test_ff_batch_autotune_keeps_results(pb, batch, batch_ff):
     assert item in (1024, 2048, 4096) and ctas in (2, 3, 4) and ms > 0
     after = batch_ff.collision(ft).cpu().numpy()
     assert np.abs(after - before).max() <= 1e-12 * np.abs(before).max()
+
+
+# ------------------------------------------------------------------ FP32 pair coefficients (precision "c32")
+
+@pytest.fixture(scope="module")
+def batch_c32(pb, batch):
+    inst, chs, _, f = batch
+    return pb.Batch(chs, precision="c32")
+
+
+def test_c32_batch_collision_matches_oracle(pb, batch, batch_c32):
+    """The branch-merged coefficients as FP32 pairs, net terms per entry: every instance's
+    df/dt within 1e-6 of its FP64 oracle (normwise; relative to the gross scattering where the
+    integral itself is dominated by cancellation)."""
+    import torch
+
+    inst, chs, _, _ = batch
+    b = batch_c32
+    fr = np.random.default_rng(23).uniform(0, 1, b.nstate)
+    I = b.collision(torch.tensor(fr, device="cuda")).cpu().numpy()
+    for i, ((m, _), ch) in enumerate(zip(inst, chs)):
+        a, e = b.offsets[i], b.offsets[i + 1]
+        ref, ab = oracle.Oracle(m).collision(fr[a:e], with_abs=True)
+        d = np.abs(I[a:e] - ref).max()
+        assert d <= 1e-6 * ab.max()
+        if np.abs(ref).max() >= 1e-2 * ab.max():
+            assert d <= 1e-6 * np.abs(ref).max()
+
+
+def test_c32_batch_rk4_matches_oracle(pb, batch, batch_c32):
+    import torch
+
+    inst, chs, _, f = batch
+    ft = torch.tensor(f, device="cuda")
+    batch_c32.rk4(ft, 1.0, 5)
+    got = ft.cpu().numpy()
+    for i, ((m, _), ch) in enumerate(zip(inst[:4], chs[:4])):
+        a, e = batch_c32.offsets[i], batch_c32.offsets[i + 1]
+        ref = oracle.Oracle(m).rk4(f[a:e], 1.0, 5)
+        assert np.abs(got[a:e] - ref).max() <= 1e-6 * np.abs(ref).max()
+
+
+_largest = {}
+
+
+def _largest_reference(m, e, fr, f, rows):
+    """Oracle df/dt on sampled rows and the 3-step trajectory of one instance (computed once)."""
+    key = m.name
+    if key not in _largest:
+        o = oracle.Oracle(m)
+        _largest[key] = (o.collision(fr, rows=rows, with_abs=True), o.rk4(f, 1.0, 3))
+    return _largest[key]
+
+
+@pytest.mark.parametrize("precision,tol,tol_gross", [("fp32", 1e-6, 1e-6), ("ff", 1e-12, 1e-13), ("c32", 1e-6, 1e-6)])
+def test_batch_largest_instances_sampled(pb, precision, tol, tol_gross):
+    """The 36^3 instances of the batched workload (the largest rows: 4 bands, 5 modes, and 2
+    bands, 6 modes), batched with a small one, against the oracle at the bounds of each
+    precision: df/dt at a random population on sampled rows (relative to the gross scattering)
+    and f after 3 RK4 steps from the hot population (normwise)."""
+    import torch
+
+    inst = [synth.make_batch_instance(i) for i in (38, 16, 0)]
+    chs = [pb.Channels.from_model(m) for m, _ in inst]
+    b = pb.Batch(chs, precision=precision)
+    fr = np.random.default_rng(29).uniform(0, 1, b.nstate)
+    I = b.collision(torch.tensor(fr, device="cuda")).cpu().numpy()
+    f = np.concatenate([m.f_hot(e_exc=e).reshape(-1)[c.state_ids()] for (m, e), c in zip(inst, chs)])
+    ft = torch.tensor(f, device="cuda")
+    b.rk4(ft, 1.0, 3)
+    got = ft.cpu().numpy()
+    for i, ((m, e), ch) in enumerate(zip(inst, chs)):
+        a, z = b.offsets[i], b.offsets[i + 1]
+        rows = np.unique(np.concatenate([np.arange(0, ch.nstate, 41), [ch.nstate - 1]]))
+        (ref, ab), fref = _largest_reference(m, e, fr[a:z], f[a:z], rows)
+        d = np.abs(I[a:z][rows] - ref).max()
+        assert d <= tol_gross * ab.max(), f"instance {i}: {d / ab.max():.2e} of the gross scattering"
+        assert np.abs(got[a:z] - fref).max() <= tol * np.abs(fref).max()

@@ -325,6 +325,14 @@ def test_transport_map_and_solve(pb):
     Fin = np.random.default_rng(5).normal(size=(o.nstate, 3))
     ref, _ = o.transport_map(f0, v, Fin)
     assert nrel(dev.transport_map(T(f0), T(v), T(Fin)).cpu().numpy(), ref) <= TOL
+    # the host-buffer pass with the same weights gives the same iterate bit for bit, and its
+    # residual numbers are those of the device pass
+    dev_out = dev.transport_iterate(T(v), T(Fin))
+    res_host = np.zeros(3)
+    host_out = dev.transport_iterate_host(T(v), Fin, resid=res_host)
+    assert np.array_equal(host_out, dev_out.cpu().numpy())
+    d = np.abs(host_out - Fin).max()
+    assert res_host[1] == d and res_host[2] == np.abs(host_out).max() and res_host[0] == d / res_host[2]
     F, iters, res, ok = dev.transport(T(f0), T(v), tol=1e-12, maxit=3000)
     Fr, iters_r, res_r, ok_r = o.transport(f0, v, tol=1e-12, maxit=3000)
     assert ok and ok_r and abs(iters - iters_r) <= 1
