@@ -159,7 +159,7 @@ def function_source(text: str, name: str) -> str:
 HOT_FUNCTIONS = ("ff_split", "ff_to_double", "ff_mac", "ff_mac_lazy", "ff_add", "warp_sum", "partners4", "group_f",
                  "k_stream_ff", "k_stream_sym", "ff_prod", "ff_reduce_scatter",
                  "sym_columns_out", "mbar_init", "mbar_expect_tx", "mbar_try_wait", "mbar_wait", "bulk_g2s",
-                 "fence_proxy_async", "k_stream_sym_bulk")
+                 "fence_proxy_async", "k_stream_sym_bulk", "half_smem", "k_stream_sym_half")
 
 
 def kernel_source_hash(names=HOT_FUNCTIONS) -> str:

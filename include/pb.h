@@ -161,7 +161,7 @@ void pb_channels_free(pb_channels *ch);
  *                     exact by an FMA, plus first-order terms in the low part of the float-float
  *                     f; FP64 for the per-state combination and the RK4 update.  df/dt within
  *                     about 1e-6 of Eq. 2 (normwise).  Needs complete rows (no cutoffs), branch
- *                     merging and tile_sweep 0/2 (PB_EINVAL otherwise).  Transport, the
+ *                     merging and tile_sweep 0 or 2..6 (PB_EINVAL otherwise).  Transport, the
  *                     no-allocation call and, after pb_dev_set_g2, every sweep run the FF rows;
  *                     the adjoint calls return PB_EINVAL. */
 enum { PB_VARIANT_FF = 0, PB_VARIANT_F64 = 1, PB_VARIANT_LITERAL = 2, PB_VARIANT_G32 = 3, PB_VARIANT_G16 = 4,
@@ -202,11 +202,16 @@ typedef struct pb_dev_opts {
                                 each tile to its rows and, through the reverse channels (P_in(p,s) =
                                 P_out(s,p)), to its columns: about 8 bytes per state pair; 2 always stream
                                 the index */
-  int32_t tile_sweep;        /* the symmetric tile sweep (dense_rows 3): 0 automatic (= 2); 1 each thread
+  int32_t tile_sweep;        /* the symmetric tile sweep (dense_rows 3): 0 automatic (= 3); 1 each thread
                                 loads its 4 x 4 entries of a tile from global memory (3 CTAs per SM);
                                 2 one persistent CTA per SM with 256 threads keeps three tiles in flight in
                                 shared memory through TMA bulk copies (cp.async.bulk, mbarrier-counted),
-                                its bounded waits reporting through pb_dev_check */
+                                its bounded waits reporting through pb_dev_check; 3 the same ring in
+                                half-tiles (32 x 64 entries, 32 KB), the column sums of a tile carried in
+                                registers across its two halves: two stages per CTA and three CTAs per SM
+                                (ctas_per_sm 2: three stages, two CTAs).  PB_VARIANT_C32: 0 or 2 its
+                                default launch shape (two stages, three CTAs per SM), 3..6 other shapes
+                                (3 x 2, 2 x 2, 4 x 1, 6 x 1 stages x CTAs) */
   int32_t adjoint;           /* 1: reserve the accumulators of the deferred |g|^2 gradient
                                 (pb_rtbte_rk4_vjp_defer): FF with branch merging, one float-float
                                 (u, v) per stored state pair (16 bytes); G32/G16/H16, three doubles per

@@ -2307,6 +2307,176 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_stream_sym_bulk(const int2 *
   }
 }
 
+// The same float-float tile sweep in half-tiles: the unit of staging is 32 rows x 64 columns of a
+// tile (32 KB, contiguous in the tile's row-major layout), so a CTA of 256 threads holds three
+// units in shared memory and two CTAs fit on an SM (16 warps, each CTA with its own barrier).
+// A CTA takes both halves of each of its tiles in turn: rows are complete within a half (one
+// float-float (A, C) partial per row and partner block, as above); the column sums of a tile
+// stay in registers across its two halves and go to the per-warp table after the second, and
+// the table is combined after the next unit's barrier.  Columns are written only every other
+// unit, so one table suffices.  Thread (ti, tj) takes rows 2 ti, 2 ti + 1 of the half and
+// columns tj, tj + 16, tj + 32, tj + 48.
+constexpr unsigned kHalfTileBytes = kTileBytes / 2;
+constexpr unsigned kHalfStageBytes = kHalfTileBytes + (kTile / 2 + kTile) * sizeof(float2);
+template <int NST>
+constexpr size_t half_smem() {
+  return (size_t)NST * kHalfStageBytes + 64 + kSymColBytes;
+}
+
+// NST stages per CTA, CPS resident CTAs per SM (3 x 2 or 2 x 3 fit in the SM's shared memory)
+template <int NST, int CPS>
+__global__ void __launch_bounds__(kSymThreads, CPS) k_stream_sym_half(const int2 *__restrict__ tiles, int nt,
+                                                                       const float4 *__restrict__ tc,
+                                                                       const float2 *__restrict__ fg, int ns, int nb,
+                                                                       float4 *__restrict__ tp, int *__restrict__ err) {
+  constexpr int kHalfStages = NST;
+  static_assert(NST >= 2 && NST <= 4, "the ring needs 2..4 stages");
+  constexpr int R = 2, NV = 2 * R, HR = kTile / 2;
+  extern __shared__ __align__(128) unsigned char ssm[];
+  unsigned long long *bars = (unsigned long long *)(ssm + kHalfStages * kHalfStageBytes);
+  int2 *stile = (int2 *)(bars + kHalfStages);  // the tile of each stage's unit
+  float2 *colred = (float2 *)(ssm + kHalfStages * kHalfStageBytes + 64);  // [8 warps][A | C][64 columns]
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, tj = tid & 15, ti = tid >> 4;
+  const int G = (int)gridDim.x;
+  const int nloc = (int)blockIdx.x < nt ? (nt - 1 - (int)blockIdx.x) / G + 1 : 0;
+  const int nunit = 2 * nloc;
+  for (int i = tid; i < kHalfStages * (HR + kTile); i += kSymThreads) {
+    float2 *fz = (float2 *)(ssm + (i / (HR + kTile)) * kHalfStageBytes + kHalfTileBytes);
+    fz[i % (HR + kTile)] = make_float2(0.f, 0.f);
+  }
+  if (tid == 0) {
+    for (int k = 0; k < kHalfStages; ++k) mbar_init(bars + k, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_proxy_async();
+  __syncthreads();
+  // thread 0: units are issued in order; issIJ is the tile being issued, aheadIJ the next one
+  int issued = 0;
+  int2 issIJ = make_int2(0, 0), aheadIJ = make_int2(0, 0);
+  if (tid == 0 && nloc > 0) {
+    issIJ = tiles[blockIdx.x];
+    if (nloc > 1) aheadIJ = tiles[(int)blockIdx.x + G];
+  }
+  auto issue = [&](int v) {  // unit v = 2 k + h: half h of the CTA's tile k
+    const int k = v >> 1, h = v & 1, s = v % kHalfStages;
+    if (h == 0 && k > 0) {
+      issIJ = aheadIJ;
+      if (k + 1 < nloc) aheadIJ = tiles[(int)blockIdx.x + (k + 1) * G];
+    }
+    const int t = (int)blockIdx.x + k * G;
+    stile[s] = issIJ;
+    unsigned char *buf = ssm + (size_t)s * kHalfStageBytes;
+    const int nr = min(HR, ns - (issIJ.x * kTile + h * HR)), nc = min(kTile, ns - issIJ.y * kTile);
+    const unsigned br = nr > 0 ? (unsigned)(nr * sizeof(float2) + 15) / 16 * 16 : 0u;
+    const unsigned bc = (unsigned)(nc * sizeof(float2) + 15) / 16 * 16;
+    mbar_expect_tx(bars + s, kHalfTileBytes + br + bc);
+    const unsigned char *src = (const unsigned char *)(tc + (size_t)t * kTile * kTile) + (size_t)h * kHalfTileBytes;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) bulk_g2s(buf + q * (kHalfTileBytes / 2), src + q * (kHalfTileBytes / 2), kHalfTileBytes / 2, bars + s);
+    if (br) bulk_g2s(buf + kHalfTileBytes, fg + (size_t)issIJ.x * kTile + h * HR, br, bars + s);
+    bulk_g2s(buf + kHalfTileBytes + HR * sizeof(float2), fg + (size_t)issIJ.y * kTile, bc, bars + s);
+  };
+  if (tid == 0)
+    for (; issued < kHalfStages && issued < nunit; ++issued) issue(issued);
+  int2 prevIJ = make_int2(0, 0);  // the tile of the previous unit
+  bool ok = true;
+  float cA[4][2], cC[4][2];  // column sums of the current tile, carried across its halves
+  for (int u = 0; u <= nunit; ++u) {
+    const bool have = u < nunit;
+    if (!__syncthreads_and(tid == 0 && have ? mbar_wait(bars + u % kHalfStages, (unsigned)((u / kHalfStages) & 1))
+                                            : true)) {
+      ok = false;
+      break;
+    }
+    if (tid == 0 && u >= 1 && issued < nunit) {
+      fence_proxy_async();  // the generic reads of unit u-1's stage before its refill
+      issue(issued);
+      ++issued;
+    }
+    // the previous tile's column table (written after its second half) is complete
+    if ((u & 1) == 0 && u >= 2 && prevIJ.x != prevIJ.y) sym_columns_out(colred, prevIJ, nb, lane, wid, tp);
+    if (!have) break;
+    const int s = u % kHalfStages, h = u & 1;
+    const int2 IJ = stile[s];
+    prevIJ = IJ;
+    const bool diag = IJ.x == IJ.y;
+    const float4 *__restrict__ T = (const float4 *)(ssm + (size_t)s * kHalfStageBytes);
+    const float2 *__restrict__ fr = (const float2 *)(ssm + (size_t)s * kHalfStageBytes + kHalfTileBytes);
+    const float2 *__restrict__ fc = fr + HR;
+    float2 fcol[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) fcol[j] = fc[tj + 16 * j];
+    float rA[R][2], rC[R][2];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int row = ti * R + i;
+      const float2 fs = fr[row];
+      float4 e[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) e[j] = T[row * kTile + tj + 16 * j];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (j == 0) {
+          ff_prod(rA[i][0], rA[i][1], fcol[j], e[j].x, e[j].y);
+          ff_prod(rC[i][0], rC[i][1], fcol[j], e[j].z, e[j].w);
+        } else {
+          ff_mac_lazy(rA[i][0], rA[i][1], fcol[j], e[j].x, e[j].y);
+          ff_mac_lazy(rC[i][0], rC[i][1], fcol[j], e[j].z, e[j].w);
+        }
+        if (!diag) {
+          if (h == 0 && i == 0) {
+            ff_prod(cA[j][0], cA[j][1], fs, e[j].z, e[j].w);
+            ff_prod(cC[j][0], cC[j][1], fs, e[j].x, e[j].y);
+          } else {
+            ff_mac_lazy(cA[j][0], cA[j][1], fs, e[j].z, e[j].w);
+            ff_mac_lazy(cC[j][0], cC[j][1], fs, e[j].x, e[j].y);
+          }
+        }
+      }
+    }
+    // rows: the 16 lanes of a half-warp share them; lanes 4m .. 4m + 3 end with value m = (row, A | C)
+    {
+      float2 v[NV];
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        v[2 * i] = make_float2(rA[i][0], rA[i][1]);
+        v[2 * i + 1] = make_float2(rC[i][0], rC[i][1]);
+      }
+      ff_reduce_scatter<NV, 8>(v, lane);
+      const int idx = tj >> 2;
+      if ((tj & 3) == 0) {
+        const int row = IJ.x * kTile + h * HR + ti * R + (idx >> 1);
+        ((float2 *)tp)[2 * ((long long)row * nb + IJ.y) + (idx & 1)] = v[0];
+      }
+    }
+    if (!diag && h == 1) {
+      // columns of the whole tile: lanes tj and tj + 16 share them (one level), then the warps
+      // (after the next unit's barrier)
+      const bool up = lane & 16;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int jk = m >> 1, jo = jk + 2;  // kept / sent column slot
+        const float2 a = (m & 1) ? make_float2(cC[jk][0], cC[jk][1]) : make_float2(cA[jk][0], cA[jk][1]);
+        const float2 c = (m & 1) ? make_float2(cC[jo][0], cC[jo][1]) : make_float2(cA[jo][0], cA[jo][1]);
+        const float2 send = up ? a : c, keep = up ? c : a;
+        const float2 w = ff_add(keep, make_float2(__shfl_xor_sync(0xFFFFFFFFu, send.x, 16),
+                                                  __shfl_xor_sync(0xFFFFFFFFu, send.y, 16)));
+        const int col = tj + 16 * ((up ? 2 : 0) + jk);
+        colred[(wid * 2 + (m & 1)) * kTile + col] = w;
+      }
+    }
+  }
+  if (!ok) {
+    *err = 2;
+    if (tid == 0) {  // drain: wait (bounded) for every copy this CTA issued
+      for (int k = 0; k < kHalfStages; ++k) {
+        const int uses = issued / kHalfStages + (k < issued % kHalfStages ? 1 : 0);
+        if (uses > 0) mbar_wait(bars + k, (unsigned)((uses - 1) & 1));
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------ finalisers
 
 // Row totals of the (A, B) partials (coefficient variants) or of the literal sums.

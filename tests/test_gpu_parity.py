@@ -241,12 +241,14 @@ def test_branch_merged_and_per_channel_sweeps(pb, name, variant, merge, dense):
             assert dev.bytes_per_channel < other_rows.bytes_per_channel
 
 
-@pytest.mark.parametrize("tile_sweep", [1, 2], ids=["global-loads", "bulk-copies"])
+@pytest.mark.parametrize("tile_sweep", [1, 2, 3], ids=["global-loads", "bulk-copies", "half-tiles"])
 @pytest.mark.parametrize("name", ["odd81", "odd99", "win16", "tiny8"])
 def test_tile_sweep_shapes(pb, name, tile_sweep):
-    """The symmetric tile sweep with per-thread global loads and with the TMA bulk-copy ring:
-    collision, rates and RK4 against the oracle on complete rows whose
-    last 64-state block is ragged (odd for odd81 / odd99); the shapes agree to rounding."""
+    """The symmetric tile sweep with per-thread global loads, with the TMA bulk-copy ring of
+    whole tiles and with the ring of half-tiles (two CTAs per SM): collision, rates and RK4
+    against the oracle on complete rows whose last 64-state block is ragged (odd for odd81 /
+    odd99; for odd81 the second half of the last block holds no state); the shapes agree to
+    rounding."""
     m = SMALL[name]()
     o = oracle.Oracle(m)
     ch = pb.Channels.from_model(m)
@@ -266,15 +268,16 @@ def test_tile_sweep_shapes(pb, name, tile_sweep):
     assert np.abs(other.collision(T(f)).cpu().numpy() - I).max() <= MUTUAL * ab.max()
 
 
+@pytest.mark.parametrize("tile_sweep", [2, 3])
 @pytest.mark.parametrize("name", ["odd81", "win16"])
-def test_tile_sweep_signed_inputs(pb, name):
-    """The bulk-copy tile sweep with occupations of both signs (outside the physical [0, 1]:
+def test_tile_sweep_signed_inputs(pb, name, tile_sweep):
+    """The bulk-copy tile sweeps with occupations of both signs (outside the physical [0, 1]:
     products and partial sums of either sign in the float-float tile sums) and with their
     absolute values, against the oracle."""
     m = SMALL[name]()
     o = oracle.Oracle(m)
     ch = pb.Channels.from_model(m)
-    dev = pb.Device(ch, tile_sweep=2)
+    dev = pb.Device(ch, tile_sweep=tile_sweep)
     rng = np.random.default_rng(35)
     f = rng.uniform(0, 1, o.nstate)
     f[rng.choice(o.nstate, size=o.nstate // 10, replace=False)] *= -0.5
@@ -683,11 +686,11 @@ def test_full_size_bulk_copy_sweep(pb, big):
     bulk.check()
 
 
-def test_full_size_tile_sweep_shapes(pb, big):
-    """The global-load tile sweep at 40^3 against the full oracle and the default bulk-copy
-    ring (2850 tiles, about 19 per CTA of the persistent ring, so every stage is refilled many
-    times); no bounded wait gave up."""
-    tile_sweep = 1
+@pytest.mark.parametrize("tile_sweep", [1, 2, 3])
+def test_full_size_tile_sweep_shapes(pb, big, tile_sweep):
+    """Every tile sweep at 40^3 against the full oracle and the default (2850 tiles, about 19
+    per CTA of the persistent rings, so every stage is refilled many times); no bounded wait
+    gave up."""
     m, o, dev = big
     alt = pb.Device(dev.channels, variant="ff", tile_sweep=tile_sweep)
     f = o.window_values(m.f_hot())
