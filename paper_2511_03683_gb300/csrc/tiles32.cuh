@@ -317,14 +317,15 @@ __global__ void k_pairs_c32(const float2 *__restrict__ A, const float2 *__restri
 }
 
 // Epilogue of the C32 sweep: a 256-thread CTA takes SPC states; each warp adds the block
-// partials of SPC / 8 states (lanes over the blocks, float-float, then a 32-lane butterfly), and
-// warp 0 applies the prefactor and the RK4 stage arithmetic in FP64, one lane per state.
+// partials of SPC / 8 states (lanes over the blocks in float-float, then one 32-lane float-float
+// reduce-scatter of the SPC / 8 values), and warp 0 applies the prefactor and the RK4 stage
+// arithmetic in FP64, one lane per state.
 template <int STAGE, bool RATE = false, int SPC = 32>
 __global__ void __launch_bounds__(256) k_fin_c32(const float *__restrict__ tp, int nb, int nsp, int ns, double c,
                                                  const double *__restrict__ ysrc, double *__restrict__ out,
                                                  double *__restrict__ f, double *__restrict__ acc,
                                                  double *__restrict__ y, float2 *__restrict__ yff, double dt) {
-  constexpr int SPW = SPC / 8;
+  constexpr int SPW = SPC / 8, LPV = 32 / SPW;  // states per warp, lanes per state after the reduce-scatter
   __shared__ float2 tot[SPC];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int base = blockIdx.x * SPC;
@@ -334,19 +335,18 @@ __global__ void __launch_bounds__(256) k_fin_c32(const float *__restrict__ tp, i
     if (STAGE >= 0) in.f = f[r0];
     if (STAGE >= 1) in.acc = acc[r0];
   }
+  float2 v[SPW];
 #pragma unroll
   for (int q = 0; q < SPW; ++q) {
     const int r = base + SPW * wid + q;
-    float2 N = make_float2(0.f, 0.f);
+    v[q] = make_float2(0.f, 0.f);
     if (r < nsp) {
       const float *__restrict__ row = tp + (long long)r * nb;
-      for (int k = lane; k < nb; k += 32) N = ff_add(N, make_float2(row[k], 0.f));
+      for (int k = lane; k < nb; k += 32) v[q] = ff_add(v[q], make_float2(row[k], 0.f));
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-      N = ff_add(N, make_float2(__shfl_xor_sync(0xFFFFFFFFu, N.x, o), __shfl_xor_sync(0xFFFFFFFFu, N.y, o)));
-    if (lane == 0) tot[SPW * wid + q] = N;
   }
+  ff_reduce_scatter<SPW, 16>(v, lane);
+  if ((lane & (LPV - 1)) == 0) tot[SPW * wid + lane / LPV] = v[0];
   __syncthreads();
   if (wid != 0 || lane >= SPC || r0 >= ns) return;
   const float2 Tt = tot[lane];

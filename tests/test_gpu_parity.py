@@ -733,6 +733,43 @@ def test_full_size_1000_steps_two_arithmetics(pb, big):
     assert (e * fa).sum() < (e * f0).sum()
 
 
+def _trajectory_fixture(name):
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", f"trajectory_{name}.txt")
+    return np.loadtxt(path, ndmin=2)
+
+
+@pytest.mark.parametrize("variant,tol", [("ff", TOL), ("c32", C32_TOL)])
+def test_1000_step_trajectory_against_the_oracle(pb, variant, tol):
+    """The rt-BTE workload on the 24^3 grids (1028 states, 6.3e6 channels): 1000 classic RK4
+    steps of 1 fs from the hot population, against the oracle's own trajectory
+    (tests/golden/trajectory_window24.txt, written by the oracle alone) after 250, 500, 750 and
+    1000 steps: normwise 1e-12 for the FP64-accurate default, 1e-6 for the FP32 coefficient
+    tiles."""
+    m = synth.make_config("window24")
+    ch = pb.Channels.from_model(m)
+    dev = pb.Device(ch, variant=variant)
+    ref = _trajectory_fixture("window24")
+    f = T(m.f_hot().reshape(-1)[ch.state_ids()])
+    for k in range(ref.shape[1]):
+        dev.rk4(f, 1.0, 250)
+        err = nrel(f.cpu().numpy(), ref[:, k])
+        print(f"{variant}: step {250 * (k + 1)}: normwise error {err:.2e}")
+        assert err <= tol
+    dev.check()
+
+
+def test_full_size_50_steps_against_the_oracle(big):
+    """The 40^3 workload: 50 RK4 steps of 1 fs against the oracle's trajectory
+    (tests/golden/trajectory_window40.txt) at 1e-12 normwise."""
+    m, o, dev = big
+    ref = _trajectory_fixture("window40")[:, 0]
+    f = T(o.window_values(m.f_hot()))
+    dev.rk4(f, 1.0, 50)
+    assert nrel(f.cpu().numpy(), ref) <= TOL
+
+
 def test_full_size_transport_solve_matches_oracle(pb, big):
     """pb_iter_transport on the 40^3 workload for x, y, z to 1e-10 against the oracle's own
     iteration: same iteration count (+-1), conductivity-like tensor and isotropy."""
