@@ -371,6 +371,12 @@ def test_single_state(pb):
     assert abs(dev.rates(T([0.4])).cpu().numpy()[0] - ref) <= 1e-13 * ref
     # the self channel's in- and out-scattering cancel
     assert abs(dev.collision(T([0.4])).cpu().numpy()[0]) <= 1e-13 * 0.4 * ref
+    # the FP32 coefficient tiles: one diagonal tile with one state; the self pair's two FP32
+    # coefficients are equal, so its net term and its first-order terms vanish exactly
+    d32 = pb.Device(ch, variant="c32")
+    assert abs(d32.rates(T([0.4])).cpu().numpy()[0] - ref) <= 1e-6 * ref
+    assert d32.collision(T([0.4])).cpu().numpy()[0] == 0.0
+    d32.check()
 
 
 # ------------------------------------------------------------------ mixed precision
