@@ -211,7 +211,8 @@ typedef struct pb_dev_opts {
                                 registers across its two halves: two stages per CTA and three CTAs per SM
                                 (ctas_per_sm 2: three stages, two CTAs).  PB_VARIANT_C32: 0 or 2 its
                                 default launch shape (two stages, three CTAs per SM), 3..6 other shapes
-                                (3 x 2, 2 x 2, 4 x 1, 6 x 1 stages x CTAs) */
+                                (3 x 2, 2 x 2, 4 x 1, 6 x 1 stages x CTAs), 7 and 8 half-tiles
+                                (3 x 4, 4 x 3) */
   int32_t adjoint;           /* 1: reserve the accumulators of the deferred |g|^2 gradient
                                 (pb_rtbte_rk4_vjp_defer): FF with branch merging, one float-float
                                 (u, v) per stored state pair (16 bytes); G32/G16/H16, three doubles per

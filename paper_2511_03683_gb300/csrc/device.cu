@@ -27,15 +27,20 @@ constexpr size_t kAlign = 256;
 constexpr int kFinBlock = 256;
 // launch shapes of the FP32 tile sweep (pb_dev_opts.tile_sweep 2..6): stages per CTA and
 // resident CTAs per SM
+// (7, 8: half-tiles)
 template <typename F>
 void with_c32_shape(int shape, F &&fn) {
   using std::integral_constant;
+  using std::false_type;
+  using std::true_type;
   switch (shape) {
-    case 3: fn(integral_constant<int, 3>(), integral_constant<int, 2>()); break;
-    case 4: fn(integral_constant<int, 2>(), integral_constant<int, 2>()); break;
-    case 5: fn(integral_constant<int, 4>(), integral_constant<int, 1>()); break;
-    case 6: fn(integral_constant<int, 6>(), integral_constant<int, 1>()); break;
-    default: fn(integral_constant<int, 2>(), integral_constant<int, 3>()); break;
+    case 3: fn(integral_constant<int, 3>(), integral_constant<int, 2>(), false_type()); break;
+    case 4: fn(integral_constant<int, 2>(), integral_constant<int, 2>(), false_type()); break;
+    case 5: fn(integral_constant<int, 4>(), integral_constant<int, 1>(), false_type()); break;
+    case 6: fn(integral_constant<int, 6>(), integral_constant<int, 1>(), false_type()); break;
+    case 7: fn(integral_constant<int, 3>(), integral_constant<int, 4>(), true_type()); break;
+    case 8: fn(integral_constant<int, 4>(), integral_constant<int, 3>(), true_type()); break;
+    default: fn(integral_constant<int, 2>(), integral_constant<int, 3>(), false_type()); break;
   }
 }
 
@@ -537,8 +542,8 @@ int resolve_opts(const pb_channels *ch, const pb_dev_opts *opts, int sm_count, p
     return set_error(PB_EINVAL, "pb_dev: variant %d is not available in this build", d.variant);
   if (d.merge_branches < 0 || d.merge_branches > 2) return set_error(PB_EINVAL, "pb_dev: merge_branches must be 0..2");
   if (d.dense_rows < 0 || d.dense_rows > 3) return set_error(PB_EINVAL, "pb_dev: dense_rows must be 0..3");
-  if (d.tile_sweep < 0 || d.tile_sweep > 6 || (d.tile_sweep > 3 && d.variant != PB_VARIANT_C32))
-    return set_error(PB_EINVAL, "pb_dev: tile_sweep must be 0..3 (0..6 for the FP32 coefficient tiles)");
+  if (d.tile_sweep < 0 || d.tile_sweep > 8 || (d.tile_sweep > 3 && d.variant != PB_VARIANT_C32))
+    return set_error(PB_EINVAL, "pb_dev: tile_sweep must be 0..3 (0..8 for the FP32 coefficient tiles)");
   if (d.adjoint < 0 || d.adjoint > 1) return set_error(PB_EINVAL, "pb_dev: adjoint must be 0 or 1");
   // automatic: the half-tile ring (measured 38.8 us per 40^3 sweep against 42.6 us for whole tiles);
   // for C32 its own default shape
@@ -1166,11 +1171,17 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
     }
   }
   if (d->c32)
-    with_c32_shape(d->c32_shape, [&](auto nst, auto cps) {
+    with_c32_shape(d->c32_shape, [&](auto nst, auto cps, auto half) {
       const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-      const int sm32 = (int)dev::c32_smem<nst()>();
-      cudaFuncSetAttribute(dev::k_stream_c32<dev::MODE_COLL, nst(), cps()>, A, sm32);
-      cudaFuncSetAttribute(dev::k_stream_c32<dev::MODE_RATE, nst(), cps()>, A, sm32);
+      if constexpr (decltype(half)::value) {
+        const int sm32 = (int)dev::c32_half_smem<nst()>();
+        cudaFuncSetAttribute(dev::k_stream_c32_half<dev::MODE_COLL, nst(), cps()>, A, sm32);
+        cudaFuncSetAttribute(dev::k_stream_c32_half<dev::MODE_RATE, nst(), cps()>, A, sm32);
+      } else {
+        const int sm32 = (int)dev::c32_smem<nst()>();
+        cudaFuncSetAttribute(dev::k_stream_c32<dev::MODE_COLL, nst(), cps()>, A, sm32);
+        cudaFuncSetAttribute(dev::k_stream_c32<dev::MODE_RATE, nst(), cps()>, A, sm32);
+      }
     });
   if (d->smem_f > 48 * 1024) {
     set_stream_smem<uint32_t>((int)d->smem_f);
@@ -1319,15 +1330,25 @@ int launch_stream_t(pb_dev *d, int mode, const double *fd, const float2 *fff, co
   } else if (d->variant == PB_VARIANT_FF && d->sym && d->c32 && part == d->part && fff == d->yff) {
     // FP32 coefficient tiles through the bulk-copy ring (tiles32.cuh)
     float *tp = (float *)d->tpart;
-    with_c32_shape(d->c32_shape, [&](auto nst, auto cps) {
+    with_c32_shape(d->c32_shape, [&](auto nst, auto cps, auto half) {
       const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(d->td.nt, (int64_t)d->sm_count * cps()));
-      const size_t sm32 = dev::c32_smem<nst()>();
-      if (coll)
-        dev::k_stream_c32<dev::MODE_COLL, nst(), cps()><<<gs, dev::kC32Threads, sm32, st>>>(
-            d->tiles, d->td.nt, d->tc32, fff, ns, d->td.nb, tp, d->err);
-      else
-        dev::k_stream_c32<dev::MODE_RATE, nst(), cps()><<<gs, dev::kC32Threads, sm32, st>>>(
-            d->tiles, d->td.nt, d->tc32, fff, ns, d->td.nb, tp, d->err);
+      if constexpr (decltype(half)::value) {
+        const size_t sm32 = dev::c32_half_smem<nst()>();
+        if (coll)
+          dev::k_stream_c32_half<dev::MODE_COLL, nst(), cps()><<<gs, dev::kC32Threads, sm32, st>>>(
+              d->tiles, d->td.nt, d->tc32, fff, ns, d->td.nb, tp, d->err);
+        else
+          dev::k_stream_c32_half<dev::MODE_RATE, nst(), cps()><<<gs, dev::kC32Threads, sm32, st>>>(
+              d->tiles, d->td.nt, d->tc32, fff, ns, d->td.nb, tp, d->err);
+      } else {
+        const size_t sm32 = dev::c32_smem<nst()>();
+        if (coll)
+          dev::k_stream_c32<dev::MODE_COLL, nst(), cps()><<<gs, dev::kC32Threads, sm32, st>>>(
+              d->tiles, d->td.nt, d->tc32, fff, ns, d->td.nb, tp, d->err);
+        else
+          dev::k_stream_c32<dev::MODE_RATE, nst(), cps()><<<gs, dev::kC32Threads, sm32, st>>>(
+              d->tiles, d->td.nt, d->tc32, fff, ns, d->td.nb, tp, d->err);
+      }
     });
   } else if (d->variant == PB_VARIANT_FF && d->sym && !d->c32 && part == d->part) {
     // symmetric tiles; the rate mode needs the same (A, B) partials

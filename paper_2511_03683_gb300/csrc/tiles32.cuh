@@ -257,6 +257,149 @@ __global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32(const int2 *__r
   }
 }
 
+// The same sweep in half-tiles (32 rows x 64 columns, 16 KB, contiguous in the tile): a tile's
+// column sums stay in registers across its two halves and go through the per-warp table after the
+// second, which is combined after the next unit's barrier (columns are written only every other
+// unit, so one table suffices).  Three 17 KB stages and the 2 KB table take 53 KB, so four CTAs
+// (32 warps) fit on an SM.  Thread (ti, tj) takes rows 2 ti, 2 ti + 1 of the unit and columns
+// tj + 16 j.
+constexpr unsigned kC32HalfBytes = kC32TileBytes / 2;
+constexpr unsigned kC32HalfStageBytes = kC32HalfBytes + (kTile / 2 + kTile) * sizeof(float2);
+template <int NST>
+constexpr size_t c32_half_smem() {
+  return (size_t)NST * kC32HalfStageBytes + 128 + kC32ColFloats * sizeof(float);
+}
+
+template <int MODE, int NST, int CPS>
+__global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32_half(const int2 *__restrict__ tiles, int nt,
+                                                                       const float2 *__restrict__ tc,
+                                                                       const float2 *__restrict__ fg, int ns, int nb,
+                                                                       float *__restrict__ tp, int *__restrict__ err) {
+  static_assert(NST >= 2 && NST <= 8, "the ring needs 2..8 stages");
+  constexpr int R = 2, HR = kTile / 2;
+  extern __shared__ __align__(128) unsigned char ssm[];
+  unsigned long long *bars = (unsigned long long *)(ssm + NST * kC32HalfStageBytes);
+  int2 *stile = (int2 *)(bars + NST);
+  float *colred = (float *)(ssm + NST * kC32HalfStageBytes + 128);  // [8 warps][64 columns]
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, tj = tid & 15, ti = tid >> 4;
+  const int G = (int)gridDim.x;
+  const int nloc = (int)blockIdx.x < nt ? (nt - 1 - (int)blockIdx.x) / G + 1 : 0;
+  const int nunit = 2 * nloc;
+  for (int i = tid; i < NST * (HR + kTile); i += kC32Threads) {
+    float2 *fz = (float2 *)(ssm + (i / (HR + kTile)) * kC32HalfStageBytes + kC32HalfBytes);
+    fz[i % (HR + kTile)] = make_float2(0.f, 0.f);
+  }
+  if (tid == 0) {
+    for (int k = 0; k < NST; ++k) mbar_init(bars + k, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_proxy_async();
+  __syncthreads();
+  int issued = 0;
+  int2 issIJ = make_int2(0, 0), aheadIJ = make_int2(0, 0);
+  if (tid == 0 && nloc > 0) {
+    issIJ = tiles[blockIdx.x];
+    if (nloc > 1) aheadIJ = tiles[(int)blockIdx.x + G];
+  }
+  auto issue = [&](int v) {  // unit v = 2 k + h: half h of the CTA's tile k
+    const int k = v >> 1, h = v & 1, s = v % NST;
+    if (h == 0 && k > 0) {
+      issIJ = aheadIJ;
+      if (k + 1 < nloc) aheadIJ = tiles[(int)blockIdx.x + (k + 1) * G];
+    }
+    const int t = (int)blockIdx.x + k * G;
+    stile[s] = issIJ;
+    unsigned char *buf = ssm + (size_t)s * kC32HalfStageBytes;
+    const int nr = min(HR, ns - (issIJ.x * kTile + h * HR)), nc = min(kTile, ns - issIJ.y * kTile);
+    const unsigned br = nr > 0 ? (unsigned)(nr * sizeof(float2) + 15) / 16 * 16 : 0u;
+    const unsigned bc = (unsigned)(nc * sizeof(float2) + 15) / 16 * 16;
+    mbar_expect_tx(bars + s, kC32HalfBytes + br + bc);
+    const unsigned char *src = (const unsigned char *)(tc + (size_t)t * kTile * kTile) + (size_t)h * kC32HalfBytes;
+    bulk_g2s(buf, src, kC32HalfBytes, bars + s);
+    if (br) bulk_g2s(buf + kC32HalfBytes, fg + (size_t)issIJ.x * kTile + h * HR, br, bars + s);
+    bulk_g2s(buf + kC32HalfBytes + HR * sizeof(float2), fg + (size_t)issIJ.y * kTile, bc, bars + s);
+  };
+  if (tid == 0)
+    for (; issued < NST && issued < nunit; ++issued) issue(issued);
+  int2 prevIJ = make_int2(0, 0);
+  bool ok = true;
+  float cv[4];  // column sums of the current tile, carried across its halves
+  for (int u = 0; u <= nunit; ++u) {
+    const bool have = u < nunit;
+    if (!__syncthreads_and(tid == 0 && have ? mbar_wait(bars + u % NST, (unsigned)((u / NST) & 1)) : true)) {
+      ok = false;
+      break;
+    }
+    if (tid == 0 && u >= 1 && issued < nunit) {
+      fence_proxy_async();  // the generic reads of unit u-1's stage before its refill
+      issue(issued);
+      ++issued;
+    }
+    if ((u & 1) == 0 && u >= 2 && prevIJ.x != prevIJ.y) c32_columns_out(colred, prevIJ, nb, tid, tp);
+    if (!have) break;
+    const int s = u % NST, h = u & 1;
+    const int2 IJ = stile[s];
+    prevIJ = IJ;
+    const bool diag = IJ.x == IJ.y;
+    const float2 *__restrict__ T = (const float2 *)(ssm + (size_t)s * kC32HalfStageBytes);
+    const float2 *__restrict__ fr = (const float2 *)(ssm + (size_t)s * kC32HalfStageBytes + kC32HalfBytes);
+    const float2 *__restrict__ fc = fr + HR;
+    float2 fcol[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) fcol[j] = fc[tj + 16 * j];
+    if (h == 0)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cv[j] = 0.f;
+    float rv[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) rv[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int row = ti * R + i;
+      const float2 fs = fr[row];
+      float2 e[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) e[j] = T[row * kTile + tj + 16 * j];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float a = e[j].x, b = e[j].y;
+        if (MODE == MODE_COLL) {
+          const float t = c32_term(a, b, fs, fcol[j]);
+          rv[i] = __fadd_rn(rv[i], t);
+          if (!diag) cv[j] = __fsub_rn(cv[j], t);
+        } else {  // 1/tau summands: row s: P_out + f_p d; column p (reverse channel): P_in - f_s d
+          const float d = __fsub_rn(a, b);
+          rv[i] = __fadd_rn(rv[i], __fmaf_rn(fcol[j].y, d, __fmaf_rn(fcol[j].x, d, b)));
+          if (!diag) cv[j] = __fadd_rn(cv[j], __fmaf_rn(-fs.y, d, __fmaf_rn(-fs.x, d, a)));
+        }
+      }
+    }
+    // rows: the 16 lanes of a half-warp share them; lanes 8i .. 8i + 7 end with the total of row i
+    f32_reduce_scatter<R, 8>(rv, lane);
+    if ((tj & 7) == 0) tp[(long long)(IJ.x * kTile + h * HR + ti * R + (tj >> 3)) * nb + IJ.y] = rv[0];
+    if (!diag && h == 1) {
+      // columns of the whole tile: lanes tj and tj + 16 share them (one level), then the warps
+      // (after the next unit's barrier)
+      const bool up = lane & 16;
+#pragma unroll
+      for (int jk = 0; jk < 2; ++jk) {
+        const int jo = jk + 2;
+        const float kept = up ? cv[jo] : cv[jk], sent = up ? cv[jk] : cv[jo];
+        colred[wid * kTile + tj + 16 * ((up ? 2 : 0) + jk)] = __fadd_rn(kept, __shfl_xor_sync(0xFFFFFFFFu, sent, 16));
+      }
+    }
+  }
+  if (!ok) {
+    *err = 2;
+    if (tid == 0) {
+      for (int k = 0; k < NST; ++k) {
+        const int uses = issued / NST + (k < issued % NST ? 1 : 0);
+        if (uses > 0) mbar_wait(bars + k, (unsigned)((uses - 1) & 1));
+      }
+    }
+  }
+}
+
 // The same FP32 pair coefficients as a row stream, for the batched rt-BTE (precision 2): entry
 // e of the branch-merged rows holds C[e] = rounded (P_in, P_out) of (row state, partner colp[e]);
 // one warp per item (a piece of one row), each lane two 4-entry groups per trip, partners'

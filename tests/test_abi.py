@@ -124,7 +124,7 @@ def test_builder_cutoffs_match_oracle_count(pb, g2_min, nsig):
     assert ch.nchannels == oracle.Oracle(m, g2_min=g2_min, delta_nsigma=nsig).count_channels()
 
 
-@pytest.mark.parametrize("field,bad", [("variant", 9), ("merge_branches", 3), ("dense_rows", 4), ("tile_sweep", 4),
+@pytest.mark.parametrize("field,bad", [("variant", 9), ("merge_branches", 3), ("dense_rows", 4), ("tile_sweep", 9),
                                        ("tile_sweep", -1), ("stream_mode", 3), ("channel_per_lane", 6),
                                        ("transport_gather", 7), ("ctas_per_sm", 9), ("item_channels", 100),
                                        ("adjoint", 2)])

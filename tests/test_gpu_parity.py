@@ -550,6 +550,31 @@ def test_c32_collision_rates_conservation(pb, name):
     dev.check()
 
 
+@pytest.mark.parametrize("shape", [3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("name", ["odd81", "odd99", "tiny8"])
+def test_c32_launch_shapes(pb, name, shape):
+    """Every launch shape of the FP32 tile sweep (stages x CTAs per SM; 7, 8: half-tiles) on
+    ragged complete rows (odd81: the last block's second half holds no state): collision and rates
+    against the oracle at the C32 bound, RK4 steps, and the same integral as the default shape to
+    FP32 rounding."""
+    m = SMALL[name]()
+    o = oracle.Oracle(m)
+    ch = pb.Channels.from_model(m)
+    dev = pb.Device(ch, variant="c32", tile_sweep=shape)
+    f = np.random.default_rng(41).uniform(0, 1, o.nstate)
+    ref, ab = o.collision(f, with_abs=True)
+    I = dev.collision(T(f)).cpu().numpy()
+    check_I(I, ref, ab, tol=C32_TOL, abs_tol=C32_TOL)
+    assert nrel(dev.rates(T(f)).cpu().numpy(), o.rates(f)) <= C32_TOL
+    f0 = o.window_values(m.f_hot())
+    ft = T(f0)
+    dev.rk4(ft, 1.0, 3)
+    assert nrel(ft.cpu().numpy(), o.rk4(f0, 1.0, 3)) <= C32_TOL
+    dev.check()
+    default = pb.Device(ch, variant="c32")
+    assert np.abs(default.collision(T(f)).cpu().numpy() - I).max() <= 1e-7 * ab.max()
+
+
 def test_c32_signed_inputs(pb):
     """The net-term arithmetic holds for occupations of either sign (as the adjoint and
     finite-difference probes use them): random f in [-1, 1] on the ragged 99-state case."""
