@@ -301,7 +301,10 @@ int pb_transport_setup(pb_dev *dev, const double *f0, void *stream);
 /* One pass of the transport map with the weights of the last pb_transport_setup:
  * F3out = tau (v + W F3in), all device double[nstate][3], without any host
  * synchronisation.  If resid3 (device double[3]) is not NULL it receives
- * (max|F3out-F3in| / max|F3out|, max|F3out-F3in|, max|F3out|). */
+ * (max|F3out-F3in| / max|F3out|, max|F3out-F3in|, max|F3out|).  The pass's four launches are
+ * replayed from a CUDA graph captured on the first call with this set of pointers (the last two
+ * sets are kept, so an iteration that alternates between two buffers replays both); when
+ * `stream` is itself being captured, the launches are recorded into the caller's capture. */
 int pb_transport_iterate(pb_dev *dev, const double *vel3, const double *F3in, double *F3out, double *resid3,
                          void *stream);
 

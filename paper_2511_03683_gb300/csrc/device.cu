@@ -477,6 +477,13 @@ struct pb_dev {
   // RK4 graph cache
   cudaStream_t cap = nullptr;
   cudaGraphExec_t rk_exec = nullptr;
+  // transport-pass graphs (pb_transport_iterate), one per argument set, the last two kept
+  struct TrGraph {
+    const double *vel3 = nullptr, *Fin = nullptr;
+    double *Fout = nullptr, *res = nullptr;
+    cudaGraphExec_t exec = nullptr;
+  } trg[2];
+  int trg_next = 0;
   double *rk_f = nullptr;
   double rk_dt = 0.0;
   pb::dev::ChanGeom geom() const {
@@ -1267,6 +1274,8 @@ extern "C" int pb_dev_selftest_wait(pb_dev *d, int32_t wait_us, void *stream) {
 extern "C" void pb_dev_destroy(pb_dev *d) {
   if (!d) return;
   if (d->rk_exec) cudaGraphExecDestroy(d->rk_exec);
+  for (auto &g : d->trg)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   if (d->cap) cudaStreamDestroy(d->cap);
   delete d;
 }
@@ -1596,8 +1605,9 @@ void launch_tr_lane(pb_dev *d, const IDX *col, const float2 *Fin, cudaStream_t s
   }
 }
 
+// res3: where the residual numbers go (d->scal when null)
 int transport_pass(pb_dev *d, const float2 *Fin_ff, const double *vel3, const double *Fold, double *Fnew,
-                   float2 *Fnew_ff, cudaStream_t st) {
+                   float2 *Fnew_ff, cudaStream_t st, double *res3 = nullptr) {
   const int n = (int)d->nitems;
   const float4 *W4 = (const float4 *)d->wt;
   const int64_t need = (d->nitems * 32 + dev::kBlock - 1) / dev::kBlock;
@@ -1616,7 +1626,7 @@ int transport_pass(pb_dev *d, const float2 *Fin_ff, const double *vel3, const do
   dev::k_fin_tr<<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->tau, vel3, Fold, Fnew,
                                                     Fnew_ff, d->red);
   PB_LAUNCHED("k_fin_tr");
-  dev::k_red_final<<<1, 256, 0, st>>>(d->red, d->nfin_blocks, d->scal);
+  dev::k_red_final<<<1, 256, 0, st>>>(d->red, d->nfin_blocks, res3 ? res3 : d->scal);
   PB_LAUNCHED("k_red_final");
   return PB_OK;
 }
@@ -1719,16 +1729,64 @@ extern "C" int pb_transport_setup(pb_dev *d, const double *f0, void *stream) {
   return ensure_weights(d, f0, (cudaStream_t)stream);
 }
 
+namespace {
+// The four launches of one transport pass (conversion of F3in, sweep, epilogue, residual) as a
+// CUDA graph for this argument set: captured on first use, the last two argument sets kept
+// (an iteration alternates between two buffers).
+int transport_graph(pb_dev *d, const double *vel3, const double *F3in, double *F3out, double *resid3,
+                    cudaGraphExec_t *out) {
+  for (auto &g : d->trg)
+    if (g.exec && g.vel3 == vel3 && g.Fin == F3in && g.Fout == F3out && g.res == resid3) {
+      *out = g.exec;
+      return PB_OK;
+    }
+  if (!d->cap) PB_CUDA(cudaStreamCreateWithFlags(&d->cap, cudaStreamNonBlocking));
+  PB_CUDA(cudaStreamBeginCapture(d->cap, cudaStreamCaptureModeThreadLocal));
+  int rc = to_ff(d, F3in, 3 * d->ns, d->Fff, d->cap);
+  if (rc == PB_OK) rc = transport_pass(d, d->Fff, vel3, F3in, F3out, d->Fff, d->cap, resid3);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(d->cap, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  auto &g = d->trg[d->trg_next];
+  d->trg_next ^= 1;
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g = pb_dev::TrGraph{};
+  e = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    g.exec = nullptr;
+    return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  g.vel3 = vel3;
+  g.Fin = F3in;
+  g.Fout = F3out;
+  g.res = resid3;
+  *out = g.exec;
+  return PB_OK;
+}
+}  // namespace
+
 extern "C" int pb_transport_iterate(pb_dev *d, const double *vel3, const double *F3in, double *F3out,
                                     double *resid3, void *stream) {
   clear_error();
   if (!d || !vel3 || !F3in || !F3out) return set_error(PB_EINVAL, "pb_transport_iterate: null argument");
   if (!d->transport) return set_error(PB_EINVAL, "transport buffers were not reserved (pb_dev_opts.transport = 0)");
   cudaStream_t st = (cudaStream_t)stream;
-  int rc;
-  if ((rc = to_ff(d, F3in, 3 * d->ns, d->Fff, st))) return rc;
-  if ((rc = transport_pass(d, d->Fff, vel3, F3in, F3out, d->Fff, st))) return rc;
-  if (resid3) PB_CUDA(cudaMemcpyAsync(resid3, d->scal, 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  PB_CUDA(cudaStreamIsCapturing(st, &cs));
+  if (cs != cudaStreamCaptureStatusNone) {  // the caller is capturing: record the launches themselves
+    int rc;
+    if ((rc = to_ff(d, F3in, 3 * d->ns, d->Fff, st))) return rc;
+    return transport_pass(d, d->Fff, vel3, F3in, F3out, d->Fff, st, resid3);
+  }
+  cudaGraphExec_t exec = nullptr;
+  int rc = transport_graph(d, vel3, F3in, F3out, resid3, &exec);
+  if (rc) return rc;
+  PB_CUDA(cudaGraphLaunch(exec, st));
   return PB_OK;
 }
 

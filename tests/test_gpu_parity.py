@@ -346,6 +346,31 @@ def test_transport_map_and_solve(pb):
     assert nrel(F, Fr) <= 1e-9
 
 
+def test_transport_iterate_replays_graphs(pb):
+    """pb_transport_iterate replays one captured graph per argument set: an iteration that
+    alternates between two buffers (with and without the residual output) gives, bit for bit,
+    the iterates and residuals of the host-buffer pass, which launches the kernels directly."""
+    import torch
+
+    m = synth.make_window4(12)
+    o = oracle.Oracle(m)
+    dev = pb.Device(pb.Channels.from_model(m), transport=True)
+    f0 = o.window_values(m.f_fermi(m.emin() - 0.2))
+    v = T(o.window_values(m.vel))
+    dev.transport_setup(T(f0))
+    F = np.random.default_rng(3).normal(size=(o.nstate, 3))
+    a, b, res = T(F), T(np.zeros_like(F)), T(np.zeros(3))
+    Fh = F.copy()
+    for it in range(6):
+        src, dst = (a, b) if it % 2 == 0 else (b, a)
+        dev.transport_iterate(v, src, out=dst, resid=res if it < 4 else None)
+        rh = np.zeros(3)
+        Fh = dev.transport_iterate_host(v, Fh, resid=rh)
+        assert np.array_equal(dst.cpu().numpy(), Fh)
+        if it < 4:
+            assert np.array_equal(res.cpu().numpy(), rh)
+
+
 def test_no_channels(pb):
     """Acoustic-only modes on a 1x1x1 grid: no channel survives, every output is zero."""
     eps = np.array([[0.0, 0.1]])
