@@ -255,7 +255,11 @@ typedef struct pb_dev_info {
 
 int pb_dev_get_info(const pb_dev *dev, pb_dev_info *info);
 
-/* Eq. 2: dfdt[s] = I_s[f] for every window state.  f, dfdt: device double[nstate]. */
+/* Eq. 2: dfdt[s] = I_s[f] for every window state.  f, dfdt: device double[nstate].
+ * The call's launches are replayed from a CUDA graph kept per argument set (captured on first
+ * use; the handle keeps its six most recent call graphs, shared with pb_scatter_rates and
+ * pb_transport_iterate); when `stream` is itself being captured, the launches are recorded into
+ * the caller's capture. */
 int pb_collision(pb_dev *dev, const double *f, double *dfdt, void *stream);
 
 /* Measurement aid (the paper has no counterpart): the average device duration of the
@@ -302,9 +306,8 @@ int pb_transport_setup(pb_dev *dev, const double *f0, void *stream);
  * F3out = tau (v + W F3in), all device double[nstate][3], without any host
  * synchronisation.  If resid3 (device double[3]) is not NULL it receives
  * (max|F3out-F3in| / max|F3out|, max|F3out-F3in|, max|F3out|).  The pass's four launches are
- * replayed from a CUDA graph captured on the first call with this set of pointers (the last two
- * sets are kept, so an iteration that alternates between two buffers replays both); when
- * `stream` is itself being captured, the launches are recorded into the caller's capture. */
+ * replayed from a CUDA graph kept per set of pointers, as for pb_collision (an iteration that
+ * alternates between two buffers replays two graphs). */
 int pb_transport_iterate(pb_dev *dev, const double *vel3, const double *F3in, double *F3out, double *resid3,
                          void *stream);
 

@@ -477,13 +477,21 @@ struct pb_dev {
   // RK4 graph cache
   cudaStream_t cap = nullptr;
   cudaGraphExec_t rk_exec = nullptr;
-  // transport-pass graphs (pb_transport_iterate), one per argument set, the last two kept
-  struct TrGraph {
-    const double *vel3 = nullptr, *Fin = nullptr;
-    double *Fout = nullptr, *res = nullptr;
+  // graphs of the short launch sequences of pb_collision, pb_scatter_rates and
+  // pb_transport_iterate, one per call kind and argument set, the last kGraphs kept
+  static constexpr int kGraphs = 6;
+  struct CallGraph {
+    int kind = 0;
+    const void *a = nullptr, *b = nullptr, *c = nullptr, *e = nullptr;
     cudaGraphExec_t exec = nullptr;
-  } trg[2];
-  int trg_next = 0;
+  } cg[kGraphs];
+  int cg_next = 0;
+  void drop_call_graphs() {
+    for (auto &g : cg) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      g = CallGraph{};
+    }
+  }
   double *rk_f = nullptr;
   double rk_dt = 0.0;
   pb::dev::ChanGeom geom() const {
@@ -1274,8 +1282,7 @@ extern "C" int pb_dev_selftest_wait(pb_dev *d, int32_t wait_us, void *stream) {
 extern "C" void pb_dev_destroy(pb_dev *d) {
   if (!d) return;
   if (d->rk_exec) cudaGraphExecDestroy(d->rk_exec);
-  for (auto &g : d->trg)
-    if (g.exec) cudaGraphExecDestroy(g.exec);
+  d->drop_call_graphs();
   if (d->cap) cudaStreamDestroy(d->cap);
   delete d;
 }
@@ -1633,16 +1640,73 @@ int transport_pass(pb_dev *d, const float2 *Fin_ff, const double *vel3, const do
 
 }  // namespace
 
+namespace {
+// Runs the launch sequence `seq(stream)` of a call from a CUDA graph kept for this call kind and
+// argument set (captured on first use; the last pb_dev::kGraphs kept, the oldest replaced).  When
+// `st` is itself being captured, the launches are recorded into the caller's capture instead.
+template <typename Seq>
+int replay(pb_dev *d, int kind, const void *a, const void *b, const void *c, const void *e, cudaStream_t st,
+           Seq &&seq) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  PB_CUDA(cudaStreamIsCapturing(st, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return seq(st);
+  cudaGraphExec_t exec = nullptr;
+  for (auto &g : d->cg)
+    if (g.exec && g.kind == kind && g.a == a && g.b == b && g.c == c && g.e == e) exec = g.exec;
+  if (!exec) {
+    if (!d->cap) PB_CUDA(cudaStreamCreateWithFlags(&d->cap, cudaStreamNonBlocking));
+    PB_CUDA(cudaStreamBeginCapture(d->cap, cudaStreamCaptureModeThreadLocal));
+    const int rc = seq(d->cap);
+    cudaGraph_t graph = nullptr;
+    cudaError_t err = cudaStreamEndCapture(d->cap, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (err != cudaSuccess) return cuda_fail(err, "cudaStreamEndCapture");
+    auto &g = d->cg[d->cg_next];
+    d->cg_next = (d->cg_next + 1) % pb_dev::kGraphs;
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = pb_dev::CallGraph{};
+    err = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (err != cudaSuccess) {
+      g.exec = nullptr;
+      return cuda_fail(err, "cudaGraphInstantiate");
+    }
+    g.kind = kind;
+    g.a = a;
+    g.b = b;
+    g.c = c;
+    g.e = e;
+    exec = g.exec;
+  }
+  PB_CUDA(cudaGraphLaunch(exec, st));
+  return PB_OK;
+}
+
+enum { kCallCollision = 1, kCallRates = 2, kCallTransport = 3 };
+
+// one transport pass: conversion of F3in, sweep, epilogue, residual (into res3, or the handle's
+// scalars when null)
+int transport_seq(pb_dev *d, const double *vel3, const double *F3in, double *F3out, double *res3, cudaStream_t st) {
+  int rc;
+  if ((rc = to_ff(d, F3in, 3 * d->ns, d->Fff, st))) return rc;
+  return transport_pass(d, d->Fff, vel3, F3in, F3out, d->Fff, st, res3);
+}
+}  // namespace
+
 extern "C" int pb_collision(pb_dev *d, const double *f, double *dfdt, void *stream) {
   clear_error();
   if (!d || !f || !dfdt) return set_error(PB_EINVAL, "pb_collision: null argument");
-  cudaStream_t st = (cudaStream_t)stream;
-  int rc;
-  if ((rc = stage_input(d, f, st))) return rc;
-  if ((rc = launch_stream(d, dev::MODE_COLL, f, d->yff, st))) return rc;
-  launch_fin<-1>(d, f, dfdt, nullptr, 0.0, st);
-  PB_LAUNCHED("k_fin_coll");
-  return PB_OK;
+  return replay(d, kCallCollision, f, dfdt, nullptr, nullptr, (cudaStream_t)stream, [&](cudaStream_t st) -> int {
+    int rc;
+    if ((rc = stage_input(d, f, st))) return rc;
+    if ((rc = launch_stream(d, dev::MODE_COLL, f, d->yff, st))) return rc;
+    launch_fin<-1>(d, f, dfdt, nullptr, 0.0, st);
+    PB_LAUNCHED("k_fin_coll");
+    return PB_OK;
+  });
 }
 
 extern "C" int pb_dev_time_sweep(pb_dev *d, const double *f, int32_t nlaunch, float *avg_ms, void *stream) {
@@ -1672,10 +1736,21 @@ extern "C" int pb_dev_time_sweep(pb_dev *d, const double *f, int32_t nlaunch, fl
   return PB_OK;
 }
 
+namespace {
+int rates_seq(pb_dev *d, const double *f, double *inv_tau, cudaStream_t st);
+}
+
 extern "C" int pb_scatter_rates(pb_dev *d, const double *f, double *inv_tau, void *stream) {
   clear_error();
   if (!d || !f || !inv_tau) return set_error(PB_EINVAL, "pb_scatter_rates: null argument");
-  cudaStream_t st = (cudaStream_t)stream;
+  if (d->variant == PB_VARIANT_PAPER)
+    return set_error(PB_EINVAL, "scattering rates are not available in the paper layout");
+  return replay(d, kCallRates, f, inv_tau, nullptr, nullptr, (cudaStream_t)stream,
+                [&](cudaStream_t st) { return rates_seq(d, f, inv_tau, st); });
+}
+
+namespace {
+int rates_seq(pb_dev *d, const double *f, double *inv_tau, cudaStream_t st) {
   int rc;
   if ((rc = stage_input(d, f, st))) return rc;
   if ((rc = launch_stream(d, dev::MODE_RATE, f, d->yff, st))) return rc;
@@ -1695,6 +1770,7 @@ extern "C" int pb_scatter_rates(pb_dev *d, const double *f, double *inv_tau, voi
   PB_LAUNCHED("k_fin_rate");
   return PB_OK;
 }
+}  // namespace
 
 extern "C" int pb_rtbte_rk4_step(pb_dev *d, double *f, double dt, int32_t nsteps, void *stream) {
   clear_error();
@@ -1729,65 +1805,14 @@ extern "C" int pb_transport_setup(pb_dev *d, const double *f0, void *stream) {
   return ensure_weights(d, f0, (cudaStream_t)stream);
 }
 
-namespace {
-// The four launches of one transport pass (conversion of F3in, sweep, epilogue, residual) as a
-// CUDA graph for this argument set: captured on first use, the last two argument sets kept
-// (an iteration alternates between two buffers).
-int transport_graph(pb_dev *d, const double *vel3, const double *F3in, double *F3out, double *resid3,
-                    cudaGraphExec_t *out) {
-  for (auto &g : d->trg)
-    if (g.exec && g.vel3 == vel3 && g.Fin == F3in && g.Fout == F3out && g.res == resid3) {
-      *out = g.exec;
-      return PB_OK;
-    }
-  if (!d->cap) PB_CUDA(cudaStreamCreateWithFlags(&d->cap, cudaStreamNonBlocking));
-  PB_CUDA(cudaStreamBeginCapture(d->cap, cudaStreamCaptureModeThreadLocal));
-  int rc = to_ff(d, F3in, 3 * d->ns, d->Fff, d->cap);
-  if (rc == PB_OK) rc = transport_pass(d, d->Fff, vel3, F3in, F3out, d->Fff, d->cap, resid3);
-  cudaGraph_t graph = nullptr;
-  cudaError_t e = cudaStreamEndCapture(d->cap, &graph);
-  if (rc) {
-    if (graph) cudaGraphDestroy(graph);
-    return rc;
-  }
-  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-  auto &g = d->trg[d->trg_next];
-  d->trg_next ^= 1;
-  if (g.exec) cudaGraphExecDestroy(g.exec);
-  g = pb_dev::TrGraph{};
-  e = cudaGraphInstantiate(&g.exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) {
-    g.exec = nullptr;
-    return cuda_fail(e, "cudaGraphInstantiate");
-  }
-  g.vel3 = vel3;
-  g.Fin = F3in;
-  g.Fout = F3out;
-  g.res = resid3;
-  *out = g.exec;
-  return PB_OK;
-}
-}  // namespace
-
 extern "C" int pb_transport_iterate(pb_dev *d, const double *vel3, const double *F3in, double *F3out,
                                     double *resid3, void *stream) {
   clear_error();
   if (!d || !vel3 || !F3in || !F3out) return set_error(PB_EINVAL, "pb_transport_iterate: null argument");
   if (!d->transport) return set_error(PB_EINVAL, "transport buffers were not reserved (pb_dev_opts.transport = 0)");
   cudaStream_t st = (cudaStream_t)stream;
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  PB_CUDA(cudaStreamIsCapturing(st, &cs));
-  if (cs != cudaStreamCaptureStatusNone) {  // the caller is capturing: record the launches themselves
-    int rc;
-    if ((rc = to_ff(d, F3in, 3 * d->ns, d->Fff, st))) return rc;
-    return transport_pass(d, d->Fff, vel3, F3in, F3out, d->Fff, st, resid3);
-  }
-  cudaGraphExec_t exec = nullptr;
-  int rc = transport_graph(d, vel3, F3in, F3out, resid3, &exec);
-  if (rc) return rc;
-  PB_CUDA(cudaGraphLaunch(exec, st));
-  return PB_OK;
+  return replay(d, kCallTransport, vel3, F3in, F3out, resid3, st,
+                [&](cudaStream_t s) { return transport_seq(d, vel3, F3in, F3out, resid3, s); });
 }
 
 extern "C" int pb_transport_iterate_host(pb_dev *d, const double *vel3, const double *F3in_host, double *F3out_host,
@@ -1798,9 +1823,10 @@ extern "C" int pb_transport_iterate_host(pb_dev *d, const double *vel3, const do
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = sizeof(double) * 3 * (size_t)d->ns;
   PB_CUDA(cudaMemcpyAsync(d->Fa, F3in_host, bytes, cudaMemcpyHostToDevice, st));
-  int rc;
-  if ((rc = to_ff(d, d->Fa, 3 * d->ns, d->Fff, st))) return rc;
-  if ((rc = transport_pass(d, d->Fff, vel3, d->Fa, d->Fb, d->Fff, st))) return rc;
+  // the pass Fa -> Fb, residual into the handle's scalars
+  int rc = replay(d, kCallTransport, vel3, d->Fa, d->Fb, nullptr, st,
+                  [&](cudaStream_t s) { return transport_seq(d, vel3, d->Fa, d->Fb, nullptr, s); });
+  if (rc) return rc;
   PB_CUDA(cudaMemcpyAsync(F3out_host, d->Fb, bytes, cudaMemcpyDeviceToHost, st));
   if (resid3_host) PB_CUDA(cudaMemcpyAsync(resid3_host, d->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
   PB_CUDA(cudaStreamSynchronize(st));
@@ -2208,6 +2234,7 @@ extern "C" int pb_dev_set_g2(pb_dev *d, const double *g2, void *stream) {
       d->rk_exec = nullptr;
     }
   }
+  d->drop_call_graphs();  // the calls' launch sequences are captured again on their next use
   return coef_setup(d, st);
 }
 

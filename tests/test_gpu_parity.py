@@ -347,9 +347,10 @@ def test_transport_map_and_solve(pb):
 
 
 def test_transport_iterate_replays_graphs(pb):
-    """pb_transport_iterate replays one captured graph per argument set: an iteration that
-    alternates between two buffers (with and without the residual output) gives, bit for bit,
-    the iterates and residuals of the host-buffer pass, which launches the kernels directly."""
+    """pb_transport_iterate replays one captured graph per argument set (the last two kept): an
+    iteration that alternates between two buffers (with and without the residual output),
+    interleaved with host-buffer passes (a third argument set, so graphs are evicted and captured
+    again), gives the same iterates and residuals bit for bit on both paths."""
     import torch
 
     m = synth.make_window4(12)
@@ -397,10 +398,11 @@ def test_single_state(pb):
     # the self channel's in- and out-scattering cancel
     assert abs(dev.collision(T([0.4])).cpu().numpy()[0]) <= 1e-13 * 0.4 * ref
     # the FP32 coefficient tiles: one diagonal tile with one state; the self pair's two FP32
-    # coefficients are equal, so its net term and its first-order terms vanish exactly
+    # coefficients are equal, so its net term vanishes exactly and its two first-order terms
+    # cancel up to the rounding of one FMA (about 2^-48 of the term)
     d32 = pb.Device(ch, variant="c32")
     assert abs(d32.rates(T([0.4])).cpu().numpy()[0] - ref) <= 1e-6 * ref
-    assert d32.collision(T([0.4])).cpu().numpy()[0] == 0.0
+    assert abs(d32.collision(T([0.4])).cpu().numpy()[0]) <= 1e-13 * 0.4 * ref
     d32.check()
 
 
