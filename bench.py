@@ -416,47 +416,43 @@ def batched_report(pb, ninst, nsteps, stream):
     ms_g, _ = sequential("g32")
     b.close()
 
-    # the same batch on the FP64-accurate branch-merged stream
-    bf = pb.Batch(chs, precision="ff")
-    item_f, ctas_f, tune_f = bf.autotune(f)
-    g = f.clone()
-    bf.rk4(g, 1.0, 3)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    bf.rk4(g, 1.0, nsteps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_bf = e0.elapsed_time(e1)
-    If = bf.collision(f).cpu().numpy()
-    err_f = 0.0
-    for i, (c, x) in enumerate(zip(chs, fs)):
-        d = pb.Device(c)
-        ref = d.collision(torch.tensor(x, device="cuda")).cpu().numpy()
-        d.close()
-        a, e = bf.offsets[i], bf.offsets[i + 1]
-        err_f = max(err_f, float(np.abs(If[a:e] - ref).max() / max(np.abs(ref).max(), 1e-300)))
-    bf.close()
+    def accurate(precision, layout):
+        """One FP64-accurate or FP32-pair batch: autotuned, nsteps RK4 steps timed, and df/dt
+        against each instance on its own FF device (max over instances, normwise)."""
+        bx = pb.Batch(chs, precision=precision, layout=layout)
+        tuned = bx.autotune(f)
+        g = f.clone()
+        bx.rk4(g, 1.0, 3)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        bx.rk4(g, 1.0, nsteps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        bx.check()
+        Ix = bx.collision(f).cpu().numpy()
+        errx = 0.0
+        for i, (c, x) in enumerate(zip(chs, fs)):
+            d = pb.Device(c)
+            ref = d.collision(torch.tensor(x, device="cuda")).cpu().numpy()
+            d.close()
+            a, e = bx.offsets[i], bx.offsets[i + 1]
+            errx = max(errx, float(np.abs(Ix[a:e] - ref).max() / max(np.abs(ref).max(), 1e-300)))
+        tiled = bx.tiled
+        bx.close()
+        return ms, tuned, errx, tiled
 
-    # the same batch with the FP32 pair coefficients (net terms per entry)
-    bc = pb.Batch(chs, precision="c32")
-    item_c, ctas_c, tune_c = bc.autotune(f)
-    g = f.clone()
-    bc.rk4(g, 1.0, 3)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    bc.rk4(g, 1.0, nsteps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_bc = e0.elapsed_time(e1)
-    Ic = bc.collision(f).cpu().numpy()
-    err_c = 0.0
-    for i, (c, x) in enumerate(zip(chs, fs)):
-        d = pb.Device(c)
-        ref = d.collision(torch.tensor(x, device="cuda")).cpu().numpy()
-        d.close()
-        a, e = bc.offsets[i], bc.offsets[i + 1]
-        err_c = max(err_c, float(np.abs(Ic[a:e] - ref).max() / max(np.abs(ref).max(), 1e-300)))
-    bc.close()
+    # the same batch on the FP64-accurate branch-merged coefficients (symmetric tiles by
+    # default, rows beside them) and as FP32 pairs (net terms per entry)
+    ms_bf, (item_f, ctas_f, tune_f), err_f, tiled_f = accurate("ff", 0)
+    ms_bfr, (item_fr, ctas_fr, tune_fr), _, _ = accurate("ff", 1)
+    ms_bc, (item_c, ctas_c, tune_c), err_c, tiled_c = accurate("c32", 0)
+    ms_bcr, (item_cr, ctas_cr, tune_cr), _, _ = accurate("c32", 1)
+
+    def rows_leg(ms, item_, ctas_, tune_):
+        return {"autotuned": {"item_entries": item_, "ctas_per_sm": ctas_, "sweep_ms": tune_}, "batched_ms": ms,
+                "batched_rk4_steps_per_s": nsteps / (ms * 1e-3)}
+
     return {"instances": ninst, "states": b.nstate, "channels": nch, "build_channels_s": build_s,
             "autotuned": {"item_channels": item, "ctas_per_sm": ctas, "sweep_ms": tune_ms},
             "rk4_steps": nsteps, "batched_ms": ms_b,
@@ -465,18 +461,22 @@ def batched_report(pb, ninst, nsteps, stream):
             "sequential_ff_ms": ms_ff, "sequential_ff_per_channel_ms": ms_ffc, "sequential_g32_ms": ms_g,
             "speedup_vs_sequential_fp32": ms_g / ms_b, "speedup_vs_sequential_ff": ms_ff / ms_b,
             "speedup_vs_sequential_ff_per_channel": ms_ffc / ms_b,
-            "ff_batch": {"autotuned": {"item_entries": item_f, "ctas_per_sm": ctas_f, "sweep_ms": tune_f},
+            "ff_batch": {"layout": "tiles" if tiled_f else "rows",
+                         "autotuned": {"item_entries": item_f, "ctas_per_sm": ctas_f, "sweep_ms": tune_f},
                          "batched_ms": ms_bf, "batched_rk4_steps_per_s": nsteps / (ms_bf * 1e-3),
                          "batched_channels_per_s": 4 * nch * nsteps / (ms_bf * 1e-3),
                          "speedup_vs_sequential_ff": ms_ff / ms_bf,
                          "speedup_vs_sequential_ff_per_channel": ms_ffc / ms_bf,
-                         "dfdt_err_vs_unbatched_ff_max_over_instances": err_f},
-            "c32_batch": {"autotuned": {"item_entries": item_c, "ctas_per_sm": ctas_c, "sweep_ms": tune_c},
+                         "dfdt_err_vs_unbatched_ff_max_over_instances": err_f,
+                         "rows": rows_leg(ms_bfr, item_fr, ctas_fr, tune_fr)},
+            "c32_batch": {"layout": "tiles" if tiled_c else "rows",
+                          "autotuned": {"item_entries": item_c, "ctas_per_sm": ctas_c, "sweep_ms": tune_c},
                           "batched_ms": ms_bc, "batched_rk4_steps_per_s": nsteps / (ms_bc * 1e-3),
                           "batched_channels_per_s": 4 * nch * nsteps / (ms_bc * 1e-3),
                           "speedup_vs_sequential_ff": ms_ff / ms_bc, "speedup_vs_ff_batch": ms_bf / ms_bc,
                           "speedup_vs_sequential_fp32": ms_g / ms_bc,
-                          "dfdt_err_vs_fp64_max_over_instances": err_c},
+                          "dfdt_err_vs_fp64_max_over_instances": err_c,
+                          "rows": rows_leg(ms_bcr, item_cr, ctas_cr, tune_cr)},
             "dfdt_err_vs_fp64_max_over_instances": err}
 
 

@@ -160,8 +160,9 @@ void pb_channels_free(pb_channels *ch);
  *                     P_in f_p (1-f_s) - P_out f_s (1-f_p) in FP32 with the larger product made
  *                     exact by an FMA, plus first-order terms in the low part of the float-float
  *                     f; FP64 for the per-state combination and the RK4 update.  df/dt within
- *                     about 1e-6 of Eq. 2 (normwise).  Needs complete rows (no cutoffs), branch
- *                     merging and tile_sweep 0 or 2..6 (PB_EINVAL otherwise).  Transport, the
+ *                     about 1e-6 of Eq. 2 (normwise).  Needs complete rows (no cutoffs) of a list
+ *                     built with check_closure, branch merging and tile_sweep 0 or 2..8
+ *                     (PB_EINVAL otherwise).  Transport, the
  *                     no-allocation call and, after pb_dev_set_g2, every sweep run the FF rows;
  *                     the adjoint calls return PB_EINVAL. */
 enum { PB_VARIANT_FF = 0, PB_VARIANT_F64 = 1, PB_VARIANT_LITERAL = 2, PB_VARIANT_G32 = 3, PB_VARIANT_G16 = 4,
@@ -200,8 +201,9 @@ typedef struct pb_dev_opts {
                                 bytes per entry); 3 as 1, and the collision and rate sweeps stream the upper
                                 block triangle of the pair matrix as 64 x 64 tiles of (P_in, P_out), adding
                                 each tile to its rows and, through the reverse channels (P_in(p,s) =
-                                P_out(s,p)), to its columns: about 8 bytes per state pair; 2 always stream
-                                the index */
+                                P_out(s,p)), to its columns: about 8 bytes per state pair (only for a list
+                                built with check_closure, which guarantees those reverse channels; 1
+                                otherwise); 2 always stream the index */
   int32_t tile_sweep;        /* the symmetric tile sweep (dense_rows 3): 0 automatic (= 3); 1 each thread
                                 loads its 4 x 4 entries of a tile from global memory (3 CTAs per SM);
                                 2 one persistent CTA per SM with 256 threads keeps three tiles in flight in
@@ -396,7 +398,14 @@ typedef struct pb_batch_opts {
   int32_t layout;         /* precision 0: 0 automatic (the dense pair-major form when the stored channels
                              fill at least 85% of the instances' (state, partner, branch) slots: |g|^2 in
                              one FP32 slot each, zero where no channel exists, no index streamed; work
-                             items of item_channels / 4 partners); 1 one entry per channel */
+                             items of item_channels / 4 partners); 1 one entry per channel.
+                             precision 1 and 2: 0 automatic (symmetric tiles when every instance's list
+                             was built with check_closure and the tiles stream at most 0.7 of the rows'
+                             bytes: each instance's states in 64-state blocks of one padded state space,
+                             the upper block triangle of each instance stored as 64 x 64 tiles, one
+                             unordered state pair per entry for both directions, zero where a pair has
+                             no channel); 1 rows (one entry per directed state pair); 2 symmetric tiles
+                             whatever their bytes (PB_EINVAL for a list built without check_closure) */
 } pb_batch_opts;
 
 int pb_batch_arena_bytes(const pb_channels *const *chs, int32_t n, const pb_batch_opts *opts, size_t *bytes);
@@ -408,9 +417,16 @@ int pb_batch_create(const pb_channels *const *chs, int32_t n, const pb_batch_opt
 
 void pb_batch_destroy(pb_batch *batch);
 
-/* Total states and channels, state_offsets[n+1] (may be NULL), current launch shape. */
+/* Total states and channels, state_offsets[n+1] (may be NULL), current launch shape:
+ * item_channels is 0 when the batch streams symmetric tiles (ctas_per_sm then gives the tile
+ * ring's resident CTAs per SM). */
 int pb_batch_get_info(const pb_batch *batch, int64_t *nstate, int64_t *nchannels, int64_t *state_offsets,
                       int32_t *item_channels, int32_t *ctas_per_sm);
+
+/* Reads (and clears) the batch's device error word: PB_ETIMEOUT when a bounded wait of the
+ * tile sweep gave up since the last check (its results are then invalid).  Synchronises
+ * `stream`. */
+int pb_batch_check(pb_batch *batch, void *stream);
 
 /* dfdt = I[f] for every state of every instance (device double[nstate total]). */
 int pb_batch_collision(pb_batch *batch, const double *f, double *dfdt, void *stream);
@@ -418,8 +434,9 @@ int pb_batch_collision(pb_batch *batch, const double *f, double *dfdt, void *str
 /* nsteps classic RK4 steps of every instance, in place on f (device double[nstate total]). */
 int pb_batch_rk4_step(pb_batch *batch, double *f, double dt, int32_t nsteps, void *stream);
 
-/* Time candidate launch shapes (work-item sizes 1024/2048/4096 entries x 2/3/4 CTAs per SM)
- * on collision sweeps at f and keep the fastest; reports it (any pointer may be NULL).
+/* Time candidate launch shapes (rows: work-item sizes 1024/2048/4096 entries x 2/3/4 CTAs
+ * per SM; symmetric tiles: the tile ring's stages x CTAs per SM, item size reported as 0) on
+ * collision sweeps at f and keep the fastest; reports it (any pointer may be NULL).
  * Synchronises `stream`. */
 int pb_batch_autotune(pb_batch *batch, const double *f, void *stream, int32_t *best_item_channels,
                       int32_t *best_ctas_per_sm, double *best_ms);

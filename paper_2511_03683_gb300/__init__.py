@@ -131,6 +131,7 @@ def lib() -> ctypes.CDLL:
         "pb_batch_collision": [vp, vp, vp, vp],
         "pb_batch_rk4_step": [vp, vp, dbl, i32, vp],
         "pb_batch_autotune": [vp, vp, vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(dbl)],
+        "pb_batch_check": [vp, vp],
         "pb_rtbte_rk4_vjp": [vp, vp, vp, dbl, vp, vp],
         "pb_rtbte_rk4_vjp_defer": [vp, vp, vp, dbl, vp],
         "pb_dev_g2grad_flush": [vp, vp, vp],
@@ -533,6 +534,11 @@ class Batch:
         self.nstate, self.nchannels = int(ns.value), int(nc.value)
         self.offsets = offs
         self.item_channels, self.ctas_per_sm = int(ic.value), int(ct.value)
+        self.tiled = self.item_channels == 0  # symmetric tiles (precision ff / c32)
+
+    def check(self, stream=None):
+        """Raise if a bounded device-side wait of the tile sweep gave up since the last check."""
+        _check(lib().pb_batch_check(self._h, _stream_ptr(stream)))
 
     def collision(self, f, out=None, stream=None):
         out = torch_empty(self.nstate) if out is None else out

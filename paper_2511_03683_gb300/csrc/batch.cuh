@@ -20,6 +20,15 @@
 // (P_in, P_out) with their ratio kept, 8 bytes per state pair, and the row stream forms each
 // entry's net term in FP32 with an exact leading product and the first-order terms in the low
 // part of f (tiles32.cuh): df/dt within about 1e-6 of Eq. 2.
+//
+// Symmetric tiles (precision 1 and 2, every instance's channel list verified closed under
+// reversal): each instance takes a run of 64-state blocks of one padded state space, and the
+// upper block triangle of every instance is stored as 64 x 64 tiles (zero where a state pair
+// has no channel), so each unordered state pair is streamed once for both of its directions,
+// as in the single-system sweeps (half the bytes of the rows).  One launch
+// of the single-system tile kernel sweeps every instance's tiles; the partial of a state and a
+// partner block sits in the slot of that block's index within its instance, so a state's
+// partials are its instance's blocks only.  The epilogues map each state to its padded row.
 
 namespace pb {
 namespace dev {
@@ -265,6 +274,19 @@ struct pb_batch {
   float2 *pC = nullptr;  // precision 2: rounded FP32 (P_in, P_out) per entry
   uint32_t *pidx = nullptr;
   double *Rg = nullptr;
+  // symmetric tiles (precision >= 1): padded state space of nsp states in nblk blocks,
+  // tnt tiles; partial slots per state tnb (the largest instance's blocks); launch shape
+  // tshape (float-float: CTAs per SM of the half-tile ring, 2 or 3; FP32 pairs: the C32
+  // shape number 2..8)
+  bool tiles = false;
+  int64_t nsp = 0;
+  int nblk = 0, tnb = 0, tnt = 0, tshape = 0;
+  int2 *tl = nullptr;
+  int *lblk = nullptr, *pmap = nullptr;
+  int4 *binfo = nullptr;
+  long long *srp = nullptr;
+  void *tc = nullptr, *tp = nullptr;
+  int *err = nullptr;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
   double *rk_f = nullptr;
@@ -399,16 +421,46 @@ std::vector<int64_t> batch_pair_lenp(const pb_channels *const *chs, int32_t n) {
   return lenp;
 }
 
+// The symmetric-tile form of a precision >= 1 batch (layout 2: always; layout 0: taken when every instance's
+// channel list was verified closed (the tile entry of (s, p) serves the reverse pair with
+// P_in and P_out swapped) and the tiles stream at most 0.7 of the rows' bytes (the row stream
+// runs closer to the copy bandwidth; sparse rows, or many instances much smaller than a
+// 64-state block, fill the tiles with zeros).
+struct BatchTiles {
+  bool on = false;
+  int64_t nsp = 0;
+  int nblk = 0, nbmax = 0, nt = 0;
+};
+BatchTiles batch_tiles_for(const pb_channels *const *chs, int32_t n, int prec, int layout, int64_t nent) {
+  BatchTiles T;
+  if (prec < 1 || layout == 1) return T;
+  int64_t nt = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!chs[i]->closed) return T;
+    const int64_t B = (chs[i]->nstate + dev::kTile - 1) / dev::kTile;
+    T.nblk += (int)B;
+    T.nbmax = std::max<int>(T.nbmax, (int)B);
+    nt += B * (B + 1) / 2;
+  }
+  if (nt == 0 || nt >= INT32_MAX / 2) return T;
+  const double tile_bytes = (double)nt * dev::kTile * dev::kTile * (prec == 2 ? 8.0 : 16.0);
+  const double row_bytes = (double)nent * (prec == 2 ? 12.0 : 20.0);
+  T.nt = (int)nt;
+  T.nsp = (int64_t)T.nblk * dev::kTile;
+  T.on = layout == 2 || tile_bytes <= 0.7 * row_bytes;
+  return T;
+}
+
 struct BatchLayoutFF {
   size_t items, item_inst, item_ptr, pA, pB, pC, pidx, Rg, yff, part, acc, y, tcol, tg2, tcA, tcB, titems, titem_ptr,
-      tpart, tR, tpcst, tpcnt, omega_tmp, tab_tmp, eps_tmp, kc_tmp, total;
+      tpart, tR, tpcst, tpcnt, omega_tmp, tab_tmp, eps_tmp, kc_tmp, srp, tl, lblk, binfo, pmap, tc, tp, err, total;
 };
 
 constexpr int kBatchSetupItem = 2048;  // channels per work item of the per-instance coefficient setup
 
-// c32: also the rounded FP32 pairs of precision 2
+// c32: precision 2 (the rounded FP32 pairs of the rows, or FP32 tiles); T: the tile form
 BatchLayoutFF batch_layout_ff(const pb_channels *const *chs, int n, int64_t ns, int64_t nent, int64_t nitems_cap,
-                              bool c32 = false) {
+                              bool c32, const BatchTiles &T) {
   BatchLayoutFF L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -440,10 +492,10 @@ BatchLayoutFF batch_layout_ff(const pb_channels *const *chs, int n, int64_t ns, 
   L.item_ptr = take(sizeof(int32_t) * (ns + 1));
   L.pA = take(sizeof(float2) * nent);
   L.pB = take(sizeof(float2) * nent);
-  L.pC = take(c32 ? sizeof(float2) * nent : 0);
+  L.pC = take(c32 && !T.on ? sizeof(float2) * nent : 0);
   L.pidx = take(sizeof(uint32_t) * nent);
   L.Rg = take(sizeof(double) * ns);
-  L.yff = take(sizeof(float2) * ns);
+  L.yff = take(sizeof(float2) * (T.on ? T.nsp : ns));  // tiles: the padded state space
   L.part = take(sizeof(Part4) * nitems_cap);
   L.acc = take(sizeof(double) * ns);
   L.y = take(sizeof(double) * ns);
@@ -461,6 +513,15 @@ BatchLayoutFF batch_layout_ff(const pb_channels *const *chs, int n, int64_t ns, 
   L.tab_tmp = take(sizeof(double2) * maxq);
   L.eps_tmp = take(sizeof(double) * maxs);
   L.kc_tmp = take(sizeof(short4) * maxs);
+  const size_t te = c32 ? sizeof(float2) : sizeof(float4), pe = c32 ? sizeof(float) : sizeof(float4);
+  L.srp = take(T.on ? sizeof(int64_t) * (ns + 1) : 0);
+  L.tl = take(T.on ? sizeof(int2) * T.nt : 0);
+  L.lblk = take(T.on ? sizeof(int32_t) * T.nblk : 0);
+  L.binfo = take(T.on ? sizeof(int4) * T.nblk : 0);
+  L.pmap = take(T.on ? sizeof(int32_t) * ns : 0);
+  L.tc = take(T.on ? te * T.nt * dev::kTile * dev::kTile : 0);
+  L.tp = take(T.on ? pe * T.nsp * T.nbmax : 0);
+  L.err = take(sizeof(int));
   L.total = o;
   return L;
 }
@@ -507,7 +568,39 @@ int batch_upload_plan(pb_batch *b, int item_ch, cudaStream_t st, bool csr = fals
   return PB_OK;
 }
 
+// the tile sweep of every instance in one launch (the single-system kernels, with the slot map)
+int batch_sweep_tiles(pb_batch *b, cudaStream_t st) {
+  const int nsp = (int)b->nsp, nt = b->tnt;
+  if (b->prec == 2) {
+    with_c32_shape(b->tshape, [&](auto nst, auto cps, auto half) {
+      const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)b->sm_count * cps()));
+      const float2 *tc = (const float2 *)b->tc;
+      float *tp = (float *)b->tp;
+      if constexpr (decltype(half)::value)
+        dev::k_stream_c32_half<dev::MODE_COLL, nst(), cps()><<<gs, dev::kC32Threads, dev::c32_half_smem<nst()>(), st>>>(
+            b->tl, nt, tc, b->yff, nsp, b->tnb, tp, b->err, b->lblk);
+      else
+        dev::k_stream_c32<dev::MODE_COLL, nst(), cps()><<<gs, dev::kC32Threads, dev::c32_smem<nst()>(), st>>>(
+            b->tl, nt, tc, b->yff, nsp, b->tnb, tp, b->err, b->lblk);
+    });
+    PB_LAUNCHED("k_stream_c32 (batch tiles)");
+    return PB_OK;
+  }
+  const float4 *tc = (const float4 *)b->tc;
+  float4 *tp = (float4 *)b->tp;
+  const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)b->sm_count * b->tshape));
+  if (b->tshape == 3)
+    dev::k_stream_sym_half<2, 3><<<gs, dev::kSymThreads, dev::half_smem<2>(), st>>>(b->tl, nt, tc, b->yff, nsp, b->tnb,
+                                                                                    tp, b->err, b->lblk);
+  else
+    dev::k_stream_sym_half<3, 2><<<gs, dev::kSymThreads, dev::half_smem<3>(), st>>>(b->tl, nt, tc, b->yff, nsp, b->tnb,
+                                                                                    tp, b->err, b->lblk);
+  PB_LAUNCHED("k_stream_sym_half (batch tiles)");
+  return PB_OK;
+}
+
 int batch_sweep(pb_batch *b, cudaStream_t st) {
+  if (b->tiles) return batch_sweep_tiles(b, st);
   if (b->prec == 2) {
     const int64_t need = (b->nitems * 32 + dev::kBlock - 1) / dev::kBlock;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)b->sm_count * b->ctas));
@@ -542,6 +635,24 @@ int batch_sweep(pb_batch *b, cudaStream_t st) {
 // src: the stage input (f for STAGE <= 0, y after), read by the FP64-accurate epilogue
 template <int STAGE>
 int batch_fin(pb_batch *b, double *out, double *f, double dt, cudaStream_t st, const double *src) {
+  if (b->tiles) {
+    // the instances' prefactors are folded into the tiles: c = 1; states index f, y and the
+    // outputs, their padded rows the partials and the next stage's float-float input
+    const int ns = (int)b->ns;
+    if (b->prec == 2) {
+      dev::k_fin_c32<STAGE><<<(ns + 31) / 32, 256, 0, st>>>((const float *)b->tp, b->tnb, ns, ns, 1.0, src, out, f,
+                                                            b->acc, b->y, b->yff, dt, b->pmap, b->binfo);
+      PB_LAUNCHED("k_fin_c32 (batch tiles)");
+    } else {
+      dev::TileSrc ts{(const float4 *)b->tp, b->tnb, ns};
+      ts.pmap = b->pmap;
+      ts.binfo = b->binfo;
+      dev::k_fin_tiles<STAGE><<<(ns + 31) / 32, 256, 0, st>>>(ts, ns, 1.0, b->Rg, src, out, f, b->acc, b->y, b->yff,
+                                                              dt);
+      PB_LAUNCHED("k_fin_tiles (batch tiles)");
+    }
+    return PB_OK;
+  }
   if (b->prec == 2) {
     // the partials are sums of t (prefactors folded in): the plain-sum epilogue with c = -1 gives
     // I = -c A = A; it writes the next stage's float-float input like the FF batch
@@ -564,6 +675,12 @@ int batch_fin(pb_batch *b, double *out, double *f, double dt, cudaStream_t st, c
 }
 
 int batch_stage_input(pb_batch *b, const double *f, cudaStream_t st) {
+  if (b->tiles) {
+    dev::k_to_ff_map<<<(int)std::max<int64_t>(1, std::min<int64_t>((b->ns + 255) / 256, 1024)), 256, 0, st>>>(
+        f, (int)b->ns, b->pmap, b->yff);
+    PB_LAUNCHED("k_to_ff_map (batch tiles)");
+    return PB_OK;
+  }
   if (b->prec >= 1) {
     dev::k_to_ff<<<(int)std::max<int64_t>(1, std::min<int64_t>((b->ns + 255) / 256, 1024)), 256, 0, st>>>(
         f, (long long)b->ns, b->yff);
@@ -707,6 +824,72 @@ int batch_setup_ff(pb_batch *b, const pb_channels *const *chs, int n, const Batc
   return PB_OK;
 }
 
+// CTAs per SM of a tile launch shape
+int batch_tile_cps(const pb_batch *b) {
+  if (b->prec != 2) return b->tshape;
+  int c = 0;
+  with_c32_shape(b->tshape, [&](auto, auto cps, auto) { c = cps(); });
+  return c;
+}
+
+// The tile form: block table, tile list and state map on the host, then the tiles zeroed and
+// every stored pair scattered into them from the instances' branch-merged pair rows
+// (prefactors folded in).
+int batch_setup_tiles(pb_batch *b, const pb_channels *const *chs, int n, cudaStream_t st) {
+  std::vector<long long> srp((size_t)b->ns + 1, 0);
+  for (int64_t r = 0; r < b->ns; ++r) srp[r + 1] = srp[r] + b->lenp[r];
+  std::vector<int2> tl;
+  std::vector<int32_t> lblk, pmap((size_t)b->ns);
+  std::vector<int4> binfo;
+  tl.reserve((size_t)b->tnt);
+  int G0 = 0;
+  for (int i = 0; i < n; ++i) {
+    const int ns_i = (int)chs[i]->nstate, B = (ns_i + dev::kTile - 1) / dev::kTile;
+    const int tbase = (int)tl.size();
+    for (int I = 0; I < B; ++I)
+      for (int J = I; J < B; ++J) tl.push_back(make_int2(G0 + I, G0 + J));
+    for (int g = 0; g < B; ++g) {
+      lblk.push_back(g);
+      binfo.push_back(make_int4(G0, tbase, ns_i, B));
+    }
+    for (int s = 0; s < ns_i; ++s) pmap[b->soff[i] + s] = G0 * dev::kTile + s;
+    G0 += B;
+  }
+  if ((int)tl.size() != b->tnt || G0 != b->nblk) return set_error(PB_EINVAL, "pb_batch_create: tile plan mismatch");
+  PB_CUDA(cudaMemcpyAsync(b->srp, srp.data(), sizeof(long long) * srp.size(), cudaMemcpyHostToDevice, st));
+  PB_CUDA(cudaMemcpyAsync(b->tl, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice, st));
+  PB_CUDA(cudaMemcpyAsync(b->lblk, lblk.data(), sizeof(int32_t) * lblk.size(), cudaMemcpyHostToDevice, st));
+  PB_CUDA(cudaMemcpyAsync(b->binfo, binfo.data(), sizeof(int4) * binfo.size(), cudaMemcpyHostToDevice, st));
+  PB_CUDA(cudaMemcpyAsync(b->pmap, pmap.data(), sizeof(int32_t) * pmap.size(), cudaMemcpyHostToDevice, st));
+  const size_t tbytes = (size_t)b->tnt * dev::kTile * dev::kTile * (b->prec == 2 ? sizeof(float2) : sizeof(float4));
+  PB_CUDA(cudaMemsetAsync(b->tc, 0, tbytes, st));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((b->ns * 32 + 255) / 256, (int64_t)b->sm_count * 8));
+  if (b->prec == 2)
+    dev::k_tiles_scatter<true><<<grid, 256, 0, st>>>(b->srp, (int)b->ns, b->pidx, b->pA, b->pB, b->pmap, b->binfo,
+                                                     b->tc);
+  else
+    dev::k_tiles_scatter<false><<<grid, 256, 0, st>>>(b->srp, (int)b->ns, b->pidx, b->pA, b->pB, b->pmap, b->binfo,
+                                                      b->tc);
+  PB_LAUNCHED("k_tiles_scatter (batch)");
+  PB_CUDA(cudaStreamSynchronize(st));  // the host tables are released on return
+  // dynamic shared memory of every launch shape the autotuner may pick
+  const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if (b->prec == 2) {
+    for (int shape : {2, 3, 4, 7, 8})
+      with_c32_shape(shape, [&](auto nst, auto cps, auto half) {
+        if constexpr (decltype(half)::value)
+          cudaFuncSetAttribute(dev::k_stream_c32_half<dev::MODE_COLL, nst(), cps()>, A, (int)dev::c32_half_smem<nst()>());
+        else
+          cudaFuncSetAttribute(dev::k_stream_c32<dev::MODE_COLL, nst(), cps()>, A, (int)dev::c32_smem<nst()>());
+      });
+  } else {
+    cudaFuncSetAttribute(dev::k_stream_sym_half<2, 3>, A, (int)dev::half_smem<2>());
+    cudaFuncSetAttribute(dev::k_stream_sym_half<3, 2>, A, (int)dev::half_smem<3>());
+  }
+  PB_CUDA(cudaGetLastError());
+  return PB_OK;
+}
+
 }  // namespace
 
 extern "C" int pb_batch_arena_bytes(const pb_channels *const *chs, int32_t n, const pb_batch_opts *opts,
@@ -723,7 +906,8 @@ extern "C" int pb_batch_arena_bytes(const pb_channels *const *chs, int32_t n, co
       const std::vector<int64_t> lenp = batch_pair_lenp(chs, n);
       int64_t nent = 0;
       for (int64_t l : lenp) nent += l;
-      *bytes = batch_layout_ff(chs, n, ns, nent, batch_items_count(lenp, kBatchMinItem), prec == 2).total;
+      const BatchTiles T = batch_tiles_for(chs, n, prec, opts ? opts->layout : 0, nent);
+      *bytes = batch_layout_ff(chs, n, ns, nent, batch_items_count(lenp, kBatchMinItem), prec == 2, T).total;
     } else {
       pb_batch_opts o{};
       if (opts) o = *opts;
@@ -755,7 +939,13 @@ extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const p
     return set_error(PB_EINVAL, "pb_batch_create: item_channels must be 0 or a multiple of 64 >= %d", kBatchMinItem);
   if (o.ctas_per_sm < 0 || o.ctas_per_sm > 4) return set_error(PB_EINVAL, "pb_batch_create: ctas_per_sm must be 0..4");
   if (o.precision < 0 || o.precision > 2) return set_error(PB_EINVAL, "pb_batch: precision must be 0, 1 or 2");
-  if (o.layout < 0 || o.layout > 1) return set_error(PB_EINVAL, "pb_batch: layout must be 0 or 1");
+  if (o.layout < 0 || o.layout > (o.precision >= 1 ? 2 : 1))
+    return set_error(PB_EINVAL, "pb_batch: layout must be 0 or 1 (precision 0), 0..2 (precision 1, 2)");
+  if (o.layout == 2)
+    for (int i = 0; i < n; ++i)
+      if (!chs[i]->closed)
+        return set_error(PB_EINVAL, "pb_batch: layout 2 (symmetric tiles) needs channel lists built with the "
+                                    "closure check (list %d was not)", i);
   cudaStream_t st = (cudaStream_t)stream;
   pb_batch *b = new (std::nothrow) pb_batch();
   if (!b) return set_error(PB_ENOMEM, "pb_batch_create: out of host memory");
@@ -782,7 +972,8 @@ extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const p
     if (b->prec >= 1) {
       int64_t nent = 0;
       for (int64_t l : b->lenp) nent += l;
-      const BatchLayoutFF LF = batch_layout_ff(chs, n, ns, nent, b->nitems_cap, b->prec == 2);
+      const BatchTiles T = batch_tiles_for(chs, n, b->prec, o.layout, nent);
+      const BatchLayoutFF LF = batch_layout_ff(chs, n, ns, nent, b->nitems_cap, b->prec == 2, T);
       if (bytes < LF.total) {
         delete b;
         return set_error(PB_ENOMEM, "pb_batch_create: arena of %zu bytes is smaller than the %zu needed", bytes,
@@ -803,8 +994,34 @@ extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const p
       b->part = (Part4 *)(A + LF.part);
       b->acc = (double *)(A + LF.acc);
       b->y = (double *)(A + LF.y);
-      status = batch_setup_ff(b, chs, n, LF, st);
-      if (status == PB_OK && b->prec == 2 && nent > 0) {
+      b->err = (int *)(A + LF.err);
+      if (T.on) {
+        b->tiles = true;
+        b->nsp = T.nsp;
+        b->nblk = T.nblk;
+        b->tnb = T.nbmax;
+        b->tnt = T.nt;
+        b->tshape = b->prec == 2 ? 2 : 3;  // 2 stages x 3 CTAs per SM for both
+        b->srp = (long long *)(A + LF.srp);
+        b->tl = (int2 *)(A + LF.tl);
+        b->lblk = (int32_t *)(A + LF.lblk);
+        b->binfo = (int4 *)(A + LF.binfo);
+        b->pmap = (int32_t *)(A + LF.pmap);
+        b->tc = A + LF.tc;
+        b->tp = A + LF.tp;
+      }
+      {
+        // the error word; the padding of the stage input and the partial slots no instance
+        // writes stay zero
+        cudaError_t e = cudaMemsetAsync(b->err, 0, sizeof(int), st);
+        if (e == cudaSuccess && T.on) e = cudaMemsetAsync(b->yff, 0, sizeof(float2) * (size_t)T.nsp, st);
+        if (e == cudaSuccess && T.on)
+          e = cudaMemsetAsync(b->tp, 0, (b->prec == 2 ? sizeof(float) : sizeof(float4)) * (size_t)T.nsp * T.nbmax, st);
+        if (e != cudaSuccess) status = cuda_fail(e, "pb_batch_create: clear");
+      }
+      if (status == PB_OK) status = batch_setup_ff(b, chs, n, LF, st);
+      if (status == PB_OK && b->tiles) status = batch_setup_tiles(b, chs, n, st);
+      if (status == PB_OK && !b->tiles && b->prec == 2 && nent > 0) {
         dev::k_pairs_c32<<<(int)std::min<int64_t>((nent + 255) / 256, 8192), 256, 0, st>>>(b->pA, b->pB,
                                                                                            (long long)nent, b->pC);
         cudaError_t e = cudaGetLastError();
@@ -974,8 +1191,24 @@ extern "C" int pb_batch_get_info(const pb_batch *b, int64_t *nstate, int64_t *nc
     *nchannels = s;
   }
   if (state_offsets) std::memcpy(state_offsets, b->soff.data(), sizeof(int64_t) * (b->n + 1));
-  if (item_channels) *item_channels = b->item_ch;
-  if (ctas_per_sm) *ctas_per_sm = b->ctas;
+  if (item_channels) *item_channels = b->tiles ? 0 : b->item_ch;
+  if (ctas_per_sm) *ctas_per_sm = b->tiles ? batch_tile_cps(b) : b->ctas;
+  return PB_OK;
+}
+
+extern "C" int pb_batch_check(pb_batch *b, void *stream) {
+  clear_error();
+  if (!b) return set_error(PB_EINVAL, "pb_batch_check: null argument");
+  if (!b->err) return PB_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  int h = 0;
+  PB_CUDA(cudaMemcpyAsync(&h, b->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PB_CUDA(cudaStreamSynchronize(st));
+  if (h) {
+    PB_CUDA(cudaMemsetAsync(b->err, 0, sizeof(int), st));  // reported once
+    PB_CUDA(cudaStreamSynchronize(st));
+    return set_error(PB_ETIMEOUT, "a bounded device-side wait gave up (error word %d)", h);
+  }
   return PB_OK;
 }
 
@@ -1029,6 +1262,42 @@ extern "C" int pb_batch_autotune(pb_batch *b, const double *f, void *stream, int
   clear_error();
   if (!b || !f) return set_error(PB_EINVAL, "pb_batch_autotune: null argument");
   cudaStream_t st = (cudaStream_t)stream;
+  if (b->tiles) {
+    // the tile form: the launch shapes of the tile ring (stages x CTAs per SM)
+    const std::vector<int> shapes = b->prec == 2 ? std::vector<int>{2, 3, 4, 7, 8} : std::vector<int>{3, 2};
+    int bs = b->tshape;
+    float best = 1e30f;
+    cudaEvent_t e0, e1;
+    PB_CUDA(cudaEventCreate(&e0));
+    PB_CUDA(cudaEventCreate(&e1));
+    int rc = batch_stage_input(b, f, st);
+    for (size_t a = 0; a < shapes.size() && rc == PB_OK; ++a) {
+      b->tshape = shapes[a];
+      if ((rc = batch_sweep(b, st))) break;  // warm-up
+      cudaEventRecord(e0, st);
+      for (int k = 0; k < 3 && rc == PB_OK; ++k) rc = batch_sweep(b, st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        bs = shapes[a];
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->tshape = bs;
+    if (b->exec) {  // the captured step holds the previous shape
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    if (rc) return rc;
+    if (best_item) *best_item = 0;
+    if (best_ctas) *best_ctas = batch_tile_cps(b);
+    if (best_ms) *best_ms = best / 3.0;
+    return PB_OK;
+  }
   const int items[3] = {1024, 2048, 4096};
   const int ctas[3] = {2, 3, 4};
   int bi = b->item_ch, bc = b->ctas;

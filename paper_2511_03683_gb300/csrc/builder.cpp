@@ -300,6 +300,7 @@ extern "C" int pb_build_channels(const pb_model *m, pb_g2_fn g2fn, void *user, c
         return set_error(PB_ENOTCLOSED, "pb_build_channels: channel %lld has no reverse channel with equal |g|^2",
                          (long long)fail);
       }
+      ch->closed = true;
     }
   } catch (const std::bad_alloc &) {
     delete ch;

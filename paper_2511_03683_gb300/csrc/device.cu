@@ -596,9 +596,10 @@ bool merge_for(const pb_dev_opts &o) {
   return (o.variant == PB_VARIANT_FF || o.variant == PB_VARIANT_F64) && o.merge_branches != 2;
 }
 
-// symmetric tiles: FF, branch-merged, complete rows, dense_rows automatic or 3
-bool sym_for(const pb_dev_opts &o, bool merged, bool complete) {
-  return merged && complete && o.variant == PB_VARIANT_FF && (o.dense_rows == 0 || o.dense_rows == 3) &&
+// symmetric tiles: FF, branch-merged, complete rows of a list verified closed under reversal
+// (the entry of (s, p) serves (p, s) with P_in and P_out swapped), dense_rows automatic or 3
+bool sym_for(const pb_dev_opts &o, bool merged, bool complete, bool closed) {
+  return merged && complete && closed && o.variant == PB_VARIANT_FF && (o.dense_rows == 0 || o.dense_rows == 3) &&
          o.stream_mode != 2;
 }
 
@@ -756,10 +757,10 @@ extern "C" int pb_dev_arena_bytes(const pb_channels *ch, const pb_dev_opts *opts
     bool complete = false;
     const bool merged = make_plans(ch, opts, o, sm, P, S, &complete);
     const int nfin = (int)((P.ns + kFinBlock - 1) / kFinBlock);
-    const bool sym = sym_for(o, merged, complete);
+    const bool sym = sym_for(o, merged, complete, ch->closed);
     if (c32 && !sym)
       return set_error(PB_EINVAL, "pb_dev: the FP32 coefficient tiles (C32) need complete rows (every window state "
-                                  "a partner of every other: no |g| or delta cutoffs)");
+                                  "a partner of every other: no |g| or delta cutoffs) of a closure-checked list");
     *bytes = make_layout(ch, P, merged ? &S : nullptr, o.variant, o.transport != 0, nfin, sym,
                          gdense_for(ch, o, sm), o.adjoint != 0, c32 ? sizeof(float2) : sizeof(float4)).total;
   } catch (const std::bad_alloc &) {
@@ -831,11 +832,11 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->item_ch = o.item_channels;
   d->transport = o.transport != 0;
   d->nfin_blocks = (int)((d->ns + kFinBlock - 1) / kFinBlock);
-  d->sym = sym_for(o, merged, complete);
+  d->sym = sym_for(o, merged, complete, ch->closed);
   if (c32 && !d->sym) {
     delete d;
     return set_error(PB_EINVAL, "pb_dev: the FP32 coefficient tiles (C32) need complete rows (every window state a "
-                                "partner of every other: no |g| or delta cutoffs)");
+                                "partner of every other: no |g| or delta cutoffs) of a closure-checked list");
   }
   d->c32 = c32;
   d->c32_shape = o.tile_sweep;

@@ -181,6 +181,12 @@ __global__ void k_to_ff(const double *__restrict__ x, long long n, float2 *__res
     out[i] = ff_split(x[i]);
 }
 
+// the same into a padded state space: out[pmap[i]] (the padding keeps its zeros)
+__global__ void k_to_ff_map(const double *__restrict__ x, int n, const int *__restrict__ pmap,
+                            float2 *__restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[pmap[i]] = ff_split(x[i]);
+}
+
 struct ChanGeom {
   const uint32_t *col;   // packed partner | nu << 24
   const double *g2;      // |g|^2 per channel (0 on padding)
@@ -2151,9 +2157,10 @@ constexpr size_t kSymColBytes = (size_t)(kSymThreads / 32) * 2 * kTile * sizeof(
 constexpr size_t kSymBulkSmem = (size_t)kSymStages * kSymStageBytes + 64 + 2 * kSymColBytes;
 
 // the column partials of a finished off-diagonal tile: one (column, A | C) value per lane pair
-// (lanes l and l ^ 16 take warps 0-3 and 4-7), renormalised, into tp
-__device__ __forceinline__ void sym_columns_out(const float2 *__restrict__ colred, int2 IJ, int nb, int lane, int wid,
-                                                float4 *__restrict__ tp) {
+// (lanes l and l ^ 16 take warps 0-3 and 4-7), renormalised, into tp (slot: the tile's row block,
+// slotI; the batched sweep numbers a state's partner blocks within its instance)
+__device__ __forceinline__ void sym_columns_out(const float2 *__restrict__ colred, int2 IJ, int slotI, int nb, int lane,
+                                                int wid, float4 *__restrict__ tp) {
   constexpr int NW = kSymThreads / 32, WG = NW / 2;
   const int g = lane >> 4;
   const int q = (lane & 15) + 16 * wid;  // 0 .. 127
@@ -2162,7 +2169,7 @@ __device__ __forceinline__ void sym_columns_out(const float2 *__restrict__ colre
 #pragma unroll
   for (int w = 1; w < WG; ++w) acc = ff_add(acc, colred[((g * WG + w) * 2 + comp) * kTile + col]);
   acc = ff_add(acc, make_float2(__shfl_xor_sync(0xFFFFFFFFu, acc.x, 16), __shfl_xor_sync(0xFFFFFFFFu, acc.y, 16)));
-  if (g == 0) ((float2 *)tp)[2 * ((long long)(IJ.y * kTile + col) * nb + IJ.x) + comp] = acc;
+  if (g == 0) ((float2 *)tp)[2 * ((long long)(IJ.y * kTile + col) * nb + slotI) + comp] = acc;
 }
 
 __global__ void __launch_bounds__(kSymThreads, 1) k_stream_sym_bulk(const int2 *__restrict__ tiles, int nt,
@@ -2223,7 +2230,8 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_stream_sym_bulk(const int2 *
       ++issued;
       if (issued < nloc) nextIJ = tiles[(int)blockIdx.x + issued * G];
     }
-    if (k >= 1 && prevIJ.x != prevIJ.y) sym_columns_out(colred0 + ((k - 1) & 1) * (kSymColBytes / sizeof(float2)), prevIJ, nb, lane, wid, tp);
+    if (k >= 1 && prevIJ.x != prevIJ.y)
+      sym_columns_out(colred0 + ((k - 1) & 1) * (kSymColBytes / sizeof(float2)), prevIJ, prevIJ.x, nb, lane, wid, tp);
     if (!have) break;
     const int s = k % kSymStages;
     const int2 IJ = stile[s];
@@ -2324,11 +2332,14 @@ constexpr size_t half_smem() {
 }
 
 // NST stages per CTA, CPS resident CTAs per SM (3 x 2 or 2 x 3 fit in the SM's shared memory)
+// lblk (batched sweep, else null): the block index of each block within its instance, which
+// numbers the partial slots; blocks are global otherwise
 template <int NST, int CPS>
 __global__ void __launch_bounds__(kSymThreads, CPS) k_stream_sym_half(const int2 *__restrict__ tiles, int nt,
                                                                        const float4 *__restrict__ tc,
                                                                        const float2 *__restrict__ fg, int ns, int nb,
-                                                                       float4 *__restrict__ tp, int *__restrict__ err) {
+                                                                       float4 *__restrict__ tp, int *__restrict__ err,
+                                                                       const int *__restrict__ lblk = nullptr) {
   constexpr int kHalfStages = NST;
   static_assert(NST >= 2 && NST <= 4, "the ring needs 2..4 stages");
   constexpr int R = 2, NV = 2 * R, HR = kTile / 2;
@@ -2379,6 +2390,7 @@ __global__ void __launch_bounds__(kSymThreads, CPS) k_stream_sym_half(const int2
   if (tid == 0)
     for (; issued < kHalfStages && issued < nunit; ++issued) issue(issued);
   int2 prevIJ = make_int2(0, 0);  // the tile of the previous unit
+  int prevI = 0;                  // its row block's slot index
   bool ok = true;
   float cA[4][2], cC[4][2];  // column sums of the current tile, carried across its halves
   for (int u = 0; u <= nunit; ++u) {
@@ -2394,11 +2406,13 @@ __global__ void __launch_bounds__(kSymThreads, CPS) k_stream_sym_half(const int2
       ++issued;
     }
     // the previous tile's column table (written after its second half) is complete
-    if ((u & 1) == 0 && u >= 2 && prevIJ.x != prevIJ.y) sym_columns_out(colred, prevIJ, nb, lane, wid, tp);
+    if ((u & 1) == 0 && u >= 2 && prevIJ.x != prevIJ.y) sym_columns_out(colred, prevIJ, prevI, nb, lane, wid, tp);
     if (!have) break;
     const int s = u % kHalfStages, h = u & 1;
     const int2 IJ = stile[s];
+    const int Il = lblk ? lblk[IJ.x] : IJ.x, Jl = lblk ? lblk[IJ.y] : IJ.y;  // slot blocks
     prevIJ = IJ;
+    prevI = Il;
     const bool diag = IJ.x == IJ.y;
     const float4 *__restrict__ T = (const float4 *)(ssm + (size_t)s * kHalfStageBytes);
     const float2 *__restrict__ fr = (const float2 *)(ssm + (size_t)s * kHalfStageBytes + kHalfTileBytes);
@@ -2446,7 +2460,7 @@ __global__ void __launch_bounds__(kSymThreads, CPS) k_stream_sym_half(const int2
       const int idx = tj >> 2;
       if ((tj & 3) == 0) {
         const int row = IJ.x * kTile + h * HR + ti * R + (idx >> 1);
-        ((float2 *)tp)[2 * ((long long)row * nb + IJ.y) + (idx & 1)] = v[0];
+        ((float2 *)tp)[2 * ((long long)row * nb + Jl) + (idx & 1)] = v[0];
       }
     }
     if (!diag && h == 1) {
@@ -2501,6 +2515,10 @@ struct ItemSrc {
 struct TileSrc {
   const float4 *tp;  // [nsp][nb]: state-major, one partial (A hi, A lo, C hi, C lo) per block of partner states
   int nb, nsp;
+  // batched tiles: the padded row of every state and the block table (the number of partner
+  // blocks of a state is its system's, binfo[block].w); null for one system
+  const int *pmap = nullptr;
+  const int4 *binfo = nullptr;
 };
 
 // Collision epilogue fused with the RK4 stage arithmetic.
@@ -2525,10 +2543,11 @@ __device__ __forceinline__ FinIn fin_load(int r, const double *__restrict__ R, c
 }
 
 // out[r] = I (STAGE < 0), or the RK4 stage arithmetic with k_{STAGE+1} = I
+// ry: the state's row of yff when that is a padded state space (batched tiles), else r
 template <int STAGE, bool GSTATE>
 __device__ __forceinline__ void fin_stage(int r, double I, const FinIn &in, double *__restrict__ out,
                                           double *__restrict__ f, double *__restrict__ acc, double *__restrict__ y,
-                                          float2 *__restrict__ yff, double dt) {
+                                          float2 *__restrict__ yff, double dt, int ry = -1) {
   if (STAGE < 0) {
     out[r] = I;
     return;
@@ -2552,14 +2571,14 @@ __device__ __forceinline__ void fin_stage(int r, double I, const FinIn &in, doub
   if (GSTATE)
     rec_set_f(reinterpret_cast<uint4 *>(yff) + r, yn);  // yff points at the uint4 record array
   else
-    yff[r] = ff_split(yn);
+    yff[ry < 0 ? r : ry] = ff_split(yn);
 }
 
 template <bool LIT, int STAGE, bool GSTATE>
 __device__ __forceinline__ void fin_apply(int r, double A, double B, double c, const FinIn &in,
                                           double *__restrict__ out, double *__restrict__ f, double *__restrict__ acc,
-                                          double *__restrict__ y, float2 *__restrict__ yff, double dt) {
-  fin_stage<STAGE, GSTATE>(r, LIT ? -c * A : c * (A - in.y * (in.R - B)), in, out, f, acc, y, yff, dt);
+                                          double *__restrict__ y, float2 *__restrict__ yff, double dt, int ry = -1) {
+  fin_stage<STAGE, GSTATE>(r, LIT ? -c * A : c * (A - in.y * (in.R - B)), in, out, f, acc, y, yff, dt, ry);
 }
 
 template <bool LIT, int STAGE, bool GSTATE = false, typename SRC = ItemSrc>
@@ -2605,14 +2624,17 @@ __global__ void __launch_bounds__(256) k_fin_tiles(TileSrc src, int ns, double c
   // the warp's states are loaded together (up to 96 partner blocks), the rest after
   const int nb = src.nb;
   float4 w[SPW][3];
+  int nbq[SPW];  // partner blocks of each state
 #pragma unroll
   for (int q = 0; q < SPW; ++q) {
     const int r = base + SPW * wid + q;
-    const float4 *__restrict__ row = src.tp + (long long)r * nb;
+    const int pr = src.pmap && r < src.nsp ? src.pmap[r] : r;
+    nbq[q] = src.binfo && r < src.nsp ? src.binfo[pr / kTile].w : nb;
+    const float4 *__restrict__ row = src.tp + (long long)pr * nb;
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
       const int k = lane + 32 * m;
-      w[q][m] = r < src.nsp && k < nb ? row[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+      w[q][m] = r < src.nsp && k < nbq[q] ? row[k] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
   float2 v[NV];
@@ -2627,8 +2649,8 @@ __global__ void __launch_bounds__(256) k_fin_tiles(TileSrc src, int ns, double c
     }
     const int r = base + SPW * wid + q;
     if (r < src.nsp) {
-      const float4 *__restrict__ row = src.tp + (long long)r * nb;
-      for (int k = lane + 96; k < nb; k += 32) {
+      const float4 *__restrict__ row = src.tp + (long long)(src.pmap ? src.pmap[r] : r) * nb;
+      for (int k = lane + 96; k < nbq[q]; k += 32) {
         const float4 x = row[k];
         v[2 * q] = ff_add(v[2 * q], make_float2(x.x, x.y));
         v[2 * q + 1] = ff_add(v[2 * q + 1], make_float2(x.z, x.w));
@@ -2649,7 +2671,7 @@ __global__ void __launch_bounds__(256) k_fin_tiles(TileSrc src, int ns, double c
   if (RATE)
     out[r0] = c * (in.R - B);
   else
-    fin_apply<false, STAGE, false>(r0, A, B, c, in, out, f, acc, y, yff, dt);
+    fin_apply<false, STAGE, false>(r0, A, B, c, in, out, f, acc, y, yff, dt, src.pmap ? src.pmap[r0] : r0);
 }
 
 template <bool LIT, typename SRC = ItemSrc>

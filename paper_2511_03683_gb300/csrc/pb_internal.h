@@ -44,4 +44,5 @@ struct pb_channels {
   std::vector<int32_t> col;        // [nch] partner window index
   std::vector<uint8_t> nu;         // [nch] branch
   std::vector<double> g2;          // [nch] |g|^2, eV^2
+  bool closed = false;             // the builder verified that every channel's reverse exists with equal |g|^2
 };

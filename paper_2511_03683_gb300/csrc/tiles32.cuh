@@ -79,6 +79,43 @@ __global__ void k_tiles_fill_c32(const int2 *__restrict__ tiles, int nt, const f
   }
 }
 
+// The tiles of a batch (several systems in one padded block space) from their branch-merged
+// pair rows, which need not be complete: one warp per row s, every stored pair (s, p) whose
+// local block pair (I, J) lies in the upper triangle (I <= J) written to its tile entry; the
+// tiles were zeroed before, pairs without channels stay zero, and zero padding entries are
+// skipped.  binfo[g] of block g = (first block of its system, the system's first tile, its
+// states, its blocks); tiles are numbered row-major over the system's upper block triangle.
+// C32: the pairs rounded to FP32 with their ratio kept, else float-float (float4 per entry).
+template <bool C32>
+__global__ void k_tiles_scatter(const long long *__restrict__ srp, int ns, const uint32_t *__restrict__ pidx,
+                                const float2 *__restrict__ coefA, const float2 *__restrict__ coefB,
+                                const int *__restrict__ pmap, const int4 *__restrict__ binfo, void *__restrict__ tc) {
+  const int lane = threadIdx.x & 31;
+  const int w0 = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)(((long long)gridDim.x * blockDim.x) >> 5);
+  for (int r = w0; r < ns; r += nw) {
+    const int pr = pmap[r];
+    const int4 bi = binfo[pr / kTile];
+    const int I = pr / kTile - bi.x;
+    for (long long e = srp[r] + lane; e < srp[r + 1]; e += 32) {
+      const float2 a = coefA[e], b = coefB[e];
+      if (a.x == 0.f && a.y == 0.f && b.x == 0.f && b.y == 0.f) continue;
+      const int pp = pmap[pidx[e]];
+      const int J = pp / kTile - bi.x;
+      if (J < I) continue;
+      const long long t = (long long)bi.y + (long long)I * (2 * bi.w - I + 1) / 2 + (J - I);
+      const long long k = t * kTile * kTile + (pr % kTile) * kTile + pp % kTile;
+      const double pin = ff_to_double(a.x, a.y), pout = pin + ff_to_double(b.x, b.y);
+      if (C32) {
+        ((float2 *)tc)[k] = c32_round_pair(pin, pout);
+      } else {
+        const float2 x = ff_split(pin), y = ff_split(pout);
+        ((float4 *)tc)[k] = make_float4(x.x, x.y, y.x, y.y);
+      }
+    }
+  }
+}
+
 // t(s, p) above from the entry's rounded (P_in, P_out) = (a, b) and the float-float occupations
 // fs of s and fp of p
 __device__ __forceinline__ float c32_term(float a, float b, float2 fs, float2 fp) {
@@ -118,14 +155,15 @@ __device__ __forceinline__ void f32_reduce_scatter(float (&v)[NV], int lane) {
 }
 
 // the column sums of a finished off-diagonal tile: threads 0..63 add the 8 warps' values of
-// one column each and write them to the column state's partial for block IJ.x
-__device__ __forceinline__ void c32_columns_out(const float *__restrict__ colred, int2 IJ, int nb, int tid,
+// one column each and write them to the column state's partial for the tile's row block (slot
+// slotI)
+__device__ __forceinline__ void c32_columns_out(const float *__restrict__ colred, int2 IJ, int slotI, int nb, int tid,
                                                 float *__restrict__ tp) {
   if (tid >= kTile) return;
   float acc = colred[tid];
 #pragma unroll
   for (int w = 1; w < kC32Threads / 32; ++w) acc = __fadd_rn(acc, colred[w * kTile + tid]);
-  tp[(long long)(IJ.y * kTile + tid) * nb + IJ.x] = acc;
+  tp[(long long)(IJ.y * kTile + tid) * nb + slotI] = acc;
 }
 
 // One persistent 256-thread CTA (CPS per SM) streams its share of the tiles through NST
@@ -136,11 +174,14 @@ __device__ __forceinline__ void c32_columns_out(const float *__restrict__ colred
 // 1/tau_s summands P_out + f_p d (row s) and P_in - f_s d (column p, the reverse channel), each
 // with its f_l term.  The per-warp column table is double buffered and combined in the next
 // iteration, so a tile costs one CTA barrier.
+// lblk (batched sweep, else null): the block index of each block within its instance, which
+// numbers the partial slots
 template <int MODE, int NST, int CPS>
 __global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32(const int2 *__restrict__ tiles, int nt,
                                                                   const float2 *__restrict__ tc,
                                                                   const float2 *__restrict__ fg, int ns, int nb,
-                                                                  float *__restrict__ tp, int *__restrict__ err) {
+                                                                  float *__restrict__ tp, int *__restrict__ err,
+                                                                  const int *__restrict__ lblk = nullptr) {
   // the stage of tile k - 1 is refilled (with tile k - 1 + NST) only after the wait for tile k, so
   // one stage would wait for a copy not yet issued
   static_assert(NST >= 2 && NST <= 8, "the ring needs 2..8 stages");
@@ -182,6 +223,7 @@ __global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32(const int2 *__r
   int2 nextIJ = make_int2(0, 0);
   if (tid == 0 && issued < nloc) nextIJ = tiles[(int)blockIdx.x + issued * G];
   int2 prevIJ = make_int2(0, 0);
+  int prevI = 0;
   bool ok = true;
   for (int k = 0; k <= nloc; ++k) {
     const bool have = k < nloc;
@@ -195,11 +237,14 @@ __global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32(const int2 *__r
       ++issued;
       if (issued < nloc) nextIJ = tiles[(int)blockIdx.x + issued * G];
     }
-    if (k >= 1 && prevIJ.x != prevIJ.y) c32_columns_out(colred0 + ((k - 1) & 1) * kC32ColFloats, prevIJ, nb, tid, tp);
+    if (k >= 1 && prevIJ.x != prevIJ.y)
+      c32_columns_out(colred0 + ((k - 1) & 1) * kC32ColFloats, prevIJ, prevI, nb, tid, tp);
     if (!have) break;
     const int s = k % NST;
     const int2 IJ = stile[s];
+    const int Il = lblk ? lblk[IJ.x] : IJ.x, Jl = lblk ? lblk[IJ.y] : IJ.y;  // slot blocks
     prevIJ = IJ;
+    prevI = Il;
     const bool diag = IJ.x == IJ.y;
     const float2 *__restrict__ T = (const float2 *)(ssm + (size_t)s * kC32StageBytes);
     const float2 *__restrict__ fr = (const float2 *)(ssm + (size_t)s * kC32StageBytes + kC32TileBytes);
@@ -233,7 +278,7 @@ __global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32(const int2 *__r
     }
     // rows: the 16 lanes of a half-warp share them; lanes 4i .. 4i + 3 end with the total of row i
     f32_reduce_scatter<R, 8>(rv, lane);
-    if ((tj & 3) == 0) tp[(long long)(IJ.x * kTile + ti * R + (tj >> 2)) * nb + IJ.y] = rv[0];
+    if ((tj & 3) == 0) tp[(long long)(IJ.x * kTile + ti * R + (tj >> 2)) * nb + Jl] = rv[0];
     if (!diag) {
       // columns: lanes tj and tj + 16 share them (one level), then the 8 warps (next iteration)
       float *colred = colred0 + (k & 1) * kC32ColFloats;
@@ -274,7 +319,8 @@ template <int MODE, int NST, int CPS>
 __global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32_half(const int2 *__restrict__ tiles, int nt,
                                                                        const float2 *__restrict__ tc,
                                                                        const float2 *__restrict__ fg, int ns, int nb,
-                                                                       float *__restrict__ tp, int *__restrict__ err) {
+                                                                       float *__restrict__ tp, int *__restrict__ err,
+                                                                       const int *__restrict__ lblk = nullptr) {
   static_assert(NST >= 2 && NST <= 8, "the ring needs 2..8 stages");
   constexpr int R = 2, HR = kTile / 2;
   extern __shared__ __align__(128) unsigned char ssm[];
@@ -322,6 +368,7 @@ __global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32_half(const int2
   if (tid == 0)
     for (; issued < NST && issued < nunit; ++issued) issue(issued);
   int2 prevIJ = make_int2(0, 0);
+  int prevI = 0;
   bool ok = true;
   float cv[4];  // column sums of the current tile, carried across its halves
   for (int u = 0; u <= nunit; ++u) {
@@ -335,11 +382,13 @@ __global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32_half(const int2
       issue(issued);
       ++issued;
     }
-    if ((u & 1) == 0 && u >= 2 && prevIJ.x != prevIJ.y) c32_columns_out(colred, prevIJ, nb, tid, tp);
+    if ((u & 1) == 0 && u >= 2 && prevIJ.x != prevIJ.y) c32_columns_out(colred, prevIJ, prevI, nb, tid, tp);
     if (!have) break;
     const int s = u % NST, h = u & 1;
     const int2 IJ = stile[s];
+    const int Il = lblk ? lblk[IJ.x] : IJ.x, Jl = lblk ? lblk[IJ.y] : IJ.y;  // slot blocks
     prevIJ = IJ;
+    prevI = Il;
     const bool diag = IJ.x == IJ.y;
     const float2 *__restrict__ T = (const float2 *)(ssm + (size_t)s * kC32HalfStageBytes);
     const float2 *__restrict__ fr = (const float2 *)(ssm + (size_t)s * kC32HalfStageBytes + kC32HalfBytes);
@@ -376,7 +425,7 @@ __global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32_half(const int2
     }
     // rows: the 16 lanes of a half-warp share them; lanes 8i .. 8i + 7 end with the total of row i
     f32_reduce_scatter<R, 8>(rv, lane);
-    if ((tj & 7) == 0) tp[(long long)(IJ.x * kTile + h * HR + ti * R + (tj >> 3)) * nb + IJ.y] = rv[0];
+    if ((tj & 7) == 0) tp[(long long)(IJ.x * kTile + h * HR + ti * R + (tj >> 3)) * nb + Jl] = rv[0];
     if (!diag && h == 1) {
       // columns of the whole tile: lanes tj and tj + 16 share them (one level), then the warps
       // (after the next unit's barrier)
@@ -463,11 +512,15 @@ __global__ void k_pairs_c32(const float2 *__restrict__ A, const float2 *__restri
 // partials of SPC / 8 states (lanes over the blocks in float-float, then one 32-lane float-float
 // reduce-scatter of the SPC / 8 values), and warp 0 applies the prefactor and the RK4 stage
 // arithmetic in FP64, one lane per state.
+// pmap, binfo (batched tiles, else null): each state's padded row and the block table, whose
+// .w gives the partner blocks of a state's system; nsp is then the number of states
 template <int STAGE, bool RATE = false, int SPC = 32>
 __global__ void __launch_bounds__(256) k_fin_c32(const float *__restrict__ tp, int nb, int nsp, int ns, double c,
                                                  const double *__restrict__ ysrc, double *__restrict__ out,
                                                  double *__restrict__ f, double *__restrict__ acc,
-                                                 double *__restrict__ y, float2 *__restrict__ yff, double dt) {
+                                                 double *__restrict__ y, float2 *__restrict__ yff, double dt,
+                                                 const int *__restrict__ pmap = nullptr,
+                                                 const int4 *__restrict__ binfo = nullptr) {
   constexpr int SPW = SPC / 8, LPV = 32 / SPW;  // states per warp, lanes per state after the reduce-scatter
   __shared__ float2 tot[SPC];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -484,8 +537,9 @@ __global__ void __launch_bounds__(256) k_fin_c32(const float *__restrict__ tp, i
     const int r = base + SPW * wid + q;
     v[q] = make_float2(0.f, 0.f);
     if (r < nsp) {
-      const float *__restrict__ row = tp + (long long)r * nb;
-      for (int k = lane; k < nb; k += 32) v[q] = ff_add(v[q], make_float2(row[k], 0.f));
+      const int pr = pmap ? pmap[r] : r, nbr = binfo ? binfo[pr / kTile].w : nb;
+      const float *__restrict__ row = tp + (long long)pr * nb;
+      for (int k = lane; k < nbr; k += 32) v[q] = ff_add(v[q], make_float2(row[k], 0.f));
     }
   }
   ff_reduce_scatter<SPW, 16>(v, lane);
@@ -498,7 +552,7 @@ __global__ void __launch_bounds__(256) k_fin_c32(const float *__restrict__ tp, i
     out[r0] = I;
     return;
   }
-  fin_stage<STAGE, false>(r0, I, in, out, f, acc, y, yff, dt);
+  fin_stage<STAGE, false>(r0, I, in, out, f, acc, y, yff, dt, pmap ? pmap[r0] : r0);
 }
 
 }  // namespace dev

@@ -620,6 +620,28 @@ def test_c32_rk4(pb):
     dev.check()
 
 
+def test_symmetric_tiles_need_a_closure_checked_list(pb):
+    """The tiles serve each pair (s, p) and its reverse from one entry, which holds only when the
+    reverse channels exist with equal |g|^2: a list built without the closure check streams the
+    rows and meets the oracle all the same; C32, which needs the tiles, refuses it."""
+    m = synth.make_window4(12)
+    o = oracle.Oracle(m)
+    checked_ch = pb.Channels.from_model(m)
+    checked = pb.Device(checked_ch)
+    unchecked_ch = pb.Channels.from_model(m, check_closure=False)
+    unchecked = pb.Device(unchecked_ch)
+    # the streamed bytes of the positional rows (dense_rows 1), not of the tiles
+    rows = pb.Device(checked_ch, dense_rows=1)
+    assert unchecked.bytes_per_channel == rows.bytes_per_channel != checked.bytes_per_channel
+    f = np.random.default_rng(57).uniform(0, 1, o.nstate)
+    ref, ab = o.collision(f, with_abs=True)
+    check_I(unchecked.collision(T(f)).cpu().numpy(), ref, ab)
+    check_I(checked.collision(T(f)).cpu().numpy(), ref, ab)
+    with pytest.raises(pb.PBError) as e:
+        pb.Device(unchecked_ch, variant="c32")
+    assert e.value.code == pb.PB_EINVAL
+
+
 def test_c32_needs_complete_rows_and_the_tile_sweep(pb):
     m = synth.make_window4(16)
     ch = pb.Channels.from_model(m, g2_min=5e-4, delta_nsigma=4.0)
