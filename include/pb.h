@@ -267,9 +267,13 @@ int pb_collision(pb_dev *dev, const double *f, double *dfdt, void *stream);
 /* Measurement aid (the paper has no counterpart): the average device duration of the
  * collision sweep kernel alone, from CUDA events recorded on `stream` around `nlaunch`
  * back-to-back launches of it on f (device double[nstate]); the stage-input conversion runs
- * once before the first event and no finaliser runs.  Leaves the partial sums of the last
- * launch in the handle's scratch; synchronises `stream`.  nlaunch in 1..10000. */
-int pb_dev_time_sweep(pb_dev *dev, const double *f, int32_t nlaunch, float *avg_ms, void *stream);
+ * once before the first event and no finaliser runs.  order 0: every launch takes the tile
+ * list in its stored order; 1: the launches alternate between that order and the reverse, as
+ * the RK4 stages of the symmetric-tile sweeps do (each then starts on the tiles the launch before
+ * it left in L2).  Leaves the partial sums of the last launch in the handle's scratch;
+ * synchronises `stream`.  nlaunch in 1..10000. */
+int pb_dev_time_sweep(pb_dev *dev, const double *f, int32_t nlaunch, int32_t order, float *avg_ms,
+                      void *stream);
 
 /* Scattering rates 1/tau_s = -dI_s/df_s
  *   = (2pi/hbar)(1/N_q) sum |g|^2 [G(x+w)(N+f_p) + G(x-w)(N+1-f_p)],  x = eps_s - eps_p.

@@ -111,7 +111,7 @@ def lib() -> ctypes.CDLL:
         "pb_dev_get_info": [vp, ctypes.POINTER(_DevInfo)],
         "pb_dev_check": [vp, vp],
         "pb_dev_selftest_wait": [vp, i32, vp],
-        "pb_dev_time_sweep": [vp, vp, i32, ctypes.POINTER(ctypes.c_float), vp],
+        "pb_dev_time_sweep": [vp, vp, i32, i32, ctypes.POINTER(ctypes.c_float), vp],
         "pb_collision": [vp, vp, vp, vp],
         "pb_collision_static": [vp, vp, vp, vp],
         "pb_scatter_rates": [vp, vp, vp, vp],
@@ -350,12 +350,13 @@ class Device:
         wait_us microseconds); the next check() raises PBError(PB_ETIMEOUT) and clears it."""
         _check(lib().pb_dev_selftest_wait(self._h, int(wait_us), _stream_ptr(stream)))
 
-    def time_sweep(self, f, nlaunch: int = 20, stream=None) -> float:
+    def time_sweep(self, f, nlaunch: int = 20, order: int = 0, stream=None) -> float:
         """Average device milliseconds of the collision sweep kernel alone (CUDA events on
-        the stream around nlaunch back-to-back launches)."""
+        the stream around nlaunch back-to-back launches); order 1 alternates the tile order of
+        the launches as the RK4 stages do."""
         ms = ctypes.c_float(0.0)
-        _check(lib().pb_dev_time_sweep(self._h, _dev_vec(f, self.nstate, "f"), int(nlaunch), ctypes.byref(ms),
-                                       _stream_ptr(stream)))
+        _check(lib().pb_dev_time_sweep(self._h, _dev_vec(f, self.nstate, "f"), int(nlaunch), int(order),
+                                       ctypes.byref(ms), _stream_ptr(stream)))
         return float(ms.value)
 
     def rates(self, f, out=None, stream=None):

@@ -281,6 +281,7 @@ struct pb_batch {
   bool tiles = false;
   int64_t nsp = 0;
   int nblk = 0, tnb = 0, tnt = 0, tshape = 0;
+  int rev = 0;  // the next tile sweep takes the tile list from its end (alternating RK4 stages)
   int2 *tl = nullptr;
   int *lblk = nullptr, *pmap = nullptr;
   int4 *binfo = nullptr;
@@ -578,10 +579,10 @@ int batch_sweep_tiles(pb_batch *b, cudaStream_t st) {
       float *tp = (float *)b->tp;
       if constexpr (decltype(half)::value)
         dev::k_stream_c32_half<dev::MODE_COLL, nst(), cps()><<<gs, dev::kC32Threads, dev::c32_half_smem<nst()>(), st>>>(
-            b->tl, nt, tc, b->yff, nsp, b->tnb, tp, b->err, b->lblk);
+            b->tl, nt, tc, b->yff, nsp, b->tnb, tp, b->err, b->lblk, b->rev);
       else
         dev::k_stream_c32<dev::MODE_COLL, nst(), cps()><<<gs, dev::kC32Threads, dev::c32_smem<nst()>(), st>>>(
-            b->tl, nt, tc, b->yff, nsp, b->tnb, tp, b->err, b->lblk);
+            b->tl, nt, tc, b->yff, nsp, b->tnb, tp, b->err, b->lblk, b->rev);
     });
     PB_LAUNCHED("k_stream_c32 (batch tiles)");
     return PB_OK;
@@ -591,10 +592,10 @@ int batch_sweep_tiles(pb_batch *b, cudaStream_t st) {
   const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)b->sm_count * b->tshape));
   if (b->tshape == 3)
     dev::k_stream_sym_half<2, 3><<<gs, dev::kSymThreads, dev::half_smem<2>(), st>>>(b->tl, nt, tc, b->yff, nsp, b->tnb,
-                                                                                    tp, b->err, b->lblk);
+                                                                                    tp, b->err, b->lblk, b->rev);
   else
     dev::k_stream_sym_half<3, 2><<<gs, dev::kSymThreads, dev::half_smem<3>(), st>>>(b->tl, nt, tc, b->yff, nsp, b->tnb,
-                                                                                    tp, b->err, b->lblk);
+                                                                                    tp, b->err, b->lblk, b->rev);
   PB_LAUNCHED("k_stream_sym_half (batch tiles)");
   return PB_OK;
 }
@@ -692,13 +693,25 @@ int batch_stage_input(pb_batch *b, const double *f, cudaStream_t st) {
   return PB_OK;
 }
 
-int batch_rk4_launches(pb_batch *b, double *f, double dt, cudaStream_t st) {
+// the tile sweeps of stages 2 and 4 take the tile list from its end (each starts on the tiles
+// the sweep before it left in L2)
+int batch_rk4_stages(pb_batch *b, double *f, double dt, cudaStream_t st) {
   int rc;
+  b->rev = 0;
   if ((rc = batch_sweep(b, st)) || (rc = batch_fin<0>(b, nullptr, f, dt, st, f))) return rc;
+  b->rev = 1;
   if ((rc = batch_sweep(b, st)) || (rc = batch_fin<1>(b, nullptr, f, dt, st, b->y))) return rc;
+  b->rev = 0;
   if ((rc = batch_sweep(b, st)) || (rc = batch_fin<2>(b, nullptr, f, dt, st, b->y))) return rc;
+  b->rev = 1;
   if ((rc = batch_sweep(b, st)) || (rc = batch_fin<3>(b, nullptr, f, dt, st, b->y))) return rc;
   return PB_OK;
+}
+
+int batch_rk4_launches(pb_batch *b, double *f, double dt, cudaStream_t st) {
+  const int rc = batch_rk4_stages(b, f, dt, st);
+  b->rev = 0;
+  return rc;
 }
 
 }  // namespace

@@ -451,6 +451,9 @@ struct pb_dev {
   int half_cps = 3;       // its resident CTAs per SM: 3 (two stages each) or 2 (three stages)
   bool c32 = false;
   int c32_shape = 2;  // pb_dev_opts.tile_sweep: the launch shape (with_c32_shape)
+  // the next tile sweep takes the tile list from its end (the RK4 stages alternate, so that each
+  // sweep starts on the tiles the previous one left in L2)
+  int rev = 0;
   float2 *tc32 = nullptr;
   int64_t *rp_real = nullptr;  // unpadded CSR row offsets [ns+1]
   float2 *vjpG = nullptr;      // adjoint gather table [ns][3]
@@ -1353,18 +1356,18 @@ int launch_stream_t(pb_dev *d, int mode, const double *fd, const float2 *fff, co
         const size_t sm32 = dev::c32_half_smem<nst()>();
         if (coll)
           dev::k_stream_c32_half<dev::MODE_COLL, nst(), cps()><<<gs, dev::kC32Threads, sm32, st>>>(
-              d->tiles, d->td.nt, d->tc32, fff, ns, d->td.nb, tp, d->err);
+              d->tiles, d->td.nt, d->tc32, fff, ns, d->td.nb, tp, d->err, nullptr, d->rev);
         else
           dev::k_stream_c32_half<dev::MODE_RATE, nst(), cps()><<<gs, dev::kC32Threads, sm32, st>>>(
-              d->tiles, d->td.nt, d->tc32, fff, ns, d->td.nb, tp, d->err);
+              d->tiles, d->td.nt, d->tc32, fff, ns, d->td.nb, tp, d->err, nullptr, d->rev);
       } else {
         const size_t sm32 = dev::c32_smem<nst()>();
         if (coll)
           dev::k_stream_c32<dev::MODE_COLL, nst(), cps()><<<gs, dev::kC32Threads, sm32, st>>>(
-              d->tiles, d->td.nt, d->tc32, fff, ns, d->td.nb, tp, d->err);
+              d->tiles, d->td.nt, d->tc32, fff, ns, d->td.nb, tp, d->err, nullptr, d->rev);
         else
           dev::k_stream_c32<dev::MODE_RATE, nst(), cps()><<<gs, dev::kC32Threads, sm32, st>>>(
-              d->tiles, d->td.nt, d->tc32, fff, ns, d->td.nb, tp, d->err);
+              d->tiles, d->td.nt, d->tc32, fff, ns, d->td.nb, tp, d->err, nullptr, d->rev);
       }
     });
   } else if (d->variant == PB_VARIANT_FF && d->sym && !d->c32 && part == d->part) {
@@ -1374,10 +1377,10 @@ int launch_stream_t(pb_dev *d, int mode, const double *fd, const float2 *fff, co
       const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(d->td.nt, (int64_t)d->sm_count * cps));
       if (cps == 3)
         dev::k_stream_sym_half<2, 3><<<gs, dev::kSymThreads, dev::half_smem<2>(), st>>>(
-            d->tiles, d->td.nt, d->tcoef, fff, ns, d->td.nb, d->tpart, d->err);
+            d->tiles, d->td.nt, d->tcoef, fff, ns, d->td.nb, d->tpart, d->err, nullptr, d->rev);
       else
         dev::k_stream_sym_half<3, 2><<<gs, dev::kSymThreads, dev::half_smem<3>(), st>>>(
-            d->tiles, d->td.nt, d->tcoef, fff, ns, d->td.nb, d->tpart, d->err);
+            d->tiles, d->td.nt, d->tcoef, fff, ns, d->td.nb, d->tpart, d->err, nullptr, d->rev);
     } else if (d->sym_nt && fff == d->yff) {  // the bulk copies read f from this padded arena buffer
       const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(d->td.nt, (int64_t)d->sm_count));
       dev::k_stream_sym_bulk<<<gs, dev::kSymThreads, dev::kSymBulkSmem, st>>>(d->tiles, d->td.nt, d->tcoef, fff, ns,
@@ -1514,21 +1517,34 @@ int stage_input(pb_dev *d, const double *f, cudaStream_t st) {
 }
 
 // One RK4 step on the device vector f (the stage-0 ff copy must already be in yff).
-int rk4_launches(pb_dev *d, double *f, double dt, cudaStream_t st) {
+// the four stages; the tile sweeps of stages 2 and 4 take the tile list from its end, so that
+// each starts on the tiles the sweep before it left in L2 (and the next step's first sweep on
+// those of the fourth)
+int rk4_stages(pb_dev *d, double *f, double dt, cudaStream_t st) {
   int rc;
+  d->rev = 0;
   if ((rc = launch_stream(d, dev::MODE_COLL, f, d->yff, st))) return rc;
   launch_fin<0>(d, f, nullptr, f, dt, st);
   PB_LAUNCHED("rk4 stage 1");
+  d->rev = 1;
   if ((rc = launch_stream(d, dev::MODE_COLL, d->y, d->yff, st))) return rc;
   launch_fin<1>(d, d->y, nullptr, f, dt, st);
   PB_LAUNCHED("rk4 stage 2");
+  d->rev = 0;
   if ((rc = launch_stream(d, dev::MODE_COLL, d->y, d->yff, st))) return rc;
   launch_fin<2>(d, d->y, nullptr, f, dt, st);
   PB_LAUNCHED("rk4 stage 3");
+  d->rev = 1;
   if ((rc = launch_stream(d, dev::MODE_COLL, d->y, d->yff, st))) return rc;
   launch_fin<3>(d, d->y, nullptr, f, dt, st);
   PB_LAUNCHED("rk4 stage 4");
   return PB_OK;
+}
+
+int rk4_launches(pb_dev *d, double *f, double dt, cudaStream_t st) {
+  const int rc = rk4_stages(d, f, dt, st);
+  d->rev = 0;
+  return rc;
 }
 
 int ensure_rk_graph(pb_dev *d, double *f, double dt) {
@@ -1710,10 +1726,12 @@ extern "C" int pb_collision(pb_dev *d, const double *f, double *dfdt, void *stre
   });
 }
 
-extern "C" int pb_dev_time_sweep(pb_dev *d, const double *f, int32_t nlaunch, float *avg_ms, void *stream) {
+extern "C" int pb_dev_time_sweep(pb_dev *d, const double *f, int32_t nlaunch, int32_t order, float *avg_ms,
+                                 void *stream) {
   clear_error();
   if (!d || !f || !avg_ms) return set_error(PB_EINVAL, "pb_dev_time_sweep: null argument");
   if (nlaunch < 1 || nlaunch > 10000) return set_error(PB_EINVAL, "pb_dev_time_sweep: nlaunch must be 1..10000");
+  if (order < 0 || order > 1) return set_error(PB_EINVAL, "pb_dev_time_sweep: order must be 0 or 1");
   cudaStream_t st = (cudaStream_t)stream;
   int rc;
   if ((rc = stage_input(d, f, st))) return rc;
@@ -1724,7 +1742,11 @@ extern "C" int pb_dev_time_sweep(pb_dev *d, const double *f, int32_t nlaunch, fl
     return set_error(PB_ECUDA, "pb_dev_time_sweep: cudaEventCreate");
   }
   cudaError_t e = cudaEventRecord(e0, st);
-  for (int i = 0; i < nlaunch && e == cudaSuccess && rc == PB_OK; ++i) rc = launch_stream(d, dev::MODE_COLL, f, d->yff, st);
+  for (int i = 0; i < nlaunch && e == cudaSuccess && rc == PB_OK; ++i) {
+    d->rev = order == 1 ? (i & 1) : 0;
+    rc = launch_stream(d, dev::MODE_COLL, f, d->yff, st);
+  }
+  d->rev = 0;
   if (e == cudaSuccess && rc == PB_OK) e = cudaEventRecord(e1, st);
   if (e == cudaSuccess && rc == PB_OK) e = cudaEventSynchronize(e1);
   float ms = 0.f;

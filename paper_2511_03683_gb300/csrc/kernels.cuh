@@ -2333,13 +2333,16 @@ constexpr size_t half_smem() {
 
 // NST stages per CTA, CPS resident CTAs per SM (3 x 2 or 2 x 3 fit in the SM's shared memory)
 // lblk (batched sweep, else null): the block index of each block within its instance, which
-// numbers the partial slots; blocks are global otherwise
+// numbers the partial slots; blocks are global otherwise.  rev: take the tile list from its end
+// (tile nt - 1 - t in place of t), so that a sweep following one in list order starts on the
+// tiles the L2 still holds; the partials do not depend on the order.
 template <int NST, int CPS>
 __global__ void __launch_bounds__(kSymThreads, CPS) k_stream_sym_half(const int2 *__restrict__ tiles, int nt,
                                                                        const float4 *__restrict__ tc,
                                                                        const float2 *__restrict__ fg, int ns, int nb,
                                                                        float4 *__restrict__ tp, int *__restrict__ err,
-                                                                       const int *__restrict__ lblk = nullptr) {
+                                                                       const int *__restrict__ lblk = nullptr,
+                                                                       int rev = 0) {
   constexpr int kHalfStages = NST;
   static_assert(NST >= 2 && NST <= 4, "the ring needs 2..4 stages");
   constexpr int R = 2, NV = 2 * R, HR = kTile / 2;
@@ -2363,18 +2366,22 @@ __global__ void __launch_bounds__(kSymThreads, CPS) k_stream_sym_half(const int2
   __syncthreads();
   // thread 0: units are issued in order; issIJ is the tile being issued, aheadIJ the next one
   int issued = 0;
+  auto tix = [&](int k) {  // the CTA's k-th tile
+    const int t = (int)blockIdx.x + k * G;
+    return rev ? nt - 1 - t : t;
+  };
   int2 issIJ = make_int2(0, 0), aheadIJ = make_int2(0, 0);
   if (tid == 0 && nloc > 0) {
-    issIJ = tiles[blockIdx.x];
-    if (nloc > 1) aheadIJ = tiles[(int)blockIdx.x + G];
+    issIJ = tiles[tix(0)];
+    if (nloc > 1) aheadIJ = tiles[tix(1)];
   }
   auto issue = [&](int v) {  // unit v = 2 k + h: half h of the CTA's tile k
     const int k = v >> 1, h = v & 1, s = v % kHalfStages;
     if (h == 0 && k > 0) {
       issIJ = aheadIJ;
-      if (k + 1 < nloc) aheadIJ = tiles[(int)blockIdx.x + (k + 1) * G];
+      if (k + 1 < nloc) aheadIJ = tiles[tix(k + 1)];
     }
-    const int t = (int)blockIdx.x + k * G;
+    const int t = tix(k);
     stile[s] = issIJ;
     unsigned char *buf = ssm + (size_t)s * kHalfStageBytes;
     const int nr = min(HR, ns - (issIJ.x * kTile + h * HR)), nc = min(kTile, ns - issIJ.y * kTile);

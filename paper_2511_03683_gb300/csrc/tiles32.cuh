@@ -175,13 +175,15 @@ __device__ __forceinline__ void c32_columns_out(const float *__restrict__ colred
 // with its f_l term.  The per-warp column table is double buffered and combined in the next
 // iteration, so a tile costs one CTA barrier.
 // lblk (batched sweep, else null): the block index of each block within its instance, which
-// numbers the partial slots
+// numbers the partial slots.  rev: take the tile list from its end (tile nt - 1 - t in place of
+// t), so that a sweep following one in list order starts on the tiles the L2 still holds.
 template <int MODE, int NST, int CPS>
 __global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32(const int2 *__restrict__ tiles, int nt,
                                                                   const float2 *__restrict__ tc,
                                                                   const float2 *__restrict__ fg, int ns, int nb,
                                                                   float *__restrict__ tp, int *__restrict__ err,
-                                                                  const int *__restrict__ lblk = nullptr) {
+                                                                  const int *__restrict__ lblk = nullptr,
+                                                                  int rev = 0) {
   // the stage of tile k - 1 is refilled (with tile k - 1 + NST) only after the wait for tile k, so
   // one stage would wait for a copy not yet issued
   static_assert(NST >= 2 && NST <= 8, "the ring needs 2..8 stages");
@@ -204,9 +206,13 @@ __global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32(const int2 *__r
   fence_proxy_async();
   __syncthreads();
   int issued = 0;
+  auto tix = [&](int k) {  // the CTA's k-th tile
+    const int t = (int)blockIdx.x + k * G;
+    return rev ? nt - 1 - t : t;
+  };
   auto issue = [&](int k, int2 IJ) {
     const int s = k % NST;
-    const int t = (int)blockIdx.x + k * G;
+    const int t = tix(k);
     stile[s] = IJ;
     unsigned char *buf = ssm + (size_t)s * kC32StageBytes;
     const int nr = min(kTile, ns - IJ.x * kTile), nc = min(kTile, ns - IJ.y * kTile);
@@ -219,9 +225,9 @@ __global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32(const int2 *__r
     bulk_g2s(buf + kC32TileBytes + kTile * sizeof(float2), fg + (size_t)IJ.y * kTile, bc, bars + s);
   };
   if (tid == 0)
-    for (; issued < NST && issued < nloc; ++issued) issue(issued, tiles[(int)blockIdx.x + issued * G]);
+    for (; issued < NST && issued < nloc; ++issued) issue(issued, tiles[tix(issued)]);
   int2 nextIJ = make_int2(0, 0);
-  if (tid == 0 && issued < nloc) nextIJ = tiles[(int)blockIdx.x + issued * G];
+  if (tid == 0 && issued < nloc) nextIJ = tiles[tix(issued)];
   int2 prevIJ = make_int2(0, 0);
   int prevI = 0;
   bool ok = true;
@@ -235,7 +241,7 @@ __global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32(const int2 *__r
       fence_proxy_async();  // the generic reads of tile k-1's stage before its refill
       issue(issued, nextIJ);
       ++issued;
-      if (issued < nloc) nextIJ = tiles[(int)blockIdx.x + issued * G];
+      if (issued < nloc) nextIJ = tiles[tix(issued)];
     }
     if (k >= 1 && prevIJ.x != prevIJ.y)
       c32_columns_out(colred0 + ((k - 1) & 1) * kC32ColFloats, prevIJ, prevI, nb, tid, tp);
@@ -320,7 +326,8 @@ __global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32_half(const int2
                                                                        const float2 *__restrict__ tc,
                                                                        const float2 *__restrict__ fg, int ns, int nb,
                                                                        float *__restrict__ tp, int *__restrict__ err,
-                                                                       const int *__restrict__ lblk = nullptr) {
+                                                                       const int *__restrict__ lblk = nullptr,
+                                                                       int rev = 0) {
   static_assert(NST >= 2 && NST <= 8, "the ring needs 2..8 stages");
   constexpr int R = 2, HR = kTile / 2;
   extern __shared__ __align__(128) unsigned char ssm[];
@@ -342,18 +349,22 @@ __global__ void __launch_bounds__(kC32Threads, CPS) k_stream_c32_half(const int2
   fence_proxy_async();
   __syncthreads();
   int issued = 0;
+  auto tix = [&](int k) {  // the CTA's k-th tile
+    const int t = (int)blockIdx.x + k * G;
+    return rev ? nt - 1 - t : t;
+  };
   int2 issIJ = make_int2(0, 0), aheadIJ = make_int2(0, 0);
   if (tid == 0 && nloc > 0) {
-    issIJ = tiles[blockIdx.x];
-    if (nloc > 1) aheadIJ = tiles[(int)blockIdx.x + G];
+    issIJ = tiles[tix(0)];
+    if (nloc > 1) aheadIJ = tiles[tix(1)];
   }
   auto issue = [&](int v) {  // unit v = 2 k + h: half h of the CTA's tile k
     const int k = v >> 1, h = v & 1, s = v % NST;
     if (h == 0 && k > 0) {
       issIJ = aheadIJ;
-      if (k + 1 < nloc) aheadIJ = tiles[(int)blockIdx.x + (k + 1) * G];
+      if (k + 1 < nloc) aheadIJ = tiles[tix(k + 1)];
     }
-    const int t = (int)blockIdx.x + k * G;
+    const int t = tix(k);
     stile[s] = issIJ;
     unsigned char *buf = ssm + (size_t)s * kC32HalfStageBytes;
     const int nr = min(HR, ns - (issIJ.x * kTile + h * HR)), nc = min(kTile, ns - issIJ.y * kTile);

@@ -300,8 +300,12 @@ def test_time_sweep_measures_without_changing_results(pb):
     ms = dev.time_sweep(T(f), 5)
     assert 0.0 < ms < 100.0
     assert np.array_equal(dev.collision(T(f)).cpu().numpy(), before)
+    assert 0.0 < dev.time_sweep(T(f), 6, order=1) < 100.0  # alternating tile order, as in RK4
+    assert np.array_equal(dev.collision(T(f)).cpu().numpy(), before)
     with pytest.raises(pb.PBError):
         dev.time_sweep(T(f), 0)
+    with pytest.raises(pb.PBError):
+        dev.time_sweep(T(f), 2, order=2)
 
 
 @pytest.mark.parametrize("gather", [1, 2, 3, 4, 5, 6])
