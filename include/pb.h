@@ -287,7 +287,9 @@ int pb_rtbte_rk4_step(pb_dev *dev, double *f, double dt, int32_t nsteps, void *s
 
 /* Same as pb_rtbte_rk4_step with HOST buffers: copies f_host_in (double[nstate]) to the
  * device, runs nsteps steps, copies the result to f_host_out, and synchronises `stream`.
- * The host buffers should be pinned for asynchronous copies; pageable memory works. */
+ * The host buffers should be pinned for asynchronous copies; pageable memory works.  With
+ * nsteps = 1 and page-locked buffers, both copies and the step's launches are one CUDA graph,
+ * replayed per (f_host_in, f_host_out, dt) from the handle's call-graph cache. */
 int pb_rtbte_rk4_host(pb_dev *dev, const double *f_host_in, double *f_host_out, double dt, int32_t nsteps,
                       void *stream);
 
@@ -322,8 +324,9 @@ int pb_transport_iterate(pb_dev *dev, const double *vel3, const double *F3in, do
  * pb_transport_setup, copies the new iterate to F3out_host (which may equal F3in_host) and, if
  * resid3_host is not NULL, the three residual numbers of pb_transport_iterate to it, then
  * synchronises `stream`.  vel3 is a device vector as there.  The host buffers should be pinned
- * for asynchronous copies; pageable memory works.  Needs opts.transport != 0 (the copies use the
- * handle's own iterate buffers). */
+ * for asynchronous copies; pageable memory works (page-locked buffers: the copies and the pass
+ * are one CUDA graph, replayed per buffer set from the handle's call-graph cache).  Needs
+ * opts.transport != 0 (the copies use the handle's own iterate buffers). */
 int pb_transport_iterate_host(pb_dev *dev, const double *vel3, const double *F3in_host, double *F3out_host,
                               double *resid3_host, void *stream);
 

@@ -1702,7 +1702,17 @@ int replay(pb_dev *d, int kind, const void *a, const void *b, const void *c, con
   return PB_OK;
 }
 
-enum { kCallCollision = 1, kCallRates = 2, kCallTransport = 3 };
+enum { kCallCollision = 1, kCallRates = 2, kCallTransport = 3, kCallRk4Host = 4, kCallTransportHost = 5 };
+
+// page-locked host memory (pinned or registered), which a graph's copy nodes may address
+bool pinned_host(const void *p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
 
 // one transport pass: conversion of F3in, sweep, epilogue, residual (into res3, or the handle's
 // scalars when null)
@@ -1812,8 +1822,26 @@ extern "C" int pb_rtbte_rk4_host(pb_dev *d, const double *f_host_in, double *f_h
                                  void *stream) {
   clear_error();
   if (!d || !f_host_in || !f_host_out) return set_error(PB_EINVAL, "pb_rtbte_rk4_host: null argument");
+  if (nsteps < 0 || !std::isfinite(dt)) return set_error(PB_EINVAL, "pb_rtbte_rk4_host: bad dt or nsteps");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = sizeof(double) * (size_t)d->ns;
+  if (nsteps == 1 && pinned_host(f_host_in) && pinned_host(f_host_out)) {
+    // one step from page-locked buffers: both copies and the step's launches in one graph,
+    // replayed per (buffers, dt)
+    uint64_t dtk = 0;
+    std::memcpy(&dtk, &dt, sizeof dtk);
+    int rc = replay(d, kCallRk4Host, f_host_in, f_host_out, (const void *)(uintptr_t)dtk, nullptr, st,
+                    [&](cudaStream_t s) -> int {
+                      PB_CUDA(cudaMemcpyAsync(d->fstage, f_host_in, bytes, cudaMemcpyHostToDevice, s));
+                      int r = stage_input(d, d->fstage, s);
+                      if (r || (r = rk4_launches(d, d->fstage, dt, s))) return r;
+                      PB_CUDA(cudaMemcpyAsync(f_host_out, d->fstage, bytes, cudaMemcpyDeviceToHost, s));
+                      return PB_OK;
+                    });
+    if (rc) return rc;
+    PB_CUDA(cudaStreamSynchronize(st));
+    return PB_OK;
+  }
   PB_CUDA(cudaMemcpyAsync(d->fstage, f_host_in, bytes, cudaMemcpyHostToDevice, st));
   int rc = pb_rtbte_rk4_step(d, d->fstage, dt, nsteps, stream);
   if (rc) return rc;
@@ -1845,6 +1873,20 @@ extern "C" int pb_transport_iterate_host(pb_dev *d, const double *vel3, const do
   if (!d->transport) return set_error(PB_EINVAL, "transport buffers were not reserved (pb_dev_opts.transport = 0)");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = sizeof(double) * 3 * (size_t)d->ns;
+  if (pinned_host(F3in_host) && pinned_host(F3out_host) && (!resid3_host || pinned_host(resid3_host))) {
+    // page-locked buffers: the copies and the pass in one graph, replayed per buffer set
+    int rc = replay(d, kCallTransportHost, vel3, F3in_host, F3out_host, resid3_host, st, [&](cudaStream_t s) -> int {
+      PB_CUDA(cudaMemcpyAsync(d->Fa, F3in_host, bytes, cudaMemcpyHostToDevice, s));
+      const int r = transport_seq(d, vel3, d->Fa, d->Fb, nullptr, s);
+      if (r) return r;
+      PB_CUDA(cudaMemcpyAsync(F3out_host, d->Fb, bytes, cudaMemcpyDeviceToHost, s));
+      if (resid3_host) PB_CUDA(cudaMemcpyAsync(resid3_host, d->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      return PB_OK;
+    });
+    if (rc) return rc;
+    PB_CUDA(cudaStreamSynchronize(st));
+    return PB_OK;
+  }
   PB_CUDA(cudaMemcpyAsync(d->Fa, F3in_host, bytes, cudaMemcpyHostToDevice, st));
   // the pass Fa -> Fb, residual into the handle's scalars
   int rc = replay(d, kCallTransport, vel3, d->Fa, d->Fb, nullptr, st,

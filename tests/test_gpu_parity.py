@@ -376,6 +376,42 @@ def test_transport_iterate_replays_graphs(pb):
             assert np.array_equal(res.cpu().numpy(), rh)
 
 
+@pytest.mark.parametrize("variant", ["ff", "c32"])
+def test_host_buffer_calls_from_pinned_memory(pb, variant):
+    """From page-locked host buffers the host-buffer calls replay one graph holding both copies
+    and the launches: one RK4 step per call (in place on one pinned buffer, then with another dt,
+    then from pageable memory) and transport passes with the residual, bit for bit the device
+    calls' results."""
+    import torch
+
+    m = synth.make_window4(12)
+    o = oracle.Oracle(m)
+    dev = pb.Device(pb.Channels.from_model(m), variant=variant, transport=True)
+    f0 = o.window_values(m.f_hot())
+    fd = T(f0)
+    fh = torch.tensor(f0).pin_memory()
+    for dt in (1.0, 1.0, 1.0, 0.5, 0.5, 1.0):
+        dev.rk4(fd, dt, 1)
+        dev.rk4_host(fh, dt, 1, out=fh)
+        assert np.array_equal(fh.numpy(), fd.cpu().numpy())
+    out = dev.rk4_host(fh.numpy().copy(), 1.0, 1)  # pageable: the copies outside the graph
+    dev.rk4(fd, 1.0, 1)
+    assert np.array_equal(out, fd.cpu().numpy())
+    fe = o.window_values(m.f_fermi(m.emin() - 0.2))
+    v = T(o.window_values(m.vel))
+    dev.transport_setup(T(fe))
+    F = np.random.default_rng(4).normal(size=(o.nstate, 3))
+    Fd, Fo, res = T(F), T(np.zeros_like(F)), T(np.zeros(3))
+    Fh = torch.tensor(F).pin_memory()
+    rh = torch.zeros(3, dtype=torch.float64).pin_memory()
+    for it in range(4):
+        src, dst = (Fd, Fo) if it % 2 == 0 else (Fo, Fd)
+        dev.transport_iterate(v, src, out=dst, resid=res)
+        dev.transport_iterate_host(v, Fh, out=Fh, resid=rh)
+        assert np.array_equal(Fh.numpy(), dst.cpu().numpy())
+        assert np.array_equal(rh.numpy(), res.cpu().numpy())
+
+
 def test_no_channels(pb):
     """Acoustic-only modes on a 1x1x1 grid: no channel survives, every output is zero."""
     eps = np.array([[0.0, 0.1]])
