@@ -335,3 +335,33 @@ def test_tile_batch_needs_a_closure_checked_list(pb):
     fr = np.random.default_rng(53).uniform(0, 1, b.nstate)
     ref, ab = oracle.Oracle(m).collision(fr, with_abs=True)
     assert np.abs(b.collision(torch.tensor(fr, device="cuda")).cpu().numpy() - ref).max() <= 1e-13 * ab.max()
+
+
+_traj = {}
+
+
+@pytest.mark.parametrize("precision,tol,tol_n", [("ff", 1e-12, 1e-12), ("c32", 1e-6, 1e-5)])
+def test_tile_batch_200_step_trajectory(pb, precision, tol, tol_n):
+    """200 RK4 steps of 1 fs of three small instances in one tile batch (the stages alternate
+    the tile order) against each instance's oracle trajectory, normwise, and the carrier number
+    of every instance conserved (sum_s I_s = 0 on a closed list: to rounding in float-float; the
+    FP32 net terms enter a state's row sum and its partner's column sum grouped differently, so
+    there it drifts by the FP32 rounding of the sums)."""
+    import torch
+
+    inst = small_instances(3)
+    chs = [pb.Channels.from_model(m) for m, _ in inst]
+    b = pb.Batch(chs, precision=precision)
+    assert b.tiled
+    f = np.concatenate([m.f_hot(e_exc=e).reshape(-1)[c.state_ids()] for (m, e), c in zip(inst, chs)])
+    ft = torch.tensor(f, device="cuda")
+    b.rk4(ft, 1.0, 200)
+    got = ft.cpu().numpy()
+    b.check()
+    for i, ((m, e), ch) in enumerate(zip(inst, chs)):
+        a, z = b.offsets[i], b.offsets[i + 1]
+        if m.name not in _traj:
+            _traj[m.name] = oracle.Oracle(m).rk4(f[a:z], 1.0, 200)
+        ref = _traj[m.name]
+        assert np.abs(got[a:z] - ref).max() <= tol * np.abs(ref).max(), i
+        assert abs(got[a:z].sum() - f[a:z].sum()) <= tol_n * f[a:z].sum()
