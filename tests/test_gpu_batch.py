@@ -351,7 +351,7 @@ def test_tile_batch_200_step_trajectory(pb, precision, tol, tol_n):
 
     inst = small_instances(3)
     chs = [pb.Channels.from_model(m) for m, _ in inst]
-    b = pb.Batch(chs, precision=precision)
+    b = pb.Batch(chs, precision=precision, layout=2)  # tiles (these small rows would stay rows)
     assert b.tiled
     f = np.concatenate([m.f_hot(e_exc=e).reshape(-1)[c.state_ids()] for (m, e), c in zip(inst, chs)])
     ft = torch.tensor(f, device="cuda")
