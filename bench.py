@@ -164,9 +164,19 @@ HOT_FUNCTIONS = ("ff_split", "ff_to_double", "ff_mac", "ff_mac_lazy", "ff_add", 
                  "fence_proxy_async", "k_stream_sym_bulk", "half_smem", "k_stream_sym_half")
 
 
-def kernel_source_hash(names=HOT_FUNCTIONS) -> str:
+# the FP32 coefficient-tile sweep (tiles32.cuh) and the helpers of kernels.cuh it inlines
+HOT_FUNCTIONS_C32 = ("c32_smem", "c32_term", "f32_reduce_scatter", "c32_columns_out", "k_stream_c32", "ff_split",
+                     "mbar_init", "mbar_expect_tx", "mbar_try_wait", "mbar_wait", "bulk_g2s", "fence_proxy_async")
+
+
+def kernel_source_hash(variant: str = "ff") -> str:
     """Hash of the collision sweep's own source (the kernel and the helpers it inlines)."""
-    text = open(os.path.join(ROOT, "paper_2511_03683_gb300", "csrc", "kernels.cuh")).read()
+    csrc = os.path.join(ROOT, "paper_2511_03683_gb300", "csrc")
+    text = open(os.path.join(csrc, "kernels.cuh")).read()
+    names = HOT_FUNCTIONS
+    if variant == "c32":
+        text += "\n" + open(os.path.join(csrc, "tiles32.cuh")).read()
+        names = HOT_FUNCTIONS_C32
     h = hashlib.sha256()
     for n in names:
         h.update(function_source(text, n).encode())
@@ -180,7 +190,7 @@ def ncu_traffic(workload: str, variant: str, bytes_per_launch: float):
     try:
         d = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
         e = d[f"{workload}:{variant}"]
-        if e.get("source_hash") != kernel_source_hash():
+        if e.get("source_hash") != kernel_source_hash(variant):
             return None
         if abs(float(e["algorithmic_bytes_per_launch"]) - bytes_per_launch) > 1e-6 * bytes_per_launch:
             return None
