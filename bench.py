@@ -74,7 +74,7 @@ class Clocks:
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,clocks.mem")
 
     def __init__(self, index: int):
         self.index = index
@@ -111,7 +111,8 @@ class Clocks:
             if len(parts) < 9:
                 continue
             try:
-                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                mem = float(parts[9]) if len(parts) > 9 else float("nan")
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9], mem))
             except ValueError:
                 continue
         os.unlink(self.path)
@@ -121,8 +122,9 @@ class Clocks:
         loaded = [r for r in rows if r[0] > 0.5 * mx] or rows
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        mems = [r[3] for r in loaded if r[3] == r[3]]
         return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": mx, "reasons": reasons,
-                "samples": len(rows)}
+                "samples": len(rows), "mem_mhz": statistics.median(mems) if mems else None}
 
 
 def measured_hbm():
