@@ -760,8 +760,8 @@ def run_ours(args):
         fnp, Fnp = f_host.numpy(), F_host.numpy()
 
         def e2e_step():
-            dev.rk4_host(f_host, dt, 1, out=f_host)
-            dev.transport_iterate_host(v, F_host, out=F_host)
+            dev.rk4_host(f_host, dt, 1, out=f_host, stream=stream)
+            dev.transport_iterate_host(v, F_host, out=F_host, stream=stream)
 
         for _ in range(max(3, min(args.warmup, 5))):
             e2e_step()
