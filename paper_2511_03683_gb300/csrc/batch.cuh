@@ -914,6 +914,14 @@ extern "C" int pb_batch_arena_bytes(const pb_channels *const *chs, int32_t n, co
   if (rc) return rc;
   const int prec = opts ? opts->precision : 0;
   if (prec < 0 || prec > 2) return set_error(PB_EINVAL, "pb_batch: precision must be 0, 1 or 2");
+  const int layout = opts ? opts->layout : 0;
+  if (layout < 0 || layout > (prec >= 1 ? 2 : 1))
+    return set_error(PB_EINVAL, "pb_batch: layout must be 0 or 1 (precision 0), 0..2 (precision 1, 2)");
+  if (layout == 2)
+    for (int i = 0; i < n; ++i)
+      if (!chs[i]->closed)
+        return set_error(PB_EINVAL, "pb_batch: layout 2 (symmetric tiles) needs channel lists built with the "
+                                    "closure check (list %d was not)", i);
   try {
     if (prec >= 1) {
       const std::vector<int64_t> lenp = batch_pair_lenp(chs, n);

@@ -217,3 +217,38 @@ def test_c32_arena_and_options(pb):
     cut = pb.Channels.from_model(m, g2_min=5e-4, delta_nsigma=4.0)
     assert arena(cut, variant=pb.VARIANTS["c32"])[0] == pb.PB_EINVAL
     assert "complete rows" in L.pb_last_error().decode()
+
+
+def test_batch_arena_and_layouts_on_the_host(pb):
+    """pb_batch_arena_bytes sizes a batch arena without a GPU. The symmetric-tile form of a
+    precision-1 batch (layout 2; layout 0 takes it when it streams fewer bytes) adds each
+    instance's upper block triangle as 64 x 64 tiles of 16 B entries, one tile partial per padded
+    state and partner block of the largest instance, and the padded maps to the rows' arena.
+    Layouts out of range, and layout 2 on a list built without the closure check, are
+    PB_EINVAL; such a list still sizes a row batch."""
+    import ctypes
+
+    m = synth.make_window4(12)
+    chs = [pb.Channels.from_model(m), pb.Channels.from_model(synth.make_tiny(3))]
+    unchecked = [pb.Channels.from_model(m, check_closure=False)]
+
+    def arena(prec, layout, lists=chs):
+        arr = (ctypes.c_void_p * len(lists))(*[c._h.value for c in lists])
+        o = pb._BatchOpts(0, 0, prec, layout)
+        n = ctypes.c_size_t(0)
+        rc = pb.lib().pb_batch_arena_bytes(arr, len(lists), ctypes.byref(o), ctypes.byref(n))
+        return rc, n.value
+
+    blocks = [(c.nstate + 63) // 64 for c in chs]
+    nt = sum(b * (b + 1) // 2 for b in blocks)
+    nsp = 64 * sum(blocks)
+    rc_rows, rows = arena(1, 1)
+    rc_tiles, tiles = arena(1, 2)
+    assert rc_rows == rc_tiles == pb.PB_OK
+    assert 16 * nt * 4096 + 16 * nsp * max(blocks) <= tiles - rows <= 16 * nt * 4096 + 16 * nsp * max(blocks) + 65536
+    rc_c32, c32 = arena(2, 2)
+    assert rc_c32 == pb.PB_OK and 0 < c32
+    for prec, layout in ((0, 2), (1, 3), (2, -1), (0, -1)):
+        assert arena(prec, layout)[0] == pb.PB_EINVAL
+    assert arena(1, 2, unchecked)[0] == pb.PB_EINVAL
+    assert arena(1, 0, unchecked)[0] == pb.PB_OK
