@@ -160,9 +160,9 @@ void pb_channels_free(pb_channels *ch);
  *                     P_in f_p (1-f_s) - P_out f_s (1-f_p) in FP32 with the larger product made
  *                     exact by an FMA, plus first-order terms in the low part of the float-float
  *                     f; FP64 for the per-state combination and the RK4 update.  df/dt within
- *                     about 1e-6 of Eq. 2 (normwise).  Needs complete rows (no cutoffs) of a list
- *                     built with check_closure, branch merging and tile_sweep 0 or 2..8
- *                     (PB_EINVAL otherwise).  Transport, the
+ *                     about 1e-6 of Eq. 2 (normwise).  Needs the symmetric tiles (a list built with
+ *                     check_closure whose rows are complete, or miss few partners, or dense_rows
+ *                     3), branch merging and tile_sweep 0 or 2..8 (PB_EINVAL otherwise).  Transport, the
  *                     no-allocation call and, after pb_dev_set_g2, every sweep run the FF rows;
  *                     the adjoint calls return PB_EINVAL. */
 enum { PB_VARIANT_FF = 0, PB_VARIANT_F64 = 1, PB_VARIANT_LITERAL = 2, PB_VARIANT_G32 = 3, PB_VARIANT_G16 = 4,
@@ -195,14 +195,16 @@ typedef struct pb_dev_opts {
                                 every state pair (s, p) once at setup and stream one entry per pair (Eq. 2
                                 depends on nu only through |g|^2, N and the deltas, all fixed with eps,
                                 omega, sigma and T); 2 stream one entry per channel */
-  int32_t dense_rows;        /* FF, branch-merged, when every row holds every window state in order (no
-                                cutoffs): 0 automatic (= 3); 1 the collision, rate and transport sweeps take
-                                each entry's partner from its position and stream no index (16 instead of 18
-                                bytes per entry); 3 as 1, and the collision and rate sweeps stream the upper
-                                block triangle of the pair matrix as 64 x 64 tiles of (P_in, P_out), adding
-                                each tile to its rows and, through the reverse channels (P_in(p,s) =
+  int32_t dense_rows;        /* FF, branch-merged: 0 automatic (= 3 when every row holds every window state
+                                in order, i.e. no cutoffs, or when the tiles below stream at most 0.7 of the
+                                rows' bytes; else 2); 1 (complete rows only) the collision, rate and
+                                transport sweeps take each entry's partner from its position and stream no
+                                index (16 instead of 18 bytes per entry); 3 as 1 where the rows are complete,
+                                and the collision and rate sweeps stream the upper block triangle of the pair
+                                matrix as 64 x 64 tiles of (P_in, P_out), zero where a pair has no channel,
+                                adding each tile to its rows and, through the reverse channels (P_in(p,s) =
                                 P_out(s,p)), to its columns: about 8 bytes per state pair (only for a list
-                                built with check_closure, which guarantees those reverse channels; 1
+                                built with check_closure, which guarantees those reverse channels; 1 or 2
                                 otherwise); 2 always stream the index */
   int32_t tile_sweep;        /* the symmetric tile sweep (dense_rows 3): 0 automatic (= 3); 1 each thread
                                 loads its 4 x 4 entries of a tile from global memory (3 CTAs per SM);

@@ -878,11 +878,11 @@ int batch_setup_tiles(pb_batch *b, const pb_channels *const *chs, int n, cudaStr
   PB_CUDA(cudaMemsetAsync(b->tc, 0, tbytes, st));
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((b->ns * 32 + 255) / 256, (int64_t)b->sm_count * 8));
   if (b->prec == 2)
-    dev::k_tiles_scatter<true><<<grid, 256, 0, st>>>(b->srp, (int)b->ns, b->pidx, b->pA, b->pB, b->pmap, b->binfo,
-                                                     b->tc);
+    dev::k_tiles_scatter<true, uint32_t><<<grid, 256, 0, st>>>(b->srp, (int)b->ns, b->pidx, b->pA, b->pB, b->pmap,
+                                                               b->binfo, 0, b->tc);
   else
-    dev::k_tiles_scatter<false><<<grid, 256, 0, st>>>(b->srp, (int)b->ns, b->pidx, b->pA, b->pB, b->pmap, b->binfo,
-                                                      b->tc);
+    dev::k_tiles_scatter<false, uint32_t><<<grid, 256, 0, st>>>(b->srp, (int)b->ns, b->pidx, b->pA, b->pB, b->pmap,
+                                                                b->binfo, 0, b->tc);
   PB_LAUNCHED("k_tiles_scatter (batch)");
   PB_CUDA(cudaStreamSynchronize(st));  // the host tables are released on return
   // dynamic shared memory of every launch shape the autotuner may pick

@@ -451,6 +451,7 @@ struct pb_dev {
   int half_cps = 3;       // its resident CTAs per SM: 3 (two stages each) or 2 (three stages)
   bool c32 = false;
   int c32_shape = 2;  // pb_dev_opts.tile_sweep: the launch shape (with_c32_shape)
+  bool complete = false;  // every row holds every state (tiles filled by position, else scattered)
   // the next tile sweep takes the tile list from its end (the RK4 stages alternate, so that each
   // sweep starts on the tiles the previous one left in L2)
   int rev = 0;
@@ -599,11 +600,22 @@ bool merge_for(const pb_dev_opts &o) {
   return (o.variant == PB_VARIANT_FF || o.variant == PB_VARIANT_F64) && o.merge_branches != 2;
 }
 
-// symmetric tiles: FF, branch-merged, complete rows of a list verified closed under reversal
-// (the entry of (s, p) serves (p, s) with P_in and P_out swapped), dense_rows automatic or 3
-bool sym_for(const pb_dev_opts &o, bool merged, bool complete, bool closed) {
-  return merged && complete && closed && o.variant == PB_VARIANT_FF && (o.dense_rows == 0 || o.dense_rows == 3) &&
-         o.stream_mode != 2;
+// whether the symmetric tiles of ns states stream at most 0.7 of the bytes of a branch-merged
+// row stream of nsw entries (float-float P_in and D and a 16- or 32-bit partner index): rows
+// that miss some partners, but not many
+bool tiles_pay(int64_t ns, int64_t nsw) {
+  const double nb = (double)((ns + dev::kTile - 1) / dev::kTile);
+  const double tile_bytes = nb * (nb + 1) / 2 * dev::kTile * dev::kTile * 16.0;
+  const double row_bytes = (double)nsw * (16.0 + (ns <= 65536 ? 2.0 : 4.0));
+  return tile_bytes <= 0.7 * row_bytes;
+}
+
+// symmetric tiles: FF, branch-merged, a list verified closed under reversal (the entry of (s, p)
+// serves (p, s) with P_in and P_out swapped); dense_rows 3, or automatic (0) on complete rows or
+// when the tiles stream fewer bytes than the rows (pays)
+bool sym_for(const pb_dev_opts &o, bool merged, bool complete, bool closed, bool pays) {
+  if (!(merged && closed && o.variant == PB_VARIANT_FF && o.stream_mode != 2)) return false;
+  return o.dense_rows == 3 || (o.dense_rows == 0 && (complete || pays));
 }
 
 // work-item size of the branch-merged sweep: the caller's, the bulk ring's, or the default
@@ -760,10 +772,10 @@ extern "C" int pb_dev_arena_bytes(const pb_channels *ch, const pb_dev_opts *opts
     bool complete = false;
     const bool merged = make_plans(ch, opts, o, sm, P, S, &complete);
     const int nfin = (int)((P.ns + kFinBlock - 1) / kFinBlock);
-    const bool sym = sym_for(o, merged, complete, ch->closed);
+    const bool sym = sym_for(o, merged, complete, ch->closed, merged && tiles_pay(S.ns, S.nchp));
     if (c32 && !sym)
-      return set_error(PB_EINVAL, "pb_dev: the FP32 coefficient tiles (C32) need complete rows (every window state "
-                                  "a partner of every other: no |g| or delta cutoffs) of a closure-checked list");
+      return set_error(PB_EINVAL, "pb_dev: the FP32 coefficient tiles (C32) need the symmetric tiles: a "
+                                  "closure-checked list whose rows are complete or miss few partners (or dense_rows 3)");
     *bytes = make_layout(ch, P, merged ? &S : nullptr, o.variant, o.transport != 0, nfin, sym,
                          gdense_for(ch, o, sm), o.adjoint != 0, c32 ? sizeof(float2) : sizeof(float4)).total;
   } catch (const std::bad_alloc &) {
@@ -835,11 +847,12 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->item_ch = o.item_channels;
   d->transport = o.transport != 0;
   d->nfin_blocks = (int)((d->ns + kFinBlock - 1) / kFinBlock);
-  d->sym = sym_for(o, merged, complete, ch->closed);
+  d->sym = sym_for(o, merged, complete, ch->closed, merged && tiles_pay(S.ns, S.nchp));
+  d->complete = complete;
   if (c32 && !d->sym) {
     delete d;
-    return set_error(PB_EINVAL, "pb_dev: the FP32 coefficient tiles (C32) need complete rows (every window state a "
-                                "partner of every other: no |g| or delta cutoffs) of a closure-checked list");
+    return set_error(PB_EINVAL, "pb_dev: the FP32 coefficient tiles (C32) need the symmetric tiles: a "
+                                "closure-checked list whose rows are complete or miss few partners (or dense_rows 3)");
   }
   d->c32 = c32;
   d->c32_shape = o.tile_sweep;
@@ -1980,7 +1993,25 @@ int coef_setup(pb_dev *d, cudaStream_t st) {
       else    dev::k_pair_coef<false><<<pg, 256, 0, st>>>(cs, d->pcnt, (long long)d->nsw, d->ccoefA, d->ccoefB, d->coefA, d->coefB, 1.0, d->g2);
       PB_LAUNCHED("k_pair_coef");
     }
-    if (d->sym) {
+    if (d->sym && !d->complete) {
+      // rows that miss some partners: the tiles zeroed, then every stored pair scattered in
+      const size_t tb = (size_t)d->td.nt * dev::kTile * dev::kTile * (d->c32 ? sizeof(float2) : sizeof(float4));
+      void *tc = d->c32 ? (void *)d->tc32 : (void *)d->tcoef;
+      PB_CUDA(cudaMemsetAsync(tc, 0, tb, st));
+      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((d->ns * 32 + 255) / 256, (int64_t)d->sm_count * 8));
+      const long long *srp = (const long long *)d->srp;
+      const float2 *cA = (const float2 *)d->coefA, *cB = (const float2 *)d->coefB;
+      const int ns = (int)d->ns, nb = d->td.nb;
+      if (d->c32 && d->sidx16)
+        dev::k_tiles_scatter<true, uint16_t><<<grid, 256, 0, st>>>(srp, ns, d->sidx16, cA, cB, nullptr, nullptr, nb, tc);
+      else if (d->c32)
+        dev::k_tiles_scatter<true, uint32_t><<<grid, 256, 0, st>>>(srp, ns, d->sidx32, cA, cB, nullptr, nullptr, nb, tc);
+      else if (d->sidx16)
+        dev::k_tiles_scatter<false, uint16_t><<<grid, 256, 0, st>>>(srp, ns, d->sidx16, cA, cB, nullptr, nullptr, nb, tc);
+      else
+        dev::k_tiles_scatter<false, uint32_t><<<grid, 256, 0, st>>>(srp, ns, d->sidx32, cA, cB, nullptr, nullptr, nb, tc);
+      PB_LAUNCHED("k_tiles_scatter");
+    } else if (d->sym) {
       const long long n = (long long)d->td.nt * dev::kTile * dev::kTile;
       const int grid = (int)std::min<long long>((n + 255) / 256, 8192);
       if (d->c32)

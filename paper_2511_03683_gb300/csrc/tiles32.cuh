@@ -79,28 +79,31 @@ __global__ void k_tiles_fill_c32(const int2 *__restrict__ tiles, int nt, const f
   }
 }
 
-// The tiles of a batch (several systems in one padded block space) from their branch-merged
-// pair rows, which need not be complete: one warp per row s, every stored pair (s, p) whose
-// local block pair (I, J) lies in the upper triangle (I <= J) written to its tile entry; the
-// tiles were zeroed before, pairs without channels stay zero, and zero padding entries are
-// skipped.  binfo[g] of block g = (first block of its system, the system's first tile, its
-// states, its blocks); tiles are numbered row-major over the system's upper block triangle.
-// C32: the pairs rounded to FP32 with their ratio kept, else float-float (float4 per entry).
-template <bool C32>
-__global__ void k_tiles_scatter(const long long *__restrict__ srp, int ns, const uint32_t *__restrict__ pidx,
+// The symmetric tiles from branch-merged pair rows that need not be complete (the batch's
+// systems, or one system whose rows miss some partners): one warp per row s, every stored pair
+// (s, p) whose block pair (I, J) lies in the upper triangle (I <= J) written to its tile entry;
+// the tiles were zeroed before, pairs without channels stay zero, and zero padding entries are
+// skipped.  Several systems share one padded block space through pmap (each state's padded row)
+// and binfo[g] of block g = (first block of its system, the system's first tile, its states, its
+// blocks); with both null there is one system of ns states in nbs blocks.  Tiles are numbered
+// row-major over each system's upper block triangle.  C32: the pairs rounded to FP32 with their
+// ratio kept, else float-float (float4 per entry).
+template <bool C32, typename IDX>
+__global__ void k_tiles_scatter(const long long *__restrict__ srp, int ns, const IDX *__restrict__ pidx,
                                 const float2 *__restrict__ coefA, const float2 *__restrict__ coefB,
-                                const int *__restrict__ pmap, const int4 *__restrict__ binfo, void *__restrict__ tc) {
+                                const int *__restrict__ pmap, const int4 *__restrict__ binfo, int nbs,
+                                void *__restrict__ tc) {
   const int lane = threadIdx.x & 31;
   const int w0 = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)(((long long)gridDim.x * blockDim.x) >> 5);
   for (int r = w0; r < ns; r += nw) {
-    const int pr = pmap[r];
-    const int4 bi = binfo[pr / kTile];
+    const int pr = pmap ? pmap[r] : r;
+    const int4 bi = binfo ? binfo[pr / kTile] : make_int4(0, 0, ns, nbs);
     const int I = pr / kTile - bi.x;
     for (long long e = srp[r] + lane; e < srp[r + 1]; e += 32) {
       const float2 a = coefA[e], b = coefB[e];
       if (a.x == 0.f && a.y == 0.f && b.x == 0.f && b.y == 0.f) continue;
-      const int pp = pmap[pidx[e]];
+      const int pp = pmap ? pmap[pidx[e]] : (int)pidx[e];
       const int J = pp / kTile - bi.x;
       if (J < I) continue;
       const long long t = (long long)bi.y + (long long)I * (2 * bi.w - I + 1) / 2 + (J - I);

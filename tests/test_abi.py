@@ -191,7 +191,8 @@ def test_fp16_variant_sizes_like_bf16(pb):
 def test_c32_arena_and_options(pb):
     """The FP32 coefficient tiles (c32) hold 8 bytes per state pair of the upper block triangle
     instead of 16: the arena is the FF arena less 8 * tiles * 64^2 bytes (up to region
-    alignment).  They need complete rows and the bulk-copy tile sweep: PB_EINVAL otherwise."""
+    alignment).  They need the symmetric tiles (automatic on complete rows, forced by
+    dense_rows 3 on sparse ones) and the bulk-copy tile sweep: PB_EINVAL otherwise."""
     import ctypes
 
     m = synth.make_window4(12)
@@ -216,7 +217,48 @@ def test_c32_arena_and_options(pb):
         assert arena(ch, variant=pb.VARIANTS["c32"], **kw)[0] == pb.PB_EINVAL
     cut = pb.Channels.from_model(m, g2_min=5e-4, delta_nsigma=4.0)
     assert arena(cut, variant=pb.VARIANTS["c32"])[0] == pb.PB_EINVAL
-    assert "complete rows" in L.pb_last_error().decode()
+    assert "symmetric tiles" in L.pb_last_error().decode()
+    assert arena(cut, variant=pb.VARIANTS["c32"], dense_rows=3)[0] == pb.PB_OK
+
+
+def acoustic_tiny(n):
+    """The n^3 two-band model with three acoustic modes only (zero at Gamma: no channel joins
+    the two states of one k point)."""
+    t = synth.make_tiny(n)
+    s = synth.acoustic_shape(t.nk).reshape(-1)
+    return t.with_(omega=np.stack([15e-3 * s, 20e-3 * s, 25e-3 * s], axis=1))
+
+
+def test_tiles_on_rows_that_miss_partners(pb):
+    """The FF device takes the symmetric tiles (zero where a pair has no channel) on rows that
+    miss few partners, when the tiles stream at most 0.7 of the rows' bytes: an acoustic-only
+    model (no channel between the bands at one k point) gets them automatically, a list with the
+    cutoffs on (a fifth of its pairs stored) keeps the rows unless dense_rows 3 forces the tiles;
+    a list built without the closure check never gets them."""
+    import ctypes
+
+    L = pb.lib()
+
+    def arena(chs, **kw):
+        o = pb._DevOpts()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        n = ctypes.c_size_t(0)
+        assert L.pb_dev_arena_bytes(chs._h, ctypes.byref(o), ctypes.byref(n)) == pb.PB_OK
+        return n.value
+
+    def tile_bytes(chs):
+        nb = (chs.nstate + 63) // 64
+        return 16 * nb * (nb + 1) // 2 * 64 * 64
+
+    acoustic = pb.Channels.from_model(acoustic_tiny(5))
+    assert acoustic.nchannels < acoustic.nstate ** 2 * 3  # no channel between the bands at one k
+    assert arena(acoustic) - arena(acoustic, dense_rows=2) >= tile_bytes(acoustic)
+    m = synth.make_window4(16)
+    cut = pb.Channels.from_model(m, g2_min=5e-4, delta_nsigma=4.0)
+    assert arena(cut, dense_rows=3) - arena(cut) >= tile_bytes(cut)
+    unchecked = pb.Channels.from_model(m, g2_min=5e-4, delta_nsigma=4.0, check_closure=False)
+    assert arena(unchecked, dense_rows=3) == arena(unchecked)
 
 
 def test_batch_arena_and_layouts_on_the_host(pb):

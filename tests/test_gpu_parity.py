@@ -660,6 +660,46 @@ def test_c32_rk4(pb):
     dev.check()
 
 
+def _acoustic_tiny(n):
+    t = synth.make_tiny(n)
+    s = synth.acoustic_shape(t.nk).reshape(-1)
+    return t.with_(omega=np.stack([15e-3 * s, 20e-3 * s, 25e-3 * s], axis=1))
+
+
+@pytest.mark.parametrize("variant", ["ff", "c32"])
+@pytest.mark.parametrize("case", ["acoustic", "cutoffs"])
+def test_tiles_on_rows_that_miss_partners(pb, variant, case):
+    """Symmetric tiles filled by scattering rows that miss partners (zero where a pair has no
+    channel): an acoustic-only model (no channel between the bands at one k point; tiles taken
+    automatically) and the 16^3 window with the |g| and delta cutoffs (tiles forced with
+    dense_rows 3): collision, rates and 3 RK4 steps against the identically built oracle, and the
+    float-float tiles against the rows of the same list."""
+    if case == "acoustic":
+        m, kw, dev_kw = _acoustic_tiny(6), {}, {}
+    else:
+        m, kw, dev_kw = synth.make_window4(16), dict(g2_min=5e-4, delta_nsigma=4.0), dict(dense_rows=3)
+    o = oracle.Oracle(m, **kw)
+    ch = pb.Channels.from_model(m, **kw)
+    dev = pb.Device(ch, variant=variant, **dev_kw)
+    rows = pb.Device(ch, dense_rows=2)
+    assert dev.bytes_per_channel != rows.bytes_per_channel  # the tiles, not the rows
+    tol = TOL if variant == "ff" else C32_TOL
+    f = np.random.default_rng(61).uniform(0, 1, o.nstate)
+    ref, ab = o.collision(f, with_abs=True)
+    I = dev.collision(T(f)).cpu().numpy()
+    if variant == "ff":
+        check_I(I, ref, ab)
+        assert np.abs(I - rows.collision(T(f)).cpu().numpy()).max() <= MUTUAL * ab.max()
+    else:
+        assert np.abs(I - ref).max() <= tol * ab.max()
+    assert nrel(dev.rates(T(f)).cpu().numpy(), o.rates(f)) <= tol
+    f0 = o.window_values(m.f_hot())
+    ft = T(f0)
+    dev.rk4(ft, 1.0, 3)
+    assert nrel(ft.cpu().numpy(), o.rk4(f0, 1.0, 3)) <= tol
+    dev.check()
+
+
 def test_symmetric_tiles_need_a_closure_checked_list(pb):
     """The tiles serve each pair (s, p) and its reverse from one entry, which holds only when the
     reverse channels exist with equal |g|^2: a list built without the closure check streams the
