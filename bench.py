@@ -445,6 +445,7 @@ def batched_report(pb, ninst, nsteps, stream):
     ms_ff, err = sequential("ff")
     ms_ffc, _ = sequential("ff", merge_branches=2)
     ms_g, _ = sequential("g32")
+    ms_64, _ = sequential("f64")  # the plain FP64 GPU path (native FP64 FMAs, branch-merged)
     b.close()
 
     def accurate(precision, layout):
@@ -490,13 +491,14 @@ def batched_report(pb, ninst, nsteps, stream):
             "batched_channels_per_s": 4 * nch * nsteps / (ms_b * 1e-3),
             "batched_rk4_steps_per_s": nsteps / (ms_b * 1e-3),
             "sequential_ff_ms": ms_ff, "sequential_ff_per_channel_ms": ms_ffc, "sequential_g32_ms": ms_g,
+            "sequential_f64_ms": ms_64, "speedup_vs_sequential_f64": ms_64 / ms_b,
             "speedup_vs_sequential_fp32": ms_g / ms_b, "speedup_vs_sequential_ff": ms_ff / ms_b,
             "speedup_vs_sequential_ff_per_channel": ms_ffc / ms_b,
             "ff_batch": {"layout": "tiles" if tiled_f else "rows",
                          "autotuned": {"item_entries": item_f, "ctas_per_sm": ctas_f, "sweep_ms": tune_f},
                          "batched_ms": ms_bf, "batched_rk4_steps_per_s": nsteps / (ms_bf * 1e-3),
                          "batched_channels_per_s": 4 * nch * nsteps / (ms_bf * 1e-3),
-                         "speedup_vs_sequential_ff": ms_ff / ms_bf,
+                         "speedup_vs_sequential_ff": ms_ff / ms_bf, "speedup_vs_sequential_f64": ms_64 / ms_bf,
                          "speedup_vs_sequential_ff_per_channel": ms_ffc / ms_bf,
                          "dfdt_err_vs_unbatched_ff_max_over_instances": err_f,
                          "rows": rows_leg(ms_bfr, item_fr, ctas_fr, tune_fr)},
@@ -505,6 +507,7 @@ def batched_report(pb, ninst, nsteps, stream):
                           "batched_ms": ms_bc, "batched_rk4_steps_per_s": nsteps / (ms_bc * 1e-3),
                           "batched_channels_per_s": 4 * nch * nsteps / (ms_bc * 1e-3),
                           "speedup_vs_sequential_ff": ms_ff / ms_bc, "speedup_vs_ff_batch": ms_bf / ms_bc,
+                          "speedup_vs_sequential_f64": ms_64 / ms_bc,
                           "speedup_vs_sequential_fp32": ms_g / ms_bc,
                           "dfdt_err_vs_fp64_max_over_instances": err_c,
                           "rows": rows_leg(ms_bcr, item_cr, ctas_cr, tune_cr)},
