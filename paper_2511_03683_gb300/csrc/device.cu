@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <type_traits>
@@ -78,15 +79,18 @@ void plan_items(const std::vector<int64_t> &rp, int item_ch, std::vector<Item> &
 bool pair_rows(const pb_channels *ch, std::vector<int64_t> &rp) {
   const int64_t ns = ch->nstate;
   rp.assign(ns + 1, 0);
-  bool complete = true;
+  int complete = 1;
+  // rows counted in parallel (each into rp[r + 1]), then the offsets summed in order
+#pragma omp parallel for schedule(dynamic, 16) reduction(&& : complete)
   for (int64_t r = 0; r < ns; ++r) {
     int64_t runs = 0;
     for (int64_t c = ch->row_ptr[r]; c < ch->row_ptr[r + 1]; ++c)
       if (c == ch->row_ptr[r] || ch->col[c] != ch->col[c - 1]) ++runs;
     complete = complete && runs == ns;
-    rp[r + 1] = rp[r] + (runs + kRowPad - 1) / kRowPad * kRowPad;
+    rp[r + 1] = (runs + kRowPad - 1) / kRowPad * kRowPad;
   }
-  return complete;
+  for (int64_t r = 0; r < ns; ++r) rp[r + 1] += rp[r];
+  return complete != 0;
 }
 
 void plan_from_rp(const std::vector<int64_t> &rp, int item_ch, Plan &P) {
@@ -1026,15 +1030,21 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   // host staging of the padded arrays
   int status = PB_OK;
   try {
-    std::vector<uint32_t> colp((size_t)P.nchp);
-    std::vector<double> g2p((size_t)P.nchp, 0.0);
+    // rows in parallel (each writes only its own padded range; the arrays are filled, not
+    // zeroed first)
+    std::unique_ptr<uint32_t[]> colp(new uint32_t[(size_t)P.nchp]);
+    std::unique_ptr<double[]> g2p(new double[(size_t)P.nchp]);
+#pragma omp parallel for schedule(dynamic, 16)
     for (int64_t r = 0; r < d->ns; ++r) {
       const int64_t a = ch->row_ptr[r], len = ch->row_ptr[r + 1] - a, b = P.rp[r], lenp = P.rp[r + 1] - b;
       for (int64_t i = 0; i < len; ++i) {
         colp[b + i] = (uint32_t)ch->col[a + i] | ((uint32_t)ch->nu[a + i] << kPartnerBits);
         g2p[b + i] = ch->g2[a + i];
       }
-      for (int64_t i = len; i < lenp; ++i) colp[b + i] = (uint32_t)r;  // padding: self, branch 0, g2 = 0
+      for (int64_t i = len; i < lenp; ++i) {  // padding: self, branch 0, g2 = 0
+        colp[b + i] = (uint32_t)r;
+        g2p[b + i] = 0.0;
+      }
     }
     std::vector<short4> kc((size_t)d->ns);
     const int N2 = ch->nk[1], N3 = ch->nk[2];
@@ -1094,18 +1104,20 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
         UP(d->citem_ptr, P.item_ptr.data(), sizeof(int32_t) * (d->ns + 1));
         UP(d->citems, P.items.data(), sizeof(Item) * P.nitems);
       }
-      UP(d->col, colp.data(), sizeof(uint32_t) * P.nchp);
+      UP(d->col, colp.get(), sizeof(uint32_t) * P.nchp);
       if (d->col16) {
-        std::vector<uint16_t> c16((size_t)P.nchp);
+        std::unique_ptr<uint16_t[]> c16(new uint16_t[(size_t)P.nchp]);
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < P.nchp; ++i) c16[i] = (uint16_t)(colp[i] & kPartnerMask);
-        UP(d->col16, c16.data(), sizeof(uint16_t) * P.nchp);  // pageable source: staged before return
+        UP(d->col16, c16.get(), sizeof(uint16_t) * P.nchp);  // pageable source: staged before return
       }
-      UP(d->g2, g2p.data(), sizeof(double) * P.nchp);
+      UP(d->g2, g2p.get(), sizeof(double) * P.nchp);
       if (merged) {
         // one entry per run of equal partner in each row; padding entries: self, no channels
-        std::vector<uint32_t> sidx((size_t)S.nchp);
-        std::vector<int64_t> cst((size_t)S.nchp, 0);
-        std::vector<uint8_t> cn((size_t)S.nchp, 0);
+        std::unique_ptr<uint32_t[]> sidx(new uint32_t[(size_t)S.nchp]);
+        std::unique_ptr<int64_t[]> cst(new int64_t[(size_t)S.nchp]);
+        std::unique_ptr<uint8_t[]> cn(new uint8_t[(size_t)S.nchp]);
+#pragma omp parallel for schedule(dynamic, 16)
         for (int64_t r = 0; r < d->ns; ++r) {
           const int64_t a = ch->row_ptr[r], len = ch->row_ptr[r + 1] - a;
           int64_t e = S.rp[r];
@@ -1119,17 +1131,22 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
             cn[e] = 1;
             ++e;
           }
-          for (; e < S.rp[r + 1]; ++e) sidx[e] = (uint32_t)r;
+          for (; e < S.rp[r + 1]; ++e) {
+            sidx[e] = (uint32_t)r;
+            cst[e] = 0;
+            cn[e] = 0;
+          }
         }
         if (d->sidx16) {
-          std::vector<uint16_t> s16((size_t)S.nchp);
+          std::unique_ptr<uint16_t[]> s16(new uint16_t[(size_t)S.nchp]);
+#pragma omp parallel for schedule(static)
           for (int64_t i = 0; i < S.nchp; ++i) s16[i] = (uint16_t)sidx[i];
-          UP(d->sidx16, s16.data(), sizeof(uint16_t) * S.nchp);
+          UP(d->sidx16, s16.get(), sizeof(uint16_t) * S.nchp);
         } else {
-          UP(d->sidx32, sidx.data(), sizeof(uint32_t) * S.nchp);
+          UP(d->sidx32, sidx.get(), sizeof(uint32_t) * S.nchp);
         }
-        UP(d->pcstart, cst.data(), sizeof(int64_t) * S.nchp);
-        UP(d->pcnt, cn.data(), S.nchp);
+        UP(d->pcstart, cst.get(), sizeof(int64_t) * S.nchp);
+        UP(d->pcnt, cn.get(), S.nchp);
         UP(d->srp, S.rp.data(), sizeof(int64_t) * (d->ns + 1));
         {
           std::vector<Item> gi;
