@@ -405,7 +405,10 @@ def batched_report(pb, ninst, nsteps, stream):
     chs = [pb.Channels.from_model(m) for m, _ in inst]
     build_s = time.perf_counter() - t0
     fs = [m.f_hot(e_exc=e).reshape(-1)[c.state_ids()] for (m, e), c in zip(inst, chs)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     b = pb.Batch(chs)
+    create_b = time.perf_counter() - t0
     f = torch.tensor(np.concatenate(fs), device="cuda")
     item, ctas, tune_ms = b.autotune(f)
     nch = b.nchannels
@@ -451,7 +454,10 @@ def batched_report(pb, ninst, nsteps, stream):
     def accurate(precision, layout):
         """One FP64-accurate or FP32-pair batch: autotuned, nsteps RK4 steps timed, and df/dt
         against each instance on its own FF device (max over instances, normwise)."""
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
         bx = pb.Batch(chs, precision=precision, layout=layout)
+        create_s = time.perf_counter() - t1
         tuned = bx.autotune(f)
         g = f.clone()
         bx.rk4(g, 1.0, 3)
@@ -472,20 +478,21 @@ def batched_report(pb, ninst, nsteps, stream):
             errx = max(errx, float(np.abs(Ix[a:e] - ref).max() / max(np.abs(ref).max(), 1e-300)))
         tiled = bx.tiled
         bx.close()
-        return ms, tuned, errx, tiled
+        return ms, tuned, errx, tiled, create_s
 
     # the same batch on the FP64-accurate branch-merged coefficients (symmetric tiles by
     # default, rows beside them) and as FP32 pairs (net terms per entry)
-    ms_bf, (item_f, ctas_f, tune_f), err_f, tiled_f = accurate("ff", 0)
-    ms_bfr, (item_fr, ctas_fr, tune_fr), _, _ = accurate("ff", 1)
-    ms_bc, (item_c, ctas_c, tune_c), err_c, tiled_c = accurate("c32", 0)
-    ms_bcr, (item_cr, ctas_cr, tune_cr), _, _ = accurate("c32", 1)
+    ms_bf, (item_f, ctas_f, tune_f), err_f, tiled_f, create_f = accurate("ff", 0)
+    ms_bfr, (item_fr, ctas_fr, tune_fr), _, _, _ = accurate("ff", 1)
+    ms_bc, (item_c, ctas_c, tune_c), err_c, tiled_c, create_c = accurate("c32", 0)
+    ms_bcr, (item_cr, ctas_cr, tune_cr), _, _, _ = accurate("c32", 1)
 
     def rows_leg(ms, item_, ctas_, tune_):
         return {"autotuned": {"item_entries": item_, "ctas_per_sm": ctas_, "sweep_ms": tune_}, "batched_ms": ms,
                 "batched_rk4_steps_per_s": nsteps / (ms * 1e-3)}
 
     return {"instances": ninst, "states": b.nstate, "channels": nch, "build_channels_s": build_s,
+            "create_s": create_b,
             "autotuned": {"item_channels": item, "ctas_per_sm": ctas, "sweep_ms": tune_ms},
             "rk4_steps": nsteps, "batched_ms": ms_b,
             "batched_channels_per_s": 4 * nch * nsteps / (ms_b * 1e-3),
@@ -494,7 +501,7 @@ def batched_report(pb, ninst, nsteps, stream):
             "sequential_f64_ms": ms_64, "speedup_vs_sequential_f64": ms_64 / ms_b,
             "speedup_vs_sequential_fp32": ms_g / ms_b, "speedup_vs_sequential_ff": ms_ff / ms_b,
             "speedup_vs_sequential_ff_per_channel": ms_ffc / ms_b,
-            "ff_batch": {"layout": "tiles" if tiled_f else "rows",
+            "ff_batch": {"layout": "tiles" if tiled_f else "rows", "create_s": create_f,
                          "autotuned": {"item_entries": item_f, "ctas_per_sm": ctas_f, "sweep_ms": tune_f},
                          "batched_ms": ms_bf, "batched_rk4_steps_per_s": nsteps / (ms_bf * 1e-3),
                          "batched_channels_per_s": 4 * nch * nsteps / (ms_bf * 1e-3),
@@ -502,7 +509,7 @@ def batched_report(pb, ninst, nsteps, stream):
                          "speedup_vs_sequential_ff_per_channel": ms_ffc / ms_bf,
                          "dfdt_err_vs_unbatched_ff_max_over_instances": err_f,
                          "rows": rows_leg(ms_bfr, item_fr, ctas_fr, tune_fr)},
-            "c32_batch": {"layout": "tiles" if tiled_c else "rows",
+            "c32_batch": {"layout": "tiles" if tiled_c else "rows", "create_s": create_c,
                           "autotuned": {"item_entries": item_c, "ctas_per_sm": ctas_c, "sweep_ms": tune_c},
                           "batched_ms": ms_bc, "batched_rk4_steps_per_s": nsteps / (ms_bc * 1e-3),
                           "batched_channels_per_s": 4 * nch * nsteps / (ms_bc * 1e-3),
