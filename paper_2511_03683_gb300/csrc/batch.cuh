@@ -411,14 +411,21 @@ BatchLayout batch_layout(const pb_channels *const *chs, int n, int64_t ns, int64
 // Sweep entries per row of the FP64-accurate batch: one per run of equal partner (state pair),
 // padded to kRowPad.
 std::vector<int64_t> batch_pair_lenp(const pb_channels *const *chs, int32_t n) {
-  std::vector<int64_t> lenp;
-  for (int i = 0; i < n; ++i)
-    for (int64_t r = 0; r < chs[i]->nstate; ++r) {
+  int64_t total = 0;
+  for (int i = 0; i < n; ++i) total += chs[i]->nstate;
+  std::vector<int64_t> lenp((size_t)total);
+  int64_t off = 0;
+  for (int i = 0; i < n; ++i) {
+    const pb_channels *ch = chs[i];
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t r = 0; r < ch->nstate; ++r) {
       int64_t runs = 0;
-      for (int64_t c = chs[i]->row_ptr[r]; c < chs[i]->row_ptr[r + 1]; ++c)
-        if (c == chs[i]->row_ptr[r] || chs[i]->col[c] != chs[i]->col[c - 1]) ++runs;
-      lenp.push_back((runs + kRowPad - 1) / kRowPad * kRowPad);
+      for (int64_t c = ch->row_ptr[r]; c < ch->row_ptr[r + 1]; ++c)
+        if (c == ch->row_ptr[r] || ch->col[c] != ch->col[c - 1]) ++runs;
+      lenp[off + r] = (runs + kRowPad - 1) / kRowPad * kRowPad;
     }
+    off += ch->nstate;
+  }
   return lenp;
 }
 
@@ -459,9 +466,10 @@ struct BatchLayoutFF {
 
 constexpr int kBatchSetupItem = 2048;  // channels per work item of the per-instance coefficient setup
 
-// c32: precision 2 (the rounded FP32 pairs of the rows, or FP32 tiles); T: the tile form
+// c32: precision 2 (the rounded FP32 pairs of the rows, or FP32 tiles); T: the tile form;
+// lenp: the padded pair entries of every row (batch_pair_lenp)
 BatchLayoutFF batch_layout_ff(const pb_channels *const *chs, int n, int64_t ns, int64_t nent, int64_t nitems_cap,
-                              bool c32, const BatchTiles &T) {
+                              bool c32, const BatchTiles &T, const std::vector<int64_t> &lenp) {
   BatchLayoutFF L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -470,6 +478,7 @@ BatchLayoutFF batch_layout_ff(const pb_channels *const *chs, int n, int64_t ns, 
     return at;
   };
   size_t maxq = 0, maxs = 0, maxc = 0, maxp = 0, maxi = 0;
+  int64_t so = 0;
   for (int i = 0; i < n; ++i) {
     const pb_channels *ch = chs[i];
     size_t c = 0, p = 0, it = 0;
@@ -477,11 +486,9 @@ BatchLayoutFF batch_layout_ff(const pb_channels *const *chs, int n, int64_t ns, 
       const int64_t len = ch->row_ptr[r + 1] - ch->row_ptr[r], lp = (len + kRowPad - 1) / kRowPad * kRowPad;
       c += (size_t)lp;
       if (lp > 0) it += (size_t)std::max<int64_t>(1, (lp + kBatchSetupItem - 1) / kBatchSetupItem);
-      int64_t runs = 0;
-      for (int64_t k = ch->row_ptr[r]; k < ch->row_ptr[r + 1]; ++k)
-        if (k == ch->row_ptr[r] || ch->col[k] != ch->col[k - 1]) ++runs;
-      p += (size_t)((runs + kRowPad - 1) / kRowPad * kRowPad);
+      p += (size_t)lenp[so + r];
     }
+    so += ch->nstate;
     maxq = std::max(maxq, (size_t)ch->nq * ch->nmodes);
     maxs = std::max(maxs, (size_t)ch->nstate);
     maxc = std::max(maxc, c);
@@ -747,25 +754,28 @@ int batch_setup_ff(pb_batch *b, const pb_channels *const *chs, int n, const Batc
     for (int64_t r = 0; r < ns_i; ++r)
       rp[r + 1] = rp[r] + (ch->row_ptr[r + 1] - ch->row_ptr[r] + kRowPad - 1) / kRowPad * kRowPad;
     const int64_t nc = rp[ns_i];
-    std::vector<uint32_t> hcol((size_t)nc);
-    std::vector<double> hg2((size_t)nc, 0.0);
-    const int64_t np = [&] {
-      int64_t t = 0;
-      for (int64_t r = 0; r < ns_i; ++r) t += b->lenp[so + r];
-      return t;
-    }();
-    std::vector<uint32_t> hpidx((size_t)np);
-    std::vector<int64_t> hcst((size_t)np, 0);
-    std::vector<uint8_t> hcnt((size_t)np, 0);
-    int64_t e = 0;
+    // first pair entry of every row, then the rows filled in parallel (each writes only its own
+    // ranges; the arrays are filled, not zeroed first)
+    std::vector<int64_t> pe((size_t)ns_i + 1, 0);
+    for (int64_t r = 0; r < ns_i; ++r) pe[r + 1] = pe[r] + b->lenp[so + r];
+    const int64_t np = pe[ns_i];
+    std::unique_ptr<uint32_t[]> hcol(new uint32_t[(size_t)nc]);
+    std::unique_ptr<double[]> hg2(new double[(size_t)nc]);
+    std::unique_ptr<uint32_t[]> hpidx(new uint32_t[(size_t)np]);
+    std::unique_ptr<int64_t[]> hcst(new int64_t[(size_t)np]);
+    std::unique_ptr<uint8_t[]> hcnt(new uint8_t[(size_t)np]);
+#pragma omp parallel for schedule(dynamic, 16)
     for (int64_t r = 0; r < ns_i; ++r) {
       const int64_t a = ch->row_ptr[r], len = ch->row_ptr[r + 1] - a;
       for (int64_t k = 0; k < len; ++k) {
         hcol[rp[r] + k] = (uint32_t)ch->col[a + k] | ((uint32_t)ch->nu[a + k] << kPartnerBits);
         hg2[rp[r] + k] = ch->g2[a + k];
       }
-      for (int64_t k = len; k < rp[r + 1] - rp[r]; ++k) hcol[rp[r] + k] = (uint32_t)r;
-      const int64_t e0 = e;
+      for (int64_t k = len; k < rp[r + 1] - rp[r]; ++k) {
+        hcol[rp[r] + k] = (uint32_t)r;
+        hg2[rp[r] + k] = 0.0;
+      }
+      int64_t e = pe[r];
       for (int64_t k = 0; k < len; ++k) {
         if (k > 0 && ch->col[a + k] == ch->col[a + k - 1]) {
           ++hcnt[e - 1];
@@ -776,7 +786,11 @@ int batch_setup_ff(pb_batch *b, const pb_channels *const *chs, int n, const Batc
         hcnt[e] = 1;
         ++e;
       }
-      for (; e < e0 + b->lenp[so + r]; ++e) hpidx[e] = (uint32_t)(so + r);
+      for (; e < pe[r + 1]; ++e) {
+        hpidx[e] = (uint32_t)(so + r);
+        hcst[e] = 0;
+        hcnt[e] = 0;
+      }
     }
     std::vector<Item> hit;
     std::vector<int32_t> hptr;
@@ -788,13 +802,13 @@ int batch_setup_ff(pb_batch *b, const pb_channels *const *chs, int n, const Batc
       hkc[r] = make_short4((short)(ik / (N2 * N3)), (short)((ik / N3) % N2), (short)(ik % N3), 0);
     }
     const size_t nq = (size_t)ch->nq * ch->nmodes;
-    PB_CUDA(cudaMemcpyAsync(tcol, hcol.data(), sizeof(uint32_t) * nc, cudaMemcpyHostToDevice, st));
-    PB_CUDA(cudaMemcpyAsync(tg2, hg2.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, st));
+    PB_CUDA(cudaMemcpyAsync(tcol, hcol.get(), sizeof(uint32_t) * nc, cudaMemcpyHostToDevice, st));
+    PB_CUDA(cudaMemcpyAsync(tg2, hg2.get(), sizeof(double) * nc, cudaMemcpyHostToDevice, st));
     PB_CUDA(cudaMemcpyAsync(titems, hit.data(), sizeof(Item) * hit.size(), cudaMemcpyHostToDevice, st));
     PB_CUDA(cudaMemcpyAsync(titem_ptr, hptr.data(), sizeof(int32_t) * hptr.size(), cudaMemcpyHostToDevice, st));
-    PB_CUDA(cudaMemcpyAsync(tpcst, hcst.data(), sizeof(int64_t) * np, cudaMemcpyHostToDevice, st));
-    PB_CUDA(cudaMemcpyAsync(tpcnt, hcnt.data(), np, cudaMemcpyHostToDevice, st));
-    PB_CUDA(cudaMemcpyAsync(b->pidx + poff, hpidx.data(), sizeof(uint32_t) * np, cudaMemcpyHostToDevice, st));
+    PB_CUDA(cudaMemcpyAsync(tpcst, hcst.get(), sizeof(int64_t) * np, cudaMemcpyHostToDevice, st));
+    PB_CUDA(cudaMemcpyAsync(tpcnt, hcnt.get(), np, cudaMemcpyHostToDevice, st));
+    PB_CUDA(cudaMemcpyAsync(b->pidx + poff, hpidx.get(), sizeof(uint32_t) * np, cudaMemcpyHostToDevice, st));
     PB_CUDA(cudaMemcpyAsync(om, ch->omega.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, st));
     PB_CUDA(cudaMemcpyAsync(ep, ch->eps.data(), sizeof(double) * ns_i, cudaMemcpyHostToDevice, st));
     PB_CUDA(cudaMemcpyAsync(kc, hkc.data(), sizeof(short4) * ns_i, cudaMemcpyHostToDevice, st));
@@ -928,7 +942,7 @@ extern "C" int pb_batch_arena_bytes(const pb_channels *const *chs, int32_t n, co
       int64_t nent = 0;
       for (int64_t l : lenp) nent += l;
       const BatchTiles T = batch_tiles_for(chs, n, prec, opts ? opts->layout : 0, nent);
-      *bytes = batch_layout_ff(chs, n, ns, nent, batch_items_count(lenp, kBatchMinItem), prec == 2, T).total;
+      *bytes = batch_layout_ff(chs, n, ns, nent, batch_items_count(lenp, kBatchMinItem), prec == 2, T, lenp).total;
     } else {
       pb_batch_opts o{};
       if (opts) o = *opts;
@@ -994,7 +1008,7 @@ extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const p
       int64_t nent = 0;
       for (int64_t l : b->lenp) nent += l;
       const BatchTiles T = batch_tiles_for(chs, n, b->prec, o.layout, nent);
-      const BatchLayoutFF LF = batch_layout_ff(chs, n, ns, nent, b->nitems_cap, b->prec == 2, T);
+      const BatchLayoutFF LF = batch_layout_ff(chs, n, ns, nent, b->nitems_cap, b->prec == 2, T, b->lenp);
       if (bytes < LF.total) {
         delete b;
         return set_error(PB_ENOMEM, "pb_batch_create: arena of %zu bytes is smaller than the %zu needed", bytes,
