@@ -1133,15 +1133,19 @@ extern "C" int pb_batch_create(const pb_channels *const *chs, int32_t n, const p
       hin[i].nm = ch->nmodes;
       hin[i].doff = i == 0 ? 0 : hin[i - 1].doff + (long long)chs[i - 1]->nstate * hin[i - 1].npp * hin[i - 1].nm;
       for (int64_t s = 0; s < ch->nstate; ++s) hcs[b->soff[i] + s] = c * norm;
+      // the instance's rows in parallel from their first padded channel (hg2 is zero-filled)
+      std::vector<int64_t> rs((size_t)ch->nstate + 1, coff);
+      for (int64_t s = 0; s < ch->nstate; ++s) rs[s + 1] = rs[s] + b->lenp[b->soff[i] + s];
+#pragma omp parallel for schedule(dynamic, 16)
       for (int64_t s = 0; s < ch->nstate; ++s) {
-        const int64_t a = ch->row_ptr[s], len = ch->row_ptr[s + 1] - a, lp = b->lenp[b->soff[i] + s];
+        const int64_t a = ch->row_ptr[s], len = ch->row_ptr[s + 1] - a, c0 = rs[s], lp = rs[s + 1] - c0;
         for (int64_t k = 0; k < len; ++k) {
-          hcol[coff + k] = (uint32_t)ch->col[a + k] | ((uint32_t)ch->nu[a + k] << kPartnerBits);
-          hg2[coff + k] = (float)ch->g2[a + k];
+          hcol[c0 + k] = (uint32_t)ch->col[a + k] | ((uint32_t)ch->nu[a + k] << kPartnerBits);
+          hg2[c0 + k] = (float)ch->g2[a + k];
         }
-        for (int64_t k = len; k < lp; ++k) hcol[coff + k] = (uint32_t)s;
-        coff += lp;
+        for (int64_t k = len; k < lp; ++k) hcol[c0 + k] = (uint32_t)s;
       }
+      coff = rs[ch->nstate];
       // device: (w, N) table, padded FP32 table, state records
       std::vector<short4> hkc((size_t)ch->nstate);
       const int N2 = ch->nk[1], N3 = ch->nk[2];
