@@ -36,7 +36,9 @@
  *    Device calls are asynchronous on that stream unless stated.
  *  - Concurrency: the device calls on one pb_dev (or pb_batch) share that handle's scratch
  *    regions, so they must not overlap on the GPU: issue them on one stream, or order the
- *    streams.  Separate handles are independent.
+ *    streams.  A handle also keeps host state (its call-graph cache and the launch settings
+ *    a call records), so calls on one handle from several host threads must be serialised by
+ *    the caller.  Separate handles are independent.
  *  - Ownership: the library owns only its opaque host handles (pb_channels, pb_dev).  All
  *    device memory is the caller's: pb_dev_create carves its arrays out of one caller-
  *    allocated device arena and never frees it; vectors passed to the compute calls are
