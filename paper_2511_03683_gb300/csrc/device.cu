@@ -299,7 +299,7 @@ Layout make_layout(const pb_channels *ch, const Plan &P, const Plan *S, int vari
   L.rp_real = take(sizeof(int64_t) * (ns + 1));
   L.vjpG = take(sizeof(float2) * 3 * ns);
   L.g2tab = take(sizeof(float4) * 2 * 4 * ns);
-  L.vecs = take(sizeof(double) * 8 * ns);
+  L.vecs = take(sizeof(double) * 9 * ns);
   L.total = o;
   return L;
 }
@@ -463,7 +463,7 @@ struct pb_dev {
   int64_t *rp_real = nullptr;  // unpadded CSR row offsets [ns+1]
   float2 *vjpG = nullptr;      // adjoint gather table [ns][3]
   float4 *g2tab = nullptr;     // |g|^2-gradient stage table [4 stages][ns][2]
-  double *vecs = nullptr;      // 8 scratch vectors of nstate doubles (adjoint stages)
+  double *vecs = nullptr;      // 9 scratch vectors of nstate doubles (adjoint stages, the step's f)
   // paper layout (PB_VARIANT_PAPER)
   uint32_t *hcol = nullptr;
   double *hg2 = nullptr;
@@ -1732,7 +1732,8 @@ int replay(pb_dev *d, int kind, const void *a, const void *b, const void *c, con
   return PB_OK;
 }
 
-enum { kCallCollision = 1, kCallRates = 2, kCallTransport = 3, kCallRk4Host = 4, kCallTransportHost = 5 };
+enum { kCallCollision = 1, kCallRates = 2, kCallTransport = 3, kCallRk4Host = 4, kCallTransportHost = 5,
+       kCallVjp = 6, kCallVjpDefer = 7 };
 
 // page-locked host memory (pinned or registered), which a graph's copy nodes may address
 bool pinned_host(const void *p) {
@@ -2250,8 +2251,7 @@ extern "C" int pb_collision_vjp(pb_dev *d, const double *f, const double *lam, d
 
 namespace {
 // one RK4 adjoint step; defer: the |g|^2 gradient goes to the pair accumulators (FF merged)
-int rk4_vjp_impl(pb_dev *d, const double *f, double *lam, double dt, double *grad_g2, bool defer, void *stream) {
-  cudaStream_t st = (cudaStream_t)stream;
+int rk4_vjp_seq(pb_dev *d, const double *f, double *lam, double dt, double *grad_g2, bool defer, cudaStream_t st) {
   const bool want_g2 = grad_g2 || defer;
   const int64_t ns = d->ns;
   double *u2 = d->vecs, *u3 = u2 + ns, *u4 = u3 + ns, *acc = u4 + ns, *ga = acc + ns, *gb = ga + ns, *mu0 = gb + ns,
@@ -2299,6 +2299,18 @@ int rk4_vjp_impl(pb_dev *d, const double *f, double *lam, double dt, double *gra
   if (defer) return d->mixed() ? g2accg_launch<4>(d, st) : g2acc_launch<4>(d, st);
   if (grad_g2 && (rc = g2grad_launch<4>(d, grad_g2, st))) return rc;
   return PB_OK;
+}
+
+// The step's launches (about 17) replayed from a graph per (lam, dt, grad_g2); f, which a
+// backward pass changes from step to step, is first copied into the handle's ninth vector.
+int rk4_vjp_impl(pb_dev *d, const double *f, double *lam, double dt, double *grad_g2, bool defer, void *stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  double *fc = d->vecs + 8 * d->ns;
+  PB_CUDA(cudaMemcpyAsync(fc, f, sizeof(double) * (size_t)d->ns, cudaMemcpyDeviceToDevice, st));
+  uint64_t dtk = 0;
+  std::memcpy(&dtk, &dt, sizeof dtk);
+  return replay(d, defer ? kCallVjpDefer : kCallVjp, lam, (const void *)(uintptr_t)dtk, grad_g2, nullptr, st,
+                [&](cudaStream_t s) -> int { return rk4_vjp_seq(d, fc, lam, dt, grad_g2, defer, s); });
 }
 
 int rk4_vjp_check(pb_dev *d, const double *f, const double *lam, double dt, const char *who) {
