@@ -459,6 +459,10 @@ struct pb_dev {
   // the next tile sweep takes the tile list from its end (the RK4 stages alternate, so that each
   // sweep starts on the tiles the previous one left in L2)
   int rev = 0;
+  // pb_iter_transport: page-locked host copies of the residual numbers of two successive
+  // passes (allocated on the first solve), so that the next pass runs while one is checked
+  double *hres = nullptr;
+  cudaEvent_t hres_ev[2] = {nullptr, nullptr};
   float2 *tc32 = nullptr;
   int64_t *rp_real = nullptr;  // unpadded CSR row offsets [ns+1]
   float2 *vjpG = nullptr;      // adjoint gather table [ns][3]
@@ -1318,6 +1322,9 @@ extern "C" void pb_dev_destroy(pb_dev *d) {
   if (d->rk_exec) cudaGraphExecDestroy(d->rk_exec);
   d->drop_call_graphs();
   if (d->cap) cudaStreamDestroy(d->cap);
+  if (d->hres) cudaFreeHost(d->hres);
+  for (cudaEvent_t e : d->hres_ev)
+    if (e) cudaEventDestroy(e);
   delete d;
 }
 
@@ -1733,7 +1740,7 @@ int replay(pb_dev *d, int kind, const void *a, const void *b, const void *c, con
 }
 
 enum { kCallCollision = 1, kCallRates = 2, kCallTransport = 3, kCallRk4Host = 4, kCallTransportHost = 5,
-       kCallVjp = 6, kCallVjpDefer = 7 };
+       kCallVjp = 6, kCallVjpDefer = 7, kCallSolvePass = 8 };
 
 // page-locked host memory (pinned or registered), which a graph's copy nodes may address
 bool pinned_host(const void *p) {
@@ -1949,20 +1956,37 @@ extern "C" int pb_iter_transport(pb_dev *d, const double *f0, const double *vel3
   const int g3 = (int)((3 * d->ns + 255) / 256);
   dev::k_tr_init<<<g3, 256, 0, st>>>(d->tau, vel3, (int)d->ns, d->Fa, d->Fff);
   PB_LAUNCHED("k_tr_init");
-  double *Fcur = d->Fa, *Fnext = d->Fb;
+  if (!d->hres) {
+    PB_CUDA(cudaMallocHost((void **)&d->hres, 6 * sizeof(double)));
+    for (cudaEvent_t &e : d->hres_ev) PB_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  double *Fbuf[2] = {d->Fa, d->Fb};  // pass i reads Fbuf[i % 2] and writes Fbuf[(i + 1) % 2]
+  // pass i: replayed from one of two graphs (Fa -> Fb, Fb -> Fa), its residual numbers copied
+  // to hres[3 (i % 2)] and an event recorded after them
+  auto enqueue = [&](int32_t i) -> int {
+    const double *Fc = Fbuf[i & 1];
+    double *Fn = Fbuf[(i + 1) & 1];
+    const int r = replay(d, kCallSolvePass, vel3, Fc, Fn, nullptr, st,
+                         [&](cudaStream_t s) -> int { return transport_pass(d, d->Fff, vel3, Fc, Fn, d->Fff, s); });
+    if (r) return r;
+    PB_CUDA(cudaMemcpyAsync(d->hres + 3 * (i & 1), d->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PB_CUDA(cudaEventRecord(d->hres_ev[i & 1], st));
+    return PB_OK;
+  };
+  // one pass ahead: pass i + 1 is queued before pass i's residual is read.  The extra pass after
+  // the converged one only writes the other buffer (and the scratch), not the result.
   double res = INFINITY;
   int32_t it = 0;
-  double h[3] = {0, 0, 0};
+  if (maxit > 0 && (rc = enqueue(0))) return rc;
   while (it < maxit) {
-    if ((rc = transport_pass(d, d->Fff, vel3, Fcur, Fnext, d->Fff, st))) return rc;
-    PB_CUDA(cudaMemcpyAsync(h, d->scal, sizeof h, cudaMemcpyDeviceToHost, st));
-    PB_CUDA(cudaStreamSynchronize(st));
-    std::swap(Fcur, Fnext);
+    if (it + 1 < maxit && (rc = enqueue(it + 1))) return rc;
+    PB_CUDA(cudaEventSynchronize(d->hres_ev[it & 1]));
+    res = d->hres[3 * (it & 1)];
     ++it;
-    res = h[0];
     if (!std::isfinite(res)) break;
     if (res <= tol) break;
   }
+  double *Fcur = Fbuf[it & 1];  // the iterate after `it` passes
   PB_CUDA(cudaMemcpyAsync(F3, Fcur, sizeof(double) * 3 * d->ns, cudaMemcpyDeviceToDevice, st));
   PB_CUDA(cudaStreamSynchronize(st));
   if (iters) *iters = it;
