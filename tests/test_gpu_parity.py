@@ -350,6 +350,35 @@ def test_transport_map_and_solve(pb):
     assert nrel(F, Fr) <= 1e-9
 
 
+def test_transport_solve_counts_its_passes(pb):
+    """pb_iter_transport queues each pass before it checks the previous one's residual: with
+    maxit 0 it returns F^0 = tau v, with tol 0 it stops after exactly maxit passes and returns
+    the iterate of that many device passes (bit for bit) with its residual, and a tolerance met
+    by the first pass stops after one pass."""
+    import torch
+
+    m = synth.make_window4(12)
+    o = oracle.Oracle(m)
+    dev = pb.Device(pb.Channels.from_model(m), transport=True)
+    fe = T(o.window_values(m.f_fermi(m.emin() - 0.2)))
+    v = T(o.window_values(m.vel))
+    F0, it0, _, ok0 = dev.transport(fe, v, tol=0.0, maxit=0)
+    assert it0 == 0 and not ok0
+    F0 = F0.clone()
+    res = T(np.zeros(3))
+    for k in (1, 2, 3, 6):
+        Fk, itk, rk, okk = dev.transport(fe, v, tol=0.0, maxit=k)
+        assert itk == k and not okk
+        G = F0.clone()
+        for _ in range(k):
+            G = dev.transport_iterate(v, G.clone(), resid=res)
+        assert torch.equal(Fk, G)
+        assert rk == res.cpu().numpy()[0]
+    F1, it1, r1, ok1 = dev.transport(fe, v, tol=1e30, maxit=10)
+    assert it1 == 1 and ok1
+    assert torch.equal(F1, dev.transport_iterate(v, F0.clone()))
+
+
 def test_transport_iterate_replays_graphs(pb):
     """pb_transport_iterate replays one captured graph per argument set (the last two kept): an
     iteration that alternates between two buffers (with and without the residual output),
