@@ -304,7 +304,11 @@ int pb_rtbte_rk4_host(pb_dev *dev, const double *f_host_in, double *f_host_out, 
  * from F^0 = tau v until max|F^{i+1}-F^i| <= tol * max|F^{i+1}|.
  * f0: device double[nstate]; vel3, F3: device double[nstate][3].  On return (stream
  * synchronised) *iters holds the iterations done and *resid the last relative change;
- * PB_ENOCONV if maxit was reached first (F3 then holds the last iterate).
+ * PB_ENOCONV if maxit was reached first (F3 then holds the last iterate).  Each pass is
+ * replayed from a CUDA graph, and the next pass is queued before the host reads the previous
+ * pass's residual (one extra pass runs after the converged one; it changes neither F3 nor the
+ * result); the residual numbers go through 48 bytes of page-locked host memory that the
+ * handle allocates on its first solve and frees in pb_dev_destroy.
  * Needs a pb_dev created with opts.transport != 0. */
 int pb_iter_transport(pb_dev *dev, const double *f0, const double *vel3, double tol, int32_t maxit, double *F3,
                       int32_t *iters, double *resid, void *stream);
