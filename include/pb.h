@@ -359,7 +359,10 @@ int pb_collision_vjp(pb_dev *dev, const double *f, const double *lam, double *gr
 
 /* Discrete adjoint of one classic RK4 step from f (device double[nstate]): on entry lam holds
  * dL/df_{n+1}, on return dL/df_n; grad_g2 (or NULL) accumulates dL/dg2 as above.  The four
- * stage inputs are recomputed from f. */
+ * stage inputs are recomputed from f.  f is first copied into the handle; the step's launches
+ * are then replayed from a CUDA graph kept per (lam, dt, grad_g2) in the handle's call-graph
+ * cache (as is pb_rtbte_rk4_vjp_defer's, per (lam, dt)), so a backward pass that keeps one lam
+ * vector replays one graph whatever its f. */
 int pb_rtbte_rk4_vjp(pb_dev *dev, const double *f, double *lam, double dt, double *grad_g2, void *stream);
 
 /* The same RK4 adjoint step with the |g|^2 gradient deferred.  Eq. 2 is linear in each
