@@ -263,9 +263,10 @@ int pb_dev_get_info(const pb_dev *dev, pb_dev_info *info);
 
 /* Eq. 2: dfdt[s] = I_s[f] for every window state.  f, dfdt: device double[nstate].
  * The call's launches are replayed from a CUDA graph kept per argument set (captured on first
- * use; the handle keeps its six most recent call graphs, shared with pb_scatter_rates and
- * pb_transport_iterate); when `stream` is itself being captured, the launches are recorded into
- * the caller's capture. */
+ * use; the handle keeps its twelve most recent call graphs, shared with pb_scatter_rates,
+ * pb_transport_iterate, the host-buffer calls, the RK4 adjoint steps and the transport solver's
+ * passes); when `stream` is itself being captured, the launches are recorded into the caller's
+ * capture. */
 int pb_collision(pb_dev *dev, const double *f, double *dfdt, void *stream);
 
 /* Measurement aid (the paper has no counterpart): the average device duration of the

@@ -491,7 +491,7 @@ struct pb_dev {
   cudaGraphExec_t rk_exec = nullptr;
   // graphs of the short launch sequences of pb_collision, pb_scatter_rates and
   // pb_transport_iterate, one per call kind and argument set, the last kGraphs kept
-  static constexpr int kGraphs = 6;
+  static constexpr int kGraphs = 12;
   struct CallGraph {
     int kind = 0;
     const void *a = nullptr, *b = nullptr, *c = nullptr, *e = nullptr;

@@ -379,11 +379,30 @@ def test_transport_solve_counts_its_passes(pb):
     assert torch.equal(F1, dev.transport_iterate(v, F0.clone()))
 
 
+def test_call_graph_cache_evicts_and_recaptures(pb):
+    """More argument sets than the handle keeps graphs for (twelve): collision calls into 15
+    output buffers, twice round, so that every graph is evicted and captured again, all give the
+    first call's integral bit for bit."""
+    import torch
+
+    m = synth.make_window4(12)
+    o = oracle.Oracle(m)
+    dev = pb.Device(pb.Channels.from_model(m))
+    f = T(np.random.default_rng(71).uniform(0, 1, o.nstate))
+    ref = dev.collision(f).cpu().numpy()
+    outs = [torch.empty(o.nstate, dtype=torch.float64, device="cuda") for _ in range(15)]
+    for _ in range(2):
+        for out in outs:
+            out.zero_()
+            dev.collision(f, out=out)
+            assert np.array_equal(out.cpu().numpy(), ref)
+
+
 def test_transport_iterate_replays_graphs(pb):
-    """pb_transport_iterate replays one captured graph per argument set (the last two kept): an
-    iteration that alternates between two buffers (with and without the residual output),
-    interleaved with host-buffer passes (a third argument set, so graphs are evicted and captured
-    again), gives the same iterates and residuals bit for bit on both paths."""
+    """pb_transport_iterate replays one captured graph per argument set: an iteration that
+    alternates between two buffers (with and without the residual output), interleaved with
+    host-buffer passes (another argument set), gives the same iterates and residuals bit for bit
+    on both paths."""
     import torch
 
     m = synth.make_window4(12)
