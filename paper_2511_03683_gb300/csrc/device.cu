@@ -489,6 +489,7 @@ struct pb_dev {
   // RK4 graph cache
   cudaStream_t cap = nullptr;
   cudaGraphExec_t rk_exec = nullptr;
+  cudaGraphExec_t rk_exec_in = nullptr;  // the same step preceded by the stage-input conversion of f
   // graphs of the short launch sequences of pb_collision, pb_scatter_rates and
   // pb_transport_iterate, one per call kind and argument set, the last kGraphs kept
   static constexpr int kGraphs = 12;
@@ -1320,6 +1321,7 @@ extern "C" int pb_dev_selftest_wait(pb_dev *d, int32_t wait_us, void *stream) {
 extern "C" void pb_dev_destroy(pb_dev *d) {
   if (!d) return;
   if (d->rk_exec) cudaGraphExecDestroy(d->rk_exec);
+  if (d->rk_exec_in) cudaGraphExecDestroy(d->rk_exec_in);
   d->drop_call_graphs();
   if (d->cap) cudaStreamDestroy(d->cap);
   if (d->hres) cudaFreeHost(d->hres);
@@ -1584,27 +1586,41 @@ int rk4_launches(pb_dev *d, double *f, double dt, cudaStream_t st) {
   return rc;
 }
 
+void drop_rk_graphs(pb_dev *d) {
+  if (d->rk_exec) cudaGraphExecDestroy(d->rk_exec);
+  if (d->rk_exec_in) cudaGraphExecDestroy(d->rk_exec_in);
+  d->rk_exec = d->rk_exec_in = nullptr;
+}
+
+// two graphs of one RK4 step on f: rk_exec (its stage input already in yff, as the last stage
+// of a step leaves it) and rk_exec_in (the conversion of f first, for a call's first step)
 int ensure_rk_graph(pb_dev *d, double *f, double dt) {
-  if (d->rk_exec && d->rk_f == f && d->rk_dt == dt) return PB_OK;
-  if (d->rk_exec) {
-    cudaGraphExecDestroy(d->rk_exec);
-    d->rk_exec = nullptr;
-  }
+  if (d->rk_exec && d->rk_exec_in && d->rk_f == f && d->rk_dt == dt) return PB_OK;
+  drop_rk_graphs(d);
   if (!d->cap) PB_CUDA(cudaStreamCreateWithFlags(&d->cap, cudaStreamNonBlocking));
-  PB_CUDA(cudaStreamBeginCapture(d->cap, cudaStreamCaptureModeThreadLocal));
-  int rc = rk4_launches(d, f, dt, d->cap);
-  cudaGraph_t graph = nullptr;
-  cudaError_t e = cudaStreamEndCapture(d->cap, &graph);
-  if (rc) {
-    if (graph) cudaGraphDestroy(graph);
-    return rc;
-  }
-  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-  e = cudaGraphInstantiate(&d->rk_exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) {
-    d->rk_exec = nullptr;
-    return cuda_fail(e, "cudaGraphInstantiate");
+  for (int with_input = 0; with_input < 2; ++with_input) {
+    PB_CUDA(cudaStreamBeginCapture(d->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = with_input ? stage_input(d, f, d->cap) : PB_OK;
+    if (rc == PB_OK) rc = rk4_launches(d, f, dt, d->cap);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(d->cap, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      drop_rk_graphs(d);
+      return rc;
+    }
+    if (e != cudaSuccess) {
+      drop_rk_graphs(d);
+      return cuda_fail(e, "cudaStreamEndCapture");
+    }
+    cudaGraphExec_t &exec = with_input ? d->rk_exec_in : d->rk_exec;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      exec = nullptr;
+      drop_rk_graphs(d);
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
   }
   d->rk_f = f;
   d->rk_dt = dt;
@@ -1851,8 +1867,8 @@ extern "C" int pb_rtbte_rk4_step(pb_dev *d, double *f, double dt, int32_t nsteps
   cudaStream_t st = (cudaStream_t)stream;
   int rc = ensure_rk_graph(d, f, dt);
   if (rc) return rc;
-  if ((rc = stage_input(d, f, st))) return rc;
-  for (int32_t i = 0; i < nsteps; ++i) PB_CUDA(cudaGraphLaunch(d->rk_exec, st));
+  PB_CUDA(cudaGraphLaunch(d->rk_exec_in, st));  // the first step converts f itself
+  for (int32_t i = 1; i < nsteps; ++i) PB_CUDA(cudaGraphLaunch(d->rk_exec, st));
   return PB_OK;
 }
 
@@ -2378,10 +2394,7 @@ extern "C" int pb_dev_set_g2(pb_dev *d, const double *g2, void *stream) {
     // the caller may give the two stored copies of a channel different values: the symmetric
     // tiles (which take a pair's reverse from its own entry) no longer apply; stream rows
     d->sym = false;
-    if (d->rk_exec) {
-      cudaGraphExecDestroy(d->rk_exec);
-      d->rk_exec = nullptr;
-    }
+    drop_rk_graphs(d);
   }
   d->drop_call_graphs();  // the calls' launch sequences are captured again on their next use
   return coef_setup(d, st);
