@@ -286,8 +286,10 @@ int pb_dev_time_sweep(pb_dev *dev, const double *f, int32_t nlaunch, int32_t ord
 int pb_scatter_rates(pb_dev *dev, const double *f, double *inv_tau, void *stream);
 
 /* nsteps classic RK4 steps of the field-free rt-BTE df/dt = I[f] (Eq. 1 with F = 0),
- * step dt (fs), in place on the device vector f.  Steps are replayed from a CUDA graph
- * captured on first use (the capture uses an internal stream). */
+ * step dt (fs), in place on the device vector f.  Steps are replayed from CUDA graphs captured
+ * on first use per (f, dt) (the capture uses an internal stream): the call's first step from a
+ * graph that also converts f into the sweeps' stage input, the others from one that takes it
+ * from the step before. */
 int pb_rtbte_rk4_step(pb_dev *dev, double *f, double dt, int32_t nsteps, void *stream);
 
 /* Same as pb_rtbte_rk4_step with HOST buffers: copies f_host_in (double[nstate]) to the
