@@ -1504,6 +1504,10 @@ int launch_stream(pb_dev *d, int mode, const double *fd, const float2 *fff, cuda
 
 int fin_grid(const pb_dev *d) { return d->nfin_blocks; }
 
+// the tile epilogues: 8 states per CTA unless 32 per CTA still give four CTAs per SM (with 32
+// per CTA a 40^3 step had 149 CTAs for 152 SMs, and the C32 RK4 step ran 14% slower)
+bool fin_small(const pb_dev *d) { return (d->ns + 31) / 32 < 4 * (int64_t)d->sm_count; }
+
 // ydst: where a stage writes the next stage's input (default d->y)
 template <int STAGE>
 void launch_fin(pb_dev *d, const double *ysrc, double *out, double *f, double dt, cudaStream_t st,
@@ -1519,14 +1523,14 @@ void launch_fin(pb_dev *d, const double *ysrc, double *out, double *f, double dt
         dev::ItemSrc{d->variant == PB_VARIANT_PAPER ? d->t_item_ptr : d->item_ptr, d->part}, (int)d->ns, d->c, d->R, ysrc,
                                                                     out, f, d->acc, y, d->yff, dt);
   else if (d->sym && d->c32)
-    if (d->ns <= 2048)
+    if (fin_small(d))
       dev::k_fin_c32<STAGE, false, 8><<<(int)((d->ns + 7) / 8), 256, 0, st>>>(
           (const float *)d->tpart, d->td.nb, d->td.nsp, (int)d->ns, d->c, ysrc, out, f, d->acc, y, d->yff, dt);
     else
       dev::k_fin_c32<STAGE><<<(int)((d->ns + 31) / 32), 256, 0, st>>>(
           (const float *)d->tpart, d->td.nb, d->td.nsp, (int)d->ns, d->c, ysrc, out, f, d->acc, y, d->yff, dt);
   else if (d->sym)
-    if (d->ns <= 2048)  // few states: more, smaller CTAs
+    if (fin_small(d))
       dev::k_fin_tiles<STAGE, false, 8><<<(int)((d->ns + 7) / 8), 256, 0, st>>>(
           dev::TileSrc{d->tpart, d->td.nb, d->td.nsp}, (int)d->ns, d->c, d->R, ysrc, out, f, d->acc, y, d->yff, dt);
     else
@@ -1844,10 +1848,18 @@ int rates_seq(pb_dev *d, const double *f, double *inv_tau, cudaStream_t st) {
   if (d->variant == PB_VARIANT_LITERAL || d->mixed())
     dev::k_fin_rate<true><<<fin_grid(d), kFinBlock, 0, st>>>(dev::ItemSrc{d->fwd_item_ptr(), d->part}, (int)d->ns,
                                                              d->mixed() ? d->gscale() : d->c, d->R, inv_tau);
+  else if (d->sym && d->c32 && fin_small(d))
+    dev::k_fin_c32<-1, true, 8><<<(int)((d->ns + 7) / 8), 256, 0, st>>>((const float *)d->tpart, d->td.nb, d->td.nsp,
+                                                                       (int)d->ns, d->c, nullptr, inv_tau, nullptr,
+                                                                       nullptr, nullptr, nullptr, 0.0);
   else if (d->sym && d->c32)
     dev::k_fin_c32<-1, true><<<(int)((d->ns + 31) / 32), 256, 0, st>>>((const float *)d->tpart, d->td.nb, d->td.nsp,
                                                                        (int)d->ns, d->c, nullptr, inv_tau, nullptr,
                                                                        nullptr, nullptr, nullptr, 0.0);
+  else if (d->sym && fin_small(d))
+    dev::k_fin_tiles<-1, true, 8><<<(int)((d->ns + 7) / 8), 256, 0, st>>>(
+        dev::TileSrc{d->tpart, d->td.nb, d->td.nsp}, (int)d->ns, d->c, d->R, nullptr, inv_tau, nullptr, nullptr, nullptr,
+        nullptr, 0.0);
   else if (d->sym)
     dev::k_fin_tiles<-1, true><<<(int)((d->ns + 31) / 32), 256, 0, st>>>(
         dev::TileSrc{d->tpart, d->td.nb, d->td.nsp}, (int)d->ns, d->c, d->R, nullptr, inv_tau, nullptr, nullptr, nullptr,
