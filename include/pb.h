@@ -179,7 +179,12 @@ typedef struct pb_dev_opts {
                                 4-channel groups per lane, 3 through L1 with one channel per lane;
                                 one channel per lane with lazily renormalised float-float sums: 4 one
                                 1024-thread CTA per SM with F in shared memory (5 if F does not fit) and
-                                the next trip in registers, 5 the same through L1, 6 = 3 with lazy sums */
+                                the next trip in registers, 5 the same through L1, 6 = 3 with lazy sums;
+                                7 row blocks on complete branch-merged float-float rows: a warp takes
+                                four rows and one segment of their partners, each partner's F (shared
+                                memory) read once for the four rows, the weights through a per-warp
+                                ring of asynchronous copies, one 768-thread CTA per SM (PB_EINVAL where
+                                the rows do not qualify or F and the rings exceed shared memory) */
   int32_t transport_ctas;    /* resident 256-thread transport CTAs per SM, 1..8 (0 = 8 with L1 gathers) */
   int32_t channel_per_lane;  /* FP32/BF16/FP16 sweep shape: 0 automatic (= 5 when the channel list fills at
                                 least 85% of the (state, branch, partner) slots, else 4); one channel per

@@ -51,7 +51,7 @@ struct Layout {
   size_t rp, item_ptr, items, col, coefA, coefB, g2, wt, eps, kc, R, omega, tab, part, acc, y, yff, fstage, Fa, Fb,
       Fff, tau, invtau, red, scal, obs, g2lo, gstate, tab32, col16, rp_real, vjpG, g2tab, vecs, hcol, hg2, hA, hB, sc,
       entries, hitems, titems, t_item_ptr, err, citems, citem_ptr, cpart, ccoefA, ccoefB, sidx16, sidx32, pcstart,
-      pcnt, srp, gitems, tiles, tcoef, tpart, g2d, gditems, gdptr, gacc, gaccg, total;
+      pcnt, srp, gitems, tiles, tcoef, tpart, g2d, gditems, gdptr, gacc, gaccg, trptr, trpart, total;
 };
 
 struct Plan {
@@ -219,7 +219,7 @@ TileDims tile_dims(int64_t ns) {
 // tile_entry: bytes per pair of the symmetric tiles (16 float-float, 8 for the FP32 tiles of C32)
 Layout make_layout(const pb_channels *ch, const Plan &P, const Plan *S, int variant, bool transport,
                    int nfin_blocks, bool sym = false, const GDense &gd = GDense(), bool gacc = false,
-                   size_t tile_entry = sizeof(float4)) {
+                   size_t tile_entry = sizeof(float4), int tr_nseg = 0) {
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -300,8 +300,38 @@ Layout make_layout(const pb_channels *ch, const Plan &P, const Plan *S, int vari
   L.vjpG = take(sizeof(float2) * 3 * ns);
   L.g2tab = take(sizeof(float4) * 2 * 4 * ns);
   L.vecs = take(sizeof(double) * 9 * ns);
+  L.trptr = take(tr_nseg ? sizeof(int32_t) * (ns + 1) : 0);
+  L.trpart = take(tr_nseg ? sizeof(Part4) * ns * (size_t)tr_nseg : 0);
   L.total = o;
   return L;
+}
+
+// Segments of the row-block transport sweep (k_stream_tr_rows, pb_dev_opts.transport_gather 7)
+// over complete rows: enough
+// (row block, segment) items to give every warp of one wave about one item, each segment at most
+// dev::kTrSegMax partners (the lazy float-float sums' bound) and, where the rows allow, at least
+// 256; seglen a multiple of 32.  nseg = 0 where the sweep is not asked for or does not apply (rows not
+// complete and branch-merged, another variant, or F of every state and the weight rings too large
+// for shared memory).
+struct TrRows {
+  int nseg = 0, seglen = 0;
+};
+TrRows tr_rows_for(int64_t ns, int sm, bool transport, bool merged, bool complete, int variant,
+                   const pb_dev_opts &o) {
+  TrRows t;
+  if (!transport || o.transport_gather != 7 || !merged || !complete || variant != PB_VARIANT_FF ||
+      o.dense_rows == 2 || ns < 1 ||
+      ns > (int64_t)1 << 20 || dev::tr_rows_smem((int)ns) > (size_t)227 * 1024)
+    return t;
+  const int64_t nwarps = (int64_t)std::max(sm, 1) * (dev::kTrThreads / 32);
+  const int64_t nblk = (ns + dev::kTrRows - 1) / dev::kTrRows;
+  int64_t nseg = std::max<int64_t>((ns + dev::kTrSegMax - 1) / dev::kTrSegMax,
+                                   std::min<int64_t>(nwarps / nblk, (ns + 255) / 256));
+  nseg = std::max<int64_t>(nseg, 1);
+  const int64_t seglen = ((ns + nseg - 1) / nseg + 31) / 32 * 32;
+  t.seglen = (int)seglen;
+  t.nseg = (int)((ns + seglen - 1) / seglen);
+  return t;
 }
 
 int cuda_fail(cudaError_t e, const char *what) {
@@ -466,6 +496,10 @@ struct pb_dev {
   float2 *tc32 = nullptr;
   int64_t *rp_real = nullptr;  // unpadded CSR row offsets [ns+1]
   float2 *vjpG = nullptr;      // adjoint gather table [ns][3]
+  int tr_nseg = 0, tr_seglen = 0;  // row-block transport sweep: segments per row, partners per segment
+  int32_t *trptr = nullptr;        // its partial ranges per row (r * tr_nseg) for the finaliser
+  Part4 *trpart = nullptr;         // its (row, segment) partials [ns][tr_nseg]
+  size_t smem_Frows = 0;           // its shared-memory F
   float4 *g2tab = nullptr;     // |g|^2-gradient stage table [4 stages][ns][2]
   double *vecs = nullptr;      // 9 scratch vectors of nstate doubles (adjoint stages, the step's f)
   // paper layout (PB_VARIANT_PAPER)
@@ -590,8 +624,8 @@ int resolve_opts(const pb_channels *ch, const pb_dev_opts *opts, int sm_count, p
   if (d.stream_mode < 0 || d.stream_mode > 2) return set_error(PB_EINVAL, "pb_dev: stream_mode must be 0..2");
   if (d.channel_per_lane < 0 || d.channel_per_lane > 5)
     return set_error(PB_EINVAL, "pb_dev: channel_per_lane must be 0..5");
-  if (d.transport_gather < 0 || d.transport_gather > 6 || d.transport_ctas < 0 || d.transport_ctas > 8)
-    return set_error(PB_EINVAL, "pb_dev: transport_gather must be 0..6 and transport_ctas 0..8");
+  if (d.transport_gather < 0 || d.transport_gather > 7 || d.transport_ctas < 0 || d.transport_ctas > 8)
+    return set_error(PB_EINVAL, "pb_dev: transport_gather must be 0..7 and transport_ctas 0..8");
   if (d.item_channels < 0 || d.item_channels % 64 != 0)
     return set_error(PB_EINVAL, "pb_dev: item_channels must be a non-negative multiple of 64");
   if (d.item_channels == 0 && d.stream_mode == 2) d.item_channels = 2048;  // bulk ring fits shared memory
@@ -785,8 +819,10 @@ extern "C" int pb_dev_arena_bytes(const pb_channels *ch, const pb_dev_opts *opts
     if (c32 && !sym)
       return set_error(PB_EINVAL, "pb_dev: the FP32 coefficient tiles (C32) need the symmetric tiles: a "
                                   "closure-checked list whose rows are complete or miss few partners (or dense_rows 3)");
+    const TrRows tr = tr_rows_for(P.ns, sm, o.transport != 0, merged, complete, o.variant, o);
     *bytes = make_layout(ch, P, merged ? &S : nullptr, o.variant, o.transport != 0, nfin, sym,
-                         gdense_for(ch, o, sm), o.adjoint != 0, c32 ? sizeof(float2) : sizeof(float4)).total;
+                         gdense_for(ch, o, sm), o.adjoint != 0, c32 ? sizeof(float2) : sizeof(float4), tr.nseg)
+                 .total;
   } catch (const std::bad_alloc &) {
     return set_error(PB_ENOMEM, "pb_dev_arena_bytes: out of host memory");
   }
@@ -874,8 +910,11 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->gd_npp = gd.npp;
   d->gd_nitems = (int)gd.nitems;
   d->gd_bytes = gd.bytes;
+  const TrRows trr = tr_rows_for(d->ns, sm, d->transport, merged, complete, o.variant, o);
+  d->tr_nseg = trr.nseg;
+  d->tr_seglen = trr.seglen;
   d->L = make_layout(ch, P, merged ? &S : nullptr, o.variant, d->transport, d->nfin_blocks, d->sym, gd,
-                     o.adjoint != 0, c32 ? sizeof(float2) : sizeof(float4));
+                     o.adjoint != 0, c32 ? sizeof(float2) : sizeof(float4), trr.nseg);
   if (arena_bytes < d->L.total) {
     const size_t need = d->L.total;
     delete d;
@@ -923,6 +962,10 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   d->col16 = d->ns <= 65536 ? (uint16_t *)(A + L.col16) : nullptr;
   d->rp_real = (int64_t *)(A + L.rp_real);
   d->vjpG = (float2 *)(A + L.vjpG);
+  if (d->tr_nseg) {
+    d->trptr = (int32_t *)(A + L.trptr);
+    d->trpart = (Part4 *)(A + L.trpart);
+  }
   d->g2tab = (float4 *)(A + L.g2tab);
   if (d->mixed() && o.adjoint) d->gaccg = (double *)(A + L.gaccg);
   d->vecs = (double *)(A + L.vecs);
@@ -1028,6 +1071,17 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
   }
   // complete rows: the FF sweeps take partners from entry positions (needs f in shared memory)
   d->dense = merged && complete && o.dense_rows != 2 && d->variant == PB_VARIANT_FF && d->smem_f && !d->bulk;
+  // the row-block transport sweep (one CTA per SM, each partner's F read once for four rows):
+  // measured slower than shape 4 on GB300 (64 against 57.8 us per 40^3 iteration), so only on request
+  const bool rows_fit = d->tr_nseg && dev::tr_rows_smem((int)d->ns) <= (size_t)smem_optin;
+  if (d->transport && d->dense && rows_fit && o.transport_gather == 7) {
+    d->tr_shape = 7;
+  } else if (d->transport && o.transport_gather == 7) {
+    delete d;
+    return set_error(PB_EINVAL, "pb_dev_create: transport_gather 7 needs complete, branch-merged float-float rows "
+                                "whose F (24 bytes per state) and weight rings fit in shared memory");
+  }
+  d->smem_Frows = d->tr_shape == 7 ? dev::tr_rows_smem((int)d->ns) : 0;
   d->ctas_tr = d->smem_F ? (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(228 * 1024) / (d->smem_F + 1024))) : 8;
   if (o.transport_ctas > 0) d->ctas_tr = std::min(d->ctas_tr, o.transport_ctas);
   if (!d->smem_F && o.transport_ctas > 0) d->ctas_tr = o.transport_ctas;
@@ -1101,6 +1155,11 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
         plan_items(rpd, gd.item, gi, gp);
         UP(d->gd_items, gi.data(), sizeof(Item) * gi.size());
         UP(d->gd_item_ptr, gp.data(), sizeof(int32_t) * gp.size());
+      }
+      if (d->tr_nseg) {  // the row-block transport sweep's partials: row r owns r * nseg .. (r + 1) * nseg
+        std::vector<int32_t> tp((size_t)d->ns + 1);
+        for (int64_t r = 0; r <= d->ns; ++r) tp[(size_t)r] = (int32_t)(r * d->tr_nseg);
+        UP(d->trptr, tp.data(), sizeof(int32_t) * tp.size());
       }
       UP(d->rp_real, ch->row_ptr.data(), sizeof(int64_t) * (d->ns + 1));
       UP(d->item_ptr, W.item_ptr.data(), sizeof(int32_t) * (d->ns + 1));
@@ -1246,6 +1305,9 @@ extern "C" int pb_dev_create(const pb_channels *ch, const pb_dev_opts *opts, voi
     cudaFuncSetAttribute(dev::k_stream_tr<true, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_F);
     cudaFuncSetAttribute(dev::k_stream_tr<true, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_F);
   }
+  if (d->smem_Frows > 48 * 1024)
+    cudaFuncSetAttribute(dev::k_stream_tr_rows<dev::kTrRows>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)d->smem_Frows);
   if (d->smem_F1k > 48 * 1024) {
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaFuncSetAttribute(dev::k_stream_tr_lane<uint32_t, 1024, true, true, true>, A, (int)d->smem_F1k);
@@ -1693,7 +1755,14 @@ int transport_pass(pb_dev *d, const float2 *Fin_ff, const double *vel3, const do
   const float4 *W4 = (const float4 *)d->wt;
   const int64_t need = (d->nitems * 32 + dev::kBlock - 1) / dev::kBlock;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)d->sm_count * d->ctas_tr));
-  if (d->smem_F) {
+  const bool rows = d->tr_shape == 7;
+  if (rows) {
+    const int64_t nit = (d->ns + dev::kTrRows - 1) / dev::kTrRows * (int64_t)d->tr_nseg;
+    constexpr int wpc = dev::kTrThreads / 32;
+    const int gr = (int)std::max<int64_t>(1, std::min<int64_t>((nit + wpc - 1) / wpc, d->sm_count));
+    dev::k_stream_tr_rows<dev::kTrRows><<<gr, dev::kTrThreads, d->smem_Frows, st>>>(
+        d->wt, (const long long *)d->srp, Fin_ff, (int)d->ns, d->tr_nseg, d->tr_seglen, d->trpart);
+  } else if (d->smem_F) {
     if (d->sidx16) dev::k_stream_tr<true, uint16_t><<<grid, dev::kBlock, d->smem_F, st>>>(d->items, n, W4, d->sidx16, Fin_ff, (int)d->ns, d->part);
     else           dev::k_stream_tr<true, uint32_t><<<grid, dev::kBlock, d->smem_F, st>>>(d->items, n, W4, d->sidx32, Fin_ff, (int)d->ns, d->part);
   } else if (d->tr_lane) {
@@ -1704,8 +1773,8 @@ int transport_pass(pb_dev *d, const float2 *Fin_ff, const double *vel3, const do
     else           dev::k_stream_tr<false, uint32_t><<<grid, dev::kBlock, 0, st>>>(d->items, n, W4, d->sidx32, Fin_ff, (int)d->ns, d->part);
   }
   PB_LAUNCHED("k_stream_tr");
-  dev::k_fin_tr<<<fin_grid(d), kFinBlock, 0, st>>>(d->item_ptr, d->part, (int)d->ns, d->tau, vel3, Fold, Fnew,
-                                                    Fnew_ff, d->red);
+  dev::k_fin_tr<<<fin_grid(d), kFinBlock, 0, st>>>(rows ? d->trptr : d->item_ptr, rows ? d->trpart : d->part,
+                                                    (int)d->ns, d->tau, vel3, Fold, Fnew, Fnew_ff, d->red);
   PB_LAUNCHED("k_fin_tr");
   dev::k_red_final<<<1, 256, 0, st>>>(d->red, d->nfin_blocks, res3 ? res3 : d->scal);
   PB_LAUNCHED("k_red_final");

@@ -936,6 +936,122 @@ __global__ void __launch_bounds__(NT, NT == 1024 ? 1 : 8) k_stream_tr_lane(const
   }
 }
 
+// Transport sweep over complete rows in row blocks.  A warp takes RB consecutive rows and one
+// segment of their partner states, consecutive lanes on consecutive partners: each partner's F
+// (three float-float values, read from shared memory) serves the RB rows, and each weight row is
+// read once, 256 contiguous bytes per warp and trip.  The weights reach shared memory through a
+// per-warp ring of D trips filled by asynchronous copies (cp.async, 8 bytes per lane and row, each
+// lane reading back only what it copied itself), so D - 1 trips of loads stay in flight without
+// holding registers.  Work items are numbered segment-major (item = seg * nblk + block): in a
+// launch of one wave a CTA's warps need F only over one or two segments, and only that range is
+// staged.  Each lane adds at most seglen / 32 <= 64 terms per sum with lazy renormalisation; the
+// warp's RB x 3 sums are reduce-scattered over its lanes (full float-float additions), and the
+// (row, segment) totals go to part[row * nseg + seg] in FP64, which the transport finaliser adds
+// over a row's nseg segments.  W + srp[r] is row r's first weight, its partners in state order
+// (complete rows).  Shared memory: F of up to ns states (24 bytes each), then the rings.
+constexpr int kTrRows = 4;          // rows per warp item
+constexpr int kTrSegMax = 2048;     // longest segment (64 terms per lane)
+constexpr int kTrThreads = 768;     // one CTA per SM, 24 warps, up to 85 registers a thread
+constexpr int kTrRing = 4;          // trips per warp ring (three in flight)
+__host__ __device__ constexpr size_t tr_rows_ring_offset(int ns) {
+  return ((size_t)ns * 3 * sizeof(float2) + 127) / 128 * 128;
+}
+__host__ __device__ constexpr size_t tr_rows_smem(int ns) {
+  return tr_rows_ring_offset(ns) + (size_t)(kTrThreads / 32) * kTrRing * kTrRows * 32 * sizeof(float2);
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int RB>
+__global__ void __launch_bounds__(kTrThreads, 1) k_stream_tr_rows(const float2 *__restrict__ W,
+                                                                  const long long *__restrict__ srp,
+                                                                  const float2 *__restrict__ F, int ns, int nseg,
+                                                                  int seglen, Part4 *__restrict__ part) {
+  static_assert(RB % 2 == 0, "rows are reduced in pairs");
+  constexpr int D = kTrRing;
+  extern __shared__ __align__(128) unsigned char trsm[];
+  float2 *Fs = (float2 *)trsm;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float2 *ring = (float2 *)(trsm + tr_rows_ring_offset(ns)) + (size_t)wib * D * RB * 32 + lane;  // [D][RB][32]
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  const int nblk = (ns + RB - 1) / RB, nit = nblk * nseg;
+  const int wpb = (int)(blockDim.x >> 5), i0 = (int)blockIdx.x * wpb;
+  // the partner range this CTA reads: its items' segments when the launch is one wave
+  int cbeg = 0, cend = ns;
+  if (nit <= nwarps) {
+    if (i0 >= nit) return;
+    const int i1 = min(nit, i0 + wpb) - 1;
+    cbeg = (i0 / nblk) * seglen;
+    cend = min(ns, (i1 / nblk + 1) * seglen);
+  }
+  for (int i = threadIdx.x; i < 3 * (cend - cbeg); i += blockDim.x) Fs[i] = F[3 * cbeg + i];
+  __syncthreads();
+  for (int it = i0 + wib; it < nit; it += nwarps) {
+    const int seg = it / nblk, r0 = (it - seg * nblk) * RB;
+    const int cs = seg * seglen + lane, c1 = min(ns, (seg + 1) * seglen);
+    const int ntrip = (c1 - seg * seglen + 31) / 32;
+    // rows past the end read the last row again (their sums are not written)
+    const long long b0 = srp[r0];
+    const float2 *__restrict__ W0 = W + b0;
+    int ro[RB];  // row offsets from the first row, in entries
+#pragma unroll
+    for (int i = 0; i < RB; ++i) ro[i] = (int)(srp[min(r0 + i, ns - 1)] - b0);
+    auto fill = [&](int t) {  // this lane's weights of trip t into ring slot t % D (one group per call)
+      const int c = cs + 32 * t;
+      if (t < ntrip && c < c1) {
+#pragma unroll
+        for (int i = 0; i < RB; ++i) cp_async8(ring + ((t % D) * RB + i) * 32, W0 + ro[i] + c);
+      }
+      cp_async_commit();
+    };
+#pragma unroll
+    for (int t = 0; t < D - 1; ++t) fill(t);
+    float acc[RB][6];
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc[i][k] = 0.f;
+    for (int t = 0; t < ntrip; ++t) {
+      fill(t + D - 1);
+      cp_async_wait<D - 1>();  // trip t's group is complete
+      const int c = cs + 32 * t;
+      if (c < c1) {
+        const float2 *Fp = Fs + 3 * (c - cbeg);
+        const float2 fx = Fp[0], fy = Fp[1], fz = Fp[2];
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+          const float2 w = ring[((t % D) * RB + i) * 32];
+          ff_mac_lazy(acc[i][0], acc[i][1], fx, w.x, w.y);
+          ff_mac_lazy(acc[i][2], acc[i][3], fy, w.x, w.y);
+          ff_mac_lazy(acc[i][4], acc[i][5], fz, w.x, w.y);
+        }
+      }
+    }
+    cp_async_wait<0>();  // nothing of this item left in flight before the ring is reused
+    // two rows (six sums, two zeros) at a time: lanes 4k .. 4k + 3 end with sum k of the pair
+#pragma unroll
+    for (int q = 0; q < RB / 2; ++q) {
+      float2 v[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int i = 2 * q + m / 3, k = m % 3;
+        v[m] = m < 6 ? make_float2(acc[i][2 * k], acc[i][2 * k + 1]) : make_float2(0.f, 0.f);
+      }
+      ff_reduce_scatter<8, 16>(v, lane);
+      const int m = lane >> 2, row = r0 + 2 * q + m / 3;
+      if ((lane & 3) == 0 && m < 6 && row < ns)
+        (&part[(long long)row * nseg + seg].x)[m % 3] = ff_to_double(v[0].x, v[0].y);
+    }
+  }
+}
+
 // ------------------------------------------------------------ mixed precision (FP32 / BF16 / FP16 |g|^2)
 //
 // The literal per-channel form of Eq. 2 in FP32: stream |g|^2 (FP32, BF16 or scaled FP16) and the packed

@@ -126,7 +126,7 @@ def test_builder_cutoffs_match_oracle_count(pb, g2_min, nsig):
 
 @pytest.mark.parametrize("field,bad", [("variant", 9), ("merge_branches", 3), ("dense_rows", 4), ("tile_sweep", 9),
                                        ("tile_sweep", -1), ("stream_mode", 3), ("channel_per_lane", 6),
-                                       ("transport_gather", 7), ("ctas_per_sm", 9), ("item_channels", 100),
+                                       ("transport_gather", 8), ("ctas_per_sm", 9), ("item_channels", 100),
                                        ("adjoint", 2)])
 def test_device_options_are_checked_on_the_host(pb, field, bad):
     """pb_dev_arena_bytes resolves and checks pb_dev_opts without touching a GPU: every field

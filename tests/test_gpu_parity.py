@@ -308,7 +308,7 @@ def test_time_sweep_measures_without_changing_results(pb):
         dev.time_sweep(T(f), 2, order=2)
 
 
-@pytest.mark.parametrize("gather", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("gather", [1, 2, 3, 4, 5, 6, 7])
 def test_transport_sweep_shapes(pb, gather):
     """Every transport sweep shape (shared-memory or L1 gathers, 256- or 1024-thread CTAs,
     eager or lazily renormalised float-float sums) on a ragged case: rows of many lengths
@@ -321,6 +321,37 @@ def test_transport_sweep_shapes(pb, gather):
     Fin = np.random.default_rng(6).normal(size=(o.nstate, 3))
     ref, _ = o.transport_map(f0, v, Fin)
     assert nrel(dev.transport_map(T(f0), T(v), T(Fin)).cpu().numpy(), ref) <= TOL
+
+
+@pytest.mark.parametrize("name", ["tiny4", "odd81", "odd99", "win16", "tiny8"])
+def test_transport_row_blocks(pb, name):
+    """The row-block transport sweep (transport_gather 7): four rows per warp item, a ragged last
+    block where nstate is not a multiple of four (81, 99), one segment of partners per item or
+    several (324 states: two, the second shorter; 1024: four), against the oracle's transport
+    map and against the one-row-per-item shape 4 (the automatic one)."""
+    m = SMALL[name]()
+    o = oracle.Oracle(m)
+    ch = pb.Channels.from_model(m)
+    f0 = o.window_values(m.f_fermi(m.emin() - 0.2))
+    v = o.window_values(m.vel)
+    Fin = np.random.default_rng(16).normal(size=(o.nstate, 3))
+    ref, _ = o.transport_map(f0, v, Fin)
+    got = {}
+    for gather in (0, 7, 4):
+        dev = pb.Device(ch, transport=True, transport_gather=gather)
+        got[gather] = dev.transport_map(T(f0), T(v), T(Fin)).cpu().numpy()
+        assert nrel(got[gather], ref) <= TOL
+    assert np.array_equal(got[0], got[4])  # the automatic shape
+    assert nrel(got[7], got[4]) <= 1e-14
+
+
+def test_transport_row_blocks_need_complete_rows(pb):
+    """transport_gather 7 on a list whose rows miss partners (|g|^2 cutoff) is PB_EINVAL at creation."""
+    m = synth.make_window4(12)
+    ch = pb.Channels.from_model(m, g2_min=1e-3)
+    with pytest.raises(pb.PBError):
+        pb.Device(ch, transport=True, transport_gather=7)
+    pb.Device(ch, transport=True)  # the automatic shape takes any list
 
 
 def test_transport_map_and_solve(pb):
