@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--variant", default="ff")
     ap.add_argument("--tile-sweep", type=int, default=0, help="pb_dev_opts.tile_sweep of the bench device")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="pb_dev_opts.ctas_per_sm of the bench device")
+    ap.add_argument("--transport-gather", type=int, default=0,
+                    help="pb_dev_opts.transport_gather of the bench device (the transport sweep shape)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
@@ -652,7 +654,8 @@ def run_ours(args):
     ch = pb.Channels.from_model(m)
     build_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    dev = pb.Device(ch, variant=args.variant, transport=True, tile_sweep=args.tile_sweep, ctas_per_sm=args.ctas_per_sm)
+    dev = pb.Device(ch, variant=args.variant, transport=True, tile_sweep=args.tile_sweep, ctas_per_sm=args.ctas_per_sm,
+                    transport_gather=args.transport_gather)
     torch.cuda.synchronize()
     create_s = time.perf_counter() - t0
     ids = ch.state_ids()
@@ -810,7 +813,8 @@ def run_ours(args):
     if rank == 0:
         cfg = workload_config(args.workload)
         cfg.update({"nstate": ns, "channels": nch, "variant": args.variant, "tile_sweep": args.tile_sweep,
-                    "ctas_per_sm": args.ctas_per_sm, "l2": "inputs larger than L2 "
+                    "ctas_per_sm": args.ctas_per_sm, "transport_gather": args.transport_gather,
+                    "l2": "inputs larger than L2 "
                     f"({dev.bytes_per_channel * nch / 1e9:.2f} GB streamed per sweep vs 0.13 GB L2)"
                     if args.workload == "window40" else "inputs fit in L2 (latency/parity workload)",
                     "parallelism": f"{ws} independent replica(s)"})
