@@ -169,6 +169,32 @@ def test_adjoint_accumulators_are_sized_per_state_pair(pb):
     assert abs(grow - 24 * ch.nstate ** 2) <= 4096  # up to the alignment of the arena regions
 
 
+def test_row_block_transport_partials_are_sized_per_row_and_segment(pb):
+    """transport_gather 7 reserves one FP64 (x, y, z) partial of 32 bytes per (row, segment) and
+    a row index of nstate + 1 int32 on complete rows with transport, and nothing otherwise: not
+    without transport, not on the automatic shape, not on a list whose rows miss partners."""
+    import ctypes
+
+    L = pb.lib()
+
+    def arena(ch, **kw):
+        o = pb._DevOpts()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        n = ctypes.c_size_t(0)
+        assert L.pb_dev_arena_bytes(ch._h, ctypes.byref(o), ctypes.byref(n)) == pb.PB_OK
+        return n.value
+
+    ch = pb.Channels.from_model(synth.make_window4(16))  # complete rows, 324 states
+    ns = ch.nstate
+    grow = arena(ch, transport=1, transport_gather=7) - arena(ch, transport=1)
+    nseg = round(grow / (32 * ns))  # the segments (two at 324 states on any SM count of 3 or more)
+    assert nseg >= 1 and abs(grow - (32 * ns * nseg + 4 * (ns + 1))) <= 2048  # up to the regions' alignment
+    assert arena(ch, transport_gather=7) == arena(ch)
+    cut = pb.Channels.from_model(synth.make_window4(12), g2_min=1e-3)
+    assert arena(cut, transport=1, transport_gather=7) == arena(cut, transport=1)
+
+
 def test_fp16_variant_sizes_like_bf16(pb):
     """The FP16 |g|^2 variant (h16) keeps 2 bytes per value like BF16 (g16): the same arena."""
     import ctypes
