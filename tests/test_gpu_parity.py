@@ -952,6 +952,33 @@ def test_full_size_transport_map_sampled(big):
     assert np.abs(out[rows] - ref).max() <= TOL * np.abs(ref).max()
 
 
+def test_full_size_transport_row_blocks_sampled(pb, big):
+    """The row-block transport sweep (transport_gather 7) at 40^3: 1189 blocks of four rows, three
+    segments of 1600 partners (the last 1556), 3567 items in one wave of 24-warp CTAs, each CTA
+    staging F over its one or two segments; sampled rows against the oracle and all rows against
+    the automatic shape."""
+    m, o, dev = big
+    rb = pb.Device(dev.channels, variant="ff", transport=True, transport_gather=7)
+    f0 = o.window_values(m.f_fermi(o.model.emin() - 0.2))
+    v = o.window_values(m.vel)
+    Fin = np.random.default_rng(17).normal(size=(o.nstate, 3))
+    out = rb.transport_map(T(f0), T(v), T(Fin)).cpu().numpy()
+    rows = np.unique(np.concatenate([np.arange(3, o.nstate, 197), [o.nstate - 1]]))
+    ref, _ = o.transport_map(f0, v, Fin, rows=rows)
+    assert np.abs(out[rows] - ref).max() <= TOL * np.abs(ref).max()
+    assert nrel(out, dev.transport_map(T(f0), T(v), T(Fin)).cpu().numpy()) <= 1e-14
+
+
+def test_full_size_paper_layout_sampled(pb, big):
+    """The paper's own layout (half list, sc_col, signed target gather) at 40^3 on sampled rows."""
+    m, o, dev = big
+    pap = pb.Device(dev.channels, variant="paper")
+    f = o.window_values(m.f_hot())
+    rows = np.unique(np.concatenate([np.arange(0, o.nstate, 61), [o.nstate - 1]]))
+    ref, ab = o.collision(f, rows=rows, with_abs=True)
+    check_I(pap.collision(T(f)).cpu().numpy()[rows], ref, ab)
+
+
 def test_full_size_1000_steps_two_arithmetics(pb, big):
     """The 40^3 workload's dynamics: 1000 RK4 steps of 1 fs with the float-float default and
     with native FP64 FMAs (independent arithmetic) agree, and the particle number sum_s f_s is
