@@ -2808,67 +2808,79 @@ __global__ void k_fin_rate(SRC src, int ns, double c, const double *__restrict__
 }
 
 // F_new = tau (v + sum W F); ff copy for the next pass; per-block max |dF| and max |F|.
+// max over the block of (a, b), both non-negative: warp shuffles, then one step through shared
+// memory (exact, so the order does not matter); the result is valid in thread 0
+__device__ __forceinline__ double2 block_max2(double a, double b) {
+  __shared__ double2 wm[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a = fmax(a, __shfl_xor_sync(0xFFFFFFFFu, a, o));
+    b = fmax(b, __shfl_xor_sync(0xFFFFFFFFu, b, o));
+  }
+  if (lane == 0) wm[wid] = make_double2(a, b);
+  __syncthreads();
+  double2 v = make_double2(0.0, 0.0);
+  if (wid == 0) {
+    v = lane < (int)((blockDim.x + 31) >> 5) ? wm[lane] : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v.x = fmax(v.x, __shfl_xor_sync(0xFFFFFFFFu, v.x, o));
+      v.y = fmax(v.y, __shfl_xor_sync(0xFFFFFFFFu, v.y, o));
+    }
+  }
+  return v;
+}
+
 __global__ void __launch_bounds__(256) k_fin_tr(const int *__restrict__ item_ptr, const Part4 *__restrict__ part,
                                                 int ns, const double *__restrict__ tau,
                                                 const double *__restrict__ vel3, const double *__restrict__ Fold,
                                                 double *__restrict__ Fnew, float2 *__restrict__ Fff,
                                                 double2 *__restrict__ red) {
-  __shared__ double sd[256], sf[256];
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   double dm = 0.0, fm = 0.0;
   if (r < ns) {
+    // the row's own inputs first, so that their latency overlaps that of the partials
+    const double t = tau[r];
+    double vv[3], fo[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      vv[a] = vel3[3 * r + a];
+      fo[a] = Fold ? Fold[3 * r + a] : 0.0;
+    }
     double X = 0.0, Y = 0.0, Z = 0.0;
-    for (int i = item_ptr[r]; i < item_ptr[r + 1]; ++i) {
+    const int i1 = item_ptr[r + 1];
+    for (int i = item_ptr[r]; i < i1; ++i) {
       const Part4 v = part[i];
       X += v.x;
       Y += v.y;
       Z += v.z;
     }
     const double S[3] = {X, Y, Z};
-    const double t = tau[r];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double Fn = t * (vel3[3 * r + a] + S[a]);
-      if (Fold) dm = fmax(dm, fabs(Fn - Fold[3 * r + a]));
+      const double Fn = t * (vv[a] + S[a]);
+      if (Fold) dm = fmax(dm, fabs(Fn - fo[a]));
       fm = fmax(fm, fabs(Fn));
       Fnew[3 * r + a] = Fn;
       Fff[3 * r + a] = ff_split(Fn);
     }
   }
-  sd[threadIdx.x] = dm;
-  sf[threadIdx.x] = fm;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      sd[threadIdx.x] = fmax(sd[threadIdx.x], sd[threadIdx.x + o]);
-      sf[threadIdx.x] = fmax(sf[threadIdx.x], sf[threadIdx.x + o]);
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) red[blockIdx.x] = make_double2(sd[0], sf[0]);
+  const double2 m = block_max2(dm, fm);
+  if (threadIdx.x == 0) red[blockIdx.x] = m;
 }
 
 __global__ void k_red_final(const double2 *__restrict__ red, int n, double *__restrict__ out) {
-  __shared__ double sd[256], sf[256];
   double d = 0.0, m = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     d = fmax(d, red[i].x);
     m = fmax(m, red[i].y);
   }
-  sd[threadIdx.x] = d;
-  sf[threadIdx.x] = m;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      sd[threadIdx.x] = fmax(sd[threadIdx.x], sd[threadIdx.x + o]);
-      sf[threadIdx.x] = fmax(sf[threadIdx.x], sf[threadIdx.x + o]);
-    }
-    __syncthreads();
-  }
+  const double2 v = block_max2(d, m);
   if (threadIdx.x == 0) {
-    out[0] = sf[0] > 0.0 ? sd[0] / sf[0] : 0.0;
-    out[1] = sd[0];
-    out[2] = sf[0];
+    out[0] = v.y > 0.0 ? v.x / v.y : 0.0;
+    out[1] = v.x;
+    out[2] = v.y;
   }
 }
 
